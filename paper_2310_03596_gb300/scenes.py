@@ -1,0 +1,204 @@
+"""Seeded synthetic particle scenes for the impact and collapse workloads.
+
+This module is the one piece shared by the CPU oracle's tests and the CUDA path. It builds, from a
+seed, what a user hands the solver at initialisation: particle positions, velocities, volumes,
+material ids and ownership labels, plus the fixed bucket grid, walls and materials of the scene.
+It holds none of the method's arithmetic (no hashing, sorting, fluxes, integration or balancing).
+
+Random numbers come from SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014; the finaliser constants are Vigna's published ones), evaluated per
+particle as a counter-based generator: draw k of particle `id` is mix(seed ^ (id * GOLDEN) +
+(k + 1) * GOLDEN). Draws 0-2 jitter the three axes, draw 3 picks a random label.
+
+Workloads (sizes as stated by the workload definitions; dx lattice spacing, h = 1.3 dx):
+  cube_impact       16^3 aluminium cube, dx 1 mm, -100 m/s onto a wall at z = 0, one label
+  taylor_bar        aluminium rod r 5 mm x 40 mm, dx 0.125 mm (1.61 M), 200 m/s onto a wall, K = 4
+  projectile_plate  steel sphere r 5 mm at 1000 m/s onto an aluminium plate 60x60x10 mm, dx 0.2 mm,
+                    K = 8 equal-count x-slabs, two materials
+  collapse_block    aluminium block 0.4 x 0.2 x 0.1 m at dx 0.5 mm (64 M) on a floor, gravity, K = 16
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+# Materials: (rho0 kg/m^3, bulk modulus K Pa, shear modulus G Pa, yield stress Y Pa)
+ALUMINIUM = (2700.0, 70.0e9, 26.0e9, 300.0e6)
+STEEL = (7850.0, 160.0e9, 80.0e9, 1.0e9)
+
+
+def splitmix64_draw(seed: int, ids: np.ndarray, k: int) -> np.ndarray:
+    """Draw number k (0-based) of the counter-based SplitMix64 stream of each particle id."""
+    with np.errstate(over="ignore"):
+        s = np.uint64(seed) ^ (ids.astype(np.uint64) * GOLDEN)
+        z = s + np.uint64(k + 1) * GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def unit_double(z: np.ndarray) -> np.ndarray:
+    """Top 53 bits of a 64-bit draw as a double in [0, 1)."""
+    return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+@dataclasses.dataclass
+class Scene:
+    """Initial particle set and the fixed setting it lives in (SoA, numpy, FP64 positions)."""
+
+    name: str
+    pos: np.ndarray            # (N, 3) float64
+    vel: np.ndarray            # (N, 3) float64
+    vol: np.ndarray            # (N,) float64
+    material: np.ndarray       # (N,) uint8, index into materials
+    label: np.ndarray          # (N,) uint8, ownership label in [0, K)
+    materials: list            # [(rho0, K, G, Y), ...]
+    h: float
+    cfl: float
+    grid_lo: tuple             # lower corner of the fixed bucket grid
+    grid_dims: tuple           # buckets per axis; bucket side is 2h
+    walls: list                # [(axis, position), ...] rigid mirror planes
+    gravity: tuple
+    K: int
+    swap_period: int
+    alpha: float
+    steps: int
+    dx: float
+
+    @property
+    def n(self) -> int:
+        return int(self.pos.shape[0])
+
+
+def _jitter(pos: np.ndarray, ids: np.ndarray, seed: int, amp: float) -> np.ndarray:
+    out = pos.copy()
+    for ax in range(3):
+        u = unit_double(splitmix64_draw(seed, ids, ax))
+        out[:, ax] += amp * (2.0 * u - 1.0)
+    return out
+
+
+def _random_labels(ids: np.ndarray, seed: int, K: int) -> np.ndarray:
+    z = splitmix64_draw(seed, ids, 3)
+    return ((z >> np.uint64(32)) % np.uint64(K)).astype(np.uint8)
+
+
+def _grid_around(pos: np.ndarray, h: float, margin_lo, margin_hi):
+    cell = 2.0 * h
+    lo = pos.min(axis=0) - np.asarray(margin_lo, dtype=np.float64)
+    hi = pos.max(axis=0) + np.asarray(margin_hi, dtype=np.float64)
+    dims = tuple(int(math.ceil((hi[a] - lo[a]) / cell)) for a in range(3))
+    return tuple(float(v) for v in lo), dims
+
+
+def _lattice(nx: int, ny: int, nz: int, dx: float, origin=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """Cell-centred lattice points origin + (i + 1/2) dx, x fastest."""
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    p = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1).astype(np.float64)
+    return (p + 0.5) * dx + np.asarray(origin, dtype=np.float64)
+
+
+def cube_impact(n_side: int = 16, dx: float = 1.0e-3, seed: int = 0, speed: float = 100.0,
+                jitter: float = 0.01, steps: int = 10, K: int = 1) -> Scene:
+    """Elastic-plastic aluminium cube falling at `speed` onto a rigid wall z = 0 it touches."""
+    h = 1.3 * dx
+    pos = _lattice(n_side, n_side, n_side, dx)
+    ids = np.arange(pos.shape[0], dtype=np.uint64)
+    if jitter:
+        pos = _jitter(pos, ids, seed, jitter * dx)
+    n = pos.shape[0]
+    vel = np.zeros((n, 3))
+    vel[:, 2] = -speed
+    lo, dims = _grid_around(pos, h, (4 * h, 4 * h, 4 * h), (4 * h, 4 * h, 4 * h))
+    label = _random_labels(ids, seed, K) if K > 1 else np.zeros(n, np.uint8)
+    return Scene("cube_impact", pos, vel, np.full(n, dx ** 3), np.zeros(n, np.uint8), label,
+                 [ALUMINIUM], h, 0.3, lo, dims, [(2, 0.0)], (0.0, 0.0, 0.0), K, 1, 0.1, steps, dx)
+
+
+def taylor_bar(dx: float = 0.125e-3, radius: float = 5.0e-3, length: float = 40.0e-3,
+               speed: float = 200.0, seed: int = 1, K: int = 4, swap_period: int = 1,
+               steps: int = 100) -> Scene:
+    """Aluminium rod along z, base on the rigid wall z = 0, moving at -speed along z."""
+    h = 1.3 * dx
+    nr = int(round(radius / dx))
+    nl = int(round(length / dx))
+    pos = _lattice(2 * nr, 2 * nr, nl, dx, origin=(-nr * dx, -nr * dx, 0.0))
+    keep = pos[:, 0] ** 2 + pos[:, 1] ** 2 <= radius ** 2
+    pos = pos[keep]
+    ids = np.arange(pos.shape[0], dtype=np.uint64)
+    pos = _jitter(pos, ids, seed, 0.01 * dx)
+    n = pos.shape[0]
+    vel = np.zeros((n, 3))
+    vel[:, 2] = -speed
+    m = 4 * h
+    lo, dims = _grid_around(pos, h, (m, m, m), (m, m, m))
+    return Scene("taylor_bar", pos, vel, np.full(n, dx ** 3), np.zeros(n, np.uint8),
+                 _random_labels(ids, seed, K), [ALUMINIUM], h, 0.3, lo, dims, [(2, 0.0)],
+                 (0.0, 0.0, 0.0), K, swap_period, 0.1, steps, dx)
+
+
+def projectile_plate(dx: float = 0.2e-3, radius: float = 5.0e-3, plate=(60.0e-3, 60.0e-3, 10.0e-3),
+                     speed: float = 1000.0, seed: int = 2, K: int = 8, swap_period: int = 20,
+                     steps: int = 500) -> Scene:
+    """Steel sphere just above an aluminium plate (top face z = 0), moving at -speed along z."""
+    h = 1.3 * dx
+    px, py, pz = (int(round(v / dx)) for v in plate)
+    plate_pos = _lattice(px, py, pz, dx, origin=(-px * dx / 2, -py * dx / 2, -pz * dx))
+    nr = int(round(radius / dx))
+    sph = _lattice(2 * nr, 2 * nr, 2 * nr, dx, origin=(-nr * dx, -nr * dx, -nr * dx))
+    sph = sph[(sph ** 2).sum(axis=1) <= radius ** 2]
+    sph[:, 2] += radius + dx
+    pos = np.concatenate([plate_pos, sph])
+    mat = np.concatenate([np.zeros(plate_pos.shape[0], np.uint8), np.ones(sph.shape[0], np.uint8)])
+    ids = np.arange(pos.shape[0], dtype=np.uint64)
+    pos = _jitter(pos, ids, seed, 0.01 * dx)
+    n = pos.shape[0]
+    vel = np.zeros((n, 3))
+    vel[mat == 1, 2] = -speed
+    # equal-count slabs along x
+    order = np.argsort(pos[:, 0], kind="stable")
+    label = np.empty(n, np.uint8)
+    label[order] = (np.arange(n) * K // n).astype(np.uint8)
+    m = 8.0e-3
+    lo, dims = _grid_around(pos, h, (m, m, m), (m, m, m))
+    return Scene("projectile_plate", pos, vel, np.full(n, dx ** 3), mat, label, [ALUMINIUM, STEEL],
+                 h, 0.3, lo, dims, [], (0.0, 0.0, 0.0), K, swap_period, 0.1, steps, dx)
+
+
+def collapse_block(dx: float = 0.5e-3, size=(0.4, 0.2, 0.1), seed: int = 4, K: int = 16,
+                   swap_period: int = 10, steps: int = 200, gravity: float = 9.81) -> Scene:
+    """Aluminium block at rest on a rigid floor z = 0 under gravity, random labels."""
+    h = 1.3 * dx
+    nx, ny, nz = (int(round(v / dx)) for v in size)
+    pos = _lattice(nx, ny, nz, dx)
+    ids = np.arange(pos.shape[0], dtype=np.uint64)
+    pos = _jitter(pos, ids, seed, 0.01 * dx)
+    n = pos.shape[0]
+    m = 4 * h
+    lo, dims = _grid_around(pos, h, (m, m, m), (m, m, m))
+    return Scene("collapse_block", pos, np.zeros((n, 3)), np.full(n, dx ** 3), np.zeros(n, np.uint8),
+                 _random_labels(ids, seed, K), [ALUMINIUM], h, 0.3, lo, dims, [(2, 0.0)],
+                 (0.0, 0.0, -gravity), K, swap_period, 0.1, steps, dx)
+
+
+def adjoint_cube(n_side: int = 64, seed: int = 3, steps: int = 200) -> Scene:
+    """The cube impact scaled up, used for the gradient workload."""
+    s = cube_impact(n_side=n_side, seed=seed, steps=steps)
+    s.name = "adjoint_cube"
+    return s
+
+
+WORKLOADS = {
+    "cube_impact": cube_impact,
+    "taylor_bar": taylor_bar,
+    "projectile_plate": projectile_plate,
+    "adjoint_cube": adjoint_cube,
+    "collapse_block": collapse_block,
+}
