@@ -1,0 +1,211 @@
+/* gsph.h - C-ABI of the GB300-native (sm_103a) particle-decomposition Gamma-SPH-ALE hot path.
+ *
+ * One context owns all device state of one particle set on one GPU. The calls follow the paper's
+ * statement of the problem: initialise particles and materials, step, query the state, the MGPU
+ * boundary set and the exchange volume (Unfer, Colle, Limido, "A novel multi-GPU parallelization
+ * paradigm for SPH applied to solid mechanics", Sec. II, Sec. III).
+ *
+ * Conventions (all calls):
+ *  - Every call returns a gsph_status; nothing aborts the process. Kernel launches are asynchronous:
+ *    an error raised inside a kernel (a bounded wait that ran out, an invalid label) is recorded in
+ *    the context and returned by the next synchronising call (gsph_sync, gsph_get_*).
+ *  - Caller pointers are borrowed for the duration of the call only. `on_device` = 1 means the
+ *    pointer is a device pointer of the context's GPU, 0 a host pointer. Host transfers are
+ *    synchronous with respect to the host; device transfers are ordered on `stream`.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *  - Particle arrays are in "slot" order. The library re-sorts particles by bucket hash every step,
+ *    so slot order changes; GSPH_F_ID gives each slot's persistent particle id (0..n-1 in the order
+ *    of gsph_set_particles).
+ */
+#ifndef GSPH_H
+#define GSPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GSPH_MAX_MATERIALS 4
+#define GSPH_MAX_WALLS 6
+#define GSPH_MAX_LABELS 16
+#define GSPH_NRATE 15
+#define GSPH_BALANCE_HASH_MAX 1000
+
+typedef enum {
+    GSPH_OK = 0,
+    GSPH_INVALID_ARG = 1,          /* a null pointer, size or config value out of range */
+    GSPH_OOM = 2,                  /* device allocation failed; the context is unchanged */
+    GSPH_CUDA_ERROR = 3,           /* a CUDA runtime call or kernel launch failed */
+    GSPH_PARTICLE_LEFT_DOMAIN = 4, /* warning: particles outside the bucket grid (garbage hash) */
+    GSPH_DEVICE_TIMEOUT = 5,       /* a bounded device-side wait gave up; results are invalid */
+    GSPH_NOT_READY = 6,            /* the call needs particles (gsph_set_particles) first */
+    GSPH_DEVICE_ERROR = 7          /* a kernel flagged invalid data (e.g. a label >= K) */
+} gsph_status;
+
+typedef enum {
+    GSPH_FP64 = 0,        /* every step in FP64 */
+    GSPH_FP32_SPLIT = 1   /* pair fluxes in FP32 with Kahan-compensated per-particle sums;
+                             positions, integration and conservation sums in FP64 */
+} gsph_precision;
+
+typedef struct {
+    double rho0;   /* reference density, kg/m^3 */
+    double K;      /* bulk modulus, Pa (linear EOS p = K (rho/rho0 - 1)) */
+    double G;      /* shear modulus, Pa */
+    double Y;      /* yield stress, Pa (von Mises perfect plasticity) */
+} gsph_material;
+
+typedef struct {
+    int32_t axis;  /* 0, 1, 2: rigid mirror plane x_axis = pos */
+    int32_t pad;
+    double pos;
+} gsph_wall;
+
+typedef struct {
+    double grid_lo[3];          /* lower corner of the fixed bucket grid (Sec. I) */
+    int32_t grid_dims[3];       /* buckets per axis; bucket side is 2h; product < 2^27 */
+    int32_t n_materials;        /* 1..GSPH_MAX_MATERIALS; > 1 turns on per-type swaps (Sec. III.B) */
+    double h;                   /* smoothing length (uniform, Sec. II); kernel support 2h */
+    double cfl;                 /* dt = cfl * h / max(c + |v|) */
+    gsph_material materials[GSPH_MAX_MATERIALS];
+    int32_t n_walls;
+    int32_t K;                  /* ownership labels, 1..GSPH_MAX_LABELS (Sec. II) */
+    gsph_wall walls[GSPH_MAX_WALLS];
+    double gravity[3];
+    double alpha;               /* Cg bias towards the all-types Cg, Sec. III.B (paper: 0.1) */
+    int32_t swap_period;        /* run the swap heuristic every P steps (Sec. III: 20); 0 = never */
+    int32_t precision;          /* gsph_precision */
+    int32_t device;             /* CUDA device ordinal */
+    int32_t diagnostics;        /* 1: keep neighbour counts and rates of the last step */
+} gsph_config;
+
+typedef enum {
+    /* state, FP64, n values each */
+    GSPH_F_X = 0, GSPH_F_Y, GSPH_F_Z, GSPH_F_VX, GSPH_F_VY, GSPH_F_VZ,
+    GSPH_F_W,            /* particle volume */
+    GSPH_F_M,            /* particle mass */
+    GSPH_F_E,            /* specific total energy e + |v|^2/2 */
+    GSPH_F_SXX, GSPH_F_SYY, GSPH_F_SZZ, GSPH_F_SXY, GSPH_F_SXZ, GSPH_F_SYZ, /* deviatoric stress */
+    GSPH_F_MATERIAL,     /* uint8 */
+    GSPH_F_LABEL,        /* uint8 ownership label */
+    GSPH_F_ID,           /* uint32 persistent id */
+    /* outputs of the last step, in the same slot order as the state after that step */
+    GSPH_F_HASH,         /* uint32 bucket hash at the start of the step (sorted) */
+    GSPH_F_COMM_HASH,    /* uint32 communication hash (Sec. II step c) */
+    GSPH_F_FLAG,         /* uint8 MGPU boundary flag */
+    GSPH_F_NREAL,        /* int32 real neighbours (diagnostics only) */
+    GSPH_F_NIMAGE,       /* int32 wall-image neighbours (diagnostics only) */
+    GSPH_F_RATES,        /* FP64 n x 15 rates: dw, dm, d(mv)[3], d(mE), L[9] (diagnostics only) */
+    GSPH_F_BOUNDARY,     /* uint32 slots of the MGPU boundary set, label-major, each label in
+                            communication-hash order (Sec. II step d); length = boundary_total */
+    GSPH_F_COUNT_
+} gsph_field;
+
+typedef struct {
+    int64_t step;                       /* steps taken by this context */
+    int64_t n;
+    int32_t K;
+    int32_t pad;
+    int64_t garbage;                    /* particles outside the grid at the last hash */
+    int64_t boundary[GSPH_MAX_LABELS];  /* MGPU boundary particles per label, last step */
+    int64_t boundary_total;
+    double exchange_fraction;           /* boundary_total / n (Sec. II, the exchange volume) */
+    int64_t record_bytes;               /* bytes of one particle's interaction record */
+    int64_t bytes_hash_broadcast;       /* step b: n * 4 * (K - 1) */
+    int64_t bytes_boundary_broadcast;   /* step d: boundary_total * record_bytes * (K - 1) */
+    int64_t bytes_swap;                 /* state bytes of the particles moved by the last swap pass */
+    int64_t swapped_last_pass;          /* particles that changed label in the last swap pass */
+    int64_t swap_passes;
+} gsph_exchange_stats;
+
+typedef struct {
+    /* summed device time per phase (ms) over the steps recorded since gsph_set_timing, from CUDA
+       events recorded on the launch stream around each phase */
+    double hash_sort_ms;   /* bucket hash + radix sort */
+    double reorder_ms;     /* permutation into sorted order, bucket ranges, interaction records */
+    double swap_ms;        /* swap heuristic passes */
+    double comm_ms;        /* communication hash, flags, boundary lists */
+    double interact_ms;    /* interaction loop + integration (one kernel) */
+    int64_t steps;         /* steps recorded */
+    int64_t interact_launches;
+} gsph_timings;
+
+typedef struct gsph_ctx gsph_ctx;
+
+/* Status code as text (static storage). */
+const char *gsph_status_str(gsph_status s);
+
+/* Create a context on cfg->device with the configuration copied. Errors: INVALID_ARG for a null
+ * pointer or an out-of-range field (h <= 0, cfl <= 0, dims < 1 or product >= 2^27, K not in
+ * 1..16, materials not in 1..4, walls > 6, axis not in 0..2, precision unknown), CUDA_ERROR if
+ * the device cannot be selected. */
+gsph_status gsph_create(const gsph_config *cfg, gsph_ctx **out);
+
+/* Free every device buffer and the context (null is accepted). */
+void gsph_destroy(gsph_ctx *ctx);
+
+/* Sec. II premise: load n particles (1 <= n < 2^27). pos and vel are n x 3 row-major FP64; vol is
+ * the particle volume; material and label are uint8 (material < n_materials, label < K). Mass is
+ * rho0 * vol, the specific total energy |v|^2 / 2, deviatoric stress 0; ids are 0..n-1 in input
+ * order. Reallocates device buffers if n grows. Errors: INVALID_ARG, OOM, CUDA_ERROR,
+ * DEVICE_ERROR (a material or label out of range, found on the device). */
+gsph_status gsph_set_particles(gsph_ctx *ctx, int64_t n, const double *pos, const double *vel,
+                               const double *vol, const uint8_t *material, const uint8_t *label,
+                               int32_t on_device, void *stream);
+
+/* Overwrite one state field (GSPH_F_X .. GSPH_F_ID) of the current slot order from src (n values
+ * of the field's type). The time step is recomputed before the next step. */
+gsph_status gsph_put_field(gsph_ctx *ctx, gsph_field f, const void *src, int32_t on_device,
+                           void *stream);
+
+/* Copy one field to dst (n values of the field's type; GSPH_F_RATES: 15 n doubles;
+ * GSPH_F_BOUNDARY: boundary_total uint32). Synchronises the stream for host copies.
+ * Errors: NOT_READY before particles exist or for diagnostics fields when diagnostics are off. */
+gsph_status gsph_get_field(gsph_ctx *ctx, gsph_field f, void *dst, int32_t on_device, void *stream);
+
+/* Sec. II steps a-g, repeated nsteps times, enqueued on stream: dt from the current state, bucket
+ * hash, radix sort, reorder, swap heuristic when the step index is a multiple of swap_period
+ * (Sec. III), communication hash and MGPU boundary set (K > 1), interaction loop with integration.
+ * Asynchronous: returns after enqueueing. */
+gsph_status gsph_step(gsph_ctx *ctx, int32_t nsteps, void *stream);
+
+/* Sec. III.A/B: one swap-heuristic pass over all label pairs on the current state, enqueued on
+ * stream (labels change in place; per-label particle counts do not). */
+gsph_status gsph_swap_now(gsph_ctx *ctx, void *stream);
+
+/* Waits for the context's work on stream and returns any error recorded by its kernels. */
+gsph_status gsph_sync(gsph_ctx *ctx, void *stream);
+
+/* Exchange statistics of the last step (synchronises). */
+gsph_status gsph_get_exchange_stats(gsph_ctx *ctx, void *stream, gsph_exchange_stats *out);
+
+/* FP64 device reductions of the current state (synchronises): out = {sum m, sum m vx, sum m vy,
+ * sum m vz, sum m E, sum w}. */
+gsph_status gsph_get_conserved(gsph_ctx *ctx, void *stream, double out[6]);
+
+/* Time step the next step will use (synchronises). */
+gsph_status gsph_get_dt(gsph_ctx *ctx, void *stream, double *dt);
+
+/* Number of particles and of buckets (grid product; the garbage hash equals it). */
+gsph_status gsph_get_sizes(gsph_ctx *ctx, int64_t *n, int64_t *ncell);
+
+/* Per-phase CUDA-event timing: max_steps > 0 arms it for up to max_steps steps (resets the
+ * totals), 0 disarms. gsph_get_timings synchronises and returns the totals so far. */
+gsph_status gsph_set_timing(gsph_ctx *ctx, int32_t max_steps);
+gsph_status gsph_get_timings(gsph_ctx *ctx, gsph_timings *out);
+
+/* Stateless radix sort (Sec. I "radix sort" of the bucket hashes): stable ascending sort of n
+ * (key, value) uint32 pairs in device memory by the low key_bits bits of the key (1..32), in
+ * place. workspace: device scratch of at least gsph_radix_sort_workspace(n, key_bits) bytes,
+ * owned by the caller. Asynchronous on stream. Errors: INVALID_ARG (null pointers, n < 0 or
+ * n >= 2^31, key_bits out of range, workspace too small), CUDA_ERROR. */
+size_t gsph_radix_sort_workspace(int64_t n, int32_t key_bits);
+gsph_status gsph_radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, int32_t key_bits,
+                                  void *workspace, size_t workspace_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

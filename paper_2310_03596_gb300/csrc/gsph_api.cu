@@ -1,0 +1,579 @@
+// gsph_api.cu - the C-ABI of libgsph: context, device buffers, the step in the paper's order
+// (Sec. II steps a-g with the swap heuristic of Sec. III), field access, statistics and timing.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gsph_internal.cuh"
+
+namespace gsph {
+// k_sort.cu
+cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t *hist, uint32_t *tot,
+                             int64_t n, int bits, cudaStream_t s, bool *in_alt);
+size_t radix_hist_words(int64_t n);
+cudaError_t launch_hash(const DevParams &P, int64_t n, const double *x, const double *y, const double *z,
+                        uint32_t *key, uint32_t *val, unsigned long long *garbage, cudaStream_t s);
+// k_reorder_comm.cu
+cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint32_t *perm,
+                           const State &A, double *xs, double *ys, double *zs, uint8_t *lab_s, uint8_t *mat_s,
+                           uint32_t *id_s, uint2 *cellr, void *pos, void *rec, int *err, cudaStream_t s);
+cudaError_t launch_comm(const DevParams &P, int64_t n, const uint32_t *skey, const uint8_t *lab_s, uint32_t *mask,
+                        uint8_t *flag, uint32_t *comm, uint32_t *block_counts, unsigned long long *label_total,
+                        uint32_t *blist, cudaStream_t s);
+int comm_blocks(int64_t n);
+cudaError_t launch_init(const DevParams &P, int64_t n, const double *pos, const double *vel, const double *vol,
+                        const uint8_t *mat, const uint8_t *lab, const State &A, int *err, cudaStream_t s);
+cudaError_t launch_dt_from_state(const DevParams &P, int64_t n, const State &A, unsigned long long *sig, double *dt,
+                                 cudaStream_t s);
+cudaError_t launch_finalize_dt(const DevParams &P, unsigned long long *sig, double *dt, cudaStream_t s);
+cudaError_t launch_conserved(int64_t n, const State &A, double *part, double *out, cudaStream_t s);
+// k_interact.cu
+cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n, const uint32_t *skey,
+                            const uint2 *cellr, const void *pos, const void *rec, const double *xs, const double *ys,
+                            const double *zs, const uint32_t *perm, const State &A, const State &B,
+                            const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
+                            unsigned long long *sig, int32_t *nreal, int32_t *nimage, double *rates, cudaStream_t s);
+// k_swap.cu
+size_t swap_scratch_bytes(int K, int nmat);
+cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const double *x, const double *y, const double *z,
+                             uint8_t *lab, const uint8_t *mat, const uint32_t *id, void *scratch, uint16_t *bh,
+                             cudaStream_t s);
+unsigned long long *swap_moved_ptr(void *scratch);
+}  // namespace gsph
+
+using namespace gsph;
+
+enum { PH_START = 0, PH_SORT, PH_REORDER, PH_SWAP, PH_COMM, PH_INTERACT, PH_COUNT };
+
+struct gsph_ctx {
+    gsph_config cfg;
+    DevParams P;
+    bool split = false;
+    int64_t n = 0;
+    int64_t step = 0;
+    bool dt_dirty = true;
+    bool have_step = false;
+    State A{}, B{};
+    std::vector<void *> allocs;
+    // per-step buffers
+    uint32_t *key0 = nullptr, *val0 = nullptr, *key1 = nullptr, *val1 = nullptr, *hist = nullptr, *tot = nullptr;
+    uint32_t *skey = nullptr, *perm = nullptr;
+    uint2 *cellr = nullptr;
+    uint32_t *mask = nullptr;
+    double *xs = nullptr, *ys = nullptr, *zs = nullptr;
+    uint8_t *lab_s = nullptr, *mat_s = nullptr;
+    uint32_t *id_s = nullptr;
+    void *pos = nullptr, *rec = nullptr;
+    uint8_t *flag = nullptr;
+    uint32_t *comm = nullptr, *blist = nullptr, *bcounts = nullptr;
+    unsigned long long *label_off = nullptr;   // K + 1
+    unsigned long long *garbage = nullptr;
+    unsigned long long *sig = nullptr;
+    double *dt = nullptr;
+    int *err = nullptr;
+    int32_t *nreal = nullptr, *nimage = nullptr;
+    double *rates = nullptr;
+    void *swap_scratch = nullptr;
+    uint16_t *bh = nullptr;
+    double *cons_part = nullptr, *cons_out = nullptr;
+    // statistics
+    int64_t swap_passes = 0;
+    int64_t swapped_total_prev = 0;
+    // timing
+    int timing_max = 0, timing_used = 0;
+    std::vector<cudaEvent_t> ev;
+};
+
+#define GSPH_CK(call)                                      \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return GSPH_CUDA_ERROR;     \
+    } while (0)
+
+static void free_buffers(gsph_ctx *c) {
+    for (void *p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+    c->A = State{};
+    c->B = State{};
+    c->n = 0;
+}
+
+template <class T> static cudaError_t dalloc(gsph_ctx *c, T **p, size_t count) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    if (e != cudaSuccess) { *p = nullptr; return e; }
+    c->allocs.push_back(q);
+    *p = (T *)q;
+    return cudaSuccess;
+}
+
+static cudaError_t alloc_state(gsph_ctx *c, State &S, int64_t n) {
+    for (int k = 0; k < 15; ++k) {
+        cudaError_t e = dalloc(c, &S.f[k], (size_t)n);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = dalloc(c, &S.mat, (size_t)n);
+    if (e == cudaSuccess) e = dalloc(c, &S.label, (size_t)n);
+    if (e == cudaSuccess) e = dalloc(c, &S.id, (size_t)n);
+    return e;
+}
+
+static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
+    const size_t N = (size_t)n, C = (size_t)c->P.ncell;
+    cudaError_t e;
+#define A_(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
+    A_(alloc_state(c, c->A, n));
+    A_(alloc_state(c, c->B, n));
+    A_(dalloc(c, &c->key0, N)); A_(dalloc(c, &c->val0, N));
+    A_(dalloc(c, &c->key1, N)); A_(dalloc(c, &c->val1, N));
+    A_(dalloc(c, &c->hist, radix_hist_words(n)));
+    A_(dalloc(c, &c->tot, 256));
+    A_(dalloc(c, &c->cellr, C));
+    A_(dalloc(c, &c->mask, C));
+    A_(dalloc(c, &c->xs, N)); A_(dalloc(c, &c->ys, N)); A_(dalloc(c, &c->zs, N));
+    A_(dalloc(c, &c->lab_s, N)); A_(dalloc(c, &c->mat_s, N)); A_(dalloc(c, &c->id_s, N));
+    if (c->split) {
+        A_(dalloc(c, (float4 **)&c->pos, N));
+        A_(dalloc(c, (RecF **)&c->rec, N));
+    } else {
+        A_(dalloc(c, (D4 **)&c->pos, N));
+        A_(dalloc(c, (RecD **)&c->rec, N));
+    }
+    A_(dalloc(c, &c->flag, N));
+    A_(dalloc(c, &c->comm, N));
+    A_(dalloc(c, &c->blist, N));
+    A_(dalloc(c, &c->bcounts, (size_t)kMaxLabel * (size_t)comm_blocks(n)));
+    A_(dalloc(c, &c->label_off, (size_t)kMaxLabel + 1));
+    A_(dalloc(c, &c->garbage, 1));
+    A_(dalloc(c, &c->sig, 1));
+    A_(dalloc(c, &c->dt, 1));
+    A_(dalloc(c, &c->err, 1));
+    if (c->cfg.diagnostics) {
+        A_(dalloc(c, &c->nreal, N));
+        A_(dalloc(c, &c->nimage, N));
+        A_(dalloc(c, &c->rates, N * kNRate));
+    }
+    A_(dalloc(c, (char **)&c->swap_scratch, swap_scratch_bytes(c->P.K_labels, c->P.nmat)));
+    A_(dalloc(c, &c->bh, N));
+    A_(dalloc(c, &c->cons_part, ((N + 255) / 256 + 1) * 6));
+    A_(dalloc(c, &c->cons_out, 6));
+#undef A_
+    e = cudaMemset(c->err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->garbage, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->label_off, 0, (kMaxLabel + 1) * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->swap_scratch, 0, swap_scratch_bytes(c->P.K_labels, c->P.nmat));
+    return e;
+}
+
+static bool config_ok(const gsph_config *c) {
+    if (!(c->h > 0.0) || !(c->cfl > 0.0)) return false;
+    int64_t prod = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (c->grid_dims[a] < 1 || !std::isfinite(c->grid_lo[a])) return false;
+        prod *= c->grid_dims[a];
+        if (prod >= ((int64_t)1 << 27)) return false;
+    }
+    if (c->K < 1 || c->K > GSPH_MAX_LABELS) return false;
+    if (c->n_materials < 1 || c->n_materials > GSPH_MAX_MATERIALS) return false;
+    for (int k = 0; k < c->n_materials; ++k) {
+        const gsph_material &m = c->materials[k];
+        if (!(m.rho0 > 0) || !(m.K > 0) || !(m.G >= 0) || !(m.Y > 0)) return false;
+    }
+    if (c->n_walls < 0 || c->n_walls > GSPH_MAX_WALLS) return false;
+    for (int k = 0; k < c->n_walls; ++k)
+        if (c->walls[k].axis < 0 || c->walls[k].axis > 2 || !std::isfinite(c->walls[k].pos)) return false;
+    if (c->precision != GSPH_FP64 && c->precision != GSPH_FP32_SPLIT) return false;
+    if (c->swap_period < 0) return false;
+    if (!(c->alpha >= 0.0 && c->alpha <= 1.0)) return false;
+    return true;
+}
+
+static void fill_params(const gsph_config &c, DevParams &P) {
+    std::memset(&P, 0, sizeof(P));
+    const double PI = 3.14159265358979323846;
+    for (int a = 0; a < 3; ++a) {
+        P.lo[a] = c.grid_lo[a];
+        P.dims[a] = c.grid_dims[a];
+        P.g[a] = c.gravity[a];
+    }
+    P.h = c.h;
+    P.cell = 2.0 * c.h;
+    P.R2 = P.cell * P.cell;
+    P.cfl = c.cfl;
+    P.ncell = (uint32_t)((int64_t)c.grid_dims[0] * c.grid_dims[1] * c.grid_dims[2]);
+    P.nwalls = c.n_walls;
+    for (int k = 0; k < c.n_walls; ++k) {
+        P.wall_axis[k] = c.walls[k].axis;
+        P.wall_pos[k] = c.walls[k].pos;
+    }
+    P.nmat = c.n_materials;
+    for (int k = 0; k < c.n_materials; ++k) {
+        const gsph_material &m = c.materials[k];
+        P.rho0[k] = m.rho0; P.K[k] = m.K; P.G[k] = m.G; P.Y[k] = m.Y;
+        P.Mmod[k] = m.K + 4.0 * m.G / 3.0;
+        P.f_rho0[k] = (float)m.rho0; P.f_K[k] = (float)m.K; P.f_G[k] = (float)m.G;
+        P.f_Mmod[k] = (float)P.Mmod[k];
+    }
+    double aw = 21.0 / (16.0 * PI * c.h * c.h * c.h);
+    P.kdw = 5.0 * aw / c.h;
+    P.alpha = c.alpha;
+    P.K_labels = c.K;
+    P.f_cell = (float)P.cell;
+    P.f_inv_h = (float)(1.0 / c.h);
+    P.f_kdw = (float)P.kdw;
+    // FP32 r^2 of candidates is within ~1.4e-6 R2 of the FP64 value; outside +-1.2e-5 R2 the FP32
+    // comparison is therefore exact, inside it the FP64 positions decide.
+    P.f_R2lo = (float)(P.R2 * (1.0 - 1.2e-5));
+    P.f_R2hi = (float)(P.R2 * (1.0 + 1.2e-5));
+}
+
+static int key_bits(uint32_t ncell) {
+    int b = 1;
+    while (b < 32 && (((uint64_t)1 << b) <= (uint64_t)ncell)) ++b;
+    return b;
+}
+
+static void rec_event(gsph_ctx *c, int phase, cudaStream_t s) {
+    if (c->timing_used < c->timing_max) cudaEventRecord(c->ev[(size_t)c->timing_used * PH_COUNT + phase], s);
+}
+
+static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
+    const DevParams &P = c->P;
+    const int64_t n = c->n;
+    if (c->dt_dirty) {
+        GSPH_CK(launch_dt_from_state(P, n, c->A, c->sig, c->dt, s));
+        c->dt_dirty = false;
+    }
+    rec_event(c, PH_START, s);
+    // a. bucket hash and the radix sort by hash (Sec. I)
+    GSPH_CK(cudaMemsetAsync(c->garbage, 0, sizeof(unsigned long long), s));
+    GSPH_CK(launch_hash(P, n, c->A.f[FX], c->A.f[FY], c->A.f[FZ], c->key0, c->val0, c->garbage, s));
+    bool alt = false;
+    GSPH_CK(radix_sort_pairs(c->key0, c->val0, c->key1, c->val1, c->hist, c->tot, n, key_bits(P.ncell), s, &alt));
+    c->skey = alt ? c->key1 : c->key0;
+    c->perm = alt ? c->val1 : c->val0;
+    rec_event(c, PH_SORT, s);
+    // sorted view, bucket ranges, interaction records
+    GSPH_CK(cudaMemsetAsync(c->cellr, 0, (size_t)P.ncell * sizeof(uint2), s));
+    GSPH_CK(launch_reorder(c->split, P, n, c->skey, c->perm, c->A, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s,
+                           c->cellr, c->pos, c->rec, c->err, s));
+    rec_event(c, PH_REORDER, s);
+    // Sec. III: periodic swap heuristic on the sorted view
+    if (P.K_labels > 1 && c->cfg.swap_period > 0 && (c->step % c->cfg.swap_period) == 0) {
+        GSPH_CK(launch_swap_pass(P, n, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s, c->swap_scratch, c->bh, s));
+        ++c->swap_passes;
+    }
+    rec_event(c, PH_SWAP, s);
+    // b-d. communication hash, MGPU boundary flags and set
+    GSPH_CK(launch_comm(P, n, c->skey, c->lab_s, c->mask, c->flag, c->comm, c->bcounts, c->label_off, c->blist, s));
+    rec_event(c, PH_COMM, s);
+    // f-g. interaction loop fused with the integration; next dt
+    GSPH_CK(launch_interact(c->split, c->cfg.diagnostics != 0, P, n, c->skey, c->cellr, c->pos, c->rec, c->xs, c->ys,
+                            c->zs, c->perm, c->A, c->B, c->lab_s, c->mat_s, c->id_s, c->dt, c->sig, c->nreal,
+                            c->nimage, c->rates, s));
+    GSPH_CK(launch_finalize_dt(P, c->sig, c->dt, s));
+    rec_event(c, PH_INTERACT, s);
+    if (c->timing_used < c->timing_max) ++c->timing_used;
+    State t = c->A;
+    c->A = c->B;
+    c->B = t;
+    ++c->step;
+    c->have_step = true;
+    return GSPH_OK;
+}
+
+static gsph_status read_err(gsph_ctx *c, cudaStream_t s) {
+    int h = 0;
+    GSPH_CK(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GSPH_CK(cudaStreamSynchronize(s));
+    if (h & kErrTimeout) return GSPH_DEVICE_TIMEOUT;
+    if (h) return GSPH_DEVICE_ERROR;
+    return GSPH_OK;
+}
+
+static size_t field_elem_bytes(gsph_field f) {
+    switch (f) {
+        case GSPH_F_MATERIAL: case GSPH_F_LABEL: case GSPH_F_FLAG: return 1;
+        case GSPH_F_ID: case GSPH_F_HASH: case GSPH_F_COMM_HASH: case GSPH_F_NREAL: case GSPH_F_NIMAGE:
+        case GSPH_F_BOUNDARY: return 4;
+        case GSPH_F_RATES: return 8 * kNRate;
+        default: return 8;
+    }
+}
+
+extern "C" {
+
+const char *gsph_status_str(gsph_status s) {
+    switch (s) {
+        case GSPH_OK: return "ok";
+        case GSPH_INVALID_ARG: return "invalid argument";
+        case GSPH_OOM: return "device out of memory";
+        case GSPH_CUDA_ERROR: return "CUDA error";
+        case GSPH_PARTICLE_LEFT_DOMAIN: return "particles left the bucket grid";
+        case GSPH_DEVICE_TIMEOUT: return "bounded device wait timed out";
+        case GSPH_NOT_READY: return "no particles loaded";
+        case GSPH_DEVICE_ERROR: return "invalid data found on the device";
+    }
+    return "unknown status";
+}
+
+gsph_status gsph_create(const gsph_config *cfg, gsph_ctx **out) {
+    if (!cfg || !out) return GSPH_INVALID_ARG;
+    *out = nullptr;
+    if (!config_ok(cfg)) return GSPH_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) return GSPH_CUDA_ERROR;
+    if (cudaSetDevice(cfg->device) != cudaSuccess) return GSPH_CUDA_ERROR;
+    gsph_ctx *c = new (std::nothrow) gsph_ctx();
+    if (!c) return GSPH_OOM;
+    c->cfg = *cfg;
+    c->split = cfg->precision == GSPH_FP32_SPLIT;
+    fill_params(*cfg, c->P);
+    *out = c;
+    return GSPH_OK;
+}
+
+void gsph_destroy(gsph_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->cfg.device);
+    cudaDeviceSynchronize();
+    free_buffers(c);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    delete c;
+}
+
+gsph_status gsph_set_particles(gsph_ctx *c, int64_t n, const double *pos, const double *vel, const double *vol,
+                               const uint8_t *material, const uint8_t *label, int32_t on_device, void *stream) {
+    if (!c || n < 1 || n >= ((int64_t)1 << 27) || !pos || !vel || !vol || !material || !label) return GSPH_INVALID_ARG;
+    GSPH_CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    GSPH_CK(cudaStreamSynchronize(s));
+    if (n != c->n) {
+        free_buffers(c);
+        cudaError_t e = alloc_all(c, n);
+        if (e != cudaSuccess) {
+            free_buffers(c);
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? GSPH_OOM : GSPH_CUDA_ERROR;
+        }
+        c->n = n;
+    }
+    void *stage = nullptr;
+    const double *dpos = pos, *dvel = vel, *dvol = vol;
+    const uint8_t *dmat = material, *dlab = label;
+    if (!on_device) {
+        const size_t nb = (size_t)n;
+        cudaError_t e = cudaMalloc(&stage, nb * 8 * 7 + nb * 2);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? GSPH_OOM : GSPH_CUDA_ERROR;
+        }
+        char *q = (char *)stage;
+        e = cudaMemcpyAsync(q, pos, nb * 24, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(q + nb * 24, vel, nb * 24, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(q + nb * 48, vol, nb * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(q + nb * 56, material, nb, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(q + nb * 57, label, nb, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(s);
+            cudaFree(stage);
+            return GSPH_CUDA_ERROR;
+        }
+        dpos = (const double *)q;
+        dvel = (const double *)(q + nb * 24);
+        dvol = (const double *)(q + nb * 48);
+        dmat = (const uint8_t *)(q + nb * 56);
+        dlab = (const uint8_t *)(q + nb * 57);
+    }
+    cudaError_t e = cudaMemsetAsync(c->err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_init(c->P, n, dpos, dvel, dvol, dmat, dlab, c->A, c->err, s);
+    if (e == cudaSuccess) e = launch_dt_from_state(c->P, n, c->A, c->sig, c->dt, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    if (stage) cudaFree(stage);
+    if (e != cudaSuccess || e2 != cudaSuccess) return GSPH_CUDA_ERROR;
+    c->dt_dirty = false;
+    c->step = 0;
+    c->have_step = false;
+    c->swap_passes = 0;
+    return read_err(c, s);
+}
+
+gsph_status gsph_put_field(gsph_ctx *c, gsph_field f, const void *src, int32_t on_device, void *stream) {
+    if (!c || !src || (int)f < 0 || f > GSPH_F_ID) return GSPH_INVALID_ARG;
+    if (c->n == 0) return GSPH_NOT_READY;
+    GSPH_CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    void *dst = f <= GSPH_F_SYZ ? (void *)c->A.f[f]
+              : f == GSPH_F_MATERIAL ? (void *)c->A.mat : f == GSPH_F_LABEL ? (void *)c->A.label : (void *)c->A.id;
+    GSPH_CK(cudaMemcpyAsync(dst, src, (size_t)c->n * field_elem_bytes(f),
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if (!on_device) GSPH_CK(cudaStreamSynchronize(s));
+    c->dt_dirty = true;
+    return GSPH_OK;
+}
+
+gsph_status gsph_get_field(gsph_ctx *c, gsph_field f, void *dst, int32_t on_device, void *stream) {
+    if (!c || !dst || (int)f < 0 || f >= GSPH_F_COUNT_) return GSPH_INVALID_ARG;
+    if (c->n == 0) return GSPH_NOT_READY;
+    GSPH_CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const void *src = nullptr;
+    size_t count = (size_t)c->n;
+    if (f <= GSPH_F_SYZ) src = c->A.f[f];
+    else if (f == GSPH_F_MATERIAL) src = c->A.mat;
+    else if (f == GSPH_F_LABEL) src = c->A.label;
+    else if (f == GSPH_F_ID) src = c->A.id;
+    else {
+        if (!c->have_step) return GSPH_NOT_READY;
+        if (f == GSPH_F_HASH) src = c->skey;
+        else if (f == GSPH_F_COMM_HASH) src = c->comm;
+        else if (f == GSPH_F_FLAG) src = c->flag;
+        else if (f == GSPH_F_BOUNDARY) {
+            unsigned long long tot = 0;
+            GSPH_CK(cudaMemcpyAsync(&tot, c->label_off + c->P.K_labels, sizeof(tot), cudaMemcpyDeviceToHost, s));
+            GSPH_CK(cudaStreamSynchronize(s));
+            count = (size_t)tot;
+            src = c->blist;
+        } else {
+            if (!c->cfg.diagnostics) return GSPH_NOT_READY;
+            src = f == GSPH_F_NREAL ? (const void *)c->nreal : f == GSPH_F_NIMAGE ? (const void *)c->nimage
+                                                                                   : (const void *)c->rates;
+        }
+    }
+    if (count > 0)
+        GSPH_CK(cudaMemcpyAsync(dst, src, count * field_elem_bytes(f),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (!on_device) GSPH_CK(cudaStreamSynchronize(s));
+    return GSPH_OK;
+}
+
+gsph_status gsph_step(gsph_ctx *c, int32_t nsteps, void *stream) {
+    if (!c || nsteps < 0) return GSPH_INVALID_ARG;
+    if (c->n == 0) return GSPH_NOT_READY;
+    GSPH_CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < nsteps; ++k) {
+        gsph_status st = enqueue_step(c, s);
+        if (st != GSPH_OK) return st;
+    }
+    return GSPH_OK;
+}
+
+gsph_status gsph_swap_now(gsph_ctx *c, void *stream) {
+    if (!c) return GSPH_INVALID_ARG;
+    if (c->n == 0) return GSPH_NOT_READY;
+    GSPH_CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    GSPH_CK(launch_swap_pass(c->P, c->n, c->A.f[FX], c->A.f[FY], c->A.f[FZ], c->A.label, c->A.mat, c->A.id,
+                             c->swap_scratch, c->bh, s));
+    ++c->swap_passes;
+    return GSPH_OK;
+}
+
+gsph_status gsph_sync(gsph_ctx *c, void *stream) {
+    if (!c) return GSPH_INVALID_ARG;
+    if (c->n == 0) return GSPH_OK;
+    GSPH_CK(cudaSetDevice(c->cfg.device));
+    return read_err(c, (cudaStream_t)stream);
+}
+
+gsph_status gsph_get_exchange_stats(gsph_ctx *c, void *stream, gsph_exchange_stats *out) {
+    if (!c || !out) return GSPH_INVALID_ARG;
+    if (c->n == 0) return GSPH_NOT_READY;
+    GSPH_CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    std::memset(out, 0, sizeof(*out));
+    unsigned long long off[kMaxLabel + 1] = {0}, garb = 0, moved = 0;
+    GSPH_CK(cudaMemcpyAsync(off, c->label_off, sizeof(off), cudaMemcpyDeviceToHost, s));
+    GSPH_CK(cudaMemcpyAsync(&garb, c->garbage, sizeof(garb), cudaMemcpyDeviceToHost, s));
+    GSPH_CK(cudaMemcpyAsync(&moved, swap_moved_ptr(c->swap_scratch), sizeof(moved), cudaMemcpyDeviceToHost, s));
+    GSPH_CK(cudaStreamSynchronize(s));
+    const int K = c->P.K_labels;
+    out->step = c->step;
+    out->n = c->n;
+    out->K = K;
+    out->garbage = c->have_step ? (int64_t)garb : 0;
+    if (c->have_step) {
+        for (int k = 0; k < K; ++k) out->boundary[k] = (int64_t)((k + 1 < K ? off[k + 1] : off[K]) - off[k]);
+        out->boundary_total = (int64_t)off[K];
+    }
+    out->exchange_fraction = (double)out->boundary_total / (double)c->n;
+    out->record_bytes = c->split ? (int64_t)(sizeof(float4) + sizeof(RecF)) : (int64_t)(sizeof(D4) + sizeof(RecD));
+    out->bytes_hash_broadcast = c->n * 4 * (K - 1);
+    out->bytes_boundary_broadcast = out->boundary_total * out->record_bytes * (K - 1);
+    out->swapped_last_pass = (int64_t)moved;
+    out->bytes_swap = (int64_t)moved * (15 * 8 + 6);
+    out->swap_passes = c->swap_passes;
+    return out->garbage > 0 ? GSPH_PARTICLE_LEFT_DOMAIN : GSPH_OK;
+}
+
+gsph_status gsph_get_conserved(gsph_ctx *c, void *stream, double out[6]) {
+    if (!c || !out) return GSPH_INVALID_ARG;
+    if (c->n == 0) return GSPH_NOT_READY;
+    GSPH_CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    GSPH_CK(launch_conserved(c->n, c->A, c->cons_part, c->cons_out, s));
+    GSPH_CK(cudaMemcpyAsync(out, c->cons_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GSPH_CK(cudaStreamSynchronize(s));
+    return GSPH_OK;
+}
+
+gsph_status gsph_get_dt(gsph_ctx *c, void *stream, double *dt) {
+    if (!c || !dt) return GSPH_INVALID_ARG;
+    if (c->n == 0) return GSPH_NOT_READY;
+    GSPH_CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->dt_dirty) {
+        GSPH_CK(launch_dt_from_state(c->P, c->n, c->A, c->sig, c->dt, s));
+        c->dt_dirty = false;
+    }
+    GSPH_CK(cudaMemcpyAsync(dt, c->dt, sizeof(double), cudaMemcpyDeviceToHost, s));
+    GSPH_CK(cudaStreamSynchronize(s));
+    return GSPH_OK;
+}
+
+gsph_status gsph_get_sizes(gsph_ctx *c, int64_t *n, int64_t *ncell) {
+    if (!c) return GSPH_INVALID_ARG;
+    if (n) *n = c->n;
+    if (ncell) *ncell = (int64_t)c->P.ncell;
+    return GSPH_OK;
+}
+
+gsph_status gsph_set_timing(gsph_ctx *c, int32_t max_steps) {
+    if (!c || max_steps < 0) return GSPH_INVALID_ARG;
+    GSPH_CK(cudaSetDevice(c->cfg.device));
+    GSPH_CK(cudaDeviceSynchronize());
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    c->ev.clear();
+    c->timing_max = 0;
+    c->timing_used = 0;
+    if (max_steps == 0) return GSPH_OK;
+    c->ev.resize((size_t)max_steps * PH_COUNT);
+    for (auto &e : c->ev) GSPH_CK(cudaEventCreate(&e));
+    c->timing_max = max_steps;
+    return GSPH_OK;
+}
+
+gsph_status gsph_get_timings(gsph_ctx *c, gsph_timings *out) {
+    if (!c || !out) return GSPH_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    GSPH_CK(cudaSetDevice(c->cfg.device));
+    for (int k = 0; k < c->timing_used; ++k) {
+        cudaEvent_t *e = &c->ev[(size_t)k * PH_COUNT];
+        GSPH_CK(cudaEventSynchronize(e[PH_INTERACT]));
+        float t[PH_COUNT] = {0};
+        for (int p = 1; p < PH_COUNT; ++p) GSPH_CK(cudaEventElapsedTime(&t[p], e[p - 1], e[p]));
+        out->hash_sort_ms += t[PH_SORT];
+        out->reorder_ms += t[PH_REORDER];
+        out->swap_ms += t[PH_SWAP];
+        out->comm_ms += t[PH_COMM];
+        out->interact_ms += t[PH_INTERACT];
+    }
+    out->steps = c->timing_used;
+    out->interact_launches = c->timing_used;
+    return GSPH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// gsph_internal.cuh - device-side layout and helpers shared by the CUDA translation units of libgsph.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gsph.h"
+
+namespace gsph {
+
+constexpr int kMaxMat = GSPH_MAX_MATERIALS;
+constexpr int kMaxWall = GSPH_MAX_WALLS;
+constexpr int kMaxLabel = GSPH_MAX_LABELS;
+constexpr int kNRate = GSPH_NRATE;
+constexpr uint32_t kFullMask = 0xffffffffu;
+
+// Device error bits (OR-ed into Ctx::d_err).
+constexpr int kErrLabel = 1;      // a label >= K
+constexpr int kErrMaterial = 2;   // a material >= n_materials
+constexpr int kErrTimeout = 4;    // a bounded device wait gave up
+
+// Parameters every kernel receives by value.
+struct DevParams {
+    double lo[3];
+    double cell;         // bucket side 2h
+    double R2;           // (2h)^2, the strict support predicate r^2 < R2
+    double h;
+    double cfl;
+    double g[3];
+    double wall_pos[kMaxWall];
+    double rho0[kMaxMat], K[kMaxMat], G[kMaxMat], Y[kMaxMat];
+    double Mmod[kMaxMat];    // K + (4 G) / 3, the longitudinal modulus
+    double kdw;              // 5 * 21 / (16 pi h^3) / h: |dW/dr| = kdw * q (1 - q/2)^3
+    double alpha;
+    int dims[3];
+    uint32_t ncell;          // grid product; the garbage hash
+    int nwalls;
+    int wall_axis[kMaxWall];
+    int nmat;
+    int K_labels;
+    // FP32 copies for the split path
+    float f_cell, f_inv_h, f_kdw, f_R2lo, f_R2hi;
+    float f_rho0[kMaxMat], f_K[kMaxMat], f_G[kMaxMat], f_Mmod[kMaxMat];
+};
+
+// FP64 state in structure-of-arrays form.
+struct State {
+    double *f[15];           // x y z vx vy vz w m E sxx syy szz sxy sxz syz
+    uint8_t *mat, *label;
+    uint32_t *id;
+};
+enum { FX = 0, FY, FZ, FVX, FVY, FVZ, FW, FM, FE, FSXX, FSYY, FSZZ, FSXY, FSXZ, FSYZ };
+
+// Interaction records of sorted particles.
+// Split path: pos4 = (x, y, z relative to the particle's own bucket corner, w) in FP32 and
+// rec = {(vx, vy, vz, rho), (p, Z, E, sxx), (syy, sxy, sxz, syz)}; szz = -(sxx + syy).
+struct RecF { float4 a, b, c; };
+// 32-byte aligned FP64 4-vector (loads as one 256-bit or two 128-bit transactions).
+struct __align__(32) D4 { double x, y, z, w; };
+__host__ __device__ __forceinline__ D4 make_d4(double x, double y, double z, double w) { return D4{x, y, z, w}; }
+// FP64 path: pos = (x, y, z, w) absolute and rec = {(vx, vy, vz, rho), (p, Z, E, sxx),
+// (syy, szz, sxy, sxz), (syz, -, -, -)}.
+struct RecD { D4 a, b, c, d; };
+
+// ---------------------------------------------------------------------------------------------
+// Exactly rounded FP64 helpers: every product and sum rounded separately (no contraction), so that
+// the integer decisions made from them (hash, support predicate, balancing hash) are the same on
+// any IEEE machine that evaluates the same operation sequence.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ double dist2_rn(double dx, double dy, double dz) {
+    double a = __dmul_rn(dx, dx);
+    double b = __dmul_rn(dy, dy);
+    double c = __dmul_rn(dz, dz);
+    return __dadd_rn(__dadd_rn(a, b), c);
+}
+
+// Bucket coordinate along one axis: -1 below the grid, dim at or beyond the top.
+__device__ __forceinline__ int bucket_coord(double x, double lo, double cell, int dim) {
+    double t = __ddiv_rn(__dsub_rn(x, lo), cell);
+    if (!(t >= 0.0)) return -1;
+    if (t >= (double)dim) return dim;
+    return (int)t;
+}
+
+__device__ __forceinline__ int bucket_coord_signed(double x, double lo, double cell) {
+    return (int)floor(__ddiv_rn(__dsub_rn(x, lo), cell));
+}
+
+__device__ __forceinline__ uint32_t hash_of(const DevParams &P, double x, double y, double z) {
+    int cx = bucket_coord(x, P.lo[0], P.cell, P.dims[0]);
+    int cy = bucket_coord(y, P.lo[1], P.cell, P.dims[1]);
+    int cz = bucket_coord(z, P.lo[2], P.cell, P.dims[2]);
+    if (cx < 0 || cy < 0 || cz < 0 || cx >= P.dims[0] || cy >= P.dims[1] || cz >= P.dims[2]) return P.ncell;
+    return (uint32_t)cx + (uint32_t)P.dims[0] * ((uint32_t)cy + (uint32_t)P.dims[1] * (uint32_t)cz);
+}
+
+__device__ __forceinline__ void decode_cell(const DevParams &P, uint32_t c, int &cx, int &cy, int &cz) {
+    cx = (int)(c % (uint32_t)P.dims[0]);
+    uint32_t r = c / (uint32_t)P.dims[0];
+    cy = (int)(r % (uint32_t)P.dims[1]);
+    cz = (int)(r / (uint32_t)P.dims[1]);
+}
+
+// Signal speed c + |v| of one particle, exactly rounded (the CFL max is order independent, so the
+// time step is reproducible bit for bit).
+__device__ __forceinline__ double signal_speed(const DevParams &P, int mat, double m, double w,
+                                               double vx, double vy, double vz) {
+    double rho = __ddiv_rn(m, w);
+    double c = __dsqrt_rn(__ddiv_rn(P.Mmod[mat], rho));
+    return __dadd_rn(c, __dsqrt_rn(dist2_rn(vx, vy, vz)));
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace gsph

@@ -1,0 +1,343 @@
+// k_reorder_comm.cu - reorder into hash order with bucket ranges and interaction records (Sec. I),
+// communication hash, MGPU boundary flags and boundary set (Sec. II steps b-d, K virtual labels),
+// particle initialisation and the FP64 reductions (time step, conserved sums).
+#include "gsph_internal.cuh"
+
+namespace gsph {
+
+// ---------------------------------------------------------------------------------------------
+// Reorder: sorted slot s takes old slot o = perm[s]. Writes the sorted FP64 positions, label,
+// material and id, the bucket range of each occupied bucket (ranges of empty buckets stay 0,0 from
+// the memset), and the interaction record of the particle.
+// ---------------------------------------------------------------------------------------------
+template <bool SPLIT>
+__global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const uint32_t *__restrict__ skey,
+                                                 const uint32_t *__restrict__ perm, State A,
+                                                 double *__restrict__ xs, double *__restrict__ ys,
+                                                 double *__restrict__ zs, uint8_t *__restrict__ lab_s,
+                                                 uint8_t *__restrict__ mat_s, uint32_t *__restrict__ id_s,
+                                                 uint2 *__restrict__ cellr, void *__restrict__ pos_out,
+                                                 void *__restrict__ rec_out, int *__restrict__ err) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    uint32_t k = skey[s];
+    uint32_t o = perm[s];
+    double x = A.f[FX][o], y = A.f[FY][o], z = A.f[FZ][o];
+    xs[s] = x; ys[s] = y; zs[s] = z;
+    uint8_t lab = A.label[o], mat = A.mat[o];
+    // invalid values are reported and clamped so that no later kernel indexes out of range
+    if (lab >= P.K_labels) { atomicOr(err, kErrLabel); lab = 0; }
+    if (mat >= P.nmat) { atomicOr(err, kErrMaterial); mat = 0; }
+    lab_s[s] = lab;
+    mat_s[s] = mat;
+    id_s[s] = A.id[o];
+    if (k < P.ncell) {
+        if (s == 0 || skey[s - 1] != k) cellr[k].x = (uint32_t)s;
+        if (s == n - 1 || skey[s + 1] != k) cellr[k].y = (uint32_t)(s + 1);
+    }
+    double w = A.f[FW][o], m = A.f[FM][o];
+    double vx = A.f[FVX][o], vy = A.f[FVY][o], vz = A.f[FVZ][o];
+    double E = A.f[FE][o];
+    double sxx = A.f[FSXX][o], syy = A.f[FSYY][o], szz = A.f[FSZZ][o];
+    double sxy = A.f[FSXY][o], sxz = A.f[FSXZ][o], syz = A.f[FSYZ][o];
+    if (SPLIT) {
+        RecF r;
+        float4 p4 = make_float4(0.f, 0.f, 0.f, (float)w);
+        if (k < P.ncell) {
+            int cx, cy, cz;
+            decode_cell(P, k, cx, cy, cz);
+            // position relative to the particle's own bucket corner: |.| < 2h, so FP32 keeps it to
+            // about 2^-24 * 2h
+            p4.x = (float)(x - (P.lo[0] + (double)cx * P.cell));
+            p4.y = (float)(y - (P.lo[1] + (double)cy * P.cell));
+            p4.z = (float)(z - (P.lo[2] + (double)cz * P.cell));
+        }
+        // p = K (rho/rho0 - 1) = K (m - rho0 w) / (rho0 w): the cancelling difference in FP64
+        double rw = P.rho0[mat] * w;
+        float pf = P.f_K[mat] * (float)(m - rw) / (float)rw;
+        float rho = (float)m / (float)w;
+        float c = sqrtf(P.f_Mmod[mat] / rho);
+        r.a = make_float4((float)vx, (float)vy, (float)vz, rho);
+        r.b = make_float4(pf, rho * c, (float)E, (float)sxx);
+        r.c = make_float4((float)syy, (float)sxy, (float)sxz, (float)syz);
+        ((float4 *)pos_out)[s] = p4;
+        ((RecF *)rec_out)[s] = r;
+        (void)szz;
+    } else {
+        RecD r;
+        double rho = m / w;
+        double pr = P.K[mat] * (rho / P.rho0[mat] - 1.0);
+        double c = sqrt(P.Mmod[mat] / rho);
+        r.a = make_d4(vx, vy, vz, rho);
+        r.b = make_d4(pr, rho * c, E, sxx);
+        r.c = make_d4(syy, szz, sxy, sxz);
+        r.d = make_d4(syz, 0.0, 0.0, 0.0);
+        ((D4 *)pos_out)[s] = make_d4(x, y, z, w);
+        ((RecD *)rec_out)[s] = r;
+    }
+}
+
+cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint32_t *perm,
+                           const State &A, double *xs, double *ys, double *zs, uint8_t *lab_s, uint8_t *mat_s,
+                           uint32_t *id_s, uint2 *cellr, void *pos, void *rec, int *err, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    unsigned g = (unsigned)((n + 255) / 256);
+    if (split)
+        k_reorder<true><<<g, 256, 0, s>>>(P, n, skey, perm, A, xs, ys, zs, lab_s, mat_s, id_s, cellr, pos, rec, err);
+    else
+        k_reorder<false><<<g, 256, 0, s>>>(P, n, skey, perm, A, xs, ys, zs, lab_s, mat_s, id_s, cellr, pos, rec, err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Communication hash (Sec. II steps b-c with K virtual labels). On one device the hash broadcast of
+// step b becomes a per-bucket OR of label bits: mask[c] has bit k set when a particle of label k
+// is in bucket c. A particle is an MGPU boundary particle when the 27 buckets around it hold a
+// label other than its own.
+// ---------------------------------------------------------------------------------------------
+__global__ void k_label_mask(DevParams P, int64_t n, const uint32_t *__restrict__ skey,
+                             const uint8_t *__restrict__ lab_s, uint32_t *__restrict__ mask) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t k = s < n ? skey[s] : 0xffffffffu;
+    uint32_t bit = (s < n && k < P.ncell) ? (1u << (lab_s[s] & 31)) : 0u;
+    // sorted keys: lanes of one bucket combine their bits first, one atomic per bucket and warp
+    unsigned peers = __match_any_sync(kFullMask, k);
+    uint32_t acc = __reduce_or_sync(peers, bit);
+    if (s < n && k < P.ncell && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicOr(&mask[k], acc);
+}
+
+// Flags, communication hash and per-block counts per label (block_counts[label * nblk + block]).
+constexpr int CM_THREADS = 256;
+__global__ void __launch_bounds__(CM_THREADS) k_comm(DevParams P, int64_t n, const uint32_t *__restrict__ skey,
+                                                     const uint8_t *__restrict__ lab_s,
+                                                     const uint32_t *__restrict__ mask, uint8_t *__restrict__ flag,
+                                                     uint32_t *__restrict__ comm, uint32_t *__restrict__ block_counts,
+                                                     int nblk) {
+    __shared__ uint32_t cnt[kMaxLabel];
+    if (threadIdx.x < kMaxLabel) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) {
+        uint32_t k = skey[s];
+        uint8_t f = 0;
+        if (k < P.ncell) {
+            int cx, cy, cz;
+            decode_cell(P, k, cx, cy, cz);
+            uint32_t acc = 0;
+            for (int dz = -1; dz <= 1; ++dz) {
+                int Z = cz + dz;
+                if (Z < 0 || Z >= P.dims[2]) continue;
+                for (int dy = -1; dy <= 1; ++dy) {
+                    int Y = cy + dy;
+                    if (Y < 0 || Y >= P.dims[1]) continue;
+                    uint32_t row = (uint32_t)P.dims[0] * ((uint32_t)Y + (uint32_t)P.dims[1] * (uint32_t)Z);
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int X = cx + dx;
+                        if (X < 0 || X >= P.dims[0]) continue;
+                        acc |= __ldg(mask + row + (uint32_t)X);
+                    }
+                }
+            }
+            uint32_t lab = lab_s[s];
+            f = (acc & ~(1u << lab)) != 0u;
+            if (f) atomicAdd(&cnt[lab], 1u);
+        }
+        flag[s] = f;
+        comm[s] = f ? k : P.ncell;
+    }
+    __syncthreads();
+    if (threadIdx.x < P.K_labels) block_counts[(size_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Exclusive scan of the label-major block counts (single block; K * nblk entries), total per label
+// into label_total[0..K) and the overall total into label_total[K].
+__global__ void __launch_bounds__(1024) k_comm_scan(uint32_t *__restrict__ block_counts, int64_t entries,
+                                                    int nblk, int K, unsigned long long *__restrict__ label_total) {
+    __shared__ uint32_t warp_tmp[32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    uint32_t carry = 0;
+    for (int64_t b = 0; b < entries; b += 1024) {
+        int64_t i = b + threadIdx.x;
+        uint32_t v = i < entries ? block_counts[i] : 0u;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFullMask, x, o);
+            if (l >= o) x += y;
+        }
+        if (l == 31) warp_tmp[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t t = warp_tmp[l];
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(kFullMask, t, o);
+                if (l >= o) t += y;
+            }
+            warp_tmp[l] = t;
+        }
+        __syncthreads();
+        uint32_t e = carry + (w > 0 ? warp_tmp[w - 1] : 0u) + x - v;
+        if (i < entries) {
+            block_counts[i] = e;
+            // the first entry of each label row starts that label's list
+            if (i % nblk == 0) label_total[i / nblk] = e;
+        }
+        carry += warp_tmp[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) label_total[K] = carry;
+}
+
+// Stable compaction of the flagged slots into label-major lists (slot order = communication-hash
+// order within a label, since slots are sorted by hash and flagged particles keep their hash).
+__global__ void __launch_bounds__(CM_THREADS) k_boundary_scatter(int64_t n, const uint8_t *__restrict__ lab_s,
+                                                                 const uint8_t *__restrict__ flag,
+                                                                 const uint32_t *__restrict__ block_offsets,
+                                                                 int nblk, uint32_t *__restrict__ out) {
+    constexpr int W = CM_THREADS / 32;
+    __shared__ uint32_t wc[W][kMaxLabel];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool f = s < n && flag[s];
+    uint32_t lab = f ? lab_s[s] : 0xffffffffu;
+    unsigned peers = __match_any_sync(kFullMask, lab);
+    uint32_t rank = __popc(peers & lanemask_lt());
+    for (int i = threadIdx.x; i < W * kMaxLabel; i += CM_THREADS) (&wc[0][0])[i] = 0;
+    __syncthreads();
+    if (f && (__ffs(peers) - 1) == l) wc[w][lab] = __popc(peers);
+    __syncthreads();
+    if (f) {
+        uint32_t before = 0;
+        for (int k = 0; k < w; ++k) before += wc[k][lab];
+        out[block_offsets[(size_t)lab * nblk + blockIdx.x] + before + rank] = (uint32_t)s;
+    }
+}
+
+cudaError_t launch_comm(const DevParams &P, int64_t n, const uint32_t *skey, const uint8_t *lab_s, uint32_t *mask,
+                        uint8_t *flag, uint32_t *comm, uint32_t *block_counts, unsigned long long *label_total,
+                        uint32_t *blist, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(mask, 0, (size_t)P.ncell * 4, s);
+    if (e != cudaSuccess) return e;
+    unsigned g = (unsigned)((n + CM_THREADS - 1) / CM_THREADS);
+    k_label_mask<<<g, CM_THREADS, 0, s>>>(P, n, skey, lab_s, mask);
+    k_comm<<<g, CM_THREADS, 0, s>>>(P, n, skey, lab_s, mask, flag, comm, block_counts, (int)g);
+    k_comm_scan<<<1, 1024, 0, s>>>(block_counts, (int64_t)P.K_labels * g, (int)g, P.K_labels, label_total);
+    k_boundary_scatter<<<g, CM_THREADS, 0, s>>>(n, lab_s, flag, block_counts, (int)g, blist);
+    return cudaGetLastError();
+}
+
+int comm_blocks(int64_t n) { return (int)((n + CM_THREADS - 1) / CM_THREADS); }
+
+// ---------------------------------------------------------------------------------------------
+// Initialisation from user arrays (pos/vel n x 3 row-major).
+// ---------------------------------------------------------------------------------------------
+__global__ void k_init_state(DevParams P, int64_t n, const double *__restrict__ pos, const double *__restrict__ vel,
+                             const double *__restrict__ vol, const uint8_t *__restrict__ mat,
+                             const uint8_t *__restrict__ lab, State A, int *__restrict__ err) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double vx = vel[3 * i], vy = vel[3 * i + 1], vz = vel[3 * i + 2];
+    A.f[FX][i] = pos[3 * i];
+    A.f[FY][i] = pos[3 * i + 1];
+    A.f[FZ][i] = pos[3 * i + 2];
+    A.f[FVX][i] = vx;
+    A.f[FVY][i] = vy;
+    A.f[FVZ][i] = vz;
+    uint8_t m = mat[i], l = lab[i];
+    if (m >= P.nmat) { atomicOr(err, kErrMaterial); m = 0; }
+    if (l >= P.K_labels) atomicOr(err, kErrLabel);
+    A.f[FW][i] = vol[i];
+    A.f[FM][i] = __dmul_rn(P.rho0[m], vol[i]);
+    A.f[FE][i] = __dmul_rn(0.5, dist2_rn(vx, vy, vz));
+    for (int k = FSXX; k <= FSYZ; ++k) A.f[k][i] = 0.0;
+    A.mat[i] = m;
+    A.label[i] = l;
+    A.id[i] = (uint32_t)i;
+}
+
+cudaError_t launch_init(const DevParams &P, int64_t n, const double *pos, const double *vel, const double *vol,
+                        const uint8_t *mat, const uint8_t *lab, const State &A, int *err, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_init_state<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, n, pos, vel, vol, mat, lab, A, err);
+    return cudaGetLastError();
+}
+
+// Maximum signal speed over the state (bit pattern of a non-negative double, so integer max is
+// the floating-point max), then dt = cfl * h / max.
+__global__ void k_signal_max(DevParams P, int64_t n, State A, unsigned long long *__restrict__ sig) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (i < n) {
+        int m = A.mat[i] < P.nmat ? A.mat[i] : 0;
+        v = signal_speed(P, m, A.f[FM][i], A.f[FW][i], A.f[FVX][i], A.f[FVY][i], A.f[FVZ][i]);
+    }
+    unsigned long long b = __double_as_longlong(v);
+    for (int o = 16; o; o >>= 1) {
+        unsigned long long c = __shfl_xor_sync(kFullMask, b, o);
+        b = c > b ? c : b;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(sig, b);
+}
+
+__global__ void k_finalize_dt(DevParams P, unsigned long long *__restrict__ sig, double *__restrict__ dt) {
+    double mx = __longlong_as_double((long long)*sig);
+    *dt = __ddiv_rn(__dmul_rn(P.cfl, P.h), mx);
+    *sig = 0ull;
+}
+
+cudaError_t launch_dt_from_state(const DevParams &P, int64_t n, const State &A, unsigned long long *sig, double *dt,
+                                 cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(sig, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    if (n > 0) k_signal_max<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, n, A, sig);
+    k_finalize_dt<<<1, 1, 0, s>>>(P, sig, dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_dt(const DevParams &P, unsigned long long *sig, double *dt, cudaStream_t s) {
+    k_finalize_dt<<<1, 1, 0, s>>>(P, sig, dt);
+    return cudaGetLastError();
+}
+
+// FP64 conserved sums {m, m vx, m vy, m vz, m E, w}: per-block partials, then one block adds the
+// partials in block order (deterministic).
+__global__ void __launch_bounds__(256) k_conserved_partial(int64_t n, State A, double *__restrict__ part) {
+    __shared__ double sh[6][256];
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    if (i < n) {
+        double m = A.f[FM][i];
+        v[0] = m;
+        v[1] = m * A.f[FVX][i];
+        v[2] = m * A.f[FVY][i];
+        v[3] = m * A.f[FVZ][i];
+        v[4] = m * A.f[FE][i];
+        v[5] = A.f[FW][i];
+    }
+    for (int k = 0; k < 6; ++k) sh[k][threadIdx.x] = v[k];
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+            for (int k = 0; k < 6; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) part[(size_t)blockIdx.x * 6 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_conserved_final(int nblk, const double *__restrict__ part, double *__restrict__ out) {
+    if (threadIdx.x < 6) {
+        double acc = 0.0;
+        for (int b = 0; b < nblk; ++b) acc += part[(size_t)b * 6 + threadIdx.x];
+        out[threadIdx.x] = acc;
+    }
+}
+
+cudaError_t launch_conserved(int64_t n, const State &A, double *part, double *out, cudaStream_t s) {
+    int nblk = (int)((n + 255) / 256);
+    if (nblk < 1) nblk = 1;
+    k_conserved_partial<<<nblk, 256, 0, s>>>(n, A, part);
+    k_conserved_final<<<1, 32, 0, s>>>(nblk, part, out);
+    return cudaGetLastError();
+}
+
+}  // namespace gsph

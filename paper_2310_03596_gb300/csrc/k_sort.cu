@@ -1,0 +1,248 @@
+// k_sort.cu - bucket hash (Sec. I) and the LSD radix sort of (hash, slot) pairs (Sec. I).
+//
+// Radix sort: 8-bit digits, one pass per digit. Each pass is three launches:
+//   k_rs_hist    per-tile digit histogram (tile = 4096 keys), warp-aggregated shared atomics;
+//   k_rs_rowscan one block per digit: exclusive scan of that digit's per-tile counts, digit total;
+//   k_rs_scatter reloads the tile, ranks each key among equal digits in tile order (warp match_any,
+//                per-warp counters, cross-warp prefix), scatters keys and values.
+// The ranking follows tile order, so every pass is stable and the sort is stable overall.
+// Bytes per key per pass: 4 (hist) + 8 read + 8 written (scatter) + 2*4*256/4096 (counts).
+#include "gsph_internal.cuh"
+
+namespace gsph {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_IPT = 16;
+constexpr int RS_TILE = RS_THREADS * RS_IPT;
+constexpr int RS_BINS = 256;
+
+// Item order inside a tile: warp-major, then round, then lane (each round reads 32 consecutive
+// keys, so loads are coalesced and the item order is the key order).
+__device__ __forceinline__ int64_t rs_item(int64_t tile_base, int w, int r, int l) {
+    return tile_base + (int64_t)w * (32 * RS_IPT) + r * 32 + l;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t *__restrict__ keys, int64_t n,
+                                                        int shift, uint32_t *__restrict__ hist, int nblk) {
+    __shared__ uint32_t sh[RS_BINS];
+    for (int i = threadIdx.x; i < RS_BINS; i += RS_THREADS) sh[i] = 0;
+    __syncthreads();
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+#pragma unroll 4
+    for (int r = 0; r < RS_IPT; ++r) {
+        int64_t idx = rs_item(base, w, r, l);
+        bool valid = idx < n;
+        uint32_t d = valid ? (__ldg(keys + idx) >> shift) & 0xffu : 0xffffffffu;
+        unsigned peers = __match_any_sync(kFullMask, d);
+        if (valid && (__ffs(peers) - 1) == l) atomicAdd(&sh[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < RS_BINS; i += RS_THREADS) hist[(size_t)i * nblk + blockIdx.x] = sh[i];
+}
+
+// Block-wide exclusive scan helper (blockDim.x == 1024); returns the exclusive prefix of v and
+// the block total in *total.
+__device__ __forceinline__ uint32_t block_excl_scan_1024(uint32_t v, uint32_t *warp_tmp, uint32_t *total) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFullMask, x, o);
+        if (l >= o) x += y;
+    }
+    if (l == 31) warp_tmp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = warp_tmp[l];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFullMask, s, o);
+            if (l >= o) s += y;
+        }
+        warp_tmp[l] = s;  // inclusive over warps
+    }
+    __syncthreads();
+    uint32_t before = (w > 0 ? warp_tmp[w - 1] : 0u) + x - v;
+    *total = warp_tmp[31];
+    __syncthreads();
+    return before;
+}
+
+__global__ void __launch_bounds__(1024) k_rs_rowscan(uint32_t *__restrict__ hist, int nblk,
+                                                     uint32_t *__restrict__ tot) {
+    __shared__ uint32_t warp_tmp[32];
+    uint32_t *row = hist + (size_t)blockIdx.x * nblk;
+    uint32_t carry = 0;
+    for (int b = 0; b < nblk; b += 1024) {
+        int i = b + threadIdx.x;
+        uint32_t v = i < nblk ? row[i] : 0u;
+        uint32_t t;
+        uint32_t e = block_excl_scan_1024(v, warp_tmp, &t);
+        if (i < nblk) row[i] = carry + e;
+        carry += t;
+    }
+    if (threadIdx.x == 0) tot[blockIdx.x] = carry;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *__restrict__ kin,
+                                                           const uint32_t *__restrict__ vin,
+                                                           uint32_t *__restrict__ kout,
+                                                           uint32_t *__restrict__ vout, int64_t n,
+                                                           int shift, const uint32_t *__restrict__ hist,
+                                                           const uint32_t *__restrict__ tot, int nblk) {
+    __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
+    __shared__ uint32_t base_sh[RS_BINS];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    // digit bases: exclusive scan of the digit totals plus this tile's exclusive offset
+    {
+        const int d = threadIdx.x;  // RS_THREADS == RS_BINS
+        uint32_t t = tot[d];
+        uint32_t x = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFullMask, x, o);
+            if (l >= o) x += y;
+        }
+        __shared__ uint32_t ws[RS_WARPS];
+        if (l == 31) ws[w] = x;
+        for (int k = 0; k < RS_WARPS; ++k) wcnt[k][d] = 0;
+        __syncthreads();
+        uint32_t pre = 0;
+        for (int k = 0; k < w; ++k) pre += ws[k];
+        base_sh[d] = pre + x - t + hist[(size_t)d * nblk + blockIdx.x];
+    }
+    __syncthreads();
+    uint32_t key[RS_IPT], val[RS_IPT], rank[RS_IPT];
+#pragma unroll
+    for (int r = 0; r < RS_IPT; ++r) {
+        int64_t idx = rs_item(base, w, r, l);
+        bool valid = idx < n;
+        key[r] = valid ? __ldg(kin + idx) : 0xffffffffu;
+        val[r] = valid ? __ldg(vin + idx) : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < RS_IPT; ++r) {
+        uint32_t d = (key[r] >> shift) & 0xffu;
+        unsigned peers = __match_any_sync(kFullMask, d);
+        uint32_t before = wcnt[w][d];
+        rank[r] = before + __popc(peers & lanemask_lt());
+        __syncwarp();
+        if ((__ffs(peers) - 1) == l) wcnt[w][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;
+        uint32_t run = 0;
+#pragma unroll
+        for (int k = 0; k < RS_WARPS; ++k) {
+            uint32_t t = wcnt[k][d];
+            wcnt[k][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_IPT; ++r) {
+        int64_t idx = rs_item(base, w, r, l);
+        if (idx < n) {
+            uint32_t d = (key[r] >> shift) & 0xffu;
+            uint32_t pos = base_sh[d] + wcnt[w][d] + rank[r];
+            kout[pos] = key[r];
+            vout[pos] = val[r];
+        }
+    }
+}
+
+// Sec. I: bucket hash of every slot; val = slot. Counts particles outside the grid.
+__global__ void k_hash(DevParams P, int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                       const double *__restrict__ z, uint32_t *__restrict__ key, uint32_t *__restrict__ val,
+                       unsigned long long *__restrict__ garbage) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool g = false;
+    if (i < n) {
+        uint32_t k = hash_of(P, x[i], y[i], z[i]);
+        key[i] = k;
+        val[i] = (uint32_t)i;
+        g = (k == P.ncell);
+    }
+    unsigned b = __ballot_sync(kFullMask, g);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(garbage, (unsigned long long)__popc(b));
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------------------
+static inline int rs_nblk(int64_t n) { return (int)((n + RS_TILE - 1) / RS_TILE); }
+
+size_t radix_hist_words(int64_t n) { return (size_t)RS_BINS * (size_t)(rs_nblk(n) > 0 ? rs_nblk(n) : 1); }
+
+// Sorts (k0, v0) by the low `bits` bits using (k1, v1) as the other buffer. Returns true when the
+// result ends in (k1, v1).
+cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t *hist,
+                             uint32_t *tot, int64_t n, int bits, cudaStream_t s, bool *in_alt) {
+    *in_alt = false;
+    if (n <= 0) return cudaSuccess;
+    int nblk = rs_nblk(n);
+    int passes = (bits + 7) / 8;
+    uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
+    for (int p = 0; p < passes; ++p) {
+        int shift = 8 * p;
+        k_rs_hist<<<nblk, RS_THREADS, 0, s>>>(ki, n, shift, hist, nblk);
+        k_rs_rowscan<<<RS_BINS, 1024, 0, s>>>(hist, nblk, tot);
+        k_rs_scatter<<<nblk, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, hist, tot, nblk);
+        uint32_t *t = ki; ki = ko; ko = t;
+        t = vi; vi = vo; vo = t;
+    }
+    *in_alt = (passes & 1) != 0;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hash(const DevParams &P, int64_t n, const double *x, const double *y, const double *z,
+                        uint32_t *key, uint32_t *val, unsigned long long *garbage, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int th = 256;
+    k_hash<<<(unsigned)((n + th - 1) / th), th, 0, s>>>(P, n, x, y, z, key, val, garbage);
+    return cudaGetLastError();
+}
+
+}  // namespace gsph
+
+// ---------------------------------------------------------------------------------------------
+// Stateless C-ABI sort
+// ---------------------------------------------------------------------------------------------
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+extern "C" size_t gsph_radix_sort_workspace(int64_t n, int32_t key_bits) {
+    (void)key_bits;
+    if (n < 0) return 0;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    return align256(nn * 4) * 2 + align256(gsph::radix_hist_words(n) * 4) + align256(gsph::RS_BINS * 4);
+}
+
+extern "C" gsph_status gsph_radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, int32_t key_bits,
+                                             void *workspace, size_t workspace_bytes, void *stream) {
+    if (n < 0 || n >= ((int64_t)1 << 31) || key_bits < 1 || key_bits > 32) return GSPH_INVALID_ARG;
+    if (n == 0) return GSPH_OK;
+    if (!keys || !vals || !workspace) return GSPH_INVALID_ARG;
+    if (workspace_bytes < gsph_radix_sort_workspace(n, key_bits)) return GSPH_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *p = (char *)workspace;
+    uint32_t *k1 = (uint32_t *)p;
+    p += align256((size_t)n * 4);
+    uint32_t *v1 = (uint32_t *)p;
+    p += align256((size_t)n * 4);
+    uint32_t *hist = (uint32_t *)p;
+    p += align256(gsph::radix_hist_words(n) * 4);
+    uint32_t *tot = (uint32_t *)p;
+    bool alt = false;
+    cudaError_t e = gsph::radix_sort_pairs(keys, vals, k1, v1, hist, tot, n, key_bits, s, &alt);
+    if (e == cudaSuccess && alt) {
+        e = cudaMemcpyAsync(keys, k1, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(vals, v1, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+    }
+    return e == cudaSuccess ? GSPH_OK : GSPH_CUDA_ERROR;
+}

@@ -1,0 +1,301 @@
+"""Thin ctypes binding of libgsph (include/gsph.h): argument marshalling only.
+
+Every step of the hot path runs in the CUDA library. PyTorch provides device buffers and streams
+where the caller wants them (torch tensors on the context's GPU are passed by data pointer). If the
+library is missing, load() raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgsph.so")
+
+MAX_MAT, MAX_WALL, MAX_LABEL, NRATE = 4, 6, 16, 15
+FP64, FP32_SPLIT = 0, 1
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "device out of memory", 3: "CUDA error",
+          4: "particles left the bucket grid", 5: "bounded device wait timed out", 6: "no particles loaded",
+          7: "invalid data found on the device"}
+OK, INVALID_ARG, OOM, CUDA_ERROR, PARTICLE_LEFT_DOMAIN, DEVICE_TIMEOUT, NOT_READY, DEVICE_ERROR = range(8)
+
+# gsph_field
+FIELDS = ["x", "y", "z", "vx", "vy", "vz", "w", "m", "E", "sxx", "syy", "szz", "sxy", "sxz", "syz",
+          "material", "label", "id", "hash", "comm_hash", "flag", "nreal", "nimage", "rates", "boundary"]
+FIELD = {name: k for k, name in enumerate(FIELDS)}
+FIELD_DTYPE = {**{f: np.float64 for f in FIELDS[:15]}, "material": np.uint8, "label": np.uint8,
+               "id": np.uint32, "hash": np.uint32, "comm_hash": np.uint32, "flag": np.uint8,
+               "nreal": np.int32, "nimage": np.int32, "rates": np.float64, "boundary": np.uint32}
+
+
+class GsphError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+class Material(C.Structure):
+    _fields_ = [("rho0", C.c_double), ("K", C.c_double), ("G", C.c_double), ("Y", C.c_double)]
+
+
+class Wall(C.Structure):
+    _fields_ = [("axis", C.c_int32), ("pad", C.c_int32), ("pos", C.c_double)]
+
+
+class Config(C.Structure):
+    _fields_ = [("grid_lo", C.c_double * 3), ("grid_dims", C.c_int32 * 3), ("n_materials", C.c_int32),
+                ("h", C.c_double), ("cfl", C.c_double), ("materials", Material * MAX_MAT),
+                ("n_walls", C.c_int32), ("K", C.c_int32), ("walls", Wall * MAX_WALL),
+                ("gravity", C.c_double * 3), ("alpha", C.c_double), ("swap_period", C.c_int32),
+                ("precision", C.c_int32), ("device", C.c_int32), ("diagnostics", C.c_int32)]
+
+
+class ExchangeStats(C.Structure):
+    _fields_ = [("step", C.c_int64), ("n", C.c_int64), ("K", C.c_int32), ("pad", C.c_int32),
+                ("garbage", C.c_int64), ("boundary", C.c_int64 * MAX_LABEL), ("boundary_total", C.c_int64),
+                ("exchange_fraction", C.c_double), ("record_bytes", C.c_int64),
+                ("bytes_hash_broadcast", C.c_int64), ("bytes_boundary_broadcast", C.c_int64),
+                ("bytes_swap", C.c_int64), ("swapped_last_pass", C.c_int64), ("swap_passes", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("pad", "boundary")}
+        d["boundary"] = list(self.boundary)[: self.K]
+        return d
+
+
+class Timings(C.Structure):
+    _fields_ = [("hash_sort_ms", C.c_double), ("reorder_ms", C.c_double), ("swap_ms", C.c_double),
+                ("comm_ms", C.c_double), ("interact_ms", C.c_double), ("steps", C.c_int64),
+                ("interact_launches", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+EXPORTS = ["gsph_status_str", "gsph_create", "gsph_destroy", "gsph_set_particles", "gsph_put_field",
+           "gsph_get_field", "gsph_step", "gsph_swap_now", "gsph_sync", "gsph_get_exchange_stats",
+           "gsph_get_conserved", "gsph_get_dt", "gsph_get_sizes", "gsph_set_timing", "gsph_get_timings",
+           "gsph_radix_sort_workspace", "gsph_radix_sort_pairs"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH):
+    """Loads libgsph.so (built by paper_2310_03596_gb300.build). Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgsph.so is not built ({path}); run paper_2310_03596_gb300.build.build()")
+        L = C.CDLL(path)
+        P, vp = C.POINTER, C.c_void_p
+        L.gsph_status_str.argtypes = [C.c_int]
+        L.gsph_status_str.restype = C.c_char_p
+        L.gsph_create.argtypes = [P(Config), P(vp)]
+        L.gsph_destroy.argtypes = [vp]
+        L.gsph_destroy.restype = None
+        L.gsph_set_particles.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, C.c_int32, vp]
+        L.gsph_put_field.argtypes = [vp, C.c_int, vp, C.c_int32, vp]
+        L.gsph_get_field.argtypes = [vp, C.c_int, vp, C.c_int32, vp]
+        L.gsph_step.argtypes = [vp, C.c_int32, vp]
+        L.gsph_swap_now.argtypes = [vp, vp]
+        L.gsph_sync.argtypes = [vp, vp]
+        L.gsph_get_exchange_stats.argtypes = [vp, vp, P(ExchangeStats)]
+        L.gsph_get_conserved.argtypes = [vp, vp, P(C.c_double)]
+        L.gsph_get_dt.argtypes = [vp, vp, P(C.c_double)]
+        L.gsph_get_sizes.argtypes = [vp, P(C.c_int64), P(C.c_int64)]
+        L.gsph_set_timing.argtypes = [vp, C.c_int32]
+        L.gsph_get_timings.argtypes = [vp, P(Timings)]
+        L.gsph_radix_sort_workspace.argtypes = [C.c_int64, C.c_int32]
+        L.gsph_radix_sort_workspace.restype = C.c_size_t
+        L.gsph_radix_sort_pairs.argtypes = [vp, vp, C.c_int64, C.c_int32, vp, C.c_size_t, vp]
+        _lib = L
+        return L
+
+
+def check(code: int, what: str, allow=(OK,)) -> int:
+    if code not in allow:
+        raise GsphError(code, what)
+    return code
+
+
+def config_from_scene(scene, precision: int = FP32_SPLIT, device: int = 0, diagnostics: bool = False) -> Config:
+    c = Config()
+    for a in range(3):
+        c.grid_lo[a] = scene.grid_lo[a]
+        c.grid_dims[a] = scene.grid_dims[a]
+        c.gravity[a] = scene.gravity[a]
+    c.n_materials = len(scene.materials)
+    for k, (rho0, K, G, Y) in enumerate(scene.materials):
+        c.materials[k] = Material(rho0, K, G, Y)
+    c.h = scene.h
+    c.cfl = scene.cfl
+    c.n_walls = len(scene.walls)
+    for k, (axis, pos) in enumerate(scene.walls):
+        c.walls[k] = Wall(axis, 0, pos)
+    c.K = scene.K
+    c.alpha = scene.alpha
+    c.swap_period = scene.swap_period
+    c.precision = precision
+    c.device = device
+    c.diagnostics = int(diagnostics)
+    return c
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+class Solver:
+    """One libgsph context (one particle set on one GPU)."""
+
+    def __init__(self, config: Config):
+        self.L = load()
+        self.cfg = config
+        h = C.c_void_p()
+        check(self.L.gsph_create(C.byref(config), C.byref(h)), "gsph_create")
+        self.h = h
+        self.n = 0
+
+    @classmethod
+    def from_scene(cls, scene, precision: int = FP32_SPLIT, device: int = 0, diagnostics: bool = False,
+                   stream=None) -> "Solver":
+        s = cls(config_from_scene(scene, precision, device, diagnostics))
+        s.set_particles(scene.pos, scene.vel, scene.vol, scene.material, scene.label, stream=stream)
+        return s
+
+    def close(self) -> None:
+        if self.h:
+            self.L.gsph_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------------------------- state
+    def set_particles(self, pos, vel, vol, material, label, stream=None) -> None:
+        arrs = [pos, vel, vol, material, label]
+        if all(_is_torch(a) and a.is_cuda for a in arrs):
+            for a in arrs:
+                assert a.is_contiguous()
+            ptrs = [a.data_ptr() for a in arrs]
+            n = int(vol.shape[0])
+            on_dev = 1
+            keep = arrs
+        else:
+            keep = [np.ascontiguousarray(pos, np.float64), np.ascontiguousarray(vel, np.float64),
+                    np.ascontiguousarray(vol, np.float64), np.ascontiguousarray(material, np.uint8),
+                    np.ascontiguousarray(label, np.uint8)]
+            ptrs = [a.ctypes.data for a in keep]
+            n = int(keep[2].shape[0])
+            on_dev = 0
+        check(self.L.gsph_set_particles(self.h, n, *ptrs, on_dev, _stream_handle(stream)), "gsph_set_particles")
+        self.n = n
+        del keep
+
+    def step(self, nsteps: int = 1, stream=None) -> None:
+        check(self.L.gsph_step(self.h, int(nsteps), _stream_handle(stream)), "gsph_step")
+
+    def swap_now(self, stream=None) -> None:
+        check(self.L.gsph_swap_now(self.h, _stream_handle(stream)), "gsph_swap_now")
+
+    def sync(self, stream=None) -> None:
+        check(self.L.gsph_sync(self.h, _stream_handle(stream)), "gsph_sync")
+
+    def _count(self, field: str) -> int:
+        if field == "rates":
+            return self.n * NRATE
+        if field == "boundary":
+            return int(self.exchange_stats()["boundary_total"])
+        return self.n
+
+    def get(self, field: str, stream=None) -> np.ndarray:
+        """Copies one field to a new numpy array (host)."""
+        cnt = self._count(field)
+        out = np.empty(max(cnt, 1), FIELD_DTYPE[field])
+        check(self.L.gsph_get_field(self.h, FIELD[field], out.ctypes.data, 0, _stream_handle(stream)),
+              f"gsph_get_field({field})")
+        out = out[:cnt]
+        return out.reshape(self.n, NRATE) if field == "rates" else out
+
+    def get_into(self, field: str, dst, stream=None) -> None:
+        """Copies one field into a device tensor (torch, on the context's GPU)."""
+        check(self.L.gsph_get_field(self.h, FIELD[field], dst.data_ptr(), 1, _stream_handle(stream)),
+              f"gsph_get_field({field})")
+
+    def put(self, field: str, values, stream=None) -> None:
+        if _is_torch(values) and values.is_cuda:
+            check(self.L.gsph_put_field(self.h, FIELD[field], values.data_ptr(), 1, _stream_handle(stream)),
+                  f"gsph_put_field({field})")
+            return
+        a = np.ascontiguousarray(values, FIELD_DTYPE[field])
+        assert a.shape[0] == self.n
+        check(self.L.gsph_put_field(self.h, FIELD[field], a.ctypes.data, 0, _stream_handle(stream)),
+              f"gsph_put_field({field})")
+
+    def put_state(self, d: dict, stream=None) -> None:
+        for f in FIELDS[:18]:
+            if f in d:
+                self.put(f, d[f], stream)
+
+    def state(self, stream=None) -> dict:
+        return {f: self.get(f, stream) for f in FIELDS[:18]}
+
+    # ---------------------------------------------------------------------------- queries
+    def exchange_stats(self, stream=None) -> dict:
+        st = ExchangeStats()
+        check(self.L.gsph_get_exchange_stats(self.h, _stream_handle(stream), C.byref(st)), "gsph_get_exchange_stats",
+              allow=(OK, PARTICLE_LEFT_DOMAIN))
+        return st.as_dict()
+
+    def conserved(self, stream=None) -> np.ndarray:
+        out = (C.c_double * 6)()
+        check(self.L.gsph_get_conserved(self.h, _stream_handle(stream), out), "gsph_get_conserved")
+        return np.array(out[:])
+
+    def dt(self, stream=None) -> float:
+        v = C.c_double()
+        check(self.L.gsph_get_dt(self.h, _stream_handle(stream), C.byref(v)), "gsph_get_dt")
+        return v.value
+
+    def sizes(self):
+        n, c = C.c_int64(), C.c_int64()
+        check(self.L.gsph_get_sizes(self.h, C.byref(n), C.byref(c)), "gsph_get_sizes")
+        return n.value, c.value
+
+    def set_timing(self, max_steps: int) -> None:
+        check(self.L.gsph_set_timing(self.h, int(max_steps)), "gsph_set_timing")
+
+    def timings(self) -> dict:
+        t = Timings()
+        check(self.L.gsph_get_timings(self.h, C.byref(t)), "gsph_get_timings")
+        return t.as_dict()
+
+
+def radix_sort_pairs(keys, vals, key_bits: int, stream=None) -> None:
+    """Stable in-place sort of two uint32 device tensors (torch int32 views) by the low key_bits."""
+    import torch
+
+    L = load()
+    n = int(keys.numel())
+    ws_bytes = int(L.gsph_radix_sort_workspace(n, key_bits))
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=keys.device)
+    check(L.gsph_radix_sort_pairs(keys.data_ptr(), vals.data_ptr(), n, key_bits, ws.data_ptr(), ws_bytes,
+                                  _stream_handle(stream)), "gsph_radix_sort_pairs")

@@ -1,0 +1,210 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle on the same seeded inputs.
+
+Integer, index and order outputs (bucket hash, sort order, neighbour counts, flags, communication
+hash, boundary set, labels after swaps, dt) must match bit for bit. FP64 state must match within
+1e-12 of each field's max-norm per step; the split path within 2e-5 per step and 1e-3 after 100 free
+steps (spec tolerances; relative to the field's max-norm over particles).
+"""
+import numpy as np
+import pytest
+
+from oracle import orc
+from paper_2310_03596_gb300 import gsph, scenes
+
+pytestmark = pytest.mark.gpu
+
+STATE_F = orc.FIELDS
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _maxnorm_err(g, o):
+    scale = np.abs(o).max()
+    return np.abs(g - o).max() / scale if scale > 0 else np.abs(g - o).max()
+
+
+def _lockstep(scene, precision, steps, tol, swap=True):
+    P = orc.params_of(scene)
+    sol = gsph.Solver.from_scene(scene, precision=precision, diagnostics=True)
+    worst = {f: 0.0 for f in STATE_F}
+    try:
+        for k in range(steps):
+            st = orc.OracleState.from_arrays(sol.state())
+            do_swap = swap and scene.K > 1 and scene.swap_period > 0 and k % scene.swap_period == 0
+            dt_gpu = sol.dt()
+            out = orc.step(P, st, do_swap=do_swap, want_rates=True)
+            sol.step(1)
+            sol.sync()
+            assert dt_gpu == out["dt"]
+            assert np.array_equal(sol.get("hash"), out["key"]), "hash / sort order"
+            assert np.array_equal(sol.get("id"), st.id), "sort order"
+            assert np.array_equal(sol.get("label"), st.label), "labels"
+            assert np.array_equal(sol.get("material"), st.mat)
+            assert np.array_equal(sol.get("nreal"), out["nreal"]), "real neighbour counts"
+            assert np.array_equal(sol.get("nimage"), out["nimage"]), "image neighbour counts"
+            assert np.array_equal(sol.get("flag"), out["flag"]), "MGPU boundary flags"
+            assert np.array_equal(sol.get("comm_hash"), out["comm"]), "communication hash"
+            stats = sol.exchange_stats()
+            assert stats["boundary"] == out["count"].tolist()
+            off, lst = orc.boundary_lists(st.label, out["comm"], P.dims[0] * P.dims[1] * P.dims[2], scene.K)
+            assert np.array_equal(sol.get("boundary"), lst), "boundary set order"
+            for f in STATE_F:
+                e = _maxnorm_err(sol.get(f), getattr(st, f))
+                worst[f] = max(worst[f], e)
+                assert e <= tol, (k, f, e)
+    finally:
+        sol.close()
+    return worst
+
+
+def test_radix_sort_matches_stable_argsort():
+    import torch
+    rng = np.random.default_rng(0)
+    for n, bits in [(1, 8), (4095, 8), (4096, 12), (4097, 17), (100_003, 24), (1_000_000, 27), (70_000, 32)]:
+        k = rng.integers(0, 2 ** bits, size=n, dtype=np.uint64).astype(np.uint32)
+        if n > 1000:
+            k[: n // 3] = np.sort(k[: n // 3])      # a pre-sorted run, as after the previous step
+            k[n // 2: n // 2 + 500] = 7             # a long run of equal keys
+        keys = torch.from_numpy(k.view(np.int32)).cuda()
+        vals = torch.arange(n, dtype=torch.int32, device="cuda")
+        gsph.radix_sort_pairs(keys, vals, bits)
+        torch.cuda.synchronize()
+        perm = np.argsort(k, kind="stable")
+        assert np.array_equal(keys.cpu().numpy().view(np.uint32), k[perm])
+        assert np.array_equal(vals.cpu().numpy(), perm.astype(np.int32))
+
+
+@pytest.mark.parametrize("precision,tol", [(gsph.FP64, 1e-12), (gsph.FP32_SPLIT, 2e-5)])
+def test_cube_impact_lockstep(precision, tol):
+    # 16^3 cube on a wall, one label: 10 steps (the cube-impact workload at its stated size)
+    _lockstep(scenes.cube_impact(), precision, 10, tol)
+
+
+@pytest.mark.parametrize("precision,tol", [(gsph.FP64, 1e-12), (gsph.FP32_SPLIT, 2e-5)])
+def test_labels_swaps_and_boundary_lockstep(precision, tol):
+    # random labels, swap heuristic every step, ragged size (not a multiple of any block size)
+    s = scenes.taylor_bar(dx=0.5e-3, K=4, swap_period=1)
+    assert s.n % 128 != 0
+    _lockstep(s, precision, 4, tol)
+
+
+def test_two_materials_per_type_swaps_lockstep():
+    s = scenes.projectile_plate(dx=1e-3, plate=(20e-3, 20e-3, 4e-3), radius=3e-3, K=8, swap_period=1)
+    _lockstep(s, gsph.FP64, 3, 1e-12)
+
+
+def test_sixteen_labels_gravity_lockstep():
+    s = scenes.collapse_block(dx=4e-3, size=(0.12, 0.06, 0.04), K=16, swap_period=2)
+    _lockstep(s, gsph.FP32_SPLIT, 4, 2e-5)
+
+
+def test_split_free_running_100_steps():
+    s = scenes.cube_impact(n_side=12, steps=100)
+    P = orc.params_of(s)
+    st = orc.OracleState.from_scene(s)
+    for _ in range(100):
+        orc.step(P, st)
+    sol = gsph.Solver.from_scene(s, precision=gsph.FP32_SPLIT)
+    try:
+        sol.step(100)
+        sol.sync()
+        g = sol.state()
+        order = np.argsort(g["id"])
+        ref = np.argsort(st.id)
+        for f in STATE_F:
+            e = _maxnorm_err(g[f][order], getattr(st, f)[ref])
+            assert e <= 1e-3, (f, e)
+    finally:
+        sol.close()
+
+
+def test_conservation_on_device():
+    s = scenes.cube_impact(n_side=12)
+    sol = gsph.Solver.from_scene(s, precision=gsph.FP32_SPLIT)
+    try:
+        c0 = sol.conserved()
+        sol.step(20)
+        c1 = sol.conserved()
+        assert abs(c1[0] - c0[0]) <= 1e-9 * c0[0]          # mass
+        scale = abs(c0[3])
+        assert abs(c1[1] - c0[1]) <= 1e-6 * scale and abs(c1[2] - c0[2]) <= 1e-6 * scale   # x, y momentum
+        assert c1[3] > c0[3]                               # the wall pushes back
+    finally:
+        sol.close()
+
+
+def test_particles_outside_the_grid_are_garbage():
+    s = scenes.cube_impact(n_side=6)
+    s.pos[:5, 2] += 1.0          # far above the grid
+    sol = gsph.Solver.from_scene(s, precision=gsph.FP64, diagnostics=True)
+    try:
+        sol.step(1)
+        st = sol.exchange_stats()
+        assert st["garbage"] == 5
+        key = sol.get("hash")
+        C = s.grid_dims[0] * s.grid_dims[1] * s.grid_dims[2]
+        assert (key[-5:] == C).all() and (key[:-5] < C).all()
+        assert (sol.get("nreal")[-5:] == 0).all()
+    finally:
+        sol.close()
+
+
+def test_invalid_label_reported():
+    s = scenes.cube_impact(n_side=4)
+    s.label[3] = 5               # K = 1
+    c = gsph.config_from_scene(s, precision=gsph.FP64)
+    sol = gsph.Solver(c)
+    try:
+        with pytest.raises(gsph.GsphError) as ei:
+            sol.set_particles(s.pos, s.vel, s.vol, s.material, s.label)
+        assert ei.value.code == gsph.DEVICE_ERROR
+    finally:
+        sol.close()
+
+
+def test_single_particle_and_one_bucket():
+    s = scenes.cube_impact(n_side=1)
+    P = orc.params_of(s)
+    sol = gsph.Solver.from_scene(s, precision=gsph.FP64, diagnostics=True)
+    try:
+        st = orc.OracleState.from_arrays(sol.state())
+        orc.step(P, st)
+        sol.step(1)
+        for f in STATE_F:
+            assert _maxnorm_err(sol.get(f), getattr(st, f)) <= 1e-12
+    finally:
+        sol.close()
+    # many particles in a single bucket: everyone neighbours everyone
+    s = scenes.cube_impact(n_side=2, jitter=0.0, dx=0.4e-3)
+    s.h = 1.0e-3
+    s.walls = []
+    P = orc.params_of(s)
+    sol = gsph.Solver.from_scene(s, precision=gsph.FP32_SPLIT, diagnostics=True)
+    try:
+        st = orc.OracleState.from_arrays(sol.state())
+        out = orc.step(P, st)
+        sol.step(1)
+        assert np.array_equal(sol.get("nreal"), out["nreal"])
+        assert (out["nreal"] == 7).all()
+    finally:
+        sol.close()
+
+
+def test_swap_now_matches_oracle_pass():
+    for K, seed in ((2, 1), (5, 2), (16, 3)):
+        s = scenes.taylor_bar(dx=0.4e-3, K=K, seed=seed)
+        P = orc.params_of(s)
+        sol = gsph.Solver.from_scene(s, precision=gsph.FP64)
+        try:
+            st = orc.OracleState.from_arrays(sol.state())
+            moved, _ = orc.swap_pass(P, st)
+            sol.swap_now()
+            sol.sync()
+            assert np.array_equal(sol.get("label"), st.label), K
+            assert sol.exchange_stats()["swapped_last_pass"] == moved
+        finally:
+            sol.close()
