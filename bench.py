@@ -1,0 +1,373 @@
+"""Benchmark of the particle-decomposition Gamma-SPH-ALE hot path on GB300.
+
+Workload: the Taylor-bar impact (aluminium rod r 5 mm x 40 mm at dx 0.125 mm, 1,607,680 particles,
+200 m/s onto a rigid wall, K = 4 random ownership labels, communication hash every step and the swap
+heuristic every step). A step is one pass of the whole hot path: bucket hash, radix sort, reorder,
+swap pass, communication hash and MGPU boundary set, interaction loop fused with the integration.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0. `value` is particle-steps/s of the FP32-split path with the state resident
+in HBM, timed with CUDA events on the launch stream; the FP64 path is measured beside it. Under
+torchrun every rank runs its own replica (independent problems: weak scaling, no collective on the
+data path). `--impl reference` times the plain FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic FP operations of one ordered pair evaluation: the pair flux (160: distance, normal,
+# kernel gradient, normal velocities and tractions, acoustic Riemann state, interface state, mass,
+# momentum and energy fluxes) plus the per-particle accumulation of volume, mass, momentum, energy
+# and velocity-gradient rates (60), counted on the oracle's pair function as written.
+FLOPS_PER_PAIR = 220
+SMS, FP32_LANES = 152, 128
+
+
+def algorithmic_bytes_per_particle_step(key_passes: int, K: int, swap_every: int) -> dict:
+    """Compulsory HBM bytes per particle and step of each kernel (state read/written once)."""
+    state = 15 * 8 + 6          # FP64 fields + material, label, id
+    rec = 64                    # FP32 interaction record (position + state)
+    b = {
+        "hash": 24 + 8,                                   # x y z in, key + slot out
+        "sort": key_passes * (4 + 8 + 8),                 # histogram read + key/slot in and out
+        "reorder": 8 + state + 24 + 6 + rec,              # key+perm, gathered state, sorted x, ids, records
+        "comm": 4 + 1 + 1 + 4 + 4,                        # key, label, flag, comm hash, list entry
+        "interact": rec + 8 + state + 24 + 6 + state,     # own record, key/perm, state in, state out
+    }
+    if K > 1 and swap_every > 0:
+        pairs = K * (K - 1) // 2
+        b["swap"] = pairs * (2.0 / K) * (24 + 1 + 1 + 4 + 2) / swap_every
+    b["total"] = sum(b.values())
+    return b
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _traffic_from_profile(kernel_src: str, profile: str):
+    """dram bytes per launch recorded in a committed ncu summary, if it was taken on this source."""
+    path = os.path.join(ROOT, "profiles", profile)
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"source_sha256:\s*([0-9a-f]{16,64})", txt)
+    t = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
+    if not m or not t:
+        return None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    return float(t.group(1)) if sha.startswith(m.group(1)) else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[4:8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def workload_config(n: int, K: int, swap_period: int, world: int) -> dict:
+    return {"workload": "taylor_bar: Al rod r 5 mm x 40 mm, dx 0.125 mm, 200 m/s onto a rigid wall",
+            "particles": n, "labels": K, "swap_period": swap_period, "precision": "fp32-split",
+            "l2": f"inputs larger than L2 ({n * 600 / 1e6:.0f} MB of state and records resident)",
+            "parallelism": f"{world} independent replica(s)"}
+
+
+def run_reference(args, rank: int):
+    """The plain FP64 CPU oracle on the host cores, one bounded sample of the workload per step."""
+    from oracle import orc
+    from paper_2310_03596_gb300 import scenes
+
+    if rank != 0:
+        return None
+    full = scenes.taylor_bar()
+    # bounded sample: the base of the rod (on the wall) with about 1/10 of the particles per step, so
+    # that warmup + steps finish within a few minutes on the host
+    frac = min(0.1, 100.0 / (14.0 * max(1, args.steps + args.warmup)) * 1.0)
+    zcut = 40e-3 * frac
+    keep = full.pos[:, 2] < zcut
+    s = scenes.taylor_bar()
+    s.pos, s.vel, s.vol = full.pos[keep], full.vel[keep], full.vol[keep]
+    s.material, s.label = full.material[keep], full.label[keep]
+    P = orc.params_of(s)
+    st = orc.OracleState.from_scene(s)
+    orc.lib()
+    for k in range(args.warmup):
+        orc.step(P, st, do_swap=True)
+    t = time.perf_counter()
+    pairs = 0
+    for k in range(args.steps):
+        out = orc.step(P, st, do_swap=True)
+        pairs += int(out["nreal"].sum() + out["nimage"].sum())
+    el = time.perf_counter() - t
+    value = s.n * args.steps / el
+    sample = (f"base {zcut * 1e3:.2f} mm of the Taylor bar ({s.n} of {full.n} particles, wall contact "
+              f"included), full step incl. swap pass, {args.steps} steps")
+    return {"impl": "reference", "metric": "particle-steps/sec", "value": value, "unit": "particle-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(full.n, full.K, full.swap_period, args.gpus),
+            "pair_interactions_per_s": pairs / el,
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def cpu_baseline():
+    """One full oracle step of the whole workload on one host core."""
+    from oracle import orc
+    from paper_2310_03596_gb300 import scenes
+
+    s = scenes.taylor_bar()
+    P = orc.params_of(s)
+    st = orc.OracleState.from_scene(s)
+    orc.lib()
+    t = time.perf_counter()
+    orc.step(P, st, do_swap=True)
+    el = time.perf_counter() - t
+    return {"value": s.n / el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"one full step (hash, sort, swap pass, comm hash, interaction, integration) of the "
+                      f"{s.n}-particle Taylor bar, {el:.1f} s on one core"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_2310_03596_gb300 import gsph, scenes
+
+    s = scenes.taylor_bar()
+    stream = torch.cuda.current_stream()
+    sol = gsph.Solver.from_scene(s, precision=gsph.FP32_SPLIT, device=local, stream=stream)
+    n = s.n
+    _, ncell = sol.sizes()
+    key_passes = (int(ncell).bit_length() + 7) // 8
+
+    sol.step(args.warmup, stream)
+    sol.sync(stream)
+    st0 = sol.exchange_stats(stream)
+    sol.set_timing(args.steps)
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if rank == 0:
+        clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sol.step(args.steps, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop() if rank == 0 else None
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    sol.sync(stream)
+    st1 = sol.exchange_stats(stream)
+    tm = sol.timings()
+    pairs = st1["pairs_total"] - st0["pairs_total"]
+    launches = st1["kernel_launches"] - st0["kernel_launches"]
+    sec = ms * 1e-3
+    value = world * n * args.steps / sec
+    pair_rate = world * pairs / sec
+
+    # FP64 path on the same workload, fewer steps (its pair math runs on the FP64 units)
+    sol64 = gsph.Solver.from_scene(s, precision=gsph.FP64, device=local, stream=stream)
+    sol64.step(3, stream)
+    sol64.sync(stream)
+    p0 = sol64.exchange_stats(stream)["pairs_total"]
+    sol64.set_timing(args.fp64_steps)
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    sol64.step(args.fp64_steps, stream)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = f0.elapsed_time(f1)
+    p1 = sol64.exchange_stats(stream)["pairs_total"]
+    tm64 = sol64.timings()
+    sol64.close()
+
+    # end to end through the public API with host buffers: upload the particle set from pinned host
+    # memory, run the steps, read the whole state back
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+           for k, v in (("pos", s.pos), ("vel", s.vel), ("vol", s.vol), ("mat", s.material), ("lab", s.label))}
+    out_host = torch.empty((15, n), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    sol.set_particles(pin["pos"].numpy(), pin["vel"].numpy(), pin["vol"].numpy(), pin["mat"].numpy(),
+                      pin["lab"].numpy(), stream=stream)
+    sol.step(args.steps, stream)
+    outs = out_host.numpy()
+    for k, f in enumerate(gsph.FIELDS[:15]):
+        sol.get(f, stream, out=outs[k])
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t
+    if dist is not None:
+        t2 = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t2, op=dist.ReduceOp.MAX)
+        e2e_s = float(t2.item())
+    h2d = n * (24 + 24 + 8 + 1 + 1)
+    d2h = n * 15 * 8
+
+    if rank != 0:
+        sol.close()
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    peaks, peaks_kind = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    it_ms = tm["interact_ms"] / max(tm["steps"], 1)
+    flops_per_launch = FLOPS_PER_PAIR * pairs / args.steps
+    achieved = flops_per_launch / (it_ms * 1e-3) / 1e12
+    traffic = _traffic_from_profile(os.path.join(ROOT, "paper_2310_03596_gb300", "csrc", "k_interact.cu"),
+                                    "k_interact_taylor_bar_split.md")
+    ab = algorithmic_bytes_per_particle_step(key_passes, s.K, s.swap_period)
+    step_ms = ms / args.steps
+    hbm_ach = ab["total"] * n / (step_ms * 1e-3) / 1e9
+    line = {
+        "metric": "particle-steps/sec",
+        "value": value,
+        "unit": "particle-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": step_ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": workload_config(n, s.K, s.swap_period, world),
+        "pair_interactions_per_s": pair_rate,
+        "pairs_per_step": pairs / args.steps,
+        "phase_ms_per_step": {k[:-3]: v / max(tm["steps"], 1) for k, v in tm.items() if k.endswith("_ms")},
+        "fp64": {"value": world * n * args.fp64_steps / (ms64 * 1e-3), "unit": "particle-steps/s",
+                 "ms_per_step": ms64 / args.fp64_steps,
+                 "pair_interactions_per_s": world * (p1 - p0) / (ms64 * 1e-3),
+                 "interact_ms": tm64["interact_ms"] / max(tm64["steps"], 1), "steps": args.fp64_steps},
+        "roofline": {"kernel": "k_interact (FP32 split)", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
+                     "flops_per_launch": flops_per_launch, "launch_ms": it_ms,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sm_max_mhz, {peaks_kind})"},
+        "hbm_step": {"bytes_per_particle_step": ab, "achieved_GBps": hbm_ach, "peak_GBps": peaks["hbm_gbs"],
+                     "frac": hbm_ach / peaks["hbm_gbs"], "peak_source": f"hbm_gbs ({peaks_kind})"},
+        "e2e": {"value": world * n * args.steps / e2e_s, "unit": "particle-steps/s",
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                "what": "upload of the particle set from pinned host memory, the steps, read-back of the "
+                        "15 state fields, through the public API"},
+        "gpu_launches": launches,
+        "clocks": ck,
+        "exchange": {k: st1[k] for k in ("boundary_total", "exchange_fraction", "bytes_boundary_broadcast",
+                                         "swapped_last_pass", "swap_passes")},
+    }
+    sol.close()
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -68,7 +68,8 @@ typedef struct {
     int32_t grid_dims[3];       /* buckets per axis; bucket side is 2h; product < 2^27 */
     int32_t n_materials;        /* 1..GSPH_MAX_MATERIALS; > 1 turns on per-type swaps (Sec. III.B) */
     double h;                   /* smoothing length (uniform, Sec. II); kernel support 2h */
-    double cfl;                 /* dt = cfl * h / max(c + |v|) */
+    double cfl;                 /* dt = cfl * h / max(c + |v|), the signal speed in correctly
+                                   rounded FP32 from the FP32 roundings of m, w, v */
     gsph_material materials[GSPH_MAX_MATERIALS];
     int32_t n_walls;
     int32_t K;                  /* ownership labels, 1..GSPH_MAX_LABELS (Sec. II) */
@@ -118,6 +119,9 @@ typedef struct {
     int64_t bytes_swap;                 /* state bytes of the particles moved by the last swap pass */
     int64_t swapped_last_pass;          /* particles that changed label in the last swap pass */
     int64_t swap_passes;
+    int64_t pairs_total;                /* ordered pair interactions evaluated (sum over particles of
+                                           real + image neighbours) since gsph_set_particles */
+    int64_t kernel_launches;            /* kernels this context launched since gsph_set_particles */
 } gsph_exchange_stats;
 
 typedef struct {
@@ -146,7 +150,7 @@ gsph_status gsph_create(const gsph_config *cfg, gsph_ctx **out);
 /* Free every device buffer and the context (null is accepted). */
 void gsph_destroy(gsph_ctx *ctx);
 
-/* Sec. II premise: load n particles (1 <= n < 2^27). pos and vel are n x 3 row-major FP64; vol is
+/* Sec. II premise: load n particles (1 <= n < 2^26). pos and vel are n x 3 row-major FP64; vol is
  * the particle volume; material and label are uint8 (material < n_materials, label < K). Mass is
  * rho0 * vol, the specific total energy |v|^2 / 2, deviatoric stress 0; ids are 0..n-1 in input
  * order. Reallocates device buffers if n grows. Errors: INVALID_ARG, OOM, CUDA_ERROR,

@@ -400,12 +400,19 @@ void rates_all(const orc_params *P, const StateT<T> &s, const Mat<T> *mats, int6
     }
 }
 
-// Sound speed plus speed, the CFL signal speed of one particle.
-double signal_speed(const orc_params *P, const orc_state *S, int64_t i) {
+// CFL signal speed c + |v| of one particle (reading: evaluated in FP32, each operation correctly
+// rounded, from the FP32 roundings of m, w and v; the time step only needs a few digits, and the
+// FP32 sequence is cheap on GPUs whose FP64 units are scarce).
+float signal_speed(const orc_params *P, const orc_state *S, int64_t i) {
     const orc_material &M = P->mat[S->mat[i]];
-    double rho = S->m[i] / S->w[i];
-    double c = std::sqrt((M.K + 4.0 * M.G / 3.0) / rho);
-    double v2 = dist2(S->vx[i], S->vy[i], S->vz[i]);
+    float Mmod = (float)(M.K + 4.0 * M.G / 3.0);
+    float rho = (float)S->m[i] / (float)S->w[i];
+    float c = std::sqrt(Mmod / rho);
+    float vx = (float)S->vx[i], vy = (float)S->vy[i], vz = (float)S->vz[i];
+    float a = vx * vx;
+    float b = vy * vy;
+    float d = vz * vz;
+    float v2 = (a + b) + d;
     return c + std::sqrt(v2);
 }
 
@@ -589,9 +596,9 @@ void orc_rates(const orc_params *P, const orc_state *S, int64_t nsub, const int6
 }
 
 double orc_dt(const orc_params *P, const orc_state *S) {
-    double mx = 0.0;
+    float mx = 0.0f;
     for (int64_t i = 0; i < S->n; ++i) mx = std::max(mx, signal_speed(P, S, i));
-    return (P->cfl * P->h) / mx;
+    return (P->cfl * P->h) / (double)mx;
 }
 
 void orc_integrate(const orc_params *P, orc_state *S, const double *rates, double dt) {
@@ -655,6 +662,8 @@ int64_t orc_cg(const orc_params *P, int64_t n, const double *x, const double *y,
 }
 
 int32_t orc_balancing_hash(const double own[3], const double oth[3], const double p[3]) {
+    // Per label pair (FP64): middle M of the Cg segment, unit direction u from the own Cg to the
+    // other, scale 1000 / (half the Cg distance).
     double M[3], d[3];
     for (int a = 0; a < 3; ++a) {
         M[a] = (own[a] + oth[a]) * 0.5;
@@ -663,15 +672,20 @@ int32_t orc_balancing_hash(const double own[3], const double oth[3], const doubl
     double dn = std::sqrt(dist2(d[0], d[1], d[2]));
     if (!(dn > 0.0)) return 0;
     double ell = dn * 0.5;
-    double t = ((p[0] - M[0]) * d[0] + (p[1] - M[1]) * d[1]) + (p[2] - M[2]) * d[2];
-    t = t / dn;                          // signed distance of the projection past the midpoint
-    if (!(t > 0.0)) return 0;            // own side of the middle: not a swap candidate
-    if (t >= ell) return ORC_HASH_MAX;   // beyond the other Cg
-    double k = std::floor((1000.0 * t) / ell);
-    int32_t h = (int32_t)k;
-    if (h < 1) h = 1;
-    if (h > ORC_HASH_MAX) h = ORC_HASH_MAX;
-    return h;
+    float u[3] = {(float)(d[0] / dn), (float)(d[1] / dn), (float)(d[2] / dn)};
+    float scale = (float)(1000.0 / ell);
+    // Per particle (reading: the offset from M in FP64, rounded to FP32, then FP32 arithmetic, each
+    // operation rounded): signed distance t of the projection past the middle.
+    float e0 = (float)(p[0] - M[0]), e1 = (float)(p[1] - M[1]), e2 = (float)(p[2] - M[2]);
+    float a0 = e0 * u[0];
+    float a1 = e1 * u[1];
+    float a2 = e2 * u[2];
+    float t = (a0 + a1) + a2;
+    if (!(t > 0.0f)) return 0;                       // own side of the middle: not a swap candidate
+    float k = std::floor(t * scale);                 // proportional to the distance past the middle
+    if (k >= (float)ORC_HASH_MAX) return ORC_HASH_MAX;   // at or beyond the other Cg
+    if (k < 1.0f) return 1;
+    return (int32_t)k;
 }
 
 int64_t orc_swap_pass(const orc_params *P, int64_t n, const double *x, const double *y,

@@ -159,7 +159,7 @@ class OracleState:
         n = len(d["x"])
         s = cls(n)
         for f in FIELDS + ("mat", "label", "id"):
-            getattr(s, f)[:] = d[f]
+            getattr(s, f)[:] = d[f] if f in d else d["material"]
         return s
 
     def arrays(self) -> dict:

@@ -18,34 +18,41 @@ cudaError_t launch_hash(const DevParams &P, int64_t n, const double *x, const do
 // k_reorder_comm.cu
 cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint32_t *perm,
                            const State &A, double *xs, double *ys, double *zs, uint8_t *lab_s, uint8_t *mat_s,
-                           uint32_t *id_s, uint2 *cellr, void *pos, void *rec, int *err, cudaStream_t s);
+                           uint32_t *id_s, uint2 *cellr, float *cxs, void *pos, void *rec, int *err, cudaStream_t s);
 cudaError_t launch_comm(const DevParams &P, int64_t n, const uint32_t *skey, const uint8_t *lab_s, uint32_t *mask,
                         uint8_t *flag, uint32_t *comm, uint32_t *block_counts, unsigned long long *label_total,
                         uint32_t *blist, cudaStream_t s);
 int comm_blocks(int64_t n);
 cudaError_t launch_init(const DevParams &P, int64_t n, const double *pos, const double *vel, const double *vol,
                         const uint8_t *mat, const uint8_t *lab, const State &A, int *err, cudaStream_t s);
-cudaError_t launch_dt_from_state(const DevParams &P, int64_t n, const State &A, unsigned long long *sig, double *dt,
+cudaError_t launch_dt_from_state(const DevParams &P, int64_t n, const State &A, unsigned int *sig, double *dt,
                                  cudaStream_t s);
-cudaError_t launch_finalize_dt(const DevParams &P, unsigned long long *sig, double *dt, cudaStream_t s);
+cudaError_t launch_finalize_dt(const DevParams &P, unsigned int *sig, double *dt, cudaStream_t s);
 cudaError_t launch_conserved(int64_t n, const State &A, double *part, double *out, cudaStream_t s);
 // k_interact.cu
 cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n, const uint32_t *skey,
-                            const uint2 *cellr, const void *pos, const void *rec, const double *xs, const double *ys,
-                            const double *zs, const uint32_t *perm, const State &A, const State &B,
+                            const uint2 *cellr, const void *pos, const void *rec, const float *cxs,
+                            const double *xs, const double *ys, const double *zs, int kmax, uint32_t *list,
+                            uint32_t *cnt, const uint32_t *perm, const State &A, const State &B,
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
-                            unsigned long long *sig, int32_t *nreal, int32_t *nimage, double *rates, cudaStream_t s);
+                            unsigned int *sig, unsigned long long *pairs, int32_t *nreal, int32_t *nimage,
+                            double *rates, cudaStream_t s);
 // k_swap.cu
 size_t swap_scratch_bytes(int K, int nmat);
 cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const double *x, const double *y, const double *z,
                              uint8_t *lab, const uint8_t *mat, const uint32_t *id, void *scratch, uint16_t *bh,
-                             cudaStream_t s);
+                             int *err, int grid, cudaStream_t s);
+int swap_grid_blocks();
 unsigned long long *swap_moved_ptr(void *scratch);
 }  // namespace gsph
 
 using namespace gsph;
 
 enum { PH_START = 0, PH_SORT, PH_REORDER, PH_SWAP, PH_COMM, PH_INTERACT, PH_COUNT };
+
+// Neighbour-list capacity per particle (an interior particle of the lattice has 80 real neighbours;
+// particles with more finish the rest by re-scanning, so results do not depend on it).
+constexpr int kNbrMax = 96;
 
 struct gsph_ctx {
     gsph_config cfg;
@@ -63,6 +70,8 @@ struct gsph_ctx {
     uint2 *cellr = nullptr;
     uint32_t *mask = nullptr;
     double *xs = nullptr, *ys = nullptr, *zs = nullptr;
+    float *cxs = nullptr;
+    uint32_t *nbr = nullptr, *nbr_cnt = nullptr;   // neighbour lists (kNbrMax x n, column-major), counts
     uint8_t *lab_s = nullptr, *mat_s = nullptr;
     uint32_t *id_s = nullptr;
     void *pos = nullptr, *rec = nullptr;
@@ -70,7 +79,8 @@ struct gsph_ctx {
     uint32_t *comm = nullptr, *blist = nullptr, *bcounts = nullptr;
     unsigned long long *label_off = nullptr;   // K + 1
     unsigned long long *garbage = nullptr;
-    unsigned long long *sig = nullptr;
+    unsigned int *sig = nullptr;
+    unsigned long long *pairs = nullptr;
     double *dt = nullptr;
     int *err = nullptr;
     int32_t *nreal = nullptr, *nimage = nullptr;
@@ -78,9 +88,10 @@ struct gsph_ctx {
     void *swap_scratch = nullptr;
     uint16_t *bh = nullptr;
     double *cons_part = nullptr, *cons_out = nullptr;
+    int swap_grid = 0;
     // statistics
     int64_t swap_passes = 0;
-    int64_t swapped_total_prev = 0;
+    int64_t launches = 0;
     // timing
     int timing_max = 0, timing_used = 0;
     std::vector<cudaEvent_t> ev;
@@ -133,6 +144,9 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     A_(dalloc(c, &c->cellr, C));
     A_(dalloc(c, &c->mask, C));
     A_(dalloc(c, &c->xs, N)); A_(dalloc(c, &c->ys, N)); A_(dalloc(c, &c->zs, N));
+    A_(dalloc(c, &c->cxs, N));
+    A_(dalloc(c, &c->nbr, N * (size_t)kNbrMax));
+    A_(dalloc(c, &c->nbr_cnt, N));
     A_(dalloc(c, &c->lab_s, N)); A_(dalloc(c, &c->mat_s, N)); A_(dalloc(c, &c->id_s, N));
     if (c->split) {
         A_(dalloc(c, (float4 **)&c->pos, N));
@@ -148,6 +162,7 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     A_(dalloc(c, &c->label_off, (size_t)kMaxLabel + 1));
     A_(dalloc(c, &c->garbage, 1));
     A_(dalloc(c, &c->sig, 1));
+    A_(dalloc(c, &c->pairs, 1));
     A_(dalloc(c, &c->dt, 1));
     A_(dalloc(c, &c->err, 1));
     if (c->cfg.diagnostics) {
@@ -162,6 +177,7 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
 #undef A_
     e = cudaMemset(c->err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->garbage, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->pairs, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->label_off, 0, (kMaxLabel + 1) * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->swap_scratch, 0, swap_scratch_bytes(c->P.K_labels, c->P.nmat));
     return e;
@@ -229,6 +245,11 @@ static void fill_params(const gsph_config &c, DevParams &P) {
     P.f_R2hi = (float)(P.R2 * (1.0 + 1.2e-5));
 }
 
+static int64_t swap_pass_launches(const DevParams &P) {
+    (void)P;
+    return 1;   // one cooperative kernel per pass
+}
+
 static int key_bits(uint32_t ncell) {
     int b = 1;
     while (b < 32 && (((uint64_t)1 << b) <= (uint64_t)ncell)) ++b;
@@ -245,6 +266,7 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     if (c->dt_dirty) {
         GSPH_CK(launch_dt_from_state(P, n, c->A, c->sig, c->dt, s));
         c->dt_dirty = false;
+        c->launches += 2;
     }
     rec_event(c, PH_START, s);
     // a. bucket hash and the radix sort by hash (Sec. I)
@@ -254,26 +276,32 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     GSPH_CK(radix_sort_pairs(c->key0, c->val0, c->key1, c->val1, c->hist, c->tot, n, key_bits(P.ncell), s, &alt));
     c->skey = alt ? c->key1 : c->key0;
     c->perm = alt ? c->val1 : c->val0;
+    c->launches += 1 + 3 * ((key_bits(P.ncell) + 7) / 8);
     rec_event(c, PH_SORT, s);
     // sorted view, bucket ranges, interaction records
     GSPH_CK(cudaMemsetAsync(c->cellr, 0, (size_t)P.ncell * sizeof(uint2), s));
     GSPH_CK(launch_reorder(c->split, P, n, c->skey, c->perm, c->A, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s,
-                           c->cellr, c->pos, c->rec, c->err, s));
+                           c->cellr, c->cxs, c->pos, c->rec, c->err, s));
+    c->launches += 1;
     rec_event(c, PH_REORDER, s);
     // Sec. III: periodic swap heuristic on the sorted view
     if (P.K_labels > 1 && c->cfg.swap_period > 0 && (c->step % c->cfg.swap_period) == 0) {
-        GSPH_CK(launch_swap_pass(P, n, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s, c->swap_scratch, c->bh, s));
+        GSPH_CK(launch_swap_pass(P, n, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s, c->swap_scratch, c->bh,
+                                 c->err, c->swap_grid, s));
         ++c->swap_passes;
+        c->launches += swap_pass_launches(P);
     }
     rec_event(c, PH_SWAP, s);
     // b-d. communication hash, MGPU boundary flags and set
     GSPH_CK(launch_comm(P, n, c->skey, c->lab_s, c->mask, c->flag, c->comm, c->bcounts, c->label_off, c->blist, s));
+    c->launches += 4;
     rec_event(c, PH_COMM, s);
     // f-g. interaction loop fused with the integration; next dt
-    GSPH_CK(launch_interact(c->split, c->cfg.diagnostics != 0, P, n, c->skey, c->cellr, c->pos, c->rec, c->xs, c->ys,
-                            c->zs, c->perm, c->A, c->B, c->lab_s, c->mat_s, c->id_s, c->dt, c->sig, c->nreal,
-                            c->nimage, c->rates, s));
+    GSPH_CK(launch_interact(c->split, c->cfg.diagnostics != 0, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs,
+                            c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, c->lab_s, c->mat_s, c->id_s, c->dt, c->sig, c->pairs,
+                            c->nreal, c->nimage, c->rates, s));
     GSPH_CK(launch_finalize_dt(P, c->sig, c->dt, s));
+    c->launches += 3;
     rec_event(c, PH_INTERACT, s);
     if (c->timing_used < c->timing_max) ++c->timing_used;
     State t = c->A;
@@ -331,6 +359,13 @@ gsph_status gsph_create(const gsph_config *cfg, gsph_ctx **out) {
     c->cfg = *cfg;
     c->split = cfg->precision == GSPH_FP32_SPLIT;
     fill_params(*cfg, c->P);
+    if (cfg->K > 1) {
+        c->swap_grid = swap_grid_blocks();
+        if (c->swap_grid < 1) {
+            delete c;
+            return GSPH_CUDA_ERROR;
+        }
+    }
     *out = c;
     return GSPH_OK;
 }
@@ -346,7 +381,7 @@ void gsph_destroy(gsph_ctx *c) {
 
 gsph_status gsph_set_particles(gsph_ctx *c, int64_t n, const double *pos, const double *vel, const double *vol,
                                const uint8_t *material, const uint8_t *label, int32_t on_device, void *stream) {
-    if (!c || n < 1 || n >= ((int64_t)1 << 27) || !pos || !vel || !vol || !material || !label) return GSPH_INVALID_ARG;
+    if (!c || n < 1 || n >= ((int64_t)1 << 26) || !pos || !vel || !vol || !material || !label) return GSPH_INVALID_ARG;
     GSPH_CK(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
     GSPH_CK(cudaStreamSynchronize(s));
@@ -388,6 +423,7 @@ gsph_status gsph_set_particles(gsph_ctx *c, int64_t n, const double *pos, const 
         dlab = (const uint8_t *)(q + nb * 57);
     }
     cudaError_t e = cudaMemsetAsync(c->err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->pairs, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = launch_init(c->P, n, dpos, dvel, dvol, dmat, dlab, c->A, c->err, s);
     if (e == cudaSuccess) e = launch_dt_from_state(c->P, n, c->A, c->sig, c->dt, s);
     cudaError_t e2 = cudaStreamSynchronize(s);
@@ -397,6 +433,7 @@ gsph_status gsph_set_particles(gsph_ctx *c, int64_t n, const double *pos, const 
     c->step = 0;
     c->have_step = false;
     c->swap_passes = 0;
+    c->launches = 3;
     return read_err(c, s);
 }
 
@@ -467,8 +504,9 @@ gsph_status gsph_swap_now(gsph_ctx *c, void *stream) {
     GSPH_CK(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
     GSPH_CK(launch_swap_pass(c->P, c->n, c->A.f[FX], c->A.f[FY], c->A.f[FZ], c->A.label, c->A.mat, c->A.id,
-                             c->swap_scratch, c->bh, s));
+                             c->swap_scratch, c->bh, c->err, c->swap_grid, s));
     ++c->swap_passes;
+    c->launches += swap_pass_launches(c->P);
     return GSPH_OK;
 }
 
@@ -485,10 +523,11 @@ gsph_status gsph_get_exchange_stats(gsph_ctx *c, void *stream, gsph_exchange_sta
     GSPH_CK(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
     std::memset(out, 0, sizeof(*out));
-    unsigned long long off[kMaxLabel + 1] = {0}, garb = 0, moved = 0;
+    unsigned long long off[kMaxLabel + 1] = {0}, garb = 0, moved = 0, pairs = 0;
     GSPH_CK(cudaMemcpyAsync(off, c->label_off, sizeof(off), cudaMemcpyDeviceToHost, s));
     GSPH_CK(cudaMemcpyAsync(&garb, c->garbage, sizeof(garb), cudaMemcpyDeviceToHost, s));
     GSPH_CK(cudaMemcpyAsync(&moved, swap_moved_ptr(c->swap_scratch), sizeof(moved), cudaMemcpyDeviceToHost, s));
+    GSPH_CK(cudaMemcpyAsync(&pairs, c->pairs, sizeof(pairs), cudaMemcpyDeviceToHost, s));
     GSPH_CK(cudaStreamSynchronize(s));
     const int K = c->P.K_labels;
     out->step = c->step;
@@ -506,6 +545,8 @@ gsph_status gsph_get_exchange_stats(gsph_ctx *c, void *stream, gsph_exchange_sta
     out->swapped_last_pass = (int64_t)moved;
     out->bytes_swap = (int64_t)moved * (15 * 8 + 6);
     out->swap_passes = c->swap_passes;
+    out->pairs_total = (int64_t)pairs;
+    out->kernel_launches = c->launches;
     return out->garbage > 0 ? GSPH_PARTICLE_LEFT_DOMAIN : GSPH_OK;
 }
 

@@ -100,13 +100,16 @@ __device__ __forceinline__ void decode_cell(const DevParams &P, uint32_t c, int 
     cz = (int)(r / (uint32_t)P.dims[1]);
 }
 
-// Signal speed c + |v| of one particle, exactly rounded (the CFL max is order independent, so the
-// time step is reproducible bit for bit).
-__device__ __forceinline__ double signal_speed(const DevParams &P, int mat, double m, double w,
-                                               double vx, double vy, double vz) {
-    double rho = __ddiv_rn(m, w);
-    double c = __dsqrt_rn(__ddiv_rn(P.Mmod[mat], rho));
-    return __dadd_rn(c, __dsqrt_rn(dist2_rn(vx, vy, vz)));
+// CFL signal speed c + |v| of one particle, evaluated in FP32 with correctly rounded operations on
+// the FP32 roundings of m, w, v (the max over particles is order independent, so the time step is
+// reproducible bit for bit on any IEEE machine evaluating the same sequence).
+__device__ __forceinline__ float signal_speed32(const DevParams &P, int mat, double m, double w,
+                                                double vx, double vy, double vz) {
+    const float rho = __fdiv_rn((float)m, (float)w);
+    const float c = __fsqrt_rn(__fdiv_rn(P.f_Mmod[mat], rho));
+    const float fx = (float)vx, fy = (float)vy, fz = (float)vz;
+    const float v2 = __fadd_rn(__fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy)), __fmul_rn(fz, fz));
+    return __fadd_rn(c, __fsqrt_rn(v2));
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {

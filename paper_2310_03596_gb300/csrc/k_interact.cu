@@ -1,11 +1,18 @@
-// k_interact.cu - the interaction loop (Sec. II step f) fused with the integration (step g).
+// k_interact.cu - the interaction loop (Sec. II step f) fused with the integration (step g), as two
+// kernels.
 //
-// One lane per sorted particle i. The 27 buckets around i are visited as 9 rows of 3 buckets that
-// are contiguous in hash order. Phase 1 tests candidates and appends the in-support ones to a per-lane
-// list in shared memory (column-major, conflict-free); phase 2 evaluates the pair fluxes of the listed
-// neighbours in lockstep, so the heavy pair math runs with every lane busy instead of at the ~17% hit
-// rate of the raw candidate stream. Wall images (mirror planes) are searched around the mirrored point
-// with the same two phases.
+// k_nbr_list: one lane per sorted particle i; a warp holds 32 consecutive particles of the hash order,
+//   which share most of their 27-bucket neighbourhoods. The neighbourhood is visited as 9 rows of 3
+//   buckets that are contiguous in hash order. The warp streams the union of its lanes' candidate
+//   ranges through shared memory in batches of 32 records (x shifted into a frame common to the warp),
+//   every lane tests each staged candidate against its own 3-bucket window with straight-line code,
+//   and appends the in-support ones to a column-major list in global memory (entry = slot | bucket
+//   offset). Light on registers, so the candidate stream runs at full occupancy.
+// k_pair: one lane per particle walks its list (the next neighbour's record requested while the
+//   current pair is evaluated): pair fluxes, per-particle sums, then the wall images (mirror planes,
+//   searched around the mirrored point; only particles near a wall find any), then the integration.
+//   A particle with more neighbours than the list holds finishes the rest by re-scanning its
+//   buckets in the same order, so results never depend on the list capacity.
 //
 // Pair formulation (reading of the Gamma-SPH-ALE interface state; the paper cites it from another
 // work): transport velocity v0 = v; acoustic Riemann problem on the pair normal n (L = lower sorted
@@ -13,18 +20,20 @@
 // traction t* n plus the averaged tangential traction; Wendland C2 gradient |dW/dr| n.
 //
 // Split path: pair math in FP32 from FP32 records (positions relative to each particle's bucket corner,
-// so differences keep ~2^-24 * 2h), FP32 Kahan-compensated per-particle sums, FP64 integration. The
-// support predicate stays exact: the FP32 r^2 decides only outside a band of relative width 1.2e-5
-// around (2h)^2, inside which the FP64 positions decide with the same rounding as FP64 code.
+// so differences keep ~2^-24 * 2h), FP32 sums with Kahan compensation for the conserved quantities
+// (volume, mass, momentum, energy) and plain FP32 sums for the velocity gradient, FP64 integration of
+// the conserved variables, positions and stress (the stress rate itself in FP32). The support predicate
+// stays exact: the FP32 r^2 decides only outside a band of relative width 1.2e-5 around (2h)^2, inside
+// which the FP64 positions decide with the same rounding as FP64 code.
 #include <type_traits>
 
 #include "gsph_internal.cuh"
 
 namespace gsph {
 
-constexpr int IT_THREADS = 128;
-constexpr int IT_CAP = 48;                 // list entries per lane before a flush
-constexpr uint32_t IT_JMASK = (1u << 27) - 1;
+constexpr int NL_THREADS = 256;            // neighbour-list kernel
+constexpr int PK_THREADS = 128;            // pair kernel
+constexpr uint32_t IT_JMASK = (1u << 26) - 1;   // list entry: slot (26 bits) | bucket offset (6 bits)
 
 template <class R> struct PIn { R vx, vy, vz, rho, p, Z, E, sxx, syy, szz, sxy, sxz, syz, w; };
 
@@ -50,6 +59,23 @@ __device__ __forceinline__ PIn<double> load_rec(const RecD *__restrict__ rec, do
     return q;
 }
 
+__device__ __forceinline__ PIn<float> unpack(const RecF &r, float w) {
+    PIn<float> q;
+    q.vx = r.a.x; q.vy = r.a.y; q.vz = r.a.z; q.rho = r.a.w;
+    q.p = r.b.x; q.Z = r.b.y; q.E = r.b.z; q.sxx = r.b.w;
+    q.syy = r.c.x; q.szz = -(r.b.w + r.c.x); q.sxy = r.c.y; q.sxz = r.c.z; q.syz = r.c.w;
+    q.w = w;
+    return q;
+}
+__device__ __forceinline__ PIn<double> unpack(const RecD &r, double w) {
+    PIn<double> q;
+    q.vx = r.a.x; q.vy = r.a.y; q.vz = r.a.z; q.rho = r.a.w;
+    q.p = r.b.x; q.Z = r.b.y; q.E = r.b.z; q.sxx = r.b.w;
+    q.syy = r.c.x; q.szz = r.c.y; q.sxy = r.c.z; q.sxz = r.c.w; q.syz = r.d.x;
+    q.w = w;
+    return q;
+}
+
 // Mirror image of a state in the plane normal to `ax`.
 template <class R> __device__ __forceinline__ void mirror(PIn<R> &q, int ax) {
     if (ax == 0) { q.vx = -q.vx; q.sxy = -q.sxy; q.sxz = -q.sxz; }
@@ -62,45 +88,53 @@ __device__ __forceinline__ double rsqrt_r(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float rcp_r(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double rcp_r(double x) { return 1.0 / x; }
 
-template <class R> struct PairRes { R Fm, Fmv[3], Fe, a, n[3], uL, uR; };
+template <class R> struct PairRes { R Fm, Fmv[3], Fe, a, n[3], du_vol; };
 
-// Pair fluxes with L = left state, R = right state, d = x_R - x_L.
+// Pair fluxes on the canonical pair: d = x_R - x_L with L the lower sorted slot, `me` the particle
+// being updated and `oth` its neighbour, iL = (me is L). Every per-particle projection is taken on the
+// same canonical normal at both ends of the pair and every symmetric combination uses commutative
+// operations, so the two ends produce bitwise-opposite fluxes; only the Riemann inputs are ordered.
 template <class R>
-__device__ __forceinline__ void pair_terms(R d0, R d1, R d2, const PIn<R> &L, const PIn<R> &Rr, R inv_h, R kdw,
-                                           PairRes<R> &o) {
+__device__ __forceinline__ void pair_terms(R d0, R d1, R d2, const PIn<R> &me, const PIn<R> &oth, bool iL, R inv_h,
+                                           R kdw, PairRes<R> &o) {
     const R half = R(0.5);
-    R r2 = d0 * d0 + d1 * d1 + d2 * d2;
-    R inv_r = rsqrt_r(r2);
-    R r = r2 * inv_r;
-    R n0 = d0 * inv_r, n1 = d1 * inv_r, n2 = d2 * inv_r;
-    R q = r * inv_h;
-    R sq = R(1) - half * q;
-    R a = kdw * q * sq * sq * sq;
-    R uL = L.vx * n0 + L.vy * n1 + L.vz * n2;
-    R uR = Rr.vx * n0 + Rr.vy * n1 + Rr.vz * n2;
-    R sL0 = L.sxx * n0 + L.sxy * n1 + L.sxz * n2 - L.p * n0;
-    R sL1 = L.sxy * n0 + L.syy * n1 + L.syz * n2 - L.p * n1;
-    R sL2 = L.sxz * n0 + L.syz * n1 + L.szz * n2 - L.p * n2;
-    R sR0 = Rr.sxx * n0 + Rr.sxy * n1 + Rr.sxz * n2 - Rr.p * n0;
-    R sR1 = Rr.sxy * n0 + Rr.syy * n1 + Rr.syz * n2 - Rr.p * n1;
-    R sR2 = Rr.sxz * n0 + Rr.syz * n1 + Rr.szz * n2 - Rr.p * n2;
-    R tL = sL0 * n0 + sL1 * n1 + sL2 * n2;
-    R tR = sR0 * n0 + sR1 * n1 + sR2 * n2;
-    R izs = rcp_r(L.Z + Rr.Z);
-    R us = (L.Z * uL + Rr.Z * uR + (tR - tL)) * izs;
-    R ts = (Rr.Z * tL + L.Z * tR + L.Z * Rr.Z * (uR - uL)) * izs;
-    R du = us - half * (uL + uR);
-    R rhoE = half * (L.rho + Rr.rho);
-    R EE = half * (L.E + Rr.E);
-    R tm = half * (tL + tR);
-    R vE0 = half * (L.vx + Rr.vx) + du * n0;
-    R vE1 = half * (L.vy + Rr.vy) + du * n1;
-    R vE2 = half * (L.vz + Rr.vz) + du * n2;
-    R TE0 = ts * n0 + (half * (sL0 + sR0) - tm * n0);
-    R TE1 = ts * n1 + (half * (sL1 + sR1) - tm * n1);
-    R TE2 = ts * n2 + (half * (sL2 + sR2) - tm * n2);
-    R wwa = R(2) * L.w * Rr.w * a;
-    R mf = rhoE * du;
+    const R r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    const R inv_r = rsqrt_r(r2);
+    const R r = r2 * inv_r;
+    const R n0 = d0 * inv_r, n1 = d1 * inv_r, n2 = d2 * inv_r;
+    const R q = r * inv_h;
+    const R sq = R(1) - half * q;
+    const R a = kdw * q * sq * sq * sq;
+    // normal velocity, traction sigma n (sigma = -p I + S) and normal traction of each particle
+    const R um = me.vx * n0 + me.vy * n1 + me.vz * n2;
+    const R uo = oth.vx * n0 + oth.vy * n1 + oth.vz * n2;
+    const R sm0 = me.sxx * n0 + me.sxy * n1 + me.sxz * n2 - me.p * n0;
+    const R sm1 = me.sxy * n0 + me.syy * n1 + me.syz * n2 - me.p * n1;
+    const R sm2 = me.sxz * n0 + me.syz * n1 + me.szz * n2 - me.p * n2;
+    const R so0 = oth.sxx * n0 + oth.sxy * n1 + oth.sxz * n2 - oth.p * n0;
+    const R so1 = oth.sxy * n0 + oth.syy * n1 + oth.syz * n2 - oth.p * n1;
+    const R so2 = oth.sxz * n0 + oth.syz * n1 + oth.szz * n2 - oth.p * n2;
+    const R tmn = sm0 * n0 + sm1 * n1 + sm2 * n2;
+    const R ton = so0 * n0 + so1 * n1 + so2 * n2;
+    // acoustic Riemann problem, left = L, right = R
+    const R uL = iL ? um : uo, uR = iL ? uo : um;
+    const R tL = iL ? tmn : ton, tR = iL ? ton : tmn;
+    const R ZL = iL ? me.Z : oth.Z, ZR = iL ? oth.Z : me.Z;
+    const R izs = rcp_r(ZL + ZR);
+    const R us = (ZL * uL + ZR * uR + (tR - tL)) * izs;
+    const R ts = (ZR * tL + ZL * tR + ZL * ZR * (uR - uL)) * izs;
+    const R du = us - half * (um + uo);
+    const R rhoE = half * (me.rho + oth.rho);
+    const R EE = half * (me.E + oth.E);
+    const R tm = half * (tmn + ton);
+    const R vE0 = half * (me.vx + oth.vx) + du * n0;
+    const R vE1 = half * (me.vy + oth.vy) + du * n1;
+    const R vE2 = half * (me.vz + oth.vz) + du * n2;
+    const R TE0 = ts * n0 + (half * (sm0 + so0) - tm * n0);
+    const R TE1 = ts * n1 + (half * (sm1 + so1) - tm * n1);
+    const R TE2 = ts * n2 + (half * (sm2 + so2) - tm * n2);
+    const R wwa = R(2) * me.w * oth.w * a;
+    const R mf = rhoE * du;
     o.Fm = wwa * mf;
     o.Fmv[0] = wwa * (mf * vE0 - TE0);
     o.Fmv[1] = wwa * (mf * vE1 - TE1);
@@ -108,25 +142,33 @@ __device__ __forceinline__ void pair_terms(R d0, R d1, R d2, const PIn<R> &L, co
     o.Fe = wwa * (mf * EE - (TE0 * vE0 + TE1 * vE1 + TE2 * vE2));
     o.a = a;
     o.n[0] = n0; o.n[1] = n1; o.n[2] = n2;
-    o.uL = uL;
-    o.uR = uR;
+    o.du_vol = uR - uL;
 }
 
-// Per-particle sums: Kahan-compensated in FP32, plain in FP64.
+// Per-particle sums. FP32: Kahan-compensated for the conserved quantities (fields 0-5: volume, mass,
+// momentum, energy), plain for the velocity gradient (fields 6-14, which only feed the stress rate).
+// FP64: plain.
 template <class R> struct Acc;
 template <> struct Acc<float> {
-    float s[kNRate], c[kNRate];
+    float s[kNRate], c[6];
     __device__ __forceinline__ void zero() {
 #pragma unroll
-        for (int k = 0; k < kNRate; ++k) { s[k] = 0.f; c[k] = 0.f; }
+        for (int k = 0; k < kNRate; ++k) s[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) c[k] = 0.f;
     }
     __device__ __forceinline__ void add(int k, float x) {
-        float y = x - c[k];
-        float t = s[k] + y;
-        c[k] = (t - s[k]) - y;
-        s[k] = t;
+        if (k < 6) {
+            const float y = x - c[k];
+            const float t = s[k] + y;
+            c[k] = (t - s[k]) - y;
+            s[k] = t;
+        } else {
+            s[k] += x;
+        }
     }
-    __device__ __forceinline__ double get(int k) const { return (double)s[k] - (double)c[k]; }
+    __device__ __forceinline__ double get(int k) const { return k < 6 ? (double)s[k] - (double)c[k] : (double)s[k]; }
+    __device__ __forceinline__ float getr(int k) const { return k < 6 ? s[k] - c[k] : s[k]; }
 };
 template <> struct Acc<double> {
     double s[kNRate];
@@ -136,6 +178,7 @@ template <> struct Acc<double> {
     }
     __device__ __forceinline__ void add(int k, double x) { s[k] += x; }
     __device__ __forceinline__ double get(int k) const { return s[k]; }
+    __device__ __forceinline__ double getr(int k) const { return s[k]; }
 };
 
 // Adds one pair to the sums of particle i. sg = -1 when i is the left state (n points from i to j),
@@ -143,7 +186,7 @@ template <> struct Acc<double> {
 template <class R>
 __device__ __forceinline__ void accumulate(Acc<R> &acc, const PairRes<R> &o, R sg, const PIn<R> &me,
                                            const PIn<R> &oth) {
-    acc.add(0, me.w * oth.w * o.a * (o.uR - o.uL));
+    acc.add(0, me.w * oth.w * o.a * o.du_vol);
     acc.add(1, sg * o.Fm);
     acc.add(2, sg * o.Fmv[0]);
     acc.add(3, sg * o.Fmv[1]);
@@ -165,36 +208,159 @@ struct Types {
     using Rec = typename std::conditional<SPLIT, RecF, RecD>::type;
 };
 
-// Search centre of one source (0 = real neighbours, 1.. = images in wall k-1).
-struct Centre {
-    int bx, by, bz;
-    float ox, oy, oz;      // split path: i (or its mirror) relative to the centre bucket corner
-    double X, Y, Z;        // FP64 search point (i or its mirror)
-};
+// Row window of one search centre: the particles of buckets (bx-1 .. bx+1, Yc, Zc), which are
+// contiguous in hash order. rs = 0xffffffff, re = 0 when empty.
+__device__ __forceinline__ void row_window(const DevParams &P, const uint2 *__restrict__ cellr, int bx, int Yc, int Zc,
+                                           uint32_t &rs, uint32_t &re) {
+    rs = 0xffffffffu;
+    re = 0u;
+    if (Yc < 0 || Yc >= P.dims[1] || Zc < 0 || Zc >= P.dims[2] || bx < -1 || bx > P.dims[0]) return;
+    const uint32_t rb = (uint32_t)P.dims[0] * ((uint32_t)Yc + (uint32_t)P.dims[1] * (uint32_t)Zc);
+    uint2 cm = make_uint2(0, 0), c0 = make_uint2(0, 0), cp = make_uint2(0, 0);
+    if (bx - 1 >= 0 && bx - 1 < P.dims[0]) cm = __ldg(&cellr[rb + bx - 1]);
+    if (bx >= 0 && bx < P.dims[0]) c0 = __ldg(&cellr[rb + bx]);
+    if (bx + 1 >= 0 && bx + 1 < P.dims[0]) cp = __ldg(&cellr[rb + bx + 1]);
+    const bool em = cm.y > cm.x, e0 = c0.y > c0.x, ep = cp.y > cp.x;
+    if (em || e0 || ep) {
+        rs = em ? cm.x : (e0 ? c0.x : cp.x);
+        re = ep ? cp.y : (e0 ? c0.y : cm.y);
+    }
+}
 
-template <bool SPLIT, bool DIAG>
-__global__ void __launch_bounds__(IT_THREADS, SPLIT ? 4 : 2)
-k_interact(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *__restrict__ cellr,
-           const typename Types<SPLIT>::Pos *__restrict__ pos, const typename Types<SPLIT>::Rec *__restrict__ rec,
-           const double *__restrict__ xs, const double *__restrict__ ys, const double *__restrict__ zs,
-           const uint32_t *__restrict__ perm, State A, State B, const uint8_t *__restrict__ lab_s,
-           const uint8_t *__restrict__ mat_s, const uint32_t *__restrict__ id_s, const double *__restrict__ dt_ptr,
-           unsigned long long *__restrict__ sig, int32_t *__restrict__ nreal_out, int32_t *__restrict__ nimage_out,
-           double *__restrict__ rates_out) {
-    using R = typename Types<SPLIT>::R;
-    __shared__ uint32_t list[IT_CAP * IT_THREADS];
-    const int tid = threadIdx.x;
-    const int64_t s = (int64_t)blockIdx.x * IT_THREADS + tid;
+// Exact support predicate from the FP64 positions (real neighbour, or image in wall `wax` at `wpos`).
+__device__ __forceinline__ bool support_exact(const DevParams &P, const double *__restrict__ xs,
+                                              const double *__restrict__ ys, const double *__restrict__ zs,
+                                              uint32_t j, double X, double Y, double Z, int wax, double wpos) {
+    double qx = xs[j], qy = ys[j], qz = zs[j];
+    const double two_w = __dmul_rn(2.0, wpos);
+    if (wax == 0) qx = __dsub_rn(two_w, qx);
+    if (wax == 1) qy = __dsub_rn(two_w, qy);
+    if (wax == 2) qz = __dsub_rn(two_w, qz);
+    return dist2_rn(__dsub_rn(qx, X), __dsub_rn(qy, Y), __dsub_rn(qz, Z)) < P.R2;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Neighbour list (real neighbours). list[k * n + i], k < kmax; cnt[i] = number found (may exceed kmax).
+// ---------------------------------------------------------------------------------------------
+template <bool SPLIT>
+__global__ void __launch_bounds__(NL_THREADS) k_nbr_list(DevParams P, int64_t n, const uint32_t *__restrict__ skey,
+                                                         const uint2 *__restrict__ cellr,
+                                                         const typename Types<SPLIT>::Pos *__restrict__ pos,
+                                                         const float *__restrict__ cxs, const double *__restrict__ xs,
+                                                         const double *__restrict__ ys, const double *__restrict__ zs,
+                                                         int kmax, uint32_t *__restrict__ list,
+                                                         uint32_t *__restrict__ cnt_out) {
+    using Pos = typename Types<SPLIT>::Pos;
+    __shared__ Pos stage[NL_THREADS];
+    __shared__ float stage_cx[NL_THREADS];
+    const int tid = threadIdx.x, lane = tid & 31, wbase = tid & ~31;
+    const int64_t s = (int64_t)blockIdx.x * NL_THREADS + tid;
     const bool valid = s < n;
     const uint32_t key = valid ? skey[s] : P.ncell;
     const bool active = valid && key < P.ncell;
     int cx = 0, cy = 0, cz = 0;
     if (active) decode_cell(P, key, cx, cy, cz);
-    const double X = valid ? xs[s] : 0.0, Y = valid ? ys[s] : 0.0, Z = valid ? zs[s] : 0.0;
-    PIn<R> me;
-    R mrx = 0, mry = 0, mrz = 0;   // own position: relative (split) or absolute (FP64)
+    float ox = 0.f, oy = 0.f, oz = 0.f;
+    double X = 0.0, Y = 0.0, Z = 0.0;
     if (active) {
-        auto p = pos[s];
+        const Pos p = pos[s];
+        ox = (float)p.x; oy = (float)p.y; oz = (float)p.z;
+        if (!SPLIT) { X = (double)p.x; Y = (double)p.y; Z = (double)p.z; }
+    }
+    const float fcell = P.f_cell;
+    uint32_t cnt = 0;
+    bool need = active;
+    while (true) {
+        const unsigned todo = __ballot_sync(kFullMask, need);
+        if (!todo) break;
+        const int leader = __ffs(todo) - 1;
+        const int gby = __shfl_sync(kFullMask, cy, leader), gbz = __shfl_sync(kFullMask, cz, leader);
+        const int gbx = __shfl_sync(kFullMask, cx, leader);
+        // a group shares the bucket row and lies within 4 buckets of the leader in x, so staged and own
+        // x in the group frame stay below 12h and their FP32 rounding stays well inside the band
+        const bool ing = need && cy == gby && cz == gbz && abs(cx - gbx) <= 4;
+        const float bxf = (float)cx;
+        const float oxg = ox + (float)(cx - gbx) * fcell;   // own x in the group frame
+        for (int row = 0; row < 9; ++row) {
+            const int dcy = row % 3 - 1, dcz = row / 3 - 1;
+            const int Yc = gby + dcy, Zc = gbz + dcz;
+            if (Yc < 0 || Yc >= P.dims[1] || Zc < 0 || Zc >= P.dims[2]) continue;
+            uint32_t rs = 0xffffffffu, re = 0u;
+            if (ing) row_window(P, cellr, cx, Yc, Zc, rs, re);
+            const uint32_t lo = __reduce_min_sync(kFullMask, rs);
+            const uint32_t hi = __reduce_max_sync(kFullMask, re);
+            const float oyr = oy - (float)dcy * fcell, ozr = oz - (float)dcz * fcell;
+            const uint32_t code_yz = (uint32_t)(dcy + 1) << 28 | (uint32_t)(dcz + 1) << 30;
+            for (uint32_t b = lo; b < hi; b += 32) {
+                const uint32_t jl = b + lane;
+                if (jl < hi) {
+                    Pos q = pos[jl];
+                    const float cxj = cxs[jl];
+                    if (SPLIT) q.x = (float)q.x + (cxj - (float)gbx) * fcell;
+                    stage[tid] = q;
+                    stage_cx[tid] = cxj;
+                }
+                __syncwarp();
+                const int m = (int)min(32u, hi - b);
+                if (ing) {
+                    for (int t = 0; t < m; ++t) {
+                        const uint32_t j = b + (uint32_t)t;
+                        const float dcxf = stage_cx[wbase + t] - bxf;
+                        const Pos pj = stage[wbase + t];
+                        const bool ok = fabsf(dcxf) < 1.5f && (int64_t)j != s;   // own window, not self
+                        bool hit;
+                        if (SPLIT) {
+                            const float ex = (float)pj.x - oxg;
+                            const float ey = (float)pj.y - oyr;
+                            const float ez = (float)pj.z - ozr;
+                            const float r2 = ex * ex + ey * ey + ez * ez;
+                            hit = ok && r2 < P.f_R2lo;
+                            if (ok && !hit && r2 < P.f_R2hi)   // rounding band: exactly rounded FP64 decides
+                                hit = support_exact(P, xs, ys, zs, j, xs[s], ys[s], zs[s], -1, 0.0);
+                        } else {
+                            hit = ok && dist2_rn(__dsub_rn((double)pj.x, X), __dsub_rn((double)pj.y, Y),
+                                                 __dsub_rn((double)pj.z, Z)) < P.R2;
+                        }
+                        if (hit) {
+                            if ((int)cnt < kmax)
+                                list[(size_t)cnt * (size_t)n + (size_t)s] = j | (uint32_t)(int)(dcxf + 1.0f) << 26 | code_yz;
+                            ++cnt;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        need = need && !ing;
+    }
+    if (valid) cnt_out[s] = cnt;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Pair kernel: list walk, wall images, integration.
+// ---------------------------------------------------------------------------------------------
+template <bool SPLIT, bool DIAG>
+__global__ void __launch_bounds__(PK_THREADS, SPLIT ? 4 : 2)
+k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *__restrict__ cellr,
+       const typename Types<SPLIT>::Pos *__restrict__ pos, const typename Types<SPLIT>::Rec *__restrict__ rec,
+       const float *__restrict__ cxs, const double *__restrict__ xs, const double *__restrict__ ys,
+       const double *__restrict__ zs, int kmax, const uint32_t *__restrict__ list,
+       const uint32_t *__restrict__ cnt_in, const uint32_t *__restrict__ perm, State A, State B,
+       const uint8_t *__restrict__ lab_s, const uint8_t *__restrict__ mat_s, const uint32_t *__restrict__ id_s,
+       const double *__restrict__ dt_ptr, unsigned int *__restrict__ sig, unsigned long long *__restrict__ pairs,
+       int32_t *__restrict__ nreal_out, int32_t *__restrict__ nimage_out, double *__restrict__ rates_out) {
+    using R = typename Types<SPLIT>::R;
+    using Pos = typename Types<SPLIT>::Pos;
+    using Rec = typename Types<SPLIT>::Rec;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t s = (int64_t)blockIdx.x * PK_THREADS + tid;
+    const bool valid = s < n;
+    const uint32_t key = valid ? skey[s] : P.ncell;
+    const bool active = valid && key < P.ncell;
+    PIn<R> me;
+    R mrx = 0, mry = 0, mrz = 0;   // own position: relative to the own bucket corner (split) or absolute
+    if (active) {
+        const Pos p = pos[s];
         mrx = p.x; mry = p.y; mrz = p.z;
         me = load_rec(rec, p.w, s);
     } else {
@@ -202,280 +368,265 @@ k_interact(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint
     }
     const R inv_h = SPLIT ? (R)P.f_inv_h : (R)(1.0 / P.h);
     const R kdw = SPLIT ? (R)P.f_kdw : (R)P.kdw;
-    const float fcell = P.f_cell;
+    const R fcell = SPLIT ? (R)P.f_cell : (R)P.cell;
     Acc<R> acc;
     acc.zero();
-    int nr = 0, ni = 0;
+    const uint32_t cnt = active ? cnt_in[s] : 0u;
+    const int nl = (int)min(cnt, (uint32_t)kmax);
 
-    for (int src = 0; src <= P.nwalls; ++src) {
+    // one real neighbour: canonical orientation (the lower sorted slot is the left state); both ends
+    // of the pair evaluate x_R - x_L from the same operands in the same order
+    auto real_pair = [&](uint32_t e, const Pos &pj, const Rec &rj) {
+        const uint32_t jj = e & IT_JMASK;
+        const int ex = (int)(e >> 26 & 3u) - 1, ey = (int)(e >> 28 & 3u) - 1, ez = (int)(e >> 30) - 1;
+        const PIn<R> oth = unpack(rj, (R)pj.w);
+        const bool iL = s < (int64_t)jj;
+        const R ax = iL ? (R)pj.x : mrx, bx = iL ? mrx : (R)pj.x;
+        const R ay = iL ? (R)pj.y : mry, by = iL ? mry : (R)pj.y;
+        const R az = iL ? (R)pj.z : mrz, bz = iL ? mrz : (R)pj.z;
+        R d0, d1, d2;
+        if (SPLIT) {
+            const R f = iL ? fcell : -fcell;
+            d0 = (ax - bx) + (R)ex * f;
+            d1 = (ay - by) + (R)ey * f;
+            d2 = (az - bz) + (R)ez * f;
+        } else {
+            d0 = ax - bx; d1 = ay - by; d2 = az - bz;
+        }
+        PairRes<R> o;
+        pair_terms<R>(d0, d1, d2, me, oth, iL, inv_h, kdw, o);
+        accumulate<R>(acc, o, iL ? R(-1) : R(1), me, oth);
+    };
+
+    // ---- listed real neighbours, all lanes in lockstep, next record prefetched
+    {
+        const int mc = __reduce_max_sync(kFullMask, nl);
+        uint32_t en = nl > 0 ? list[(size_t)s] : 0u;
+        Pos pn = pos[en & IT_JMASK];
+        Rec rn = rec[en & IT_JMASK];
+        for (int k = 0; k < mc; ++k) {
+            const uint32_t e = en;
+            const Pos pj = pn;
+            const Rec rj = rn;
+            if (k + 1 < nl) {
+                en = list[(size_t)(k + 1) * (size_t)n + (size_t)s];
+                pn = pos[en & IT_JMASK];
+                rn = rec[en & IT_JMASK];
+            }
+            if (k < nl) real_pair(e, pj, rj);
+        }
+    }
+
+    // ---- neighbours beyond the list capacity, and the wall images: re-scan the buckets around the
+    // own position (overflow) or the mirrored position (images) in the list's candidate order
+    const double X = valid ? xs[s] : 0.0, Y = valid ? ys[s] : 0.0, Z = valid ? zs[s] : 0.0;
+    int cx = 0, cy = 0, cz = 0;
+    if (active) decode_cell(P, key, cx, cy, cz);
+    int ni = 0;
+    for (int src = (__any_sync(kFullMask, (int)cnt > kmax) ? 0 : 1); src <= P.nwalls; ++src) {
         const int wax = src > 0 ? P.wall_axis[src - 1] : -1;
         const double wpos = src > 0 ? P.wall_pos[src - 1] : 0.0;
-        Centre C;
-        C.X = X; C.Y = Y; C.Z = Z;
-        if (src == 0) {
-            C.bx = cx; C.by = cy; C.bz = cz;
-            C.ox = (float)mrx; C.oy = (float)mry; C.oz = (float)mrz;
-        } else {
-            double two_w = __dmul_rn(2.0, wpos);
-            if (wax == 0) C.X = __dsub_rn(two_w, X);
-            if (wax == 1) C.Y = __dsub_rn(two_w, Y);
-            if (wax == 2) C.Z = __dsub_rn(two_w, Z);
-            C.bx = bucket_coord_signed(C.X, P.lo[0], P.cell);
-            C.by = bucket_coord_signed(C.Y, P.lo[1], P.cell);
-            C.bz = bucket_coord_signed(C.Z, P.lo[2], P.cell);
-            C.ox = (float)(C.X - (P.lo[0] + (double)C.bx * P.cell));
-            C.oy = (float)(C.Y - (P.lo[1] + (double)C.by * P.cell));
-            C.oz = (float)(C.Z - (P.lo[2] + (double)C.bz * P.cell));
-        }
-        bool done = !active;
-        int row = -1;
-        uint32_t j = 0, jend = 0, s1 = 0, s2 = 0;
-        int dcy = 0, dcz = 0;
-        int cnt = 0;
-        while (__any_sync(kFullMask, !done)) {
-            // ---- phase 1: fill the lane lists
-            while (true) {
-                const bool want = !done && cnt < IT_CAP;
-                if (!__any_sync(kFullMask, want)) break;
-                if (!want) continue;
-                if (j < jend) {
-                    const uint32_t jj = j++;
-                    if (src == 0 && (int64_t)jj == s) continue;
-                    const int dcx = jj < s1 ? -1 : (jj < s2 ? 0 : 1);
-                    bool hit;
-                    auto pj = pos[jj];
-                    if (SPLIT) {
-                        float ex = ((float)pj.x - C.ox) + (float)dcx * fcell;
-                        float ey = ((float)pj.y - C.oy) + (float)dcy * fcell;
-                        float ez = ((float)pj.z - C.oz) + (float)dcz * fcell;
-                        float r2 = ex * ex + ey * ey + ez * ez;
-                        hit = r2 < P.f_R2lo;
-                        if (!hit && r2 < P.f_R2hi) {
-                            // inside the rounding band: decide with exactly rounded FP64
-                            double qx = xs[jj], qy = ys[jj], qz = zs[jj];
-                            double two_w = __dmul_rn(2.0, wpos);
-                            if (wax == 0) qx = __dsub_rn(two_w, qx);
-                            if (wax == 1) qy = __dsub_rn(two_w, qy);
-                            if (wax == 2) qz = __dsub_rn(two_w, qz);
-                            hit = dist2_rn(__dsub_rn(qx, X), __dsub_rn(qy, Y), __dsub_rn(qz, Z)) < P.R2;
-                        }
-                    } else {
-                        double qx = (double)pj.x, qy = (double)pj.y, qz = (double)pj.z;
-                        double two_w = __dmul_rn(2.0, wpos);
-                        if (wax == 0) qx = __dsub_rn(two_w, qx);
-                        if (wax == 1) qy = __dsub_rn(two_w, qy);
-                        if (wax == 2) qz = __dsub_rn(two_w, qz);
-                        hit = dist2_rn(__dsub_rn(qx, X), __dsub_rn(qy, Y), __dsub_rn(qz, Z)) < P.R2;
-                    }
-                    if (hit) {
-                        const uint32_t code = (uint32_t)((dcx + 1) + 3 * (dcy + 1) + 9 * (dcz + 1));
-                        list[cnt * IT_THREADS + tid] = jj | (code << 27);
-                        ++cnt;
-                    }
-                } else {
-                    ++row;
-                    if (row >= 9) {
-                        done = true;
-                        continue;
-                    }
-                    dcy = row % 3 - 1;
-                    dcz = row / 3 - 1;
-                    const int Yc = C.by + dcy, Zc = C.bz + dcz;
-                    j = jend = s1 = s2 = 0;
-                    if (Yc >= 0 && Yc < P.dims[1] && Zc >= 0 && Zc < P.dims[2] && C.bx >= -1 && C.bx <= P.dims[0]) {
-                        const uint32_t rb = (uint32_t)P.dims[0] * ((uint32_t)Yc + (uint32_t)P.dims[1] * (uint32_t)Zc);
-                        uint2 cm = make_uint2(0, 0), c0 = make_uint2(0, 0), cp = make_uint2(0, 0);
-                        if (C.bx - 1 >= 0 && C.bx - 1 < P.dims[0]) cm = __ldg(&cellr[rb + C.bx - 1]);
-                        if (C.bx >= 0 && C.bx < P.dims[0]) c0 = __ldg(&cellr[rb + C.bx]);
-                        if (C.bx + 1 >= 0 && C.bx + 1 < P.dims[0]) cp = __ldg(&cellr[rb + C.bx + 1]);
-                        const bool em = cm.y > cm.x, e0 = c0.y > c0.x, ep = cp.y > cp.x;
-                        if (em || e0 || ep) {
-                            uint32_t lo = em ? cm.x : (e0 ? c0.x : cp.x);
-                            uint32_t hi = ep ? cp.y : (e0 ? c0.y : cm.y);
-                            s1 = em ? cm.y : lo;
-                            s2 = ep ? cp.x : hi;
-                            j = lo;
-                            jend = hi;
-                        }
-                    }
-                }
+        double CX = X, CY = Y, CZ = Z;
+        int bx = cx, by = cy, bz = cz;
+        R ox = mrx, oy = mry, oz = mrz;
+        if (src > 0) {
+            const double two_w = __dmul_rn(2.0, wpos);
+            if (wax == 0) CX = __dsub_rn(two_w, X);
+            if (wax == 1) CY = __dsub_rn(two_w, Y);
+            if (wax == 2) CZ = __dsub_rn(two_w, Z);
+            bx = bucket_coord_signed(CX, P.lo[0], P.cell);
+            by = bucket_coord_signed(CY, P.lo[1], P.cell);
+            bz = bucket_coord_signed(CZ, P.lo[2], P.cell);
+            if (SPLIT) {
+                ox = (R)(CX - (P.lo[0] + (double)bx * P.cell));
+                oy = (R)(CY - (P.lo[1] + (double)by * P.cell));
+                oz = (R)(CZ - (P.lo[2] + (double)bz * P.cell));
+            } else {
+                ox = (R)CX; oy = (R)CY; oz = (R)CZ;
             }
-            // ---- phase 2: pair fluxes of the listed neighbours
-            const int mc = __reduce_max_sync(kFullMask, cnt);
-            for (int k = 0; k < mc; ++k) {
-                if (k >= cnt) continue;
-                const uint32_t e = list[k * IT_THREADS + tid];
-                const uint32_t jj = e & IT_JMASK;
-                const uint32_t code = e >> 27;
-                const int ex = (int)(code % 3u) - 1, ey = (int)((code / 3u) % 3u) - 1, ez = (int)(code / 9u) - 1;
-                auto pj = pos[jj];
-                PIn<R> oth = load_rec(rec, (R)pj.w, jj);
-                PairRes<R> o;
-                if (src == 0) {
-                    const bool iL = s < (int64_t)jj;
-                    R d0, d1, d2;
-                    if (SPLIT) {
-                        // canonical difference x_R - x_L = (r_R - r_L) + (c_R - c_L) 2h: both ends of
-                        // the pair evaluate the same operands in the same order
-                        if (iL) {
-                            d0 = ((R)pj.x - mrx) + (R)ex * (R)fcell;
-                            d1 = ((R)pj.y - mry) + (R)ey * (R)fcell;
-                            d2 = ((R)pj.z - mrz) + (R)ez * (R)fcell;
-                        } else {
-                            d0 = (mrx - (R)pj.x) + (R)(-ex) * (R)fcell;
-                            d1 = (mry - (R)pj.y) + (R)(-ey) * (R)fcell;
-                            d2 = (mrz - (R)pj.z) + (R)(-ez) * (R)fcell;
-                        }
-                    } else {
-                        if (iL) { d0 = (R)pj.x - mrx; d1 = (R)pj.y - mry; d2 = (R)pj.z - mrz; }
-                        else { d0 = mrx - (R)pj.x; d1 = mry - (R)pj.y; d2 = mrz - (R)pj.z; }
-                    }
-                    if (iL) pair_terms<R>(d0, d1, d2, me, oth, inv_h, kdw, o);
-                    else pair_terms<R>(d0, d1, d2, oth, me, inv_h, kdw, o);
-                    accumulate<R>(acc, o, iL ? R(-1) : R(1), me, oth);
-                    ++nr;
+        }
+        const bool mine = active && (src > 0 || (int)cnt > kmax);
+        if (!__any_sync(kFullMask, mine)) continue;
+        uint32_t seen = 0;
+        for (int row = 0; row < 9 && mine; ++row) {
+            const int dcy = row % 3 - 1, dcz = row / 3 - 1;
+            uint32_t rs, re;
+            row_window(P, cellr, bx, by + dcy, bz + dcz, rs, re);
+            for (uint32_t j = rs; j < re; ++j) {
+                if (src == 0 && (int64_t)j == s) continue;
+                const Pos pj = pos[j];
+                const int dcx = (int)cxs[j] - bx;
+                bool hit;
+                if (SPLIT) {
+                    const float exf = ((float)pj.x - (float)ox) + (float)dcx * (float)fcell;
+                    const float eyf = ((float)pj.y - (float)oy) + (float)dcy * (float)fcell;
+                    const float ezf = ((float)pj.z - (float)oz) + (float)dcz * (float)fcell;
+                    const float r2 = exf * exf + eyf * eyf + ezf * ezf;
+                    hit = r2 < P.f_R2lo;
+                    if (!hit && r2 < P.f_R2hi) hit = support_exact(P, xs, ys, zs, j, X, Y, Z, wax, wpos);
                 } else {
+                    hit = support_exact(P, xs, ys, zs, j, X, Y, Z, wax, wpos);
+                }
+                if (!hit) continue;
+                if (src == 0) {
+                    // real neighbour past the list capacity
+                    if (seen++ < (uint32_t)kmax) continue;
+                    const uint32_t e = j | (uint32_t)(dcx + 1) << 26 | (uint32_t)(dcy + 1) << 28 |
+                                       (uint32_t)(dcz + 1) << 30;
+                    real_pair(e, pj, rec[j]);
+                } else {
+                    PIn<R> oth = load_rec(rec, (R)pj.w, j);
                     R d0, d1, d2;
                     if (SPLIT) {
-                        d0 = ((R)pj.x - (R)C.ox) + (R)ex * (R)fcell;
-                        d1 = ((R)pj.y - (R)C.oy) + (R)ey * (R)fcell;
-                        d2 = ((R)pj.z - (R)C.oz) + (R)ez * (R)fcell;
+                        d0 = ((R)pj.x - ox) + (R)dcx * fcell;
+                        d1 = ((R)pj.y - oy) + (R)dcy * fcell;
+                        d2 = ((R)pj.z - oz) + (R)dcz * fcell;
                         if (wax == 0) d0 = -d0;
                         if (wax == 1) d1 = -d1;
                         if (wax == 2) d2 = -d2;
                     } else {
                         double qx = (double)pj.x, qy = (double)pj.y, qz = (double)pj.z;
-                        double two_w = 2.0 * wpos;
+                        const double two_w = 2.0 * wpos;
                         if (wax == 0) qx = two_w - qx;
                         if (wax == 1) qy = two_w - qy;
                         if (wax == 2) qz = two_w - qz;
                         d0 = (R)(qx - X); d1 = (R)(qy - Y); d2 = (R)(qz - Z);
                     }
                     mirror<R>(oth, wax);
-                    pair_terms<R>(d0, d1, d2, me, oth, inv_h, kdw, o);
+                    PairRes<R> o;
+                    pair_terms<R>(d0, d1, d2, me, oth, true, inv_h, kdw, o);
                     accumulate<R>(acc, o, R(-1), me, oth);
                     ++ni;
                 }
             }
-            cnt = 0;
         }
     }
+    const int nr = (int)cnt;
 
     // ---- integration (Sec. II step g): forward Euler on the conserved variables, Jaumann-rate
     // stress with radial return, positions with the velocity of the step's start.
-    double sp = 0.0;
+    float sp = 0.0f;
     if (valid) {
-    double r[kNRate];
+        const uint32_t o = perm[s];
+        const int mt = mat_s[s] < P.nmat ? mat_s[s] : 0;
+        const double dt = *dt_ptr;
+        const double w = A.f[FW][o], m = A.f[FM][o], E = A.f[FE][o];
+        const double vx = A.f[FVX][o], vy = A.f[FVY][o], vz = A.f[FVZ][o];
+        double S[6] = {A.f[FSXX][o], A.f[FSYY][o], A.f[FSZZ][o], A.f[FSXY][o], A.f[FSXZ][o], A.f[FSYZ][o]};
+        double r6[6];
 #pragma unroll
-    for (int k = 0; k < kNRate; ++k) r[k] = acc.get(k);
-    const uint32_t o = perm[s];
-    const int mt = mat_s[s] < P.nmat ? mat_s[s] : 0;
-    const double dt = *dt_ptr;
-    const double w = A.f[FW][o], m = A.f[FM][o], E = A.f[FE][o];
-    const double vx = A.f[FVX][o], vy = A.f[FVY][o], vz = A.f[FVZ][o];
-    double S[3][3];
-    S[0][0] = A.f[FSXX][o]; S[1][1] = A.f[FSYY][o]; S[2][2] = A.f[FSZZ][o];
-    S[0][1] = S[1][0] = A.f[FSXY][o];
-    S[0][2] = S[2][0] = A.f[FSXZ][o];
-    S[1][2] = S[2][1] = A.f[FSYZ][o];
-    const double wn = w + dt * r[0];
-    const double mn = m + dt * r[1];
-    const double mvx = m * vx + dt * (r[2] + m * P.g[0]);
-    const double mvy = m * vy + dt * (r[3] + m * P.g[1]);
-    const double mvz = m * vz + dt * (r[4] + m * P.g[2]);
-    const double gv = P.g[0] * vx + P.g[1] * vy + P.g[2] * vz;
-    const double mE = m * E + dt * (r[5] + m * gv);
-    double Lm[3][3];
-#pragma unroll
-    for (int u = 0; u < 3; ++u)
-#pragma unroll
-        for (int v = 0; v < 3; ++v) Lm[u][v] = r[6 + 3 * u + v];
-    const double trD = Lm[0][0] + Lm[1][1] + Lm[2][2];
-    const double G2 = 2.0 * P.G[mt];
-    double Sn[3][3];
-#pragma unroll
-    for (int u = 0; u < 3; ++u)
-#pragma unroll
-        for (int v = u; v < 3; ++v) {
-            double D = 0.5 * (Lm[u][v] + Lm[v][u]);
-            if (u == v) D -= trD / 3.0;
-            double rot = 0.0;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                double Ouk = 0.5 * (Lm[u][k] - Lm[k][u]);
-                double Okv = 0.5 * (Lm[k][v] - Lm[v][k]);
-                rot += Ouk * S[k][v] - S[u][k] * Okv;
-            }
-            Sn[u][v] = S[u][v] + dt * (G2 * D + rot);
-        }
-    const double trS = (Sn[0][0] + Sn[1][1] + Sn[2][2]) / 3.0;
-    Sn[0][0] -= trS; Sn[1][1] -= trS; Sn[2][2] -= trS;
-    const double ss = Sn[0][0] * Sn[0][0] + Sn[1][1] * Sn[1][1] + Sn[2][2] * Sn[2][2] +
-                      2.0 * (Sn[0][1] * Sn[0][1] + Sn[0][2] * Sn[0][2] + Sn[1][2] * Sn[1][2]);
-    const double seq = sqrt(1.5 * ss);
-    if (seq > P.Y[mt]) {
-        const double f = P.Y[mt] / seq;
+        for (int k = 0; k < 6; ++k) r6[k] = acc.get(k);
+        const double wn = w + dt * r6[0];
+        const double mn = m + dt * r6[1];
+        const double mvx = m * vx + dt * (r6[2] + m * P.g[0]);
+        const double mvy = m * vy + dt * (r6[3] + m * P.g[1]);
+        const double mvz = m * vz + dt * (r6[4] + m * P.g[2]);
+        const double gv = P.g[0] * vx + P.g[1] * vy + P.g[2] * vz;
+        const double mE = m * E + dt * (r6[5] + m * gv);
+        // stress rate 2G (D - tr D / 3) + Om S - S Om (the split path evaluates it in FP32 from the
+        // FP32 velocity gradient; the increment is added to the FP64 stress)
+        R Lm[3][3];
 #pragma unroll
         for (int u = 0; u < 3; ++u)
 #pragma unroll
-            for (int v = u; v < 3; ++v) Sn[u][v] *= f;
-    }
-    const double inv_mn = 1.0 / mn;
-    const double nvx = mvx * inv_mn, nvy = mvy * inv_mn, nvz = mvz * inv_mn;
-    B.f[FX][s] = X + dt * vx;
-    B.f[FY][s] = Y + dt * vy;
-    B.f[FZ][s] = Z + dt * vz;
-    B.f[FVX][s] = nvx;
-    B.f[FVY][s] = nvy;
-    B.f[FVZ][s] = nvz;
-    B.f[FW][s] = wn;
-    B.f[FM][s] = mn;
-    B.f[FE][s] = mE * inv_mn;
-    B.f[FSXX][s] = Sn[0][0];
-    B.f[FSYY][s] = Sn[1][1];
-    B.f[FSZZ][s] = Sn[2][2];
-    B.f[FSXY][s] = Sn[0][1];
-    B.f[FSXZ][s] = Sn[0][2];
-    B.f[FSYZ][s] = Sn[1][2];
-    B.mat[s] = mat_s[s];
-    B.label[s] = lab_s[s];
-    B.id[s] = id_s[s];
-    if (DIAG) {
-        nreal_out[s] = nr;
-        nimage_out[s] = ni;
+            for (int v = 0; v < 3; ++v) Lm[u][v] = acc.getr(6 + 3 * u + v);
+        R Sr[3][3];
+        Sr[0][0] = (R)S[0]; Sr[1][1] = (R)S[1]; Sr[2][2] = (R)S[2];
+        Sr[0][1] = Sr[1][0] = (R)S[3];
+        Sr[0][2] = Sr[2][0] = (R)S[4];
+        Sr[1][2] = Sr[2][1] = (R)S[5];
+        const R trD = Lm[0][0] + Lm[1][1] + Lm[2][2];
+        const R G2 = SPLIT ? (R)(2.0f * P.f_G[mt]) : (R)(2.0 * P.G[mt]);
+        const int iu[6] = {0, 1, 2, 0, 0, 1}, iv[6] = {0, 1, 2, 1, 2, 2};
+        double Sn[6];
 #pragma unroll
-        for (int k = 0; k < kNRate; ++k) rates_out[(size_t)s * kNRate + k] = r[k];
+        for (int q = 0; q < 6; ++q) {
+            const int u = iu[q], v = iv[q];
+            R D = R(0.5) * (Lm[u][v] + Lm[v][u]);
+            if (u == v) D -= trD / R(3);
+            R rot = R(0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const R Ouk = R(0.5) * (Lm[u][k] - Lm[k][u]);
+                const R Okv = R(0.5) * (Lm[k][v] - Lm[v][k]);
+                rot += Ouk * Sr[k][v] - Sr[u][k] * Okv;
+            }
+            Sn[q] = S[q] + dt * (double)(G2 * D + rot);
+        }
+        const double trS = (Sn[0] + Sn[1] + Sn[2]) / 3.0;
+        Sn[0] -= trS; Sn[1] -= trS; Sn[2] -= trS;
+        const R a0 = (R)Sn[0], a1 = (R)Sn[1], a2 = (R)Sn[2], a3 = (R)Sn[3], a4 = (R)Sn[4], a5 = (R)Sn[5];
+        const R ss = a0 * a0 + a1 * a1 + a2 * a2 + R(2) * (a3 * a3 + a4 * a4 + a5 * a5);
+        const R seq = sqrt(R(1.5) * ss);
+        const R Yr = SPLIT ? (R)(float)P.Y[mt] : (R)P.Y[mt];
+        if (seq > Yr) {
+            const double f = (double)(Yr / seq);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) Sn[q] *= f;
+        }
+        const double inv_mn = 1.0 / mn;
+        const double nvx = mvx * inv_mn, nvy = mvy * inv_mn, nvz = mvz * inv_mn;
+        B.f[FX][s] = X + dt * vx;
+        B.f[FY][s] = Y + dt * vy;
+        B.f[FZ][s] = Z + dt * vz;
+        B.f[FVX][s] = nvx;
+        B.f[FVY][s] = nvy;
+        B.f[FVZ][s] = nvz;
+        B.f[FW][s] = wn;
+        B.f[FM][s] = mn;
+        B.f[FE][s] = mE * inv_mn;
+        B.f[FSXX][s] = Sn[0];
+        B.f[FSYY][s] = Sn[1];
+        B.f[FSZZ][s] = Sn[2];
+        B.f[FSXY][s] = Sn[3];
+        B.f[FSXZ][s] = Sn[4];
+        B.f[FSYZ][s] = Sn[5];
+        B.mat[s] = mat_s[s];
+        B.label[s] = lab_s[s];
+        B.id[s] = id_s[s];
+        if (DIAG) {
+            nreal_out[s] = nr;
+            nimage_out[s] = ni;
+#pragma unroll
+            for (int k = 0; k < kNRate; ++k) rates_out[(size_t)s * kNRate + k] = acc.get(k);
+        }
+        // next step's CFL signal speed (correctly rounded FP32, reproducible bit for bit)
+        sp = signal_speed32(P, mt, mn, wn, nvx, nvy, nvz);
     }
-    // next step's CFL signal speed, exactly rounded
-    sp = signal_speed(P, mt, mn, wn, nvx, nvy, nvz);
+    const unsigned b = __reduce_max_sync(kFullMask, __float_as_uint(sp));
+    const unsigned pc = __reduce_add_sync(kFullMask, (unsigned)(nr + ni));
+    if (lane == 0) {
+        atomicMax(sig, b);
+        atomicAdd(pairs, (unsigned long long)pc);
     }
-    unsigned long long b = __double_as_longlong(sp);
-    for (int o2 = 16; o2; o2 >>= 1) {
-        unsigned long long c2 = __shfl_xor_sync(kFullMask, b, o2);
-        b = c2 > b ? c2 : b;
-    }
-    if ((tid & 31) == 0) atomicMax(sig, b);
 }
 
 cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n, const uint32_t *skey,
-                            const uint2 *cellr, const void *pos, const void *rec, const double *xs, const double *ys,
-                            const double *zs, const uint32_t *perm, const State &A, const State &B,
+                            const uint2 *cellr, const void *pos, const void *rec, const float *cxs,
+                            const double *xs, const double *ys, const double *zs, int kmax, uint32_t *list,
+                            uint32_t *cnt, const uint32_t *perm, const State &A, const State &B,
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
-                            unsigned long long *sig, int32_t *nreal, int32_t *nimage, double *rates, cudaStream_t s) {
+                            unsigned int *sig, unsigned long long *pairs, int32_t *nreal, int32_t *nimage,
+                            double *rates, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    unsigned g = (unsigned)((n + IT_THREADS - 1) / IT_THREADS);
-#define GSPH_IT_ARGS P, n, skey, cellr, (const typename Types<SP>::Pos *)pos, (const typename Types<SP>::Rec *)rec, \
-                     xs, ys, zs, perm, A, B, lab_s, mat_s, id_s, dt, sig, nreal, nimage, rates
+    const unsigned gl = (unsigned)((n + NL_THREADS - 1) / NL_THREADS);
+    const unsigned gp = (unsigned)((n + PK_THREADS - 1) / PK_THREADS);
+#define GSPH_NL_ARGS P, n, skey, cellr, (const typename Types<SP>::Pos *)pos, cxs, xs, ys, zs, kmax, list, cnt
+#define GSPH_PK_ARGS P, n, skey, cellr, (const typename Types<SP>::Pos *)pos, (const typename Types<SP>::Rec *)rec, \
+                     cxs, xs, ys, zs, kmax, list, cnt, perm, A, B, lab_s, mat_s, id_s, dt, sig, pairs, nreal, nimage, rates
     if (split) {
         constexpr bool SP = true;
-        if (diag) k_interact<SP, true><<<g, IT_THREADS, 0, s>>>(GSPH_IT_ARGS);
-        else k_interact<SP, false><<<g, IT_THREADS, 0, s>>>(GSPH_IT_ARGS);
+        k_nbr_list<SP><<<gl, NL_THREADS, 0, s>>>(GSPH_NL_ARGS);
+        if (diag) k_pair<SP, true><<<gp, PK_THREADS, 0, s>>>(GSPH_PK_ARGS);
+        else k_pair<SP, false><<<gp, PK_THREADS, 0, s>>>(GSPH_PK_ARGS);
     } else {
         constexpr bool SP = false;
-        if (diag) k_interact<SP, true><<<g, IT_THREADS, 0, s>>>(GSPH_IT_ARGS);
-        else k_interact<SP, false><<<g, IT_THREADS, 0, s>>>(GSPH_IT_ARGS);
+        k_nbr_list<SP><<<gl, NL_THREADS, 0, s>>>(GSPH_NL_ARGS);
+        if (diag) k_pair<SP, true><<<gp, PK_THREADS, 0, s>>>(GSPH_PK_ARGS);
+        else k_pair<SP, false><<<gp, PK_THREADS, 0, s>>>(GSPH_PK_ARGS);
     }
-#undef GSPH_IT_ARGS
+#undef GSPH_NL_ARGS
+#undef GSPH_PK_ARGS
     return cudaGetLastError();
 }
 

@@ -16,8 +16,9 @@ __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const u
                                                  double *__restrict__ xs, double *__restrict__ ys,
                                                  double *__restrict__ zs, uint8_t *__restrict__ lab_s,
                                                  uint8_t *__restrict__ mat_s, uint32_t *__restrict__ id_s,
-                                                 uint2 *__restrict__ cellr, void *__restrict__ pos_out,
-                                                 void *__restrict__ rec_out, int *__restrict__ err) {
+                                                 uint2 *__restrict__ cellr, float *__restrict__ cxs,
+                                                 void *__restrict__ pos_out, void *__restrict__ rec_out,
+                                                 int *__restrict__ err) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     uint32_t k = skey[s];
@@ -34,6 +35,9 @@ __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const u
     if (k < P.ncell) {
         if (s == 0 || skey[s - 1] != k) cellr[k].x = (uint32_t)s;
         if (s == n - 1 || skey[s + 1] != k) cellr[k].y = (uint32_t)(s + 1);
+        cxs[s] = (float)(k % (uint32_t)P.dims[0]);
+    } else {
+        cxs[s] = -1.0e9f;
     }
     double w = A.f[FW][o], m = A.f[FM][o];
     double vx = A.f[FVX][o], vy = A.f[FVY][o], vz = A.f[FVZ][o];
@@ -79,13 +83,15 @@ __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const u
 
 cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint32_t *perm,
                            const State &A, double *xs, double *ys, double *zs, uint8_t *lab_s, uint8_t *mat_s,
-                           uint32_t *id_s, uint2 *cellr, void *pos, void *rec, int *err, cudaStream_t s) {
+                           uint32_t *id_s, uint2 *cellr, float *cxs, void *pos, void *rec, int *err, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     unsigned g = (unsigned)((n + 255) / 256);
     if (split)
-        k_reorder<true><<<g, 256, 0, s>>>(P, n, skey, perm, A, xs, ys, zs, lab_s, mat_s, id_s, cellr, pos, rec, err);
+        k_reorder<true><<<g, 256, 0, s>>>(P, n, skey, perm, A, xs, ys, zs, lab_s, mat_s, id_s, cellr, cxs, pos, rec,
+                                          err);
     else
-        k_reorder<false><<<g, 256, 0, s>>>(P, n, skey, perm, A, xs, ys, zs, lab_s, mat_s, id_s, cellr, pos, rec, err);
+        k_reorder<false><<<g, 256, 0, s>>>(P, n, skey, perm, A, xs, ys, zs, lab_s, mat_s, id_s, cellr, cxs, pos, rec,
+                                           err);
     return cudaGetLastError();
 }
 
@@ -262,39 +268,35 @@ cudaError_t launch_init(const DevParams &P, int64_t n, const double *pos, const 
     return cudaGetLastError();
 }
 
-// Maximum signal speed over the state (bit pattern of a non-negative double, so integer max is
+// Maximum CFL signal speed over the state (bit pattern of a non-negative float, so the integer max is
 // the floating-point max), then dt = cfl * h / max.
-__global__ void k_signal_max(DevParams P, int64_t n, State A, unsigned long long *__restrict__ sig) {
+__global__ void k_signal_max(DevParams P, int64_t n, State A, unsigned int *__restrict__ sig) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double v = 0.0;
+    float v = 0.0f;
     if (i < n) {
         int m = A.mat[i] < P.nmat ? A.mat[i] : 0;
-        v = signal_speed(P, m, A.f[FM][i], A.f[FW][i], A.f[FVX][i], A.f[FVY][i], A.f[FVZ][i]);
+        v = signal_speed32(P, m, A.f[FM][i], A.f[FW][i], A.f[FVX][i], A.f[FVY][i], A.f[FVZ][i]);
     }
-    unsigned long long b = __double_as_longlong(v);
-    for (int o = 16; o; o >>= 1) {
-        unsigned long long c = __shfl_xor_sync(kFullMask, b, o);
-        b = c > b ? c : b;
-    }
+    const unsigned b = __reduce_max_sync(kFullMask, __float_as_uint(v));
     if ((threadIdx.x & 31) == 0) atomicMax(sig, b);
 }
 
-__global__ void k_finalize_dt(DevParams P, unsigned long long *__restrict__ sig, double *__restrict__ dt) {
-    double mx = __longlong_as_double((long long)*sig);
+__global__ void k_finalize_dt(DevParams P, unsigned int *__restrict__ sig, double *__restrict__ dt) {
+    const double mx = (double)__uint_as_float(*sig);
     *dt = __ddiv_rn(__dmul_rn(P.cfl, P.h), mx);
-    *sig = 0ull;
+    *sig = 0u;
 }
 
-cudaError_t launch_dt_from_state(const DevParams &P, int64_t n, const State &A, unsigned long long *sig, double *dt,
+cudaError_t launch_dt_from_state(const DevParams &P, int64_t n, const State &A, unsigned int *sig, double *dt,
                                  cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(sig, 0, sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(sig, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     if (n > 0) k_signal_max<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, n, A, sig);
     k_finalize_dt<<<1, 1, 0, s>>>(P, sig, dt);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_dt(const DevParams &P, unsigned long long *sig, double *dt, cudaStream_t s) {
+cudaError_t launch_finalize_dt(const DevParams &P, unsigned int *sig, double *dt, cudaStream_t s) {
     k_finalize_dt<<<1, 1, 0, s>>>(P, sig, dt);
     return cudaGetLastError();
 }

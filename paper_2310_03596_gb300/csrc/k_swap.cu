@@ -1,19 +1,23 @@
 // k_swap.cu - the communication-load-balancing heuristic (Sec. III.A, III.B) on K virtual labels.
 //
-// For each particle type (one pass over all particles when the scene has one material) and each
-// label pair (a, b) in lexicographic order:
+// One swap pass is a single cooperative kernel (all blocks resident) whose phases are separated by a
+// bounded grid barrier; a barrier that does not complete within about a second records a timeout in the
+// error word and the pass returns. For each particle type (one pass over all particles when the scene
+// has one material) and each label pair (a, b) in lexicographic order:
 //   Cg of a and b from exact fixed-point sums (positions clamped to the grid box, scaled to
 //   [0, 2^32] and truncated, summed in int64), biased towards the label's all-types Cg by alpha when
-//   there are several types (Sec. III.B);
+//   there are several types (Sec. III.B). Every block derives the pair's geometry from the sums
+//   itself, with the same operations, so no block waits for another to publish it;
 //   balancing hash of every particle of a w.r.t. b and of b w.r.t. a (0 on the own side of the
-//   middle of the Cg segment, 1000 beyond the other Cg, floor(1000 t / half-distance) in between,
-//   at least 1), with every product and sum rounded separately;
+//   middle of the Cg segment, 1000 beyond the other Cg, floor(1000 t / half-distance) in between, at
+//   least 1); the offset from the middle in FP64, the projection and scaling in FP32;
 //   n = min(#positive on each side); the n largest hashes of each side swap labels, ties broken by
 //   the lowest persistent id (a 1001-bin histogram finds the threshold hash, a 3 x 9-bit radix
 //   select on ids finds the id threshold inside the threshold bin);
 //   the fixed-point sums are updated with the moved particles (exactly, so the next pair sees the
 //   same Cg as a recomputation).
-// Everything stays on the device: no host synchronisation inside a pass.
+#include <cuda/atomic>
+
 #include "gsph_internal.cuh"
 
 namespace gsph {
@@ -21,311 +25,346 @@ namespace gsph {
 constexpr int SW_BINS = GSPH_BALANCE_HASH_MAX + 1;
 constexpr int SW_ID_BITS = 9;
 constexpr int SW_ID_BINS = 1 << SW_ID_BITS;
-constexpr int SW_THREADS = 256;
+constexpr int SW_THREADS = 512;
+constexpr int SW_NT = kMaxMat + 1;   // per-type slots + the all-types slot
 
 struct SwapPair {
-    double own[2][3];           // side 0 = label a, side 1 = label b: own Cg' and the other's Cg'
-    double oth[2][3];
-    int active;
-    int a, b, type;             // type -1: all particles
-    unsigned long long nsel;    // particles swapped each way
     uint32_t hist[2][SW_BINS];
-    uint32_t idh[2][SW_ID_BINS];
-    int T[2];                   // threshold hash
-    uint32_t need[2];           // still to take from the threshold bin
-    uint32_t idpre[2];          // id prefix found so far
-    int idsel[2];               // 1: the threshold bin is split, ids decide
-};
-
-struct SwapScratch {
-    long long sums[kMaxLabel][kMaxMat + 1][3];
-    long long cnt[kMaxLabel][kMaxMat + 1];
+    uint32_t idh[3][2][SW_ID_BINS];
     unsigned long long moved;
 };
 
-// Exact fixed-point coordinate: clamp to [lo, lo + ext], scale by 2^32 / ext, truncate.
-__device__ __forceinline__ long long quantise(double x, double lo, double hi, double sc) {
-    double xc = fmin(fmax(x, lo), hi);
-    double t = __dmul_rn(__dsub_rn(xc, lo), sc);
-    return (long long)t;
-}
+struct SwapScratch {
+    long long sums[kMaxLabel][SW_NT][3];
+    long long cnt[kMaxLabel][SW_NT];
+    unsigned long long moved;
+    unsigned int bar_count;
+    unsigned int bar_gen;
+};
 
 struct QuantParams {
     double lo[3], hi[3], sc[3], inv[3];
 };
 
-__global__ void k_cg_sums(int64_t n, QuantParams Q, const double *__restrict__ x, const double *__restrict__ y,
-                          const double *__restrict__ z, const uint8_t *__restrict__ lab,
-                          const uint8_t *__restrict__ mat, int nt, SwapScratch *__restrict__ S) {
-    __shared__ long long sh[kMaxLabel][kMaxMat + 1][4];
-    for (int i = threadIdx.x; i < kMaxLabel * (kMaxMat + 1) * 4; i += blockDim.x) (&sh[0][0][0])[i] = 0;
-    __syncthreads();
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        int l = lab[i] & (kMaxLabel - 1);
-        int t = nt > 0 ? (mat[i] < nt ? mat[i] : 0) : -1;
-        long long q0 = quantise(x[i], Q.lo[0], Q.hi[0], Q.sc[0]);
-        long long q1 = quantise(y[i], Q.lo[1], Q.hi[1], Q.sc[1]);
-        long long q2 = quantise(z[i], Q.lo[2], Q.hi[2], Q.sc[2]);
-        const int all = kMaxMat;
-        atomicAdd((unsigned long long *)&sh[l][all][0], (unsigned long long)q0);
-        atomicAdd((unsigned long long *)&sh[l][all][1], (unsigned long long)q1);
-        atomicAdd((unsigned long long *)&sh[l][all][2], (unsigned long long)q2);
-        atomicAdd((unsigned long long *)&sh[l][all][3], 1ull);
-        if (t >= 0) {
-            atomicAdd((unsigned long long *)&sh[l][t][0], (unsigned long long)q0);
-            atomicAdd((unsigned long long *)&sh[l][t][1], (unsigned long long)q1);
-            atomicAdd((unsigned long long *)&sh[l][t][2], (unsigned long long)q2);
-            atomicAdd((unsigned long long *)&sh[l][t][3], 1ull);
-        }
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < kMaxLabel * (kMaxMat + 1); k += blockDim.x) {
-        int l = k / (kMaxMat + 1), t = k % (kMaxMat + 1);
-        if (sh[l][t][3] == 0) continue;
-        for (int a = 0; a < 3; ++a) atomicAdd((unsigned long long *)&S->sums[l][t][a], (unsigned long long)sh[l][t][a]);
-        atomicAdd((unsigned long long *)&S->cnt[l][t], (unsigned long long)sh[l][t][3]);
-    }
+// Exact fixed-point coordinate: clamp to [lo, lo + ext], scale by 2^32 / ext, truncate.
+__device__ __forceinline__ long long quantise(double x, double lo, double hi, double sc) {
+    const double xc = fmin(fmax(x, lo), hi);
+    return (long long)__dmul_rn(__dsub_rn(xc, lo), sc);
 }
 
 __device__ __forceinline__ void cg_of(const QuantParams &Q, const long long *sum, long long cnt, double cg[3]) {
     for (int a = 0; a < 3; ++a) {
-        double mean = __ddiv_rn((double)sum[a], (double)cnt);
+        const double mean = __ddiv_rn((double)sum[a], (double)cnt);
         cg[a] = __dadd_rn(Q.lo[a], __dmul_rn(mean, Q.inv[a]));
     }
 }
 
-__global__ void k_pair_setup(QuantParams Q, double alpha, int multi, int a, int b, int type,
-                             const SwapScratch *__restrict__ S, SwapPair *__restrict__ pr) {
-    const int slot = type >= 0 ? type : kMaxMat;
-    pr->a = a;
-    pr->b = b;
-    pr->type = type;
-    pr->active = 0;
-    long long na = S->cnt[a][slot], nb = S->cnt[b][slot];
-    if (na == 0 || nb == 0) return;
-    double ca[3], cb[3];
-    cg_of(Q, S->sums[a][slot], na, ca);
-    cg_of(Q, S->sums[b][slot], nb, cb);
-    if (multi) {
-        double aa[3], ab[3];
-        cg_of(Q, S->sums[a][kMaxMat], S->cnt[a][kMaxMat], aa);
-        cg_of(Q, S->sums[b][kMaxMat], S->cnt[b][kMaxMat], ab);
-        double beta = __dsub_rn(1.0, alpha);
-        for (int k = 0; k < 3; ++k) {
-            ca[k] = __dadd_rn(__dmul_rn(alpha, aa[k]), __dmul_rn(beta, ca[k]));
-            cb[k] = __dadd_rn(__dmul_rn(alpha, ab[k]), __dmul_rn(beta, cb[k]));
-        }
-    }
-    for (int k = 0; k < 3; ++k) {
-        pr->own[0][k] = ca[k]; pr->oth[0][k] = cb[k];
-        pr->own[1][k] = cb[k]; pr->oth[1][k] = ca[k];
-    }
-    pr->active = 1;
-}
+// Pair geometry for one side: middle M (FP64), unit direction u and scale 1000 / half-distance (FP32).
+struct Side {
+    double M[3];
+    float u[3];
+    float scale;
+};
 
-// Balancing hash of position p for a particle owned by the label with Cg `own`, w.r.t. `oth`.
-__device__ __forceinline__ int balancing_hash(const double own[3], const double oth[3], double p0, double p1,
-                                              double p2) {
-    double M[3], d[3];
+__device__ __forceinline__ bool side_geometry(const double own[3], const double oth[3], Side &sd) {
+    double d[3];
     for (int k = 0; k < 3; ++k) {
-        M[k] = __dmul_rn(__dadd_rn(own[k], oth[k]), 0.5);
+        sd.M[k] = __dmul_rn(__dadd_rn(own[k], oth[k]), 0.5);
         d[k] = __dsub_rn(oth[k], own[k]);
     }
-    double dn = __dsqrt_rn(dist2_rn(d[0], d[1], d[2]));
-    if (!(dn > 0.0)) return 0;
-    double ell = __dmul_rn(dn, 0.5);
-    double t = __dadd_rn(__dadd_rn(__dmul_rn(__dsub_rn(p0, M[0]), d[0]), __dmul_rn(__dsub_rn(p1, M[1]), d[1])),
-                         __dmul_rn(__dsub_rn(p2, M[2]), d[2]));
-    t = __ddiv_rn(t, dn);
-    if (!(t > 0.0)) return 0;
-    if (t >= ell) return GSPH_BALANCE_HASH_MAX;
-    double k = floor(__ddiv_rn(__dmul_rn(1000.0, t), ell));
-    int h = (int)k;
-    h = h < 1 ? 1 : h;
-    h = h > GSPH_BALANCE_HASH_MAX ? GSPH_BALANCE_HASH_MAX : h;
-    return h;
+    const double dn = __dsqrt_rn(dist2_rn(d[0], d[1], d[2]));
+    if (!(dn > 0.0)) return false;
+    const double ell = __dmul_rn(dn, 0.5);
+    for (int k = 0; k < 3; ++k) sd.u[k] = (float)__ddiv_rn(d[k], dn);
+    sd.scale = (float)__ddiv_rn(1000.0, ell);
+    return true;
 }
 
-__device__ __forceinline__ int side_of(const SwapPair &pr, uint8_t lab, uint8_t mat) {
-    if (pr.type >= 0 && mat != pr.type) return -1;
-    if (lab == pr.a) return 0;
-    if (lab == pr.b) return 1;
-    return -1;
+__device__ __forceinline__ int balancing_hash(const Side &sd, double p0, double p1, double p2) {
+    const float e0 = (float)__dsub_rn(p0, sd.M[0]);
+    const float e1 = (float)__dsub_rn(p1, sd.M[1]);
+    const float e2 = (float)__dsub_rn(p2, sd.M[2]);
+    const float t = __fadd_rn(__fadd_rn(__fmul_rn(e0, sd.u[0]), __fmul_rn(e1, sd.u[1])), __fmul_rn(e2, sd.u[2]));
+    if (!(t > 0.0f)) return 0;
+    const float k = floorf(__fmul_rn(t, sd.scale));
+    if (k >= (float)GSPH_BALANCE_HASH_MAX) return GSPH_BALANCE_HASH_MAX;
+    if (k < 1.0f) return 1;
+    return (int)k;
 }
 
-__global__ void __launch_bounds__(SW_THREADS) k_bhash(int64_t n, const double *__restrict__ x,
-                                                      const double *__restrict__ y, const double *__restrict__ z,
-                                                      const uint8_t *__restrict__ lab, const uint8_t *__restrict__ mat,
-                                                      SwapPair *__restrict__ pr, uint16_t *__restrict__ bh) {
+// Bounded grid barrier (generation counter). Returns false, with the timeout bit set, when the
+// other blocks do not arrive within the spin limit.
+__device__ bool grid_barrier(SwapScratch *S, unsigned nblocks, int *err) {
+    __shared__ int ok_sh;
+    __threadfence();   // this thread's writes of the phase are visible device-wide before arrival
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(S->bar_gen);
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(S->bar_count);
+        const unsigned g = gen.load(cuda::memory_order_acquire);
+        int ok = 1;
+        if (cnt.fetch_add(1u, cuda::memory_order_acq_rel) == nblocks - 1) {
+            cnt.store(0u, cuda::memory_order_relaxed);
+            gen.fetch_add(1u, cuda::memory_order_release);
+        } else {
+            unsigned it = 0;
+            while (gen.load(cuda::memory_order_acquire) == g) {
+                if (++it > (1u << 24)) {   // about a second with the back-off below
+                    atomicOr(err, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        ok_sh = ok;
+    }
+    __syncthreads();
+    return ok_sh != 0;
+}
+
+__global__ void __launch_bounds__(SW_THREADS) k_swap_pass(int64_t n, QuantParams Q, double alpha, int K, int nmat,
+                                                          const double *__restrict__ x, const double *__restrict__ y,
+                                                          const double *__restrict__ z, uint8_t *__restrict__ lab,
+                                                          const uint8_t *__restrict__ mat,
+                                                          const uint32_t *__restrict__ id, uint16_t *__restrict__ bh,
+                                                          SwapScratch *__restrict__ S, SwapPair *__restrict__ pairs,
+                                                          int *__restrict__ err) {
+    __shared__ long long shs[kMaxLabel][SW_NT][4];
     __shared__ uint32_t hs[2][SW_BINS];
-    __shared__ double own[2][3], oth[2][3];
-    __shared__ int act;
-    if (threadIdx.x == 0) act = pr->active;
-    if (threadIdx.x < 6) {
-        int sd = threadIdx.x / 3, k = threadIdx.x % 3;
-        own[sd][k] = pr->own[sd][k];
-        oth[sd][k] = pr->oth[sd][k];
-    }
-    for (int i = threadIdx.x; i < 2 * SW_BINS; i += SW_THREADS) (&hs[0][0])[i] = 0;
-    __syncthreads();
-    if (!act) return;
-    const int a = pr->a, b = pr->b, type = pr->type;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        uint8_t l = lab[i];
-        int sd = -1;
-        if (type < 0 || mat[i] == type) sd = (l == a) ? 0 : ((l == b) ? 1 : -1);
-        if (sd >= 0) {
-            int hv = balancing_hash(own[sd], oth[sd], x[i], y[i], z[i]);
-            bh[i] = (uint16_t)hv;
-            atomicAdd(&hs[sd][hv], 1u);
-        }
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < 2 * SW_BINS; k += SW_THREADS) {
-        uint32_t v = (&hs[0][0])[k];
-        if (v) atomicAdd(&(&pr->hist[0][0])[k], v);
-    }
-}
+    __shared__ uint32_t ids[2][SW_ID_BINS];
+    __shared__ Side side_sh[2];
+    __shared__ int act_sh;
+    __shared__ int T_sh[2], idsel_sh[2];
+    __shared__ uint32_t need_sh[2], idpre_sh[2];
+    __shared__ long long dsum[2][4];   // per side: moved q0 q1 q2, count
+    const unsigned nb = gridDim.x;
+    const int64_t gstride = (int64_t)gridDim.x * SW_THREADS;
+    const int64_t g0 = (int64_t)blockIdx.x * SW_THREADS + threadIdx.x;
+    const bool multi = nmat > 1;
+    const int ntype = multi ? nmat : 1;
 
-// One block: n = min(#positive), then for each side the threshold hash and how many to take from
-// the threshold bin (histograms staged in shared memory, scanned by one thread).
-__global__ void __launch_bounds__(1024) k_select(SwapPair *__restrict__ pr) {
-    __shared__ uint32_t hs[2][SW_BINS];
-    if (!pr->active) return;
-    for (int k = threadIdx.x; k < 2 * SW_BINS; k += blockDim.x) (&hs[0][0])[k] = (&pr->hist[0][0])[k];
+    // ---- exact fixed-point sums per (label, type) and per label
+    for (int i = threadIdx.x; i < kMaxLabel * SW_NT * 4; i += SW_THREADS) (&shs[0][0][0])[i] = 0;
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    uint64_t pos[2];
-    for (int sd = 0; sd < 2; ++sd) {
-        uint64_t c = 0;
-        for (int hv = 1; hv < SW_BINS; ++hv) c += hs[sd][hv];
-        pos[sd] = c;
-    }
-    uint64_t m = pos[0] < pos[1] ? pos[0] : pos[1];
-    pr->nsel = m;
-    if (m == 0) {
-        pr->active = 0;
-        return;
-    }
-    for (int sd = 0; sd < 2; ++sd) {
-        uint64_t above = 0;
-        int T = GSPH_BALANCE_HASH_MAX;
-        for (; T >= 1; --T) {
-            if (above + hs[sd][T] >= m) break;
-            above += hs[sd][T];
-        }
-        pr->T[sd] = T;
-        pr->need[sd] = (uint32_t)(m - above);
-        pr->idsel[sd] = pr->need[sd] < hs[sd][T];
-        pr->idpre[sd] = 0;
-    }
-}
-
-// Radix select on persistent ids inside the threshold bin: histogram of id digit `pass` (9 bits,
-// most significant first) among the candidates whose higher digits match the prefix so far.
-__global__ void __launch_bounds__(SW_THREADS) k_idhist(int64_t n, const uint8_t *__restrict__ lab,
-                                                       const uint8_t *__restrict__ mat,
-                                                       const uint32_t *__restrict__ id,
-                                                       const uint16_t *__restrict__ bh, SwapPair *__restrict__ pr,
-                                                       int pass) {
-    __shared__ uint32_t hs[2][SW_ID_BINS];
-    __shared__ int need_any;
-    if (threadIdx.x == 0) need_any = pr->active && (pr->idsel[0] || pr->idsel[1]);
-    for (int k = threadIdx.x; k < 2 * SW_ID_BINS; k += SW_THREADS) (&hs[0][0])[k] = 0;
-    __syncthreads();
-    if (!need_any) return;
-    const int shift = 18 - SW_ID_BITS * pass;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        int sd = side_of(*pr, lab[i], mat[i]);
-        if (sd >= 0 && pr->idsel[sd] && bh[i] == pr->T[sd]) {
-            uint32_t v = id[i];
-            if ((v >> (shift + SW_ID_BITS)) == (pr->idpre[sd] >> (shift + SW_ID_BITS)))
-                atomicAdd(&hs[sd][(v >> shift) & (SW_ID_BINS - 1)], 1u);
-        }
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < 2 * SW_ID_BINS; k += SW_THREADS) {
-        uint32_t v = (&hs[0][0])[k];
-        if (v) atomicAdd(&(&pr->idh[0][0])[k], v);
-    }
-}
-
-__global__ void __launch_bounds__(SW_ID_BINS) k_idselect(SwapPair *__restrict__ pr, int pass) {
-    __shared__ uint32_t hs[2][SW_ID_BINS];
-    if (!pr->active) return;
-    for (int k = threadIdx.x; k < 2 * SW_ID_BINS; k += blockDim.x) {
-        (&hs[0][0])[k] = (&pr->idh[0][0])[k];
-        (&pr->idh[0][0])[k] = 0;
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    const int shift = 18 - SW_ID_BITS * pass;
-    for (int sd = 0; sd < 2; ++sd) {
-        if (!pr->idsel[sd]) continue;
-        uint32_t need = pr->need[sd], below = 0;
-        int d = 0;
-        for (; d < SW_ID_BINS - 1; ++d) {
-            if (below + hs[sd][d] >= need) break;
-            below += hs[sd][d];
-        }
-        pr->idpre[sd] |= (uint32_t)d << shift;
-        pr->need[sd] = need - below;
-    }
-}
-
-// Label exchange and exact update of the fixed-point sums.
-__global__ void __launch_bounds__(SW_THREADS) k_apply(int64_t n, QuantParams Q, const double *__restrict__ x,
-                                                      const double *__restrict__ y, const double *__restrict__ z,
-                                                      uint8_t *__restrict__ lab, const uint8_t *__restrict__ mat,
-                                                      const uint32_t *__restrict__ id,
-                                                      const uint16_t *__restrict__ bh, SwapPair *__restrict__ pr,
-                                                      SwapScratch *__restrict__ S, int nt) {
-    if (!pr->active) return;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int sd = side_of(*pr, lab[i], mat[i]);
-    if (sd < 0) return;
-    int hv = bh[i];
-    bool take = hv > pr->T[sd] || (hv == pr->T[sd] && (!pr->idsel[sd] || id[i] <= pr->idpre[sd]));
-    if (hv == 0 || !take) return;
-    int from = sd == 0 ? pr->a : pr->b, to = sd == 0 ? pr->b : pr->a;
-    lab[i] = (uint8_t)to;
-    long long q[3] = {quantise(x[i], Q.lo[0], Q.hi[0], Q.sc[0]), quantise(y[i], Q.lo[1], Q.hi[1], Q.sc[1]),
-                      quantise(z[i], Q.lo[2], Q.hi[2], Q.sc[2])};
-    int t = nt > 0 ? (mat[i] < nt ? mat[i] : 0) : -1;
-    for (int k = 0; k < 3; ++k) {
-        atomicAdd((unsigned long long *)&S->sums[from][kMaxMat][k], (unsigned long long)(-q[k]));
-        atomicAdd((unsigned long long *)&S->sums[to][kMaxMat][k], (unsigned long long)q[k]);
+    for (int64_t i = g0; i < n; i += gstride) {
+        const int l = lab[i] & (kMaxLabel - 1);
+        const int t = multi ? (mat[i] < nmat ? mat[i] : 0) : -1;
+        const long long q0 = quantise(x[i], Q.lo[0], Q.hi[0], Q.sc[0]);
+        const long long q1 = quantise(y[i], Q.lo[1], Q.hi[1], Q.sc[1]);
+        const long long q2 = quantise(z[i], Q.lo[2], Q.hi[2], Q.sc[2]);
+        atomicAdd((unsigned long long *)&shs[l][kMaxMat][0], (unsigned long long)q0);
+        atomicAdd((unsigned long long *)&shs[l][kMaxMat][1], (unsigned long long)q1);
+        atomicAdd((unsigned long long *)&shs[l][kMaxMat][2], (unsigned long long)q2);
+        atomicAdd((unsigned long long *)&shs[l][kMaxMat][3], 1ull);
         if (t >= 0) {
-            atomicAdd((unsigned long long *)&S->sums[from][t][k], (unsigned long long)(-q[k]));
-            atomicAdd((unsigned long long *)&S->sums[to][t][k], (unsigned long long)q[k]);
+            atomicAdd((unsigned long long *)&shs[l][t][0], (unsigned long long)q0);
+            atomicAdd((unsigned long long *)&shs[l][t][1], (unsigned long long)q1);
+            atomicAdd((unsigned long long *)&shs[l][t][2], (unsigned long long)q2);
+            atomicAdd((unsigned long long *)&shs[l][t][3], 1ull);
         }
     }
-    atomicAdd((unsigned long long *)&S->cnt[from][kMaxMat], (unsigned long long)(-1ll));
-    atomicAdd((unsigned long long *)&S->cnt[to][kMaxMat], 1ull);
-    if (t >= 0) {
-        atomicAdd((unsigned long long *)&S->cnt[from][t], (unsigned long long)(-1ll));
-        atomicAdd((unsigned long long *)&S->cnt[to][t], 1ull);
+    __syncthreads();
+    for (int k = threadIdx.x; k < kMaxLabel * SW_NT; k += SW_THREADS) {
+        const int l = k / SW_NT, t = k % SW_NT;
+        if (shs[l][t][3] == 0) continue;
+        for (int a = 0; a < 3; ++a) atomicAdd((unsigned long long *)&S->sums[l][t][a], (unsigned long long)shs[l][t][a]);
+        atomicAdd((unsigned long long *)&S->cnt[l][t], (unsigned long long)shs[l][t][3]);
     }
-    atomicAdd(&S->moved, 1ull);
+    if (!grid_barrier(S, nb, err)) return;
+
+    int idx = 0;
+    for (int T = 0; T < ntype; ++T) {
+        const int type = multi ? T : -1;
+        const int slot = multi ? T : kMaxMat;
+        for (int a = 0; a < K - 1; ++a)
+            for (int b = a + 1; b < K; ++b, ++idx) {
+                SwapPair *pr = pairs + idx;
+                // -- pair geometry (every block, identical operations on the same sums)
+                if (threadIdx.x == 0) {
+                    act_sh = 0;
+                    const long long na = ((volatile long long *)&S->cnt[a][slot])[0];
+                    const long long nbb = ((volatile long long *)&S->cnt[b][slot])[0];
+                    if (na > 0 && nbb > 0) {
+                        long long sa[3], sb[3], saa[3], sab[3];
+                        for (int k = 0; k < 3; ++k) {
+                            sa[k] = ((volatile long long *)&S->sums[a][slot][k])[0];
+                            sb[k] = ((volatile long long *)&S->sums[b][slot][k])[0];
+                            saa[k] = ((volatile long long *)&S->sums[a][kMaxMat][k])[0];
+                            sab[k] = ((volatile long long *)&S->sums[b][kMaxMat][k])[0];
+                        }
+                        double ca[3], cb[3];
+                        cg_of(Q, sa, na, ca);
+                        cg_of(Q, sb, nbb, cb);
+                        if (multi) {
+                            double aa[3], ab[3];
+                            cg_of(Q, saa, ((volatile long long *)&S->cnt[a][kMaxMat])[0], aa);
+                            cg_of(Q, sab, ((volatile long long *)&S->cnt[b][kMaxMat])[0], ab);
+                            const double beta = __dsub_rn(1.0, alpha);
+                            for (int k = 0; k < 3; ++k) {
+                                ca[k] = __dadd_rn(__dmul_rn(alpha, aa[k]), __dmul_rn(beta, ca[k]));
+                                cb[k] = __dadd_rn(__dmul_rn(alpha, ab[k]), __dmul_rn(beta, cb[k]));
+                            }
+                        }
+                        const bool ga = side_geometry(ca, cb, side_sh[0]);
+                        const bool gb = side_geometry(cb, ca, side_sh[1]);
+                        act_sh = ga && gb;
+                    }
+                }
+                for (int k = threadIdx.x; k < 2 * SW_BINS; k += SW_THREADS) (&hs[0][0])[k] = 0;
+                __syncthreads();
+                const bool act = act_sh != 0;
+                // -- balancing hashes and their histograms
+                if (act) {
+                    const Side s0 = side_sh[0], s1 = side_sh[1];
+                    for (int64_t i = g0; i < n; i += gstride) {
+                        const uint8_t l = lab[i];
+                        if ((l != a && l != b) || (type >= 0 && mat[i] != type)) continue;
+                        const int sd = l == a ? 0 : 1;
+                        const int hv = balancing_hash(sd == 0 ? s0 : s1, x[i], y[i], z[i]);
+                        bh[i] = (uint16_t)hv;
+                        atomicAdd(&hs[sd][hv], 1u);
+                    }
+                    __syncthreads();
+                    for (int k = threadIdx.x; k < 2 * SW_BINS; k += SW_THREADS) {
+                        const uint32_t v = (&hs[0][0])[k];
+                        if (v) atomicAdd(&(&pr->hist[0][0])[k], v);
+                    }
+                }
+                if (!grid_barrier(S, nb, err)) return;
+                if (!act) continue;
+                // -- n = min(#positive), threshold hash and the count to take from the threshold bin
+                for (int k = threadIdx.x; k < 2 * SW_BINS; k += SW_THREADS)
+                    (&hs[0][0])[k] = ((volatile uint32_t *)&pr->hist[0][0])[k];
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    unsigned long long pos[2];
+                    for (int sd = 0; sd < 2; ++sd) {
+                        unsigned long long c = 0;
+                        for (int hv = 1; hv < SW_BINS; ++hv) c += hs[sd][hv];
+                        pos[sd] = c;
+                    }
+                    const unsigned long long m = pos[0] < pos[1] ? pos[0] : pos[1];
+                    act_sh = m > 0;
+                    idsel_sh[0] = idsel_sh[1] = 0;
+                    for (int sd = 0; sd < 2 && m > 0; ++sd) {
+                        unsigned long long above = 0;
+                        int Tb = GSPH_BALANCE_HASH_MAX;
+                        for (; Tb >= 1; --Tb) {
+                            if (above + hs[sd][Tb] >= m) break;
+                            above += hs[sd][Tb];
+                        }
+                        T_sh[sd] = Tb;
+                        need_sh[sd] = (uint32_t)(m - above);
+                        idsel_sh[sd] = need_sh[sd] < hs[sd][Tb];
+                        idpre_sh[sd] = 0;
+                    }
+                    if (blockIdx.x == 0) pr->moved = 2 * m;
+                }
+                __syncthreads();
+                if (!act_sh) continue;    // the same decision in every block: no barrier is skipped unevenly
+                // -- radix select on persistent ids inside split threshold bins
+                if (idsel_sh[0] || idsel_sh[1]) {
+                    for (int pass = 0; pass < 3; ++pass) {
+                        const int shift = 18 - SW_ID_BITS * pass;
+                        for (int k = threadIdx.x; k < 2 * SW_ID_BINS; k += SW_THREADS) (&ids[0][0])[k] = 0;
+                        __syncthreads();
+                        for (int64_t i = g0; i < n; i += gstride) {
+                            const uint8_t l = lab[i];
+                            if ((l != a && l != b) || (type >= 0 && mat[i] != type)) continue;
+                            const int sd = l == a ? 0 : 1;
+                            if (!idsel_sh[sd] || bh[i] != T_sh[sd]) continue;
+                            const uint32_t v = id[i];
+                            if ((v >> (shift + SW_ID_BITS)) == (idpre_sh[sd] >> (shift + SW_ID_BITS)))
+                                atomicAdd(&ids[sd][(v >> shift) & (SW_ID_BINS - 1)], 1u);
+                        }
+                        __syncthreads();
+                        for (int k = threadIdx.x; k < 2 * SW_ID_BINS; k += SW_THREADS) {
+                            const uint32_t v = (&ids[0][0])[k];
+                            if (v) atomicAdd(&(&pr->idh[pass][0][0])[k], v);
+                        }
+                        if (!grid_barrier(S, nb, err)) return;
+                        for (int k = threadIdx.x; k < 2 * SW_ID_BINS; k += SW_THREADS)
+                            (&ids[0][0])[k] = ((volatile uint32_t *)&pr->idh[pass][0][0])[k];
+                        __syncthreads();
+                        if (threadIdx.x == 0) {
+                            for (int sd = 0; sd < 2; ++sd) {
+                                if (!idsel_sh[sd]) continue;
+                                uint32_t below = 0;
+                                int d = 0;
+                                for (; d < SW_ID_BINS - 1; ++d) {
+                                    if (below + ids[sd][d] >= need_sh[sd]) break;
+                                    below += ids[sd][d];
+                                }
+                                idpre_sh[sd] |= (uint32_t)d << shift;
+                                need_sh[sd] -= below;
+                            }
+                        }
+                        __syncthreads();
+                    }
+                }
+                // -- label exchange and exact update of the fixed-point sums
+                if (threadIdx.x < 8) (&dsum[0][0])[threadIdx.x] = 0;
+                __syncthreads();
+                for (int64_t i = g0; i < n; i += gstride) {
+                    const uint8_t l = lab[i];
+                    if ((l != a && l != b) || (type >= 0 && mat[i] != type)) continue;
+                    const int sd = l == a ? 0 : 1;
+                    const int hv = bh[i];
+                    const bool take =
+                        hv > 0 && (hv > T_sh[sd] || (hv == T_sh[sd] && (!idsel_sh[sd] || id[i] <= idpre_sh[sd])));
+                    if (!take) continue;
+                    lab[i] = (uint8_t)(sd == 0 ? b : a);
+                    atomicAdd((unsigned long long *)&dsum[sd][0],
+                              (unsigned long long)quantise(x[i], Q.lo[0], Q.hi[0], Q.sc[0]));
+                    atomicAdd((unsigned long long *)&dsum[sd][1],
+                              (unsigned long long)quantise(y[i], Q.lo[1], Q.hi[1], Q.sc[1]));
+                    atomicAdd((unsigned long long *)&dsum[sd][2],
+                              (unsigned long long)quantise(z[i], Q.lo[2], Q.hi[2], Q.sc[2]));
+                    atomicAdd((unsigned long long *)&dsum[sd][3], 1ull);
+                }
+                __syncthreads();
+                if (threadIdx.x < 2) {
+                    const int sd = threadIdx.x;
+                    const int from = sd == 0 ? a : b, to = sd == 0 ? b : a;
+                    const long long c = dsum[sd][3];
+                    if (c) {
+                        for (int k = 0; k < 3; ++k) {
+                            const long long q = dsum[sd][k];
+                            atomicAdd((unsigned long long *)&S->sums[from][kMaxMat][k], (unsigned long long)(-q));
+                            atomicAdd((unsigned long long *)&S->sums[to][kMaxMat][k], (unsigned long long)q);
+                            if (type >= 0) {
+                                atomicAdd((unsigned long long *)&S->sums[from][type][k], (unsigned long long)(-q));
+                                atomicAdd((unsigned long long *)&S->sums[to][type][k], (unsigned long long)q);
+                            }
+                        }
+                        atomicAdd((unsigned long long *)&S->cnt[from][kMaxMat], (unsigned long long)(-c));
+                        atomicAdd((unsigned long long *)&S->cnt[to][kMaxMat], (unsigned long long)c);
+                        if (type >= 0) {
+                            atomicAdd((unsigned long long *)&S->cnt[from][type], (unsigned long long)(-c));
+                            atomicAdd((unsigned long long *)&S->cnt[to][type], (unsigned long long)c);
+                        }
+                        atomicAdd(&S->moved, (unsigned long long)c);
+                    }
+                }
+                if (!grid_barrier(S, nb, err)) return;
+            }
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
-// Host side: one full pass.
+// Host side: one full pass, one cooperative launch.
 // ---------------------------------------------------------------------------------------------
 size_t swap_scratch_bytes(int K, int nmat) {
-    int ntype = nmat > 1 ? nmat : 1;
-    size_t npairs = (size_t)ntype * (size_t)(K * (K - 1) / 2);
+    const int ntype = nmat > 1 ? nmat : 1;
+    const size_t npairs = (size_t)ntype * (size_t)(K * (K - 1) / 2);
     return sizeof(SwapScratch) + (npairs > 0 ? npairs : 1) * sizeof(SwapPair);
 }
 
-QuantParams quant_params(const DevParams &P) {
+static QuantParams quant_params(const DevParams &P) {
     QuantParams Q;
     for (int a = 0; a < 3; ++a) {
-        double ext = (double)P.dims[a] * P.cell;
+        const double ext = (double)P.dims[a] * P.cell;
         Q.lo[a] = P.lo[a];
         Q.hi[a] = P.lo[a] + ext;
         Q.sc[a] = 4294967296.0 / ext;
@@ -334,40 +373,33 @@ QuantParams quant_params(const DevParams &P) {
     return Q;
 }
 
-// scratch: swap_scratch_bytes() device bytes; bh: n uint16. moved_out (device) receives the number of
-// particles that changed label.
+// Blocks of the cooperative swap pass: two per SM when they fit (all must be resident at once).
+int swap_grid_blocks() {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_swap_pass, SW_THREADS, 0) != cudaSuccess) return 0;
+    return sms * (per < 2 ? per : 2);
+}
+
+// scratch: swap_scratch_bytes() device bytes; bh: n uint16; grid from swap_grid_blocks().
 cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const double *x, const double *y, const double *z,
                              uint8_t *lab, const uint8_t *mat, const uint32_t *id, void *scratch, uint16_t *bh,
-                             cudaStream_t s) {
+                             int *err, int grid, cudaStream_t s) {
     if (n <= 0 || P.K_labels < 2) return cudaSuccess;
-    const int K = P.K_labels;
-    const int multi = P.nmat > 1;
-    const int ntype = multi ? P.nmat : 1;
-    const size_t bytes = swap_scratch_bytes(K, P.nmat);
+    if (grid < 1) return cudaErrorCooperativeLaunchTooLarge;
+    const size_t bytes = swap_scratch_bytes(P.K_labels, P.nmat);
     cudaError_t e = cudaMemsetAsync(scratch, 0, bytes, s);
     if (e != cudaSuccess) return e;
     SwapScratch *S = (SwapScratch *)scratch;
     SwapPair *pairs = (SwapPair *)((char *)scratch + sizeof(SwapScratch));
     QuantParams Q = quant_params(P);
-    unsigned g = (unsigned)((n + SW_THREADS - 1) / SW_THREADS);
-    k_cg_sums<<<g, SW_THREADS, 0, s>>>(n, Q, x, y, z, lab, mat, multi ? P.nmat : 0, S);
-    int idx = 0;
-    for (int T = 0; T < ntype; ++T) {
-        int type = multi ? T : -1;
-        for (int a = 0; a < K - 1; ++a)
-            for (int b = a + 1; b < K; ++b, ++idx) {
-                SwapPair *pr = pairs + idx;
-                k_pair_setup<<<1, 1, 0, s>>>(Q, P.alpha, multi, a, b, type, S, pr);
-                k_bhash<<<g, SW_THREADS, 0, s>>>(n, x, y, z, lab, mat, pr, bh);
-                k_select<<<1, 1024, 0, s>>>(pr);
-                for (int pass = 0; pass < 3; ++pass) {
-                    k_idhist<<<g, SW_THREADS, 0, s>>>(n, lab, mat, id, bh, pr, pass);
-                    k_idselect<<<1, SW_ID_BINS, 0, s>>>(pr, pass);
-                }
-                k_apply<<<g, SW_THREADS, 0, s>>>(n, Q, x, y, z, lab, mat, id, bh, pr, S, multi ? P.nmat : 0);
-            }
-    }
-    return cudaGetLastError();
+    double alpha = P.alpha;
+    int K = P.K_labels, nmat = P.nmat;
+    void *args[] = {(void *)&n, (void *)&Q, (void *)&alpha, (void *)&K, (void *)&nmat, (void *)&x, (void *)&y,
+                    (void *)&z, (void *)&lab, (void *)&mat, (void *)&id, (void *)&bh, (void *)&S, (void *)&pairs,
+                    (void *)&err};
+    return cudaLaunchCooperativeKernel((const void *)k_swap_pass, dim3(grid), dim3(SW_THREADS), args, 0, s);
 }
 
 // Number of particles moved by the last pass (device pointer into the scratch).

@@ -59,7 +59,8 @@ class ExchangeStats(C.Structure):
                 ("garbage", C.c_int64), ("boundary", C.c_int64 * MAX_LABEL), ("boundary_total", C.c_int64),
                 ("exchange_fraction", C.c_double), ("record_bytes", C.c_int64),
                 ("bytes_hash_broadcast", C.c_int64), ("bytes_boundary_broadcast", C.c_int64),
-                ("bytes_swap", C.c_int64), ("swapped_last_pass", C.c_int64), ("swap_passes", C.c_int64)]
+                ("bytes_swap", C.c_int64), ("swapped_last_pass", C.c_int64), ("swap_passes", C.c_int64),
+                ("pairs_total", C.c_int64), ("kernel_launches", C.c_int64)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("pad", "boundary")}
@@ -226,14 +227,20 @@ class Solver:
             return int(self.exchange_stats()["boundary_total"])
         return self.n
 
-    def get(self, field: str, stream=None) -> np.ndarray:
-        """Copies one field to a new numpy array (host)."""
+    def get(self, field: str, stream=None, out: np.ndarray | None = None) -> np.ndarray:
+        """Copies one field to host memory: a new numpy array, or `out` (e.g. a pinned buffer)."""
         cnt = self._count(field)
-        out = np.empty(max(cnt, 1), FIELD_DTYPE[field])
-        check(self.L.gsph_get_field(self.h, FIELD[field], out.ctypes.data, 0, _stream_handle(stream)),
+        if out is None:
+            buf = np.empty(max(cnt, 1), FIELD_DTYPE[field])
+        else:
+            buf = out.reshape(-1)
+            assert buf.dtype == FIELD_DTYPE[field] and buf.size >= cnt and buf.flags.c_contiguous
+        check(self.L.gsph_get_field(self.h, FIELD[field], buf.ctypes.data, 0, _stream_handle(stream)),
               f"gsph_get_field({field})")
-        out = out[:cnt]
-        return out.reshape(self.n, NRATE) if field == "rates" else out
+        if out is not None:
+            return out
+        buf = buf[:cnt]
+        return buf.reshape(self.n, NRATE) if field == "rates" else buf
 
     def get_into(self, field: str, dst, stream=None) -> None:
         """Copies one field into a device tensor (torch, on the context's GPU)."""

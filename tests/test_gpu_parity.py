@@ -208,3 +208,16 @@ def test_swap_now_matches_oracle_pass():
             assert sol.exchange_stats()["swapped_last_pass"] == moved
         finally:
             sol.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(gsph.FP64, 1e-12), (gsph.FP32_SPLIT, 2e-5)])
+def test_dense_neighbourhoods_beyond_list_capacity(precision, tol):
+    # h = 1.6 dx: about 137 neighbours per interior particle, more than the per-particle list holds,
+    # so the remainder goes through the re-scan path; counts and state must still match
+    s = scenes.cube_impact(n_side=10, seed=9)
+    s.h = 1.6 * s.dx
+    lo = tuple(v - 4 * s.h for v in s.pos.min(axis=0))
+    s.grid_lo = lo
+    s.grid_dims = tuple(int(np.ceil((s.pos[:, a].max() + 4 * s.h - lo[a]) / (2 * s.h))) for a in range(3))
+    worst = _lockstep(s, precision, 2, tol)
+    assert max(worst.values()) <= tol

@@ -209,7 +209,8 @@ def test_radial_return_caps_von_mises_stress():
 def test_dt_closed_form():
     s, P, st = _lattice_state(n_side=4, jitter=0.01)
     c0 = math.sqrt((KB + 4.0 * GS / 3.0) / RHO0)
-    assert orc.dt(P, st) == pytest.approx(s.cfl * s.h / (c0 + 100.0), rel=1e-14)
+    # the signal speed is evaluated in FP32 (reading), so the time step carries ~1e-7 relative error
+    assert orc.dt(P, st) == pytest.approx(s.cfl * s.h / (c0 + 100.0), rel=1e-6)
 
 
 def test_free_flight_under_gravity_without_neighbours():
