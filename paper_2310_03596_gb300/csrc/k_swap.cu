@@ -92,6 +92,59 @@ __device__ __forceinline__ int balancing_hash(const Side &sd, double p0, double 
     return (int)k;
 }
 
+// Sum of a non-negative 33-bit value over the lanes of `peers` (lanes sharing one key), exact: the
+// low 16 and high 17 bits are reduced separately in 32-bit arithmetic (at most 32 lanes).
+__device__ __forceinline__ long long group_sum33(unsigned peers, long long v) {
+    const unsigned lo = __reduce_add_sync(peers, (unsigned)(v & 0xffff));
+    const unsigned hi = __reduce_add_sync(peers, (unsigned)(v >> 16));
+    return (long long)lo + ((long long)hi << 16);
+}
+
+// Adds (q0, q1, q2, 1) of every lane to sh[key] with one shared atomic per distinct key in the warp.
+// Lanes with valid = false contribute nothing (their key may be anything).
+__device__ __forceinline__ void warp_add_sums(long long (*sh)[4], int key, bool valid, long long q0, long long q1,
+                                              long long q2) {
+    const unsigned peers = __match_any_sync(kFullMask, valid ? key : -1);
+    const long long s0 = group_sum33(peers, valid ? q0 : 0), s1 = group_sum33(peers, valid ? q1 : 0);
+    const long long s2 = group_sum33(peers, valid ? q2 : 0);
+    if (valid && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) {
+        atomicAdd((unsigned long long *)&sh[key][0], (unsigned long long)s0);
+        atomicAdd((unsigned long long *)&sh[key][1], (unsigned long long)s1);
+        atomicAdd((unsigned long long *)&sh[key][2], (unsigned long long)s2);
+        atomicAdd((unsigned long long *)&sh[key][3], (unsigned long long)__popc(peers));
+    }
+}
+
+// In-place inclusive scan of a[0..nv) in shared memory by the whole block (nv <= 2 * SW_THREADS).
+__device__ void block_inclusive_scan(uint32_t *a, int nv) {
+    __shared__ uint32_t wt[SW_THREADS / 32];
+    const int t = threadIdx.x, l = t & 31, w = t >> 5;
+    const uint32_t x0 = 2 * t < nv ? a[2 * t] : 0u, x1 = 2 * t + 1 < nv ? a[2 * t + 1] : 0u;
+    const uint32_t s2 = x0 + x1;
+    uint32_t inc = s2;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFullMask, inc, o);
+        if (l >= o) inc += y;
+    }
+    if (l == 31) wt[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t v = l < SW_THREADS / 32 ? wt[l] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFullMask, v, o);
+            if (l >= o) v += y;
+        }
+        if (l < SW_THREADS / 32) wt[l] = v;
+    }
+    __syncthreads();
+    const uint32_t base = (w > 0 ? wt[w - 1] : 0u) + inc - s2;
+    if (2 * t < nv) a[2 * t] = base + x0;
+    if (2 * t + 1 < nv) a[2 * t + 1] = base + x0 + x1;
+    __syncthreads();
+}
+
 // Bounded grid barrier (generation counter). Returns false, with the timeout bit set, when the
 // other blocks do not arrive within the spin limit.
 __device__ bool grid_barrier(SwapScratch *S, unsigned nblocks, int *err) {
@@ -123,7 +176,7 @@ __device__ bool grid_barrier(SwapScratch *S, unsigned nblocks, int *err) {
     return ok_sh != 0;
 }
 
-__global__ void __launch_bounds__(SW_THREADS) k_swap_pass(int64_t n, QuantParams Q, double alpha, int K, int nmat,
+__global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantParams Q, double alpha, int K, int nmat,
                                                           const double *__restrict__ x, const double *__restrict__ y,
                                                           const double *__restrict__ z, uint8_t *__restrict__ lab,
                                                           const uint8_t *__restrict__ mat,
@@ -144,25 +197,23 @@ __global__ void __launch_bounds__(SW_THREADS) k_swap_pass(int64_t n, QuantParams
     const bool multi = nmat > 1;
     const int ntype = multi ? nmat : 1;
 
-    // ---- exact fixed-point sums per (label, type) and per label
+    // ---- exact fixed-point sums per (label, type) and per label (warp-aggregated shared atomics)
     for (int i = threadIdx.x; i < kMaxLabel * SW_NT * 4; i += SW_THREADS) (&shs[0][0][0])[i] = 0;
     __syncthreads();
-    for (int64_t i = g0; i < n; i += gstride) {
-        const int l = lab[i] & (kMaxLabel - 1);
-        const int t = multi ? (mat[i] < nmat ? mat[i] : 0) : -1;
-        const long long q0 = quantise(x[i], Q.lo[0], Q.hi[0], Q.sc[0]);
-        const long long q1 = quantise(y[i], Q.lo[1], Q.hi[1], Q.sc[1]);
-        const long long q2 = quantise(z[i], Q.lo[2], Q.hi[2], Q.sc[2]);
-        atomicAdd((unsigned long long *)&shs[l][kMaxMat][0], (unsigned long long)q0);
-        atomicAdd((unsigned long long *)&shs[l][kMaxMat][1], (unsigned long long)q1);
-        atomicAdd((unsigned long long *)&shs[l][kMaxMat][2], (unsigned long long)q2);
-        atomicAdd((unsigned long long *)&shs[l][kMaxMat][3], 1ull);
-        if (t >= 0) {
-            atomicAdd((unsigned long long *)&shs[l][t][0], (unsigned long long)q0);
-            atomicAdd((unsigned long long *)&shs[l][t][1], (unsigned long long)q1);
-            atomicAdd((unsigned long long *)&shs[l][t][2], (unsigned long long)q2);
-            atomicAdd((unsigned long long *)&shs[l][t][3], 1ull);
+    for (int64_t base = (int64_t)blockIdx.x * SW_THREADS; base < n; base += gstride) {
+        const int64_t i = base + threadIdx.x;
+        const bool v = i < n;
+        const int l = v ? (lab[i] & (kMaxLabel - 1)) : 0;
+        const int t = (v && multi) ? (mat[i] < nmat ? mat[i] : 0) : 0;
+        long long q0 = 0, q1 = 0, q2 = 0;
+        if (v) {
+            q0 = quantise(x[i], Q.lo[0], Q.hi[0], Q.sc[0]);
+            q1 = quantise(y[i], Q.lo[1], Q.hi[1], Q.sc[1]);
+            q2 = quantise(z[i], Q.lo[2], Q.hi[2], Q.sc[2]);
         }
+        long long(*flat)[4] = &shs[0][0];
+        warp_add_sums(flat, l * SW_NT + kMaxMat, v, q0, q1, q2);
+        if (multi) warp_add_sums(flat, l * SW_NT + t, v, q0, q1, q2);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < kMaxLabel * SW_NT; k += SW_THREADS) {
@@ -217,13 +268,21 @@ __global__ void __launch_bounds__(SW_THREADS) k_swap_pass(int64_t n, QuantParams
                 // -- balancing hashes and their histograms
                 if (act) {
                     const Side s0 = side_sh[0], s1 = side_sh[1];
-                    for (int64_t i = g0; i < n; i += gstride) {
-                        const uint8_t l = lab[i];
-                        if ((l != a && l != b) || (type >= 0 && mat[i] != type)) continue;
-                        const int sd = l == a ? 0 : 1;
-                        const int hv = balancing_hash(sd == 0 ? s0 : s1, x[i], y[i], z[i]);
-                        bh[i] = (uint16_t)hv;
-                        atomicAdd(&hs[sd][hv], 1u);
+                    for (int64_t base = (int64_t)blockIdx.x * SW_THREADS; base < n; base += gstride) {
+                        const int64_t i = base + threadIdx.x;
+                        int key = -1;
+                        if (i < n) {
+                            const uint8_t l = lab[i];
+                            if ((l == a || l == b) && (type < 0 || mat[i] == type)) {
+                                const int sd = l == a ? 0 : 1;
+                                const int hv = balancing_hash(sd == 0 ? s0 : s1, x[i], y[i], z[i]);
+                                bh[i] = (uint16_t)hv;
+                                if (hv > 0) key = sd * SW_BINS + hv;   // only positive hashes are counted
+                            }
+                        }
+                        const unsigned peers = __match_any_sync(kFullMask, key);
+                        if (key >= 0 && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
+                            atomicAdd(&(&hs[0][0])[key], (uint32_t)__popc(peers));
                     }
                     __syncthreads();
                     for (int k = threadIdx.x; k < 2 * SW_BINS; k += SW_THREADS) {
@@ -233,36 +292,31 @@ __global__ void __launch_bounds__(SW_THREADS) k_swap_pass(int64_t n, QuantParams
                 }
                 if (!grid_barrier(S, nb, err)) return;
                 if (!act) continue;
-                // -- n = min(#positive), threshold hash and the count to take from the threshold bin
-                for (int k = threadIdx.x; k < 2 * SW_BINS; k += SW_THREADS)
-                    (&hs[0][0])[k] = ((volatile uint32_t *)&pr->hist[0][0])[k];
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    unsigned long long pos[2];
-                    for (int sd = 0; sd < 2; ++sd) {
-                        unsigned long long c = 0;
-                        for (int hv = 1; hv < SW_BINS; ++hv) c += hs[sd][hv];
-                        pos[sd] = c;
-                    }
-                    const unsigned long long m = pos[0] < pos[1] ? pos[0] : pos[1];
-                    act_sh = m > 0;
-                    idsel_sh[0] = idsel_sh[1] = 0;
-                    for (int sd = 0; sd < 2 && m > 0; ++sd) {
-                        unsigned long long above = 0;
-                        int Tb = GSPH_BALANCE_HASH_MAX;
-                        for (; Tb >= 1; --Tb) {
-                            if (above + hs[sd][Tb] >= m) break;
-                            above += hs[sd][Tb];
-                        }
-                        T_sh[sd] = Tb;
-                        need_sh[sd] = (uint32_t)(m - above);
-                        idsel_sh[sd] = need_sh[sd] < hs[sd][Tb];
-                        idpre_sh[sd] = 0;
-                    }
-                    if (blockIdx.x == 0) pr->moved = 2 * m;
+                // -- n = min(#positive), threshold hash and the count to take from the threshold bin:
+                // cum[sd][r] = particles of side sd with hash >= 1000 - r (block scans, every block)
+                __shared__ uint32_t cum[2][SW_BINS - 1];
+                for (int k = threadIdx.x; k < 2 * (SW_BINS - 1); k += SW_THREADS) {
+                    const int sd = k / (SW_BINS - 1), r = k % (SW_BINS - 1);
+                    cum[sd][r] = ((volatile uint32_t *)&pr->hist[sd][0])[GSPH_BALANCE_HASH_MAX - r];
                 }
                 __syncthreads();
-                if (!act_sh) continue;    // the same decision in every block: no barrier is skipped unevenly
+                block_inclusive_scan(cum[0], SW_BINS - 1);
+                block_inclusive_scan(cum[1], SW_BINS - 1);
+                const uint32_t m = min(cum[0][SW_BINS - 2], cum[1][SW_BINS - 2]);
+                if (m == 0) continue;    // the same decision in every block: no barrier is skipped unevenly
+                for (int k = threadIdx.x; k < 2 * (SW_BINS - 1); k += SW_THREADS) {
+                    const int sd = k / (SW_BINS - 1), r = k % (SW_BINS - 1);
+                    const uint32_t above = r > 0 ? cum[sd][r - 1] : 0u;
+                    if (cum[sd][r] >= m && above < m) {
+                        const int Tb = GSPH_BALANCE_HASH_MAX - r;
+                        T_sh[sd] = Tb;
+                        need_sh[sd] = m - above;
+                        idsel_sh[sd] = (m - above) < (cum[sd][r] - above);
+                        idpre_sh[sd] = 0;
+                    }
+                }
+                if (blockIdx.x == 0 && threadIdx.x == 0) pr->moved = 2ull * m;
+                __syncthreads();
                 // -- radix select on persistent ids inside split threshold bins
                 if (idsel_sh[0] || idsel_sh[1]) {
                     for (int pass = 0; pass < 3; ++pass) {
@@ -287,18 +341,22 @@ __global__ void __launch_bounds__(SW_THREADS) k_swap_pass(int64_t n, QuantParams
                         for (int k = threadIdx.x; k < 2 * SW_ID_BINS; k += SW_THREADS)
                             (&ids[0][0])[k] = ((volatile uint32_t *)&pr->idh[pass][0][0])[k];
                         __syncthreads();
-                        if (threadIdx.x == 0) {
-                            for (int sd = 0; sd < 2; ++sd) {
-                                if (!idsel_sh[sd]) continue;
-                                uint32_t below = 0;
-                                int d = 0;
-                                for (; d < SW_ID_BINS - 1; ++d) {
-                                    if (below + ids[sd][d] >= need_sh[sd]) break;
-                                    below += ids[sd][d];
-                                }
-                                idpre_sh[sd] |= (uint32_t)d << shift;
-                                need_sh[sd] -= below;
+                        block_inclusive_scan(ids[0], SW_ID_BINS);
+                        block_inclusive_scan(ids[1], SW_ID_BINS);
+                        __shared__ uint32_t upd[2][2];
+                        for (int k = threadIdx.x; k < 2 * SW_ID_BINS; k += SW_THREADS) {
+                            const int sd = k / SW_ID_BINS, d = k % SW_ID_BINS;
+                            if (!idsel_sh[sd]) continue;
+                            const uint32_t below = d > 0 ? ids[sd][d - 1] : 0u;
+                            if (ids[sd][d] >= need_sh[sd] && below < need_sh[sd]) {
+                                upd[sd][0] = (uint32_t)d;
+                                upd[sd][1] = below;
                             }
+                        }
+                        __syncthreads();
+                        if (threadIdx.x < 2 && idsel_sh[threadIdx.x]) {
+                            idpre_sh[threadIdx.x] |= upd[threadIdx.x][0] << shift;
+                            need_sh[threadIdx.x] -= upd[threadIdx.x][1];
                         }
                         __syncthreads();
                     }
@@ -306,22 +364,27 @@ __global__ void __launch_bounds__(SW_THREADS) k_swap_pass(int64_t n, QuantParams
                 // -- label exchange and exact update of the fixed-point sums
                 if (threadIdx.x < 8) (&dsum[0][0])[threadIdx.x] = 0;
                 __syncthreads();
-                for (int64_t i = g0; i < n; i += gstride) {
-                    const uint8_t l = lab[i];
-                    if ((l != a && l != b) || (type >= 0 && mat[i] != type)) continue;
-                    const int sd = l == a ? 0 : 1;
-                    const int hv = bh[i];
-                    const bool take =
-                        hv > 0 && (hv > T_sh[sd] || (hv == T_sh[sd] && (!idsel_sh[sd] || id[i] <= idpre_sh[sd])));
-                    if (!take) continue;
-                    lab[i] = (uint8_t)(sd == 0 ? b : a);
-                    atomicAdd((unsigned long long *)&dsum[sd][0],
-                              (unsigned long long)quantise(x[i], Q.lo[0], Q.hi[0], Q.sc[0]));
-                    atomicAdd((unsigned long long *)&dsum[sd][1],
-                              (unsigned long long)quantise(y[i], Q.lo[1], Q.hi[1], Q.sc[1]));
-                    atomicAdd((unsigned long long *)&dsum[sd][2],
-                              (unsigned long long)quantise(z[i], Q.lo[2], Q.hi[2], Q.sc[2]));
-                    atomicAdd((unsigned long long *)&dsum[sd][3], 1ull);
+                for (int64_t base = (int64_t)blockIdx.x * SW_THREADS; base < n; base += gstride) {
+                    const int64_t i = base + threadIdx.x;
+                    int sd = -1;
+                    long long q0 = 0, q1 = 0, q2 = 0;
+                    if (i < n) {
+                        const uint8_t l = lab[i];
+                        if ((l == a || l == b) && (type < 0 || mat[i] == type)) {
+                            const int side = l == a ? 0 : 1;
+                            const int hv = bh[i];
+                            const bool take = hv > 0 && (hv > T_sh[side] ||
+                                                         (hv == T_sh[side] && (!idsel_sh[side] || id[i] <= idpre_sh[side])));
+                            if (take) {
+                                sd = side;
+                                lab[i] = (uint8_t)(side == 0 ? b : a);
+                                q0 = quantise(x[i], Q.lo[0], Q.hi[0], Q.sc[0]);
+                                q1 = quantise(y[i], Q.lo[1], Q.hi[1], Q.sc[1]);
+                                q2 = quantise(z[i], Q.lo[2], Q.hi[2], Q.sc[2]);
+                            }
+                        }
+                    }
+                    if (__any_sync(kFullMask, sd >= 0)) warp_add_sums(dsum, sd < 0 ? 0 : sd, sd >= 0, q0, q1, q2);
                 }
                 __syncthreads();
                 if (threadIdx.x < 2) {
