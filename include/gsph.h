@@ -209,6 +209,24 @@ size_t gsph_radix_sort_workspace(int64_t n, int32_t key_bits);
 gsph_status gsph_radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, int32_t key_bits,
                                   void *workspace, size_t workspace_bytes, void *stream);
 
+/* The same stable sort, for callers that cannot allocate device memory: for instance code that runs
+ * while another component owns every free byte of the GPU in its own pool, or code on a
+ * latency-critical stream that must not pay the device-wide synchronisation cudaMalloc/cudaFree can
+ * bring. The paper has no counterpart; this is a deployment convenience.
+ * The scratch is a fixed array inside the library: GSPH_SORT_NOALLOC_BYTES of device memory, held on
+ * every GPU that loads the library until the process exits. n must not exceed
+ * GSPH_SORT_NOALLOC_MAX_N; larger n returns GSPH_INVALID_ARG before any work. keys and vals are
+ * device pointers on the current device; the call allocates nothing and needs no workspace.
+ * The first call on a device looks up the array's device address (once per device, with that device
+ * current); make that first call before any stream capture. All calls share the one array and it
+ * keeps the last call's contents: calls that overlap on the GPU (two streams, two host threads)
+ * race, so serialise them. Errors: INVALID_ARG (null pointers, n out of range, key_bits not in
+ * 1..32), CUDA_ERROR. */
+#define GSPH_SORT_NOALLOC_MAX_N 1048576
+#define GSPH_SORT_NOALLOC_BYTES 8651776
+gsph_status gsph_radix_sort_pairs_noalloc(uint32_t *keys, uint32_t *vals, int64_t n, int32_t key_bits,
+                                          void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -7,6 +7,8 @@
 //                per-warp counters, cross-warp prefix), scatters keys and values.
 // The ranking follows tile order, so every pass is stable and the sort is stable overall.
 // Bytes per key per pass: 4 (hist) + 8 read + 8 written (scatter) + 2*4*256/4096 (counts).
+#include <mutex>
+
 #include "gsph_internal.cuh"
 
 namespace gsph {
@@ -238,6 +240,67 @@ extern "C" gsph_status gsph_radix_sort_pairs(uint32_t *keys, uint32_t *vals, int
     uint32_t *hist = (uint32_t *)p;
     p += align256(gsph::radix_hist_words(n) * 4);
     uint32_t *tot = (uint32_t *)p;
+    bool alt = false;
+    cudaError_t e = gsph::radix_sort_pairs(keys, vals, k1, v1, hist, tot, n, key_bits, s, &alt);
+    if (e == cudaSuccess && alt) {
+        e = cudaMemcpyAsync(keys, k1, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(vals, v1, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+    }
+    return e == cudaSuccess ? GSPH_OK : GSPH_CUDA_ERROR;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free variant of the stateless sort. The scratch lives in a fixed device array of this
+// library (held on every GPU that loads the library until the process exits), so the call needs no
+// cudaMalloc/cudaFree and no caller-provided workspace.
+// ---------------------------------------------------------------------------------------------
+namespace {
+constexpr int64_t kNoAllocMaxN = (int64_t)1 << 20;
+constexpr size_t kNoAllocKeyBytes = (size_t)kNoAllocMaxN * 4;
+constexpr size_t kNoAllocHistBytes = (size_t)gsph::RS_BINS * (size_t)(kNoAllocMaxN / gsph::RS_TILE) * 4;
+constexpr size_t kNoAllocBytes = 2 * kNoAllocKeyBytes + kNoAllocHistBytes + gsph::RS_BINS * 4;
+static_assert(kNoAllocKeyBytes % 256 == 0 && kNoAllocHistBytes % 256 == 0, "256-byte aligned sections");
+
+static __device__ __align__(256) unsigned char g_sort_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void *g_scratch_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_sort_scratch on the current device, looked up once per device. In host code
+// the array's name only stands for it; the address that kernels may use comes from the runtime.
+cudaError_t noalloc_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_sort_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+extern "C" gsph_status gsph_radix_sort_pairs_noalloc(uint32_t *keys, uint32_t *vals, int64_t n, int32_t key_bits,
+                                                     void *stream) {
+    if (n < 0 || n > kNoAllocMaxN || key_bits < 1 || key_bits > 32) return GSPH_INVALID_ARG;
+    if (n == 0) return GSPH_OK;
+    if (!keys || !vals) return GSPH_INVALID_ARG;
+    void *base = nullptr;
+    if (noalloc_scratch(&base) != cudaSuccess) return GSPH_CUDA_ERROR;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *p = (char *)base;
+    uint32_t *k1 = (uint32_t *)p;
+    uint32_t *v1 = (uint32_t *)(p + kNoAllocKeyBytes);
+    uint32_t *hist = (uint32_t *)(p + 2 * kNoAllocKeyBytes);
+    uint32_t *tot = (uint32_t *)(p + 2 * kNoAllocKeyBytes + kNoAllocHistBytes);
+    // every scratch word the sort reads is written earlier in the same call (per-tile histograms,
+    // their scans, the other key/value buffer), so nothing has to be cleared between calls
     bool alt = false;
     cudaError_t e = gsph::radix_sort_pairs(keys, vals, k1, v1, hist, tot, n, key_bits, s, &alt);
     if (e == cudaSuccess && alt) {

@@ -80,7 +80,8 @@ class Timings(C.Structure):
 EXPORTS = ["gsph_status_str", "gsph_create", "gsph_destroy", "gsph_set_particles", "gsph_put_field",
            "gsph_get_field", "gsph_step", "gsph_swap_now", "gsph_sync", "gsph_get_exchange_stats",
            "gsph_get_conserved", "gsph_get_dt", "gsph_get_sizes", "gsph_set_timing", "gsph_get_timings",
-           "gsph_radix_sort_workspace", "gsph_radix_sort_pairs"]
+           "gsph_radix_sort_workspace", "gsph_radix_sort_pairs", "gsph_radix_sort_pairs_noalloc"]
+SORT_NOALLOC_MAX_N = 1 << 20
 
 _lib = None
 _lock = threading.Lock()
@@ -116,6 +117,7 @@ def load(path: str = LIB_PATH):
         L.gsph_radix_sort_workspace.argtypes = [C.c_int64, C.c_int32]
         L.gsph_radix_sort_workspace.restype = C.c_size_t
         L.gsph_radix_sort_pairs.argtypes = [vp, vp, C.c_int64, C.c_int32, vp, C.c_size_t, vp]
+        L.gsph_radix_sort_pairs_noalloc.argtypes = [vp, vp, C.c_int64, C.c_int32, vp]
         _lib = L
         return L
 
@@ -306,3 +308,11 @@ def radix_sort_pairs(keys, vals, key_bits: int, stream=None) -> None:
     ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=keys.device)
     check(L.gsph_radix_sort_pairs(keys.data_ptr(), vals.data_ptr(), n, key_bits, ws.data_ptr(), ws_bytes,
                                   _stream_handle(stream)), "gsph_radix_sort_pairs")
+
+
+def radix_sort_pairs_noalloc(keys, vals, key_bits: int, stream=None) -> None:
+    """The same sort with no allocation at all (library-owned fixed scratch, n <= SORT_NOALLOC_MAX_N),
+    for callers that cannot allocate device memory. Calls that overlap on the GPU race."""
+    L = load()
+    check(L.gsph_radix_sort_pairs_noalloc(keys.data_ptr(), vals.data_ptr(), int(keys.numel()), key_bits,
+                                          _stream_handle(stream)), "gsph_radix_sort_pairs_noalloc")
