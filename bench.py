@@ -345,7 +345,7 @@ def main():
                  "ms_per_step": ms64 / args.fp64_steps,
                  "pair_interactions_per_s": world * (p1 - p0) / (ms64 * 1e-3),
                  "interact_ms": tm64["interact_ms"] / max(tm64["steps"], 1), "steps": args.fp64_steps},
-        "roofline": {"kernel": "k_interact (FP32 split)", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+        "roofline": {"kernel": "interaction phase: k_nbr_list + k_pair (FP32 split), one launch each per step", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                      "flops_per_launch": flops_per_launch, "launch_ms": it_ms,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sm_max_mhz, {peaks_kind})"},

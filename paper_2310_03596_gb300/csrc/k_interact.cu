@@ -167,7 +167,9 @@ template <> struct Acc<float> {
             s[k] += x;
         }
     }
-    __device__ __forceinline__ double get(int k) const { return k < 6 ? (double)s[k] - (double)c[k] : (double)s[k]; }
+    // the compensated sum s - c rounded once to FP32 keeps the compensation's benefit (one rounding
+    // of the final value instead of one per term) and widens with a single conversion
+    __device__ __forceinline__ double get(int k) const { return (double)(k < 6 ? s[k] - c[k] : s[k]); }
     __device__ __forceinline__ float getr(int k) const { return k < 6 ? s[k] - c[k] : s[k]; }
 };
 template <> struct Acc<double> {
@@ -243,7 +245,7 @@ __device__ __forceinline__ bool support_exact(const DevParams &P, const double *
 // Neighbour list (real neighbours). list[k * n + i], k < kmax; cnt[i] = number found (may exceed kmax).
 // ---------------------------------------------------------------------------------------------
 template <bool SPLIT>
-__global__ void __launch_bounds__(NL_THREADS) k_nbr_list(DevParams P, int64_t n, const uint32_t *__restrict__ skey,
+__global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t n, const uint32_t *__restrict__ skey,
                                                          const uint2 *__restrict__ cellr,
                                                          const typename Types<SPLIT>::Pos *__restrict__ pos,
                                                          const float *__restrict__ cxs, const double *__restrict__ xs,
@@ -251,8 +253,9 @@ __global__ void __launch_bounds__(NL_THREADS) k_nbr_list(DevParams P, int64_t n,
                                                          int kmax, uint32_t *__restrict__ list,
                                                          uint32_t *__restrict__ cnt_out) {
     using Pos = typename Types<SPLIT>::Pos;
+    // staged candidate: (x in the group frame, y, z relative to its bucket corner, bucket x as int bits)
+    // on the split path; (x, y, z, bucket x) in FP64 on the FP64 path
     __shared__ Pos stage[NL_THREADS];
-    __shared__ float stage_cx[NL_THREADS];
     const int tid = threadIdx.x, lane = tid & 31, wbase = tid & ~31;
     const int64_t s = (int64_t)blockIdx.x * NL_THREADS + tid;
     const bool valid = s < n;
@@ -268,7 +271,10 @@ __global__ void __launch_bounds__(NL_THREADS) k_nbr_list(DevParams P, int64_t n,
         if (!SPLIT) { X = (double)p.x; Y = (double)p.y; Z = (double)p.z; }
     }
     const float fcell = P.f_cell;
+    const uint32_t self = (uint32_t)s;
     uint32_t cnt = 0;
+    uint32_t *out = list + (size_t)s;          // next free list slot of this particle (column-major)
+    const size_t colstep = (size_t)n;
     bool need = active;
     while (true) {
         const unsigned todo = __ballot_sync(kFullMask, need);
@@ -279,7 +285,6 @@ __global__ void __launch_bounds__(NL_THREADS) k_nbr_list(DevParams P, int64_t n,
         // a group shares the bucket row and lies within 4 buckets of the leader in x, so staged and own
         // x in the group frame stay below 12h and their FP32 rounding stays well inside the band
         const bool ing = need && cy == gby && cz == gbz && abs(cx - gbx) <= 4;
-        const float bxf = (float)cx;
         const float oxg = ox + (float)(cx - gbx) * fcell;   // own x in the group frame
         for (int row = 0; row < 9; ++row) {
             const int dcy = row % 3 - 1, dcz = row / 3 - 1;
@@ -290,42 +295,76 @@ __global__ void __launch_bounds__(NL_THREADS) k_nbr_list(DevParams P, int64_t n,
             const uint32_t lo = __reduce_min_sync(kFullMask, rs);
             const uint32_t hi = __reduce_max_sync(kFullMask, re);
             const float oyr = oy - (float)dcy * fcell, ozr = oz - (float)dcz * fcell;
+            // list entry = slot | (dcx + 1) << 26 | (dcy + 1) << 28 | (dcz + 1) << 30; the dcx field is
+            // (cx_j - cx + 1) & 3, formed from the staged bucket x by one subtraction
             const uint32_t code_yz = (uint32_t)(dcy + 1) << 28 | (uint32_t)(dcz + 1) << 30;
+            const int cxm1 = cx - 1;
             for (uint32_t b = lo; b < hi; b += 32) {
                 const uint32_t jl = b + lane;
-                if (jl < hi) {
-                    Pos q = pos[jl];
-                    const float cxj = cxs[jl];
-                    if (SPLIT) q.x = (float)q.x + (cxj - (float)gbx) * fcell;
+                {
+                    Pos q;
+                    if (jl < hi) {
+                        q = pos[jl];
+                        const float cxj = cxs[jl];
+                        if (SPLIT) {
+                            q.x = (float)q.x + (cxj - (float)gbx) * fcell;
+                            q.w = __int_as_float((int)cxj);
+                        } else {
+                            q.w = (double)cxj;
+                        }
+                    } else {
+                        // past the end of the range: a far-away sentinel that no test accepts
+                        q.x = 1.0e30f; q.y = 1.0e30f; q.z = 1.0e30f;
+                        q.w = SPLIT ? __int_as_float(-0x40000000) : -1.0e9;
+                    }
                     stage[tid] = q;
-                    stage_cx[tid] = cxj;
                 }
                 __syncwarp();
-                const int m = (int)min(32u, hi - b);
                 if (ing) {
-                    for (int t = 0; t < m; ++t) {
-                        const uint32_t j = b + (uint32_t)t;
-                        const float dcxf = stage_cx[wbase + t] - bxf;
+                    // straight-line tests build a hit mask and a band mask over the staged batch;
+                    // stores and the rare FP64 decisions follow per set bit. On the split path a
+                    // candidate outside the own 3-bucket window is more than 2h away, so its FP32 r^2
+                    // cannot fall below the band and the fast test needs no window check.
+                    uint32_t hitm = 0u, bandm = 0u;
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) {
                         const Pos pj = stage[wbase + t];
-                        const bool ok = fabsf(dcxf) < 1.5f && (int64_t)j != s;   // own window, not self
-                        bool hit;
                         if (SPLIT) {
                             const float ex = (float)pj.x - oxg;
                             const float ey = (float)pj.y - oyr;
                             const float ez = (float)pj.z - ozr;
                             const float r2 = ex * ex + ey * ey + ez * ez;
-                            hit = ok && r2 < P.f_R2lo;
-                            if (ok && !hit && r2 < P.f_R2hi)   // rounding band: exactly rounded FP64 decides
-                                hit = support_exact(P, xs, ys, zs, j, xs[s], ys[s], zs[s], -1, 0.0);
+                            if (r2 < P.f_R2lo) hitm |= 1u << t;
+                            if (r2 < P.f_R2hi) bandm |= 1u << t;
                         } else {
-                            hit = ok && dist2_rn(__dsub_rn((double)pj.x, X), __dsub_rn((double)pj.y, Y),
-                                                 __dsub_rn((double)pj.z, Z)) < P.R2;
+                            const int cxj = (int)pj.w;
+                            if ((uint32_t)(cxj - cxm1) <= 2u &&
+                                dist2_rn(__dsub_rn((double)pj.x, X), __dsub_rn((double)pj.y, Y),
+                                         __dsub_rn((double)pj.z, Z)) < P.R2)
+                                hitm |= 1u << t;
                         }
-                        if (hit) {
-                            if ((int)cnt < kmax)
-                                list[(size_t)cnt * (size_t)n + (size_t)s] = j | (uint32_t)(int)(dcxf + 1.0f) << 26 | code_yz;
-                            ++cnt;
-                        }
+                    }
+                    bandm &= ~hitm;
+                    if (self - b < 32u) {   // never its own neighbour
+                        hitm &= ~(1u << (self - b));
+                        bandm &= ~(1u << (self - b));
+                    }
+                    while (bandm) {         // rounding band: own window, then exactly rounded FP64 decides
+                        const int t = __ffs(bandm) - 1;
+                        bandm &= bandm - 1;
+                        const int cxj = __float_as_int((float)stage[wbase + t].w);
+                        if ((uint32_t)(cxj - cxm1) <= 2u &&
+                            support_exact(P, xs, ys, zs, b + (uint32_t)t, xs[s], ys[s], zs[s], -1, 0.0))
+                            hitm |= 1u << t;
+                    }
+                    while (hitm) {          // in stage order, i.e. ascending slot
+                        const int t = __ffs(hitm) - 1;
+                        hitm &= hitm - 1;
+                        const Pos pj = stage[wbase + t];
+                        const int cxj = SPLIT ? __float_as_int((float)pj.w) : (int)pj.w;
+                        if (cnt < (uint32_t)kmax) *out = (b + (uint32_t)t) | (uint32_t)(cxj - cxm1) << 26 | code_yz;
+                        out += colstep;
+                        ++cnt;
                     }
                 }
                 __syncwarp();
@@ -398,21 +437,26 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
         accumulate<R>(acc, o, iL ? R(-1) : R(1), me, oth);
     };
 
-    // ---- listed real neighbours, all lanes in lockstep, next record prefetched
+    // ---- listed real neighbours, all lanes in lockstep; the list entry two ahead and the record one
+    // ahead are in flight while the current pair is evaluated
     {
         const int mc = __reduce_max_sync(kFullMask, nl);
-        uint32_t en = nl > 0 ? list[(size_t)s] : 0u;
-        Pos pn = pos[en & IT_JMASK];
-        Rec rn = rec[en & IT_JMASK];
+        const uint32_t *lp = list + (size_t)s;
+        const size_t colstep = (size_t)n;
+        uint32_t e1 = nl > 0 ? lp[0] : 0u;
+        uint32_t e2 = nl > 1 ? lp[colstep] : 0u;
+        Pos pn = pos[e1 & IT_JMASK];
+        Rec rn = rec[e1 & IT_JMASK];
         for (int k = 0; k < mc; ++k) {
-            const uint32_t e = en;
+            const uint32_t e = e1;
             const Pos pj = pn;
             const Rec rj = rn;
+            e1 = e2;
             if (k + 1 < nl) {
-                en = list[(size_t)(k + 1) * (size_t)n + (size_t)s];
-                pn = pos[en & IT_JMASK];
-                rn = rec[en & IT_JMASK];
+                pn = pos[e1 & IT_JMASK];
+                rn = rec[e1 & IT_JMASK];
             }
+            if (k + 2 < nl) e2 = lp[(size_t)(k + 2) * colstep];
             if (k < nl) real_pair(e, pj, rj);
         }
     }
