@@ -326,16 +326,28 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                     // candidate outside the own 3-bucket window is more than 2h away, so its FP32 r^2
                     // cannot fall below the band and the fast test needs no window check.
                     uint32_t hitm = 0u, bandm = 0u;
+                    if (SPLIT) {
+                        // the sign of r^2 - R2lo (resp. R2hi) is shifted into the masks, candidate t
+                        // ending at bit 31 - t; one reversal at the end restores bit t
+                        const float band_w = P.f_R2lo - P.f_R2hi;
+#pragma unroll
+                        for (int t = 0; t < 32; ++t) {
+                            const Pos pj = stage[wbase + t];
+                            const float ex = (float)pj.x - oxg;
+                            const float ey = (float)pj.y - oyr;
+                            const float ez = (float)pj.z - ozr;
+                            const float dlo = fmaf(ex, ex, fmaf(ey, ey, fmaf(ez, ez, -P.f_R2lo)));
+                            const float dhi = dlo + band_w;
+                            hitm = __funnelshift_l(__float_as_uint(dlo), hitm, 1);
+                            bandm = __funnelshift_l(__float_as_uint(dhi), bandm, 1);
+                        }
+                        hitm = __brev(hitm);
+                        bandm = __brev(bandm);
+                    }
 #pragma unroll
                     for (int t = 0; t < 32; ++t) {
                         const Pos pj = stage[wbase + t];
                         if (SPLIT) {
-                            const float ex = (float)pj.x - oxg;
-                            const float ey = (float)pj.y - oyr;
-                            const float ez = (float)pj.z - ozr;
-                            const float r2 = ex * ex + ey * ey + ez * ez;
-                            if (r2 < P.f_R2lo) hitm |= 1u << t;
-                            if (r2 < P.f_R2hi) bandm |= 1u << t;
                         } else {
                             const int cxj = (int)pj.w;
                             if ((uint32_t)(cxj - cxm1) <= 2u &&
