@@ -200,6 +200,23 @@ gsph_status gsph_get_sizes(gsph_ctx *ctx, int64_t *n, int64_t *ncell);
 gsph_status gsph_set_timing(gsph_ctx *ctx, int32_t max_steps);
 gsph_status gsph_get_timings(gsph_ctx *ctx, gsph_timings *out);
 
+/* Overrides the time step of the next gsph_step (the one after is again the CFL step). Used to replay
+ * a recorded dt schedule, e.g. for finite differences with the schedule frozen. dt > 0. */
+gsph_status gsph_set_dt(gsph_ctx *ctx, double dt, void *stream);
+
+/* One reverse-mode step of the interaction loop and integration (Sec. II steps f-g), FP64, with the
+ * neighbour set of the current state and the time step dt held fixed: the transpose of the Jacobian
+ * of the step y_{n+1} = Step(y_n) at the current state y_n. Needs a context created with
+ * precision GSPH_FP64 and diagnostics = 1 (the step's FP64 rates are recomputed internally).
+ * lam_next: device, 15 x n doubles, field-major (field f of slot s at f*n + s, fields in gsph_field
+ * order X..SYZ), dJ/dy_{n+1} in the slot order y_{n+1} has (the hash order of this step, as after
+ * gsph_step). lam_prev: device, same layout, receives dJ/dy_n in the current slot order.
+ * grad: host, receives this step's direct contributions to dJ/dY and dJ/dG of material 0.
+ * Does not advance the state. Errors: INVALID_ARG (null pointers, dt <= 0, wrong context kind),
+ * NOT_READY, OOM, CUDA_ERROR. */
+gsph_status gsph_adjoint_step(gsph_ctx *ctx, const double *lam_next, double *lam_prev, double dt,
+                              double grad[2], void *stream);
+
 /* Stateless radix sort (Sec. I "radix sort" of the bucket hashes): stable ascending sort of n
  * (key, value) uint32 pairs in device memory by the low key_bits bits of the key (1..32), in
  * place. workspace: device scratch of at least gsph_radix_sort_workspace(n, key_bits) bytes,

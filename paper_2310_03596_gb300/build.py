@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgsph.so")
-SOURCES = ["k_sort.cu", "k_reorder_comm.cu", "k_interact.cu", "k_swap.cu", "gsph_api.cu"]
+SOURCES = ["k_sort.cu", "k_reorder_comm.cu", "k_interact.cu", "k_swap.cu", "k_adjoint.cu", "gsph_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-diag-suppress", "177"]

@@ -44,6 +44,13 @@ cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const double *x, con
                              int *err, int grid, cudaStream_t s);
 int swap_grid_blocks();
 unsigned long long *swap_moved_ptr(void *scratch);
+// k_adjoint.cu
+size_t adjoint_scratch_doubles(int64_t n);
+cudaError_t launch_adjoint(const DevParams &P, int64_t n, const uint32_t *skey, const uint2 *cellr, const void *pos,
+                           const void *rec, const double *xs, const double *ys, const double *zs, int kmax,
+                           const uint32_t *list, const uint32_t *cnt, const uint32_t *perm, const State &A,
+                           const uint8_t *mat_s, const double *rates, double dt, const double *lam_next,
+                           double *lam_prev, double *scratch, double *grad_out, cudaStream_t s);
 }  // namespace gsph
 
 using namespace gsph;
@@ -88,6 +95,8 @@ struct gsph_ctx {
     void *swap_scratch = nullptr;
     uint16_t *bh = nullptr;
     double *cons_part = nullptr, *cons_out = nullptr;
+    double *adj_scratch = nullptr;   // allocated on the first adjoint step
+    size_t adj_scratch_n = 0;
     int swap_grid = 0;
     // statistics
     int64_t swap_passes = 0;
@@ -106,6 +115,8 @@ struct gsph_ctx {
 static void free_buffers(gsph_ctx *c) {
     for (void *p : c->allocs) cudaFree(p);
     c->allocs.clear();
+    c->adj_scratch = nullptr;
+    c->adj_scratch_n = 0;
     c->A = State{};
     c->B = State{};
     c->n = 0;
@@ -309,6 +320,28 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     c->B = t;
     ++c->step;
     c->have_step = true;
+    return GSPH_OK;
+}
+
+// Hash, sort, reorder, neighbour lists and the step's FP64 rates of the current state, without
+// advancing it (the integration result goes to the scratch state B).
+static gsph_status enqueue_forward_pieces(gsph_ctx *c, cudaStream_t s) {
+    const DevParams &P = c->P;
+    const int64_t n = c->n;
+    GSPH_CK(cudaMemsetAsync(c->garbage, 0, sizeof(unsigned long long), s));
+    GSPH_CK(launch_hash(P, n, c->A.f[FX], c->A.f[FY], c->A.f[FZ], c->key0, c->val0, c->garbage, s));
+    bool alt = false;
+    GSPH_CK(radix_sort_pairs(c->key0, c->val0, c->key1, c->val1, c->hist, c->tot, n, key_bits(P.ncell), s, &alt));
+    c->skey = alt ? c->key1 : c->key0;
+    c->perm = alt ? c->val1 : c->val0;
+    GSPH_CK(cudaMemsetAsync(c->cellr, 0, (size_t)P.ncell * sizeof(uint2), s));
+    GSPH_CK(launch_reorder(c->split, P, n, c->skey, c->perm, c->A, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s,
+                           c->cellr, c->cxs, c->pos, c->rec, c->err, s));
+    GSPH_CK(launch_interact(c->split, true, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs, c->ys, c->zs,
+                            kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, c->lab_s, c->mat_s, c->id_s, c->dt,
+                            c->sig, c->pairs, c->nreal, c->nimage, c->rates, s));
+    c->launches += 4 + 3 * ((key_bits(P.ncell) + 7) / 8);
+    c->dt_dirty = true;   // the signal-speed word now holds the scratch state's maximum
     return GSPH_OK;
 }
 
@@ -573,6 +606,49 @@ gsph_status gsph_get_dt(gsph_ctx *c, void *stream, double *dt) {
     GSPH_CK(cudaMemcpyAsync(dt, c->dt, sizeof(double), cudaMemcpyDeviceToHost, s));
     GSPH_CK(cudaStreamSynchronize(s));
     return GSPH_OK;
+}
+
+gsph_status gsph_set_dt(gsph_ctx *c, double dt, void *stream) {
+    if (!c || !(dt > 0.0)) return GSPH_INVALID_ARG;
+    if (c->n == 0) return GSPH_NOT_READY;
+    GSPH_CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    GSPH_CK(cudaMemcpyAsync(c->dt, &dt, sizeof(double), cudaMemcpyHostToDevice, s));
+    GSPH_CK(cudaMemsetAsync(c->sig, 0, sizeof(unsigned int), s));
+    GSPH_CK(cudaStreamSynchronize(s));
+    c->dt_dirty = false;
+    return GSPH_OK;
+}
+
+gsph_status gsph_adjoint_step(gsph_ctx *c, const double *lam_next, double *lam_prev, double dt, double grad[2],
+                              void *stream) {
+    if (!c || !lam_next || !lam_prev || !grad || !(dt > 0.0)) return GSPH_INVALID_ARG;
+    if (c->split || !c->cfg.diagnostics) return GSPH_INVALID_ARG;
+    if (c->n == 0) return GSPH_NOT_READY;
+    GSPH_CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t need = adjoint_scratch_doubles(c->n);
+    if (c->adj_scratch_n < need) {
+        double *p = nullptr;
+        cudaError_t e = dalloc(c, &p, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? GSPH_OOM : GSPH_CUDA_ERROR;
+        }
+        c->adj_scratch = p;
+        c->adj_scratch_n = need;
+    }
+    GSPH_CK(cudaMemcpyAsync(c->dt, &dt, sizeof(double), cudaMemcpyHostToDevice, s));
+    gsph_status st = enqueue_forward_pieces(c, s);
+    if (st != GSPH_OK) return st;
+    double *gdev = c->adj_scratch + need - 2;
+    GSPH_CK(launch_adjoint(c->P, c->n, c->skey, c->cellr, c->pos, c->rec, c->xs, c->ys, c->zs, kNbrMax, c->nbr,
+                           c->nbr_cnt, c->perm, c->A, c->mat_s, c->rates, dt, lam_next, lam_prev, c->adj_scratch,
+                           gdev, s));
+    c->launches += 3;
+    GSPH_CK(cudaMemcpyAsync(grad, gdev, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GSPH_CK(cudaStreamSynchronize(s));
+    return read_err(c, s);
 }
 
 gsph_status gsph_get_sizes(gsph_ctx *c, int64_t *n, int64_t *ncell) {

@@ -80,7 +80,8 @@ class Timings(C.Structure):
 EXPORTS = ["gsph_status_str", "gsph_create", "gsph_destroy", "gsph_set_particles", "gsph_put_field",
            "gsph_get_field", "gsph_step", "gsph_swap_now", "gsph_sync", "gsph_get_exchange_stats",
            "gsph_get_conserved", "gsph_get_dt", "gsph_get_sizes", "gsph_set_timing", "gsph_get_timings",
-           "gsph_radix_sort_workspace", "gsph_radix_sort_pairs", "gsph_radix_sort_pairs_noalloc"]
+           "gsph_radix_sort_workspace", "gsph_radix_sort_pairs", "gsph_radix_sort_pairs_noalloc",
+           "gsph_set_dt", "gsph_adjoint_step"]
 SORT_NOALLOC_MAX_N = 1 << 20
 
 _lib = None
@@ -118,6 +119,8 @@ def load(path: str = LIB_PATH):
         L.gsph_radix_sort_workspace.restype = C.c_size_t
         L.gsph_radix_sort_pairs.argtypes = [vp, vp, C.c_int64, C.c_int32, vp, C.c_size_t, vp]
         L.gsph_radix_sort_pairs_noalloc.argtypes = [vp, vp, C.c_int64, C.c_int32, vp]
+        L.gsph_set_dt.argtypes = [vp, C.c_double, vp]
+        L.gsph_adjoint_step.argtypes = [vp, vp, vp, C.c_double, P(C.c_double), vp]
         _lib = L
         return L
 
@@ -288,6 +291,19 @@ class Solver:
         n, c = C.c_int64(), C.c_int64()
         check(self.L.gsph_get_sizes(self.h, C.byref(n), C.byref(c)), "gsph_get_sizes")
         return n.value, c.value
+
+    def set_dt(self, dt: float, stream=None) -> None:
+        """Time step of the next step (replay of a recorded schedule)."""
+        check(self.L.gsph_set_dt(self.h, float(dt), _stream_handle(stream)), "gsph_set_dt")
+
+    def adjoint_step(self, lam_next, lam_prev, dt: float, stream=None):
+        """Reverse-mode step at the current state (FP64 context with diagnostics): lam_prev = dJ/dy_n
+        from lam_next = dJ/dy_{n+1} (device tensors, 15 x n float64, field-major). Returns the step's
+        direct (dJ/dY, dJ/dG) contributions."""
+        g = (C.c_double * 2)()
+        check(self.L.gsph_adjoint_step(self.h, lam_next.data_ptr(), lam_prev.data_ptr(), float(dt), g,
+                                       _stream_handle(stream)), "gsph_adjoint_step")
+        return g[0], g[1]
 
     def set_timing(self, max_steps: int) -> None:
         check(self.L.gsph_set_timing(self.h, int(max_steps)), "gsph_set_timing")
