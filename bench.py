@@ -127,6 +127,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def reduce_max(x: float, dist, device=None) -> float:
+    """Maximum of x over the ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, seconds_max: float) -> float:
+    """Whole-job throughput of independent replicas: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 def workload_config(n: int, K: int, swap_period: int, world: int) -> dict:
     return {"workload": "taylor_bar: Al rod r 5 mm x 40 mm, dx 0.125 mm, 200 m/s onto a rigid wall",
             "particles": n, "labels": K, "swap_period": swap_period, "precision": "fp32-split",
@@ -252,19 +267,15 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop() if rank == 0 else None
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(e0.elapsed_time(e1), dist, device="cuda")
     sol.sync(stream)
     st1 = sol.exchange_stats(stream)
     tm = sol.timings()
     pairs = st1["pairs_total"] - st0["pairs_total"]
     launches = st1["kernel_launches"] - st0["kernel_launches"]
     sec = ms * 1e-3
-    value = world * n * args.steps / sec
-    pair_rate = world * pairs / sec
+    value = job_rate(world, n * args.steps, sec)
+    pair_rate = job_rate(world, pairs, sec)
 
     # FP64 path on the same workload, fewer steps (its pair math runs on the FP64 units)
     sol64 = gsph.Solver.from_scene(s, precision=gsph.FP64, device=local, stream=stream)
@@ -298,11 +309,7 @@ def main():
     for k, f in enumerate(gsph.FIELDS[:15]):
         sol.get(f, stream, out=outs[k])
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t
-    if dist is not None:
-        t2 = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t2, op=dist.ReduceOp.MAX)
-        e2e_s = float(t2.item())
+    e2e_s = reduce_max(time.perf_counter() - t, dist, device="cuda")
     h2d = n * (24 + 24 + 8 + 1 + 1)
     d2h = n * 15 * 8
 
