@@ -32,7 +32,7 @@ cudaError_t launch_conserved(int64_t n, const State &A, double *part, double *ou
 // k_interact.cu
 cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n, const uint32_t *skey,
                             const uint2 *cellr, const void *pos, const void *rec, const float *cxs,
-                            const double *xs, const double *ys, const double *zs, int kmax, uint32_t *list,
+                            const double *xs, const double *ys, const double *zs, int kmax, uint2 *list,
                             uint32_t *cnt, const uint32_t *perm, const State &A, const State &B,
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
                             unsigned int *sig, unsigned long long *pairs, int32_t *nreal, int32_t *nimage,
@@ -48,7 +48,7 @@ unsigned long long *swap_moved_ptr(void *scratch);
 size_t adjoint_scratch_doubles(int64_t n);
 cudaError_t launch_adjoint(const DevParams &P, int64_t n, const uint32_t *skey, const uint2 *cellr, const void *pos,
                            const void *rec, const double *xs, const double *ys, const double *zs, int kmax,
-                           const uint32_t *list, const uint32_t *cnt, const uint32_t *perm, const State &A,
+                           const uint2 *list, const uint32_t *cnt, const uint32_t *perm, const State &A,
                            const uint8_t *mat_s, const double *rates, double dt, const double *lam_next,
                            double *lam_prev, double *scratch, double *grad_out, cudaStream_t s);
 }  // namespace gsph
@@ -57,9 +57,10 @@ using namespace gsph;
 
 enum { PH_START = 0, PH_SORT, PH_REORDER, PH_SWAP, PH_COMM, PH_INTERACT, PH_COUNT };
 
-// Neighbour-list capacity per particle (an interior particle of the lattice has 80 real neighbours;
-// particles with more finish the rest by re-scanning, so results do not depend on it).
-constexpr int kNbrMax = 96;
+// Neighbour-list capacity per particle, in entries of one 32-candidate batch each (an interior
+// particle of the lattice has 80 real neighbours in about 20 batches; particles with more entries
+// finish the rest by re-scanning, so results do not depend on it).
+constexpr int kNbrMax = 40;
 
 struct gsph_ctx {
     gsph_config cfg;
@@ -78,7 +79,8 @@ struct gsph_ctx {
     uint32_t *mask = nullptr;
     double *xs = nullptr, *ys = nullptr, *zs = nullptr;
     float *cxs = nullptr;
-    uint32_t *nbr = nullptr, *nbr_cnt = nullptr;   // neighbour lists (kNbrMax x n, column-major), counts
+    uint2 *nbr = nullptr;                         // neighbour lists (kNbrMax x n entries, column-major)
+    uint32_t *nbr_cnt = nullptr;                  // entries per particle
     uint8_t *lab_s = nullptr, *mat_s = nullptr;
     uint32_t *id_s = nullptr;
     void *pos = nullptr, *rec = nullptr;

@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(128) k_adj_pair(DevParams P, int64_t n, const 
                                                   const uint2 *__restrict__ cellr, const D4 *__restrict__ pos,
                                                   const RecD *__restrict__ rec, const double *__restrict__ xs,
                                                   const double *__restrict__ ys, const double *__restrict__ zs,
-                                                  int kmax, const uint32_t *__restrict__ list,
+                                                  int kmax, const uint2 *__restrict__ list,
                                                   const uint32_t *__restrict__ cnt_in,
                                                   const uint32_t *__restrict__ perm,
                                                   const uint8_t *__restrict__ mat_s, const double *__restrict__ mu,
@@ -514,9 +514,14 @@ __global__ void __launch_bounds__(128) k_adj_pair(DevParams P, int64_t n, const 
                 add_bar(bk, kL ? bL : bR);
                 for (int c = 0; c < 3; ++c) xb[c] += kL ? -db[c] : db[c];
             };
+            // listed neighbours: the set bits of each entry's mask, slots base + t in ascending order
             const uint32_t cnt = cnt_in[s];
-            const int nl = (int)min(cnt, (uint32_t)kmax);
-            for (int k = 0; k < nl; ++k) real_pair(list[(size_t)k * n + s] & ADJ_JMASK);
+            const int ne = (int)min(cnt, (uint32_t)kmax);
+            uint32_t nlist = 0;
+            for (int k = 0; k < ne; ++k) {
+                const uint2 e = list[(size_t)k * n + s];
+                for (uint32_t m = e.x; m; m &= m - 1u, ++nlist) real_pair((e.y & ADJ_JMASK) + (uint32_t)(__ffs(m) - 1));
+            }
             // beyond the list capacity, and the wall images: re-scan around the own / mirrored point
             int cx, cy, cz;
             decode_cell(P, key, cx, cy, cz);
@@ -556,7 +561,7 @@ __global__ void __launch_bounds__(128) k_adj_pair(DevParams P, int64_t n, const 
                         if (wax == 2) qz = __dsub_rn(two_w, qz);
                         if (!(dist2_rn(__dsub_rn(qx, X), __dsub_rn(qy, Y), __dsub_rn(qz, Z)) < P.R2)) continue;
                         if (src == 0) {
-                            if (seen++ < (uint32_t)kmax) continue;   // already in the list
+                            if (seen++ < nlist) continue;   // already in the list
                             real_pair(j);
                             continue;
                         }
@@ -676,7 +681,7 @@ size_t adjoint_scratch_doubles(int64_t n) {
 // and FP64 rates - must already be computed for this step). scratch: adjoint_scratch_doubles(n).
 cudaError_t launch_adjoint(const DevParams &P, int64_t n, const uint32_t *skey, const uint2 *cellr, const void *pos,
                            const void *rec, const double *xs, const double *ys, const double *zs, int kmax,
-                           const uint32_t *list, const uint32_t *cnt, const uint32_t *perm, const State &A,
+                           const uint2 *list, const uint32_t *cnt, const uint32_t *perm, const State &A,
                            const uint8_t *mat_s, const double *rates, double dt, const double *lam_next,
                            double *lam_prev, double *scratch, double *grad_out, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;

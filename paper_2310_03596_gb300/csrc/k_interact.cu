@@ -5,11 +5,13 @@
 //   which share most of their 27-bucket neighbourhoods. The neighbourhood is visited as 9 rows of 3
 //   buckets that are contiguous in hash order. The warp streams the union of its lanes' candidate
 //   ranges through shared memory in batches of 32 records (x shifted into a frame common to the warp),
-//   every lane tests each staged candidate against its own 3-bucket window with straight-line code,
-//   and appends the in-support ones to a column-major list in global memory (entry = slot | bucket
-//   offset). Light on registers, so the candidate stream runs at full occupancy.
-// k_pair: one lane per particle walks its list (the next neighbour's record requested while the
-//   current pair is evaluated): pair fluxes, per-particle sums, then the wall images (mirror planes,
+//   every lane tests each staged candidate against its own 3-bucket window with straight-line code
+//   into a 32-bit hit mask, and appends one entry per batch with any hit to a column-major list in
+//   global memory (entry = hit mask, batch base slot | row offset). Light on registers, so the
+//   candidate stream runs at full occupancy; no per-neighbour bookkeeping.
+// k_pair: one lane per particle walks the set bits of its entries in ascending slot order (the next
+//   neighbour's record requested while the current pair is evaluated): pair fluxes, per-particle
+//   sums, then the wall images (mirror planes,
 //   searched around the mirrored point; only particles near a wall find any), then the integration.
 //   A particle with more neighbours than the list holds finishes the rest by re-scanning its
 //   buckets in the same order, so results never depend on the list capacity.
@@ -33,7 +35,7 @@ namespace gsph {
 
 constexpr int NL_THREADS = 256;            // neighbour-list kernel
 constexpr int PK_THREADS = 128;            // pair kernel
-constexpr uint32_t IT_JMASK = (1u << 26) - 1;   // list entry: slot (26 bits) | bucket offset (6 bits)
+constexpr uint32_t IT_JMASK = (1u << 26) - 1;   // list entry .y: batch base slot (26 bits) | row offset (4 bits)
 
 template <class R> struct PIn { R vx, vy, vz, rho, p, Z, E, sxx, syy, szz, sxy, sxz, syz, w; };
 
@@ -242,7 +244,9 @@ __device__ __forceinline__ bool support_exact(const DevParams &P, const double *
 }
 
 // ---------------------------------------------------------------------------------------------
-// Neighbour list (real neighbours). list[k * n + i], k < kmax; cnt[i] = number found (may exceed kmax).
+// Neighbour list (real neighbours). list[k * n + i], k < kmax: (mask, base | (dcy + 1) << 26 | (dcz + 1) << 28),
+// the neighbours being slots base + t for the set bits t of mask, in ascending (row, slot) order;
+// cnt[i] = number of entries found (may exceed kmax).
 // ---------------------------------------------------------------------------------------------
 template <bool SPLIT>
 __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t n, const uint32_t *__restrict__ skey,
@@ -250,7 +254,7 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                                                          const typename Types<SPLIT>::Pos *__restrict__ pos,
                                                          const float *__restrict__ cxs, const double *__restrict__ xs,
                                                          const double *__restrict__ ys, const double *__restrict__ zs,
-                                                         int kmax, uint32_t *__restrict__ list,
+                                                         int kmax, uint2 *__restrict__ list,
                                                          uint32_t *__restrict__ cnt_out) {
     using Pos = typename Types<SPLIT>::Pos;
     // staged candidate: (x in the group frame, y, z relative to its bucket corner, bucket x as int bits)
@@ -273,7 +277,7 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
     const float fcell = P.f_cell;
     const uint32_t self = (uint32_t)s;
     uint32_t cnt = 0;
-    uint32_t *out = list + (size_t)s;          // next free list slot of this particle (column-major)
+    uint2 *out = list + (size_t)s;             // next free list entry of this particle (column-major)
     const size_t colstep = (size_t)n;
     bool need = active;
     while (true) {
@@ -295,9 +299,7 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
             const uint32_t lo = __reduce_min_sync(kFullMask, rs);
             const uint32_t hi = __reduce_max_sync(kFullMask, re);
             const float oyr = oy - (float)dcy * fcell, ozr = oz - (float)dcz * fcell;
-            // list entry = slot | (dcx + 1) << 26 | (dcy + 1) << 28 | (dcz + 1) << 30; the dcx field is
-            // (cx_j - cx + 1) & 3, formed from the staged bucket x by one subtraction
-            const uint32_t code_yz = (uint32_t)(dcy + 1) << 28 | (uint32_t)(dcz + 1) << 30;
+            const uint32_t code_yz = (uint32_t)(dcy + 1) << 26 | (uint32_t)(dcz + 1) << 28;
             const int cxm1 = cx - 1;
             for (uint32_t b = lo; b < hi; b += 32) {
                 const uint32_t jl = b + lane;
@@ -369,12 +371,8 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                             support_exact(P, xs, ys, zs, b + (uint32_t)t, xs[s], ys[s], zs[s], -1, 0.0))
                             hitm |= 1u << t;
                     }
-                    while (hitm) {          // in stage order, i.e. ascending slot
-                        const int t = __ffs(hitm) - 1;
-                        hitm &= hitm - 1;
-                        const Pos pj = stage[wbase + t];
-                        const int cxj = SPLIT ? __float_as_int((float)pj.w) : (int)pj.w;
-                        if (cnt < (uint32_t)kmax) *out = (b + (uint32_t)t) | (uint32_t)(cxj - cxm1) << 26 | code_yz;
+                    if (hitm) {
+                        if (cnt < (uint32_t)kmax) *out = make_uint2(hitm, b | code_yz);
                         out += colstep;
                         ++cnt;
                     }
@@ -395,7 +393,7 @@ __global__ void __launch_bounds__(PK_THREADS, SPLIT ? 4 : 2)
 k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *__restrict__ cellr,
        const typename Types<SPLIT>::Pos *__restrict__ pos, const typename Types<SPLIT>::Rec *__restrict__ rec,
        const float *__restrict__ cxs, const double *__restrict__ xs, const double *__restrict__ ys,
-       const double *__restrict__ zs, int kmax, const uint32_t *__restrict__ list,
+       const double *__restrict__ zs, int kmax, const uint2 *__restrict__ list,
        const uint32_t *__restrict__ cnt_in, const uint32_t *__restrict__ perm, State A, State B,
        const uint8_t *__restrict__ lab_s, const uint8_t *__restrict__ mat_s, const uint32_t *__restrict__ id_s,
        const double *__restrict__ dt_ptr, unsigned int *__restrict__ sig, unsigned long long *__restrict__ pairs,
@@ -423,13 +421,13 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
     Acc<R> acc;
     acc.zero();
     const uint32_t cnt = active ? cnt_in[s] : 0u;
-    const int nl = (int)min(cnt, (uint32_t)kmax);
+    const int ne = (int)min(cnt, (uint32_t)kmax);
+    const R cxf = SPLIT ? (R)(active ? cxs[s] : 0.0f) : R(0);   // own bucket x
 
-    // one real neighbour: canonical orientation (the lower sorted slot is the left state); both ends
-    // of the pair evaluate x_R - x_L from the same operands in the same order
-    auto real_pair = [&](uint32_t e, const Pos &pj, const Rec &rj) {
-        const uint32_t jj = e & IT_JMASK;
-        const int ex = (int)(e >> 26 & 3u) - 1, ey = (int)(e >> 28 & 3u) - 1, ez = (int)(e >> 30) - 1;
+    // one real neighbour jj, in row (dcy, dcz) = code - 1 and bucket x cxj: canonical orientation (the
+    // lower sorted slot is the left state); both ends of the pair evaluate x_R - x_L from the same
+    // operands in the same order
+    auto real_pair = [&](uint32_t jj, uint32_t code, R cxj, const Pos &pj, const Rec &rj) {
         const PIn<R> oth = unpack(rj, (R)pj.w);
         const bool iL = s < (int64_t)jj;
         const R ax = iL ? (R)pj.x : mrx, bx = iL ? mrx : (R)pj.x;
@@ -438,9 +436,10 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
         R d0, d1, d2;
         if (SPLIT) {
             const R f = iL ? fcell : -fcell;
-            d0 = (ax - bx) + (R)ex * f;
-            d1 = (ay - by) + (R)ey * f;
-            d2 = (az - bz) + (R)ez * f;
+            const R ex = cxj - cxf, ey = (R)((int)(code & 3u) - 1), ez = (R)((int)(code >> 2) - 1);
+            d0 = (ax - bx) + ex * f;
+            d1 = (ay - by) + ey * f;
+            d2 = (az - bz) + ez * f;
         } else {
             d0 = ax - bx; d1 = ay - by; d2 = az - bz;
         }
@@ -449,27 +448,53 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
         accumulate<R>(acc, o, iL ? R(-1) : R(1), me, oth);
     };
 
-    // ---- listed real neighbours, all lanes in lockstep; the list entry two ahead and the record one
-    // ahead are in flight while the current pair is evaluated
+    // ---- listed real neighbours, all lanes in lockstep: the set bits of the current entry give the
+    // slots; the entry after it and the next neighbour's record are in flight while the current pair
+    // is evaluated
+    uint32_t nlist = 0;
     {
-        const int mc = __reduce_max_sync(kFullMask, nl);
-        const uint32_t *lp = list + (size_t)s;
+        const uint2 *lp = list + (size_t)s;
         const size_t colstep = (size_t)n;
-        uint32_t e1 = nl > 0 ? lp[0] : 0u;
-        uint32_t e2 = nl > 1 ? lp[colstep] : 0u;
-        Pos pn = pos[e1 & IT_JMASK];
-        Rec rn = rec[e1 & IT_JMASK];
-        for (int k = 0; k < mc; ++k) {
-            const uint32_t e = e1;
-            const Pos pj = pn;
-            const Rec rj = rn;
-            e1 = e2;
-            if (k + 1 < nl) {
-                pn = pos[e1 & IT_JMASK];
-                rn = rec[e1 & IT_JMASK];
+        uint32_t m = 0u, y = 0u;
+        uint2 nx = make_uint2(0u, 0u);
+        if (ne > 0) { const uint2 e = lp[0]; m = e.x; y = e.y; }
+        if (ne > 1) nx = lp[colstep];
+        int ke = 2;
+        // next listed neighbour: slot j, row code c; refills the mask from the entry in flight
+        auto next = [&](uint32_t &j, uint32_t &c) -> bool {
+            if (m == 0u) return false;
+            const int t = __ffs(m) - 1;
+            m &= m - 1u;
+            j = (y & IT_JMASK) + (uint32_t)t;
+            c = y >> 26;
+            if (m == 0u) {
+                m = nx.x; y = nx.y;
+                nx = ke < ne ? lp[(size_t)ke * colstep] : make_uint2(0u, 0u);
+                ++ke;
             }
-            if (k + 2 < nl) e2 = lp[(size_t)(k + 2) * colstep];
-            if (k < nl) real_pair(e, pj, rj);
+            return true;
+        };
+        uint32_t j1 = 0u, c1 = 0u;
+        bool h1 = next(j1, c1);
+        Pos p1 = pos[j1];
+        Rec r1 = rec[j1];
+        float x1 = SPLIT ? cxs[j1] : 0.0f;
+        while (__any_sync(kFullMask, h1)) {
+            const bool h = h1;
+            const uint32_t j = j1, c = c1;
+            const Pos pj = p1;
+            const Rec rj = r1;
+            const float xj = x1;
+            h1 = next(j1, c1);
+            if (h1) {
+                p1 = pos[j1];
+                r1 = rec[j1];
+                if (SPLIT) x1 = cxs[j1];
+            }
+            if (h) {
+                real_pair(j, c, (R)xj, pj, rj);
+                ++nlist;
+            }
         }
     }
 
@@ -479,6 +504,7 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
     int cx = 0, cy = 0, cz = 0;
     if (active) decode_cell(P, key, cx, cy, cz);
     int ni = 0;
+    uint32_t nover = 0;
     for (int src = (__any_sync(kFullMask, (int)cnt > kmax) ? 0 : 1); src <= P.nwalls; ++src) {
         const int wax = src > 0 ? P.wall_axis[src - 1] : -1;
         const double wpos = src > 0 ? P.wall_pos[src - 1] : 0.0;
@@ -526,10 +552,9 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
                 if (!hit) continue;
                 if (src == 0) {
                     // real neighbour past the list capacity
-                    if (seen++ < (uint32_t)kmax) continue;
-                    const uint32_t e = j | (uint32_t)(dcx + 1) << 26 | (uint32_t)(dcy + 1) << 28 |
-                                       (uint32_t)(dcz + 1) << 30;
-                    real_pair(e, pj, rec[j]);
+                    if (seen++ < nlist) continue;
+                    real_pair(j, (uint32_t)(dcy + 1) | (uint32_t)(dcz + 1) << 2, (R)cxs[j], pj, rec[j]);
+                    ++nover;
                 } else {
                     PIn<R> oth = load_rec(rec, (R)pj.w, j);
                     R d0, d1, d2;
@@ -557,7 +582,7 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
             }
         }
     }
-    const int nr = (int)cnt;
+    const int nr = (int)(nlist + nover);
 
     // ---- integration (Sec. II step g): forward Euler on the conserved variables, Jaumann-rate
     // stress with radial return, positions with the velocity of the step's start.
@@ -659,7 +684,7 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
 
 cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n, const uint32_t *skey,
                             const uint2 *cellr, const void *pos, const void *rec, const float *cxs,
-                            const double *xs, const double *ys, const double *zs, int kmax, uint32_t *list,
+                            const double *xs, const double *ys, const double *zs, int kmax, uint2 *list,
                             uint32_t *cnt, const uint32_t *perm, const State &A, const State &B,
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
                             unsigned int *sig, unsigned long long *pairs, int32_t *nreal, int32_t *nimage,
