@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(128) k_adj_pair(DevParams P, int64_t n, const 
                 for (int c = 0; c < 3; ++c) xb[c] += kL ? -db[c] : db[c];
             };
             // listed neighbours: the set bits of each entry's mask, slots base + t in ascending order
-            const uint32_t cnt = cnt_in[s];
+            const uint32_t cnt = cnt_in[s] & 255u;   // entries found (low byte; the rest is a count)
             const int ne = (int)min(cnt, (uint32_t)kmax);
             uint32_t nlist = 0;
             for (int k = 0; k < ne; ++k) {

@@ -246,7 +246,8 @@ __device__ __forceinline__ bool support_exact(const DevParams &P, const double *
 // ---------------------------------------------------------------------------------------------
 // Neighbour list (real neighbours). list[k * n + i], k < kmax: (mask, base | (dcy + 1) << 26 | (dcz + 1) << 28),
 // the neighbours being slots base + t for the set bits t of mask, in ascending (row, slot) order;
-// cnt[i] = number of entries found (may exceed kmax).
+// cnt[i] = min(entries found, 255) | (neighbours in the stored entries) << 8. Entries found beyond kmax
+// are not stored: the pair kernel finds those neighbours by re-scanning.
 // ---------------------------------------------------------------------------------------------
 template <bool SPLIT>
 __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t n, const uint32_t *__restrict__ skey,
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
     }
     const float fcell = P.f_cell;
     const uint32_t self = (uint32_t)s;
-    uint32_t cnt = 0;
+    uint32_t cnt = 0, nlisted = 0;
     uint2 *out = list + (size_t)s;             // next free list entry of this particle (column-major)
     const size_t colstep = (size_t)n;
     bool need = active;
@@ -372,7 +373,10 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                             hitm |= 1u << t;
                     }
                     if (hitm) {
-                        if (cnt < (uint32_t)kmax) *out = make_uint2(hitm, b | code_yz);
+                        if (cnt < (uint32_t)kmax) {
+                            *out = make_uint2(hitm, b | code_yz);
+                            nlisted += (uint32_t)__popc(hitm);
+                        }
                         out += colstep;
                         ++cnt;
                     }
@@ -382,7 +386,7 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
         }
         need = need && !ing;
     }
-    if (valid) cnt_out[s] = cnt;
+    if (valid) cnt_out[s] = min(cnt, 255u) | nlisted << 8;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -420,8 +424,10 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
     const R fcell = SPLIT ? (R)P.f_cell : (R)P.cell;
     Acc<R> acc;
     acc.zero();
-    const uint32_t cnt = active ? cnt_in[s] : 0u;
-    const int ne = (int)min(cnt, (uint32_t)kmax);
+    const uint32_t cw = active ? cnt_in[s] : 0u;
+    const uint32_t cnt = cw & 255u;                  // entries found
+    const int ne = (int)min(cnt, (uint32_t)kmax);    // entries stored
+    const uint32_t nlist = cw >> 8;                  // neighbours in the stored entries
     const R cxf = SPLIT ? (R)(active ? cxs[s] : 0.0f) : R(0);   // own bucket x
 
     // one real neighbour jj, in row (dcy, dcz) = code - 1 and bucket x cxj: canonical orientation (the
@@ -451,7 +457,6 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
     // ---- listed real neighbours, all lanes in lockstep: the set bits of the current entry give the
     // slots; the entry after it and the next neighbour's record are in flight while the current pair
     // is evaluated
-    uint32_t nlist = 0;
     {
         const uint2 *lp = list + (size_t)s;
         const size_t colstep = (size_t)n;
@@ -460,41 +465,38 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
         if (ne > 0) { const uint2 e = lp[0]; m = e.x; y = e.y; }
         if (ne > 1) nx = lp[colstep];
         int ke = 2;
-        // next listed neighbour: slot j, row code c; refills the mask from the entry in flight
-        auto next = [&](uint32_t &j, uint32_t &c) -> bool {
-            if (m == 0u) return false;
+        // next listed neighbour (called only while one is left): slot j, row code c; refills the mask
+        // from the entry in flight when the current one is used up
+        auto next = [&](uint32_t &j, uint32_t &c) {
             const int t = __ffs(m) - 1;
             m &= m - 1u;
             j = (y & IT_JMASK) + (uint32_t)t;
             c = y >> 26;
             if (m == 0u) {
                 m = nx.x; y = nx.y;
-                nx = ke < ne ? lp[(size_t)ke * colstep] : make_uint2(0u, 0u);
+                if (ke < ne) nx = lp[(size_t)ke * colstep];
                 ++ke;
             }
-            return true;
         };
+        const int mc = (int)__reduce_max_sync(kFullMask, nlist);
         uint32_t j1 = 0u, c1 = 0u;
-        bool h1 = next(j1, c1);
+        if (nlist > 0) next(j1, c1);
         Pos p1 = pos[j1];
         Rec r1 = rec[j1];
         float x1 = SPLIT ? cxs[j1] : 0.0f;
-        while (__any_sync(kFullMask, h1)) {
-            const bool h = h1;
+#pragma unroll 2
+        for (int k = 0; k < mc; ++k) {
             const uint32_t j = j1, c = c1;
             const Pos pj = p1;
             const Rec rj = r1;
             const float xj = x1;
-            h1 = next(j1, c1);
-            if (h1) {
+            if ((uint32_t)k + 1 < nlist) {
+                next(j1, c1);
                 p1 = pos[j1];
                 r1 = rec[j1];
                 if (SPLIT) x1 = cxs[j1];
             }
-            if (h) {
-                real_pair(j, c, (R)xj, pj, rj);
-                ++nlist;
-            }
+            if ((uint32_t)k < nlist) real_pair(j, c, (R)xj, pj, rj);
         }
     }
 
