@@ -250,6 +250,8 @@ static void fill_params(const gsph_config &c, DevParams &P) {
     P.alpha = c.alpha;
     P.K_labels = c.K;
     P.f_cell = (float)P.cell;
+    P.f_inv_cell = (float)(1.0 / P.cell);
+    if (!std::isnormal(P.f_inv_cell)) P.f_inv_cell = std::nanf("");   // the hash then always divides in FP64
     P.f_inv_h = (float)(1.0 / c.h);
     P.f_kdw = (float)P.kdw;
     // FP32 r^2 of candidates is within ~1.4e-6 R2 of the FP64 value; outside +-1.2e-5 R2 the FP32

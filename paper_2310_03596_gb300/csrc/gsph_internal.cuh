@@ -39,6 +39,7 @@ struct DevParams {
     int K_labels;
     // FP32 copies for the split path
     float f_cell, f_inv_h, f_kdw, f_R2lo, f_R2hi;
+    float f_inv_cell;        // FP32 rounding of the FP64 reciprocal of the bucket side
     float f_rho0[kMaxMat], f_K[kMaxMat], f_G[kMaxMat], f_Mmod[kMaxMat];
 };
 
@@ -81,14 +82,36 @@ __device__ __forceinline__ int bucket_coord(double x, double lo, double cell, in
     return (int)t;
 }
 
+// bucket_coord without the FP64 division in the common case. The FP32 quotient tf of the FP32 rounding
+// of d = x - lo by the FP32 reciprocal carries three FP32 roundings, so it lies within 3.01 * 2^-24 |t|
+// of the exact d / cell, and the correctly rounded FP64 quotient t within another 2^-53 |t|. When tf
+// is farther than 2^-22 (|tf| + 1) from every integer, t lies strictly between the same two integers
+// and floor(tf) = floor(t). Otherwise (near a bucket face, NaN, infinities, differences beyond the
+// FP32 range or below its normal range, a reciprocal that is not a normal FP32 number - passed as NaN)
+// the FP64 division decides.
+__device__ __forceinline__ int bucket_coord_fast(double x, double lo, double cell, float inv_cell, int dim) {
+    const double d = __dsub_rn(x, lo);
+    const float df = __double2float_rn(d);
+    const float tf = __fmul_rn(df, inv_cell);
+    const float fl = floorf(tf);
+    const float fr = __fsub_rn(tf, fl);   // exact
+    const float eps = __fmul_rn(0x1p-22f, __fadd_rn(fabsf(tf), 1.0f));
+    if (fr > eps && fr < __fsub_rn(1.0f, eps) && fabsf(df) >= 0x1p-126f) {
+        if (fl < 0.0f) return -1;
+        if (fl >= (float)dim) return dim;
+        return (int)fl;
+    }
+    return bucket_coord(x, lo, cell, dim);
+}
+
 __device__ __forceinline__ int bucket_coord_signed(double x, double lo, double cell) {
     return (int)floor(__ddiv_rn(__dsub_rn(x, lo), cell));
 }
 
 __device__ __forceinline__ uint32_t hash_of(const DevParams &P, double x, double y, double z) {
-    int cx = bucket_coord(x, P.lo[0], P.cell, P.dims[0]);
-    int cy = bucket_coord(y, P.lo[1], P.cell, P.dims[1]);
-    int cz = bucket_coord(z, P.lo[2], P.cell, P.dims[2]);
+    int cx = bucket_coord_fast(x, P.lo[0], P.cell, P.f_inv_cell, P.dims[0]);
+    int cy = bucket_coord_fast(y, P.lo[1], P.cell, P.f_inv_cell, P.dims[1]);
+    int cz = bucket_coord_fast(z, P.lo[2], P.cell, P.f_inv_cell, P.dims[2]);
     if (cx < 0 || cy < 0 || cz < 0 || cx >= P.dims[0] || cy >= P.dims[1] || cz >= P.dims[2]) return P.ncell;
     return (uint32_t)cx + (uint32_t)P.dims[0] * ((uint32_t)cy + (uint32_t)P.dims[1] * (uint32_t)cz);
 }

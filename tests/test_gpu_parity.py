@@ -153,6 +153,47 @@ def test_particles_outside_the_grid_are_garbage():
         sol.close()
 
 
+def test_hash_on_and_near_bucket_faces():
+    """Positions on bucket faces, a few ulps and a few FP32 roundings either side of them, the grid's
+    outer faces, far outside, NaN and infinities: the device hash (FP32 quotient with an FP64
+    fallback near faces) equals the oracle's FP64 definition bit for bit, and so does the order."""
+    s = scenes.cube_impact(n_side=8)
+    n = s.n
+    P = orc.params_of(s)
+    cell, lo, dims = 2.0 * s.h, np.asarray(s.grid_lo), np.asarray(s.grid_dims)
+    rng = np.random.default_rng(7)
+    offs = np.array([0.0, 1e-300, 2.0 ** -60, 2.0 ** -40, 2.0 ** -30, 2.0 ** -24, 2.0 ** -22, 2.0 ** -20, 1e-4, 0.5])
+    pos = np.empty((n, 3))
+    for a in range(3):
+        k = rng.integers(-1, dims[a] + 2, n).astype(np.float64)
+        base = lo[a] + k * cell
+        d = rng.choice(np.concatenate([offs, -offs]), n) * cell
+        ulps = rng.integers(-3, 4, n)
+        pos[:, a] = np.array([np.nextafter(b, np.inf if u > 0 else -np.inf) if u else b
+                              for b, u in zip(base + d, ulps)])
+        for u in range(1, 3):       # a second and third ulp step where drawn
+            m = np.abs(ulps) > u
+            pos[m, a] = np.nextafter(pos[m, a], np.where(ulps[m] > 0, np.inf, -np.inf))
+    pos[0] = [np.nan, 0.0, 0.0]
+    pos[1, 1] = np.inf
+    pos[2, 2] = -np.inf
+    pos[3] = lo + dims * cell          # the far corner: outside (half-open buckets)
+    pos[4] = lo                        # the near corner: bucket 0
+    pos[5, 0] = 1e300
+    s.pos = pos
+    s.vel = np.zeros_like(pos)         # one step moves nothing, only the hash is compared
+    key_o = orc.hash_keys(P, pos[:, 0], pos[:, 1], pos[:, 2])
+    order = orc.sort_order(key_o)
+    sol = gsph.Solver.from_scene(s, precision=gsph.FP64, diagnostics=True)
+    try:
+        sol.step(1)
+        sol.sync()
+        assert np.array_equal(sol.get("hash"), key_o[order])
+        assert np.array_equal(sol.get("id"), order.astype(np.uint32))
+    finally:
+        sol.close()
+
+
 def test_invalid_label_reported():
     s = scenes.cube_impact(n_side=4)
     s.label[3] = 5               # K = 1
