@@ -12,8 +12,11 @@
 //   middle of the Cg segment, 1000 beyond the other Cg, floor(1000 t / half-distance) in between, at
 //   least 1); the offset from the middle in FP64, the projection and scaling in FP32;
 //   n = min(#positive on each side); the n largest hashes of each side swap labels, ties broken by
-//   the lowest persistent id (a 1001-bin histogram finds the threshold hash, a 3 x 9-bit radix
-//   select on ids finds the id threshold inside the threshold bin);
+//   the lowest persistent id. A 1001-bin histogram finds the threshold hash. When the threshold bin
+//   holds more particles than are needed, the exchange pass collects that bin into a short list, and
+//   every block finds the id threshold by a 3 x 9-bit radix select over the list in shared memory
+//   (the block owning a listed slot applies its swap); a bin larger than the list capacity is split
+//   by the same radix select run over all particles with a grid barrier per digit;
 //   the fixed-point sums are updated with the moved particles (exactly, so the next pair sees the
 //   same Cg as a recomputation).
 #include <cuda/atomic>
@@ -27,10 +30,12 @@ constexpr int SW_ID_BITS = 9;
 constexpr int SW_ID_BINS = 1 << SW_ID_BITS;
 constexpr int SW_THREADS = 512;
 constexpr int SW_NT = kMaxMat + 1;   // per-type slots + the all-types slot
+constexpr int SW_TCAP = 2048;        // threshold-bin list capacity per side
 
 struct SwapPair {
     uint32_t hist[2][SW_BINS];
     uint32_t idh[3][2][SW_ID_BINS];
+    uint32_t tcnt[2];                // threshold-bin list fill per side
     unsigned long long moved;
 };
 
@@ -115,6 +120,32 @@ __device__ __forceinline__ void warp_add_sums(long long (*sh)[4], int key, bool 
     }
 }
 
+// Moves the sums of the particles that changed label (dsum[side] = q0 q1 q2 count; side 0 went a -> b,
+// side 1 b -> a) into the global per-label (and per-type) fixed-point sums. Threads 0 and 1.
+__device__ __forceinline__ void flush_moved(SwapScratch *S, const long long (*dsum)[4], int a, int b, int type) {
+    if (threadIdx.x >= 2) return;
+    const int sd = threadIdx.x;
+    const int from = sd == 0 ? a : b, to = sd == 0 ? b : a;
+    const long long c = dsum[sd][3];
+    if (!c) return;
+    for (int k = 0; k < 3; ++k) {
+        const long long q = dsum[sd][k];
+        atomicAdd((unsigned long long *)&S->sums[from][kMaxMat][k], (unsigned long long)(-q));
+        atomicAdd((unsigned long long *)&S->sums[to][kMaxMat][k], (unsigned long long)q);
+        if (type >= 0) {
+            atomicAdd((unsigned long long *)&S->sums[from][type][k], (unsigned long long)(-q));
+            atomicAdd((unsigned long long *)&S->sums[to][type][k], (unsigned long long)q);
+        }
+    }
+    atomicAdd((unsigned long long *)&S->cnt[from][kMaxMat], (unsigned long long)(-c));
+    atomicAdd((unsigned long long *)&S->cnt[to][kMaxMat], (unsigned long long)c);
+    if (type >= 0) {
+        atomicAdd((unsigned long long *)&S->cnt[from][type], (unsigned long long)(-c));
+        atomicAdd((unsigned long long *)&S->cnt[to][type], (unsigned long long)c);
+    }
+    atomicAdd(&S->moved, (unsigned long long)c);
+}
+
 // In-place inclusive scan of a[0..nv) in shared memory by the whole block (nv <= 2 * SW_THREADS).
 __device__ void block_inclusive_scan(uint32_t *a, int nv) {
     __shared__ uint32_t wt[SW_THREADS / 32];
@@ -182,7 +213,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                                                           const uint8_t *__restrict__ mat,
                                                           const uint32_t *__restrict__ id, uint16_t *__restrict__ bh,
                                                           SwapScratch *__restrict__ S, SwapPair *__restrict__ pairs,
-                                                          int *__restrict__ err) {
+                                                          uint2 *__restrict__ tl, int *__restrict__ err) {
     __shared__ long long shs[kMaxLabel][SW_NT][4];
     __shared__ uint32_t hs[2][SW_BINS];
     __shared__ uint32_t ids[2][SW_ID_BINS];
@@ -191,6 +222,9 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
     __shared__ int T_sh[2], idsel_sh[2];
     __shared__ uint32_t need_sh[2], idpre_sh[2];
     __shared__ long long dsum[2][4];   // per side: moved q0 q1 q2, count
+    __shared__ uint32_t cntT_sh[2];    // particles in the threshold bin
+    __shared__ int list_sh;            // threshold bins split through the list (else the grid select)
+    __shared__ uint32_t tkey[2][SW_TCAP];
     const unsigned nb = gridDim.x;
     const int64_t gstride = (int64_t)gridDim.x * SW_THREADS;
     const int64_t g0 = (int64_t)blockIdx.x * SW_THREADS + threadIdx.x;
@@ -311,14 +345,20 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                         const int Tb = GSPH_BALANCE_HASH_MAX - r;
                         T_sh[sd] = Tb;
                         need_sh[sd] = m - above;
+                        cntT_sh[sd] = cum[sd][r] - above;
                         idsel_sh[sd] = (m - above) < (cum[sd][r] - above);
                         idpre_sh[sd] = 0;
                     }
                 }
                 if (blockIdx.x == 0 && threadIdx.x == 0) pr->moved = 2ull * m;
                 __syncthreads();
-                // -- radix select on persistent ids inside split threshold bins
-                if (idsel_sh[0] || idsel_sh[1]) {
+                if (threadIdx.x == 0)
+                    list_sh = (!idsel_sh[0] || cntT_sh[0] <= (uint32_t)SW_TCAP) &&
+                              (!idsel_sh[1] || cntT_sh[1] <= (uint32_t)SW_TCAP);
+                __syncthreads();
+                const bool use_list = list_sh != 0;
+                // -- radix select on persistent ids inside split threshold bins, over all particles
+                if (!use_list && (idsel_sh[0] || idsel_sh[1])) {
                     for (int pass = 0; pass < 3; ++pass) {
                         const int shift = 18 - SW_ID_BITS * pass;
                         for (int k = threadIdx.x; k < 2 * SW_ID_BINS; k += SW_THREADS) (&ids[0][0])[k] = 0;
@@ -361,20 +401,27 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                         __syncthreads();
                     }
                 }
-                // -- label exchange and exact update of the fixed-point sums
+                // -- label exchange and exact update of the fixed-point sums; the threshold bins that the
+                // list splits are collected instead
                 if (threadIdx.x < 8) (&dsum[0][0])[threadIdx.x] = 0;
                 __syncthreads();
                 for (int64_t base = (int64_t)blockIdx.x * SW_THREADS; base < n; base += gstride) {
                     const int64_t i = base + threadIdx.x;
-                    int sd = -1;
+                    int sd = -1, ap = -1;
                     long long q0 = 0, q1 = 0, q2 = 0;
                     if (i < n) {
                         const uint8_t l = lab[i];
                         if ((l == a || l == b) && (type < 0 || mat[i] == type)) {
                             const int side = l == a ? 0 : 1;
                             const int hv = bh[i];
-                            const bool take = hv > 0 && (hv > T_sh[side] ||
-                                                         (hv == T_sh[side] && (!idsel_sh[side] || id[i] <= idpre_sh[side])));
+                            bool take = false;
+                            if (hv > 0 && hv > T_sh[side]) {
+                                take = true;
+                            } else if (hv > 0 && hv == T_sh[side]) {
+                                if (!idsel_sh[side]) take = true;
+                                else if (!use_list) take = id[i] <= idpre_sh[side];
+                                else ap = side;
+                            }
                             if (take) {
                                 sd = side;
                                 lab[i] = (uint8_t)(side == 0 ? b : a);
@@ -385,31 +432,89 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                         }
                     }
                     if (__any_sync(kFullMask, sd >= 0)) warp_add_sums(dsum, sd < 0 ? 0 : sd, sd >= 0, q0, q1, q2);
-                }
-                __syncthreads();
-                if (threadIdx.x < 2) {
-                    const int sd = threadIdx.x;
-                    const int from = sd == 0 ? a : b, to = sd == 0 ? b : a;
-                    const long long c = dsum[sd][3];
-                    if (c) {
-                        for (int k = 0; k < 3; ++k) {
-                            const long long q = dsum[sd][k];
-                            atomicAdd((unsigned long long *)&S->sums[from][kMaxMat][k], (unsigned long long)(-q));
-                            atomicAdd((unsigned long long *)&S->sums[to][kMaxMat][k], (unsigned long long)q);
-                            if (type >= 0) {
-                                atomicAdd((unsigned long long *)&S->sums[from][type][k], (unsigned long long)(-q));
-                                atomicAdd((unsigned long long *)&S->sums[to][type][k], (unsigned long long)q);
-                            }
-                        }
-                        atomicAdd((unsigned long long *)&S->cnt[from][kMaxMat], (unsigned long long)(-c));
-                        atomicAdd((unsigned long long *)&S->cnt[to][kMaxMat], (unsigned long long)c);
-                        if (type >= 0) {
-                            atomicAdd((unsigned long long *)&S->cnt[from][type], (unsigned long long)(-c));
-                            atomicAdd((unsigned long long *)&S->cnt[to][type], (unsigned long long)c);
-                        }
-                        atomicAdd(&S->moved, (unsigned long long)c);
+                    // warp-aggregated append of (id, slot) to the side's threshold-bin list
+#pragma unroll
+                    for (int side = 0; side < 2; ++side) {
+                        const unsigned am = __ballot_sync(kFullMask, ap == side);
+                        if (!am) continue;
+                        const int lane = threadIdx.x & 31, ld = __ffs(am) - 1;
+                        uint32_t pos = 0;
+                        if (lane == ld) pos = atomicAdd(&pr->tcnt[side], (uint32_t)__popc(am));
+                        pos = __shfl_sync(kFullMask, pos, ld) + (uint32_t)__popc(am & lanemask_lt());
+                        if (ap == side && pos < (uint32_t)SW_TCAP)
+                            tl[side * SW_TCAP + pos] = make_uint2(id[i], (uint32_t)i);
                     }
                 }
+                __syncthreads();
+                flush_moved(S, dsum, a, b, type);
+                if (!grid_barrier(S, nb, err)) return;
+                if (!use_list || !(idsel_sh[0] || idsel_sh[1])) continue;
+                // -- id threshold of each listed bin: radix select in shared memory, every block
+                for (int sd = 0; sd < 2; ++sd) {
+                    if (!idsel_sh[sd]) continue;
+                    for (uint32_t k = threadIdx.x; k < cntT_sh[sd]; k += SW_THREADS)
+                        tkey[sd][k] = __ldcg(&tl[sd * SW_TCAP + k].x);
+                }
+                __syncthreads();
+                for (int pass = 0; pass < 3; ++pass) {
+                    const int shift = 18 - SW_ID_BITS * pass;
+                    for (int k = threadIdx.x; k < 2 * SW_ID_BINS; k += SW_THREADS) (&ids[0][0])[k] = 0;
+                    __syncthreads();
+                    for (int sd = 0; sd < 2; ++sd) {
+                        if (!idsel_sh[sd]) continue;
+                        for (uint32_t k = threadIdx.x; k < cntT_sh[sd]; k += SW_THREADS) {
+                            const uint32_t v = tkey[sd][k];
+                            if ((v >> (shift + SW_ID_BITS)) == (idpre_sh[sd] >> (shift + SW_ID_BITS)))
+                                atomicAdd(&ids[sd][(v >> shift) & (SW_ID_BINS - 1)], 1u);
+                        }
+                    }
+                    __syncthreads();
+                    block_inclusive_scan(ids[0], SW_ID_BINS);
+                    block_inclusive_scan(ids[1], SW_ID_BINS);
+                    __shared__ uint32_t upd2[2][2];
+                    for (int k = threadIdx.x; k < 2 * SW_ID_BINS; k += SW_THREADS) {
+                        const int sd = k / SW_ID_BINS, d = k % SW_ID_BINS;
+                        if (!idsel_sh[sd]) continue;
+                        const uint32_t below = d > 0 ? ids[sd][d - 1] : 0u;
+                        if (ids[sd][d] >= need_sh[sd] && below < need_sh[sd]) {
+                            upd2[sd][0] = (uint32_t)d;
+                            upd2[sd][1] = below;
+                        }
+                    }
+                    __syncthreads();
+                    if (threadIdx.x < 2 && idsel_sh[threadIdx.x]) {
+                        idpre_sh[threadIdx.x] |= upd2[threadIdx.x][0] << shift;
+                        need_sh[threadIdx.x] -= upd2[threadIdx.x][1];
+                    }
+                    __syncthreads();
+                }
+                // -- swaps of the listed particles up to the id threshold, each applied by the block that
+                // owns its slot in the strided partition (so no block reads a label another block wrote)
+                if (threadIdx.x < 8) (&dsum[0][0])[threadIdx.x] = 0;
+                __syncthreads();
+                for (int sd = 0; sd < 2; ++sd) {
+                    if (!idsel_sh[sd]) continue;
+                    const uint32_t c = cntT_sh[sd];
+                    for (uint32_t k0 = 0; k0 < c; k0 += SW_THREADS) {
+                        const uint32_t k = k0 + threadIdx.x;
+                        bool mv = false;
+                        long long q0 = 0, q1 = 0, q2 = 0;
+                        if (k < c) {
+                            const uint2 e = __ldcg(&tl[sd * SW_TCAP + k]);
+                            const uint32_t i = e.y;
+                            if ((i / SW_THREADS) % nb == blockIdx.x && e.x <= idpre_sh[sd]) {
+                                mv = true;
+                                lab[i] = (uint8_t)(sd == 0 ? b : a);
+                                q0 = quantise(x[i], Q.lo[0], Q.hi[0], Q.sc[0]);
+                                q1 = quantise(y[i], Q.lo[1], Q.hi[1], Q.sc[1]);
+                                q2 = quantise(z[i], Q.lo[2], Q.hi[2], Q.sc[2]);
+                            }
+                        }
+                        if (__any_sync(kFullMask, mv)) warp_add_sums(dsum, sd, mv, q0, q1, q2);
+                    }
+                }
+                __syncthreads();
+                flush_moved(S, dsum, a, b, type);
                 if (!grid_barrier(S, nb, err)) return;
             }
     }
@@ -421,7 +526,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
 size_t swap_scratch_bytes(int K, int nmat) {
     const int ntype = nmat > 1 ? nmat : 1;
     const size_t npairs = (size_t)ntype * (size_t)(K * (K - 1) / 2);
-    return sizeof(SwapScratch) + (npairs > 0 ? npairs : 1) * sizeof(SwapPair);
+    return sizeof(SwapScratch) + (npairs > 0 ? npairs : 1) * sizeof(SwapPair) + 2 * SW_TCAP * sizeof(uint2);
 }
 
 static QuantParams quant_params(const DevParams &P) {
@@ -456,12 +561,15 @@ cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const double *x, con
     if (e != cudaSuccess) return e;
     SwapScratch *S = (SwapScratch *)scratch;
     SwapPair *pairs = (SwapPair *)((char *)scratch + sizeof(SwapScratch));
+    const int ntype = P.nmat > 1 ? P.nmat : 1;
+    const size_t npairs = (size_t)ntype * (size_t)(P.K_labels * (P.K_labels - 1) / 2);
+    uint2 *tl = (uint2 *)(pairs + (npairs > 0 ? npairs : 1));
     QuantParams Q = quant_params(P);
     double alpha = P.alpha;
     int K = P.K_labels, nmat = P.nmat;
     void *args[] = {(void *)&n, (void *)&Q, (void *)&alpha, (void *)&K, (void *)&nmat, (void *)&x, (void *)&y,
                     (void *)&z, (void *)&lab, (void *)&mat, (void *)&id, (void *)&bh, (void *)&S, (void *)&pairs,
-                    (void *)&err};
+                    (void *)&tl, (void *)&err};
     return cudaLaunchCooperativeKernel((const void *)k_swap_pass, dim3(grid), dim3(SW_THREADS), args, 0, s);
 }
 
