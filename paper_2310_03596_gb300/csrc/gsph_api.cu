@@ -226,6 +226,7 @@ static void fill_params(const gsph_config &c, DevParams &P) {
         P.lo[a] = c.grid_lo[a];
         P.dims[a] = c.grid_dims[a];
         P.g[a] = c.gravity[a];
+        if (c.gravity[a] != 0.0) P.has_gravity = 1;
     }
     P.h = c.h;
     P.cell = 2.0 * c.h;
@@ -254,10 +255,12 @@ static void fill_params(const gsph_config &c, DevParams &P) {
     if (!std::isnormal(P.f_inv_cell)) P.f_inv_cell = std::nanf("");   // the hash then always divides in FP64
     P.f_inv_h = (float)(1.0 / c.h);
     P.f_kdw = (float)P.kdw;
-    // FP32 r^2 of candidates is within ~1.4e-6 R2 of the FP64 value; outside +-1.2e-5 R2 the FP32
+    // The FP32 evaluation of r^2 - R2lo for a candidate (the list kernel's |c|^2 + (|o|^2 - R2lo) - 2 c.o
+    // in frames with |coordinates| < 5h, the re-scan's direct differences) is within 7e-6 R2 of the
+    // FP64 value (coordinate roundings plus the roundings of the evaluation); outside +-3e-5 R2 the FP32
     // comparison is therefore exact, inside it the FP64 positions decide.
-    P.f_R2lo = (float)(P.R2 * (1.0 - 1.2e-5));
-    P.f_R2hi = (float)(P.R2 * (1.0 + 1.2e-5));
+    P.f_R2lo = (float)(P.R2 * (1.0 - 3e-5));
+    P.f_R2hi = (float)(P.R2 * (1.0 + 3e-5));
 }
 
 static int64_t swap_pass_launches(const DevParams &P) {

@@ -37,6 +37,7 @@ struct DevParams {
     int wall_axis[kMaxWall];
     int nmat;
     int K_labels;
+    int has_gravity;         // g != 0
     // FP32 copies for the split path
     float f_cell, f_inv_h, f_kdw, f_R2lo, f_R2hi;
     float f_inv_cell;        // FP32 rounding of the FP64 reciprocal of the bucket side

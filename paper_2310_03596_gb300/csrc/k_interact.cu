@@ -25,7 +25,7 @@
 // so differences keep ~2^-24 * 2h), FP32 sums with Kahan compensation for the conserved quantities
 // (volume, mass, momentum, energy) and plain FP32 sums for the velocity gradient, FP64 integration of
 // the conserved variables, positions and stress (the stress rate itself in FP32). The support predicate
-// stays exact: the FP32 r^2 decides only outside a band of relative width 1.2e-5 around (2h)^2, inside
+// stays exact: the FP32 r^2 decides only outside a band of relative width 3e-5 around (2h)^2, inside
 // which the FP64 positions decide with the same rounding as FP64 code.
 #include <type_traits>
 
@@ -258,8 +258,8 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                                                          int kmax, uint2 *__restrict__ list,
                                                          uint32_t *__restrict__ cnt_out) {
     using Pos = typename Types<SPLIT>::Pos;
-    // staged candidate: (x in the group frame, y, z relative to its bucket corner, bucket x as int bits)
-    // on the split path; (x, y, z, bucket x) in FP64 on the FP64 path
+    // staged candidate: split path (c, |c|^2) with c = (x in the group frame, y, z in the row frame);
+    // FP64 path (x, y, z, bucket x)
     __shared__ Pos stage[NL_THREADS];
     const int tid = threadIdx.x, lane = tid & 31, wbase = tid & ~31;
     const int64_t s = (int64_t)blockIdx.x * NL_THREADS + tid;
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
         ox = (float)p.x; oy = (float)p.y; oz = (float)p.z;
         if (!SPLIT) { X = (double)p.x; Y = (double)p.y; Z = (double)p.z; }
     }
-    const float fcell = P.f_cell;
+    const float fcell = P.f_cell, hcell = 0.5f * P.f_cell;
     const uint32_t self = (uint32_t)s;
     uint32_t cnt = 0, nlisted = 0;
     uint2 *out = list + (size_t)s;             // next free list entry of this particle (column-major)
@@ -287,10 +287,13 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
         const int leader = __ffs(todo) - 1;
         const int gby = __shfl_sync(kFullMask, cy, leader), gbz = __shfl_sync(kFullMask, cz, leader);
         const int gbx = __shfl_sync(kFullMask, cx, leader);
-        // a group shares the bucket row and lies within 4 buckets of the leader in x, so staged and own
-        // x in the group frame stay below 12h and their FP32 rounding stays well inside the band
-        const bool ing = need && cy == gby && cz == gbz && abs(cx - gbx) <= 4;
-        const float oxg = ox + (float)(cx - gbx) * fcell;   // own x in the group frame
+        // a group shares the bucket row. Split path: its buckets are the leader's and the next two in x
+        // (the leader has the lowest x bucket of its row among the remaining lanes), and the group frame
+        // has its x origin 1.5 buckets above the leader's bucket corner, so |x| < 5h for own positions
+        // and window candidates. FP64 path: within 4 buckets of the leader.
+        const bool ing = need && cy == gby && cz == gbz &&
+                         (SPLIT ? (unsigned)(cx - gbx) <= 2u : abs(cx - gbx) <= 4);
+        const float oxg = fmaf((float)(cx - gbx) - 1.5f, fcell, ox);   // own x in the group frame
         for (int row = 0; row < 9; ++row) {
             const int dcy = row % 3 - 1, dcz = row / 3 - 1;
             const int Yc = gby + dcy, Zc = gbz + dcz;
@@ -299,7 +302,11 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
             if (ing) row_window(P, cellr, cx, Yc, Zc, rs, re);
             const uint32_t lo = __reduce_min_sync(kFullMask, rs);
             const uint32_t hi = __reduce_max_sync(kFullMask, re);
-            const float oyr = oy - (float)dcy * fcell, ozr = oz - (float)dcz * fcell;
+            // own y, z in the row frame (origin at the centre of the row's buckets in y and z); the test
+            // below evaluates |c - o|^2 - R2lo as |c|^2 + (|o|^2 - R2lo) - 2 c.o
+            const float oyr = fmaf(-(float)dcy - 0.5f, fcell, oy), ozr = fmaf(-(float)dcz - 0.5f, fcell, oz);
+            const float Kr = fmaf(oxg, oxg, fmaf(oyr, oyr, fmaf(ozr, ozr, -P.f_R2lo)));
+            const float mx = -2.0f * oxg, my = -2.0f * oyr, mz = -2.0f * ozr;
             const uint32_t code_yz = (uint32_t)(dcy + 1) << 26 | (uint32_t)(dcz + 1) << 28;
             const int cxm1 = cx - 1;
             for (uint32_t b = lo; b < hi; b += 32) {
@@ -310,15 +317,18 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                         q = pos[jl];
                         const float cxj = cxs[jl];
                         if (SPLIT) {
-                            q.x = (float)q.x + (cxj - (float)gbx) * fcell;
-                            q.w = __int_as_float((int)cxj);
+                            const float qx = fmaf(cxj - (float)gbx - 1.5f, fcell, (float)q.x);
+                            const float qy = (float)q.y - hcell, qz = (float)q.z - hcell;
+                            q.x = qx; q.y = qy; q.z = qz;
+                            q.w = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
                         } else {
                             q.w = (double)cxj;
                         }
+                    } else if (SPLIT) {
+                        // past the end of the range: |c|^2 = +inf, which no test accepts
+                        q.x = 0.0f; q.y = 0.0f; q.z = 0.0f; q.w = __int_as_float(0x7f800000);
                     } else {
-                        // past the end of the range: a far-away sentinel that no test accepts
-                        q.x = 1.0e30f; q.y = 1.0e30f; q.z = 1.0e30f;
-                        q.w = SPLIT ? __int_as_float(-0x40000000) : -1.0e9;
+                        q.x = 1.0e30; q.y = 1.0e30; q.z = 1.0e30; q.w = -1.0e9;
                     }
                     stage[tid] = q;
                 }
@@ -336,10 +346,7 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
 #pragma unroll
                         for (int t = 0; t < 32; ++t) {
                             const Pos pj = stage[wbase + t];
-                            const float ex = (float)pj.x - oxg;
-                            const float ey = (float)pj.y - oyr;
-                            const float ez = (float)pj.z - ozr;
-                            const float dlo = fmaf(ex, ex, fmaf(ey, ey, fmaf(ez, ez, -P.f_R2lo)));
+                            const float dlo = fmaf(mx, (float)pj.x, fmaf(my, (float)pj.y, fmaf(mz, (float)pj.z, (float)pj.w + Kr)));
                             const float dhi = dlo + band_w;
                             hitm = __funnelshift_l(__float_as_uint(dlo), hitm, 1);
                             bandm = __funnelshift_l(__float_as_uint(dhi), bandm, 1);
@@ -367,7 +374,7 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                     while (bandm) {         // rounding band: own window, then exactly rounded FP64 decides
                         const int t = __ffs(bandm) - 1;
                         bandm &= bandm - 1;
-                        const int cxj = __float_as_int((float)stage[wbase + t].w);
+                        const int cxj = (int)cxs[b + (uint32_t)t];
                         if ((uint32_t)(cxj - cxm1) <= 2u &&
                             support_exact(P, xs, ys, zs, b + (uint32_t)t, xs[s], ys[s], zs[s], -1, 0.0))
                             hitm |= 1u << t;
@@ -601,11 +608,17 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
         for (int k = 0; k < 6; ++k) r6[k] = acc.get(k);
         const double wn = w + dt * r6[0];
         const double mn = m + dt * r6[1];
-        const double mvx = m * vx + dt * (r6[2] + m * P.g[0]);
-        const double mvy = m * vy + dt * (r6[3] + m * P.g[1]);
-        const double mvz = m * vz + dt * (r6[4] + m * P.g[2]);
-        const double gv = P.g[0] * vx + P.g[1] * vy + P.g[2] * vz;
-        const double mE = m * E + dt * (r6[5] + m * gv);
+        if (P.has_gravity) {   // body force m g and its power m g.v (skipped when g = 0: the same values)
+            const double gv = P.g[0] * vx + P.g[1] * vy + P.g[2] * vz;
+            r6[2] += m * P.g[0];
+            r6[3] += m * P.g[1];
+            r6[4] += m * P.g[2];
+            r6[5] += m * gv;
+        }
+        const double mvx = m * vx + dt * r6[2];
+        const double mvy = m * vy + dt * r6[3];
+        const double mvz = m * vz + dt * r6[4];
+        const double mE = m * E + dt * r6[5];
         // stress rate 2G (D - tr D / 3) + Om S - S Om (the split path evaluates it in FP32 from the
         // FP32 velocity gradient; the increment is added to the FP64 stress)
         R Lm[3][3];
@@ -613,11 +626,12 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
         for (int u = 0; u < 3; ++u)
 #pragma unroll
             for (int v = 0; v < 3; ++v) Lm[u][v] = acc.getr(6 + 3 * u + v);
+        // the stress of the step's start as the record holds it (the FP32 rounding on the split path)
         R Sr[3][3];
-        Sr[0][0] = (R)S[0]; Sr[1][1] = (R)S[1]; Sr[2][2] = (R)S[2];
-        Sr[0][1] = Sr[1][0] = (R)S[3];
-        Sr[0][2] = Sr[2][0] = (R)S[4];
-        Sr[1][2] = Sr[2][1] = (R)S[5];
+        Sr[0][0] = me.sxx; Sr[1][1] = me.syy; Sr[2][2] = me.szz;
+        Sr[0][1] = Sr[1][0] = me.sxy;
+        Sr[0][2] = Sr[2][0] = me.sxz;
+        Sr[1][2] = Sr[2][1] = me.syz;
         const R trD = Lm[0][0] + Lm[1][1] + Lm[2][2];
         const R G2 = SPLIT ? (R)(2.0f * P.f_G[mt]) : (R)(2.0 * P.G[mt]);
         const int iu[6] = {0, 1, 2, 0, 0, 1}, iv[6] = {0, 1, 2, 1, 2, 2};
@@ -647,7 +661,14 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
 #pragma unroll
             for (int q = 0; q < 6; ++q) Sn[q] *= f;
         }
-        const double inv_mn = 1.0 / mn;
+        double inv_mn;
+        if (SPLIT) {   // FP32 estimate refined by two Newton steps (relative error at the FP64 rounding level)
+            const double r0 = (double)__fdividef(1.0f, (float)mn);
+            const double r1 = fma(r0, fma(-mn, r0, 1.0), r0);
+            inv_mn = fma(r1, fma(-mn, r1, 1.0), r1);
+        } else {
+            inv_mn = 1.0 / mn;
+        }
         const double nvx = mvx * inv_mn, nvy = mvy * inv_mn, nvz = mvz * inv_mn;
         B.f[FX][s] = X + dt * vx;
         B.f[FY][s] = Y + dt * vy;
