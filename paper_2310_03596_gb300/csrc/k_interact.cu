@@ -90,14 +90,21 @@ __device__ __forceinline__ double rsqrt_r(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float rcp_r(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double rcp_r(double x) { return 1.0 / x; }
 
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
 template <class R> struct PairRes { R Fm, Fmv[3], Fe, a, n[3], du_vol; };
 
 // Pair fluxes on the canonical pair: d = x_R - x_L with L the lower sorted slot, `me` the particle
-// being updated and `oth` its neighbour, iL = (me is L). Every per-particle projection is taken on the
-// same canonical normal at both ends of the pair and every symmetric combination uses commutative
-// operations, so the two ends produce bitwise-opposite fluxes; only the Riemann inputs are ordered.
+// being updated and `oth` its neighbour, sgn = +1 when me is L, -1 when me is R. Every per-particle
+// projection is taken on the same canonical normal at both ends of the pair, every symmetric
+// combination uses commutative operations (the two Riemann sums of products are rounded product by
+// product, never fused), and the two antisymmetric differences are oriented by the exact factor sgn,
+// so the two ends produce bitwise-opposite fluxes.
 template <class R>
-__device__ __forceinline__ void pair_terms(R d0, R d1, R d2, const PIn<R> &me, const PIn<R> &oth, bool iL, R inv_h,
+__device__ __forceinline__ void pair_terms(R d0, R d1, R d2, const PIn<R> &me, const PIn<R> &oth, R sgn, R inv_h,
                                            R kdw, PairRes<R> &o) {
     const R half = R(0.5);
     const R r2 = d0 * d0 + d1 * d1 + d2 * d2;
@@ -118,13 +125,13 @@ __device__ __forceinline__ void pair_terms(R d0, R d1, R d2, const PIn<R> &me, c
     const R so2 = oth.sxz * n0 + oth.syz * n1 + oth.szz * n2 - oth.p * n2;
     const R tmn = sm0 * n0 + sm1 * n1 + sm2 * n2;
     const R ton = so0 * n0 + so1 * n1 + so2 * n2;
-    // acoustic Riemann problem, left = L, right = R
-    const R uL = iL ? um : uo, uR = iL ? uo : um;
-    const R tL = iL ? tmn : ton, tR = iL ? ton : tmn;
-    const R ZL = iL ? me.Z : oth.Z, ZR = iL ? oth.Z : me.Z;
-    const R izs = rcp_r(ZL + ZR);
-    const R us = (ZL * uL + ZR * uR + (tR - tL)) * izs;
-    const R ts = (ZR * tL + ZL * tR + ZL * ZR * (uR - uL)) * izs;
+    // acoustic Riemann problem, left = L, right = R:
+    //   u* = (ZL uL + ZR uR + (tR - tL)) / (ZL + ZR),  t* = (ZR tL + ZL tR + ZL ZR (uR - uL)) / (ZL + ZR)
+    const R izs = rcp_r(me.Z + oth.Z);
+    const R dRL_t = sgn * (ton - tmn);   // tR - tL
+    const R dRL_u = sgn * (uo - um);     // uR - uL
+    const R us = (add_rn(mul_rn(me.Z, um), mul_rn(oth.Z, uo)) + dRL_t) * izs;
+    const R ts = (add_rn(mul_rn(oth.Z, tmn), mul_rn(me.Z, ton)) + (me.Z * oth.Z) * dRL_u) * izs;
     const R du = us - half * (um + uo);
     const R rhoE = half * (me.rho + oth.rho);
     const R EE = half * (me.E + oth.E);
@@ -144,7 +151,7 @@ __device__ __forceinline__ void pair_terms(R d0, R d1, R d2, const PIn<R> &me, c
     o.Fe = wwa * (mf * EE - (TE0 * vE0 + TE1 * vE1 + TE2 * vE2));
     o.a = a;
     o.n[0] = n0; o.n[1] = n1; o.n[2] = n2;
-    o.du_vol = uR - uL;
+    o.du_vol = dRL_u;
 }
 
 // Per-particle sums. FP32: Kahan-compensated for the conserved quantities (fields 0-5: volume, mass,
@@ -400,7 +407,7 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
 // Pair kernel: list walk, wall images, integration.
 // ---------------------------------------------------------------------------------------------
 template <bool SPLIT, bool DIAG>
-__global__ void __launch_bounds__(PK_THREADS, SPLIT ? 4 : 2)
+__global__ void __launch_bounds__(PK_THREADS, SPLIT ? 5 : 2)
 k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *__restrict__ cellr,
        const typename Types<SPLIT>::Pos *__restrict__ pos, const typename Types<SPLIT>::Rec *__restrict__ rec,
        const float *__restrict__ cxs, const double *__restrict__ xs, const double *__restrict__ ys,
@@ -442,23 +449,21 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
     // operands in the same order
     auto real_pair = [&](uint32_t jj, uint32_t code, R cxj, const Pos &pj, const Rec &rj) {
         const PIn<R> oth = unpack(rj, (R)pj.w);
-        const bool iL = s < (int64_t)jj;
-        const R ax = iL ? (R)pj.x : mrx, bx = iL ? mrx : (R)pj.x;
-        const R ay = iL ? (R)pj.y : mry, by = iL ? mry : (R)pj.y;
-        const R az = iL ? (R)pj.z : mrz, bz = iL ? mrz : (R)pj.z;
+        // x_j - x_i from this end, then oriented L -> R by the exact factor sgn: both ends obtain the
+        // same canonical difference bit for bit (a - b = -(b - a) in IEEE arithmetic)
+        const R sgn = s < (int64_t)jj ? R(1) : R(-1);
         R d0, d1, d2;
         if (SPLIT) {
-            const R f = iL ? fcell : -fcell;
-            const R ex = cxj - cxf, ey = (R)((int)(code & 3u) - 1), ez = (R)((int)(code >> 2) - 1);
-            d0 = (ax - bx) + ex * f;
-            d1 = (ay - by) + ey * f;
-            d2 = (az - bz) + ez * f;
+            const R ey = (R)(int)(code & 3u) * fcell - fcell, ez = (R)(int)(code >> 2) * fcell - fcell;
+            d0 = sgn * (((R)pj.x - mrx) + (cxj - cxf) * fcell);
+            d1 = sgn * (((R)pj.y - mry) + ey);
+            d2 = sgn * (((R)pj.z - mrz) + ez);
         } else {
-            d0 = ax - bx; d1 = ay - by; d2 = az - bz;
+            d0 = sgn * ((R)pj.x - mrx); d1 = sgn * ((R)pj.y - mry); d2 = sgn * ((R)pj.z - mrz);
         }
         PairRes<R> o;
-        pair_terms<R>(d0, d1, d2, me, oth, iL, inv_h, kdw, o);
-        accumulate<R>(acc, o, iL ? R(-1) : R(1), me, oth);
+        pair_terms<R>(d0, d1, d2, me, oth, sgn, inv_h, kdw, o);
+        accumulate<R>(acc, o, -sgn, me, oth);
     };
 
     // ---- listed real neighbours, all lanes in lockstep: the set bits of the current entry give the
@@ -584,7 +589,7 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
                     }
                     mirror<R>(oth, wax);
                     PairRes<R> o;
-                    pair_terms<R>(d0, d1, d2, me, oth, true, inv_h, kdw, o);
+                    pair_terms<R>(d0, d1, d2, me, oth, R(1), inv_h, kdw, o);
                     accumulate<R>(acc, o, R(-1), me, oth);
                     ++ni;
                 }
