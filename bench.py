@@ -65,14 +65,15 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def _traffic_from_profile(kernel_src: str, profile: str):
-    """dram bytes per launch recorded in a committed ncu summary, if it was taken on this source."""
+def _traffic_from_profile(kernel_src: str, profile: str, kernel: str):
+    """dram bytes per launch of `kernel` recorded in a committed ncu summary, if it was taken on this
+    source."""
     path = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m = re.search(r"source_sha256:\s*([0-9a-f]{16,64})", txt)
-    t = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
+    t = re.search(r"dram_bytes_per_launch\.%s:\s*([0-9.eE+]+)" % re.escape(kernel), txt)
     if not m or not t:
         return None
     sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
@@ -324,10 +325,12 @@ def main():
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
     it_ms = tm["interact_ms"] / max(tm["steps"], 1)
+    pk_ms = tm["pair_ms"] / max(tm["steps"], 1)
+    nl_ms = tm["nbr_list_ms"] / max(tm["steps"], 1)
     flops_per_launch = FLOPS_PER_PAIR * pairs / args.steps
-    achieved = flops_per_launch / (it_ms * 1e-3) / 1e12
+    achieved = flops_per_launch / (pk_ms * 1e-3) / 1e12
     traffic = _traffic_from_profile(os.path.join(ROOT, "paper_2310_03596_gb300", "csrc", "k_interact.cu"),
-                                    "k_interact_taylor_bar_split.md")
+                                    "k_interact_taylor_bar_split.md", "k_pair")
     ab = algorithmic_bytes_per_particle_step(key_passes, s.K, s.swap_period)
     step_ms = ms / args.steps
     hbm_ach = ab["total"] * n / (step_ms * 1e-3) / 1e9
@@ -352,10 +355,13 @@ def main():
                  "ms_per_step": ms64 / args.fp64_steps,
                  "pair_interactions_per_s": world * (p1 - p0) / (ms64 * 1e-3),
                  "interact_ms": tm64["interact_ms"] / max(tm64["steps"], 1), "steps": args.fp64_steps},
-        "roofline": {"kernel": "interaction phase: k_nbr_list + k_pair (FP32 split), one launch each per step", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+        "roofline": {"kernel": "k_pair<split>: pair fluxes, per-particle sums, integration (one launch per step)",
+                     "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
-                     "flops_per_launch": flops_per_launch, "launch_ms": it_ms,
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sm_max_mhz, {peaks_kind})"},
+                     "flops_per_launch": flops_per_launch, "launch_ms": pk_ms,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sm_max_mhz, {peaks_kind})",
+                     "interaction_phase": {"nbr_list_ms": nl_ms, "pair_ms": pk_ms, "interact_ms": it_ms,
+                                           "achieved_over_phase": flops_per_launch / (it_ms * 1e-3) / 1e12}},
         "hbm_step": {"bytes_per_particle_step": ab, "achieved_GBps": hbm_ach, "peak_GBps": peaks["hbm_gbs"],
                      "frac": hbm_ach / peaks["hbm_gbs"], "peak_source": f"hbm_gbs ({peaks_kind})"},
         "e2e": {"value": world * n * args.steps / e2e_s, "unit": "particle-steps/s",

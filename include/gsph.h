@@ -131,9 +131,11 @@ typedef struct {
     double reorder_ms;     /* permutation into sorted order, bucket ranges, interaction records */
     double swap_ms;        /* swap heuristic passes */
     double comm_ms;        /* communication hash, flags, boundary lists */
-    double interact_ms;    /* interaction loop + integration (one kernel) */
+    double interact_ms;    /* interaction loop + integration: nbr_list_ms + pair_ms */
     int64_t steps;         /* steps recorded */
     int64_t interact_launches;
+    double nbr_list_ms;    /* of which the neighbour-list kernel */
+    double pair_ms;        /* of which the pair kernel (fluxes, integration) and the time-step reduction */
 } gsph_timings;
 
 typedef struct gsph_ctx gsph_ctx;

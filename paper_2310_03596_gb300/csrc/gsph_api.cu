@@ -33,7 +33,7 @@ cudaError_t launch_conserved(int64_t n, const State &A, double *part, double *ou
 cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n, const uint32_t *skey,
                             const uint2 *cellr, const void *pos, const void *rec, const float *cxs,
                             const double *xs, const double *ys, const double *zs, int kmax, uint2 *list,
-                            uint32_t *cnt, const uint32_t *perm, const State &A, const State &B,
+                            uint32_t *cnt, const uint32_t *perm, const State &A, const State &B, cudaEvent_t mid,
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
                             unsigned int *sig, unsigned long long *pairs, int32_t *nreal, int32_t *nimage,
                             double *rates, cudaStream_t s);
@@ -55,7 +55,7 @@ cudaError_t launch_adjoint(const DevParams &P, int64_t n, const uint32_t *skey, 
 
 using namespace gsph;
 
-enum { PH_START = 0, PH_SORT, PH_REORDER, PH_SWAP, PH_COMM, PH_INTERACT, PH_COUNT };
+enum { PH_START = 0, PH_SORT, PH_REORDER, PH_SWAP, PH_COMM, PH_LIST, PH_INTERACT, PH_COUNT };
 
 // Neighbour-list capacity per particle, in entries of one 32-candidate batch each (an interior
 // particle of the lattice has 80 real neighbours in about 20 batches; particles with more entries
@@ -278,6 +278,11 @@ static void rec_event(gsph_ctx *c, int phase, cudaStream_t s) {
     if (c->timing_used < c->timing_max) cudaEventRecord(c->ev[(size_t)c->timing_used * PH_COUNT + phase], s);
 }
 
+// The event of `phase` in the step being enqueued when timing is armed (recorded by the callee), else null.
+static cudaEvent_t phase_event(gsph_ctx *c, int phase) {
+    return c->timing_used < c->timing_max ? c->ev[(size_t)c->timing_used * PH_COUNT + phase] : nullptr;
+}
+
 static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     const DevParams &P = c->P;
     const int64_t n = c->n;
@@ -316,8 +321,8 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     rec_event(c, PH_COMM, s);
     // f-g. interaction loop fused with the integration; next dt
     GSPH_CK(launch_interact(c->split, c->cfg.diagnostics != 0, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs,
-                            c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, c->lab_s, c->mat_s, c->id_s, c->dt, c->sig, c->pairs,
-                            c->nreal, c->nimage, c->rates, s));
+                            c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, phase_event(c, PH_LIST),
+                            c->lab_s, c->mat_s, c->id_s, c->dt, c->sig, c->pairs, c->nreal, c->nimage, c->rates, s));
     GSPH_CK(launch_finalize_dt(P, c->sig, c->dt, s));
     c->launches += 3;
     rec_event(c, PH_INTERACT, s);
@@ -345,8 +350,8 @@ static gsph_status enqueue_forward_pieces(gsph_ctx *c, cudaStream_t s) {
     GSPH_CK(launch_reorder(c->split, P, n, c->skey, c->perm, c->A, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s,
                            c->cellr, c->cxs, c->pos, c->rec, c->err, s));
     GSPH_CK(launch_interact(c->split, true, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs, c->ys, c->zs,
-                            kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, c->lab_s, c->mat_s, c->id_s, c->dt,
-                            c->sig, c->pairs, c->nreal, c->nimage, c->rates, s));
+                            kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr, c->lab_s, c->mat_s, c->id_s,
+                            c->dt, c->sig, c->pairs, c->nreal, c->nimage, c->rates, s));
     c->launches += 4 + 3 * ((key_bits(P.ncell) + 7) / 8);
     c->dt_dirty = true;   // the signal-speed word now holds the scratch state's maximum
     return GSPH_OK;
@@ -693,7 +698,9 @@ gsph_status gsph_get_timings(gsph_ctx *c, gsph_timings *out) {
         out->reorder_ms += t[PH_REORDER];
         out->swap_ms += t[PH_SWAP];
         out->comm_ms += t[PH_COMM];
-        out->interact_ms += t[PH_INTERACT];
+        out->interact_ms += t[PH_LIST] + t[PH_INTERACT];
+        out->nbr_list_ms += t[PH_LIST];
+        out->pair_ms += t[PH_INTERACT];
     }
     out->steps = c->timing_used;
     out->interact_launches = c->timing_used;

@@ -478,7 +478,9 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
         if (ne > 1) nx = lp[colstep];
         int ke = 2;
         // next listed neighbour (called only while one is left): slot j, row code c; refills the mask
-        // from the entry in flight when the current one is used up
+        // from the entry in flight when the current one is used up. The record loads that follow are
+        // unconditional (a lane past its last neighbour reloads its last valid slot), which keeps the
+        // loop body free of branches around them
         auto next = [&](uint32_t &j, uint32_t &c) {
             const int t = __ffs(m) - 1;
             m &= m - 1u;
@@ -502,12 +504,10 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
             const Pos pj = p1;
             const Rec rj = r1;
             const float xj = x1;
-            if ((uint32_t)k + 1 < nlist) {
-                next(j1, c1);
-                p1 = pos[j1];
-                r1 = rec[j1];
-                if (SPLIT) x1 = cxs[j1];
-            }
+            if ((uint32_t)k + 1 < nlist) next(j1, c1);   // else j1 stays a valid slot
+            p1 = pos[j1];
+            r1 = rec[j1];
+            if (SPLIT) x1 = cxs[j1];
             if ((uint32_t)k < nlist) real_pair(j, c, (R)xj, pj, rj);
         }
     }
@@ -713,7 +713,7 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
 cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n, const uint32_t *skey,
                             const uint2 *cellr, const void *pos, const void *rec, const float *cxs,
                             const double *xs, const double *ys, const double *zs, int kmax, uint2 *list,
-                            uint32_t *cnt, const uint32_t *perm, const State &A, const State &B,
+                            uint32_t *cnt, const uint32_t *perm, const State &A, const State &B, cudaEvent_t mid,
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
                             unsigned int *sig, unsigned long long *pairs, int32_t *nreal, int32_t *nimage,
                             double *rates, cudaStream_t s) {
@@ -726,11 +726,13 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
     if (split) {
         constexpr bool SP = true;
         k_nbr_list<SP><<<gl, NL_THREADS, 0, s>>>(GSPH_NL_ARGS);
+        if (mid) cudaEventRecord(mid, s);
         if (diag) k_pair<SP, true><<<gp, PK_THREADS, 0, s>>>(GSPH_PK_ARGS);
         else k_pair<SP, false><<<gp, PK_THREADS, 0, s>>>(GSPH_PK_ARGS);
     } else {
         constexpr bool SP = false;
         k_nbr_list<SP><<<gl, NL_THREADS, 0, s>>>(GSPH_NL_ARGS);
+        if (mid) cudaEventRecord(mid, s);
         if (diag) k_pair<SP, true><<<gp, PK_THREADS, 0, s>>>(GSPH_PK_ARGS);
         else k_pair<SP, false><<<gp, PK_THREADS, 0, s>>>(GSPH_PK_ARGS);
     }

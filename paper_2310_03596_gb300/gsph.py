@@ -71,7 +71,7 @@ class ExchangeStats(C.Structure):
 class Timings(C.Structure):
     _fields_ = [("hash_sort_ms", C.c_double), ("reorder_ms", C.c_double), ("swap_ms", C.c_double),
                 ("comm_ms", C.c_double), ("interact_ms", C.c_double), ("steps", C.c_int64),
-                ("interact_launches", C.c_int64)]
+                ("interact_launches", C.c_int64), ("nbr_list_ms", C.c_double), ("pair_ms", C.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -252,6 +252,23 @@ def test_swap_now_matches_oracle_pass():
 
 
 @pytest.mark.parametrize("precision,tol", [(gsph.FP64, 1e-12), (gsph.FP32_SPLIT, 2e-5)])
+def test_candidates_on_the_support_surface(precision, tol):
+    # h = dx on a lattice jittered by 1e-8 dx: every interior particle has six candidates at 2 dx = 2h
+    # within about 1e-8 of the support radius, far inside the FP32 rounding band, so the FP64
+    # positions decide them; neighbour counts must still match the oracle bit for bit
+    s = scenes.cube_impact(n_side=9, seed=11, jitter=1e-8)
+    s.h = s.dx
+    lo = tuple(v - 4 * s.h for v in s.pos.min(axis=0))
+    s.grid_lo = lo
+    s.grid_dims = tuple(int(np.ceil((s.pos[:, a].max() + 4 * s.h - lo[a]) / (2 * s.h))) for a in range(3))
+    d = s.pos[:, None, :] - s.pos[None, :, :]
+    rel = (d ** 2).sum(axis=2) / (2 * s.h) ** 2 - 1.0
+    assert (np.abs(rel) < 3e-5).sum() > 6 * 7 ** 3        # the band is populated (ordered pairs)
+    worst = _lockstep(s, precision, 3, tol)
+    assert max(worst.values()) <= tol
+
+
+@pytest.mark.parametrize("precision,tol", [(gsph.FP64, 1e-12), (gsph.FP32_SPLIT, 2e-5)])
 def test_dense_neighbourhoods_beyond_list_capacity(precision, tol):
     # h = 1.6 dx: about 137 neighbours per interior particle, more than the per-particle list holds,
     # so the remainder goes through the re-scan path; counts and state must still match
