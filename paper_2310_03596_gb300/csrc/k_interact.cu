@@ -154,26 +154,31 @@ __device__ __forceinline__ void pair_terms(R d0, R d1, R d2, const PIn<R> &me, c
     o.du_vol = dRL_u;
 }
 
-// Per-particle sums. FP32: Kahan-compensated for the conserved quantities (fields 0-5: volume, mass,
-// momentum, energy), plain for the velocity gradient (fields 6-14, which only feed the stress rate).
-// FP64: plain.
+// Per-particle sums. FP32: compensated for the conserved quantities (fields 0-5: volume, mass,
+// momentum, energy) in blocks - the terms of a block of 8 pairs are summed plainly into p, and fold()
+// adds the block sum to s with Kahan compensation c -, plain for the velocity gradient (fields 6-14,
+// which only feed the stress rate). FP64: plain.
 template <class R> struct Acc;
 template <> struct Acc<float> {
-    float s[kNRate], c[6];
+    float s[kNRate], c[6], p[6];
     __device__ __forceinline__ void zero() {
 #pragma unroll
         for (int k = 0; k < kNRate; ++k) s[k] = 0.f;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) c[k] = 0.f;
+        for (int k = 0; k < 6; ++k) { c[k] = 0.f; p[k] = 0.f; }
     }
     __device__ __forceinline__ void add(int k, float x) {
-        if (k < 6) {
-            const float y = x - c[k];
+        if (k < 6) p[k] += x;
+        else s[k] += x;
+    }
+    __device__ __forceinline__ void fold() {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float y = p[k] - c[k];
             const float t = s[k] + y;
             c[k] = (t - s[k]) - y;
             s[k] = t;
-        } else {
-            s[k] += x;
+            p[k] = 0.f;
         }
     }
     // the compensated sum s - c rounded once to FP32 keeps the compensation's benefit (one rounding
@@ -183,6 +188,7 @@ template <> struct Acc<float> {
 };
 template <> struct Acc<double> {
     double s[kNRate];
+    __device__ __forceinline__ void fold() {}
     __device__ __forceinline__ void zero() {
 #pragma unroll
         for (int k = 0; k < kNRate; ++k) s[k] = 0.0;
@@ -477,13 +483,14 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
         if (ne > 0) { const uint2 e = lp[0]; m = e.x; y = e.y; }
         if (ne > 1) nx = lp[colstep];
         int ke = 2;
-        // next listed neighbour (called only while one is left): slot j, row code c; refills the mask
-        // from the entry in flight when the current one is used up. The record loads that follow are
+        // next listed neighbour (called only while one is left): slot j, row code c, the highest set bit
+        // of the mask first (the order within a batch only affects rounding); refills the mask from the
+        // entry in flight when the current one is used up. The record loads that follow are
         // unconditional (a lane past its last neighbour reloads its last valid slot), which keeps the
         // loop body free of branches around them
         auto next = [&](uint32_t &j, uint32_t &c) {
-            const int t = __ffs(m) - 1;
-            m &= m - 1u;
+            const int t = 31 - __clz(m);
+            m ^= 1u << t;
             j = (y & IT_JMASK) + (uint32_t)t;
             c = y >> 26;
             if (m == 0u) {
@@ -509,6 +516,7 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
             r1 = rec[j1];
             if (SPLIT) x1 = cxs[j1];
             if ((uint32_t)k < nlist) real_pair(j, c, (R)xj, pj, rj);
+            if ((k & 7) == 7) acc.fold();
         }
     }
 
@@ -596,6 +604,7 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
             }
         }
     }
+    acc.fold();
     const int nr = (int)(nlist + nover);
 
     // ---- integration (Sec. II step g): forward Euler on the conserved variables, Jaumann-rate
