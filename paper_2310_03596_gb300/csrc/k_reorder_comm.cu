@@ -155,42 +155,43 @@ __global__ void __launch_bounds__(CM_THREADS) k_comm(DevParams P, int64_t n, con
     if (threadIdx.x < P.K_labels) block_counts[(size_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// Exclusive scan of the label-major block counts (single block; K * nblk entries), total per label
-// into label_total[0..K) and the overall total into label_total[K].
+// Exclusive scan of the label-major block counts (single block of 1024 threads; K * nblk entries), total
+// per label into label_total[0..K) and the overall total into label_total[K]. Each thread sums a chunk
+// of consecutive entries, one block-wide scan offsets the chunks, and each thread writes its chunk's
+// prefixes: one pass over the counts.
 __global__ void __launch_bounds__(1024) k_comm_scan(uint32_t *__restrict__ block_counts, int64_t entries,
                                                     int nblk, int K, unsigned long long *__restrict__ label_total) {
     __shared__ uint32_t warp_tmp[32];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    uint32_t carry = 0;
-    for (int64_t b = 0; b < entries; b += 1024) {
-        int64_t i = b + threadIdx.x;
-        uint32_t v = i < entries ? block_counts[i] : 0u;
-        uint32_t x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(kFullMask, x, o);
-            if (l >= o) x += y;
-        }
-        if (l == 31) warp_tmp[w] = x;
-        __syncthreads();
-        if (w == 0) {
-            uint32_t t = warp_tmp[l];
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(kFullMask, t, o);
-                if (l >= o) t += y;
-            }
-            warp_tmp[l] = t;
-        }
-        __syncthreads();
-        uint32_t e = carry + (w > 0 ? warp_tmp[w - 1] : 0u) + x - v;
-        if (i < entries) {
-            block_counts[i] = e;
-            // the first entry of each label row starts that label's list
-            if (i % nblk == 0) label_total[i / nblk] = e;
-        }
-        carry += warp_tmp[31];
-        __syncthreads();
+    const int64_t chunk = (entries + 1023) / 1024;
+    const int64_t b0 = (int64_t)threadIdx.x * chunk, b1 = b0 + chunk < entries ? b0 + chunk : entries;
+    uint32_t v = 0;
+    for (int64_t i = b0; i < b1; ++i) v += block_counts[i];
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFullMask, x, o);
+        if (l >= o) x += y;
     }
-    if (threadIdx.x == 0) label_total[K] = carry;
+    if (l == 31) warp_tmp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = warp_tmp[l];
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFullMask, t, o);
+            if (l >= o) t += y;
+        }
+        warp_tmp[l] = t;
+    }
+    __syncthreads();
+    uint32_t e = (w > 0 ? warp_tmp[w - 1] : 0u) + x - v;   // exclusive prefix of this chunk
+    for (int64_t i = b0; i < b1; ++i) {
+        const uint32_t c = block_counts[i];
+        block_counts[i] = e;
+        // the first entry of each label row starts that label's list
+        if (i % nblk == 0) label_total[i / nblk] = e;
+        e += c;
+    }
+    if (threadIdx.x == 1023) label_total[K] = warp_tmp[31];
 }
 
 // Stable compaction of the flagged slots into label-major lists (slot order = communication-hash
