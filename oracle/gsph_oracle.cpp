@@ -475,33 +475,38 @@ void integrate_one(const orc_params *P, StateT<T> &s, const Mat<T> *mats, int64_
     s.S[3][i] = Sn[0][1]; s.S[4][i] = Sn[0][2]; s.S[5][i] = Sn[1][2];
 }
 
-// Fixed-point position quantum for the centre of gravity: positions clamped to the grid box and
-// scaled to [0, 2^32], truncated, so sums are exact integers.
+// Fixed-point position quantum for the centre of gravity (Sec. III.A; reading): the FP32 rounding of a
+// position, clamped to the FP32 grid box [lo, lo + ext], is scaled by s = 2^24 / ext (FP32) and
+// truncated, so every quantised coordinate is an exact integer below 2^24 + 1 and the per-label sums
+// are exact in int64. Cg = lo + (sum / count) * (1 / s) in FP64.
 struct Quant {
-    double lo[3], ext[3], s[3], inv[3];
+    float lo[3], hi[3], s[3];
+    double inv[3];
 };
 Quant quant_of(const orc_params *P) {
     Quant q;
     double cell = 2.0 * P->h;
     for (int a = 0; a < 3; ++a) {
-        q.lo[a] = P->lo[a];
-        q.ext[a] = (double)P->dims[a] * cell;
-        q.s[a] = 4294967296.0 / q.ext[a];
-        q.inv[a] = q.ext[a] / 4294967296.0;
+        double ext = (double)P->dims[a] * cell;
+        q.lo[a] = (float)P->lo[a];
+        q.hi[a] = (float)(P->lo[a] + ext);
+        q.s[a] = (float)(16777216.0 / ext);
+        q.inv[a] = 1.0 / (double)q.s[a];
     }
     return q;
 }
 inline int64_t quantise(const Quant &q, int a, double x) {
-    double hi = q.lo[a] + q.ext[a];
-    double xc = std::min(std::max(x, q.lo[a]), hi);
-    double t = (xc - q.lo[a]) * q.s[a];
+    float xf = (float)x;
+    float xc = std::fmin(std::fmax(xf, q.lo[a]), q.hi[a]);   // NaN goes to lo
+    float d = xc - q.lo[a];
+    float t = d * q.s[a];
     return (int64_t)t;
 }
 
 void cg_from_sums(const Quant &q, const int64_t sum[3], int64_t cnt, double cg[3]) {
     for (int a = 0; a < 3; ++a) {
         double mean = (double)sum[a] / (double)cnt;
-        cg[a] = q.lo[a] + mean * q.inv[a];
+        cg[a] = (double)q.lo[a] + mean * q.inv[a];
     }
 }
 
@@ -674,9 +679,10 @@ int32_t orc_balancing_hash(const double own[3], const double oth[3], const doubl
     double ell = dn * 0.5;
     float u[3] = {(float)(d[0] / dn), (float)(d[1] / dn), (float)(d[2] / dn)};
     float scale = (float)(1000.0 / ell);
-    // Per particle (reading: the offset from M in FP64, rounded to FP32, then FP32 arithmetic, each
-    // operation rounded): signed distance t of the projection past the middle.
-    float e0 = (float)(p[0] - M[0]), e1 = (float)(p[1] - M[1]), e2 = (float)(p[2] - M[2]);
+    // Per particle (reading: FP32 arithmetic, each operation rounded, on the FP32 roundings of the
+    // position and of the middle): signed distance t of the projection past the middle.
+    float Mf[3] = {(float)M[0], (float)M[1], (float)M[2]};
+    float e0 = (float)p[0] - Mf[0], e1 = (float)p[1] - Mf[1], e2 = (float)p[2] - Mf[2];
     float a0 = e0 * u[0];
     float a1 = e1 * u[1];
     float a2 = e2 * u[2];

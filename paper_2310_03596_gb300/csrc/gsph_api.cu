@@ -18,7 +18,8 @@ cudaError_t launch_hash(const DevParams &P, int64_t n, const double *x, const do
 // k_reorder_comm.cu
 cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint32_t *perm,
                            const State &A, double *xs, double *ys, double *zs, uint8_t *lab_s, uint8_t *mat_s,
-                           uint32_t *id_s, uint2 *cellr, float *cxs, void *pos, void *rec, int *err, cudaStream_t s);
+                           uint32_t *id_s, uint2 *cellr, float *cxs, void *pos, void *rec, float *xf, float *yf,
+                           float *zf, int *err, cudaStream_t s);
 cudaError_t launch_comm(const DevParams &P, int64_t n, const uint32_t *skey, const uint8_t *lab_s, uint32_t *mask,
                         uint8_t *flag, uint32_t *comm, uint32_t *block_counts, unsigned long long *label_total,
                         uint32_t *blist, cudaStream_t s);
@@ -39,7 +40,9 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
                             double *rates, cudaStream_t s);
 // k_swap.cu
 size_t swap_scratch_bytes(int K, int nmat);
-cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const double *x, const double *y, const double *z,
+cudaError_t launch_round_positions(int64_t n, const double *x, const double *y, const double *z, float *xf,
+                                   float *yf, float *zf, cudaStream_t s);
+cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const float *x, const float *y, const float *z,
                              uint8_t *lab, const uint8_t *mat, const uint32_t *id, void *scratch, uint16_t *bh,
                              int *err, int grid, cudaStream_t s);
 int swap_grid_blocks();
@@ -79,6 +82,7 @@ struct gsph_ctx {
     uint32_t *mask = nullptr;
     double *xs = nullptr, *ys = nullptr, *zs = nullptr;
     float *cxs = nullptr;
+    float *xf = nullptr, *yf = nullptr, *zf = nullptr;   // FP32 roundings of the positions (swap pass)
     uint2 *nbr = nullptr;                         // neighbour lists (kNbrMax x n entries, column-major)
     uint32_t *nbr_cnt = nullptr;                  // entries per particle
     uint8_t *lab_s = nullptr, *mat_s = nullptr;
@@ -158,6 +162,7 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     A_(dalloc(c, &c->mask, C));
     A_(dalloc(c, &c->xs, N)); A_(dalloc(c, &c->ys, N)); A_(dalloc(c, &c->zs, N));
     A_(dalloc(c, &c->cxs, N));
+    A_(dalloc(c, &c->xf, N)); A_(dalloc(c, &c->yf, N)); A_(dalloc(c, &c->zf, N));
     A_(dalloc(c, &c->nbr, N * (size_t)kNbrMax));
     A_(dalloc(c, &c->nbr_cnt, N));
     A_(dalloc(c, &c->lab_s, N)); A_(dalloc(c, &c->mat_s, N)); A_(dalloc(c, &c->id_s, N));
@@ -302,14 +307,15 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     c->launches += 1 + 3 * ((key_bits(P.ncell) + 7) / 8);
     rec_event(c, PH_SORT, s);
     // sorted view, bucket ranges, interaction records
+    const bool do_swap = P.K_labels > 1 && c->cfg.swap_period > 0 && (c->step % c->cfg.swap_period) == 0;
     GSPH_CK(cudaMemsetAsync(c->cellr, 0, (size_t)P.ncell * sizeof(uint2), s));
     GSPH_CK(launch_reorder(c->split, P, n, c->skey, c->perm, c->A, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s,
-                           c->cellr, c->cxs, c->pos, c->rec, c->err, s));
+                           c->cellr, c->cxs, c->pos, c->rec, do_swap ? c->xf : nullptr, c->yf, c->zf, c->err, s));
     c->launches += 1;
     rec_event(c, PH_REORDER, s);
     // Sec. III: periodic swap heuristic on the sorted view
-    if (P.K_labels > 1 && c->cfg.swap_period > 0 && (c->step % c->cfg.swap_period) == 0) {
-        GSPH_CK(launch_swap_pass(P, n, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s, c->swap_scratch, c->bh,
+    if (do_swap) {
+        GSPH_CK(launch_swap_pass(P, n, c->xf, c->yf, c->zf, c->lab_s, c->mat_s, c->id_s, c->swap_scratch, c->bh,
                                  c->err, c->swap_grid, s));
         ++c->swap_passes;
         c->launches += swap_pass_launches(P);
@@ -348,7 +354,7 @@ static gsph_status enqueue_forward_pieces(gsph_ctx *c, cudaStream_t s) {
     c->perm = alt ? c->val1 : c->val0;
     GSPH_CK(cudaMemsetAsync(c->cellr, 0, (size_t)P.ncell * sizeof(uint2), s));
     GSPH_CK(launch_reorder(c->split, P, n, c->skey, c->perm, c->A, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s,
-                           c->cellr, c->cxs, c->pos, c->rec, c->err, s));
+                           c->cellr, c->cxs, c->pos, c->rec, nullptr, nullptr, nullptr, c->err, s));
     GSPH_CK(launch_interact(c->split, true, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs, c->ys, c->zs,
                             kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr, c->lab_s, c->mat_s, c->id_s,
                             c->dt, c->sig, c->pairs, c->nreal, c->nimage, c->rates, s));
@@ -548,10 +554,11 @@ gsph_status gsph_swap_now(gsph_ctx *c, void *stream) {
     if (c->n == 0) return GSPH_NOT_READY;
     GSPH_CK(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
-    GSPH_CK(launch_swap_pass(c->P, c->n, c->A.f[FX], c->A.f[FY], c->A.f[FZ], c->A.label, c->A.mat, c->A.id,
-                             c->swap_scratch, c->bh, c->err, c->swap_grid, s));
+    GSPH_CK(launch_round_positions(c->n, c->A.f[FX], c->A.f[FY], c->A.f[FZ], c->xf, c->yf, c->zf, s));
+    GSPH_CK(launch_swap_pass(c->P, c->n, c->xf, c->yf, c->zf, c->A.label, c->A.mat, c->A.id, c->swap_scratch, c->bh,
+                             c->err, c->swap_grid, s));
     ++c->swap_passes;
-    c->launches += swap_pass_launches(c->P);
+    c->launches += 1 + swap_pass_launches(c->P);
     return GSPH_OK;
 }
 

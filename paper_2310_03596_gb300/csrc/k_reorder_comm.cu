@@ -6,9 +6,10 @@
 namespace gsph {
 
 // ---------------------------------------------------------------------------------------------
-// Reorder: sorted slot s takes old slot o = perm[s]. Writes the sorted FP64 positions, label,
-// material and id, the bucket range of each occupied bucket (ranges of empty buckets stay 0,0 from
-// the memset), and the interaction record of the particle.
+// Reorder: sorted slot s takes old slot o = perm[s]. Writes the sorted FP64 positions (and their FP32
+// roundings when xf is given: the swap pass's inputs), label, material and id, the bucket range of each
+// occupied bucket (ranges of empty buckets stay 0,0 from the memset), and the interaction record of the
+// particle.
 // ---------------------------------------------------------------------------------------------
 template <bool SPLIT>
 __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const uint32_t *__restrict__ skey,
@@ -18,13 +19,19 @@ __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const u
                                                  uint8_t *__restrict__ mat_s, uint32_t *__restrict__ id_s,
                                                  uint2 *__restrict__ cellr, float *__restrict__ cxs,
                                                  void *__restrict__ pos_out, void *__restrict__ rec_out,
-                                                 int *__restrict__ err) {
+                                                 float *__restrict__ xf, float *__restrict__ yf,
+                                                 float *__restrict__ zf, int *__restrict__ err) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     uint32_t k = skey[s];
     uint32_t o = perm[s];
     double x = A.f[FX][o], y = A.f[FY][o], z = A.f[FZ][o];
     xs[s] = x; ys[s] = y; zs[s] = z;
+    if (xf) {
+        xf[s] = __double2float_rn(x);
+        yf[s] = __double2float_rn(y);
+        zf[s] = __double2float_rn(z);
+    }
     uint8_t lab = A.label[o], mat = A.mat[o];
     // invalid values are reported and clamped so that no later kernel indexes out of range
     if (lab >= P.K_labels) { atomicOr(err, kErrLabel); lab = 0; }
@@ -83,15 +90,16 @@ __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const u
 
 cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint32_t *perm,
                            const State &A, double *xs, double *ys, double *zs, uint8_t *lab_s, uint8_t *mat_s,
-                           uint32_t *id_s, uint2 *cellr, float *cxs, void *pos, void *rec, int *err, cudaStream_t s) {
+                           uint32_t *id_s, uint2 *cellr, float *cxs, void *pos, void *rec, float *xf, float *yf,
+                           float *zf, int *err, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     unsigned g = (unsigned)((n + 255) / 256);
     if (split)
         k_reorder<true><<<g, 256, 0, s>>>(P, n, skey, perm, A, xs, ys, zs, lab_s, mat_s, id_s, cellr, cxs, pos, rec,
-                                          err);
+                                          xf, yf, zf, err);
     else
         k_reorder<false><<<g, 256, 0, s>>>(P, n, skey, perm, A, xs, ys, zs, lab_s, mat_s, id_s, cellr, cxs, pos, rec,
-                                           err);
+                                           xf, yf, zf, err);
     return cudaGetLastError();
 }
 

@@ -4,13 +4,14 @@
 // bounded grid barrier; a barrier that does not complete within about a second records a timeout in the
 // error word and the pass returns. For each particle type (one pass over all particles when the scene
 // has one material) and each label pair (a, b) in lexicographic order:
-//   Cg of a and b from exact fixed-point sums (positions clamped to the grid box, scaled to
-//   [0, 2^32] and truncated, summed in int64), biased towards the label's all-types Cg by alpha when
-//   there are several types (Sec. III.B). Every block derives the pair's geometry from the sums
-//   itself, with the same operations, so no block waits for another to publish it;
+//   Cg of a and b from exact fixed-point sums (the FP32 roundings of the positions clamped to the
+//   FP32 grid box, scaled to [0, 2^24] and truncated, summed in int64), biased towards the label's
+//   all-types Cg by alpha when there are several types (Sec. III.B). Every block derives the pair's
+//   geometry from the sums itself, a few threads in parallel, with the same operations, so no block
+//   waits for another to publish it;
 //   balancing hash of every particle of a w.r.t. b and of b w.r.t. a (0 on the own side of the
 //   middle of the Cg segment, 1000 beyond the other Cg, floor(1000 t / half-distance) in between, at
-//   least 1); the offset from the middle in FP64, the projection and scaling in FP32;
+//   least 1), in FP32 on the FP32 roundings of the position and of the middle;
 //   n = min(#positive on each side); the n largest hashes of each side swap labels, ties broken by
 //   the lowest persistent id. A 1001-bin histogram finds the threshold hash. When the threshold bin
 //   holds more particles than are needed, the exchange pass collects that bin into a short list, and
@@ -47,48 +48,30 @@ struct SwapScratch {
     unsigned int bar_gen;
 };
 
+// FP32 grid box lo, hi = lo + ext and scale s = 2^24 / ext per axis, and inv = 1 / s in FP64.
 struct QuantParams {
-    double lo[3], hi[3], sc[3], inv[3];
+    float lo[3], hi[3], s[3];
+    double inv[3];
 };
 
-// Exact fixed-point coordinate: clamp to [lo, lo + ext], scale by 2^32 / ext, truncate.
-__device__ __forceinline__ long long quantise(double x, double lo, double hi, double sc) {
-    const double xc = fmin(fmax(x, lo), hi);
-    return (long long)__dmul_rn(__dsub_rn(xc, lo), sc);
+// Exact fixed-point coordinate of an FP32 position: clamp to [lo, hi] (NaN goes to lo), scale, truncate.
+__device__ __forceinline__ long long quantise(float x, float lo, float hi, float s) {
+    const float xc = fminf(fmaxf(x, lo), hi);
+    return (long long)__float2ll_rz(__fmul_rn(__fsub_rn(xc, lo), s));
 }
 
-__device__ __forceinline__ void cg_of(const QuantParams &Q, const long long *sum, long long cnt, double cg[3]) {
-    for (int a = 0; a < 3; ++a) {
-        const double mean = __ddiv_rn((double)sum[a], (double)cnt);
-        cg[a] = __dadd_rn(Q.lo[a], __dmul_rn(mean, Q.inv[a]));
-    }
-}
-
-// Pair geometry for one side: middle M (FP64), unit direction u and scale 1000 / half-distance (FP32).
+// Pair geometry for one side: middle M and unit direction u from the own Cg to the other, scale
+// 1000 / half-distance, all rounded to FP32 for the per-particle hash.
 struct Side {
-    double M[3];
+    float M[3];
     float u[3];
     float scale;
 };
 
-__device__ __forceinline__ bool side_geometry(const double own[3], const double oth[3], Side &sd) {
-    double d[3];
-    for (int k = 0; k < 3; ++k) {
-        sd.M[k] = __dmul_rn(__dadd_rn(own[k], oth[k]), 0.5);
-        d[k] = __dsub_rn(oth[k], own[k]);
-    }
-    const double dn = __dsqrt_rn(dist2_rn(d[0], d[1], d[2]));
-    if (!(dn > 0.0)) return false;
-    const double ell = __dmul_rn(dn, 0.5);
-    for (int k = 0; k < 3; ++k) sd.u[k] = (float)__ddiv_rn(d[k], dn);
-    sd.scale = (float)__ddiv_rn(1000.0, ell);
-    return true;
-}
-
-__device__ __forceinline__ int balancing_hash(const Side &sd, double p0, double p1, double p2) {
-    const float e0 = (float)__dsub_rn(p0, sd.M[0]);
-    const float e1 = (float)__dsub_rn(p1, sd.M[1]);
-    const float e2 = (float)__dsub_rn(p2, sd.M[2]);
+__device__ __forceinline__ int balancing_hash(const Side &sd, float p0, float p1, float p2) {
+    const float e0 = __fsub_rn(p0, sd.M[0]);
+    const float e1 = __fsub_rn(p1, sd.M[1]);
+    const float e2 = __fsub_rn(p2, sd.M[2]);
     const float t = __fadd_rn(__fadd_rn(__fmul_rn(e0, sd.u[0]), __fmul_rn(e1, sd.u[1])), __fmul_rn(e2, sd.u[2]));
     if (!(t > 0.0f)) return 0;
     const float k = floorf(__fmul_rn(t, sd.scale));
@@ -208,8 +191,8 @@ __device__ bool grid_barrier(SwapScratch *S, unsigned nblocks, int *err) {
 }
 
 __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantParams Q, double alpha, int K, int nmat,
-                                                          const double *__restrict__ x, const double *__restrict__ y,
-                                                          const double *__restrict__ z, uint8_t *__restrict__ lab,
+                                                          const float *__restrict__ x, const float *__restrict__ y,
+                                                          const float *__restrict__ z, uint8_t *__restrict__ lab,
                                                           const uint8_t *__restrict__ mat,
                                                           const uint32_t *__restrict__ id, uint16_t *__restrict__ bh,
                                                           SwapScratch *__restrict__ S, SwapPair *__restrict__ pairs,
@@ -219,6 +202,9 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
     __shared__ uint32_t ids[2][SW_ID_BINS];
     __shared__ Side side_sh[2];
     __shared__ int act_sh;
+    __shared__ long long gn_sh[4];       // counts of a, b (this type) and of a, b (all types)
+    __shared__ double gcg_sh[4][3];      // their Cgs
+    __shared__ double gd_sh[3], gdn_sh;  // Cg_b - Cg_a, its length
     __shared__ int T_sh[2], idsel_sh[2];
     __shared__ uint32_t need_sh[2], idpre_sh[2];
     __shared__ long long dsum[2][4];   // per side: moved q0 q1 q2, count
@@ -241,9 +227,9 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
         const int t = (v && multi) ? (mat[i] < nmat ? mat[i] : 0) : 0;
         long long q0 = 0, q1 = 0, q2 = 0;
         if (v) {
-            q0 = quantise(x[i], Q.lo[0], Q.hi[0], Q.sc[0]);
-            q1 = quantise(y[i], Q.lo[1], Q.hi[1], Q.sc[1]);
-            q2 = quantise(z[i], Q.lo[2], Q.hi[2], Q.sc[2]);
+            q0 = quantise(x[i], Q.lo[0], Q.hi[0], Q.s[0]);
+            q1 = quantise(y[i], Q.lo[1], Q.hi[1], Q.s[1]);
+            q2 = quantise(z[i], Q.lo[2], Q.hi[2], Q.s[2]);
         }
         long long(*flat)[4] = &shs[0][0];
         warp_add_sums(flat, l * SW_NT + kMaxMat, v, q0, q1, q2);
@@ -265,37 +251,53 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
         for (int a = 0; a < K - 1; ++a)
             for (int b = a + 1; b < K; ++b, ++idx) {
                 SwapPair *pr = pairs + idx;
-                // -- pair geometry (every block, identical operations on the same sums)
-                if (threadIdx.x == 0) {
-                    act_sh = 0;
-                    const long long na = ((volatile long long *)&S->cnt[a][slot])[0];
-                    const long long nbb = ((volatile long long *)&S->cnt[b][slot])[0];
-                    if (na > 0 && nbb > 0) {
-                        long long sa[3], sb[3], saa[3], sab[3];
-                        for (int k = 0; k < 3; ++k) {
-                            sa[k] = ((volatile long long *)&S->sums[a][slot][k])[0];
-                            sb[k] = ((volatile long long *)&S->sums[b][slot][k])[0];
-                            saa[k] = ((volatile long long *)&S->sums[a][kMaxMat][k])[0];
-                            sab[k] = ((volatile long long *)&S->sums[b][kMaxMat][k])[0];
-                        }
-                        double ca[3], cb[3];
-                        cg_of(Q, sa, na, ca);
-                        cg_of(Q, sb, nbb, cb);
-                        if (multi) {
-                            double aa[3], ab[3];
-                            cg_of(Q, saa, ((volatile long long *)&S->cnt[a][kMaxMat])[0], aa);
-                            cg_of(Q, sab, ((volatile long long *)&S->cnt[b][kMaxMat])[0], ab);
-                            const double beta = __dsub_rn(1.0, alpha);
-                            for (int k = 0; k < 3; ++k) {
-                                ca[k] = __dadd_rn(__dmul_rn(alpha, aa[k]), __dmul_rn(beta, ca[k]));
-                                cb[k] = __dadd_rn(__dmul_rn(alpha, ab[k]), __dmul_rn(beta, cb[k]));
-                            }
-                        }
-                        const bool ga = side_geometry(ca, cb, side_sh[0]);
-                        const bool gb = side_geometry(cb, ca, side_sh[1]);
-                        act_sh = ga && gb;
+                // -- pair geometry (every block, identical operations on the same sums): counts, then the
+                // Cg components in parallel, the Cg' blend and the segment, its length, then the direction
+                // and scale. Side b's direction is the exact negation of side a's (d_b = -d_a bit for bit).
+                if (threadIdx.x < 4) {
+                    const int w = threadIdx.x, l = (w & 1) ? b : a, sl = w < 2 ? slot : kMaxMat;
+                    gn_sh[w] = ((volatile long long *)&S->cnt[l][sl])[0];
+                }
+                __syncthreads();
+                if (threadIdx.x < 12) {
+                    const int w = threadIdx.x / 3, ax = threadIdx.x % 3, l = (w & 1) ? b : a, sl = w < 2 ? slot : kMaxMat;
+                    if ((w < 2 || multi) && gn_sh[w] > 0) {
+                        const long long sm = ((volatile long long *)&S->sums[l][sl][ax])[0];
+                        const double mean = __ddiv_rn((double)sm, (double)gn_sh[w]);
+                        gcg_sh[w][ax] = __dadd_rn((double)Q.lo[ax], __dmul_rn(mean, Q.inv[ax]));
                     }
                 }
+                __syncthreads();
+                const bool have = gn_sh[0] > 0 && gn_sh[1] > 0;
+                if (have && threadIdx.x < 3) {
+                    const int ax = threadIdx.x;
+                    double ca = gcg_sh[0][ax], cb = gcg_sh[1][ax];
+                    if (multi) {   // Sec. III.B: Cg' = alpha Cg_all + (1 - alpha) Cg_type
+                        const double beta = __dsub_rn(1.0, alpha);
+                        ca = __dadd_rn(__dmul_rn(alpha, gcg_sh[2][ax]), __dmul_rn(beta, ca));
+                        cb = __dadd_rn(__dmul_rn(alpha, gcg_sh[3][ax]), __dmul_rn(beta, cb));
+                    }
+                    const float M = (float)__dmul_rn(__dadd_rn(ca, cb), 0.5);
+                    side_sh[0].M[ax] = M;
+                    side_sh[1].M[ax] = M;
+                    gd_sh[ax] = __dsub_rn(cb, ca);
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) gdn_sh = have ? __dsqrt_rn(dist2_rn(gd_sh[0], gd_sh[1], gd_sh[2])) : 0.0;
+                __syncthreads();
+                const bool act_g = have && gdn_sh > 0.0;
+                if (act_g && threadIdx.x < 4) {
+                    if (threadIdx.x < 3) {
+                        const float u = (float)__ddiv_rn(gd_sh[threadIdx.x], gdn_sh);
+                        side_sh[0].u[threadIdx.x] = u;
+                        side_sh[1].u[threadIdx.x] = -u;
+                    } else {
+                        const float sc = (float)__ddiv_rn(1000.0, __dmul_rn(gdn_sh, 0.5));
+                        side_sh[0].scale = sc;
+                        side_sh[1].scale = sc;
+                    }
+                }
+                if (threadIdx.x == 0) act_sh = act_g;
                 for (int k = threadIdx.x; k < 2 * SW_BINS; k += SW_THREADS) (&hs[0][0])[k] = 0;
                 __syncthreads();
                 const bool act = act_sh != 0;
@@ -425,9 +427,9 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                             if (take) {
                                 sd = side;
                                 lab[i] = (uint8_t)(side == 0 ? b : a);
-                                q0 = quantise(x[i], Q.lo[0], Q.hi[0], Q.sc[0]);
-                                q1 = quantise(y[i], Q.lo[1], Q.hi[1], Q.sc[1]);
-                                q2 = quantise(z[i], Q.lo[2], Q.hi[2], Q.sc[2]);
+                                q0 = quantise(x[i], Q.lo[0], Q.hi[0], Q.s[0]);
+                                q1 = quantise(y[i], Q.lo[1], Q.hi[1], Q.s[1]);
+                                q2 = quantise(z[i], Q.lo[2], Q.hi[2], Q.s[2]);
                             }
                         }
                     }
@@ -505,9 +507,9 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                             if ((i / SW_THREADS) % nb == blockIdx.x && e.x <= idpre_sh[sd]) {
                                 mv = true;
                                 lab[i] = (uint8_t)(sd == 0 ? b : a);
-                                q0 = quantise(x[i], Q.lo[0], Q.hi[0], Q.sc[0]);
-                                q1 = quantise(y[i], Q.lo[1], Q.hi[1], Q.sc[1]);
-                                q2 = quantise(z[i], Q.lo[2], Q.hi[2], Q.sc[2]);
+                                q0 = quantise(x[i], Q.lo[0], Q.hi[0], Q.s[0]);
+                                q1 = quantise(y[i], Q.lo[1], Q.hi[1], Q.s[1]);
+                                q2 = quantise(z[i], Q.lo[2], Q.hi[2], Q.s[2]);
                             }
                         }
                         if (__any_sync(kFullMask, mv)) warp_add_sums(dsum, sd, mv, q0, q1, q2);
@@ -533,10 +535,10 @@ static QuantParams quant_params(const DevParams &P) {
     QuantParams Q;
     for (int a = 0; a < 3; ++a) {
         const double ext = (double)P.dims[a] * P.cell;
-        Q.lo[a] = P.lo[a];
-        Q.hi[a] = P.lo[a] + ext;
-        Q.sc[a] = 4294967296.0 / ext;
-        Q.inv[a] = ext / 4294967296.0;
+        Q.lo[a] = (float)P.lo[a];
+        Q.hi[a] = (float)(P.lo[a] + ext);
+        Q.s[a] = (float)(16777216.0 / ext);
+        Q.inv[a] = 1.0 / (double)Q.s[a];
     }
     return Q;
 }
@@ -550,8 +552,9 @@ int swap_grid_blocks() {
     return sms * (per < 2 ? per : 2);
 }
 
-// scratch: swap_scratch_bytes() device bytes; bh: n uint16; grid from swap_grid_blocks().
-cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const double *x, const double *y, const double *z,
+// x, y, z: FP32 roundings of the positions. scratch: swap_scratch_bytes() device bytes; bh: n uint16;
+// grid from swap_grid_blocks().
+cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const float *x, const float *y, const float *z,
                              uint8_t *lab, const uint8_t *mat, const uint32_t *id, void *scratch, uint16_t *bh,
                              int *err, int grid, cudaStream_t s) {
     if (n <= 0 || P.K_labels < 2) return cudaSuccess;
@@ -571,6 +574,24 @@ cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const double *x, con
                     (void *)&z, (void *)&lab, (void *)&mat, (void *)&id, (void *)&bh, (void *)&S, (void *)&pairs,
                     (void *)&tl, (void *)&err};
     return cudaLaunchCooperativeKernel((const void *)k_swap_pass, dim3(grid), dim3(SW_THREADS), args, 0, s);
+}
+
+// FP32 roundings of FP64 positions (the swap pass's inputs when it runs outside a step).
+__global__ void k_round_positions(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                                  const double *__restrict__ z, float *__restrict__ xf, float *__restrict__ yf,
+                                  float *__restrict__ zf) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    xf[i] = __double2float_rn(x[i]);
+    yf[i] = __double2float_rn(y[i]);
+    zf[i] = __double2float_rn(z[i]);
+}
+
+cudaError_t launch_round_positions(int64_t n, const double *x, const double *y, const double *z, float *xf,
+                                   float *yf, float *zf, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_round_positions<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, x, y, z, xf, yf, zf);
+    return cudaGetLastError();
 }
 
 // Number of particles moved by the last pass (device pointer into the scratch).
