@@ -50,8 +50,11 @@ def algorithmic_bytes_per_particle_step(key_passes: int, K: int, swap_every: int
         "interact": rec + 8 + state + 24 + 6 + state,     # own record, key/perm, state in, state out
     }
     if K > 1 and swap_every > 0:
+        # the reorder writes the FP32 positions (12 B); the pass reads them and the labels once for the
+        # Cg sums, and per label pair the pair's particles (2/K of all) read position, label, material
+        # and id and write their balancing hash
         pairs = K * (K - 1) // 2
-        b["swap"] = pairs * (2.0 / K) * (24 + 1 + 1 + 4 + 2) / swap_every
+        b["swap"] = (12 + 12 + 1 + pairs * (2.0 / K) * (12 + 1 + 1 + 4 + 2)) / swap_every
     b["total"] = sum(b.values())
     return b
 
