@@ -252,7 +252,7 @@ def main():
     sol = gsph.Solver.from_scene(s, precision=gsph.FP32_SPLIT, device=local, stream=stream)
     n = s.n
     _, ncell = sol.sizes()
-    key_passes = (int(ncell).bit_length() + 7) // 8
+    key_passes = (int(ncell).bit_length() + 8) // 9   # radix passes of at most 9 bits
 
     sol.step(args.warmup, stream)
     sol.sync(stream)

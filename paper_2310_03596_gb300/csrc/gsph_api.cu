@@ -13,6 +13,7 @@ namespace gsph {
 cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t *hist, uint32_t *tot,
                              int64_t n, int bits, cudaStream_t s, bool *in_alt);
 size_t radix_hist_words(int64_t n);
+int radix_passes(int bits);
 cudaError_t launch_hash(const DevParams &P, int64_t n, const double *x, const double *y, const double *z,
                         uint32_t *key, uint32_t *val, unsigned long long *garbage, cudaStream_t s);
 // k_reorder_comm.cu
@@ -157,7 +158,7 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     A_(dalloc(c, &c->key0, N)); A_(dalloc(c, &c->val0, N));
     A_(dalloc(c, &c->key1, N)); A_(dalloc(c, &c->val1, N));
     A_(dalloc(c, &c->hist, radix_hist_words(n)));
-    A_(dalloc(c, &c->tot, 256));
+    A_(dalloc(c, &c->tot, 512));   // one total per digit value (digits of at most 9 bits)
     A_(dalloc(c, &c->cellr, C));
     A_(dalloc(c, &c->mask, C));
     A_(dalloc(c, &c->xs, N)); A_(dalloc(c, &c->ys, N)); A_(dalloc(c, &c->zs, N));
@@ -304,7 +305,7 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     GSPH_CK(radix_sort_pairs(c->key0, c->val0, c->key1, c->val1, c->hist, c->tot, n, key_bits(P.ncell), s, &alt));
     c->skey = alt ? c->key1 : c->key0;
     c->perm = alt ? c->val1 : c->val0;
-    c->launches += 1 + 3 * ((key_bits(P.ncell) + 7) / 8);
+    c->launches += 1 + 3 * radix_passes(key_bits(P.ncell));
     rec_event(c, PH_SORT, s);
     // sorted view, bucket ranges, interaction records
     const bool do_swap = P.K_labels > 1 && c->cfg.swap_period > 0 && (c->step % c->cfg.swap_period) == 0;
@@ -358,7 +359,7 @@ static gsph_status enqueue_forward_pieces(gsph_ctx *c, cudaStream_t s) {
     GSPH_CK(launch_interact(c->split, true, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs, c->ys, c->zs,
                             kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr, c->lab_s, c->mat_s, c->id_s,
                             c->dt, c->sig, c->pairs, c->nreal, c->nimage, c->rates, s));
-    c->launches += 4 + 3 * ((key_bits(P.ncell) + 7) / 8);
+    c->launches += 4 + 3 * radix_passes(key_bits(P.ncell));
     c->dt_dirty = true;   // the signal-speed word now holds the scratch state's maximum
     return GSPH_OK;
 }

@@ -1,12 +1,13 @@
 // k_sort.cu - bucket hash (Sec. I) and the LSD radix sort of (hash, slot) pairs (Sec. I).
 //
-// Radix sort: 8-bit digits, one pass per digit. Each pass is three launches:
+// Radix sort: ceil(bits / 9) passes of equal digits of at most 9 bits (18-bit bucket hashes: two passes
+// of 9), the last digit masked to the requested bits. Each pass is three launches:
 //   k_rs_hist    per-tile digit histogram (tile = 4096 keys), warp-aggregated shared atomics;
-//   k_rs_rowscan one block per digit: exclusive scan of that digit's per-tile counts, digit total;
+//   k_rs_rowscan one block per digit value: exclusive scan of its per-tile counts, digit total;
 //   k_rs_scatter reloads the tile, ranks each key among equal digits in tile order (warp match_any,
 //                per-warp counters, cross-warp prefix), scatters keys and values.
 // The ranking follows tile order, so every pass is stable and the sort is stable overall.
-// Bytes per key per pass: 4 (hist) + 8 read + 8 written (scatter) + 2*4*256/4096 (counts).
+// Bytes per key per pass: 4 (hist) + 8 read + 8 written (scatter) + 2*4*bins/4096 (counts).
 #include <mutex>
 
 #include "gsph_internal.cuh"
@@ -17,7 +18,8 @@ constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_IPT = 16;
 constexpr int RS_TILE = RS_THREADS * RS_IPT;
-constexpr int RS_BINS = 256;
+constexpr int RS_MAX_DIGIT = 9;
+constexpr int RS_BINS = 1 << RS_MAX_DIGIT;   // histogram rows allocated per tile (the widest digit)
 
 // Item order inside a tile: warp-major, then round, then lane (each round reads 32 consecutive
 // keys, so loads are coalesced and the item order is the key order).
@@ -25,10 +27,12 @@ __device__ __forceinline__ int64_t rs_item(int64_t tile_base, int w, int r, int 
     return tile_base + (int64_t)w * (32 * RS_IPT) + r * 32 + l;
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t *__restrict__ keys, int64_t n,
-                                                        int shift, uint32_t *__restrict__ hist, int nblk) {
-    __shared__ uint32_t sh[RS_BINS];
-    for (int i = threadIdx.x; i < RS_BINS; i += RS_THREADS) sh[i] = 0;
+template <int DIG>
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t *__restrict__ keys, int64_t n, int shift,
+                                                        uint32_t dmask, uint32_t *__restrict__ hist, int nblk) {
+    constexpr int BINS = 1 << DIG;
+    __shared__ uint32_t sh[BINS];
+    for (int i = threadIdx.x; i < BINS; i += RS_THREADS) sh[i] = 0;
     __syncthreads();
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int64_t base = (int64_t)blockIdx.x * RS_TILE;
@@ -36,12 +40,12 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t *__restri
     for (int r = 0; r < RS_IPT; ++r) {
         int64_t idx = rs_item(base, w, r, l);
         bool valid = idx < n;
-        uint32_t d = valid ? (__ldg(keys + idx) >> shift) & 0xffu : 0xffffffffu;
+        uint32_t d = valid ? (__ldg(keys + idx) >> shift) & dmask : 0xffffffffu;
         unsigned peers = __match_any_sync(kFullMask, d);
         if (valid && (__ffs(peers) - 1) == l) atomicAdd(&sh[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < RS_BINS; i += RS_THREADS) hist[(size_t)i * nblk + blockIdx.x] = sh[i];
+    for (int i = threadIdx.x; i < BINS; i += RS_THREADS) hist[(size_t)i * nblk + blockIdx.x] = sh[i];
 }
 
 // Block-wide exclusive scan helper (blockDim.x == 1024); returns the exclusive prefix of v and
@@ -88,21 +92,31 @@ __global__ void __launch_bounds__(1024) k_rs_rowscan(uint32_t *__restrict__ hist
     if (threadIdx.x == 0) tot[blockIdx.x] = carry;
 }
 
+template <int DIG>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *__restrict__ kin,
                                                            const uint32_t *__restrict__ vin,
                                                            uint32_t *__restrict__ kout,
-                                                           uint32_t *__restrict__ vout, int64_t n,
-                                                           int shift, const uint32_t *__restrict__ hist,
+                                                           uint32_t *__restrict__ vout, int64_t n, int shift,
+                                                           uint32_t dmask, const uint32_t *__restrict__ hist,
                                                            const uint32_t *__restrict__ tot, int nblk) {
-    __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
-    __shared__ uint32_t base_sh[RS_BINS];
+    constexpr int BINS = 1 << DIG;
+    constexpr int DPT = BINS / RS_THREADS;   // digit values per thread in the per-digit phases
+    static_assert(DPT >= 1 && BINS % RS_THREADS == 0, "digit width");
+    __shared__ uint32_t wcnt[RS_WARPS][BINS];
+    __shared__ uint32_t base_sh[BINS];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    // digit bases: exclusive scan of the digit totals plus this tile's exclusive offset
+    // digit bases: exclusive scan of the digit totals plus this tile's exclusive offset; thread t
+    // holds digits t*DPT .. t*DPT + DPT - 1
     {
-        const int d = threadIdx.x;  // RS_THREADS == RS_BINS
-        uint32_t t = tot[d];
-        uint32_t x = t;
+        const int d0 = threadIdx.x * DPT;
+        uint32_t loc[DPT], sum = 0;
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+            loc[q] = sum;
+            sum += tot[d0 + q];
+        }
+        uint32_t x = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t y = __shfl_up_sync(kFullMask, x, o);
@@ -110,11 +124,15 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *__res
         }
         __shared__ uint32_t ws[RS_WARPS];
         if (l == 31) ws[w] = x;
-        for (int k = 0; k < RS_WARPS; ++k) wcnt[k][d] = 0;
+#pragma unroll
+        for (int q = 0; q < DPT; ++q)
+            for (int k = 0; k < RS_WARPS; ++k) wcnt[k][d0 + q] = 0;
         __syncthreads();
         uint32_t pre = 0;
         for (int k = 0; k < w; ++k) pre += ws[k];
-        base_sh[d] = pre + x - t + hist[(size_t)d * nblk + blockIdx.x];
+        pre += x - sum;
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) base_sh[d0 + q] = pre + loc[q] + hist[(size_t)(d0 + q) * nblk + blockIdx.x];
     }
     __syncthreads();
     uint32_t key[RS_IPT], val[RS_IPT], rank[RS_IPT];
@@ -127,7 +145,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *__res
     }
 #pragma unroll
     for (int r = 0; r < RS_IPT; ++r) {
-        uint32_t d = (key[r] >> shift) & 0xffu;
+        uint32_t d = (key[r] >> shift) & dmask;
         unsigned peers = __match_any_sync(kFullMask, d);
         uint32_t before = wcnt[w][d];
         rank[r] = before + __popc(peers & lanemask_lt());
@@ -136,8 +154,9 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *__res
         __syncwarp();
     }
     __syncthreads();
-    {
-        const int d = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+        const int d = threadIdx.x * DPT + q;
         uint32_t run = 0;
 #pragma unroll
         for (int k = 0; k < RS_WARPS; ++k) {
@@ -151,7 +170,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *__res
     for (int r = 0; r < RS_IPT; ++r) {
         int64_t idx = rs_item(base, w, r, l);
         if (idx < n) {
-            uint32_t d = (key[r] >> shift) & 0xffu;
+            uint32_t d = (key[r] >> shift) & dmask;
             uint32_t pos = base_sh[d] + wcnt[w][d] + rank[r];
             kout[pos] = key[r];
             vout[pos] = val[r];
@@ -184,18 +203,29 @@ size_t radix_hist_words(int64_t n) { return (size_t)RS_BINS * (size_t)(rs_nblk(n
 
 // Sorts (k0, v0) by the low `bits` bits using (k1, v1) as the other buffer. Returns true when the
 // result ends in (k1, v1).
+int radix_passes(int bits) { return (bits + RS_MAX_DIGIT - 1) / RS_MAX_DIGIT; }
+
 cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t *hist,
                              uint32_t *tot, int64_t n, int bits, cudaStream_t s, bool *in_alt) {
     *in_alt = false;
     if (n <= 0) return cudaSuccess;
     int nblk = rs_nblk(n);
-    int passes = (bits + 7) / 8;
+    const int passes = radix_passes(bits);
+    const int dig = (bits + passes - 1) / passes;   // <= 9
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
     for (int p = 0; p < passes; ++p) {
-        int shift = 8 * p;
-        k_rs_hist<<<nblk, RS_THREADS, 0, s>>>(ki, n, shift, hist, nblk);
-        k_rs_rowscan<<<RS_BINS, 1024, 0, s>>>(hist, nblk, tot);
-        k_rs_scatter<<<nblk, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, hist, tot, nblk);
+        const int shift = dig * p;
+        const int width = bits - shift < dig ? bits - shift : dig;
+        const uint32_t dmask = (1u << width) - 1u;
+        if (dig > 8) {
+            k_rs_hist<9><<<nblk, RS_THREADS, 0, s>>>(ki, n, shift, dmask, hist, nblk);
+            k_rs_rowscan<<<1 << 9, 1024, 0, s>>>(hist, nblk, tot);
+            k_rs_scatter<9><<<nblk, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, dmask, hist, tot, nblk);
+        } else {
+            k_rs_hist<8><<<nblk, RS_THREADS, 0, s>>>(ki, n, shift, dmask, hist, nblk);
+            k_rs_rowscan<<<1 << 8, 1024, 0, s>>>(hist, nblk, tot);
+            k_rs_scatter<8><<<nblk, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, dmask, hist, tot, nblk);
+        }
         uint32_t *t = ki; ki = ko; ko = t;
         t = vi; vi = vo; vo = t;
     }
@@ -259,6 +289,7 @@ constexpr int64_t kNoAllocMaxN = (int64_t)1 << 20;
 constexpr size_t kNoAllocKeyBytes = (size_t)kNoAllocMaxN * 4;
 constexpr size_t kNoAllocHistBytes = (size_t)gsph::RS_BINS * (size_t)(kNoAllocMaxN / gsph::RS_TILE) * 4;
 constexpr size_t kNoAllocBytes = 2 * kNoAllocKeyBytes + kNoAllocHistBytes + gsph::RS_BINS * 4;
+static_assert(kNoAllocBytes == (size_t)GSPH_SORT_NOALLOC_BYTES, "GSPH_SORT_NOALLOC_BYTES in gsph.h");
 static_assert(kNoAllocKeyBytes % 256 == 0 && kNoAllocHistBytes % 256 == 0, "256-byte aligned sections");
 
 static __device__ __align__(256) unsigned char g_sort_scratch[kNoAllocBytes];

@@ -76,6 +76,16 @@ def test_radix_sort_matches_stable_argsort():
         perm = np.argsort(k, kind="stable")
         assert np.array_equal(keys.cpu().numpy().view(np.uint32), k[perm])
         assert np.array_equal(vals.cpu().numpy(), perm.astype(np.int32))
+    # only the low key_bits bits decide: keys with random higher bits, digit widths 8 and 9
+    for n, bits in [(50_001, 9), (70_000, 13), (65_537, 18), (9_999, 27)]:
+        k = rng.integers(0, 2 ** 32, size=n, dtype=np.uint64).astype(np.uint32)
+        keys = torch.from_numpy(k.view(np.int32)).cuda()
+        vals = torch.arange(n, dtype=torch.int32, device="cuda")
+        gsph.radix_sort_pairs(keys, vals, bits)
+        torch.cuda.synchronize()
+        perm = np.argsort(k & np.uint32((1 << bits) - 1), kind="stable")
+        assert np.array_equal(vals.cpu().numpy(), perm.astype(np.int32)), bits
+        assert np.array_equal(keys.cpu().numpy().view(np.uint32), k[perm]), bits
 
 
 @pytest.mark.parametrize("precision,tol", [(gsph.FP64, 1e-12), (gsph.FP32_SPLIT, 2e-5)])
