@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 # momentum and energy fluxes) plus the per-particle accumulation of volume, mass, momentum, energy
 # and velocity-gradient rates (60), counted on the oracle's pair function as written.
 FLOPS_PER_PAIR = 220
+LINK_GBPS = 900.0   # modelled inter-GPU link bandwidth per direction (NVLink 5 class), for the overlap report
 SMS, FP32_LANES = 152, 128
 
 
@@ -217,6 +218,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--overlap-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -299,6 +301,33 @@ def main():
     tm64 = sol64.timings()
     sol64.close()
 
+    # the interaction in the order of Sec. II steps d-f (two passes, halo gather on a second stream)
+    solo = gsph.Solver.from_scene(s, device=local, stream=stream, overlap=True)
+    solo.step(3, stream)
+    solo.sync(stream)
+    solo.set_timing(args.overlap_steps)
+    solo.step(args.overlap_steps, stream)
+    solo.sync(stream)
+    tmo = solo.timings()
+    sto = solo.exchange_stats(stream)
+    solo.close()
+    ko = max(tmo["steps"], 1)
+    recv = sto["boundary_total"] * (s.K - 1) / s.K * sto["record_bytes"]   # bytes one GPU receives per step
+    link_ms = recv / (LINK_GBPS * 1e9) * 1e3
+    overlap = {
+        "what": "Sec. II steps d-f on one device: pairs within a label while the MGPU boundary set is gathered "
+                "into a halo buffer on a second (high-priority) stream, then the boundary particles' pairs "
+                "across labels from the halo",
+        "local_ms": tmo["local_ms"] / ko, "boundary_ms": tmo["boundary_ms"] / ko,
+        "halo_gather_ms": tmo["halo_ms"] / ko,
+        "pair_two_pass_ms": tmo["pair_ms"] / ko, "pair_one_pass_ms": tm["pair_ms"] / max(tm["steps"], 1),
+        "boundary_total": sto["boundary_total"], "boundary_bytes_received_per_gpu": recv,
+        "link_model": f"{LINK_GBPS:.0f} GB/s per direction per GPU (NVLink 5 class)",
+        "link_ms_model": link_ms,
+        "hidden_fraction_model": min(1.0, (tmo["local_ms"] / ko) / link_ms) if link_ms > 0 else 1.0,
+        "steps": args.overlap_steps,
+    }
+
     # end to end through the public API with host buffers: upload the particle set from pinned host
     # memory, run the steps, read the whole state back
     pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
@@ -372,6 +401,7 @@ def main():
                 "what": "upload of the particle set from pinned host memory, the steps, read-back of the "
                         "15 state fields, through the public API"},
         "gpu_launches": launches,
+        "overlap": overlap,
         "clocks": ck,
         "exchange": {k: st1[k] for k in ("boundary_total", "exchange_fraction", "bytes_boundary_broadcast",
                                          "swapped_last_pass", "swap_passes")},

@@ -80,6 +80,13 @@ typedef struct {
     int32_t precision;          /* gsph_precision */
     int32_t device;             /* CUDA device ordinal */
     int32_t diagnostics;        /* 1: keep neighbour counts and rates of the last step */
+    int32_t overlap;            /* 1: run the interaction in the order of Sec. II steps d-f: the pairs of
+                                   particles with neighbours of their own label, while the MGPU boundary
+                                   set's records are gathered into a halo buffer on a second stream (the
+                                   broadcast of step d on one device), then each boundary particle's pairs
+                                   with other labels, their records read from the halo. Same results up to
+                                   the order of the sums; 0: one pass over all pairs (faster on one GPU) */
+    int32_t pad2;
 } gsph_config;
 
 typedef enum {
@@ -135,7 +142,12 @@ typedef struct {
     int64_t steps;         /* steps recorded */
     int64_t interact_launches;
     double nbr_list_ms;    /* of which the neighbour-list kernel */
-    double pair_ms;        /* of which the pair kernel (fluxes, integration) and the time-step reduction */
+    double pair_ms;        /* of which the pair kernel(s) (fluxes, integration) and the time-step reduction */
+    /* overlap = 1 only: the two interaction passes on the launch stream, and the halo gather on the
+       second stream (events there), which runs concurrently with the first pass */
+    double local_ms;       /* pairs within a label, integration of particles without other labels near */
+    double boundary_ms;    /* pairs across labels from the halo, integration of the boundary particles */
+    double halo_ms;        /* gather of the boundary set's records into the halo buffer */
 } gsph_timings;
 
 typedef struct gsph_ctx gsph_ctx;

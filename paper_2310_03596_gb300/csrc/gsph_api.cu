@@ -23,7 +23,7 @@ cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint
                            float *zf, int *err, cudaStream_t s);
 cudaError_t launch_comm(const DevParams &P, int64_t n, const uint32_t *skey, const uint8_t *lab_s, uint32_t *mask,
                         uint8_t *flag, uint32_t *comm, uint32_t *block_counts, unsigned long long *label_total,
-                        uint32_t *blist, cudaStream_t s);
+                        uint32_t *blist, uint32_t *hidx, cudaStream_t s);
 int comm_blocks(int64_t n);
 cudaError_t launch_init(const DevParams &P, int64_t n, const double *pos, const double *vel, const double *vol,
                         const uint8_t *mat, const uint8_t *lab, const State &A, int *err, cudaStream_t s);
@@ -38,7 +38,7 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
                             uint32_t *cnt, const uint32_t *perm, const State &A, const State &B, cudaEvent_t mid,
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
                             unsigned int *sig, unsigned long long *pairs, int32_t *nreal, int32_t *nimage,
-                            double *rates, cudaStream_t s);
+                            double *rates, const OverlapBufs *ov, cudaStream_t s);
 // k_swap.cu
 size_t swap_scratch_bytes(int K, int nmat);
 cudaError_t launch_round_positions(int64_t n, const double *x, const double *y, const double *z, float *xf,
@@ -59,7 +59,9 @@ cudaError_t launch_adjoint(const DevParams &P, int64_t n, const uint32_t *skey, 
 
 using namespace gsph;
 
-enum { PH_START = 0, PH_SORT, PH_REORDER, PH_SWAP, PH_COMM, PH_LIST, PH_INTERACT, PH_COUNT };
+enum { PH_START = 0, PH_SORT, PH_REORDER, PH_SWAP, PH_COMM, PH_LIST, PH_INTERACT,
+       PH_LOCAL, PH_HALO0, PH_HALO1,   // two-pass order only: end of the first pass; halo gather on the aux stream
+       PH_COUNT };
 
 // Neighbour-list capacity per particle, in entries of one 32-candidate batch each (an interior
 // particle of the lattice has 80 real neighbours in about 20 batches; particles with more entries
@@ -91,6 +93,14 @@ struct gsph_ctx {
     void *pos = nullptr, *rec = nullptr;
     uint8_t *flag = nullptr;
     uint32_t *comm = nullptr, *blist = nullptr, *bcounts = nullptr;
+    // two-pass interaction order (cfg.overlap)
+    uint32_t *hidx = nullptr;
+    void *hpos = nullptr, *hrec = nullptr, *part = nullptr;
+    float *hcx = nullptr;
+    int32_t *part_cnt = nullptr;
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    unsigned gather_grid = 0, boundary_grid = 0;
     unsigned long long *label_off = nullptr;   // K + 1
     unsigned long long *garbage = nullptr;
     unsigned int *sig = nullptr;
@@ -193,6 +203,19 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     A_(dalloc(c, &c->bh, N));
     A_(dalloc(c, &c->cons_part, ((N + 255) / 256 + 1) * 6));
     A_(dalloc(c, &c->cons_out, 6));
+    if (c->cfg.overlap) {
+        A_(dalloc(c, &c->hidx, N));
+        if (c->split) {
+            A_(dalloc(c, (float4 **)&c->hpos, N));
+            A_(dalloc(c, (RecF **)&c->hrec, N));
+        } else {
+            A_(dalloc(c, (D4 **)&c->hpos, N));
+            A_(dalloc(c, (RecD **)&c->hrec, N));
+        }
+        A_(dalloc(c, &c->hcx, N));
+        A_(dalloc(c, (char **)&c->part, N * 120));   // 21 floats or 15 doubles per boundary particle
+        A_(dalloc(c, &c->part_cnt, 2 * N));
+    }
 #undef A_
     e = cudaMemset(c->err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->garbage, 0, sizeof(unsigned long long));
@@ -221,6 +244,7 @@ static bool config_ok(const gsph_config *c) {
         if (c->walls[k].axis < 0 || c->walls[k].axis > 2 || !std::isfinite(c->walls[k].pos)) return false;
     if (c->precision != GSPH_FP64 && c->precision != GSPH_FP32_SPLIT) return false;
     if (c->swap_period < 0) return false;
+    if (c->overlap != 0 && c->overlap != 1) return false;
     if (!(c->alpha >= 0.0 && c->alpha <= 1.0)) return false;
     return true;
 }
@@ -323,13 +347,22 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     }
     rec_event(c, PH_SWAP, s);
     // b-d. communication hash, MGPU boundary flags and set
-    GSPH_CK(launch_comm(P, n, c->skey, c->lab_s, c->mask, c->flag, c->comm, c->bcounts, c->label_off, c->blist, s));
+    GSPH_CK(launch_comm(P, n, c->skey, c->lab_s, c->mask, c->flag, c->comm, c->bcounts, c->label_off, c->blist,
+                        c->hidx, s));
     c->launches += 4;
     rec_event(c, PH_COMM, s);
     // f-g. interaction loop fused with the integration; next dt
+    OverlapBufs ov{};
+    if (c->cfg.overlap) {
+        ov = OverlapBufs{c->flag, c->blist, c->label_off + P.K_labels, c->hidx, c->hpos, c->hrec, c->hcx, c->part,
+                         c->part_cnt, c->aux, c->ev_fork, c->ev_join, phase_event(c, PH_HALO0),
+                         phase_event(c, PH_HALO1), phase_event(c, PH_LOCAL), c->gather_grid, c->boundary_grid};
+    }
     GSPH_CK(launch_interact(c->split, c->cfg.diagnostics != 0, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs,
                             c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, phase_event(c, PH_LIST),
-                            c->lab_s, c->mat_s, c->id_s, c->dt, c->sig, c->pairs, c->nreal, c->nimage, c->rates, s));
+                            c->lab_s, c->mat_s, c->id_s, c->dt, c->sig, c->pairs, c->nreal, c->nimage, c->rates,
+                            c->cfg.overlap ? &ov : nullptr, s));
+    if (c->cfg.overlap) c->launches += 2;   // halo gather, second pair pass
     GSPH_CK(launch_finalize_dt(P, c->sig, c->dt, s));
     c->launches += 3;
     rec_event(c, PH_INTERACT, s);
@@ -358,7 +391,7 @@ static gsph_status enqueue_forward_pieces(gsph_ctx *c, cudaStream_t s) {
                            c->cellr, c->cxs, c->pos, c->rec, nullptr, nullptr, nullptr, c->err, s));
     GSPH_CK(launch_interact(c->split, true, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs, c->ys, c->zs,
                             kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr, c->lab_s, c->mat_s, c->id_s,
-                            c->dt, c->sig, c->pairs, c->nreal, c->nimage, c->rates, s));
+                            c->dt, c->sig, c->pairs, c->nreal, c->nimage, c->rates, nullptr, s));
     c->launches += 4 + 3 * radix_passes(key_bits(P.ncell));
     c->dt_dirty = true;   // the signal-speed word now holds the scratch state's maximum
     return GSPH_OK;
@@ -418,6 +451,21 @@ gsph_status gsph_create(const gsph_config *cfg, gsph_ctx **out) {
             return GSPH_CUDA_ERROR;
         }
     }
+    if (cfg->overlap) {
+        // the halo gather runs at the highest stream priority, so its few blocks are scheduled ahead of
+        // the first pair pass's and the gather (the broadcast) completes early in that pass
+        int sms = 0, prio_lo = 0, prio_hi = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg->device) != cudaSuccess ||
+            cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            gsph_destroy(c);
+            return GSPH_CUDA_ERROR;
+        }
+        c->gather_grid = (unsigned)(2 * sms);     // 256-thread blocks, grid-stride over the boundary set
+        c->boundary_grid = (unsigned)(5 * sms);   // the pair kernel's resident blocks, grid-stride
+    }
     *out = c;
     return GSPH_OK;
 }
@@ -428,6 +476,9 @@ void gsph_destroy(gsph_ctx *c) {
     cudaDeviceSynchronize();
     free_buffers(c);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->aux) cudaStreamDestroy(c->aux);
     delete c;
 }
 
@@ -701,7 +752,16 @@ gsph_status gsph_get_timings(gsph_ctx *c, gsph_timings *out) {
         cudaEvent_t *e = &c->ev[(size_t)k * PH_COUNT];
         GSPH_CK(cudaEventSynchronize(e[PH_INTERACT]));
         float t[PH_COUNT] = {0};
-        for (int p = 1; p < PH_COUNT; ++p) GSPH_CK(cudaEventElapsedTime(&t[p], e[p - 1], e[p]));
+        for (int p = 1; p <= PH_INTERACT; ++p) GSPH_CK(cudaEventElapsedTime(&t[p], e[p - 1], e[p]));
+        if (c->cfg.overlap) {
+            float tl = 0.f, tb = 0.f, th = 0.f;
+            GSPH_CK(cudaEventElapsedTime(&tl, e[PH_LIST], e[PH_LOCAL]));
+            GSPH_CK(cudaEventElapsedTime(&tb, e[PH_LOCAL], e[PH_INTERACT]));
+            GSPH_CK(cudaEventElapsedTime(&th, e[PH_HALO0], e[PH_HALO1]));
+            out->local_ms += tl;
+            out->boundary_ms += tb;
+            out->halo_ms += th;
+        }
         out->hash_sort_ms += t[PH_SORT];
         out->reorder_ms += t[PH_REORDER];
         out->swap_ms += t[PH_SWAP];

@@ -44,6 +44,22 @@ struct DevParams {
     float f_rho0[kMaxMat], f_K[kMaxMat], f_G[kMaxMat], f_Mmod[kMaxMat];
 };
 
+// Buffers, stream and events of the two-pass interaction order (Sec. II steps d-f), host side.
+struct OverlapBufs {
+    const uint8_t *flag;                 // MGPU boundary flag per slot
+    const uint32_t *blist;               // boundary list (halo index -> slot)
+    const unsigned long long *btotal;    // boundary set size (device)
+    const uint32_t *hidx;                // slot -> halo index
+    void *hpos, *hrec;                   // halo records (interaction record layout of the path)
+    float *hcx;                          // halo bucket x
+    void *part;                          // parked partial sums, 120 bytes per particle
+    int32_t *part_cnt;                   // parked neighbour counts, 2 per particle
+    cudaStream_t aux;                    // the second stream (halo gather)
+    cudaEvent_t ev_fork, ev_join;        // launch stream -> aux, aux -> launch stream
+    cudaEvent_t ev_halo0, ev_halo1, ev_local;   // timing only (null when not timing)
+    unsigned gather_grid, boundary_grid;
+};
+
 // FP64 state in structure-of-arrays form.
 struct State {
     double *f[15];           // x y z vx vy vz w m E sxx syy szz sxy sxz syz

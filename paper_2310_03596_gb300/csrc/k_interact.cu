@@ -181,6 +181,19 @@ template <> struct Acc<float> {
             p[k] = 0.f;
         }
     }
+    // parked sums of the two-pass order (after fold): field f of halo index h at b[f * n + h]
+    __device__ __forceinline__ void store(float *b, int64_t n, int64_t h) const {
+#pragma unroll
+        for (int k = 0; k < kNRate; ++k) b[k * n + h] = s[k];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) b[(kNRate + k) * n + h] = c[k];
+    }
+    __device__ __forceinline__ void load(const float *b, int64_t n, int64_t h) {
+#pragma unroll
+        for (int k = 0; k < kNRate; ++k) s[k] = b[k * n + h];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) { c[k] = b[(kNRate + k) * n + h]; p[k] = 0.f; }
+    }
     // the compensated sum s - c rounded once to FP32 keeps the compensation's benefit (one rounding
     // of the final value instead of one per term) and widens with a single conversion
     __device__ __forceinline__ double get(int k) const { return (double)(k < 6 ? s[k] - c[k] : s[k]); }
@@ -189,6 +202,14 @@ template <> struct Acc<float> {
 template <> struct Acc<double> {
     double s[kNRate];
     __device__ __forceinline__ void fold() {}
+    __device__ __forceinline__ void store(double *b, int64_t n, int64_t h) const {
+#pragma unroll
+        for (int k = 0; k < kNRate; ++k) b[k * n + h] = s[k];
+    }
+    __device__ __forceinline__ void load(const double *b, int64_t n, int64_t h) {
+#pragma unroll
+        for (int k = 0; k < kNRate; ++k) s[k] = b[k * n + h];
+    }
     __device__ __forceinline__ void zero() {
 #pragma unroll
         for (int k = 0; k < kNRate; ++k) s[k] = 0.0;
@@ -411,24 +432,71 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
 
 // ---------------------------------------------------------------------------------------------
 // Pair kernel: list walk, wall images, integration.
+//
+// Modes (Sec. II steps d-f):
+//   PM_ALL      every pair of every particle in one pass, then the integration.
+//   PM_LOCAL    the pairs of each particle with neighbours of its own label (and the wall images of
+//               those). Particles without a neighbour of another label (not MGPU boundary particles)
+//               are complete and integrate; boundary particles park their partial sums (by halo index).
+//   PM_BOUNDARY one lane per MGPU boundary particle (the boundary list, label-major): the partial sums
+//               back, the pairs with neighbours of other labels, whose records come from the halo
+//               buffer (the broadcast boundary set), then the integration.
 // ---------------------------------------------------------------------------------------------
-template <bool SPLIT, bool DIAG>
-__global__ void __launch_bounds__(PK_THREADS, SPLIT ? 5 : 2)
-k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *__restrict__ cellr,
-       const typename Types<SPLIT>::Pos *__restrict__ pos, const typename Types<SPLIT>::Rec *__restrict__ rec,
-       const float *__restrict__ cxs, const double *__restrict__ xs, const double *__restrict__ ys,
-       const double *__restrict__ zs, int kmax, const uint2 *__restrict__ list,
-       const uint32_t *__restrict__ cnt_in, const uint32_t *__restrict__ perm, State A, State B,
-       const uint8_t *__restrict__ lab_s, const uint8_t *__restrict__ mat_s, const uint32_t *__restrict__ id_s,
-       const double *__restrict__ dt_ptr, unsigned int *__restrict__ sig, unsigned long long *__restrict__ pairs,
-       int32_t *__restrict__ nreal_out, int32_t *__restrict__ nimage_out, double *__restrict__ rates_out) {
+enum { PM_ALL = 0, PM_LOCAL = 1, PM_BOUNDARY = 2 };
+
+template <bool SPLIT>
+struct PairArgs {
+    using Pos = typename Types<SPLIT>::Pos;
+    using Rec = typename Types<SPLIT>::Rec;
+    DevParams P;
+    int64_t n;
+    const uint32_t *skey;
+    const uint2 *cellr;
+    const Pos *pos;
+    const Rec *rec;
+    const float *cxs;
+    const double *xs, *ys, *zs;
+    int kmax;
+    const uint2 *list;
+    const uint32_t *cnt_in;
+    const uint32_t *perm;
+    State A, B;
+    const uint8_t *lab_s, *mat_s;
+    const uint32_t *id_s;
+    const double *dt_ptr;
+    unsigned int *sig;
+    unsigned long long *pairs;
+    int32_t *nreal_out, *nimage_out;
+    double *rates_out;
+    // two-pass order only
+    const uint8_t *flag;         // MGPU boundary flag per slot
+    const uint32_t *blist;       // boundary slots, label-major (halo index -> slot)
+    const unsigned long long *btotal;   // boundary set size
+    const uint32_t *hidx;        // slot -> halo index (boundary particles)
+    const Pos *hpos;             // halo records by halo index
+    const Rec *hrec;
+    const float *hcx;
+    void *part;                  // parked partial sums by halo index: field f at f * n + h
+    int32_t *part_cnt;           // parked real and image neighbour counts: 2 * h, 2 * h + 1
+};
+
+template <bool SPLIT, bool DIAG, int MODE>
+__device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, bool valid, int64_t hk) {
     using R = typename Types<SPLIT>::R;
     using Pos = typename Types<SPLIT>::Pos;
     using Rec = typename Types<SPLIT>::Rec;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int64_t s = (int64_t)blockIdx.x * PK_THREADS + tid;
-    const bool valid = s < n;
-    const uint32_t key = valid ? skey[s] : P.ncell;
+    const DevParams &P = a.P;
+    const int64_t n = a.n;
+    const Pos *__restrict__ pos = a.pos;
+    const Rec *__restrict__ rec = a.rec;
+    const float *__restrict__ cxs = a.cxs;
+    const double *__restrict__ xs = a.xs;
+    const double *__restrict__ ys = a.ys;
+    const double *__restrict__ zs = a.zs;
+    const uint2 *__restrict__ list = a.list;
+    const int kmax = a.kmax;
+    const int lane = threadIdx.x & 31;
+    const uint32_t key = valid ? a.skey[s] : P.ncell;
     const bool active = valid && key < P.ncell;
     PIn<R> me;
     R mrx = 0, mry = 0, mrz = 0;   // own position: relative to the own bucket corner (split) or absolute
@@ -442,9 +510,23 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
     const R inv_h = SPLIT ? (R)P.f_inv_h : (R)(1.0 / P.h);
     const R kdw = SPLIT ? (R)P.f_kdw : (R)P.kdw;
     const R fcell = SPLIT ? (R)P.f_cell : (R)P.cell;
+    // label filter of the two-pass order: PM_LOCAL takes neighbours of the own label, PM_BOUNDARY the others
+    const uint32_t mylab = (MODE != PM_ALL && valid) ? a.lab_s[s] : 0u;
+    auto take = [&](uint32_t j) -> bool {
+        if (MODE == PM_ALL) return true;
+        const bool same = a.lab_s[j] == mylab;
+        return MODE == PM_LOCAL ? same : !same;
+    };
     Acc<R> acc;
     acc.zero();
-    const uint32_t cw = active ? cnt_in[s] : 0u;
+    int nr0 = 0, ni0 = 0;
+    if (MODE == PM_BOUNDARY && valid) {   // the partial sums of the first pass
+        const R *pr = (const R *)a.part;
+        acc.load(pr, n, hk);
+        nr0 = a.part_cnt[2 * hk];
+        ni0 = a.part_cnt[2 * hk + 1];
+    }
+    const uint32_t cw = active ? a.cnt_in[s] : 0u;
     const uint32_t cnt = cw & 255u;                  // entries found
     const int ne = (int)min(cnt, (uint32_t)kmax);    // entries stored
     const uint32_t nlist = cw >> 8;                  // neighbours in the stored entries
@@ -475,6 +557,7 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
     // ---- listed real neighbours, all lanes in lockstep: the set bits of the current entry give the
     // slots; the entry after it and the next neighbour's record are in flight while the current pair
     // is evaluated
+    int nsel = 0;   // listed neighbours taken by this pass
     {
         const uint2 *lp = list + (size_t)s;
         const size_t colstep = (size_t)n;
@@ -499,29 +582,48 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
                 ++ke;
             }
         };
+        // record source: the particle arrays, or (second pass, other labels) the halo buffer
+        auto fetch = [&](uint32_t j, bool t, Pos &pj, Rec &rj, float &xj) {
+            if (MODE == PM_BOUNDARY) {
+                const uint32_t h = t ? a.hidx[j] : 0u;
+                pj = a.hpos[h];
+                rj = a.hrec[h];
+                xj = SPLIT ? a.hcx[h] : 0.0f;
+            } else {
+                pj = pos[j];
+                rj = rec[j];
+                xj = SPLIT ? cxs[j] : 0.0f;
+            }
+        };
         const int mc = (int)__reduce_max_sync(kFullMask, nlist);
         uint32_t j1 = 0u, c1 = 0u;
         if (nlist > 0) next(j1, c1);
-        Pos p1 = pos[j1];
-        Rec r1 = rec[j1];
-        float x1 = SPLIT ? cxs[j1] : 0.0f;
+        bool t1 = take(j1);
+        Pos p1;
+        Rec r1;
+        float x1;
+        fetch(j1, t1, p1, r1, x1);
 #pragma unroll 2
         for (int k = 0; k < mc; ++k) {
             const uint32_t j = j1, c = c1;
             const Pos pj = p1;
             const Rec rj = r1;
             const float xj = x1;
+            const bool tj = t1;
             if ((uint32_t)k + 1 < nlist) next(j1, c1);   // else j1 stays a valid slot
-            p1 = pos[j1];
-            r1 = rec[j1];
-            if (SPLIT) x1 = cxs[j1];
-            if ((uint32_t)k < nlist) real_pair(j, c, (R)xj, pj, rj);
+            t1 = take(j1);
+            fetch(j1, t1, p1, r1, x1);
+            if ((uint32_t)k < nlist && tj) {
+                real_pair(j, c, (R)xj, pj, rj);
+                if (MODE != PM_ALL) ++nsel;
+            }
             if ((k & 7) == 7) acc.fold();
         }
     }
 
     // ---- neighbours beyond the list capacity, and the wall images: re-scan the buckets around the
-    // own position (overflow) or the mirrored position (images) in the list's candidate order
+    // own position (overflow) or the mirrored position (images) in the list's candidate order. In the
+    // two-pass order this rare path reads the particle arrays.
     const double X = valid ? xs[s] : 0.0, Y = valid ? ys[s] : 0.0, Z = valid ? zs[s] : 0.0;
     int cx = 0, cy = 0, cz = 0;
     if (active) decode_cell(P, key, cx, cy, cz);
@@ -555,7 +657,7 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
         for (int row = 0; row < 9 && mine; ++row) {
             const int dcy = row % 3 - 1, dcz = row / 3 - 1;
             uint32_t rs, re;
-            row_window(P, cellr, bx, by + dcy, bz + dcz, rs, re);
+            row_window(P, a.cellr, bx, by + dcy, bz + dcz, rs, re);
             for (uint32_t j = rs; j < re; ++j) {
                 if (src == 0 && (int64_t)j == s) continue;
                 const Pos pj = pos[j];
@@ -575,9 +677,11 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
                 if (src == 0) {
                     // real neighbour past the list capacity
                     if (seen++ < nlist) continue;
+                    if (!take(j)) continue;
                     real_pair(j, (uint32_t)(dcy + 1) | (uint32_t)(dcz + 1) << 2, (R)cxs[j], pj, rec[j]);
                     ++nover;
                 } else {
+                    if (!take(j)) continue;
                     PIn<R> oth = load_rec(rec, (R)pj.w, j);
                     R d0, d1, d2;
                     if (SPLIT) {
@@ -605,15 +709,30 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
         }
     }
     acc.fold();
-    const int nr = (int)(nlist + nover);
+    const int ntaken = MODE == PM_ALL ? (int)nlist : nsel;   // listed neighbours summed by this pass
+    const unsigned pc = __reduce_add_sync(kFullMask, (unsigned)(ntaken + (int)nover + ni));
+    const int nr = nr0 + ntaken + (int)nover;
+    ni += ni0;
+
+    // ---- first pass of the two-pass order: a boundary particle parks its sums for the second pass
+    bool integrate = valid;
+    if (MODE == PM_LOCAL && valid && a.flag[s]) {
+        const uint32_t h = a.hidx[s];
+        acc.store((R *)a.part, n, h);
+        a.part_cnt[2 * (size_t)h] = nr;
+        a.part_cnt[2 * (size_t)h + 1] = ni;
+        integrate = false;
+    }
 
     // ---- integration (Sec. II step g): forward Euler on the conserved variables, Jaumann-rate
     // stress with radial return, positions with the velocity of the step's start.
     float sp = 0.0f;
-    if (valid) {
-        const uint32_t o = perm[s];
-        const int mt = mat_s[s] < P.nmat ? mat_s[s] : 0;
-        const double dt = *dt_ptr;
+    if (integrate) {
+        const State &A = a.A;
+        const State &B = a.B;
+        const uint32_t o = a.perm[s];
+        const int mt = a.mat_s[s] < P.nmat ? a.mat_s[s] : 0;
+        const double dt = *a.dt_ptr;
         const double w = A.f[FW][o], m = A.f[FM][o], E = A.f[FE][o];
         const double vx = A.f[FVX][o], vy = A.f[FVY][o], vz = A.f[FVZ][o];
         double S[6] = {A.f[FSXX][o], A.f[FSYY][o], A.f[FSZZ][o], A.f[FSXY][o], A.f[FSXZ][o], A.f[FSYZ][o]};
@@ -699,24 +818,82 @@ k_pair(DevParams P, int64_t n, const uint32_t *__restrict__ skey, const uint2 *_
         B.f[FSXY][s] = Sn[3];
         B.f[FSXZ][s] = Sn[4];
         B.f[FSYZ][s] = Sn[5];
-        B.mat[s] = mat_s[s];
-        B.label[s] = lab_s[s];
-        B.id[s] = id_s[s];
+        B.mat[s] = a.mat_s[s];
+        B.label[s] = a.lab_s[s];
+        B.id[s] = a.id_s[s];
         if (DIAG) {
-            nreal_out[s] = nr;
-            nimage_out[s] = ni;
+            a.nreal_out[s] = nr;
+            a.nimage_out[s] = ni;
 #pragma unroll
-            for (int k = 0; k < kNRate; ++k) rates_out[(size_t)s * kNRate + k] = acc.get(k);
+            for (int k = 0; k < kNRate; ++k) a.rates_out[(size_t)s * kNRate + k] = acc.get(k);
         }
         // next step's CFL signal speed (correctly rounded FP32, reproducible bit for bit)
         sp = signal_speed32(P, mt, mn, wn, nvx, nvy, nvz);
     }
     const unsigned b = __reduce_max_sync(kFullMask, __float_as_uint(sp));
-    const unsigned pc = __reduce_add_sync(kFullMask, (unsigned)(nr + ni));
     if (lane == 0) {
-        atomicMax(sig, b);
-        atomicAdd(pairs, (unsigned long long)pc);
+        atomicMax(a.sig, b);
+        atomicAdd(a.pairs, (unsigned long long)pc);
     }
+}
+
+template <bool SPLIT, bool DIAG, int MODE>
+__global__ void __launch_bounds__(PK_THREADS, SPLIT ? 5 : 2) k_pair(const PairArgs<SPLIT> a) {
+    if (MODE == PM_BOUNDARY) {
+        // one lane per boundary particle, warp-uniform strides over the boundary list
+        const int64_t total = (int64_t)*a.btotal;
+        const int64_t stride = (int64_t)gridDim.x * PK_THREADS;
+        for (int64_t kb = (int64_t)blockIdx.x * PK_THREADS + (threadIdx.x & ~31); kb < total; kb += stride) {
+            const int64_t k = kb + (threadIdx.x & 31);
+            const bool valid = k < total;
+            const int64_t s = valid ? (int64_t)a.blist[k] : 0;
+            pair_body<SPLIT, DIAG, MODE>(a, s, valid, k);
+        }
+    } else {
+        const int64_t s = (int64_t)blockIdx.x * PK_THREADS + threadIdx.x;
+        pair_body<SPLIT, DIAG, MODE>(a, s, s < a.n, 0);
+    }
+}
+
+// Gather of the MGPU boundary set's records into the halo buffer (the broadcast of Sec. II step d on
+// one device): halo index h holds the particle at boundary-list position h.
+template <bool SPLIT>
+__global__ void k_halo_gather(const PairArgs<SPLIT> a, typename Types<SPLIT>::Pos *hpos,
+                              typename Types<SPLIT>::Rec *hrec, float *hcx) {
+    const int64_t total = (int64_t)*a.btotal;
+    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < total; h += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = a.blist[h];
+        hpos[h] = a.pos[s];
+        hrec[h] = a.rec[s];
+        hcx[h] = a.cxs[s];
+    }
+}
+
+template <bool SPLIT>
+static PairArgs<SPLIT> pair_args(const DevParams &P, int64_t n, const uint32_t *skey, const uint2 *cellr,
+                                 const void *pos, const void *rec, const float *cxs, const double *xs,
+                                 const double *ys, const double *zs, int kmax, const uint2 *list,
+                                 const uint32_t *cnt, const uint32_t *perm, const State &A, const State &B,
+                                 const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s,
+                                 const double *dt, unsigned int *sig, unsigned long long *pairs, int32_t *nreal,
+                                 int32_t *nimage, double *rates, const OverlapBufs *ov) {
+    using Pos = typename Types<SPLIT>::Pos;
+    using Rec = typename Types<SPLIT>::Rec;
+    PairArgs<SPLIT> a;
+    a.P = P; a.n = n; a.skey = skey; a.cellr = cellr; a.pos = (const Pos *)pos; a.rec = (const Rec *)rec;
+    a.cxs = cxs; a.xs = xs; a.ys = ys; a.zs = zs; a.kmax = kmax; a.list = list; a.cnt_in = cnt; a.perm = perm;
+    a.A = A; a.B = B; a.lab_s = lab_s; a.mat_s = mat_s; a.id_s = id_s; a.dt_ptr = dt; a.sig = sig;
+    a.pairs = pairs; a.nreal_out = nreal; a.nimage_out = nimage; a.rates_out = rates;
+    a.flag = ov ? ov->flag : nullptr;
+    a.blist = ov ? ov->blist : nullptr;
+    a.btotal = ov ? ov->btotal : nullptr;
+    a.hidx = ov ? ov->hidx : nullptr;
+    a.hpos = ov ? (const Pos *)ov->hpos : nullptr;
+    a.hrec = ov ? (const Rec *)ov->hrec : nullptr;
+    a.hcx = ov ? ov->hcx : nullptr;
+    a.part = ov ? ov->part : nullptr;
+    a.part_cnt = ov ? ov->part_cnt : nullptr;
+    return a;
 }
 
 cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n, const uint32_t *skey,
@@ -725,28 +902,53 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
                             uint32_t *cnt, const uint32_t *perm, const State &A, const State &B, cudaEvent_t mid,
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
                             unsigned int *sig, unsigned long long *pairs, int32_t *nreal, int32_t *nimage,
-                            double *rates, cudaStream_t s) {
+                            double *rates, const OverlapBufs *ov, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const unsigned gl = (unsigned)((n + NL_THREADS - 1) / NL_THREADS);
     const unsigned gp = (unsigned)((n + PK_THREADS - 1) / PK_THREADS);
 #define GSPH_NL_ARGS P, n, skey, cellr, (const typename Types<SP>::Pos *)pos, cxs, xs, ys, zs, kmax, list, cnt
-#define GSPH_PK_ARGS P, n, skey, cellr, (const typename Types<SP>::Pos *)pos, (const typename Types<SP>::Rec *)rec, \
-                     cxs, xs, ys, zs, kmax, list, cnt, perm, A, B, lab_s, mat_s, id_s, dt, sig, pairs, nreal, nimage, rates
+#define GSPH_PAIR_ARGS pair_args<SP>(P, n, skey, cellr, pos, rec, cxs, xs, ys, zs, kmax, list, cnt, perm, A, B, \
+                                     lab_s, mat_s, id_s, dt, sig, pairs, nreal, nimage, rates, ov)
+#define GSPH_PAIRS(MODE_)                                                                   \
+    do {                                                                                    \
+        const auto pa = GSPH_PAIR_ARGS;                                                      \
+        const unsigned g_ = MODE_ == PM_BOUNDARY ? ov->boundary_grid : gp;                  \
+        if (diag) k_pair<SP, true, MODE_><<<g_, PK_THREADS, 0, s>>>(pa);                     \
+        else k_pair<SP, false, MODE_><<<g_, PK_THREADS, 0, s>>>(pa);                        \
+    } while (0)
+#define GSPH_INTERACT                                                                       \
+    do {                                                                                    \
+        k_nbr_list<SP><<<gl, NL_THREADS, 0, s>>>(GSPH_NL_ARGS);                             \
+        if (mid) cudaEventRecord(mid, s);                                                   \
+        if (!ov) {                                                                          \
+            GSPH_PAIRS(PM_ALL);                                                             \
+        } else {                                                                            \
+            /* step d on the second stream while the local pairs run (steps e, then f) */  \
+            cudaEventRecord(ov->ev_fork, s);                                                \
+            cudaStreamWaitEvent(ov->aux, ov->ev_fork, 0);                                   \
+            if (ov->ev_halo0) cudaEventRecord(ov->ev_halo0, ov->aux);                       \
+            k_halo_gather<SP><<<ov->gather_grid, 256, 0, ov->aux>>>(                        \
+                GSPH_PAIR_ARGS, (typename Types<SP>::Pos *)ov->hpos,                        \
+                (typename Types<SP>::Rec *)ov->hrec, ov->hcx);                              \
+            if (ov->ev_halo1) cudaEventRecord(ov->ev_halo1, ov->aux);                       \
+            cudaEventRecord(ov->ev_join, ov->aux);                                          \
+            GSPH_PAIRS(PM_LOCAL);                                                           \
+            if (ov->ev_local) cudaEventRecord(ov->ev_local, s);                             \
+            cudaStreamWaitEvent(s, ov->ev_join, 0);                                         \
+            GSPH_PAIRS(PM_BOUNDARY);                                                        \
+        }                                                                                   \
+    } while (0)
     if (split) {
         constexpr bool SP = true;
-        k_nbr_list<SP><<<gl, NL_THREADS, 0, s>>>(GSPH_NL_ARGS);
-        if (mid) cudaEventRecord(mid, s);
-        if (diag) k_pair<SP, true><<<gp, PK_THREADS, 0, s>>>(GSPH_PK_ARGS);
-        else k_pair<SP, false><<<gp, PK_THREADS, 0, s>>>(GSPH_PK_ARGS);
+        GSPH_INTERACT;
     } else {
         constexpr bool SP = false;
-        k_nbr_list<SP><<<gl, NL_THREADS, 0, s>>>(GSPH_NL_ARGS);
-        if (mid) cudaEventRecord(mid, s);
-        if (diag) k_pair<SP, true><<<gp, PK_THREADS, 0, s>>>(GSPH_PK_ARGS);
-        else k_pair<SP, false><<<gp, PK_THREADS, 0, s>>>(GSPH_PK_ARGS);
+        GSPH_INTERACT;
     }
+#undef GSPH_INTERACT
+#undef GSPH_PAIRS
+#undef GSPH_PAIR_ARGS
 #undef GSPH_NL_ARGS
-#undef GSPH_PK_ARGS
     return cudaGetLastError();
 }
 

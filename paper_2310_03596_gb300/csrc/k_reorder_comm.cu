@@ -207,7 +207,8 @@ __global__ void __launch_bounds__(1024) k_comm_scan(uint32_t *__restrict__ block
 __global__ void __launch_bounds__(CM_THREADS) k_boundary_scatter(int64_t n, const uint8_t *__restrict__ lab_s,
                                                                  const uint8_t *__restrict__ flag,
                                                                  const uint32_t *__restrict__ block_offsets,
-                                                                 int nblk, uint32_t *__restrict__ out) {
+                                                                 int nblk, uint32_t *__restrict__ out,
+                                                                 uint32_t *__restrict__ hidx) {
     constexpr int W = CM_THREADS / 32;
     __shared__ uint32_t wc[W][kMaxLabel];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -223,13 +224,15 @@ __global__ void __launch_bounds__(CM_THREADS) k_boundary_scatter(int64_t n, cons
     if (f) {
         uint32_t before = 0;
         for (int k = 0; k < w; ++k) before += wc[k][lab];
-        out[block_offsets[(size_t)lab * nblk + blockIdx.x] + before + rank] = (uint32_t)s;
+        const uint32_t at = block_offsets[(size_t)lab * nblk + blockIdx.x] + before + rank;
+        out[at] = (uint32_t)s;
+        if (hidx) hidx[s] = at;   // halo index of the two-pass interaction order
     }
 }
 
 cudaError_t launch_comm(const DevParams &P, int64_t n, const uint32_t *skey, const uint8_t *lab_s, uint32_t *mask,
                         uint8_t *flag, uint32_t *comm, uint32_t *block_counts, unsigned long long *label_total,
-                        uint32_t *blist, cudaStream_t s) {
+                        uint32_t *blist, uint32_t *hidx, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(mask, 0, (size_t)P.ncell * 4, s);
     if (e != cudaSuccess) return e;
@@ -237,7 +240,7 @@ cudaError_t launch_comm(const DevParams &P, int64_t n, const uint32_t *skey, con
     k_label_mask<<<g, CM_THREADS, 0, s>>>(P, n, skey, lab_s, mask);
     k_comm<<<g, CM_THREADS, 0, s>>>(P, n, skey, lab_s, mask, flag, comm, block_counts, (int)g);
     k_comm_scan<<<1, 1024, 0, s>>>(block_counts, (int64_t)P.K_labels * g, (int)g, P.K_labels, label_total);
-    k_boundary_scatter<<<g, CM_THREADS, 0, s>>>(n, lab_s, flag, block_counts, (int)g, blist);
+    k_boundary_scatter<<<g, CM_THREADS, 0, s>>>(n, lab_s, flag, block_counts, (int)g, blist, hidx);
     return cudaGetLastError();
 }
 

@@ -51,7 +51,8 @@ class Config(C.Structure):
                 ("h", C.c_double), ("cfl", C.c_double), ("materials", Material * MAX_MAT),
                 ("n_walls", C.c_int32), ("K", C.c_int32), ("walls", Wall * MAX_WALL),
                 ("gravity", C.c_double * 3), ("alpha", C.c_double), ("swap_period", C.c_int32),
-                ("precision", C.c_int32), ("device", C.c_int32), ("diagnostics", C.c_int32)]
+                ("precision", C.c_int32), ("device", C.c_int32), ("diagnostics", C.c_int32),
+                ("overlap", C.c_int32), ("pad2", C.c_int32)]
 
 
 class ExchangeStats(C.Structure):
@@ -71,7 +72,8 @@ class ExchangeStats(C.Structure):
 class Timings(C.Structure):
     _fields_ = [("hash_sort_ms", C.c_double), ("reorder_ms", C.c_double), ("swap_ms", C.c_double),
                 ("comm_ms", C.c_double), ("interact_ms", C.c_double), ("steps", C.c_int64),
-                ("interact_launches", C.c_int64), ("nbr_list_ms", C.c_double), ("pair_ms", C.c_double)]
+                ("interact_launches", C.c_int64), ("nbr_list_ms", C.c_double), ("pair_ms", C.c_double),
+                ("local_ms", C.c_double), ("boundary_ms", C.c_double), ("halo_ms", C.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -131,7 +133,8 @@ def check(code: int, what: str, allow=(OK,)) -> int:
     return code
 
 
-def config_from_scene(scene, precision: int = FP32_SPLIT, device: int = 0, diagnostics: bool = False) -> Config:
+def config_from_scene(scene, precision: int = FP32_SPLIT, device: int = 0, diagnostics: bool = False,
+                      overlap: bool = False) -> Config:
     c = Config()
     for a in range(3):
         c.grid_lo[a] = scene.grid_lo[a]
@@ -151,6 +154,7 @@ def config_from_scene(scene, precision: int = FP32_SPLIT, device: int = 0, diagn
     c.precision = precision
     c.device = device
     c.diagnostics = int(diagnostics)
+    c.overlap = int(overlap)
     return c
 
 
@@ -179,8 +183,8 @@ class Solver:
 
     @classmethod
     def from_scene(cls, scene, precision: int = FP32_SPLIT, device: int = 0, diagnostics: bool = False,
-                   stream=None) -> "Solver":
-        s = cls(config_from_scene(scene, precision, device, diagnostics))
+                   stream=None, overlap: bool = False) -> "Solver":
+        s = cls(config_from_scene(scene, precision, device, diagnostics, overlap))
         s.set_particles(scene.pos, scene.vel, scene.vol, scene.material, scene.label, stream=stream)
         return s
 
