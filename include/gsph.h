@@ -55,7 +55,20 @@ typedef struct {
     double K;      /* bulk modulus, Pa (linear EOS p = K (rho/rho0 - 1)) */
     double G;      /* shear modulus, Pa */
     double Y;      /* yield stress, Pa (von Mises perfect plasticity) */
+    int32_t eos;   /* GSPH_EOS_LINEAR (K) or GSPH_EOS_MIE_GRUNEISEN (c0, s, gamma0) */
+    int32_t pad;
+    double c0;     /* Mie-Gruneisen (Sec. IV names it; reading): bulk sound speed, m/s, c0 > 0 */
+    double s;      /* slope of the shock relation Us = c0 + s up, 0 <= s */
+    double gamma0; /* Gruneisen gamma at rho0 (Gamma rho = gamma0 rho0), >= 0. With mu = rho/rho0 - 1:
+                      p_H = rho0 c0^2 mu (1 + mu) / (1 - (s - 1) mu)^2 (mu > 0), rho0 c0^2 mu (mu <= 0);
+                      e_H = p_H mu / (2 rho0 (1 + mu)); p = p_H + gamma0 rho0 (e - e_H), e the specific
+                      internal energy E - |v|^2/2; sound speed from the isentropic derivative */
+    double p_min;  /* pressure cut-off for spalling (Sec. IV): p = max(p, p_min), Pa, <= 0; -INFINITY:
+                      none. Either EOS */
 } gsph_material;
+
+#define GSPH_EOS_LINEAR 0
+#define GSPH_EOS_MIE_GRUNEISEN 1
 
 typedef struct {
     int32_t axis;  /* 0, 1, 2: rigid mirror plane x_axis = pos */
@@ -226,7 +239,8 @@ gsph_status gsph_set_dt(gsph_ctx *ctx, double dt, void *stream);
  * order X..SYZ), dJ/dy_{n+1} in the slot order y_{n+1} has (the hash order of this step, as after
  * gsph_step). lam_prev: device, same layout, receives dJ/dy_n in the current slot order.
  * grad: host, receives this step's direct contributions to dJ/dY and dJ/dG of material 0.
- * Does not advance the state. Errors: INVALID_ARG (null pointers, dt <= 0, wrong context kind),
+ * Covers the linear EOS without a pressure cut-off (every material GSPH_EOS_LINEAR, p_min = -INFINITY).
+ * Does not advance the state. Errors: INVALID_ARG (null pointers, dt <= 0, wrong context kind or EOS),
  * NOT_READY, OOM, CUDA_ERROR. */
 gsph_status gsph_adjoint_step(gsph_ctx *ctx, const double *lam_next, double *lam_prev, double dt,
                               double grad[2], void *stream);

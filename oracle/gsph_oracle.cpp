@@ -44,7 +44,45 @@ inline double val(double x) { return x; }
 inline double val(const Dual &x) { return x.v; }
 using std::sqrt;
 
-template <class T> struct Mat { T rho0, K, G, Y; };
+template <class T> struct Mat {
+    T rho0, K, G, Y, c0, s, gamma0;
+    int eos;
+    double p_min;
+};
+
+// Equation of state (Sec. IV names a Mie-Gruneisen EOS with a cut-off pressure for spalling; it gives
+// no formula, so this is a reading). Linear: p = K mu with mu = rho/rho0 - 1. Mie-Gruneisen with the
+// Hugoniot of the linear shock relation Us = c0 + s up as reference curve and Gamma rho = gamma0 rho0:
+//   p_H = rho0 c0^2 mu (1 + mu) / (1 - (s - 1) mu)^2 (mu > 0),  p_H = rho0 c0^2 mu (mu <= 0),
+//   e_H = p_H mu / (2 rho0 (1 + mu))  (the Rankine-Hugoniot energy from the rest state),
+//   p = p_H + gamma0 rho0 (e - e_H).
+// The cut-off floors the pressure: p = max(p, p_min). The bulk sound speed is the isentropic
+// derivative of the uncut pressure, c_b^2 = dp/drho|_e + (p / rho^2) dp/de|_rho, floored at 0.
+template <class T> void eos_of(const Mat<T> &M, T rho, T e, T &p, T &cb2) {
+    if (M.eos == 0) {
+        p = M.K * (rho / M.rho0 - T(1.0));
+        cb2 = M.K / rho;
+    } else {
+        T mu = rho / M.rho0 - T(1.0);
+        T k0 = M.rho0 * M.c0 * M.c0;
+        T pH, dpH;
+        if (val(mu) > 0.0) {
+            T D = T(1.0) - (M.s - T(1.0)) * mu;
+            pH = k0 * mu * (T(1.0) + mu) / (D * D);
+            dpH = k0 * ((T(1.0) + T(2.0) * mu) * D + T(2.0) * (M.s - T(1.0)) * mu * (T(1.0) + mu)) / (D * D * D);
+        } else {
+            pH = k0 * mu;
+            dpH = k0;
+        }
+        T eH = pH * mu / (T(2.0) * M.rho0 * (T(1.0) + mu));
+        T deH = (dpH * mu * (T(1.0) + mu) + pH) / (T(2.0) * M.rho0 * (T(1.0) + mu) * (T(1.0) + mu));
+        p = pH + M.gamma0 * M.rho0 * (e - eH);
+        // d/drho = (1 / rho0) d/dmu at fixed e; dp/de = gamma0 rho0
+        cb2 = (dpH - M.gamma0 * M.rho0 * deH) / M.rho0 + p * M.gamma0 * M.rho0 / (rho * rho);
+        if (val(cb2) < 0.0) cb2 = T(0.0);
+    }
+    if (val(p) < M.p_min) p = T(M.p_min);
+}
 
 // Per-particle primitive state seen by the interaction loop.
 template <class T> struct Prim {
@@ -298,8 +336,17 @@ template <class T> Prim<T> prim_of(const StateT<T> &s, const Mat<T> *mats, int64
     p.v[0] = s.vx[i]; p.v[1] = s.vy[i]; p.v[2] = s.vz[i];
     p.w = s.w[i];
     p.rho = s.m[i] / s.w[i];
-    p.p = M.K * (p.rho / M.rho0 - T(1.0));
-    T c = sqrt((M.K + T(4.0) * M.G / 3.0) / p.rho);
+    T c;
+    if (M.eos == 0) {   // linear EOS: c^2 = (K + 4G/3) / rho, the longitudinal modulus
+        p.p = M.K * (p.rho / M.rho0 - T(1.0));
+        c = sqrt((M.K + T(4.0) * M.G / 3.0) / p.rho);
+        if (val(p.p) < M.p_min) p.p = T(M.p_min);
+    } else {            // specific internal energy e = E - |v|^2 / 2
+        T cb2;
+        T e = s.E[i] - T(0.5) * (p.v[0] * p.v[0] + p.v[1] * p.v[1] + p.v[2] * p.v[2]);
+        eos_of(M, p.rho, e, p.p, cb2);
+        c = sqrt(cb2 + T(4.0) * M.G / (T(3.0) * p.rho));
+    }
     p.Z = p.rho * c;
     p.E = s.E[i];
     for (int k = 0; k < 6; ++k) p.S[k] = s.S[k][i];
@@ -380,6 +427,11 @@ template <class T> void mats_of(const orc_params *P, Mat<T> *m) {
         m[k].K = T(P->mat[k].K);
         m[k].G = T(P->mat[k].G);
         m[k].Y = T(P->mat[k].Y);
+        m[k].c0 = T(P->mat[k].c0);
+        m[k].s = T(P->mat[k].s);
+        m[k].gamma0 = T(P->mat[k].gamma0);
+        m[k].eos = P->mat[k].eos;
+        m[k].p_min = P->mat[k].p_min;
     }
 }
 
@@ -405,14 +457,44 @@ void rates_all(const orc_params *P, const StateT<T> &s, const Mat<T> *mats, int6
 // FP32 sequence is cheap on GPUs whose FP64 units are scarce).
 float signal_speed(const orc_params *P, const orc_state *S, int64_t i) {
     const orc_material &M = P->mat[S->mat[i]];
-    float Mmod = (float)(M.K + 4.0 * M.G / 3.0);
     float rho = (float)S->m[i] / (float)S->w[i];
-    float c = std::sqrt(Mmod / rho);
     float vx = (float)S->vx[i], vy = (float)S->vy[i], vz = (float)S->vz[i];
     float a = vx * vx;
     float b = vy * vy;
     float d = vz * vz;
     float v2 = (a + b) + d;
+    float c;
+    if (M.eos == 0) {
+        float Mmod = (float)(M.K + 4.0 * M.G / 3.0);
+        c = std::sqrt(Mmod / rho);
+    } else {
+        // the Mie-Gruneisen sound speed of eos_of in FP32, operation by operation, from the FP32
+        // roundings of the material constants, m, w, v and E
+        float rho0 = (float)M.rho0, c0 = (float)M.c0, sm1 = (float)(M.s - 1.0), g0 = (float)M.gamma0;
+        float e = (float)S->E[i] - 0.5f * v2;
+        float mu = rho / rho0 - 1.0f;
+        float k0 = (rho0 * c0) * c0;
+        float pH, dpH;
+        if (mu > 0.0f) {
+            float D = 1.0f - sm1 * mu;
+            float D2 = D * D;
+            float q = 1.0f + mu;
+            pH = ((k0 * mu) * q) / D2;
+            dpH = (k0 * ((1.0f + 2.0f * mu) * D + (2.0f * sm1) * (mu * q))) / (D2 * D);
+        } else {
+            pH = k0 * mu;
+            dpH = k0;
+        }
+        float q = 1.0f + mu;
+        float eH = (pH * mu) / ((2.0f * rho0) * q);
+        float deH = ((dpH * mu) * q + pH) / (((2.0f * rho0) * q) * q);
+        float gr = g0 * rho0;
+        float p = pH + gr * (e - eH);
+        float cb2 = (dpH - gr * deH) / rho0 + (p * gr) / (rho * rho);
+        if (!(cb2 > 0.0f)) cb2 = 0.0f;
+        float G43 = (float)(4.0 * M.G / 3.0);
+        c = std::sqrt(cb2 + G43 / rho);
+    }
     return c + std::sqrt(v2);
 }
 
@@ -516,6 +598,12 @@ void cg_from_sums(const Quant &q, const int64_t sum[3], int64_t cnt, double cg[3
 // C entry points
 // =============================================================================================
 extern "C" {
+
+void orc_eos(const orc_params *P, int32_t mat, double rho, double e, double *p, double *cb2) {
+    Mat<double> m[ORC_MAX_MAT];
+    mats_of(P, m);
+    eos_of(m[mat], rho, e, *p, *cb2);
+}
 
 void orc_hash(const orc_params *P, int64_t n, const double *x, const double *y, const double *z,
               uint32_t *key) {

@@ -29,6 +29,10 @@ extern "C" {
 
 typedef struct {
     double rho0, K, G, Y;            /* reference density, bulk and shear modulus, yield stress */
+    int32_t eos;                     /* 0: linear p = K (rho/rho0 - 1); 1: Mie-Gruneisen (c0, s, gamma0) */
+    int32_t pad;
+    double c0, s, gamma0;            /* Mie-Gruneisen: bulk sound speed, Us-up slope, Gruneisen gamma */
+    double p_min;                    /* pressure cut-off (spall): p = max(p, p_min); -inf: none */
 } orc_material;
 
 typedef struct {
@@ -82,6 +86,10 @@ int64_t orc_neighbours_cells(const orc_params *P, int64_t n, const double *x, co
  * only the nsub listed slots are evaluated (rates of the others are left untouched). */
 void orc_rates(const orc_params *P, const orc_state *S, int64_t nsub, const int64_t *subset,
                double *rates, int32_t *nreal, int32_t *nimage);
+/* Equation of state of material mat (Sec. IV, reading): pressure at density rho and specific internal
+ * energy e (with the cut-off) and the square of the bulk sound speed (isentropic derivative of the
+ * uncut pressure, floored at 0). */
+void orc_eos(const orc_params *P, int32_t mat, double rho, double e, double *p, double *cb2);
 /* Time step from the current state: CFL * h / max_i (c_i + |v_i|). */
 double orc_dt(const orc_params *P, const orc_state *S);
 /* Sec. II step g: forward Euler update of the state (in place) from the rates. */

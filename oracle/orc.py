@@ -38,7 +38,9 @@ def build(force: bool = False) -> str:
 
 
 class Material(C.Structure):
-    _fields_ = [("rho0", C.c_double), ("K", C.c_double), ("G", C.c_double), ("Y", C.c_double)]
+    _fields_ = [("rho0", C.c_double), ("K", C.c_double), ("G", C.c_double), ("Y", C.c_double),
+                ("eos", C.c_int32), ("pad", C.c_int32), ("c0", C.c_double), ("s", C.c_double),
+                ("gamma0", C.c_double), ("p_min", C.c_double)]
 
 
 class Wall(C.Structure):
@@ -107,6 +109,19 @@ def _ptr(a: np.ndarray, ct):
     return a.ctypes.data_as(C.POINTER(ct))
 
 
+def _material_eos(scene, k: int):
+    """(eos, c0, s, gamma0, p_min) of material k of a scene: its Mie-Gruneisen constants when given,
+    else the linear EOS; the pressure cut-off, else none."""
+    eos = getattr(scene, "eos", None)
+    pmin = getattr(scene, "p_min", None)
+    mg = eos[k] if eos is not None and k < len(eos) else None
+    cut = pmin[k] if pmin is not None and k < len(pmin) and pmin[k] is not None else -np.inf
+    if mg is None:
+        return 0, 0.0, 0.0, 0.0, float(cut)
+    c0, sl, g0 = mg
+    return 1, float(c0), float(sl), float(g0), float(cut)
+
+
 def params_of(scene) -> Params:
     """Oracle parameter block from a scene description (see paper_2310_03596_gb300.scenes)."""
     p = Params()
@@ -116,7 +131,8 @@ def params_of(scene) -> Params:
         p.g[a] = scene.gravity[a]
     p.nmat = len(scene.materials)
     for k, (rho0, K, G, Y) in enumerate(scene.materials):
-        p.mat[k] = Material(rho0, K, G, Y)
+        eos, c0, sl, g0, pmin = _material_eos(scene, k)
+        p.mat[k] = Material(rho0, K, G, Y, eos, 0, c0, sl, g0, pmin)
     p.h = scene.h
     p.cfl = scene.cfl
     p.nwalls = len(scene.walls)
@@ -191,6 +207,13 @@ def hash_keys(P: Params, x, y, z) -> np.ndarray:
     lib().orc_hash(C.byref(P), len(x), _ptr(x, C.c_double), _ptr(y, C.c_double), _ptr(z, C.c_double),
                    _ptr(key, C.c_uint32))
     return key
+
+
+def eos(P: Params, mat: int, rho: float, e: float):
+    """(p, bulk sound speed squared) of material mat at density rho and specific internal energy e."""
+    p, cb2 = C.c_double(), C.c_double()
+    lib().orc_eos(C.byref(P), C.c_int32(int(mat)), C.c_double(rho), C.c_double(e), C.byref(p), C.byref(cb2))
+    return p.value, cb2.value
 
 
 def sort_order(key: np.ndarray) -> np.ndarray:

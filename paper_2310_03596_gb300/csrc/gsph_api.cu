@@ -238,6 +238,9 @@ static bool config_ok(const gsph_config *c) {
     for (int k = 0; k < c->n_materials; ++k) {
         const gsph_material &m = c->materials[k];
         if (!(m.rho0 > 0) || !(m.K > 0) || !(m.G >= 0) || !(m.Y > 0)) return false;
+        if (m.eos != GSPH_EOS_LINEAR && m.eos != GSPH_EOS_MIE_GRUNEISEN) return false;
+        if (m.eos == GSPH_EOS_MIE_GRUNEISEN && (!(m.c0 > 0) || !(m.s >= 0) || !(m.gamma0 >= 0))) return false;
+        if (!(m.p_min <= 0.0)) return false;   // NaN and positive cut-offs rejected
     }
     if (c->n_walls < 0 || c->n_walls > GSPH_MAX_WALLS) return false;
     for (int k = 0; k < c->n_walls; ++k)
@@ -275,6 +278,11 @@ static void fill_params(const gsph_config &c, DevParams &P) {
         P.Mmod[k] = m.K + 4.0 * m.G / 3.0;
         P.f_rho0[k] = (float)m.rho0; P.f_K[k] = (float)m.K; P.f_G[k] = (float)m.G;
         P.f_Mmod[k] = (float)P.Mmod[k];
+        P.eos[k] = m.eos;
+        P.c0[k] = m.c0; P.s_hug[k] = m.s; P.gamma0[k] = m.gamma0;
+        P.p_min[k] = m.p_min;
+        P.f_c0[k] = (float)m.c0; P.f_sm1[k] = (float)(m.s - 1.0); P.f_g0[k] = (float)m.gamma0;
+        P.f_G43[k] = (float)(4.0 * m.G / 3.0);
     }
     double aw = 21.0 / (16.0 * PI * c.h * c.h * c.h);
     P.kdw = 5.0 * aw / c.h;
@@ -695,6 +703,8 @@ gsph_status gsph_adjoint_step(gsph_ctx *c, const double *lam_next, double *lam_p
                               void *stream) {
     if (!c || !lam_next || !lam_prev || !grad || !(dt > 0.0)) return GSPH_INVALID_ARG;
     if (c->split || !c->cfg.diagnostics) return GSPH_INVALID_ARG;
+    for (int k = 0; k < c->cfg.n_materials; ++k)   // the reverse mode covers the linear EOS without cut-off
+        if (c->cfg.materials[k].eos != GSPH_EOS_LINEAR || !std::isinf(c->cfg.materials[k].p_min)) return GSPH_INVALID_ARG;
     if (c->n == 0) return GSPH_NOT_READY;
     GSPH_CK(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;

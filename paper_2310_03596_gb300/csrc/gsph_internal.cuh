@@ -42,6 +42,11 @@ struct DevParams {
     float f_cell, f_inv_h, f_kdw, f_R2lo, f_R2hi;
     float f_inv_cell;        // FP32 rounding of the FP64 reciprocal of the bucket side
     float f_rho0[kMaxMat], f_K[kMaxMat], f_G[kMaxMat], f_Mmod[kMaxMat];
+    // equation of state per material (0 linear, 1 Mie-Gruneisen) and pressure cut-off
+    int eos[kMaxMat];
+    double c0[kMaxMat], s_hug[kMaxMat], gamma0[kMaxMat], p_min[kMaxMat];
+    // FP32 roundings for the signal speed: c0, s - 1, gamma0, 4G/3
+    float f_c0[kMaxMat], f_sm1[kMaxMat], f_g0[kMaxMat], f_G43[kMaxMat];
 };
 
 // Buffers, stream and events of the two-pass interaction order (Sec. II steps d-f), host side.
@@ -144,12 +149,75 @@ __device__ __forceinline__ void decode_cell(const DevParams &P, uint32_t c, int 
 // the FP32 roundings of m, w, v (the max over particles is order independent, so the time step is
 // reproducible bit for bit on any IEEE machine evaluating the same sequence).
 __device__ __forceinline__ float signal_speed32(const DevParams &P, int mat, double m, double w,
-                                                double vx, double vy, double vz) {
+                                                double vx, double vy, double vz, double E) {
     const float rho = __fdiv_rn((float)m, (float)w);
-    const float c = __fsqrt_rn(__fdiv_rn(P.f_Mmod[mat], rho));
     const float fx = (float)vx, fy = (float)vy, fz = (float)vz;
     const float v2 = __fadd_rn(__fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy)), __fmul_rn(fz, fz));
+    float c;
+    if (P.eos[mat] == 0) {
+        c = __fsqrt_rn(__fdiv_rn(P.f_Mmod[mat], rho));
+    } else {
+        // Mie-Gruneisen sound speed: the same FP32 sequence as the host reference, each operation
+        // correctly rounded (no contraction)
+        const float rho0 = P.f_rho0[mat], c0 = P.f_c0[mat], sm1 = P.f_sm1[mat], g0 = P.f_g0[mat];
+        const float e = __fsub_rn((float)E, __fmul_rn(0.5f, v2));
+        const float mu = __fsub_rn(__fdiv_rn(rho, rho0), 1.0f);
+        const float k0 = __fmul_rn(__fmul_rn(rho0, c0), c0);
+        float pH, dpH;
+        if (mu > 0.0f) {
+            const float D = __fsub_rn(1.0f, __fmul_rn(sm1, mu));
+            const float D2 = __fmul_rn(D, D);
+            const float q = __fadd_rn(1.0f, mu);
+            pH = __fdiv_rn(__fmul_rn(__fmul_rn(k0, mu), q), D2);
+            const float t1 = __fmul_rn(__fadd_rn(1.0f, __fmul_rn(2.0f, mu)), D);
+            const float t2 = __fmul_rn(__fmul_rn(2.0f, sm1), __fmul_rn(mu, q));
+            dpH = __fdiv_rn(__fmul_rn(k0, __fadd_rn(t1, t2)), __fmul_rn(D2, D));
+        } else {
+            pH = __fmul_rn(k0, mu);
+            dpH = k0;
+        }
+        const float q = __fadd_rn(1.0f, mu);
+        const float r2q = __fmul_rn(__fmul_rn(2.0f, rho0), q);
+        const float eH = __fdiv_rn(__fmul_rn(pH, mu), r2q);
+        const float deH = __fdiv_rn(__fadd_rn(__fmul_rn(__fmul_rn(dpH, mu), q), pH), __fmul_rn(r2q, q));
+        const float gr = __fmul_rn(g0, rho0);
+        const float p = __fadd_rn(pH, __fmul_rn(gr, __fsub_rn(e, eH)));
+        float cb2 = __fadd_rn(__fdiv_rn(__fsub_rn(dpH, __fmul_rn(gr, deH)), rho0),
+                              __fdiv_rn(__fmul_rn(p, gr), __fmul_rn(rho, rho)));
+        if (!(cb2 > 0.0f)) cb2 = 0.0f;
+        c = __fsqrt_rn(__fadd_rn(cb2, __fdiv_rn(P.f_G43[mat], rho)));
+    }
     return __fadd_rn(c, __fsqrt_rn(v2));
+}
+
+// Pressure (with the cut-off) and sound speed (bulk part from the isentropic derivative of the uncut
+// pressure, plus the shear part 4G/3rho) of material mat at density rho and specific internal energy
+// e, FP64. Linear EOS: p = K (rho/rho0 - 1), c^2 = (K + 4G/3) / rho.
+__device__ __forceinline__ void eos_pc(const DevParams &P, int mat, double rho, double e, double &p, double &c) {
+    if (P.eos[mat] == 0) {
+        p = P.K[mat] * (rho / P.rho0[mat] - 1.0);
+        c = sqrt(P.Mmod[mat] / rho);
+    } else {
+        const double rho0 = P.rho0[mat], sl = P.s_hug[mat], g0 = P.gamma0[mat];
+        const double mu = rho / rho0 - 1.0;
+        const double k0 = rho0 * P.c0[mat] * P.c0[mat];
+        double pH, dpH;
+        if (mu > 0.0) {
+            const double D = 1.0 - (sl - 1.0) * mu;
+            pH = k0 * mu * (1.0 + mu) / (D * D);
+            dpH = k0 * ((1.0 + 2.0 * mu) * D + 2.0 * (sl - 1.0) * mu * (1.0 + mu)) / (D * D * D);
+        } else {
+            pH = k0 * mu;
+            dpH = k0;
+        }
+        const double eH = pH * mu / (2.0 * rho0 * (1.0 + mu));
+        const double deH = (dpH * mu * (1.0 + mu) + pH) / (2.0 * rho0 * (1.0 + mu) * (1.0 + mu));
+        p = pH + g0 * rho0 * (e - eH);
+        double cb2 = (dpH - g0 * rho0 * deH) / rho0 + p * g0 * rho0 / (rho * rho);
+        if (!(cb2 > 0.0)) cb2 = 0.0;
+        c = sqrt(cb2 + 4.0 * P.G[mat] / (3.0 * rho));
+    }
+    if (p < P.p_min[mat]) p = P.p_min[mat];
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {

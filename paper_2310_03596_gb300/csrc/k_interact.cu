@@ -811,7 +811,8 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         B.f[FVZ][s] = nvz;
         B.f[FW][s] = wn;
         B.f[FM][s] = mn;
-        B.f[FE][s] = mE * inv_mn;
+        const double En = mE * inv_mn;
+        B.f[FE][s] = En;
         B.f[FSXX][s] = Sn[0];
         B.f[FSYY][s] = Sn[1];
         B.f[FSZZ][s] = Sn[2];
@@ -828,7 +829,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
             for (int k = 0; k < kNRate; ++k) a.rates_out[(size_t)s * kNRate + k] = acc.get(k);
         }
         // next step's CFL signal speed (correctly rounded FP32, reproducible bit for bit)
-        sp = signal_speed32(P, mt, mn, wn, nvx, nvy, nvz);
+        sp = signal_speed32(P, mt, mn, wn, nvx, nvy, nvz, En);
     }
     const unsigned b = __reduce_max_sync(kFullMask, __float_as_uint(sp));
     if (lane == 0) {

@@ -63,13 +63,23 @@ __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const u
             p4.y = (float)(y - (P.lo[1] + (double)cy * P.cell));
             p4.z = (float)(z - (P.lo[2] + (double)cz * P.cell));
         }
-        // p = K (rho/rho0 - 1) = K (m - rho0 w) / (rho0 w): the cancelling difference in FP64
-        double rw = P.rho0[mat] * w;
-        float pf = P.f_K[mat] * (float)(m - rw) / (float)rw;
         float rho = (float)m / (float)w;
-        float c = sqrtf(P.f_Mmod[mat] / rho);
+        float pf, Zf;
+        if (P.eos[mat] == 0) {
+            // p = K (rho/rho0 - 1) = K (m - rho0 w) / (rho0 w): the cancelling difference in FP64
+            double rw = P.rho0[mat] * w;
+            pf = P.f_K[mat] * (float)(m - rw) / (float)rw;
+            if (pf < (float)P.p_min[mat]) pf = (float)P.p_min[mat];
+            Zf = rho * sqrtf(P.f_Mmod[mat] / rho);
+        } else {   // Mie-Gruneisen in FP64 (its Hugoniot terms cancel as well), rounded once
+            double pd, cd;
+            const double rd = m / w;
+            eos_pc(P, mat, rd, E - 0.5 * (vx * vx + vy * vy + vz * vz), pd, cd);
+            pf = (float)pd;
+            Zf = (float)(rd * cd);
+        }
         r.a = make_float4((float)vx, (float)vy, (float)vz, rho);
-        r.b = make_float4(pf, rho * c, (float)E, (float)sxx);
+        r.b = make_float4(pf, Zf, (float)E, (float)sxx);
         r.c = make_float4((float)syy, (float)sxy, (float)sxz, (float)syz);
         ((float4 *)pos_out)[s] = p4;
         ((RecF *)rec_out)[s] = r;
@@ -77,8 +87,8 @@ __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const u
     } else {
         RecD r;
         double rho = m / w;
-        double pr = P.K[mat] * (rho / P.rho0[mat] - 1.0);
-        double c = sqrt(P.Mmod[mat] / rho);
+        double pr, c;
+        eos_pc(P, mat, rho, E - 0.5 * (vx * vx + vy * vy + vz * vz), pr, c);
         r.a = make_d4(vx, vy, vz, rho);
         r.b = make_d4(pr, rho * c, E, sxx);
         r.c = make_d4(syy, szz, sxy, sxz);
@@ -287,7 +297,7 @@ __global__ void k_signal_max(DevParams P, int64_t n, State A, unsigned int *__re
     float v = 0.0f;
     if (i < n) {
         int m = A.mat[i] < P.nmat ? A.mat[i] : 0;
-        v = signal_speed32(P, m, A.f[FM][i], A.f[FW][i], A.f[FVX][i], A.f[FVY][i], A.f[FVZ][i]);
+        v = signal_speed32(P, m, A.f[FM][i], A.f[FW][i], A.f[FVX][i], A.f[FVY][i], A.f[FVZ][i], A.f[FE][i]);
     }
     const unsigned b = __reduce_max_sync(kFullMask, __float_as_uint(v));
     if ((threadIdx.x & 31) == 0) atomicMax(sig, b);

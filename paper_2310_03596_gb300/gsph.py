@@ -12,6 +12,8 @@ import threading
 
 import numpy as np
 
+from . import scenes
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libgsph.so")
 
@@ -39,7 +41,9 @@ class GsphError(RuntimeError):
 
 
 class Material(C.Structure):
-    _fields_ = [("rho0", C.c_double), ("K", C.c_double), ("G", C.c_double), ("Y", C.c_double)]
+    _fields_ = [("rho0", C.c_double), ("K", C.c_double), ("G", C.c_double), ("Y", C.c_double),
+                ("eos", C.c_int32), ("pad", C.c_int32), ("c0", C.c_double), ("s", C.c_double),
+                ("gamma0", C.c_double), ("p_min", C.c_double)]
 
 
 class Wall(C.Structure):
@@ -142,7 +146,8 @@ def config_from_scene(scene, precision: int = FP32_SPLIT, device: int = 0, diagn
         c.gravity[a] = scene.gravity[a]
     c.n_materials = len(scene.materials)
     for k, (rho0, K, G, Y) in enumerate(scene.materials):
-        c.materials[k] = Material(rho0, K, G, Y)
+        eos, c0, sl, g0, pmin = scenes.material_eos(scene, k)
+        c.materials[k] = Material(rho0, K, G, Y, eos, 0, c0, sl, g0, pmin)
     c.h = scene.h
     c.cfl = scene.cfl
     c.n_walls = len(scene.walls)

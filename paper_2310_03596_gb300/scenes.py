@@ -16,6 +16,8 @@ Workloads (sizes as stated by the workload definitions; dx lattice spacing, h = 
   projectile_plate  steel sphere r 5 mm at 1000 m/s onto an aluminium plate 60x60x10 mm, dx 0.2 mm,
                     K = 8 equal-count x-slabs, two materials
   collapse_block    aluminium block 0.4 x 0.2 x 0.1 m at dx 0.5 mm (64 M) on a floor, gravity, K = 16
+  hvi_bead_plate    aluminium bead r 1.5 mm at 4.05 km/s, 32 degrees from the normal, onto a 2 mm
+                    aluminium plate (Sec. IV); Mie-Gruneisen EOS with a spall cut-off, K = 4 x-slabs
 """
 from __future__ import annotations
 
@@ -31,6 +33,14 @@ _M2 = np.uint64(0x94D049BB133111EB)
 # Materials: (rho0 kg/m^3, bulk modulus K Pa, shear modulus G Pa, yield stress Y Pa)
 ALUMINIUM = (2700.0, 70.0e9, 26.0e9, 300.0e6)
 STEEL = (7850.0, 160.0e9, 80.0e9, 1.0e9)
+
+# Aluminium for the hypervelocity example (Sec. IV names Johnson-Cook in its elastic perfectly plastic
+# limit with a Mie-Gruneisen EOS and a spall cut-off pressure, without values). These are inputs, the
+# published constants of 6061-T6 aluminium (Steinberg's tables): rho0, c0, s, gamma0, G, and a yield
+# stress and spall cut-off of that alloy. K = rho0 c0^2 (only the linear EOS would use it).
+AL6061_RHO0, AL6061_C0, AL6061_S, AL6061_GAMMA0 = 2703.0, 5240.0, 1.40, 1.97
+AL6061 = (AL6061_RHO0, AL6061_RHO0 * AL6061_C0 ** 2, 27.6e9, 290.0e6)
+AL6061_P_MIN = -1.2e9
 
 
 def splitmix64_draw(seed: int, ids: np.ndarray, k: int) -> np.ndarray:
@@ -71,6 +81,8 @@ class Scene:
     alpha: float
     steps: int
     dx: float
+    eos: list = None           # per material: None (linear, K) or (c0, s, gamma0) Mie-Gruneisen
+    p_min: list = None         # per material: pressure cut-off (Pa, <= 0) or None
 
     @property
     def n(self) -> int:
@@ -188,6 +200,50 @@ def collapse_block(dx: float = 0.5e-3, size=(0.4, 0.2, 0.1), seed: int = 4, K: i
                  (0.0, 0.0, -gravity), K, swap_period, 0.1, steps, dx)
 
 
+def hvi_bead_plate(dx: float = 0.1e-3, radius: float = 1.5e-3, thickness: float = 2.0e-3,
+                   side: float = 12.0e-3, speed: float = 4050.0, angle_deg: float = 32.0, seed: int = 5,
+                   K: int = 4, swap_period: int = 10, steps: int = 200) -> Scene:
+    """Aluminium bead just above an aluminium plate (top face z = 0), moving at `speed` tilted by
+    `angle_deg` from the plate normal (the paper's hypervelocity example); Mie-Gruneisen EOS and spall
+    cut-off for both."""
+    h = 1.3 * dx
+    px, pz = int(round(side / dx)), int(round(thickness / dx))
+    plate = _lattice(px, px, pz, dx, origin=(-px * dx / 2, -px * dx / 2, -pz * dx))
+    nr = int(round(radius / dx))
+    bead = _lattice(2 * nr, 2 * nr, 2 * nr, dx, origin=(-nr * dx, -nr * dx, -nr * dx))
+    bead = bead[(bead ** 2).sum(axis=1) <= radius ** 2]
+    a = math.radians(angle_deg)
+    bead[:, 0] -= (radius + dx) * math.tan(a)    # aimed at the plate centre
+    bead[:, 2] += radius + dx
+    pos = np.concatenate([plate, bead])
+    ids = np.arange(pos.shape[0], dtype=np.uint64)
+    pos = _jitter(pos, ids, seed, 0.01 * dx)
+    n = pos.shape[0]
+    vel = np.zeros((n, 3))
+    nb = bead.shape[0]
+    vel[n - nb:, 0] = speed * math.sin(a)
+    vel[n - nb:, 2] = -speed * math.cos(a)
+    order = np.argsort(pos[:, 0], kind="stable")
+    label = np.empty(n, np.uint8)
+    label[order] = (np.arange(n) * K // n).astype(np.uint8)
+    m = 4.0e-3
+    lo, dims = _grid_around(pos, h, (m, m, m), (m, m, m))
+    return Scene("hvi_bead_plate", pos, vel, np.full(n, dx ** 3), np.zeros(n, np.uint8), label, [AL6061],
+                 h, 0.3, lo, dims, [], (0.0, 0.0, 0.0), K, swap_period, 0.1, steps, dx,
+                 eos=[(AL6061_C0, AL6061_S, AL6061_GAMMA0)], p_min=[AL6061_P_MIN])
+
+
+def material_eos(scene, k: int):
+    """(eos, c0, s, gamma0, p_min) of material k: 1 and its Mie-Gruneisen constants when the scene
+    gives them, else 0 (linear EOS); the pressure cut-off, else -inf (none)."""
+    mg = scene.eos[k] if scene.eos is not None and k < len(scene.eos) else None
+    pm = scene.p_min[k] if scene.p_min is not None and k < len(scene.p_min) and scene.p_min[k] is not None \
+        else -math.inf
+    if mg is None:
+        return 0, 0.0, 0.0, 0.0, float(pm)
+    return 1, float(mg[0]), float(mg[1]), float(mg[2]), float(pm)
+
+
 def adjoint_cube(n_side: int = 64, seed: int = 3, steps: int = 200) -> Scene:
     """The cube impact scaled up, used for the gradient workload."""
     s = cube_impact(n_side=n_side, seed=seed, steps=steps)
@@ -196,6 +252,7 @@ def adjoint_cube(n_side: int = 64, seed: int = 3, steps: int = 200) -> Scene:
 
 
 WORKLOADS = {
+    "hvi_bead_plate": hvi_bead_plate,
     "cube_impact": cube_impact,
     "taylor_bar": taylor_bar,
     "projectile_plate": projectile_plate,

@@ -145,6 +145,53 @@ def test_two_pass_order_equals_one_pass():
         two.close()
 
 
+@pytest.mark.parametrize("precision,tol", [(gsph.FP64, 1e-12), (gsph.FP32_SPLIT, 2e-5)])
+def test_hypervelocity_mie_gruneisen_lockstep(precision, tol):
+    # Sec. IV's example at a coarse spacing: aluminium bead at 4.05 km/s, 32 degrees, onto a 2 mm plate;
+    # Mie-Gruneisen EOS (compression branch at the contact) and spall cut-off, 4 labels, swaps
+    s = scenes.hvi_bead_plate(dx=0.25e-3, swap_period=2)
+    _lockstep(s, precision, 4, tol)
+
+
+@pytest.mark.parametrize("precision,tol", [(gsph.FP64, 1e-12), (gsph.FP32_SPLIT, 2e-5)])
+def test_tension_beyond_the_spall_cut_off_lockstep(precision, tol):
+    # an expanding block (v = 2e6/s * x) goes into tension at once; with the cut-off at -0.3 GPa the
+    # pressure of most particles is floored within the first steps (expansion branch of Mie-Gruneisen)
+    s = scenes.cube_impact(n_side=10, seed=13)
+    s.eos, s.p_min = [(scenes.AL6061_C0, scenes.AL6061_S, scenes.AL6061_GAMMA0)], [-3.0e8]
+    c = s.pos.mean(axis=0)
+    s.vel = 2.0e6 * (s.pos - c) * s.dx / s.dx
+    s.walls = []
+    P = orc.params_of(s)
+    _lockstep(s, precision, 4, tol)
+    sol = gsph.Solver.from_scene(s, precision=precision)
+    try:
+        sol.step(3)
+        st = sol.state()
+        rho = st["m"] / st["w"]
+        cut = 0
+        for i in range(len(rho)):
+            e = st["E"][i] - 0.5 * (st["vx"][i] ** 2 + st["vy"][i] ** 2 + st["vz"][i] ** 2)
+            p, _ = orc.eos(P, 0, rho[i], e)
+            cut += p == -3.0e8
+        assert cut > len(rho) // 2          # the floor is active for most particles
+    finally:
+        sol.close()
+
+
+def test_adjoint_refuses_other_equations_of_state():
+    s = scenes.hvi_bead_plate(dx=0.5e-3)
+    sol = gsph.Solver.from_scene(s, precision=gsph.FP64, diagnostics=True)
+    try:
+        import torch
+        lam = torch.zeros((15, s.n), dtype=torch.float64, device="cuda")
+        with pytest.raises(gsph.GsphError) as ei:
+            sol.adjoint_step(lam, torch.empty_like(lam), 1e-9)
+        assert ei.value.code == gsph.INVALID_ARG
+    finally:
+        sol.close()
+
+
 def test_split_free_running_100_steps():
     s = scenes.cube_impact(n_side=12, steps=100)
     P = orc.params_of(s)
