@@ -142,6 +142,11 @@ typedef struct {
     int64_t pairs_total;                /* ordered pair interactions evaluated (sum over particles of
                                            real + image neighbours) since gsph_set_particles */
     int64_t kernel_launches;            /* kernels this context launched since gsph_set_particles */
+    /* workload cost per label (the cost function of Sec. V, from each particle's actual neighbour
+       number): pair interactions (real + image neighbours) of the particles of each label in the last
+       step, and max over labels / mean over labels */
+    int64_t cost[GSPH_MAX_LABELS];
+    double cost_imbalance;
 } gsph_exchange_stats;
 
 typedef struct {

@@ -37,8 +37,9 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
                             const double *xs, const double *ys, const double *zs, int kmax, uint2 *list,
                             uint32_t *cnt, const uint32_t *perm, const State &A, const State &B, cudaEvent_t mid,
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
-                            unsigned int *sig, unsigned long long *pairs, int32_t *nreal, int32_t *nimage,
-                            double *rates, const OverlapBufs *ov, cudaStream_t s);
+                            unsigned int *sig, unsigned long long *pairs, unsigned long long *cost,
+                            int32_t *nreal, int32_t *nimage, double *rates, const OverlapBufs *ov,
+                            cudaStream_t s);
 // k_swap.cu
 size_t swap_scratch_bytes(int K, int nmat);
 cudaError_t launch_round_positions(int64_t n, const double *x, const double *y, const double *z, float *xf,
@@ -102,6 +103,7 @@ struct gsph_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     unsigned gather_grid = 0, boundary_grid = 0;
     unsigned long long *label_off = nullptr;   // K + 1
+    unsigned long long *cost = nullptr;        // pair interactions per label, last step
     unsigned long long *garbage = nullptr;
     unsigned int *sig = nullptr;
     unsigned long long *pairs = nullptr;
@@ -189,6 +191,7 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     A_(dalloc(c, &c->blist, N));
     A_(dalloc(c, &c->bcounts, (size_t)kMaxLabel * (size_t)comm_blocks(n)));
     A_(dalloc(c, &c->label_off, (size_t)kMaxLabel + 1));
+    A_(dalloc(c, &c->cost, (size_t)kMaxLabel));
     A_(dalloc(c, &c->garbage, 1));
     A_(dalloc(c, &c->sig, 1));
     A_(dalloc(c, &c->pairs, 1));
@@ -281,6 +284,7 @@ static void fill_params(const gsph_config &c, DevParams &P) {
         P.eos[k] = m.eos;
         P.c0[k] = m.c0; P.s_hug[k] = m.s; P.gamma0[k] = m.gamma0;
         P.p_min[k] = m.p_min;
+        P.inv_rho0[k] = 1.0 / m.rho0; P.k0[k] = m.rho0 * m.c0 * m.c0; P.inv_2rho0[k] = 1.0 / (2.0 * m.rho0);
         P.f_c0[k] = (float)m.c0; P.f_sm1[k] = (float)(m.s - 1.0); P.f_g0[k] = (float)m.gamma0;
         P.f_G43[k] = (float)(4.0 * m.G / 3.0);
     }
@@ -360,6 +364,7 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     c->launches += 4;
     rec_event(c, PH_COMM, s);
     // f-g. interaction loop fused with the integration; next dt
+    GSPH_CK(cudaMemsetAsync(c->cost, 0, (size_t)kMaxLabel * sizeof(unsigned long long), s));
     OverlapBufs ov{};
     if (c->cfg.overlap) {
         ov = OverlapBufs{c->flag, c->blist, c->label_off + P.K_labels, c->hidx, c->hpos, c->hrec, c->hcx, c->part,
@@ -368,8 +373,8 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     }
     GSPH_CK(launch_interact(c->split, c->cfg.diagnostics != 0, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs,
                             c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, phase_event(c, PH_LIST),
-                            c->lab_s, c->mat_s, c->id_s, c->dt, c->sig, c->pairs, c->nreal, c->nimage, c->rates,
-                            c->cfg.overlap ? &ov : nullptr, s));
+                            c->lab_s, c->mat_s, c->id_s, c->dt, c->sig, c->pairs, c->cost, c->nreal, c->nimage,
+                            c->rates, c->cfg.overlap ? &ov : nullptr, s));
     if (c->cfg.overlap) c->launches += 2;   // halo gather, second pair pass
     GSPH_CK(launch_finalize_dt(P, c->sig, c->dt, s));
     c->launches += 3;
@@ -399,7 +404,7 @@ static gsph_status enqueue_forward_pieces(gsph_ctx *c, cudaStream_t s) {
                            c->cellr, c->cxs, c->pos, c->rec, nullptr, nullptr, nullptr, c->err, s));
     GSPH_CK(launch_interact(c->split, true, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs, c->ys, c->zs,
                             kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr, c->lab_s, c->mat_s, c->id_s,
-                            c->dt, c->sig, c->pairs, c->nreal, c->nimage, c->rates, nullptr, s));
+                            c->dt, c->sig, c->pairs, c->cost, c->nreal, c->nimage, c->rates, nullptr, s));
     c->launches += 4 + 3 * radix_passes(key_bits(P.ncell));
     c->dt_dirty = true;   // the signal-speed word now holds the scratch state's maximum
     return GSPH_OK;
@@ -635,8 +640,9 @@ gsph_status gsph_get_exchange_stats(gsph_ctx *c, void *stream, gsph_exchange_sta
     GSPH_CK(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
     std::memset(out, 0, sizeof(*out));
-    unsigned long long off[kMaxLabel + 1] = {0}, garb = 0, moved = 0, pairs = 0;
+    unsigned long long off[kMaxLabel + 1] = {0}, garb = 0, moved = 0, pairs = 0, cost[kMaxLabel] = {0};
     GSPH_CK(cudaMemcpyAsync(off, c->label_off, sizeof(off), cudaMemcpyDeviceToHost, s));
+    GSPH_CK(cudaMemcpyAsync(cost, c->cost, sizeof(cost), cudaMemcpyDeviceToHost, s));
     GSPH_CK(cudaMemcpyAsync(&garb, c->garbage, sizeof(garb), cudaMemcpyDeviceToHost, s));
     GSPH_CK(cudaMemcpyAsync(&moved, swap_moved_ptr(c->swap_scratch), sizeof(moved), cudaMemcpyDeviceToHost, s));
     GSPH_CK(cudaMemcpyAsync(&pairs, c->pairs, sizeof(pairs), cudaMemcpyDeviceToHost, s));
@@ -659,6 +665,15 @@ gsph_status gsph_get_exchange_stats(gsph_ctx *c, void *stream, gsph_exchange_sta
     out->swap_passes = c->swap_passes;
     out->pairs_total = (int64_t)pairs;
     out->kernel_launches = c->launches;
+    if (c->have_step) {
+        double mx = 0.0, sum = 0.0;
+        for (int k = 0; k < K; ++k) {
+            out->cost[k] = (int64_t)cost[k];
+            sum += (double)cost[k];
+            mx = mx > (double)cost[k] ? mx : (double)cost[k];
+        }
+        out->cost_imbalance = sum > 0.0 ? mx / (sum / K) : 0.0;
+    }
     return out->garbage > 0 ? GSPH_PARTICLE_LEFT_DOMAIN : GSPH_OK;
 }
 

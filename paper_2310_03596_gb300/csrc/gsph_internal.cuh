@@ -45,6 +45,7 @@ struct DevParams {
     // equation of state per material (0 linear, 1 Mie-Gruneisen) and pressure cut-off
     int eos[kMaxMat];
     double c0[kMaxMat], s_hug[kMaxMat], gamma0[kMaxMat], p_min[kMaxMat];
+    double inv_rho0[kMaxMat], k0[kMaxMat], inv_2rho0[kMaxMat];   // 1/rho0, rho0 c0^2, 1/(2 rho0)
     // FP32 roundings for the signal speed: c0, s - 1, gamma0, 4G/3
     float f_c0[kMaxMat], f_sm1[kMaxMat], f_g0[kMaxMat], f_G43[kMaxMat];
 };
@@ -198,24 +199,26 @@ __device__ __forceinline__ void eos_pc(const DevParams &P, int mat, double rho, 
         p = P.K[mat] * (rho / P.rho0[mat] - 1.0);
         c = sqrt(P.Mmod[mat] / rho);
     } else {
-        const double rho0 = P.rho0[mat], sl = P.s_hug[mat], g0 = P.gamma0[mat];
-        const double mu = rho / rho0 - 1.0;
-        const double k0 = rho0 * P.c0[mat] * P.c0[mat];
+        // the reference's formulas with three divisions (1/D, 1/(1 + mu), 1/rho); FP64 scarce on GB300
+        const double sm1 = P.s_hug[mat] - 1.0, gr = P.gamma0[mat] * P.rho0[mat], k0 = P.k0[mat];
+        const double mu = rho * P.inv_rho0[mat] - 1.0;
+        const double q = 1.0 + mu, iq = 1.0 / q;
         double pH, dpH;
         if (mu > 0.0) {
-            const double D = 1.0 - (sl - 1.0) * mu;
-            pH = k0 * mu * (1.0 + mu) / (D * D);
-            dpH = k0 * ((1.0 + 2.0 * mu) * D + 2.0 * (sl - 1.0) * mu * (1.0 + mu)) / (D * D * D);
+            const double D = 1.0 - sm1 * mu, iD = 1.0 / D;
+            pH = k0 * mu * q * iD * iD;
+            dpH = k0 * ((1.0 + 2.0 * mu) * D + 2.0 * sm1 * mu * q) * iD * iD * iD;
         } else {
             pH = k0 * mu;
             dpH = k0;
         }
-        const double eH = pH * mu / (2.0 * rho0 * (1.0 + mu));
-        const double deH = (dpH * mu * (1.0 + mu) + pH) / (2.0 * rho0 * (1.0 + mu) * (1.0 + mu));
-        p = pH + g0 * rho0 * (e - eH);
-        double cb2 = (dpH - g0 * rho0 * deH) / rho0 + p * g0 * rho0 / (rho * rho);
+        const double eH = pH * mu * iq * P.inv_2rho0[mat];
+        const double deH = (dpH * mu * q + pH) * iq * iq * P.inv_2rho0[mat];
+        p = pH + gr * (e - eH);
+        const double irho = 1.0 / rho;
+        double cb2 = (dpH - gr * deH) * P.inv_rho0[mat] + p * gr * irho * irho;
         if (!(cb2 > 0.0)) cb2 = 0.0;
-        c = sqrt(cb2 + 4.0 * P.G[mat] / (3.0 * rho));
+        c = sqrt(cb2 + 4.0 * P.G[mat] / 3.0 * irho);
     }
     if (p < P.p_min[mat]) p = P.p_min[mat];
 }

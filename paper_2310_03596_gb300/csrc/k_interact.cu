@@ -466,6 +466,7 @@ struct PairArgs {
     const double *dt_ptr;
     unsigned int *sig;
     unsigned long long *pairs;
+    unsigned long long *cost;    // pair interactions per label of this step (Sec. V cost function)
     int32_t *nreal_out, *nimage_out;
     double *rates_out;
     // two-pass order only
@@ -836,6 +837,14 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         atomicMax(a.sig, b);
         atomicAdd(a.pairs, (unsigned long long)pc);
     }
+    // cost per label: this pass's pairs of the particle, summed over the lanes of each label
+    {
+        const uint32_t lab = valid ? (uint32_t)a.lab_s[s] : 0xffffffffu;
+        const unsigned mine = (unsigned)(ntaken + (int)nover + (ni - ni0));
+        const unsigned peers = __match_any_sync(kFullMask, lab);
+        const unsigned sum = __reduce_add_sync(peers, valid ? mine : 0u);
+        if (valid && (__ffs(peers) - 1) == lane && sum) atomicAdd(&a.cost[lab], (unsigned long long)sum);
+    }
 }
 
 template <bool SPLIT, bool DIAG, int MODE>
@@ -876,15 +885,16 @@ static PairArgs<SPLIT> pair_args(const DevParams &P, int64_t n, const uint32_t *
                                  const double *ys, const double *zs, int kmax, const uint2 *list,
                                  const uint32_t *cnt, const uint32_t *perm, const State &A, const State &B,
                                  const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s,
-                                 const double *dt, unsigned int *sig, unsigned long long *pairs, int32_t *nreal,
-                                 int32_t *nimage, double *rates, const OverlapBufs *ov) {
+                                 const double *dt, unsigned int *sig, unsigned long long *pairs,
+                                 unsigned long long *cost, int32_t *nreal, int32_t *nimage, double *rates,
+                                 const OverlapBufs *ov) {
     using Pos = typename Types<SPLIT>::Pos;
     using Rec = typename Types<SPLIT>::Rec;
     PairArgs<SPLIT> a;
     a.P = P; a.n = n; a.skey = skey; a.cellr = cellr; a.pos = (const Pos *)pos; a.rec = (const Rec *)rec;
     a.cxs = cxs; a.xs = xs; a.ys = ys; a.zs = zs; a.kmax = kmax; a.list = list; a.cnt_in = cnt; a.perm = perm;
     a.A = A; a.B = B; a.lab_s = lab_s; a.mat_s = mat_s; a.id_s = id_s; a.dt_ptr = dt; a.sig = sig;
-    a.pairs = pairs; a.nreal_out = nreal; a.nimage_out = nimage; a.rates_out = rates;
+    a.pairs = pairs; a.cost = cost; a.nreal_out = nreal; a.nimage_out = nimage; a.rates_out = rates;
     a.flag = ov ? ov->flag : nullptr;
     a.blist = ov ? ov->blist : nullptr;
     a.btotal = ov ? ov->btotal : nullptr;
@@ -902,14 +912,15 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
                             const double *xs, const double *ys, const double *zs, int kmax, uint2 *list,
                             uint32_t *cnt, const uint32_t *perm, const State &A, const State &B, cudaEvent_t mid,
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
-                            unsigned int *sig, unsigned long long *pairs, int32_t *nreal, int32_t *nimage,
-                            double *rates, const OverlapBufs *ov, cudaStream_t s) {
+                            unsigned int *sig, unsigned long long *pairs, unsigned long long *cost,
+                            int32_t *nreal, int32_t *nimage, double *rates, const OverlapBufs *ov,
+                            cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const unsigned gl = (unsigned)((n + NL_THREADS - 1) / NL_THREADS);
     const unsigned gp = (unsigned)((n + PK_THREADS - 1) / PK_THREADS);
 #define GSPH_NL_ARGS P, n, skey, cellr, (const typename Types<SP>::Pos *)pos, cxs, xs, ys, zs, kmax, list, cnt
 #define GSPH_PAIR_ARGS pair_args<SP>(P, n, skey, cellr, pos, rec, cxs, xs, ys, zs, kmax, list, cnt, perm, A, B, \
-                                     lab_s, mat_s, id_s, dt, sig, pairs, nreal, nimage, rates, ov)
+                                     lab_s, mat_s, id_s, dt, sig, pairs, cost, nreal, nimage, rates, ov)
 #define GSPH_PAIRS(MODE_)                                                                   \
     do {                                                                                    \
         const auto pa = GSPH_PAIR_ARGS;                                                      \

@@ -65,11 +65,13 @@ class ExchangeStats(C.Structure):
                 ("exchange_fraction", C.c_double), ("record_bytes", C.c_int64),
                 ("bytes_hash_broadcast", C.c_int64), ("bytes_boundary_broadcast", C.c_int64),
                 ("bytes_swap", C.c_int64), ("swapped_last_pass", C.c_int64), ("swap_passes", C.c_int64),
-                ("pairs_total", C.c_int64), ("kernel_launches", C.c_int64)]
+                ("pairs_total", C.c_int64), ("kernel_launches", C.c_int64),
+                ("cost", C.c_int64 * MAX_LABEL), ("cost_imbalance", C.c_double)]
 
     def as_dict(self) -> dict:
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("pad", "boundary")}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("pad", "boundary", "cost")}
         d["boundary"] = list(self.boundary)[: self.K]
+        d["cost"] = list(self.cost)[: self.K]
         return d
 
 

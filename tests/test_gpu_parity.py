@@ -50,6 +50,9 @@ def _lockstep(scene, precision, steps, tol, swap=True, overlap=False):
             assert np.array_equal(sol.get("comm_hash"), out["comm"]), "communication hash"
             stats = sol.exchange_stats()
             assert stats["boundary"] == out["count"].tolist()
+            # the Sec. V cost function: pair interactions per label
+            cost = np.bincount(st.label, weights=out["nreal"] + out["nimage"], minlength=scene.K)
+            assert stats["cost"] == cost.astype(np.int64).tolist(), "cost per label"
             off, lst = orc.boundary_lists(st.label, out["comm"], P.dims[0] * P.dims[1] * P.dims[2], scene.K)
             assert np.array_equal(sol.get("boundary"), lst), "boundary set order"
             for f in STATE_F:
