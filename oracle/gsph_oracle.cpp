@@ -435,12 +435,17 @@ template <class T> void mats_of(const orc_params *P, Mat<T> *m) {
     }
 }
 
+// Rates of every particle (or of a subset). The neighbour search (hash, buckets, support predicate)
+// uses the positions of `search` (the state itself when null), the fluxes the state s: the second
+// stage of the Heun step evaluates the predicted state over the neighbour set of the step's start.
 template <class T>
 void rates_all(const orc_params *P, const StateT<T> &s, const Mat<T> *mats, int64_t nsub,
-               const int64_t *subset, T *rates, int32_t *nreal, int32_t *nimage) {
+               const int64_t *subset, T *rates, int32_t *nreal, int32_t *nimage,
+               const StateT<T> *search = nullptr) {
     int64_t n = s.n;
+    const StateT<T> &q = search ? *search : s;
     std::vector<double> xv(n), yv(n), zv(n);
-    for (int64_t i = 0; i < n; ++i) { xv[i] = val(s.x[i]); yv[i] = val(s.y[i]); zv[i] = val(s.z[i]); }
+    for (int64_t i = 0; i < n; ++i) { xv[i] = val(q.x[i]); yv[i] = val(q.y[i]); zv[i] = val(q.z[i]); }
     std::vector<uint32_t> key(n);
     orc_hash(P, n, xv.data(), yv.data(), zv.data(), key.data());
     Buckets b = make_buckets(P, n, key.data());
@@ -846,7 +851,7 @@ void orc_step(const orc_params *P, orc_state *S, int32_t do_swap, uint32_t *key_
               uint32_t *comm_out, uint8_t *flag_out, int64_t *count_out, int32_t *nreal_out,
               int32_t *nimage_out, double *rates_out, double *dt_out) {
     int64_t n = S->n;
-    double dt = orc_dt(P, S);
+    double dt = (dt_out && *dt_out > 0.0) ? *dt_out : orc_dt(P, S);
     // a. hash, then the radix-sort step: a stable order by hash
     std::vector<uint32_t> key(n);
     orc_hash(P, n, S->x, S->y, S->z, key.data());
@@ -880,7 +885,37 @@ void orc_step(const orc_params *P, orc_state *S, int32_t do_swap, uint32_t *key_
     std::vector<double> rates((size_t)n * ORC_NRATE);
     std::vector<int32_t> nr(n), ni(n);
     rates_all(P, s, mats, 0, nullptr, rates.data(), nr.data(), ni.data());
-    for (int64_t i = 0; i < n; ++i) integrate_one(P, s, mats, i, rates.data() + ORC_NRATE * i, dt);
+    if (P->integrator == 1) {
+        // two-stage Heun in its strong-stability-preserving form (reading of the second-order variant):
+        // y* = E(y_n), y_{n+1} = (y_n + E(y*)) / 2 with E the forward Euler stage (radial return
+        // included), both stages over the neighbour set of y_n; the average is taken on the conserved
+        // variables (w, m, m v, m E, x, S), so the stress stays inside the convex yield set
+        StateT<double> s1 = s;
+        for (int64_t i = 0; i < n; ++i) integrate_one(P, s1, mats, i, rates.data() + ORC_NRATE * i, dt);
+        std::vector<double> r2((size_t)n * ORC_NRATE);
+        rates_all(P, s1, mats, 0, nullptr, r2.data(), nullptr, nullptr, &s);
+        StateT<double> s2 = s1;
+        for (int64_t i = 0; i < n; ++i) integrate_one(P, s2, mats, i, r2.data() + ORC_NRATE * i, dt);
+        for (int64_t i = 0; i < n; ++i) {
+            double m = 0.5 * (s.m[i] + s2.m[i]);
+            double mv[3] = {0.5 * (s.m[i] * s.vx[i] + s2.m[i] * s2.vx[i]),
+                            0.5 * (s.m[i] * s.vy[i] + s2.m[i] * s2.vy[i]),
+                            0.5 * (s.m[i] * s.vz[i] + s2.m[i] * s2.vz[i])};
+            double mE = 0.5 * (s.m[i] * s.E[i] + s2.m[i] * s2.E[i]);
+            s.w[i] = 0.5 * (s.w[i] + s2.w[i]);
+            s.x[i] = 0.5 * (s.x[i] + s2.x[i]);
+            s.y[i] = 0.5 * (s.y[i] + s2.y[i]);
+            s.z[i] = 0.5 * (s.z[i] + s2.z[i]);
+            for (int k = 0; k < 6; ++k) s.S[k][i] = 0.5 * (s.S[k][i] + s2.S[k][i]);
+            s.m[i] = m;
+            s.vx[i] = mv[0] / m;
+            s.vy[i] = mv[1] / m;
+            s.vz[i] = mv[2] / m;
+            s.E[i] = mE / m;
+        }
+    } else {
+        for (int64_t i = 0; i < n; ++i) integrate_one(P, s, mats, i, rates.data() + ORC_NRATE * i, dt);
+    }
     store(s, S);
     if (key_out) std::copy(skey.begin(), skey.end(), key_out);
     if (comm_out) std::copy(comm.begin(), comm.end(), comm_out);

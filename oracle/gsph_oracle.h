@@ -53,6 +53,9 @@ typedef struct {
     orc_wall wall[ORC_MAX_WALL];
     double g[3];                     /* body acceleration */
     double alpha;                    /* Cg bias towards the all-types Cg (Sec. III.B) */
+    int32_t integrator;              /* 0: forward Euler; 1: two-stage Heun (SSP-RK2), both stages with
+                                        the neighbour set of the step's start */
+    int32_t pad2;
 } orc_params;
 
 typedef struct {
@@ -122,6 +125,7 @@ int64_t orc_swap_pass(const orc_params *P, int64_t n, const double *x, const dou
  * swap pass if do_swap; communication hash; interaction loop; integration. The state is
  * replaced by the new state in the sorted order. Outputs (each may be null): sorted keys,
  * communication hash, flags, per-label flag counts, neighbour counts, the rates used, dt. */
+/* dt_out: in, a fixed time step when > 0 (else the CFL step); out, the step's dt. */
 void orc_step(const orc_params *P, orc_state *S, int32_t do_swap, uint32_t *key_out,
               uint32_t *comm_out, uint8_t *flag_out, int64_t *count_out, int32_t *nreal_out,
               int32_t *nimage_out, double *rates_out, double *dt_out);

@@ -51,7 +51,7 @@ class Params(C.Structure):
     _fields_ = [("lo", C.c_double * 3), ("dims", C.c_int32 * 3), ("nmat", C.c_int32),
                 ("h", C.c_double), ("cfl", C.c_double), ("mat", Material * MAX_MAT),
                 ("nwalls", C.c_int32), ("K", C.c_int32), ("wall", Wall * MAX_WALL),
-                ("g", C.c_double * 3), ("alpha", C.c_double)]
+                ("g", C.c_double * 3), ("alpha", C.c_double), ("integrator", C.c_int32), ("pad2", C.c_int32)]
 
 
 _DP = C.POINTER(C.c_double)
@@ -135,6 +135,7 @@ def params_of(scene) -> Params:
         p.mat[k] = Material(rho0, K, G, Y, eos, 0, c0, sl, g0, pmin)
     p.h = scene.h
     p.cfl = scene.cfl
+    p.integrator = int(getattr(scene, "integrator", 0) or 0)
     p.nwalls = len(scene.walls)
     for k, (axis, pos) in enumerate(scene.walls):
         p.wall[k] = Wall(axis, 0, pos)
@@ -321,8 +322,9 @@ def swap_pass(P: Params, st: OracleState):
     return int(tot), sw.reshape(P.K, P.K)
 
 
-def step(P: Params, st: OracleState, do_swap: bool = False, want_rates: bool = False) -> dict:
-    """One full step in the paper's order; st is replaced by the new state in sorted order."""
+def step(P: Params, st: OracleState, do_swap: bool = False, want_rates: bool = False, dt: float = 0.0) -> dict:
+    """One full step in the paper's order; st is replaced by the new state in sorted order. dt > 0
+    fixes the time step (else the CFL step)."""
     n = st.n
     key = np.zeros(n, np.uint32)
     comm = np.zeros(n, np.uint32)
@@ -331,7 +333,7 @@ def step(P: Params, st: OracleState, do_swap: bool = False, want_rates: bool = F
     nr = np.zeros(n, np.int32)
     ni = np.zeros(n, np.int32)
     r = np.zeros((n, NRATE)) if want_rates else None
-    dtv = np.zeros(1)
+    dtv = np.array([float(dt)])
     cs = st.cstruct()
     lib().orc_step(C.byref(P), C.byref(cs), int(do_swap), _ptr(key, C.c_uint32), _ptr(comm, C.c_uint32),
                    _ptr(flag, C.c_uint8), _ptr(cnt, C.c_int64), _ptr(nr, C.c_int32), _ptr(ni, C.c_int32),
