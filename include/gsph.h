@@ -99,7 +99,10 @@ typedef struct {
                                    broadcast of step d on one device), then each boundary particle's pairs
                                    with other labels, their records read from the halo. Same results up to
                                    the order of the sums; 0: one pass over all pairs (faster on one GPU) */
-    int32_t pad2;
+    int32_t integrator;         /* 0: forward Euler (Sec. II step g); 1: two-stage Heun in its strong-
+                                   stability-preserving form, y* = E(y_n), y_{n+1} = (y_n + E(y*)) / 2 on the
+                                   conserved variables, E the Euler stage with radial return, both stages
+                                   over the neighbour set of the step's start (not with overlap = 1) */
 } gsph_config;
 
 typedef enum {

@@ -39,7 +39,9 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
                             unsigned int *sig, unsigned long long *pairs, unsigned long long *cost,
                             int32_t *nreal, int32_t *nimage, double *rates, const OverlapBufs *ov,
-                            cudaStream_t s);
+                            int stage, cudaStream_t s);
+cudaError_t launch_refresh(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const State &B,
+                           void *pos, void *rec, cudaStream_t s);
 // k_swap.cu
 size_t swap_scratch_bytes(int K, int nmat);
 cudaError_t launch_round_positions(int64_t n, const double *x, const double *y, const double *z, float *xf,
@@ -251,6 +253,8 @@ static bool config_ok(const gsph_config *c) {
     if (c->precision != GSPH_FP64 && c->precision != GSPH_FP32_SPLIT) return false;
     if (c->swap_period < 0) return false;
     if (c->overlap != 0 && c->overlap != 1) return false;
+    if (c->integrator != 0 && c->integrator != 1) return false;
+    if (c->integrator == 1 && c->overlap) return false;   // the two-pass order runs the Euler step only
     if (!(c->alpha >= 0.0 && c->alpha <= 1.0)) return false;
     return true;
 }
@@ -374,8 +378,17 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     GSPH_CK(launch_interact(c->split, c->cfg.diagnostics != 0, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs,
                             c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, phase_event(c, PH_LIST),
                             c->lab_s, c->mat_s, c->id_s, c->dt, c->sig, c->pairs, c->cost, c->nreal, c->nimage,
-                            c->rates, c->cfg.overlap ? &ov : nullptr, s));
+                            c->rates, c->cfg.overlap ? &ov : nullptr, c->cfg.integrator == 1 ? 1 : 0, s));
     if (c->cfg.overlap) c->launches += 2;   // halo gather, second pair pass
+    if (c->cfg.integrator == 1) {
+        // second Heun stage: records of the prediction, then its pairs over the same lists and the average
+        GSPH_CK(launch_refresh(c->split, P, n, c->skey, c->B, c->pos, c->rec, s));
+        GSPH_CK(launch_interact(c->split, c->cfg.diagnostics != 0, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs,
+                                c->xs, c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr,
+                                c->lab_s, c->mat_s, c->id_s, c->dt, c->sig, c->pairs, c->cost, c->nreal,
+                                c->nimage, c->rates, nullptr, 2, s));
+        c->launches += 2;
+    }
     GSPH_CK(launch_finalize_dt(P, c->sig, c->dt, s));
     c->launches += 3;
     rec_event(c, PH_INTERACT, s);
@@ -404,7 +417,7 @@ static gsph_status enqueue_forward_pieces(gsph_ctx *c, cudaStream_t s) {
                            c->cellr, c->cxs, c->pos, c->rec, nullptr, nullptr, nullptr, c->err, s));
     GSPH_CK(launch_interact(c->split, true, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs, c->ys, c->zs,
                             kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr, c->lab_s, c->mat_s, c->id_s,
-                            c->dt, c->sig, c->pairs, c->cost, c->nreal, c->nimage, c->rates, nullptr, s));
+                            c->dt, c->sig, c->pairs, c->cost, c->nreal, c->nimage, c->rates, nullptr, 0, s));
     c->launches += 4 + 3 * radix_passes(key_bits(P.ncell));
     c->dt_dirty = true;   // the signal-speed word now holds the scratch state's maximum
     return GSPH_OK;

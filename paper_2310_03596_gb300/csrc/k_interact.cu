@@ -103,7 +103,9 @@ template <class R> struct PairRes { R Fm, Fmv[3], Fe, a, n[3], du_vol; };
 // combination uses commutative operations (the two Riemann sums of products are rounded product by
 // product, never fused), and the two antisymmetric differences are oriented by the exact factor sgn,
 // so the two ends produce bitwise-opposite fluxes.
-template <class R>
+// CLAMP: the pair may lie beyond the support (second Heun stage over the step-start lists), where the
+// kernel gradient is 0.
+template <class R, bool CLAMP = false>
 __device__ __forceinline__ void pair_terms(R d0, R d1, R d2, const PIn<R> &me, const PIn<R> &oth, R sgn, R inv_h,
                                            R kdw, PairRes<R> &o) {
     const R half = R(0.5);
@@ -112,7 +114,8 @@ __device__ __forceinline__ void pair_terms(R d0, R d1, R d2, const PIn<R> &me, c
     const R r = r2 * inv_r;
     const R n0 = d0 * inv_r, n1 = d1 * inv_r, n2 = d2 * inv_r;
     const R q = r * inv_h;
-    const R sq = R(1) - half * q;
+    R sq = R(1) - half * q;
+    if (CLAMP) sq = sq > R(0) ? sq : R(0);
     const R a = kdw * q * sq * sq * sq;
     // normal velocity, traction sigma n (sigma = -p I + S) and normal traction of each particle
     const R um = me.vx * n0 + me.vy * n1 + me.vz * n2;
@@ -442,7 +445,11 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
 //               back, the pairs with neighbours of other labels, whose records come from the halo
 //               buffer (the broadcast boundary set), then the integration.
 // ---------------------------------------------------------------------------------------------
-enum { PM_ALL = 0, PM_LOCAL = 1, PM_BOUNDARY = 2 };
+//   PM_HEUN1    all pairs; the Euler prediction y* = E(y_n) goes to the output state (no time step).
+//   PM_HEUN2    all pairs of the predicted state, whose records the refresh rebuilt, over the lists of the
+//               step's start (the re-scan paths decide membership on the step-start FP64 positions);
+//               y_{n+1} = (y_n + E(y*)) / 2 on the conserved variables, then the time step.
+enum { PM_ALL = 0, PM_LOCAL = 1, PM_BOUNDARY = 2, PM_HEUN1 = 3, PM_HEUN2 = 4 };
 
 template <bool SPLIT>
 struct PairArgs {
@@ -512,9 +519,10 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
     const R kdw = SPLIT ? (R)P.f_kdw : (R)P.kdw;
     const R fcell = SPLIT ? (R)P.f_cell : (R)P.cell;
     // label filter of the two-pass order: PM_LOCAL takes neighbours of the own label, PM_BOUNDARY the others
-    const uint32_t mylab = (MODE != PM_ALL && valid) ? a.lab_s[s] : 0u;
+    constexpr bool ALLPAIRS = MODE == PM_ALL || MODE == PM_HEUN1 || MODE == PM_HEUN2;
+    const uint32_t mylab = (!ALLPAIRS && valid) ? a.lab_s[s] : 0u;
     auto take = [&](uint32_t j) -> bool {
-        if (MODE == PM_ALL) return true;
+        if (ALLPAIRS) return true;
         const bool same = a.lab_s[j] == mylab;
         return MODE == PM_LOCAL ? same : !same;
     };
@@ -551,7 +559,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
             d0 = sgn * ((R)pj.x - mrx); d1 = sgn * ((R)pj.y - mry); d2 = sgn * ((R)pj.z - mrz);
         }
         PairRes<R> o;
-        pair_terms<R>(d0, d1, d2, me, oth, sgn, inv_h, kdw, o);
+        pair_terms<R, MODE == PM_HEUN2>(d0, d1, d2, me, oth, sgn, inv_h, kdw, o);
         accumulate<R>(acc, o, -sgn, me, oth);
     };
 
@@ -616,7 +624,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
             fetch(j1, t1, p1, r1, x1);
             if ((uint32_t)k < nlist && tj) {
                 real_pair(j, c, (R)xj, pj, rj);
-                if (MODE != PM_ALL) ++nsel;
+                if (!ALLPAIRS) ++nsel;
             }
             if ((k & 7) == 7) acc.fold();
         }
@@ -626,6 +634,11 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
     // own position (overflow) or the mirrored position (images) in the list's candidate order. In the
     // two-pass order this rare path reads the particle arrays.
     const double X = valid ? xs[s] : 0.0, Y = valid ? ys[s] : 0.0, Z = valid ? zs[s] : 0.0;
+    // own FP64 position of the fluxes: the step's start, or the predicted state in the second Heun stage
+    // (the search keeps X, Y, Z)
+    const double XF = (MODE == PM_HEUN2 && valid) ? a.B.f[FX][s] : X;
+    const double YF = (MODE == PM_HEUN2 && valid) ? a.B.f[FY][s] : Y;
+    const double ZF = (MODE == PM_HEUN2 && valid) ? a.B.f[FZ][s] : Z;
     int cx = 0, cy = 0, cz = 0;
     if (active) decode_cell(P, key, cx, cy, cz);
     int ni = 0;
@@ -644,12 +657,17 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
             bx = bucket_coord_signed(CX, P.lo[0], P.cell);
             by = bucket_coord_signed(CY, P.lo[1], P.cell);
             bz = bucket_coord_signed(CZ, P.lo[2], P.cell);
+            // the flux offsets use the mirrored flux position (the search one except in Heun stage 2)
+            double FX_ = XF, FY_ = YF, FZ_ = ZF;
+            if (wax == 0) FX_ = __dsub_rn(two_w, XF);
+            if (wax == 1) FY_ = __dsub_rn(two_w, YF);
+            if (wax == 2) FZ_ = __dsub_rn(two_w, ZF);
             if (SPLIT) {
-                ox = (R)(CX - (P.lo[0] + (double)bx * P.cell));
-                oy = (R)(CY - (P.lo[1] + (double)by * P.cell));
-                oz = (R)(CZ - (P.lo[2] + (double)bz * P.cell));
+                ox = (R)(FX_ - (P.lo[0] + (double)bx * P.cell));
+                oy = (R)(FY_ - (P.lo[1] + (double)by * P.cell));
+                oz = (R)(FZ_ - (P.lo[2] + (double)bz * P.cell));
             } else {
-                ox = (R)CX; oy = (R)CY; oz = (R)CZ;
+                ox = (R)FX_; oy = (R)FY_; oz = (R)FZ_;
             }
         }
         const bool mine = active && (src > 0 || (int)cnt > kmax);
@@ -664,7 +682,9 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
                 const Pos pj = pos[j];
                 const int dcx = (int)cxs[j] - bx;
                 bool hit;
-                if (SPLIT) {
+                if (MODE == PM_HEUN2) {   // membership from the step's start: the FP64 positions
+                    hit = support_exact(P, xs, ys, zs, j, X, Y, Z, wax, wpos);
+                } else if (SPLIT) {
                     const float exf = ((float)pj.x - (float)ox) + (float)dcx * (float)fcell;
                     const float eyf = ((float)pj.y - (float)oy) + (float)dcy * (float)fcell;
                     const float ezf = ((float)pj.z - (float)oz) + (float)dcz * (float)fcell;
@@ -698,11 +718,11 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
                         if (wax == 0) qx = two_w - qx;
                         if (wax == 1) qy = two_w - qy;
                         if (wax == 2) qz = two_w - qz;
-                        d0 = (R)(qx - X); d1 = (R)(qy - Y); d2 = (R)(qz - Z);
+                        d0 = (R)(qx - XF); d1 = (R)(qy - YF); d2 = (R)(qz - ZF);
                     }
                     mirror<R>(oth, wax);
                     PairRes<R> o;
-                    pair_terms<R>(d0, d1, d2, me, oth, R(1), inv_h, kdw, o);
+                    pair_terms<R, MODE == PM_HEUN2>(d0, d1, d2, me, oth, R(1), inv_h, kdw, o);
                     accumulate<R>(acc, o, R(-1), me, oth);
                     ++ni;
                 }
@@ -710,7 +730,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         }
     }
     acc.fold();
-    const int ntaken = MODE == PM_ALL ? (int)nlist : nsel;   // listed neighbours summed by this pass
+    const int ntaken = ALLPAIRS ? (int)nlist : nsel;   // listed neighbours summed by this pass
     const unsigned pc = __reduce_add_sync(kFullMask, (unsigned)(ntaken + (int)nover + ni));
     const int nr = nr0 + ntaken + (int)nover;
     ni += ni0;
@@ -734,9 +754,12 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         const uint32_t o = a.perm[s];
         const int mt = a.mat_s[s] < P.nmat ? a.mat_s[s] : 0;
         const double dt = *a.dt_ptr;
-        const double w = A.f[FW][o], m = A.f[FM][o], E = A.f[FE][o];
-        const double vx = A.f[FVX][o], vy = A.f[FVY][o], vz = A.f[FVZ][o];
-        double S[6] = {A.f[FSXX][o], A.f[FSYY][o], A.f[FSZZ][o], A.f[FSXY][o], A.f[FSXZ][o], A.f[FSYZ][o]};
+        // the state the Euler stage starts from: y_n (A through the permutation), or y* (B in slot order)
+        const State &Y0 = MODE == PM_HEUN2 ? B : A;
+        const uint32_t o0 = MODE == PM_HEUN2 ? (uint32_t)s : o;
+        const double w = Y0.f[FW][o0], m = Y0.f[FM][o0], E = Y0.f[FE][o0];
+        const double vx = Y0.f[FVX][o0], vy = Y0.f[FVY][o0], vz = Y0.f[FVZ][o0];
+        double S[6] = {Y0.f[FSXX][o0], Y0.f[FSYY][o0], Y0.f[FSZZ][o0], Y0.f[FSXY][o0], Y0.f[FSXZ][o0], Y0.f[FSYZ][o0]};
         double r6[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) r6[k] = acc.get(k);
@@ -803,16 +826,39 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         } else {
             inv_mn = 1.0 / mn;
         }
-        const double nvx = mvx * inv_mn, nvy = mvy * inv_mn, nvz = mvz * inv_mn;
-        B.f[FX][s] = X + dt * vx;
-        B.f[FY][s] = Y + dt * vy;
-        B.f[FZ][s] = Z + dt * vz;
+        double nvx = mvx * inv_mn, nvy = mvy * inv_mn, nvz = mvz * inv_mn;
+        double En = mE * inv_mn;
+        double xn = XF + dt * vx, yn = YF + dt * vy, zn = ZF + dt * vz;
+        double wo = wn, mo = mn;
+        if (MODE == PM_HEUN2) {
+            // y_{n+1} = (y_n + E(y*)) / 2 on the conserved variables w, m, m v, m E, x, S
+            const double w0 = A.f[FW][o], m0 = A.f[FM][o];
+            const double mh = 0.5 * (m0 + mn);
+            const double imh = 1.0 / mh;
+            nvx = 0.5 * (m0 * A.f[FVX][o] + mvx) * imh;
+            nvy = 0.5 * (m0 * A.f[FVY][o] + mvy) * imh;
+            nvz = 0.5 * (m0 * A.f[FVZ][o] + mvz) * imh;
+            En = 0.5 * (m0 * A.f[FE][o] + mE) * imh;
+            xn = 0.5 * (X + xn);
+            yn = 0.5 * (Y + yn);
+            zn = 0.5 * (Z + zn);
+            wo = 0.5 * (w0 + wn);
+            mo = mh;
+            Sn[0] = 0.5 * (A.f[FSXX][o] + Sn[0]);
+            Sn[1] = 0.5 * (A.f[FSYY][o] + Sn[1]);
+            Sn[2] = 0.5 * (A.f[FSZZ][o] + Sn[2]);
+            Sn[3] = 0.5 * (A.f[FSXY][o] + Sn[3]);
+            Sn[4] = 0.5 * (A.f[FSXZ][o] + Sn[4]);
+            Sn[5] = 0.5 * (A.f[FSYZ][o] + Sn[5]);
+        }
+        B.f[FX][s] = xn;
+        B.f[FY][s] = yn;
+        B.f[FZ][s] = zn;
         B.f[FVX][s] = nvx;
         B.f[FVY][s] = nvy;
         B.f[FVZ][s] = nvz;
-        B.f[FW][s] = wn;
-        B.f[FM][s] = mn;
-        const double En = mE * inv_mn;
+        B.f[FW][s] = wo;
+        B.f[FM][s] = mo;
         B.f[FE][s] = En;
         B.f[FSXX][s] = Sn[0];
         B.f[FSYY][s] = Sn[1];
@@ -823,14 +869,14 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         B.mat[s] = a.mat_s[s];
         B.label[s] = a.lab_s[s];
         B.id[s] = a.id_s[s];
-        if (DIAG) {
+        if (DIAG && MODE != PM_HEUN2) {   // the step's counts and rates: those of its start
             a.nreal_out[s] = nr;
             a.nimage_out[s] = ni;
 #pragma unroll
             for (int k = 0; k < kNRate; ++k) a.rates_out[(size_t)s * kNRate + k] = acc.get(k);
         }
         // next step's CFL signal speed (correctly rounded FP32, reproducible bit for bit)
-        sp = signal_speed32(P, mt, mn, wn, nvx, nvy, nvz, En);
+        if (MODE != PM_HEUN1) sp = signal_speed32(P, mt, mo, wo, nvx, nvy, nvz, En);
     }
     const unsigned b = __reduce_max_sync(kFullMask, __float_as_uint(sp));
     if (lane == 0) {
@@ -840,7 +886,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
     // cost per label: this pass's pairs of the particle, summed over the lanes of each label
     {
         const uint32_t lab = valid ? (uint32_t)a.lab_s[s] : 0xffffffffu;
-        const unsigned mine = (unsigned)(ntaken + (int)nover + (ni - ni0));
+        const unsigned mine = MODE == PM_HEUN2 ? 0u : (unsigned)(ntaken + (int)nover + (ni - ni0));
         const unsigned peers = __match_any_sync(kFullMask, lab);
         const unsigned sum = __reduce_add_sync(peers, valid ? mine : 0u);
         if (valid && (__ffs(peers) - 1) == lane && sum) atomicAdd(&a.cost[lab], (unsigned long long)sum);
@@ -914,7 +960,7 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
                             unsigned int *sig, unsigned long long *pairs, unsigned long long *cost,
                             int32_t *nreal, int32_t *nimage, double *rates, const OverlapBufs *ov,
-                            cudaStream_t s) {
+                            int stage, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const unsigned gl = (unsigned)((n + NL_THREADS - 1) / NL_THREADS);
     const unsigned gp = (unsigned)((n + PK_THREADS - 1) / PK_THREADS);
@@ -930,9 +976,13 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
     } while (0)
 #define GSPH_INTERACT                                                                       \
     do {                                                                                    \
-        k_nbr_list<SP><<<gl, NL_THREADS, 0, s>>>(GSPH_NL_ARGS);                             \
+        if (stage != 2) k_nbr_list<SP><<<gl, NL_THREADS, 0, s>>>(GSPH_NL_ARGS);             \
         if (mid) cudaEventRecord(mid, s);                                                   \
-        if (!ov) {                                                                          \
+        if (stage == 1) {                                                                   \
+            GSPH_PAIRS(PM_HEUN1);                                                           \
+        } else if (stage == 2) {                                                            \
+            GSPH_PAIRS(PM_HEUN2);                                                           \
+        } else if (!ov) {                                                                   \
             GSPH_PAIRS(PM_ALL);                                                             \
         } else {                                                                            \
             /* step d on the second stream while the local pairs run (steps e, then f) */  \

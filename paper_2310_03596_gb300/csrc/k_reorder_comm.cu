@@ -11,46 +11,15 @@ namespace gsph {
 // occupied bucket (ranges of empty buckets stay 0,0 from the memset), and the interaction record of the
 // particle.
 // ---------------------------------------------------------------------------------------------
+// Interaction record of one particle in slot s with bucket hash k: split path, the position relative
+// to the own bucket corner and the FP32 state; FP64 path, the FP64 position and state. Pressure and
+// impedance from the equation of state.
 template <bool SPLIT>
-__global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const uint32_t *__restrict__ skey,
-                                                 const uint32_t *__restrict__ perm, State A,
-                                                 double *__restrict__ xs, double *__restrict__ ys,
-                                                 double *__restrict__ zs, uint8_t *__restrict__ lab_s,
-                                                 uint8_t *__restrict__ mat_s, uint32_t *__restrict__ id_s,
-                                                 uint2 *__restrict__ cellr, float *__restrict__ cxs,
-                                                 void *__restrict__ pos_out, void *__restrict__ rec_out,
-                                                 float *__restrict__ xf, float *__restrict__ yf,
-                                                 float *__restrict__ zf, int *__restrict__ err) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    uint32_t k = skey[s];
-    uint32_t o = perm[s];
-    double x = A.f[FX][o], y = A.f[FY][o], z = A.f[FZ][o];
-    xs[s] = x; ys[s] = y; zs[s] = z;
-    if (xf) {
-        xf[s] = __double2float_rn(x);
-        yf[s] = __double2float_rn(y);
-        zf[s] = __double2float_rn(z);
-    }
-    uint8_t lab = A.label[o], mat = A.mat[o];
-    // invalid values are reported and clamped so that no later kernel indexes out of range
-    if (lab >= P.K_labels) { atomicOr(err, kErrLabel); lab = 0; }
-    if (mat >= P.nmat) { atomicOr(err, kErrMaterial); mat = 0; }
-    lab_s[s] = lab;
-    mat_s[s] = mat;
-    id_s[s] = A.id[o];
-    if (k < P.ncell) {
-        if (s == 0 || skey[s - 1] != k) cellr[k].x = (uint32_t)s;
-        if (s == n - 1 || skey[s + 1] != k) cellr[k].y = (uint32_t)(s + 1);
-        cxs[s] = (float)(k % (uint32_t)P.dims[0]);
-    } else {
-        cxs[s] = -1.0e9f;
-    }
-    double w = A.f[FW][o], m = A.f[FM][o];
-    double vx = A.f[FVX][o], vy = A.f[FVY][o], vz = A.f[FVZ][o];
-    double E = A.f[FE][o];
-    double sxx = A.f[FSXX][o], syy = A.f[FSYY][o], szz = A.f[FSZZ][o];
-    double sxy = A.f[FSXY][o], sxz = A.f[FSXZ][o], syz = A.f[FSYZ][o];
+__device__ __forceinline__ void write_record(const DevParams &P, int64_t s, uint32_t k, double x, double y, double z,
+                                             double w, double m, double vx, double vy, double vz, double E,
+                                             double sxx, double syy, double szz, double sxy, double sxz,
+                                             double syz, int mat, void *__restrict__ pos_out,
+                                             void *__restrict__ rec_out) {
     if (SPLIT) {
         RecF r;
         float4 p4 = make_float4(0.f, 0.f, 0.f, (float)w);
@@ -96,6 +65,68 @@ __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const u
         ((D4 *)pos_out)[s] = make_d4(x, y, z, w);
         ((RecD *)rec_out)[s] = r;
     }
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const uint32_t *__restrict__ skey,
+                                                 const uint32_t *__restrict__ perm, State A,
+                                                 double *__restrict__ xs, double *__restrict__ ys,
+                                                 double *__restrict__ zs, uint8_t *__restrict__ lab_s,
+                                                 uint8_t *__restrict__ mat_s, uint32_t *__restrict__ id_s,
+                                                 uint2 *__restrict__ cellr, float *__restrict__ cxs,
+                                                 void *__restrict__ pos_out, void *__restrict__ rec_out,
+                                                 float *__restrict__ xf, float *__restrict__ yf,
+                                                 float *__restrict__ zf, int *__restrict__ err) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    uint32_t k = skey[s];
+    uint32_t o = perm[s];
+    double x = A.f[FX][o], y = A.f[FY][o], z = A.f[FZ][o];
+    xs[s] = x; ys[s] = y; zs[s] = z;
+    if (xf) {
+        xf[s] = __double2float_rn(x);
+        yf[s] = __double2float_rn(y);
+        zf[s] = __double2float_rn(z);
+    }
+    uint8_t lab = A.label[o], mat = A.mat[o];
+    // invalid values are reported and clamped so that no later kernel indexes out of range
+    if (lab >= P.K_labels) { atomicOr(err, kErrLabel); lab = 0; }
+    if (mat >= P.nmat) { atomicOr(err, kErrMaterial); mat = 0; }
+    lab_s[s] = lab;
+    mat_s[s] = mat;
+    id_s[s] = A.id[o];
+    if (k < P.ncell) {
+        if (s == 0 || skey[s - 1] != k) cellr[k].x = (uint32_t)s;
+        if (s == n - 1 || skey[s + 1] != k) cellr[k].y = (uint32_t)(s + 1);
+        cxs[s] = (float)(k % (uint32_t)P.dims[0]);
+    } else {
+        cxs[s] = -1.0e9f;
+    }
+    write_record<SPLIT>(P, s, k, x, y, z, A.f[FW][o], A.f[FM][o], A.f[FVX][o], A.f[FVY][o], A.f[FVZ][o],
+                        A.f[FE][o], A.f[FSXX][o], A.f[FSYY][o], A.f[FSZZ][o], A.f[FSXY][o], A.f[FSXZ][o],
+                        A.f[FSYZ][o], mat, pos_out, rec_out);
+}
+
+// Records of the predicted state of the Heun step (state B in slot order), relative to the bucket
+// corners of the step's hash; the sorted view and the bucket ranges stay those of the step's start.
+template <bool SPLIT>
+__global__ void __launch_bounds__(256) k_refresh(DevParams P, int64_t n, const uint32_t *__restrict__ skey,
+                                                 State B, void *__restrict__ pos_out, void *__restrict__ rec_out) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int mat = B.mat[s] < P.nmat ? B.mat[s] : 0;
+    write_record<SPLIT>(P, s, skey[s], B.f[FX][s], B.f[FY][s], B.f[FZ][s], B.f[FW][s], B.f[FM][s], B.f[FVX][s],
+                        B.f[FVY][s], B.f[FVZ][s], B.f[FE][s], B.f[FSXX][s], B.f[FSYY][s], B.f[FSZZ][s],
+                        B.f[FSXY][s], B.f[FSXZ][s], B.f[FSYZ][s], mat, pos_out, rec_out);
+}
+
+cudaError_t launch_refresh(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const State &B,
+                           void *pos, void *rec, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    unsigned g = (unsigned)((n + 255) / 256);
+    if (split) k_refresh<true><<<g, 256, 0, s>>>(P, n, skey, B, pos, rec);
+    else k_refresh<false><<<g, 256, 0, s>>>(P, n, skey, B, pos, rec);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint32_t *perm,

@@ -195,6 +195,25 @@ def test_adjoint_refuses_other_equations_of_state():
         sol.close()
 
 
+@pytest.mark.parametrize("precision,tol", [(gsph.FP64, 1e-12), (gsph.FP32_SPLIT, 2e-5)])
+def test_heun_integrator_lockstep(precision, tol):
+    # the two-stage Heun step (y* = E(y_n), y_{n+1} = (y_n + E(y*)) / 2, step-start neighbour sets):
+    # wall images in both stages (cube impact), labels and swaps (Taylor bar), list overflow (dense)
+    s = scenes.cube_impact(n_side=12, seed=17)
+    s.integrator = 1
+    _lockstep(s, precision, 4, tol)
+    s = scenes.taylor_bar(dx=0.5e-3, K=4, swap_period=1)
+    s.integrator = 1
+    _lockstep(s, precision, 3, tol)
+    s = scenes.cube_impact(n_side=10, seed=9)
+    s.h = 1.6 * s.dx
+    lo = tuple(v - 4 * s.h for v in s.pos.min(axis=0))
+    s.grid_lo = lo
+    s.grid_dims = tuple(int(np.ceil((s.pos[:, a].max() + 4 * s.h - lo[a]) / (2 * s.h))) for a in range(3))
+    s.integrator = 1
+    _lockstep(s, precision, 2, tol)
+
+
 def test_split_free_running_100_steps():
     s = scenes.cube_impact(n_side=12, steps=100)
     P = orc.params_of(s)
