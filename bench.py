@@ -220,6 +220,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--overlap-steps", type=int, default=20)
     ap.add_argument("--hvi-steps", type=int, default=50)
+    ap.add_argument("--heun-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -327,6 +328,30 @@ def main():
                                  if k.endswith("_ms") and v > 0},
            "exchange_fraction": sth["exchange_fraction"]}
 
+    # the second-order variant: two-stage Heun on the same workload
+    s2 = scenes.taylor_bar()
+    s2.integrator = 1
+    solr = gsph.Solver.from_scene(s2, device=local, stream=stream)
+    solr.step(3, stream)
+    solr.sync(stream)
+    solr.set_timing(args.heun_steps)
+    torch.cuda.synchronize()
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    solr.step(args.heun_steps, stream)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    msr = r0.elapsed_time(r1)
+    tmr = solr.timings()
+    solr.close()
+    heun = {"what": "two-stage Heun (SSP-RK2) on the Taylor bar: Euler prediction, record refresh, second "
+                    "stage over the step-start lists, conserved-variable average",
+            "value": world * n * args.heun_steps / (msr * 1e-3), "unit": "particle-steps/s",
+            "ms_per_step": msr / args.heun_steps, "steps": args.heun_steps,
+            "phase_ms_per_step": {k[:-3]: v / max(tmr["steps"], 1) for k, v in tmr.items()
+                                  if k.endswith("_ms") and v > 0}}
+
     # the interaction in the order of Sec. II steps d-f (two passes, halo gather on a second stream)
     solo = gsph.Solver.from_scene(s, device=local, stream=stream, overlap=True)
     solo.step(3, stream)
@@ -429,6 +454,7 @@ def main():
         "gpu_launches": launches,
         "overlap": overlap,
         "hvi": hvi,
+        "heun": heun,
         "clocks": ck,
         "exchange": {k: st1[k] for k in ("boundary_total", "exchange_fraction", "bytes_boundary_broadcast",
                                          "swapped_last_pass", "swap_passes")},
