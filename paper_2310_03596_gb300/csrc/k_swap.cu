@@ -35,6 +35,7 @@ constexpr int SW_TCAP = 2048;        // threshold-bin list capacity per side
 
 struct SwapPair {
     uint32_t hist[2][SW_BINS];
+    uint32_t npos[2];                // particles with a positive hash per side
     uint32_t idh[3][2][SW_ID_BINS];
     uint32_t tcnt[2];                // threshold-bin list fill per side
     unsigned long long moved;
@@ -203,6 +204,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
     __shared__ Side side_sh[2];
     __shared__ int act_sh;
     __shared__ long long gn_sh[4];       // counts of a, b (this type) and of a, b (all types)
+    __shared__ uint32_t npos_sh[2];      // this block's positive hashes per side
     __shared__ double gcg_sh[4][3];      // their Cgs
     __shared__ double gd_sh[3], gdn_sh;  // Cg_b - Cg_a, its length
     __shared__ int T_sh[2], idsel_sh[2];
@@ -254,16 +256,14 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                 // -- pair geometry (every block, identical operations on the same sums): counts, then the
                 // Cg components in parallel, the Cg' blend and the segment, its length, then the direction
                 // and scale. Side b's direction is the exact negation of side a's (d_b = -d_a bit for bit).
-                if (threadIdx.x < 4) {
-                    const int w = threadIdx.x, l = (w & 1) ? b : a, sl = w < 2 ? slot : kMaxMat;
-                    gn_sh[w] = ((volatile long long *)&S->cnt[l][sl])[0];
-                }
-                __syncthreads();
+                // counts and sums in one round trip: thread 3w + ax reads count w and sum component ax
                 if (threadIdx.x < 12) {
                     const int w = threadIdx.x / 3, ax = threadIdx.x % 3, l = (w & 1) ? b : a, sl = w < 2 ? slot : kMaxMat;
-                    if ((w < 2 || multi) && gn_sh[w] > 0) {
+                    const long long cn = ((volatile long long *)&S->cnt[l][sl])[0];
+                    if (ax == 0) gn_sh[w] = cn;
+                    if ((w < 2 || multi) && cn > 0) {
                         const long long sm = ((volatile long long *)&S->sums[l][sl][ax])[0];
-                        const double mean = __ddiv_rn((double)sm, (double)gn_sh[w]);
+                        const double mean = __ddiv_rn((double)sm, (double)cn);
                         gcg_sh[w][ax] = __dadd_rn((double)Q.lo[ax], __dmul_rn(mean, Q.inv[ax]));
                     }
                 }
@@ -299,6 +299,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                 }
                 if (threadIdx.x == 0) act_sh = act_g;
                 for (int k = threadIdx.x; k < 2 * SW_BINS; k += SW_THREADS) (&hs[0][0])[k] = 0;
+                if (threadIdx.x < 2) npos_sh[threadIdx.x] = 0u;
                 __syncthreads();
                 const bool act = act_sh != 0;
                 // -- balancing hashes and their histograms
@@ -316,11 +317,22 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                                 if (hv > 0) key = sd * SW_BINS + hv;   // only positive hashes are counted
                             }
                         }
-                        const unsigned peers = __match_any_sync(kFullMask, key);
-                        if (key >= 0 && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
-                            atomicAdd(&(&hs[0][0])[key], (uint32_t)__popc(peers));
+                        // warps without a positive hash (most of them once labels have settled) skip the
+                        // histogram; the others count per side and add per bin
+                        const unsigned pos0 = __ballot_sync(kFullMask, key >= 0 && key < SW_BINS);
+                        const unsigned pos1 = __ballot_sync(kFullMask, key >= SW_BINS);
+                        if (pos0 | pos1) {
+                            if ((threadIdx.x & 31) == 0) {
+                                if (pos0) atomicAdd(&npos_sh[0], (uint32_t)__popc(pos0));
+                                if (pos1) atomicAdd(&npos_sh[1], (uint32_t)__popc(pos1));
+                            }
+                            const unsigned peers = __match_any_sync(kFullMask, key);
+                            if (key >= 0 && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
+                                atomicAdd(&(&hs[0][0])[key], (uint32_t)__popc(peers));
+                        }
                     }
                     __syncthreads();
+                    if (threadIdx.x < 2 && npos_sh[threadIdx.x]) atomicAdd(&pr->npos[threadIdx.x], npos_sh[threadIdx.x]);
                     for (int k = threadIdx.x; k < 2 * SW_BINS; k += SW_THREADS) {
                         const uint32_t v = (&hs[0][0])[k];
                         if (v) atomicAdd(&(&pr->hist[0][0])[k], v);
@@ -328,6 +340,8 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                 }
                 if (!grid_barrier(S, nb, err)) return;
                 if (!act) continue;
+                // n = min(#positive): no scans when a side has none (the same decision in every block)
+                if (((volatile uint32_t *)&pr->npos[0])[0] == 0u || ((volatile uint32_t *)&pr->npos[1])[0] == 0u) continue;
                 // -- n = min(#positive), threshold hash and the count to take from the threshold bin:
                 // cum[sd][r] = particles of side sd with hash >= 1000 - r (block scans, every block)
                 __shared__ uint32_t cum[2][SW_BINS - 1];
