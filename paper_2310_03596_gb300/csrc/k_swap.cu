@@ -32,10 +32,15 @@ constexpr int SW_ID_BINS = 1 << SW_ID_BITS;
 constexpr int SW_THREADS = 512;
 constexpr int SW_NT = kMaxMat + 1;   // per-type slots + the all-types slot
 constexpr int SW_TCAP = 2048;        // threshold-bin list capacity per side
+constexpr int SW_MAXCOMBO = kMaxMat * (kMaxLabel * (kMaxLabel - 1) / 2);   // (type, label pair) combinations
+constexpr int SW_SBUF = SW_MAXCOMBO * (int)(7 * sizeof(float)) + SW_MAXCOMBO * 2 * 4 > 2 * SW_TCAP * 4
+                            ? SW_MAXCOMBO * (int)(7 * sizeof(float)) + SW_MAXCOMBO * 2 * 4
+                            : 2 * SW_TCAP * 4;
 
 struct SwapPair {
     uint32_t hist[2][SW_BINS];
     uint32_t npos[2];                // particles with a positive hash per side
+    uint32_t spec[2];                // the same at the pass-start labels and sums (speculative pass)
     uint32_t idh[3][2][SW_ID_BINS];
     uint32_t tcnt[2];                // threshold-bin list fill per side
     unsigned long long moved;
@@ -68,6 +73,42 @@ struct Side {
     float u[3];
     float scale;
 };
+
+// Geometry of label pair (a, b) of one type from the current sums, by one thread with the operations of
+// the per-pair code (every rounding explicit, so the values are the same bits). Returns false when a
+// side is empty or the two Cgs coincide.
+__device__ bool combo_geometry(const SwapScratch *S, const QuantParams &Q, double alpha, bool multi, int slot, int a,
+                               int b, Side &sd) {
+    const int lab[2] = {a, b};
+    double cg[4][3];
+    long long cn[4];
+    for (int w = 0; w < 4; ++w) {
+        const int l = lab[w & 1], sl = w < 2 ? slot : kMaxMat;
+        cn[w] = ((volatile const long long *)&S->cnt[l][sl])[0];
+        if ((w < 2 || multi) && cn[w] > 0)
+            for (int ax = 0; ax < 3; ++ax) {
+                const long long sm = ((volatile const long long *)&S->sums[l][sl][ax])[0];
+                cg[w][ax] = __dadd_rn((double)Q.lo[ax], __dmul_rn(__ddiv_rn((double)sm, (double)cn[w]), Q.inv[ax]));
+            }
+    }
+    if (!(cn[0] > 0 && cn[1] > 0)) return false;
+    double d[3];
+    for (int ax = 0; ax < 3; ++ax) {
+        double ca = cg[0][ax], cb = cg[1][ax];
+        if (multi) {
+            const double beta = __dsub_rn(1.0, alpha);
+            ca = __dadd_rn(__dmul_rn(alpha, cg[2][ax]), __dmul_rn(beta, ca));
+            cb = __dadd_rn(__dmul_rn(alpha, cg[3][ax]), __dmul_rn(beta, cb));
+        }
+        sd.M[ax] = (float)__dmul_rn(__dadd_rn(ca, cb), 0.5);
+        d[ax] = __dsub_rn(cb, ca);
+    }
+    const double dn = __dsqrt_rn(dist2_rn(d[0], d[1], d[2]));
+    if (!(dn > 0.0)) return false;
+    for (int ax = 0; ax < 3; ++ax) sd.u[ax] = (float)__ddiv_rn(d[ax], dn);
+    sd.scale = (float)__ddiv_rn(1000.0, __dmul_rn(dn, 0.5));
+    return true;
+}
 
 __device__ __forceinline__ int balancing_hash(const Side &sd, float p0, float p1, float p2) {
     const float e0 = __fsub_rn(p0, sd.M[0]);
@@ -212,7 +253,9 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
     __shared__ long long dsum[2][4];   // per side: moved q0 q1 q2, count
     __shared__ uint32_t cntT_sh[2];    // particles in the threshold bin
     __shared__ int list_sh;            // threshold bins split through the list (else the grid select)
-    __shared__ uint32_t tkey[2][SW_TCAP];
+    // tkey (tie-break select) and the speculative pass's geometry and counters share one buffer
+    __shared__ __align__(16) unsigned char sbuf[SW_SBUF];
+    uint32_t(*tkey)[SW_TCAP] = (uint32_t(*)[SW_TCAP])sbuf;
     const unsigned nb = gridDim.x;
     const int64_t gstride = (int64_t)gridDim.x * SW_THREADS;
     const int64_t g0 = (int64_t)blockIdx.x * SW_THREADS + threadIdx.x;
@@ -246,12 +289,71 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
     }
     if (!grid_barrier(S, nb, err)) return;
 
+    // ---- speculative pass (exact): positive-hash counts of every (type, label pair) at the pass-start
+    // labels and sums. A pair with no positive hash on one side swaps nothing and changes nothing, so
+    // the sequential loop starts at the first pair with positive hashes on both sides: until then the
+    // labels and sums each pair sees are the pass-start ones, the state this pass evaluates.
+    const int npairs = K * (K - 1) / 2;
+    const int ncombo = ntype * npairs;
+    __shared__ int first_sh;
+    {
+        Side *spec = (Side *)sbuf;
+        uint32_t *scnt = (uint32_t *)(sbuf + SW_MAXCOMBO * sizeof(Side));
+        for (int q = threadIdx.x; q < ncombo; q += SW_THREADS) {
+            const int T = q / npairs;
+            int a = 0, rem = q % npairs;
+            while (rem >= K - 1 - a) { rem -= K - 1 - a; ++a; }
+            if (!combo_geometry(S, Q, alpha, multi, multi ? T : kMaxMat, a, a + 1 + rem, spec[q])) spec[q].scale = -1.0f;
+            scnt[2 * q] = 0u;
+            scnt[2 * q + 1] = 0u;
+        }
+        __syncthreads();
+        for (int64_t base = (int64_t)blockIdx.x * SW_THREADS; base < n; base += gstride) {
+            const int64_t i = base + threadIdx.x;
+            const bool v = i < n;
+            const int l = v ? (lab[i] & (kMaxLabel - 1)) : 0;
+            const int T = (v && multi) ? (mat[i] < nmat ? mat[i] : 0) : 0;
+            const float px = v ? x[i] : 0.0f, py = v ? y[i] : 0.0f, pz = v ? z[i] : 0.0f;
+            for (int o = 0; o < K; ++o) {   // the K - 1 pairs of the particle's label (warp-uniform loop)
+                const int a = l < o ? l : o, b = l < o ? o : l;
+                const int q = T * npairs + a * (2 * K - a - 1) / 2 + (b - a - 1);
+                int key = -1;
+                if (v && o != l) {
+                    Side g = spec[q];
+                    if (g.scale >= 0.0f) {
+                        if (l == b) { g.u[0] = -g.u[0]; g.u[1] = -g.u[1]; g.u[2] = -g.u[2]; }
+                        if (balancing_hash(g, px, py, pz) > 0) key = 2 * q + (l == a ? 0 : 1);
+                    }
+                }
+                if (__any_sync(kFullMask, key >= 0)) {   // positives are rare once labels have settled
+                    const unsigned peers = __match_any_sync(kFullMask, key);
+                    if (key >= 0 && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
+                        atomicAdd(&scnt[key], (uint32_t)__popc(peers));
+                }
+            }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < 2 * ncombo; q += SW_THREADS)
+            if (scnt[q]) atomicAdd(&pairs[q >> 1].spec[q & 1], scnt[q]);
+        if (!grid_barrier(S, nb, err)) return;
+        if (threadIdx.x == 0) {
+            int f = ncombo;
+            for (int q = 0; q < ncombo && f == ncombo; ++q)
+                if (((volatile uint32_t *)&pairs[q].spec[0])[0] > 0u && ((volatile uint32_t *)&pairs[q].spec[1])[0] > 0u) f = q;
+            first_sh = f;
+        }
+        __syncthreads();
+    }
+    const int first = first_sh;   // the same in every block
+    if (first >= ncombo) return;
+
     int idx = 0;
     for (int T = 0; T < ntype; ++T) {
         const int type = multi ? T : -1;
         const int slot = multi ? T : kMaxMat;
         for (int a = 0; a < K - 1; ++a)
             for (int b = a + 1; b < K; ++b, ++idx) {
+                if (idx < first) continue;   // no positive hashes on a side: nothing to do
                 SwapPair *pr = pairs + idx;
                 // -- pair geometry (every block, identical operations on the same sums): counts, then the
                 // Cg components in parallel, the Cg' blend and the segment, its length, then the direction
