@@ -763,21 +763,14 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         double r6[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) r6[k] = acc.get(k);
+        // split path (Euler stage): the increments of v, E and S in FP32 from the FP32 rates, each added once
+        // to the FP64 state: v_{n+1} = v + dt (F - v dm) / m_{n+1}, E_{n+1} = E + dt (dE - E dm) / m_{n+1},
+        // the same update as (m v + dt F) / m_{n+1}; w, m and x advance in FP64
+        constexpr bool FAST = SPLIT && MODE != PM_HEUN2;
         const double wn = w + dt * r6[0];
         const double mn = m + dt * r6[1];
-        if (P.has_gravity) {   // body force m g and its power m g.v (skipped when g = 0: the same values)
-            const double gv = P.g[0] * vx + P.g[1] * vy + P.g[2] * vz;
-            r6[2] += m * P.g[0];
-            r6[3] += m * P.g[1];
-            r6[4] += m * P.g[2];
-            r6[5] += m * gv;
-        }
-        const double mvx = m * vx + dt * r6[2];
-        const double mvy = m * vy + dt * r6[3];
-        const double mvz = m * vz + dt * r6[4];
-        const double mE = m * E + dt * r6[5];
-        // stress rate 2G (D - tr D / 3) + Om S - S Om (the split path evaluates it in FP32 from the
-        // FP32 velocity gradient; the increment is added to the FP64 stress)
+        double nvx, nvy, nvz, En, Sn[6];
+        double mvx = 0.0, mvy = 0.0, mvz = 0.0, mE = 0.0;
         R Lm[3][3];
 #pragma unroll
         for (int u = 0; u < 3; ++u)
@@ -792,7 +785,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         const R trD = Lm[0][0] + Lm[1][1] + Lm[2][2];
         const R G2 = SPLIT ? (R)(2.0f * P.f_G[mt]) : (R)(2.0 * P.G[mt]);
         const int iu[6] = {0, 1, 2, 0, 0, 1}, iv[6] = {0, 1, 2, 1, 2, 2};
-        double Sn[6];
+        R srate[6];   // stress rate 2G (D - tr D / 3) + Om S - S Om
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
             const int u = iu[q], v = iv[q];
@@ -805,29 +798,74 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
                 const R Okv = R(0.5) * (Lm[k][v] - Lm[v][k]);
                 rot += Ouk * Sr[k][v] - Sr[u][k] * Okv;
             }
-            Sn[q] = S[q] + dt * (double)(G2 * D + rot);
+            srate[q] = G2 * D + rot;
         }
-        const double trS = (Sn[0] + Sn[1] + Sn[2]) / 3.0;
-        Sn[0] -= trS; Sn[1] -= trS; Sn[2] -= trS;
-        const R a0 = (R)Sn[0], a1 = (R)Sn[1], a2 = (R)Sn[2], a3 = (R)Sn[3], a4 = (R)Sn[4], a5 = (R)Sn[5];
-        const R ss = a0 * a0 + a1 * a1 + a2 * a2 + R(2) * (a3 * a3 + a4 * a4 + a5 * a5);
-        const R seq = sqrt(R(1.5) * ss);
         const R Yr = SPLIT ? (R)(float)P.Y[mt] : (R)P.Y[mt];
-        if (seq > Yr) {
-            const double f = (double)(Yr / seq);
+        if (FAST) {
+            const float dtf = (float)dt, imf = 1.0f / (float)mn, mf = me.rho * me.w, dm = acc.getr(1);
+            float F[3] = {acc.getr(2), acc.getr(3), acc.getr(4)}, dE = acc.getr(5);
+            if (P.has_gravity) {
+                const float g0 = (float)P.g[0], g1 = (float)P.g[1], g2 = (float)P.g[2];
+                F[0] += mf * g0; F[1] += mf * g1; F[2] += mf * g2;
+                dE += mf * (g0 * me.vx + g1 * me.vy + g2 * me.vz);
+            }
+            nvx = vx + (double)(dtf * (F[0] - me.vx * dm) * imf);
+            nvy = vy + (double)(dtf * (F[1] - me.vy * dm) * imf);
+            nvz = vz + (double)(dtf * (F[2] - me.vz * dm) * imf);
+            En = E + (double)(dtf * (dE - me.E * dm) * imf);
+            // stress increment; its trace removed in FP32 (the state's own trace is zero to rounding)
+            float dS[6];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) Sn[q] *= f;
-        }
-        double inv_mn;
-        if (SPLIT) {   // FP32 estimate refined by two Newton steps (relative error at the FP64 rounding level)
-            const double r0 = (double)__fdividef(1.0f, (float)mn);
-            const double r1 = fma(r0, fma(-mn, r0, 1.0), r0);
-            inv_mn = fma(r1, fma(-mn, r1, 1.0), r1);
+            for (int q = 0; q < 6; ++q) dS[q] = dtf * (float)srate[q];
+            const float tr3 = (dS[0] + dS[1] + dS[2]) * (1.0f / 3.0f);
+            dS[0] -= tr3; dS[1] -= tr3; dS[2] -= tr3;
+            const float a0 = (float)Sr[0][0] + dS[0], a1 = (float)Sr[1][1] + dS[1], a2 = (float)Sr[2][2] + dS[2];
+            const float a3 = (float)Sr[0][1] + dS[3], a4 = (float)Sr[0][2] + dS[4], a5 = (float)Sr[1][2] + dS[5];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) Sn[q] = S[q] + (double)dS[q];
+            const float ss = a0 * a0 + a1 * a1 + a2 * a2 + 2.0f * (a3 * a3 + a4 * a4 + a5 * a5);
+            const float seq = sqrtf(1.5f * ss);
+            if (seq > (float)Yr) {
+                const double f = (double)((float)Yr / seq);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) Sn[q] *= f;
+            }
         } else {
-            inv_mn = 1.0 / mn;
+            if (P.has_gravity) {   // body force m g and its power m g.v (skipped when g = 0: the same values)
+                const double gv = P.g[0] * vx + P.g[1] * vy + P.g[2] * vz;
+                r6[2] += m * P.g[0];
+                r6[3] += m * P.g[1];
+                r6[4] += m * P.g[2];
+                r6[5] += m * gv;
+            }
+            mvx = m * vx + dt * r6[2];
+            mvy = m * vy + dt * r6[3];
+            mvz = m * vz + dt * r6[4];
+            mE = m * E + dt * r6[5];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) Sn[q] = S[q] + dt * (double)srate[q];
+            const double trS = (Sn[0] + Sn[1] + Sn[2]) / 3.0;
+            Sn[0] -= trS; Sn[1] -= trS; Sn[2] -= trS;
+            const R a0 = (R)Sn[0], a1 = (R)Sn[1], a2 = (R)Sn[2], a3 = (R)Sn[3], a4 = (R)Sn[4], a5 = (R)Sn[5];
+            const R ss = a0 * a0 + a1 * a1 + a2 * a2 + R(2) * (a3 * a3 + a4 * a4 + a5 * a5);
+            const R seq = sqrt(R(1.5) * ss);
+            if (seq > Yr) {
+                const double f = (double)(Yr / seq);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) Sn[q] *= f;
+            }
+            double inv_mn;
+            if (SPLIT) {   // FP32 estimate refined by two Newton steps (relative error at the FP64 rounding level)
+                const double r0 = (double)__fdividef(1.0f, (float)mn);
+                const double r1 = fma(r0, fma(-mn, r0, 1.0), r0);
+                inv_mn = fma(r1, fma(-mn, r1, 1.0), r1);
+            } else {
+                inv_mn = 1.0 / mn;
+            }
+            nvx = mvx * inv_mn; nvy = mvy * inv_mn; nvz = mvz * inv_mn;
+            En = mE * inv_mn;
         }
-        double nvx = mvx * inv_mn, nvy = mvy * inv_mn, nvz = mvz * inv_mn;
-        double En = mE * inv_mn;
+
         double xn = XF + dt * vx, yn = YF + dt * vy, zn = ZF + dt * vz;
         double wo = wn, mo = mn;
         if (MODE == PM_HEUN2) {
