@@ -297,7 +297,11 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
     using Pos = typename Types<SPLIT>::Pos;
     // staged candidate: split path (c, |c|^2) with c = (x in the group frame, y, z in the row frame);
     // FP64 path (x, y, z, bucket x)
-    __shared__ Pos stage[NL_THREADS];
+    // split path: four planes (x, y, z, |c|^2) of NL_THREADS floats, so that one 16-byte load gives a
+    // coordinate of four candidates and the tests run on packed pairs; FP64 path: one D4 per candidate
+    __shared__ __align__(16) unsigned char stage_raw[NL_THREADS * sizeof(Pos)];
+    Pos *stage = (Pos *)stage_raw;
+    float *splane = (float *)stage_raw;
     const int tid = threadIdx.x, lane = tid & 31, wbase = tid & ~31;
     const int64_t s = (int64_t)blockIdx.x * NL_THREADS + tid;
     const bool valid = s < n;
@@ -367,7 +371,14 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                     } else {
                         q.x = 1.0e30; q.y = 1.0e30; q.z = 1.0e30; q.w = -1.0e9;
                     }
-                    stage[tid] = q;
+                    if (SPLIT) {
+                        splane[tid] = (float)q.x;
+                        splane[NL_THREADS + tid] = (float)q.y;
+                        splane[2 * NL_THREADS + tid] = (float)q.z;
+                        splane[3 * NL_THREADS + tid] = (float)q.w;
+                    } else {
+                        stage[tid] = q;
+                    }
                 }
                 __syncwarp();
                 if (ing) {
@@ -379,23 +390,51 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                     if (SPLIT) {
                         // the sign of r^2 - R2lo (resp. R2hi) is shifted into the masks, candidate t
                         // ending at bit 31 - t; one reversal at the end restores bit t
-                        const float band_w = P.f_R2lo - P.f_R2hi;
+                        // r^2 - R2lo = fma(mx, x, fma(my, y, fma(mz, z, |c|^2 + Kr))) on packed pairs of
+                        // candidates (each lane of a pair rounded as the scalar operation)
+                        const uint32_t wbits = __float_as_uint(P.f_R2hi - P.f_R2lo);
+                        uint32_t umin = 0xffffffffu;
+                        const float2 mx2 = make_float2(mx, mx), my2 = make_float2(my, my), mz2 = make_float2(mz, mz);
+                        const float2 kr2 = make_float2(Kr, Kr);
+#pragma unroll
+                        for (int t = 0; t < 32; t += 4) {
+                            const float4 X4 = *(const float4 *)&splane[wbase + t];
+                            const float4 Y4 = *(const float4 *)&splane[NL_THREADS + wbase + t];
+                            const float4 Z4 = *(const float4 *)&splane[2 * NL_THREADS + wbase + t];
+                            const float4 W4 = *(const float4 *)&splane[3 * NL_THREADS + wbase + t];
+#pragma unroll
+                            for (int h2 = 0; h2 < 2; ++h2) {
+                                const float2 xx = h2 ? make_float2(X4.z, X4.w) : make_float2(X4.x, X4.y);
+                                const float2 yy = h2 ? make_float2(Y4.z, Y4.w) : make_float2(Y4.x, Y4.y);
+                                const float2 zz = h2 ? make_float2(Z4.z, Z4.w) : make_float2(Z4.x, Z4.y);
+                                const float2 ww = h2 ? make_float2(W4.z, W4.w) : make_float2(W4.x, W4.y);
+                                float2 d = __fadd2_rn(ww, kr2);
+                                d = __ffma2_rn(mz2, zz, d);
+                                d = __ffma2_rn(my2, yy, d);
+                                d = __ffma2_rn(mx2, xx, d);
+                                hitm = __funnelshift_l(__float_as_uint(d.x), hitm, 1);
+                                hitm = __funnelshift_l(__float_as_uint(d.y), hitm, 1);
+                                umin = min(umin, min(__float_as_uint(d.x), __float_as_uint(d.y)));
+                            }
+                        }
+                        hitm = __brev(hitm);
+                        // a candidate is in the band when 0 <= d < R2hi - R2lo, i.e. its bits as an unsigned
+                        // integer are below those of the band width (negative d has the sign bit set); the
+                        // smallest such bits of the batch say whether any is, and the rare batch that has
+                        // one rebuilds the band mask with the same scalar roundings
+                        if (umin < wbits) {
+#pragma unroll 4
+                            for (int t = 0; t < 32; ++t) {
+                                const float d = fmaf(mx, splane[wbase + t], fmaf(my, splane[NL_THREADS + wbase + t],
+                                                fmaf(mz, splane[2 * NL_THREADS + wbase + t], splane[3 * NL_THREADS + wbase + t] + Kr)));
+                                if (__float_as_uint(d) < wbits) bandm |= 1u << t;
+                            }
+                        }
+                    }
+                    if (!SPLIT) {
 #pragma unroll
                         for (int t = 0; t < 32; ++t) {
                             const Pos pj = stage[wbase + t];
-                            const float dlo = fmaf(mx, (float)pj.x, fmaf(my, (float)pj.y, fmaf(mz, (float)pj.z, (float)pj.w + Kr)));
-                            const float dhi = dlo + band_w;
-                            hitm = __funnelshift_l(__float_as_uint(dlo), hitm, 1);
-                            bandm = __funnelshift_l(__float_as_uint(dhi), bandm, 1);
-                        }
-                        hitm = __brev(hitm);
-                        bandm = __brev(bandm);
-                    }
-#pragma unroll
-                    for (int t = 0; t < 32; ++t) {
-                        const Pos pj = stage[wbase + t];
-                        if (SPLIT) {
-                        } else {
                             const int cxj = (int)pj.w;
                             if ((uint32_t)(cxj - cxm1) <= 2u &&
                                 dist2_rn(__dsub_rn((double)pj.x, X), __dsub_rn((double)pj.y, Y),
