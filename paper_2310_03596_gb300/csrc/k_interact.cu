@@ -37,45 +37,40 @@ constexpr int NL_THREADS = 256;            // neighbour-list kernel
 constexpr int PK_THREADS = 128;            // pair kernel
 constexpr uint32_t IT_JMASK = (1u << 26) - 1;   // list entry .y: batch base slot (26 bits) | row offset (4 bits)
 
-template <class R> struct PIn { R vx, vy, vz, rho, p, Z, E, sxx, syy, szz, sxy, sxz, syz, w; };
+// interaction inputs of one particle; txx, tyy, tzz are the diagonal of the full stress sigma = -p I + S
+template <class R> struct PIn { R vx, vy, vz, rho, Z, E, txx, tyy, tzz, sxy, sxz, syz, w; };
+
+// split record: (vx, vy, vz, rho), (sigma_zz, Z, E, sigma_xx), (sigma_yy, S_xy, S_xz, S_yz)
+__device__ __forceinline__ PIn<float> unpack(const RecF &r, float w) {
+    PIn<float> q;
+    q.vx = r.a.x; q.vy = r.a.y; q.vz = r.a.z; q.rho = r.a.w;
+    q.tzz = r.b.x; q.Z = r.b.y; q.E = r.b.z; q.txx = r.b.w;
+    q.tyy = r.c.x; q.sxy = r.c.y; q.sxz = r.c.z; q.syz = r.c.w;
+    q.w = w;
+    return q;
+}
+// FP64 record: (vx, vy, vz, rho), (p, Z, E, S_xx), (S_yy, S_zz, S_xy, S_xz), (S_yz, -, -, -)
+__device__ __forceinline__ PIn<double> unpack(const RecD &r, double w) {
+    PIn<double> q;
+    q.vx = r.a.x; q.vy = r.a.y; q.vz = r.a.z; q.rho = r.a.w;
+    q.Z = r.b.y; q.E = r.b.z;
+    q.txx = r.b.w - r.b.x; q.tyy = r.c.x - r.b.x; q.tzz = r.c.y - r.b.x;
+    q.sxy = r.c.z; q.sxz = r.c.w; q.syz = r.d.x;
+    q.w = w;
+    return q;
+}
 
 __device__ __forceinline__ PIn<float> load_rec(const RecF *__restrict__ rec, float w, int64_t j) {
     RecF r;
     r.a = __ldg(&rec[j].a);
     r.b = __ldg(&rec[j].b);
     r.c = __ldg(&rec[j].c);
-    PIn<float> q;
-    q.vx = r.a.x; q.vy = r.a.y; q.vz = r.a.z; q.rho = r.a.w;
-    q.p = r.b.x; q.Z = r.b.y; q.E = r.b.z; q.sxx = r.b.w;
-    q.syy = r.c.x; q.szz = -(r.b.w + r.c.x); q.sxy = r.c.y; q.sxz = r.c.z; q.syz = r.c.w;
-    q.w = w;
-    return q;
+    return unpack(r, w);
 }
 __device__ __forceinline__ PIn<double> load_rec(const RecD *__restrict__ rec, double w, int64_t j) {
-    PIn<double> q;
-    const D4 a = rec[j].a, b = rec[j].b, c = rec[j].c, d = rec[j].d;
-    q.vx = a.x; q.vy = a.y; q.vz = a.z; q.rho = a.w;
-    q.p = b.x; q.Z = b.y; q.E = b.z; q.sxx = b.w;
-    q.syy = c.x; q.szz = c.y; q.sxy = c.z; q.sxz = c.w; q.syz = d.x;
-    q.w = w;
-    return q;
-}
-
-__device__ __forceinline__ PIn<float> unpack(const RecF &r, float w) {
-    PIn<float> q;
-    q.vx = r.a.x; q.vy = r.a.y; q.vz = r.a.z; q.rho = r.a.w;
-    q.p = r.b.x; q.Z = r.b.y; q.E = r.b.z; q.sxx = r.b.w;
-    q.syy = r.c.x; q.szz = -(r.b.w + r.c.x); q.sxy = r.c.y; q.sxz = r.c.z; q.syz = r.c.w;
-    q.w = w;
-    return q;
-}
-__device__ __forceinline__ PIn<double> unpack(const RecD &r, double w) {
-    PIn<double> q;
-    q.vx = r.a.x; q.vy = r.a.y; q.vz = r.a.z; q.rho = r.a.w;
-    q.p = r.b.x; q.Z = r.b.y; q.E = r.b.z; q.sxx = r.b.w;
-    q.syy = r.c.x; q.szz = r.c.y; q.sxy = r.c.z; q.sxz = r.c.w; q.syz = r.d.x;
-    q.w = w;
-    return q;
+    RecD r;
+    r.a = rec[j].a; r.b = rec[j].b; r.c = rec[j].c; r.d = rec[j].d;
+    return unpack(r, w);
 }
 
 // Mirror image of a state in the plane normal to `ax`.
@@ -95,10 +90,11 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 
-template <class R> struct PairRes { R Fm, Fmv[3], Fe, a, n[3], du_vol; };
+template <class R> struct PairRes { R Fm, Fmv[3], Fe, a, n[3], du_vol, w2a; };
 
-// Pair fluxes on the canonical pair: d = x_R - x_L with L the lower sorted slot, `me` the particle
-// being updated and `oth` its neighbour, sgn = +1 when me is L, -1 when me is R. Every per-particle
+// Pair fluxes on the canonical pair: e = x_j - x_i as seen from this end (the canonical difference
+// x_R - x_L, L the lower sorted slot, is sgn e), `me` the particle being updated and `oth` its
+// neighbour, sgn = +1 when me is L, -1 when me is R. Every per-particle
 // projection is taken on the same canonical normal at both ends of the pair, every symmetric
 // combination uses commutative operations (the two Riemann sums of products are rounded product by
 // product, never fused), and the two antisymmetric differences are oriented by the exact factor sgn,
@@ -106,26 +102,27 @@ template <class R> struct PairRes { R Fm, Fmv[3], Fe, a, n[3], du_vol; };
 // CLAMP: the pair may lie beyond the support (second Heun stage over the step-start lists), where the
 // kernel gradient is 0.
 template <class R, bool CLAMP = false>
-__device__ __forceinline__ void pair_terms(R d0, R d1, R d2, const PIn<R> &me, const PIn<R> &oth, R sgn, R inv_h,
+__device__ __forceinline__ void pair_terms(R e0, R e1, R e2, const PIn<R> &me, const PIn<R> &oth, R sgn, R inv_h,
                                            R kdw, PairRes<R> &o) {
     const R half = R(0.5);
-    const R r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    const R r2 = e0 * e0 + e1 * e1 + e2 * e2;
     const R inv_r = rsqrt_r(r2);
     const R r = r2 * inv_r;
-    const R n0 = d0 * inv_r, n1 = d1 * inv_r, n2 = d2 * inv_r;
+    const R sir = sgn * inv_r;   // the canonical normal n = sgn e / r
+    const R n0 = e0 * sir, n1 = e1 * sir, n2 = e2 * sir;
     const R q = r * inv_h;
     R sq = R(1) - half * q;
     if (CLAMP) sq = sq > R(0) ? sq : R(0);
     const R a = kdw * q * sq * sq * sq;
-    // normal velocity, traction sigma n (sigma = -p I + S) and normal traction of each particle
+    // normal velocity, traction sigma n and normal traction of each particle
     const R um = me.vx * n0 + me.vy * n1 + me.vz * n2;
     const R uo = oth.vx * n0 + oth.vy * n1 + oth.vz * n2;
-    const R sm0 = me.sxx * n0 + me.sxy * n1 + me.sxz * n2 - me.p * n0;
-    const R sm1 = me.sxy * n0 + me.syy * n1 + me.syz * n2 - me.p * n1;
-    const R sm2 = me.sxz * n0 + me.syz * n1 + me.szz * n2 - me.p * n2;
-    const R so0 = oth.sxx * n0 + oth.sxy * n1 + oth.sxz * n2 - oth.p * n0;
-    const R so1 = oth.sxy * n0 + oth.syy * n1 + oth.syz * n2 - oth.p * n1;
-    const R so2 = oth.sxz * n0 + oth.syz * n1 + oth.szz * n2 - oth.p * n2;
+    const R sm0 = me.txx * n0 + me.sxy * n1 + me.sxz * n2;
+    const R sm1 = me.sxy * n0 + me.tyy * n1 + me.syz * n2;
+    const R sm2 = me.sxz * n0 + me.syz * n1 + me.tzz * n2;
+    const R so0 = oth.txx * n0 + oth.sxy * n1 + oth.sxz * n2;
+    const R so1 = oth.sxy * n0 + oth.tyy * n1 + oth.syz * n2;
+    const R so2 = oth.sxz * n0 + oth.syz * n1 + oth.tzz * n2;
     const R tmn = sm0 * n0 + sm1 * n1 + sm2 * n2;
     const R ton = so0 * n0 + so1 * n1 + so2 * n2;
     // acoustic Riemann problem, left = L, right = R:
@@ -136,25 +133,30 @@ __device__ __forceinline__ void pair_terms(R d0, R d1, R d2, const PIn<R> &me, c
     const R us = (add_rn(mul_rn(me.Z, um), mul_rn(oth.Z, uo)) + dRL_t) * izs;
     const R ts = (add_rn(mul_rn(oth.Z, tmn), mul_rn(me.Z, ton)) + (me.Z * oth.Z) * dRL_u) * izs;
     const R du = us - half * (um + uo);
-    const R rhoE = half * (me.rho + oth.rho);
-    const R EE = half * (me.E + oth.E);
-    const R tm = half * (tmn + ton);
-    const R vE0 = half * (me.vx + oth.vx) + du * n0;
-    const R vE1 = half * (me.vy + oth.vy) + du * n1;
-    const R vE2 = half * (me.vz + oth.vz) + du * n2;
-    const R TE0 = ts * n0 + (half * (sm0 + so0) - tm * n0);
-    const R TE1 = ts * n1 + (half * (sm1 + so1) - tm * n1);
-    const R TE2 = ts * n2 + (half * (sm2 + so2) - tm * n2);
-    const R wwa = R(2) * me.w * oth.w * a;
-    const R mf = rhoE * du;
-    o.Fm = wwa * mf;
-    o.Fmv[0] = wwa * (mf * vE0 - TE0);
-    o.Fmv[1] = wwa * (mf * vE1 - TE1);
-    o.Fmv[2] = wwa * (mf * vE2 - TE2);
-    o.Fe = wwa * (mf * EE - (TE0 * vE0 + TE1 * vE1 + TE2 * vE2));
+    // interface velocity and traction at twice their value (binary scalings, exact): V = 2 v_E =
+    // (v_i + v_j) + 2 du n, T = 2 sigma_E n = 2 t* n + (sigma_i n + sigma_j n) - (t_i + t_j) n
+    const R du2 = du + du, ts2 = ts + ts, tm2 = tmn + ton;
+    const R V0 = (me.vx + oth.vx) + du2 * n0;
+    const R V1 = (me.vy + oth.vy) + du2 * n1;
+    const R V2 = (me.vz + oth.vz) + du2 * n2;
+    const R T0 = ts2 * n0 + ((sm0 + so0) - tm2 * n0);
+    const R T1 = ts2 * n1 + ((sm1 + so1) - tm2 * n1);
+    const R T2 = ts2 * n2 + ((sm2 + so2) - tm2 * n2);
+    // with w2a = w_i w_j a and the mass flux mf = rho_E du (mf2 = 2 mf):
+    //   2 w_i w_j a (mf v_E - sigma_E n) = w2a (mf V - T),
+    //   2 w_i w_j a (mf E_E - sigma_E n . v_E) = (w2a / 2) (mf2 (E_i + E_j) - T . V)
+    const R w2a = me.w * oth.w * a;
+    const R mf2 = (me.rho + oth.rho) * du;
+    const R mf = half * mf2;
+    o.Fm = w2a * mf2;
+    o.Fmv[0] = w2a * (mf * V0 - T0);
+    o.Fmv[1] = w2a * (mf * V1 - T1);
+    o.Fmv[2] = w2a * (mf * V2 - T2);
+    o.Fe = (half * w2a) * (mf2 * (me.E + oth.E) - (T0 * V0 + T1 * V1 + T2 * V2));
     o.a = a;
     o.n[0] = n0; o.n[1] = n1; o.n[2] = n2;
     o.du_vol = dRL_u;
+    o.w2a = w2a;
 }
 
 // Per-particle sums. FP32: compensated for the conserved quantities (fields 0-5: volume, mass,
@@ -227,7 +229,7 @@ template <> struct Acc<double> {
 template <class R>
 __device__ __forceinline__ void accumulate(Acc<R> &acc, const PairRes<R> &o, R sg, const PIn<R> &me,
                                            const PIn<R> &oth) {
-    acc.add(0, me.w * oth.w * o.a * o.du_vol);
+    acc.add(0, o.w2a * o.du_vol);
     acc.add(1, sg * o.Fm);
     acc.add(2, sg * o.Fmv[0]);
     acc.add(3, sg * o.Fmv[1]);
@@ -583,22 +585,25 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
     // one real neighbour jj, in row (dcy, dcz) = code - 1 and bucket x cxj: canonical orientation (the
     // lower sorted slot is the left state); both ends of the pair evaluate x_R - x_L from the same
     // operands in the same order
-    auto real_pair = [&](uint32_t jj, uint32_t code, R cxj, const Pos &pj, const Rec &rj) {
+    // act = false evaluates a harmless stand-in pair (a nonzero offset, kernel weight 0) that adds zeros,
+    // so the listed-neighbour loop needs no branch around the pair
+    auto real_pair = [&](uint32_t jj, uint32_t code, R cxj, const Pos &pj, const Rec &rj, bool act) {
         const PIn<R> oth = unpack(rj, (R)pj.w);
-        // x_j - x_i from this end, then oriented L -> R by the exact factor sgn: both ends obtain the
-        // same canonical difference bit for bit (a - b = -(b - a) in IEEE arithmetic)
+        // x_j - x_i from this end; the exact factor sgn orients it L -> R inside the pair terms, so both
+        // ends obtain the same canonical normal bit for bit (a - b = -(b - a) in IEEE arithmetic)
         const R sgn = s < (int64_t)jj ? R(1) : R(-1);
         R d0, d1, d2;
         if (SPLIT) {
             const R ey = (R)(int)(code & 3u) * fcell - fcell, ez = (R)(int)(code >> 2) * fcell - fcell;
-            d0 = sgn * (((R)pj.x - mrx) + (cxj - cxf) * fcell);
-            d1 = sgn * (((R)pj.y - mry) + ey);
-            d2 = sgn * (((R)pj.z - mrz) + ez);
+            d0 = ((R)pj.x - mrx) + (cxj - cxf) * fcell;
+            d1 = ((R)pj.y - mry) + ey;
+            d2 = ((R)pj.z - mrz) + ez;
         } else {
-            d0 = sgn * ((R)pj.x - mrx); d1 = sgn * ((R)pj.y - mry); d2 = sgn * ((R)pj.z - mrz);
+            d0 = (R)pj.x - mrx; d1 = (R)pj.y - mry; d2 = (R)pj.z - mrz;
         }
+        if (!act) d0 = fcell;
         PairRes<R> o;
-        pair_terms<R, MODE == PM_HEUN2>(d0, d1, d2, me, oth, sgn, inv_h, kdw, o);
+        pair_terms<R, MODE == PM_HEUN2>(d0, d1, d2, me, oth, sgn, inv_h, act ? kdw : R(0), o);
         accumulate<R>(acc, o, -sgn, me, oth);
     };
 
@@ -661,10 +666,9 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
             if ((uint32_t)k + 1 < nlist) next(j1, c1);   // else j1 stays a valid slot
             t1 = take(j1);
             fetch(j1, t1, p1, r1, x1);
-            if ((uint32_t)k < nlist && tj) {
-                real_pair(j, c, (R)xj, pj, rj);
-                if (!ALLPAIRS) ++nsel;
-            }
+            const bool act = (uint32_t)k < nlist && tj;
+            real_pair(j, c, (R)xj, pj, rj, act);
+            if (!ALLPAIRS) nsel += act ? 1 : 0;
             if ((k & 7) == 7) acc.fold();
         }
     }
@@ -738,7 +742,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
                     // real neighbour past the list capacity
                     if (seen++ < nlist) continue;
                     if (!take(j)) continue;
-                    real_pair(j, (uint32_t)(dcy + 1) | (uint32_t)(dcz + 1) << 2, (R)cxs[j], pj, rec[j]);
+                    real_pair(j, (uint32_t)(dcy + 1) | (uint32_t)(dcz + 1) << 2, (R)cxs[j], pj, rec[j], true);
                     ++nover;
                 } else {
                     if (!take(j)) continue;
@@ -816,11 +820,20 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
 #pragma unroll
             for (int v = 0; v < 3; ++v) Lm[u][v] = acc.getr(6 + 3 * u + v);
         // the stress of the step's start as the record holds it (the FP32 rounding on the split path)
+        // (split: the record's sigma plus the pressure its trace gives; FP64: the state's S)
         R Sr[3][3];
-        Sr[0][0] = me.sxx; Sr[1][1] = me.syy; Sr[2][2] = me.szz;
-        Sr[0][1] = Sr[1][0] = me.sxy;
-        Sr[0][2] = Sr[2][0] = me.sxz;
-        Sr[1][2] = Sr[2][1] = me.syz;
+        if (SPLIT) {
+            const R pr = -(me.txx + me.tyy + me.tzz) * (R(1) / R(3));
+            Sr[0][0] = me.txx + pr; Sr[1][1] = me.tyy + pr; Sr[2][2] = me.tzz + pr;
+            Sr[0][1] = Sr[1][0] = me.sxy;
+            Sr[0][2] = Sr[2][0] = me.sxz;
+            Sr[1][2] = Sr[2][1] = me.syz;
+        } else {
+            Sr[0][0] = (R)S[0]; Sr[1][1] = (R)S[1]; Sr[2][2] = (R)S[2];
+            Sr[0][1] = Sr[1][0] = (R)S[3];
+            Sr[0][2] = Sr[2][0] = (R)S[4];
+            Sr[1][2] = Sr[2][1] = (R)S[5];
+        }
         const R trD = Lm[0][0] + Lm[1][1] + Lm[2][2];
         const R G2 = SPLIT ? (R)(2.0f * P.f_G[mt]) : (R)(2.0 * P.G[mt]);
         const int iu[6] = {0, 1, 2, 0, 0, 1}, iv[6] = {0, 1, 2, 1, 2, 2};

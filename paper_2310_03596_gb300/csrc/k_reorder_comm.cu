@@ -12,8 +12,8 @@ namespace gsph {
 // particle.
 // ---------------------------------------------------------------------------------------------
 // Interaction record of one particle in slot s with bucket hash k: split path, the position relative
-// to the own bucket corner and the FP32 state; FP64 path, the FP64 position and state. Pressure and
-// impedance from the equation of state.
+// to the own bucket corner and the FP32 state with the stress diagonal as sigma = -p I + S; FP64 path,
+// the FP64 position and state. Pressure and impedance from the equation of state.
 template <bool SPLIT>
 __device__ __forceinline__ void write_record(const DevParams &P, int64_t s, uint32_t k, double x, double y, double z,
                                              double w, double m, double vx, double vy, double vz, double E,
@@ -47,9 +47,11 @@ __device__ __forceinline__ void write_record(const DevParams &P, int64_t s, uint
             pf = (float)pd;
             Zf = (float)(rd * cd);
         }
+        // the diagonal of the full stress sigma = -p I + S (S traceless in FP32: S_zz = -(S_xx + S_yy))
+        const float fxx = (float)sxx, fyy = (float)syy, fzz = -(fxx + fyy);
         r.a = make_float4((float)vx, (float)vy, (float)vz, rho);
-        r.b = make_float4(pf, Zf, (float)E, (float)sxx);
-        r.c = make_float4((float)syy, (float)sxy, (float)sxz, (float)syz);
+        r.b = make_float4(fzz - pf, Zf, (float)E, fxx - pf);
+        r.c = make_float4(fyy - pf, (float)sxy, (float)sxz, (float)syz);
         ((float4 *)pos_out)[s] = p4;
         ((RecF *)rec_out)[s] = r;
         (void)szz;
