@@ -90,7 +90,8 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 
-template <class R> struct PairRes { R Fm, Fmv[3], Fe, a, n[3], du_vol, w2a; };
+// flux factors: the pair's mass, momentum and energy fluxes are w2a Xm, w2a Xv and (w2a / 2) Xe
+template <class R> struct PairRes { R Xm, Xv[3], Xe, a, n[3], du_vol, w2a; };
 
 // Pair fluxes on the canonical pair: e = x_j - x_i as seen from this end (the canonical difference
 // x_R - x_L, L the lower sorted slot, is sgn e), `me` the particle being updated and `oth` its
@@ -102,18 +103,18 @@ template <class R> struct PairRes { R Fm, Fmv[3], Fe, a, n[3], du_vol, w2a; };
 // CLAMP: the pair may lie beyond the support (second Heun stage over the step-start lists), where the
 // kernel gradient is 0.
 template <class R, bool CLAMP = false>
-__device__ __forceinline__ void pair_terms(R e0, R e1, R e2, const PIn<R> &me, const PIn<R> &oth, R sgn, R inv_h,
-                                           R kdw, PairRes<R> &o) {
+__device__ __forceinline__ void pair_terms(R e0, R e1, R e2, const PIn<R> &me, const PIn<R> &oth, R sgn, R inv_2h,
+                                           R kdwh, PairRes<R> &o) {
     const R half = R(0.5);
     const R r2 = e0 * e0 + e1 * e1 + e2 * e2;
     const R inv_r = rsqrt_r(r2);
     const R r = r2 * inv_r;
     const R sir = sgn * inv_r;   // the canonical normal n = sgn e / r
     const R n0 = e0 * sir, n1 = e1 * sir, n2 = e2 * sir;
-    const R q = r * inv_h;
-    R sq = R(1) - half * q;
+    // |dW/dr| = kdw q (1 - q/2)^3 with q = r / h, as (kdw / h) r (1 - r / 2h)^3
+    R sq = R(1) - inv_2h * r;
     if (CLAMP) sq = sq > R(0) ? sq : R(0);
-    const R a = kdw * q * sq * sq * sq;
+    const R a = kdwh * r * sq * sq * sq;
     // normal velocity, traction sigma n and normal traction of each particle
     const R um = me.vx * n0 + me.vy * n1 + me.vz * n2;
     const R uo = oth.vx * n0 + oth.vy * n1 + oth.vz * n2;
@@ -148,11 +149,11 @@ __device__ __forceinline__ void pair_terms(R e0, R e1, R e2, const PIn<R> &me, c
     const R w2a = me.w * oth.w * a;
     const R mf2 = (me.rho + oth.rho) * du;
     const R mf = half * mf2;
-    o.Fm = w2a * mf2;
-    o.Fmv[0] = w2a * (mf * V0 - T0);
-    o.Fmv[1] = w2a * (mf * V1 - T1);
-    o.Fmv[2] = w2a * (mf * V2 - T2);
-    o.Fe = (half * w2a) * (mf2 * (me.E + oth.E) - (T0 * V0 + T1 * V1 + T2 * V2));
+    o.Xm = mf2;
+    o.Xv[0] = mf * V0 - T0;
+    o.Xv[1] = mf * V1 - T1;
+    o.Xv[2] = mf * V2 - T2;
+    o.Xe = mf2 * (me.E + oth.E) - (T0 * V0 + T1 * V1 + T2 * V2);
     o.a = a;
     o.n[0] = n0; o.n[1] = n1; o.n[2] = n2;
     o.du_vol = dRL_u;
@@ -229,12 +230,14 @@ template <> struct Acc<double> {
 template <class R>
 __device__ __forceinline__ void accumulate(Acc<R> &acc, const PairRes<R> &o, R sg, const PIn<R> &me,
                                            const PIn<R> &oth) {
+    // sg (w2a X) = (sg w2a) X exactly: the fluxes' scale and orientation in one factor
+    const R sgw = sg * o.w2a;
     acc.add(0, o.w2a * o.du_vol);
-    acc.add(1, sg * o.Fm);
-    acc.add(2, sg * o.Fmv[0]);
-    acc.add(3, sg * o.Fmv[1]);
-    acc.add(4, sg * o.Fmv[2]);
-    acc.add(5, sg * o.Fe);
+    acc.add(1, sgw * o.Xm);
+    acc.add(2, sgw * o.Xv[0]);
+    acc.add(3, sgw * o.Xv[1]);
+    acc.add(4, sgw * o.Xv[2]);
+    acc.add(5, (R(0.5) * sgw) * o.Xe);
     // L_i += w_j (v_j - v_i) (x) a n_ij, n_ij = -sg n
     R an = -sg * o.a * oth.w;
     R g0 = an * o.n[0], g1 = an * o.n[1], g2 = an * o.n[2];
@@ -556,8 +559,8 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
     } else {
         me = PIn<R>{};
     }
-    const R inv_h = SPLIT ? (R)P.f_inv_h : (R)(1.0 / P.h);
-    const R kdw = SPLIT ? (R)P.f_kdw : (R)P.kdw;
+    const R inv_2h = SPLIT ? (R)(0.5f * P.f_inv_h) : (R)(0.5 / P.h);
+    const R kdwh = SPLIT ? (R)(P.f_kdw * P.f_inv_h) : (R)(P.kdw / P.h);
     const R fcell = SPLIT ? (R)P.f_cell : (R)P.cell;
     // label filter of the two-pass order: PM_LOCAL takes neighbours of the own label, PM_BOUNDARY the others
     constexpr bool ALLPAIRS = MODE == PM_ALL || MODE == PM_HEUN1 || MODE == PM_HEUN2;
@@ -603,7 +606,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         }
         if (!act) d0 = fcell;
         PairRes<R> o;
-        pair_terms<R, MODE == PM_HEUN2>(d0, d1, d2, me, oth, sgn, inv_h, act ? kdw : R(0), o);
+        pair_terms<R, MODE == PM_HEUN2>(d0, d1, d2, me, oth, sgn, inv_2h, act ? kdwh : R(0), o);
         accumulate<R>(acc, o, -sgn, me, oth);
     };
 
@@ -765,7 +768,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
                     }
                     mirror<R>(oth, wax);
                     PairRes<R> o;
-                    pair_terms<R, MODE == PM_HEUN2>(d0, d1, d2, me, oth, R(1), inv_h, kdw, o);
+                    pair_terms<R, MODE == PM_HEUN2>(d0, d1, d2, me, oth, R(1), inv_2h, kdwh, o);
                     accumulate<R>(acc, o, R(-1), me, oth);
                     ++ni;
                 }
