@@ -132,10 +132,16 @@ template <class T> inline void riemann(T uL, T uR, T tL, T tR, T ZL, T ZR, T &us
 // Outputs for L (R receives the negatives): Fm, Fmv, Fe are the amounts subtracted from the rates
 // of L, i.e. d(m)_L/dt -= Fm, d(mv)_L/dt -= Fmv, d(mE)_L/dt -= Fe. Also returns a = |dW/dr|, n,
 // and the normal velocities (for the volume rate).
+// L and R are the states of the Riemann problem; L0 and R0 (null: L and R) are the particles' own
+// states, whose velocities are the transport velocities v0 (they differ under MUSCL reconstruction):
+// the mass flux carries (v_E - v0_LR) . n and the volume rate the particles' normal velocities.
 template <class T> struct PairOut { T Fm, Fmv[3], Fe, a, n[3], uL, uR; };
 
 template <class T>
-inline void pair_flux(const T dlr[3], const Prim<T> &L, const Prim<T> &R, double h, PairOut<T> &o) {
+inline void pair_flux(const T dlr[3], const Prim<T> &L, const Prim<T> &R, double h, PairOut<T> &o,
+                      const Prim<T> *L0 = nullptr, const Prim<T> *R0 = nullptr) {
+    if (!L0) L0 = &L;
+    if (!R0) R0 = &R;
     T r2 = dlr[0] * dlr[0] + dlr[1] * dlr[1] + dlr[2] * dlr[2];
     T r = sqrt(r2);
     T n[3] = {dlr[0] / r, dlr[1] / r, dlr[2] / r};
@@ -154,12 +160,15 @@ inline void pair_flux(const T dlr[3], const Prim<T> &L, const Prim<T> &R, double
     T tR = sR[0] * n[0] + sR[1] * n[1] + sR[2] * n[2];
     T us, ts;
     riemann(uL, uR, tL, tR, L.Z, R.Z, us, ts);
-    T du = us - (uL + uR) / 2.0;                 // (v_E - v0_LR) . n
+    T u0L = L0->v[0] * n[0] + L0->v[1] * n[1] + L0->v[2] * n[2];
+    T u0R = R0->v[0] * n[0] + R0->v[1] * n[1] + R0->v[2] * n[2];
+    T du = us - (u0L + u0R) / 2.0;               // (v_E - v0_LR) . n
+    T dus = us - (uL + uR) / 2.0;                // the Riemann correction of the mean normal velocity
     T rhoE = (L.rho + R.rho) / 2.0;
     T EE = (L.E + R.E) / 2.0;
     T vE[3], TE[3];
     for (int k = 0; k < 3; ++k) {
-        vE[k] = (L.v[k] + R.v[k]) / 2.0 + du * n[k];
+        vE[k] = (L.v[k] + R.v[k]) / 2.0 + dus * n[k];
         // normal part from the Riemann solver, tangential part averaged
         TE[k] = ts * n[k] + ((sL[k] + sR[k]) - (tL + tR) * n[k]) / 2.0;
     }
@@ -171,8 +180,8 @@ inline void pair_flux(const T dlr[3], const Prim<T> &L, const Prim<T> &R, double
     o.Fe = ww * a * (mflux * EE - tv);
     o.a = a;
     for (int k = 0; k < 3; ++k) o.n[k] = n[k];
-    o.uL = uL;
-    o.uR = uR;
+    o.uL = u0L;
+    o.uR = u0R;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -365,12 +374,110 @@ template <class T> Prim<T> mirror_prim(const Prim<T> &p, int ax) {
     return q;
 }
 
+// ---------------------------------------------------------------------------------------------
+// MUSCL reconstruction (reading of the second-order SPH-ALE variant; the paper gives no scheme).
+// Gradients of v and of the full stress sigma = -p I + S by the SPH gradient operator
+//   G_i(phi) = sum_j w_j (phi_j - phi_i) grad_i W_ij,  grad_i W_ij = |dW/dr| (x_j - x_i) / r,
+// over the same real and image neighbours as the fluxes. On a pair (L, R) with d = x_R - x_L each
+// reconstructed component is limited by minmod against the centred difference:
+//   phi_L* = phi_L + minmod(G_L(phi) . d, phi_R - phi_L) / 2,
+//   phi_R* = phi_R - minmod(G_R(phi) . d, phi_R - phi_L) / 2,
+// so the interface states stay between the two particle values, and a component at a local extremum
+// (slope and difference of opposite signs) keeps its first-order value. Density, energy and impedance
+// keep the particle values.
+// ---------------------------------------------------------------------------------------------
+constexpr int NGRAD = ORC_NGRAD;
+
+// sigma = -p I + S as xx yy zz xy xz yz
+template <class T> inline void sigma_of(const Prim<T> &p, T sg[6]) {
+    for (int k = 0; k < 6; ++k) sg[k] = k < 3 ? p.S[k] - p.p : p.S[k];
+}
+
+template <class T> inline T minmod(T a, T b) {
+    if (!(val(a) * val(b) > 0.0)) return T(0.0);
+    return std::fabs(val(a)) < std::fabs(val(b)) ? a : b;
+}
+
+// Gradient of the mirror image of a particle in wall axis ax: d phi'/dx'_b picks up the sign of each
+// index along the axis (the field's own indices and the derivative's).
+template <class T> void mirror_grad(const T *G, int ax, T *Gm) {
+    const int ci[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Gm[3 * a + b] = ((a == ax) != (b == ax)) ? -G[3 * a + b] : G[3 * a + b];
+    for (int c = 0; c < 6; ++c)
+        for (int b = 0; b < 3; ++b) {
+            int flips = (ci[c][0] == ax) + (ci[c][1] == ax) + (b == ax);
+            T g = G[9 + 3 * c + b];
+            Gm[9 + 3 * c + b] = (flips & 1) ? -g : g;
+        }
+}
+
+template <class T>
+void grads_of(const orc_params *P, const StateT<T> &s, const Mat<T> *mats, const Buckets &b,
+              const std::vector<double> &xv, const std::vector<double> &yv, const std::vector<double> &zv,
+              const std::vector<uint32_t> &key, int64_t i, T *G) {
+    for (int k = 0; k < NGRAD; ++k) G[k] = T(0.0);
+    Prim<T> pi = prim_of(s, mats, i);
+    T si[6];
+    sigma_of(pi, si);
+    T xi[3] = {s.x[i], s.y[i], s.z[i]};
+    auto add = [&](const Prim<T> &pj, const T d[3]) {
+        T r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        T a = kernel_dw_abs(r, P->h);
+        T gw[3] = {a * d[0] / r, a * d[1] / r, a * d[2] / r};
+        T sj[6];
+        sigma_of(pj, sj);
+        for (int u = 0; u < 3; ++u)
+            for (int c = 0; c < 3; ++c) G[3 * u + c] = G[3 * u + c] + pj.w * (pj.v[u] - pi.v[u]) * gw[c];
+        for (int q = 0; q < 6; ++q)
+            for (int c = 0; c < 3; ++c) G[9 + 3 * q + c] = G[9 + 3 * q + c] + pj.w * (sj[q] - si[q]) * gw[c];
+    };
+    neighbours_of(
+        P, b, s.n, xv.data(), yv.data(), zv.data(), key.data(), i,
+        [&](int64_t j) {
+            T d[3] = {s.x[j] - xi[0], s.y[j] - xi[1], s.z[j] - xi[2]};
+            add(prim_of(s, mats, j), d);
+        },
+        [&](int k, int64_t j) {
+            const orc_wall &W = P->wall[k];
+            T xj[3] = {s.x[j], s.y[j], s.z[j]};
+            xj[W.axis] = T(2.0 * W.pos) - xj[W.axis];
+            T d[3] = {xj[0] - xi[0], xj[1] - xi[1], xj[2] - xi[2]};
+            add(mirror_prim(prim_of(s, mats, j), W.axis), d);
+        });
+}
+
+// Interface states of the pair (L, R), d = x_R - x_L: v and sigma reconstructed (the stress of the
+// returned states is the full sigma with p = 0), the rest copied.
+template <class T>
+void reconstruct(const Prim<T> &L, const T *GL, const Prim<T> &R, const T *GR, const T d[3], Prim<T> &Ls,
+                 Prim<T> &Rs) {
+    Ls = L;
+    Rs = R;
+    auto dot = [&](const T *g) { return g[0] * d[0] + g[1] * d[1] + g[2] * d[2]; };
+    for (int a = 0; a < 3; ++a) {
+        T dphi = R.v[a] - L.v[a];
+        Ls.v[a] = L.v[a] + minmod(dot(GL + 3 * a), dphi) / 2.0;
+        Rs.v[a] = R.v[a] - minmod(dot(GR + 3 * a), dphi) / 2.0;
+    }
+    T sL[6], sR[6];
+    sigma_of(L, sL);
+    sigma_of(R, sR);
+    for (int q = 0; q < 6; ++q) {
+        T dphi = sR[q] - sL[q];
+        Ls.S[q] = sL[q] + minmod(dot(GL + 9 + 3 * q), dphi) / 2.0;
+        Rs.S[q] = sR[q] - minmod(dot(GR + 9 + 3 * q), dphi) / 2.0;
+    }
+    Ls.p = T(0.0);
+    Rs.p = T(0.0);
+}
+
 // Interaction loop (Sec. II step f): rates of particle i from all its real and image neighbours.
 template <class T>
 void rates_of(const orc_params *P, const StateT<T> &s, const Mat<T> *mats, const Buckets &b,
               const std::vector<double> &xv, const std::vector<double> &yv,
               const std::vector<double> &zv, const std::vector<uint32_t> &key, int64_t i, T *r,
-              int32_t *nreal, int32_t *nimage) {
+              int32_t *nreal, int32_t *nimage, const T *grads = nullptr) {
     for (int k = 0; k < ORC_NRATE; ++k) r[k] = T(0.0);
     int32_t cr = 0, ci = 0;
     Prim<T> pi = prim_of(s, mats, i);
@@ -392,7 +499,13 @@ void rates_of(const orc_params *P, const StateT<T> &s, const Mat<T> *mats, const
             const Prim<T> &PR = i_left ? pj : pi;
             T d[3] = {s.x[rr] - s.x[l], s.y[rr] - s.y[l], s.z[rr] - s.z[l]};
             PairOut<T> o;
-            pair_flux(d, PL, PR, P->h, o);
+            if (grads) {
+                Prim<T> Ls, Rs;
+                reconstruct(PL, grads + NGRAD * l, PR, grads + NGRAD * rr, d, Ls, Rs);
+                pair_flux(d, Ls, Rs, P->h, o, &PL, &PR);
+            } else {
+                pair_flux(d, PL, PR, P->h, o);
+            }
             double sg = i_left ? -1.0 : 1.0;
             r[0] = r[0] + pi.w * pj.w * o.a * (o.uR - o.uL);
             r[1] = r[1] + sg * o.Fm;
@@ -410,7 +523,15 @@ void rates_of(const orc_params *P, const StateT<T> &s, const Mat<T> *mats, const
             xj[W.axis] = T(2.0 * W.pos) - xj[W.axis];
             T d[3] = {xj[0] - xi[0], xj[1] - xi[1], xj[2] - xi[2]};
             PairOut<T> o;
-            pair_flux(d, pi, pj, P->h, o);                     // i is the left state
+            if (grads) {                                       // i is the left state
+                T Gm[NGRAD];
+                mirror_grad(grads + NGRAD * j, W.axis, Gm);
+                Prim<T> Ls, Rs;
+                reconstruct(pi, grads + NGRAD * i, pj, Gm, d, Ls, Rs);
+                pair_flux(d, Ls, Rs, P->h, o, &pi, &pj);
+            } else {
+                pair_flux(d, pi, pj, P->h, o);
+            }
             r[0] = r[0] + pi.w * pj.w * o.a * (o.uR - o.uL);
             r[1] = r[1] - o.Fm;
             for (int q = 0; q < 3; ++q) r[2 + q] = r[2 + q] - o.Fmv[q];
@@ -449,11 +570,19 @@ void rates_all(const orc_params *P, const StateT<T> &s, const Mat<T> *mats, int6
     std::vector<uint32_t> key(n);
     orc_hash(P, n, xv.data(), yv.data(), zv.data(), key.data());
     Buckets b = make_buckets(P, n, key.data());
+    // MUSCL: the gradients of every particle first (a pair needs both ends')
+    std::vector<T> G;
+    if (P->reconstruction == 1) {
+        G.assign((size_t)n * NGRAD, T(0.0));
+        for (int64_t i = 0; i < n; ++i) grads_of(P, s, mats, b, xv, yv, zv, key, i, G.data() + NGRAD * i);
+    }
+    const T *gp = G.empty() ? nullptr : G.data();
     if (subset) {
         for (int64_t q = 0; q < nsub; ++q)
-            rates_of(P, s, mats, b, xv, yv, zv, key, subset[q], rates + ORC_NRATE * subset[q], nreal, nimage);
+            rates_of(P, s, mats, b, xv, yv, zv, key, subset[q], rates + ORC_NRATE * subset[q], nreal, nimage, gp);
     } else {
-        for (int64_t i = 0; i < n; ++i) rates_of(P, s, mats, b, xv, yv, zv, key, i, rates + ORC_NRATE * i, nreal, nimage);
+        for (int64_t i = 0; i < n; ++i)
+            rates_of(P, s, mats, b, xv, yv, zv, key, i, rates + ORC_NRATE * i, nreal, nimage, gp);
     }
 }
 
@@ -925,6 +1054,17 @@ void orc_step(const orc_params *P, orc_state *S, int32_t do_swap, uint32_t *key_
     if (nimage_out) std::copy(ni.begin(), ni.end(), nimage_out);
     if (rates_out) std::copy(rates.begin(), rates.end(), rates_out);
     if (dt_out) *dt_out = dt;
+}
+
+void orc_gradients(const orc_params *P, const orc_state *S, double *grads) {
+    StateT<double> s = load(S);
+    int64_t n = s.n;
+    Mat<double> mats[ORC_MAX_MAT];
+    mats_of(P, mats);
+    std::vector<uint32_t> key(n);
+    orc_hash(P, n, s.x.data(), s.y.data(), s.z.data(), key.data());
+    Buckets b = make_buckets(P, n, key.data());
+    for (int64_t i = 0; i < n; ++i) grads_of(P, s, mats, b, s.x, s.y, s.z, key, i, grads + NGRAD * i);
 }
 
 double orc_kernel_w(double r, double h) { return kernel_w<double>(r, h); }

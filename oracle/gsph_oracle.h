@@ -56,6 +56,10 @@ typedef struct {
     int32_t integrator;              /* 0: forward Euler; 1: two-stage Heun (SSP-RK2), both stages with
                                         the neighbour set of the step's start */
     int32_t pad2;
+    int32_t reconstruction;          /* 0: first-order Riemann states (the particle values); 1: MUSCL,
+                                        minmod-limited linear reconstruction of v and sigma at the pair
+                                        midpoint from SPH gradients */
+    int32_t pad3;
 } orc_params;
 
 typedef struct {
@@ -89,6 +93,12 @@ int64_t orc_neighbours_cells(const orc_params *P, int64_t n, const double *x, co
  * only the nsub listed slots are evaluated (rates of the others are left untouched). */
 void orc_rates(const orc_params *P, const orc_state *S, int64_t nsub, const int64_t *subset,
                double *rates, int32_t *nreal, int32_t *nimage);
+/* Gradients of the MUSCL reconstruction by the SPH gradient operator over real and image neighbours,
+ * G_i(phi) = sum_j w_j (phi_j - phi_i) grad_i W_ij, 27 per particle: [0..8] grad v (row-major,
+ * dv_a/dx_b), [9 + 3c + b] d sigma_c / dx_b for the components c = xx yy zz xy xz yz of the full
+ * stress sigma = -p I + S. */
+#define ORC_NGRAD 27
+void orc_gradients(const orc_params *P, const orc_state *S, double *grads);
 /* Equation of state of material mat (Sec. IV, reading): pressure at density rho and specific internal
  * energy e (with the cut-off) and the square of the bulk sound speed (isentropic derivative of the
  * uncut pressure, floored at 0). */

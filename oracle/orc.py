@@ -51,7 +51,8 @@ class Params(C.Structure):
     _fields_ = [("lo", C.c_double * 3), ("dims", C.c_int32 * 3), ("nmat", C.c_int32),
                 ("h", C.c_double), ("cfl", C.c_double), ("mat", Material * MAX_MAT),
                 ("nwalls", C.c_int32), ("K", C.c_int32), ("wall", Wall * MAX_WALL),
-                ("g", C.c_double * 3), ("alpha", C.c_double), ("integrator", C.c_int32), ("pad2", C.c_int32)]
+                ("g", C.c_double * 3), ("alpha", C.c_double), ("integrator", C.c_int32), ("pad2", C.c_int32),
+                ("reconstruction", C.c_int32), ("pad3", C.c_int32)]
 
 
 _DP = C.POINTER(C.c_double)
@@ -99,6 +100,7 @@ def lib():
             L.orc_kernel_dw.argtypes = [C.c_double, C.c_double]
             L.orc_kernel_dw.restype = C.c_double
             L.orc_riemann.argtypes = [C.c_double] * 6 + [_DP]
+            L.orc_gradients.argtypes = [P(Params), P(StateC), _DP]
             L.orc_forward_gradient.argtypes = [P(Params), P(StateC), C.c_int32, _DP, C.c_int64, _U32P, _DP]
             L.orc_forward_gradient.restype = C.c_double
             _lib = L
@@ -136,6 +138,7 @@ def params_of(scene) -> Params:
     p.h = scene.h
     p.cfl = scene.cfl
     p.integrator = int(getattr(scene, "integrator", 0) or 0)
+    p.reconstruction = int(getattr(scene, "reconstruction", 0) or 0)
     p.nwalls = len(scene.walls)
     for k, (axis, pos) in enumerate(scene.walls):
         p.wall[k] = Wall(axis, 0, pos)
@@ -348,6 +351,14 @@ def kernel_w(r: float, h: float) -> float:
 
 def kernel_dw(r: float, h: float) -> float:
     return lib().orc_kernel_dw(r, h)
+
+
+def gradients(P: Params, st: OracleState) -> np.ndarray:
+    """MUSCL gradients (n, 27): grad v row-major, then d sigma_c/dx_b for c = xx yy zz xy xz yz."""
+    out = np.zeros((st.n, 27))
+    cs = st.cstruct()
+    lib().orc_gradients(C.byref(P), C.byref(cs), _ptr(out, C.c_double))
+    return out
 
 
 def riemann(uL, uR, tL, tR, ZL, ZR):
