@@ -221,6 +221,7 @@ def main():
     ap.add_argument("--overlap-steps", type=int, default=20)
     ap.add_argument("--hvi-steps", type=int, default=50)
     ap.add_argument("--heun-steps", type=int, default=20)
+    ap.add_argument("--muscl-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -352,6 +353,30 @@ def main():
             "phase_ms_per_step": {k[:-3]: v / max(tmr["steps"], 1) for k, v in tmr.items()
                                   if k.endswith("_ms") and v > 0}}
 
+    # MUSCL-reconstructed Riemann states on the same workload: gradient pass, reconstructed fluxes
+    s3 = scenes.taylor_bar()
+    s3.reconstruction = 1
+    solm = gsph.Solver.from_scene(s3, device=local, stream=stream)
+    solm.step(3, stream)
+    solm.sync(stream)
+    solm.set_timing(args.muscl_steps)
+    torch.cuda.synchronize()
+    m0 = torch.cuda.Event(enable_timing=True)
+    m1 = torch.cuda.Event(enable_timing=True)
+    m0.record(stream)
+    solm.step(args.muscl_steps, stream)
+    m1.record(stream)
+    torch.cuda.synchronize()
+    msm = m0.elapsed_time(m1)
+    tmm = solm.timings()
+    solm.close()
+    muscl = {"what": "MUSCL reconstruction on the Taylor bar: SPH gradients of v and sigma (gradient pass), "
+                     "minmod-limited midpoint states of both ends for each Riemann problem",
+             "value": world * n * args.muscl_steps / (msm * 1e-3), "unit": "particle-steps/s",
+             "ms_per_step": msm / args.muscl_steps, "steps": args.muscl_steps,
+             "phase_ms_per_step": {k[:-3]: v / max(tmm["steps"], 1) for k, v in tmm.items()
+                                   if k.endswith("_ms") and v > 0}}
+
     # the interaction in the order of Sec. II steps d-f (two passes, halo gather on a second stream)
     solo = gsph.Solver.from_scene(s, device=local, stream=stream, overlap=True)
     solo.step(3, stream)
@@ -455,6 +480,7 @@ def main():
         "overlap": overlap,
         "hvi": hvi,
         "heun": heun,
+        "muscl": muscl,
         "clocks": ck,
         "exchange": {k: st1[k] for k in ("boundary_total", "exchange_fraction", "bytes_boundary_broadcast",
                                          "swapped_last_pass", "swap_passes")},

@@ -103,6 +103,16 @@ typedef struct {
                                    stability-preserving form, y* = E(y_n), y_{n+1} = (y_n + E(y*)) / 2 on the
                                    conserved variables, E the Euler stage with radial return, both stages
                                    over the neighbour set of the step's start (not with overlap = 1) */
+    int32_t reconstruction;     /* 0: first-order Riemann states (the particle values); 1: MUSCL (reading of
+                                   the second-order SPH-ALE variant): a gradient pass sums the SPH gradients
+                                   G_i(phi) = sum_j w_j (phi_j - phi_i) grad_i W_ij of v and sigma = -p I + S
+                                   over the same neighbours and images, and each pair's Riemann problem takes
+                                   v and sigma of both ends reconstructed at the midpoint, phi_L* = phi_L +
+                                   minmod(G_L . d, phi_R - phi_L) / 2 (R alike, d = x_R - x_L); density,
+                                   energy and impedance keep the particle values, the particle velocities
+                                   stay the transport velocities. Euler only: not with integrator = 1 or
+                                   overlap = 1, and gsph_adjoint_step refuses it */
+    int32_t pad2;
 } gsph_config;
 
 typedef enum {
@@ -163,7 +173,8 @@ typedef struct {
     int64_t steps;         /* steps recorded */
     int64_t interact_launches;
     double nbr_list_ms;    /* of which the neighbour-list kernel */
-    double pair_ms;        /* of which the pair kernel(s) (fluxes, integration) and the time-step reduction */
+    double pair_ms;        /* of which the pair kernel(s) (fluxes, integration; with reconstruction = 1 also
+                              the gradient pass) and the time-step reduction */
     /* overlap = 1 only: the two interaction passes on the launch stream, and the halo gather on the
        second stream (events there), which runs concurrently with the first pass */
     double local_ms;       /* pairs within a label, integration of particles without other labels near */
@@ -247,8 +258,8 @@ gsph_status gsph_set_dt(gsph_ctx *ctx, double dt, void *stream);
  * order X..SYZ), dJ/dy_{n+1} in the slot order y_{n+1} has (the hash order of this step, as after
  * gsph_step). lam_prev: device, same layout, receives dJ/dy_n in the current slot order.
  * grad: host, receives this step's direct contributions to dJ/dY and dJ/dG of material 0.
- * Covers the linear EOS without a pressure cut-off (every material GSPH_EOS_LINEAR, p_min = -INFINITY).
- * Does not advance the state. Errors: INVALID_ARG (null pointers, dt <= 0, wrong context kind or EOS),
+ * Covers the linear EOS without a pressure cut-off (every material GSPH_EOS_LINEAR, p_min = -INFINITY)
+ * and first-order Riemann states (reconstruction = 0). Does not advance the state. Errors: INVALID_ARG (null pointers, dt <= 0, wrong context kind or EOS),
  * NOT_READY, OOM, CUDA_ERROR. */
 gsph_status gsph_adjoint_step(gsph_ctx *ctx, const double *lam_next, double *lam_prev, double dt,
                               double grad[2], void *stream);

@@ -39,7 +39,7 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
                             unsigned int *sig, unsigned long long *pairs, unsigned long long *cost,
                             int32_t *nreal, int32_t *nimage, double *rates, const OverlapBufs *ov,
-                            int stage, cudaStream_t s);
+                            int stage, void *grad, cudaStream_t s);
 cudaError_t launch_refresh(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const State &B,
                            void *pos, void *rec, cudaStream_t s);
 // k_swap.cu
@@ -113,6 +113,7 @@ struct gsph_ctx {
     int *err = nullptr;
     int32_t *nreal = nullptr, *nimage = nullptr;
     double *rates = nullptr;
+    void *grad = nullptr;                      // MUSCL gradient records (reconstruction = 1)
     void *swap_scratch = nullptr;
     uint16_t *bh = nullptr;
     double *cons_part = nullptr, *cons_out = nullptr;
@@ -208,6 +209,10 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     A_(dalloc(c, &c->bh, N));
     A_(dalloc(c, &c->cons_part, ((N + 255) / 256 + 1) * 6));
     A_(dalloc(c, &c->cons_out, 6));
+    if (c->cfg.reconstruction) {   // MUSCL gradient records: 7 float4 (split) or 7 D4 per slot
+        if (c->split) A_(dalloc(c, (float4 **)&c->grad, N * 7));
+        else A_(dalloc(c, (D4 **)&c->grad, N * 7));
+    }
     if (c->cfg.overlap) {
         A_(dalloc(c, &c->hidx, N));
         if (c->split) {
@@ -255,6 +260,8 @@ static bool config_ok(const gsph_config *c) {
     if (c->overlap != 0 && c->overlap != 1) return false;
     if (c->integrator != 0 && c->integrator != 1) return false;
     if (c->integrator == 1 && c->overlap) return false;   // the two-pass order runs the Euler step only
+    if (c->reconstruction != 0 && c->reconstruction != 1) return false;
+    if (c->reconstruction == 1 && (c->integrator != 0 || c->overlap != 0)) return false;   // MUSCL: Euler, one pass
     if (!(c->alpha >= 0.0 && c->alpha <= 1.0)) return false;
     return true;
 }
@@ -378,7 +385,7 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     GSPH_CK(launch_interact(c->split, c->cfg.diagnostics != 0, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs,
                             c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, phase_event(c, PH_LIST),
                             c->lab_s, c->mat_s, c->id_s, c->dt, c->sig, c->pairs, c->cost, c->nreal, c->nimage,
-                            c->rates, c->cfg.overlap ? &ov : nullptr, c->cfg.integrator == 1 ? 1 : 0, s));
+                            c->rates, c->cfg.overlap ? &ov : nullptr, c->cfg.integrator == 1 ? 1 : 0, c->grad, s));
     if (c->cfg.overlap) c->launches += 2;   // halo gather, second pair pass
     if (c->cfg.integrator == 1) {
         // second Heun stage: records of the prediction, then its pairs over the same lists and the average
@@ -386,7 +393,7 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
         GSPH_CK(launch_interact(c->split, c->cfg.diagnostics != 0, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs,
                                 c->xs, c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr,
                                 c->lab_s, c->mat_s, c->id_s, c->dt, c->sig, c->pairs, c->cost, c->nreal,
-                                c->nimage, c->rates, nullptr, 2, s));
+                                c->nimage, c->rates, nullptr, 2, nullptr, s));
         c->launches += 2;
     }
     GSPH_CK(launch_finalize_dt(P, c->sig, c->dt, s));
@@ -417,7 +424,7 @@ static gsph_status enqueue_forward_pieces(gsph_ctx *c, cudaStream_t s) {
                            c->cellr, c->cxs, c->pos, c->rec, nullptr, nullptr, nullptr, c->err, s));
     GSPH_CK(launch_interact(c->split, true, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs, c->ys, c->zs,
                             kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr, c->lab_s, c->mat_s, c->id_s,
-                            c->dt, c->sig, c->pairs, c->cost, c->nreal, c->nimage, c->rates, nullptr, 0, s));
+                            c->dt, c->sig, c->pairs, c->cost, c->nreal, c->nimage, c->rates, nullptr, 0, nullptr, s));
     c->launches += 4 + 3 * radix_passes(key_bits(P.ncell));
     c->dt_dirty = true;   // the signal-speed word now holds the scratch state's maximum
     return GSPH_OK;
@@ -730,7 +737,7 @@ gsph_status gsph_set_dt(gsph_ctx *c, double dt, void *stream) {
 gsph_status gsph_adjoint_step(gsph_ctx *c, const double *lam_next, double *lam_prev, double dt, double grad[2],
                               void *stream) {
     if (!c || !lam_next || !lam_prev || !grad || !(dt > 0.0)) return GSPH_INVALID_ARG;
-    if (c->split || !c->cfg.diagnostics) return GSPH_INVALID_ARG;
+    if (c->split || !c->cfg.diagnostics || c->cfg.reconstruction) return GSPH_INVALID_ARG;
     for (int k = 0; k < c->cfg.n_materials; ++k)   // the reverse mode covers the linear EOS without cut-off
         if (c->cfg.materials[k].eos != GSPH_EOS_LINEAR || !std::isinf(c->cfg.materials[k].p_min)) return GSPH_INVALID_ARG;
     if (c->n == 0) return GSPH_NOT_READY;

@@ -21,6 +21,14 @@
 // slot, n from L to R); interface velocity v_E = mean v + (u* - mean u) n, density and energy means,
 // traction t* n plus the averaged tangential traction; Wendland C2 gradient |dW/dr| n.
 //
+// MUSCL reconstruction (reconstruction = 1, reading of the second-order SPH-ALE variant): a gradient
+//   pass (k_pair<PM_GRAD>) sums the SPH gradients of v and sigma = -p I + S over the same lists and
+//   images into a gradient record per particle; the flux pass (k_pair<PM_MUSCL>) reconstructs v and
+//   sigma of both ends at the pair midpoint, each component limited by minmod against the centred
+//   difference, for the Riemann problem, with the particle velocities as transport velocities. Both
+//   ends form the same reconstructed pair from the raw difference (odd in it), so the fluxes stay
+//   bitwise antisymmetric. The stress rate takes L from the gradient record.
+//
 // Split path: pair math in FP32 from FP32 records (positions relative to each particle's bucket corner,
 // so differences keep ~2^-24 * 2h), FP32 sums with Kahan compensation for the conserved quantities
 // (volume, mass, momentum, energy) and plain FP32 sums for the velocity gradient, FP64 integration of
@@ -102,9 +110,11 @@ template <class R> struct PairRes { R Xm, Xv[3], Xe, a, n[3], du_vol, w2a; };
 // so the two ends produce bitwise-opposite fluxes.
 // CLAMP: the pair may lie beyond the support (second Heun stage over the step-start lists), where the
 // kernel gradient is 0.
-template <class R, bool CLAMP = false>
+// RECON: me and oth are the reconstructed interface states and me0, oth0 the particles' own, whose
+// velocities are the transport velocities (mass flux and volume rate); otherwise me0, oth0 are unused.
+template <class R, bool CLAMP = false, bool RECON = false>
 __device__ __forceinline__ void pair_terms(R e0, R e1, R e2, const PIn<R> &me, const PIn<R> &oth, R sgn, R inv_2h,
-                                           R kdwh, PairRes<R> &o) {
+                                           R kdwh, PairRes<R> &o, const PIn<R> &me0, const PIn<R> &oth0) {
     const R half = R(0.5);
     const R r2 = e0 * e0 + e1 * e1 + e2 * e2;
     const R inv_r = rsqrt_r(r2);
@@ -133,10 +143,17 @@ __device__ __forceinline__ void pair_terms(R e0, R e1, R e2, const PIn<R> &me, c
     const R dRL_u = sgn * (uo - um);     // uR - uL
     const R us = (add_rn(mul_rn(me.Z, um), mul_rn(oth.Z, uo)) + dRL_t) * izs;
     const R ts = (add_rn(mul_rn(oth.Z, tmn), mul_rn(me.Z, ton)) + (me.Z * oth.Z) * dRL_u) * izs;
-    const R du = us - half * (um + uo);
+    // transport velocities of the particles (the interface states' own unless reconstructed)
+    R um0 = um, uo0 = uo;
+    if (RECON) {
+        um0 = me0.vx * n0 + me0.vy * n1 + me0.vz * n2;
+        uo0 = oth0.vx * n0 + oth0.vy * n1 + oth0.vz * n2;
+    }
+    const R du = us - half * (um0 + uo0);        // (v_E - v0_LR) . n, the mass flux's velocity
+    const R dus = RECON ? us - half * (um + uo) : du;   // u* - mean of the Riemann states' u
     // interface velocity and traction at twice their value (binary scalings, exact): V = 2 v_E =
     // (v_i + v_j) + 2 du n, T = 2 sigma_E n = 2 t* n + (sigma_i n + sigma_j n) - (t_i + t_j) n
-    const R du2 = du + du, ts2 = ts + ts, tm2 = tmn + ton;
+    const R du2 = dus + dus, ts2 = ts + ts, tm2 = tmn + ton;
     const R V0 = (me.vx + oth.vx) + du2 * n0;
     const R V1 = (me.vy + oth.vy) + du2 * n1;
     const R V2 = (me.vz + oth.vz) + du2 * n2;
@@ -156,8 +173,54 @@ __device__ __forceinline__ void pair_terms(R e0, R e1, R e2, const PIn<R> &me, c
     o.Xe = mf2 * (me.E + oth.E) - (T0 * V0 + T1 * V1 + T2 * V2);
     o.a = a;
     o.n[0] = n0; o.n[1] = n1; o.n[2] = n2;
-    o.du_vol = dRL_u;
+    o.du_vol = RECON ? sgn * (uo0 - um0) : dRL_u;
     o.w2a = w2a;
+}
+
+// ---- MUSCL pieces. Gradient record order: the 9 fields vx vy vz, sigma xx yy zz xy xz yz, each as
+// d/dx, d/dy, d/dz (27 values, padded to 28).
+constexpr int kNGrad = 27;
+template <class R> __device__ __forceinline__ R pin_field(const PIn<R> &q, int f) {
+    return f == 0 ? q.vx : f == 1 ? q.vy : f == 2 ? q.vz : f == 3 ? q.txx : f == 4 ? q.tyy : f == 5 ? q.tzz
+         : f == 6 ? q.sxy : f == 7 ? q.sxz : q.syz;
+}
+template <class R> __device__ __forceinline__ void set_field(PIn<R> &q, int f, R v) {
+    if (f == 0) q.vx = v; else if (f == 1) q.vy = v; else if (f == 2) q.vz = v;
+    else if (f == 3) q.txx = v; else if (f == 4) q.tyy = v; else if (f == 5) q.tzz = v;
+    else if (f == 6) q.sxy = v; else if (f == 7) q.sxz = v; else q.syz = v;
+}
+// minmod, odd in its arguments: minmod(-a, -b) = -minmod(a, b)
+template <class R> __device__ __forceinline__ R minmod(R a, R b) {
+    const R aa = a < R(0) ? -a : a, ab = b < R(0) ? -b : b;
+    return a * b > R(0) ? (aa < ab ? a : b) : R(0);
+}
+// gradient of the mirror image in wall axis ax: each index along the axis (the field's and the
+// derivative's) flips the sign
+template <class R> __device__ __forceinline__ void mirror_grad(R *G, int ax) {
+#pragma unroll
+    for (int f = 0; f < 9; ++f) {
+        const int i0 = f < 3 ? f : (f < 6 ? f - 3 : (f == 6 ? 0 : (f == 7 ? 0 : 1)));
+        const int i1 = f < 3 ? -1 : (f < 6 ? f - 3 : (f == 6 ? 1 : 2));
+        const int own = (i0 == ax) + (i1 == ax);
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            if ((own + (b == ax)) & 1) G[3 * f + b] = -G[3 * f + b];
+    }
+}
+// interface states of the pair from the raw difference e = x_oth - x_me (this end's)
+template <class R>
+__device__ __forceinline__ void reconstruct(const PIn<R> &me, const R *Gm, const PIn<R> &oth, const R *Go, R e0, R e1,
+                                            R e2, PIn<R> &mes, PIn<R> &oths) {
+    mes = me;
+    oths = oth;
+#pragma unroll
+    for (int f = 0; f < 9; ++f) {
+        const R vm = pin_field(me, f), vo = pin_field(oth, f), d = vo - vm;
+        const R sm = Gm[3 * f] * e0 + Gm[3 * f + 1] * e1 + Gm[3 * f + 2] * e2;
+        const R so = Go[3 * f] * e0 + Go[3 * f + 1] * e1 + Go[3 * f + 2] * e2;
+        set_field(mes, f, vm + R(0.5) * minmod(sm, d));
+        set_field(oths, f, vo - R(0.5) * minmod(so, d));
+    }
 }
 
 // Per-particle sums. FP32: compensated for the conserved quantities (fields 0-5: volume, mass,
@@ -227,7 +290,7 @@ template <> struct Acc<double> {
 
 // Adds one pair to the sums of particle i. sg = -1 when i is the left state (n points from i to j),
 // +1 when i is the right state; oth = the other particle's state.
-template <class R>
+template <class R, bool WITH_L = true>
 __device__ __forceinline__ void accumulate(Acc<R> &acc, const PairRes<R> &o, R sg, const PIn<R> &me,
                                            const PIn<R> &oth) {
     // sg (w2a X) = (sg w2a) X exactly: the fluxes' scale and orientation in one factor
@@ -238,6 +301,7 @@ __device__ __forceinline__ void accumulate(Acc<R> &acc, const PairRes<R> &o, R s
     acc.add(3, sgw * o.Xv[1]);
     acc.add(4, sgw * o.Xv[2]);
     acc.add(5, (R(0.5) * sgw) * o.Xe);
+    if (!WITH_L) return;
     // L_i += w_j (v_j - v_i) (x) a n_ij, n_ij = -sg n
     R an = -sg * o.a * oth.w;
     R g0 = an * o.n[0], g1 = an * o.n[1], g2 = an * o.n[2];
@@ -252,6 +316,7 @@ struct Types {
     using R = typename std::conditional<SPLIT, float, double>::type;
     using Pos = typename std::conditional<SPLIT, float4, D4>::type;
     using Rec = typename std::conditional<SPLIT, RecF, RecD>::type;
+    using G4 = typename std::conditional<SPLIT, float4, D4>::type;   // 7 per particle: the gradient record
 };
 
 // Row window of one search centre: the particles of buckets (bx-1 .. bx+1, Yc, Zc), which are
@@ -493,7 +558,10 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
 //   PM_HEUN2    all pairs of the predicted state, whose records the refresh rebuilt, over the lists of the
 //               step's start (the re-scan paths decide membership on the step-start FP64 positions);
 //               y_{n+1} = (y_n + E(y*)) / 2 on the conserved variables, then the time step.
-enum { PM_ALL = 0, PM_LOCAL = 1, PM_BOUNDARY = 2, PM_HEUN1 = 3, PM_HEUN2 = 4 };
+//   PM_GRAD     MUSCL gradient pass: the SPH gradients of v and sigma over all pairs into the gradient
+//               record (no integration).
+//   PM_MUSCL    all pairs with MUSCL-reconstructed Riemann states, then the integration.
+enum { PM_ALL = 0, PM_LOCAL = 1, PM_BOUNDARY = 2, PM_HEUN1 = 3, PM_HEUN2 = 4, PM_GRAD = 5, PM_MUSCL = 6 };
 
 template <bool SPLIT>
 struct PairArgs {
@@ -530,6 +598,8 @@ struct PairArgs {
     const float *hcx;
     void *part;                  // parked partial sums by halo index: field f at f * n + h
     int32_t *part_cnt;           // parked real and image neighbour counts: 2 * h, 2 * h + 1
+    // MUSCL only: gradient records, 7 G4 per slot (written by PM_GRAD, read by PM_MUSCL)
+    typename Types<SPLIT>::G4 *grad;
 };
 
 template <bool SPLIT, bool DIAG, int MODE>
@@ -537,6 +607,8 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
     using R = typename Types<SPLIT>::R;
     using Pos = typename Types<SPLIT>::Pos;
     using Rec = typename Types<SPLIT>::Rec;
+    using G4 = typename Types<SPLIT>::G4;
+    constexpr bool GRAD = MODE == PM_GRAD, RECON = MODE == PM_MUSCL;
     const DevParams &P = a.P;
     const int64_t n = a.n;
     const Pos *__restrict__ pos = a.pos;
@@ -563,7 +635,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
     const R kdwh = SPLIT ? (R)(P.f_kdw * P.f_inv_h) : (R)(P.kdw / P.h);
     const R fcell = SPLIT ? (R)P.f_cell : (R)P.cell;
     // label filter of the two-pass order: PM_LOCAL takes neighbours of the own label, PM_BOUNDARY the others
-    constexpr bool ALLPAIRS = MODE == PM_ALL || MODE == PM_HEUN1 || MODE == PM_HEUN2;
+    constexpr bool ALLPAIRS = MODE == PM_ALL || MODE == PM_HEUN1 || MODE == PM_HEUN2 || GRAD || RECON;
     const uint32_t mylab = (!ALLPAIRS && valid) ? a.lab_s[s] : 0u;
     auto take = [&](uint32_t j) -> bool {
         if (ALLPAIRS) return true;
@@ -572,6 +644,61 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
     };
     Acc<R> acc;
     acc.zero();
+    // MUSCL: gradient sums (PM_GRAD), or the own gradient record staged in shared memory (PM_MUSCL)
+    R gs[kNGrad];
+#pragma unroll
+    for (int k = 0; k < kNGrad; ++k) gs[k] = R(0);
+    G4 *gme = nullptr;
+    if constexpr (RECON) {
+        __shared__ G4 gsh[7 * PK_THREADS];
+        gme = gsh + threadIdx.x;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) gme[q * PK_THREADS] = valid ? a.grad[(size_t)s * 7 + q] : G4{};
+    }
+    auto load_grad = [&](const G4 *src, int stride, R *G) {
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            const G4 g = src[q * stride];
+            G[4 * q] = g.x;
+            if (4 * q + 1 < kNGrad) G[4 * q + 1] = g.y;
+            if (4 * q + 2 < kNGrad) G[4 * q + 2] = g.z;
+            if (4 * q + 3 < kNGrad) G[4 * q + 3] = g.w;
+        }
+    };
+    // one pair's work from the raw difference e (this end's x_oth - x_me) and the neighbour's state:
+    // gradient sums, or the (reconstructed) fluxes. jg: the neighbour's slot for its gradient record,
+    // wax >= 0 for a wall image (mirrored state and gradient; me is the left state)
+    auto pair_work = [&](R e0, R e1, R e2, const PIn<R> &oth, R sgn, R kw, uint32_t jg, int wax) {
+        if constexpr (GRAD) {
+            const R r2 = e0 * e0 + e1 * e1 + e2 * e2;
+            const R inv_r = rsqrt_r(r2);
+            const R r = r2 * inv_r;
+            R sq = R(1) - inv_2h * r;
+            const R c = kw * r * sq * sq * sq * oth.w * inv_r;   // w_j |dW/dr| / r
+            const R g0 = c * e0, g1 = c * e1, g2 = c * e2;       // w_j grad_i W_ij
+#pragma unroll
+            for (int f = 0; f < 9; ++f) {
+                const R d = pin_field(oth, f) - pin_field(me, f);
+                gs[3 * f] += d * g0;
+                gs[3 * f + 1] += d * g1;
+                gs[3 * f + 2] += d * g2;
+            }
+        } else if constexpr (RECON) {
+            R Gm[kNGrad], Go[kNGrad];
+            load_grad(gme, PK_THREADS, Gm);
+            load_grad(a.grad + (size_t)jg * 7, 1, Go);
+            if (wax >= 0) mirror_grad(Go, wax);
+            PIn<R> mes, oths;
+            reconstruct(me, Gm, oth, Go, e0, e1, e2, mes, oths);
+            PairRes<R> o;
+            pair_terms<R, false, true>(e0, e1, e2, mes, oths, sgn, inv_2h, kw, o, me, oth);
+            accumulate<R, false>(acc, o, -sgn, me, oth);
+        } else {
+            PairRes<R> o;
+            pair_terms<R, MODE == PM_HEUN2>(e0, e1, e2, me, oth, sgn, inv_2h, kw, o, me, oth);
+            accumulate<R>(acc, o, -sgn, me, oth);
+        }
+    };
     int nr0 = 0, ni0 = 0;
     if (MODE == PM_BOUNDARY && valid) {   // the partial sums of the first pass
         const R *pr = (const R *)a.part;
@@ -605,9 +732,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
             d0 = (R)pj.x - mrx; d1 = (R)pj.y - mry; d2 = (R)pj.z - mrz;
         }
         if (!act) d0 = fcell;
-        PairRes<R> o;
-        pair_terms<R, MODE == PM_HEUN2>(d0, d1, d2, me, oth, sgn, inv_2h, act ? kdwh : R(0), o);
-        accumulate<R>(acc, o, -sgn, me, oth);
+        pair_work(d0, d1, d2, oth, sgn, act ? kdwh : R(0), jj, -1);
     };
 
     // ---- listed real neighbours, all lanes in lockstep: the set bits of the current entry give the
@@ -767,13 +892,26 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
                         d0 = (R)(qx - XF); d1 = (R)(qy - YF); d2 = (R)(qz - ZF);
                     }
                     mirror<R>(oth, wax);
-                    PairRes<R> o;
-                    pair_terms<R, MODE == PM_HEUN2>(d0, d1, d2, me, oth, R(1), inv_2h, kdwh, o);
-                    accumulate<R>(acc, o, R(-1), me, oth);
+                    pair_work(d0, d1, d2, oth, R(1), kdwh, j, wax);
                     ++ni;
                 }
             }
         }
+    }
+    if constexpr (GRAD) {
+        if (valid) {
+            G4 *out = a.grad + (size_t)s * 7;
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                G4 g;
+                g.x = gs[4 * q];
+                g.y = 4 * q + 1 < kNGrad ? gs[4 * q + 1] : R(0);
+                g.z = 4 * q + 2 < kNGrad ? gs[4 * q + 2] : R(0);
+                g.w = 4 * q + 3 < kNGrad ? gs[4 * q + 3] : R(0);
+                out[q] = g;
+            }
+        }
+        return;
     }
     acc.fold();
     const int ntaken = ALLPAIRS ? (int)nlist : nsel;   // listed neighbours summed by this pass
@@ -818,10 +956,19 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         double nvx, nvy, nvz, En, Sn[6];
         double mvx = 0.0, mvy = 0.0, mvz = 0.0, mE = 0.0;
         R Lm[3][3];
+        if constexpr (RECON) {   // the velocity gradient of the gradient record (the same sum)
+            R Gm[kNGrad];
+            load_grad(gme, PK_THREADS, Gm);
 #pragma unroll
-        for (int u = 0; u < 3; ++u)
+            for (int u = 0; u < 3; ++u)
 #pragma unroll
-            for (int v = 0; v < 3; ++v) Lm[u][v] = acc.getr(6 + 3 * u + v);
+                for (int v = 0; v < 3; ++v) Lm[u][v] = Gm[3 * u + v];
+        } else {
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+#pragma unroll
+                for (int v = 0; v < 3; ++v) Lm[u][v] = acc.getr(6 + 3 * u + v);
+        }
         // the stress of the step's start as the record holds it (the FP32 rounding on the split path)
         // (split: the record's sigma plus the pressure its trace gives; FP64: the state's S)
         R Sr[3][3];
@@ -857,8 +1004,8 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         }
         const R Yr = SPLIT ? (R)(float)P.Y[mt] : (R)P.Y[mt];
         if (FAST) {
-            const float dtf = (float)dt, imf = 1.0f / (float)mn, mf = me.rho * me.w, dm = acc.getr(1);
-            float F[3] = {acc.getr(2), acc.getr(3), acc.getr(4)}, dE = acc.getr(5);
+            const float dtf = (float)dt, imf = 1.0f / (float)mn, mf = (float)(me.rho * me.w), dm = (float)acc.getr(1);
+            float F[3] = {(float)acc.getr(2), (float)acc.getr(3), (float)acc.getr(4)}, dE = (float)acc.getr(5);
             if (P.has_gravity) {
                 const float g0 = (float)P.g[0], g1 = (float)P.g[1], g2 = (float)P.g[2];
                 F[0] += mf * g0; F[1] += mf * g1; F[2] += mf * g2;
@@ -966,7 +1113,8 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
             a.nreal_out[s] = nr;
             a.nimage_out[s] = ni;
 #pragma unroll
-            for (int k = 0; k < kNRate; ++k) a.rates_out[(size_t)s * kNRate + k] = acc.get(k);
+            for (int k = 0; k < kNRate; ++k)
+                a.rates_out[(size_t)s * kNRate + k] = (RECON && k >= 6) ? (double)Lm[(k - 6) / 3][(k - 6) % 3] : acc.get(k);
         }
         // next step's CFL signal speed (correctly rounded FP32, reproducible bit for bit)
         if (MODE != PM_HEUN1) sp = signal_speed32(P, mt, mo, wo, nvx, nvy, nvz, En);
@@ -987,7 +1135,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
 }
 
 template <bool SPLIT, bool DIAG, int MODE>
-__global__ void __launch_bounds__(PK_THREADS, SPLIT ? 5 : 2) k_pair(const PairArgs<SPLIT> a) {
+__global__ void __launch_bounds__(PK_THREADS, SPLIT ? (MODE == PM_MUSCL ? 3 : 5) : 2) k_pair(const PairArgs<SPLIT> a) {
     if (MODE == PM_BOUNDARY) {
         // one lane per boundary particle, warp-uniform strides over the boundary list
         const int64_t total = (int64_t)*a.btotal;
@@ -1026,7 +1174,7 @@ static PairArgs<SPLIT> pair_args(const DevParams &P, int64_t n, const uint32_t *
                                  const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s,
                                  const double *dt, unsigned int *sig, unsigned long long *pairs,
                                  unsigned long long *cost, int32_t *nreal, int32_t *nimage, double *rates,
-                                 const OverlapBufs *ov) {
+                                 const OverlapBufs *ov, void *grad) {
     using Pos = typename Types<SPLIT>::Pos;
     using Rec = typename Types<SPLIT>::Rec;
     PairArgs<SPLIT> a;
@@ -1043,6 +1191,7 @@ static PairArgs<SPLIT> pair_args(const DevParams &P, int64_t n, const uint32_t *
     a.hcx = ov ? ov->hcx : nullptr;
     a.part = ov ? ov->part : nullptr;
     a.part_cnt = ov ? ov->part_cnt : nullptr;
+    a.grad = (typename Types<SPLIT>::G4 *)grad;
     return a;
 }
 
@@ -1053,13 +1202,13 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
                             unsigned int *sig, unsigned long long *pairs, unsigned long long *cost,
                             int32_t *nreal, int32_t *nimage, double *rates, const OverlapBufs *ov,
-                            int stage, cudaStream_t s) {
+                            int stage, void *grad, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const unsigned gl = (unsigned)((n + NL_THREADS - 1) / NL_THREADS);
     const unsigned gp = (unsigned)((n + PK_THREADS - 1) / PK_THREADS);
 #define GSPH_NL_ARGS P, n, skey, cellr, (const typename Types<SP>::Pos *)pos, cxs, xs, ys, zs, kmax, list, cnt
 #define GSPH_PAIR_ARGS pair_args<SP>(P, n, skey, cellr, pos, rec, cxs, xs, ys, zs, kmax, list, cnt, perm, A, B, \
-                                     lab_s, mat_s, id_s, dt, sig, pairs, cost, nreal, nimage, rates, ov)
+                                     lab_s, mat_s, id_s, dt, sig, pairs, cost, nreal, nimage, rates, ov, grad)
 #define GSPH_PAIRS(MODE_)                                                                   \
     do {                                                                                    \
         const auto pa = GSPH_PAIR_ARGS;                                                      \
@@ -1075,6 +1224,10 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
             GSPH_PAIRS(PM_HEUN1);                                                           \
         } else if (stage == 2) {                                                            \
             GSPH_PAIRS(PM_HEUN2);                                                           \
+        } else if (grad) {                                                                  \
+            /* MUSCL: the gradient pass, then the reconstructed fluxes */                  \
+            k_pair<SP, false, PM_GRAD><<<gp, PK_THREADS, 0, s>>>(GSPH_PAIR_ARGS);           \
+            GSPH_PAIRS(PM_MUSCL);                                                           \
         } else if (!ov) {                                                                   \
             GSPH_PAIRS(PM_ALL);                                                             \
         } else {                                                                            \

@@ -56,7 +56,8 @@ class Config(C.Structure):
                 ("n_walls", C.c_int32), ("K", C.c_int32), ("walls", Wall * MAX_WALL),
                 ("gravity", C.c_double * 3), ("alpha", C.c_double), ("swap_period", C.c_int32),
                 ("precision", C.c_int32), ("device", C.c_int32), ("diagnostics", C.c_int32),
-                ("overlap", C.c_int32), ("integrator", C.c_int32)]
+                ("overlap", C.c_int32), ("integrator", C.c_int32), ("reconstruction", C.c_int32),
+                ("pad2", C.c_int32)]
 
 
 class ExchangeStats(C.Structure):
@@ -163,6 +164,7 @@ def config_from_scene(scene, precision: int = FP32_SPLIT, device: int = 0, diagn
     c.diagnostics = int(diagnostics)
     c.overlap = int(overlap)
     c.integrator = int(getattr(scene, "integrator", 0) or 0)
+    c.reconstruction = int(getattr(scene, "reconstruction", 0) or 0)
     return c
 
 
