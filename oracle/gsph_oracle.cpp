@@ -192,6 +192,7 @@ template <class T> struct StateT {
     std::vector<T> x, y, z, vx, vy, vz, w, m, E, S[6];
     std::vector<uint8_t> mat, label;
     std::vector<uint32_t> id;
+    std::vector<double> hh;   // per-particle smoothing lengths (variable h), empty otherwise
     void resize(int64_t nn) {
         n = nn;
         for (auto *v : {&x, &y, &z, &vx, &vy, &vz, &w, &m, &E}) v->assign(nn, T(0.0));
@@ -213,6 +214,7 @@ StateT<double> load(const orc_state *S) {
         s.S[3][i] = S->sxy[i]; s.S[4][i] = S->sxz[i]; s.S[5][i] = S->syz[i];
         s.mat[i] = S->mat[i]; s.label[i] = S->label[i]; s.id[i] = S->id[i];
     }
+    if (S->h) s.hh.assign(S->h, S->h + S->n);
     return s;
 }
 
@@ -225,6 +227,7 @@ template <class T> void store(const StateT<T> &s, orc_state *S) {
         S->sxy[i] = val(s.S[3][i]); S->sxz[i] = val(s.S[4][i]); S->syz[i] = val(s.S[5][i]);
         S->mat[i] = s.mat[i]; S->label[i] = s.label[i]; S->id[i] = s.id[i];
     }
+    if (S->h && (int64_t)s.hh.size() == s.n) std::copy(s.hh.begin(), s.hh.end(), S->h);
 }
 
 inline int64_t ncells(const orc_params *P) {
@@ -310,18 +313,25 @@ void for_27(const orc_params *P, const Buckets &b, int64_t cx, int64_t cy, int64
 // image(k, j) for each image of particle j in wall k within the support.
 template <class FR, class FI>
 void neighbours_of(const orc_params *P, const Buckets &b, int64_t n, const double *x, const double *y,
-                   const double *z, const uint32_t *key, int64_t i, FR &&real, FI &&image) {
+                   const double *z, const uint32_t *key, int64_t i, FR &&real, FI &&image,
+                   const double *hv = nullptr) {
     int64_t C = ncells(P);
     if (key[i] >= (uint64_t)C) return;
     double cell = 2.0 * P->h;
-    double R2 = cell * cell;
+    double R2u = cell * cell;
+    // support of the pair: (2h)^2, or (h_i + h_j)^2 with per-particle smoothing lengths
+    auto R2of = [&](int64_t j) {
+        if (!hv) return R2u;
+        double sij = hv[i] + hv[j];
+        return sij * sij;
+    };
     double xi[3] = {x[i], y[i], z[i]};
     int64_t ci[3];
     for (int a = 0; a < 3; ++a) ci[a] = bucket_coord(xi[a], P->lo[a], cell, P->dims[a]);
     for_27(P, b, ci[0], ci[1], ci[2], [&](int64_t j) {
         if (j == i) return;
         double r2 = dist2(x[j] - xi[0], y[j] - xi[1], z[j] - xi[2]);
-        if (r2 < R2) real(j);
+        if (r2 < R2of(j)) real(j);
     });
     for (int k = 0; k < P->nwalls; ++k) {
         const orc_wall &W = P->wall[k];
@@ -332,7 +342,7 @@ void neighbours_of(const orc_params *P, const Buckets &b, int64_t n, const doubl
         for_27(P, b, cm[0], cm[1], cm[2], [&](int64_t j) {
             double xj[3] = {x[j], y[j], z[j]}, d[3];
             image_delta(W, xi, xj, d);
-            if (dist2(d[0], d[1], d[2]) < R2) image(k, j);
+            if (dist2(d[0], d[1], d[2]) < R2of(j)) image(k, j);
         });
     }
     (void)n;
@@ -417,13 +427,14 @@ void grads_of(const orc_params *P, const StateT<T> &s, const Mat<T> *mats, const
               const std::vector<double> &xv, const std::vector<double> &yv, const std::vector<double> &zv,
               const std::vector<uint32_t> &key, int64_t i, T *G) {
     for (int k = 0; k < NGRAD; ++k) G[k] = T(0.0);
+    const double *hv = P->variable_h ? s.hh.data() : nullptr;
     Prim<T> pi = prim_of(s, mats, i);
     T si[6];
     sigma_of(pi, si);
     T xi[3] = {s.x[i], s.y[i], s.z[i]};
-    auto add = [&](const Prim<T> &pj, const T d[3]) {
+    auto add = [&](const Prim<T> &pj, const T d[3], int64_t j) {
         T r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        T a = kernel_dw_abs(r, P->h);
+        T a = kernel_dw_abs(r, hv ? 0.5 * (hv[i] + hv[j]) : P->h);
         T gw[3] = {a * d[0] / r, a * d[1] / r, a * d[2] / r};
         T sj[6];
         sigma_of(pj, sj);
@@ -436,15 +447,16 @@ void grads_of(const orc_params *P, const StateT<T> &s, const Mat<T> *mats, const
         P, b, s.n, xv.data(), yv.data(), zv.data(), key.data(), i,
         [&](int64_t j) {
             T d[3] = {s.x[j] - xi[0], s.y[j] - xi[1], s.z[j] - xi[2]};
-            add(prim_of(s, mats, j), d);
+            add(prim_of(s, mats, j), d, j);
         },
         [&](int k, int64_t j) {
             const orc_wall &W = P->wall[k];
             T xj[3] = {s.x[j], s.y[j], s.z[j]};
             xj[W.axis] = T(2.0 * W.pos) - xj[W.axis];
             T d[3] = {xj[0] - xi[0], xj[1] - xi[1], xj[2] - xi[2]};
-            add(mirror_prim(prim_of(s, mats, j), W.axis), d);
-        });
+            add(mirror_prim(prim_of(s, mats, j), W.axis), d, j);
+        },
+        hv);
 }
 
 // Interface states of the pair (L, R), d = x_R - x_L: v and sigma reconstructed (the stress of the
@@ -482,6 +494,8 @@ void rates_of(const orc_params *P, const StateT<T> &s, const Mat<T> *mats, const
     int32_t cr = 0, ci = 0;
     Prim<T> pi = prim_of(s, mats, i);
     T xi[3] = {s.x[i], s.y[i], s.z[i]};
+    const double *hv = P->variable_h ? s.hh.data() : nullptr;
+    auto hij = [&](int64_t j) { return hv ? 0.5 * (hv[i] + hv[j]) : P->h; };   // pair smoothing length
     auto add_L = [&](const T wj, const T vj[3], const T a, const T nij[3]) {
         // L_i += w_j (v_j - v_i) (x) grad_i W_ij, grad_i W_ij = a n_{i->j}
         for (int u = 0; u < 3; ++u)
@@ -502,9 +516,9 @@ void rates_of(const orc_params *P, const StateT<T> &s, const Mat<T> *mats, const
             if (grads) {
                 Prim<T> Ls, Rs;
                 reconstruct(PL, grads + NGRAD * l, PR, grads + NGRAD * rr, d, Ls, Rs);
-                pair_flux(d, Ls, Rs, P->h, o, &PL, &PR);
+                pair_flux(d, Ls, Rs, hij(j), o, &PL, &PR);
             } else {
-                pair_flux(d, PL, PR, P->h, o);
+                pair_flux(d, PL, PR, hij(j), o);
             }
             double sg = i_left ? -1.0 : 1.0;
             r[0] = r[0] + pi.w * pj.w * o.a * (o.uR - o.uL);
@@ -528,16 +542,17 @@ void rates_of(const orc_params *P, const StateT<T> &s, const Mat<T> *mats, const
                 mirror_grad(grads + NGRAD * j, W.axis, Gm);
                 Prim<T> Ls, Rs;
                 reconstruct(pi, grads + NGRAD * i, pj, Gm, d, Ls, Rs);
-                pair_flux(d, Ls, Rs, P->h, o, &pi, &pj);
+                pair_flux(d, Ls, Rs, hij(j), o, &pi, &pj);
             } else {
-                pair_flux(d, pi, pj, P->h, o);
+                pair_flux(d, pi, pj, hij(j), o);
             }
             r[0] = r[0] + pi.w * pj.w * o.a * (o.uR - o.uL);
             r[1] = r[1] - o.Fm;
             for (int q = 0; q < 3; ++q) r[2 + q] = r[2 + q] - o.Fmv[q];
             r[5] = r[5] - o.Fe;
             add_L(pj.w, pj.v, o.a, o.n);
-        });
+        },
+        hv);
     if (nreal) nreal[i] = cr;
     if (nimage) nimage[i] = ci;
 }
@@ -762,19 +777,20 @@ void orc_cell_ranges(int64_t n, const uint32_t *sorted_key, int64_t ncell, int64
 }
 
 int64_t orc_neighbours_brute(const orc_params *P, int64_t n, const double *x, const double *y,
-                             const double *z, int64_t cap, int32_t *count, int64_t *list) {
+                             const double *z, int64_t cap, int32_t *count, int64_t *list, const double *h) {
     std::vector<uint32_t> key(n);
     orc_hash(P, n, x, y, z, key.data());
     uint32_t G = (uint32_t)ncells(P);
-    double cell = 2.0 * P->h, R2 = cell * cell;
+    double cell = 2.0 * P->h, R2u = cell * cell;
     int64_t mx = 0;
     for (int64_t i = 0; i < n; ++i) {
         int64_t c = 0;
         if (key[i] != G) {
             double xi[3] = {x[i], y[i], z[i]};
+            auto R2of = [&](int64_t j) { double sij = h ? h[i] + h[j] : 0.0; return h ? sij * sij : R2u; };
             for (int64_t j = 0; j < n; ++j) {
                 if (j == i || key[j] == G) continue;
-                if (dist2(x[j] - xi[0], y[j] - xi[1], z[j] - xi[2]) < R2) {
+                if (dist2(x[j] - xi[0], y[j] - xi[1], z[j] - xi[2]) < R2of(j)) {
                     if (c < cap) list[i * cap + c] = j;
                     ++c;
                 }
@@ -784,7 +800,7 @@ int64_t orc_neighbours_brute(const orc_params *P, int64_t n, const double *x, co
                     if (key[j] == G) continue;
                     double xj[3] = {x[j], y[j], z[j]}, d[3];
                     image_delta(P->wall[k], xi, xj, d);
-                    if (dist2(d[0], d[1], d[2]) < R2) {
+                    if (dist2(d[0], d[1], d[2]) < R2of(j)) {
                         if (c < cap) list[i * cap + c] = j + n * (1 + k);
                         ++c;
                     }
@@ -797,7 +813,7 @@ int64_t orc_neighbours_brute(const orc_params *P, int64_t n, const double *x, co
 }
 
 int64_t orc_neighbours_cells(const orc_params *P, int64_t n, const double *x, const double *y,
-                             const double *z, int64_t cap, int32_t *count, int64_t *list) {
+                             const double *z, int64_t cap, int32_t *count, int64_t *list, const double *h) {
     std::vector<uint32_t> key(n);
     orc_hash(P, n, x, y, z, key.data());
     Buckets b = make_buckets(P, n, key.data());
@@ -807,7 +823,7 @@ int64_t orc_neighbours_cells(const orc_params *P, int64_t n, const double *x, co
         neighbours_of(
             P, b, n, x, y, z, key.data(), i,
             [&](int64_t j) { if (c < cap) list[i * cap + c] = j; ++c; },
-            [&](int k, int64_t j) { if (c < cap) list[i * cap + c] = j + n * (1 + k); ++c; });
+            [&](int k, int64_t j) { if (c < cap) list[i * cap + c] = j + n * (1 + k); ++c; }, h);
         count[i] = (int32_t)c;
         mx = std::max(mx, c);
     }
@@ -824,6 +840,10 @@ void orc_rates(const orc_params *P, const orc_state *S, int64_t nsub, const int6
 
 double orc_dt(const orc_params *P, const orc_state *S) {
     float mx = 0.0f;
+    if (P->variable_h) {   // dt = cfl min_i h_i / s_i, from the FP32 quotients s_i / h_i
+        for (int64_t i = 0; i < S->n; ++i) mx = std::max(mx, signal_speed(P, S, i) / (float)S->h[i]);
+        return P->cfl / (double)mx;
+    }
     for (int64_t i = 0; i < S->n; ++i) mx = std::max(mx, signal_speed(P, S, i));
     return (P->cfl * P->h) / (double)mx;
 }
@@ -998,6 +1018,10 @@ void orc_step(const orc_params *P, orc_state *S, int32_t do_swap, uint32_t *key_
         s.mat[t] = old.mat[o]; s.label[t] = old.label[o]; s.id[t] = old.id[o];
         skey[t] = key[o];
     }
+    if (!old.hh.empty()) {
+        s.hh.resize(n);
+        for (int64_t t = 0; t < n; ++t) s.hh[t] = old.hh[perm[t]];
+    }
     std::vector<double> xv(s.x), yv(s.y), zv(s.z);
     if (do_swap) {
         std::vector<int64_t> sw(P->K * P->K);
@@ -1092,6 +1116,7 @@ double orc_forward_gradient(const orc_params *P, orc_state *S, int32_t nsteps, c
         for (int k = 0; k < 6; ++k) s.S[k][i] = d.S[k][i];
         s.mat[i] = d.mat[i]; s.label[i] = d.label[i]; s.id[i] = d.id[i];
     }
+    s.hh = d.hh;
     Mat<Dual> mats[ORC_MAX_MAT];
     mats_of(P, mats);
     mats[0].Y.d[0] = 1.0;

@@ -59,7 +59,13 @@ typedef struct {
     int32_t reconstruction;          /* 0: first-order Riemann states (the particle values); 1: MUSCL,
                                         minmod-limited linear reconstruction of v and sigma at the pair
                                         midpoint from SPH gradients */
-    int32_t pad3;
+    int32_t variable_h;              /* 0: uniform h; 1: per-particle smoothing lengths h_i (orc_state.h,
+                                        0 < h_i <= h, constant in time; Sec. V's varying particle sizes,
+                                        reading): pair smoothing length h_ij = (h_i + h_j) / 2, support
+                                        r_ij < 2 h_ij, i.e. r^2 < (h_i + h_j)^2 each operation rounded;
+                                        buckets keep the side 2h (h = the largest h_i); time step
+                                        dt = cfl / max_i fl32(s_i / fl32(h_i)) with s_i the FP32 signal
+                                        speed */
 } orc_params;
 
 typedef struct {
@@ -69,6 +75,7 @@ typedef struct {
     double *sxx, *syy, *szz, *sxy, *sxz, *syz;
     uint8_t *mat, *label;
     uint32_t *id;                    /* persistent particle id */
+    double *h;                       /* per-particle smoothing length (variable_h = 1), else unused */
 } orc_state;
 
 /* Sec. I: bucket hash of each particle; GARBAGE = dims product for particles outside the grid. */
@@ -83,10 +90,11 @@ void orc_cell_ranges(int64_t n, const uint32_t *sorted_key, int64_t ncell, int64
  * search. Lists hold slot indices; image (wall) neighbours are encoded as j + n*(1 + wall index).
  * count[i] real + image neighbours; lists are truncated at cap entries per particle.
  * Returns the largest count seen. */
+/* h: per-particle smoothing lengths (support (h_i + h_j)^2), or null for the uniform 2h. */
 int64_t orc_neighbours_brute(const orc_params *P, int64_t n, const double *x, const double *y,
-                             const double *z, int64_t cap, int32_t *count, int64_t *list);
+                             const double *z, int64_t cap, int32_t *count, int64_t *list, const double *h);
 int64_t orc_neighbours_cells(const orc_params *P, int64_t n, const double *x, const double *y,
-                             const double *z, int64_t cap, int32_t *count, int64_t *list);
+                             const double *z, int64_t cap, int32_t *count, int64_t *list, const double *h);
 
 /* Sec. II step f (interaction loop): per-particle rates (15 per particle, see above) and counts of
  * real and image neighbours. Particles are found with the 27-bucket search. If subset is non-null,

@@ -52,7 +52,7 @@ class Params(C.Structure):
                 ("h", C.c_double), ("cfl", C.c_double), ("mat", Material * MAX_MAT),
                 ("nwalls", C.c_int32), ("K", C.c_int32), ("wall", Wall * MAX_WALL),
                 ("g", C.c_double * 3), ("alpha", C.c_double), ("integrator", C.c_int32), ("pad2", C.c_int32),
-                ("reconstruction", C.c_int32), ("pad3", C.c_int32)]
+                ("reconstruction", C.c_int32), ("variable_h", C.c_int32)]
 
 
 _DP = C.POINTER(C.c_double)
@@ -64,7 +64,7 @@ class StateC(C.Structure):
     _fields_ = ([("n", C.c_int64)] +
                 [(f, _DP) for f in ("x", "y", "z", "vx", "vy", "vz", "w", "m", "E",
                                     "sxx", "syy", "szz", "sxy", "sxz", "syz")] +
-                [("mat", _U8P), ("label", _U8P), ("id", _U32P)])
+                [("mat", _U8P), ("label", _U8P), ("id", _U32P), ("h", _DP)])
 
 
 def lib():
@@ -77,7 +77,7 @@ def lib():
             L.orc_sort_order.argtypes = [C.c_int64, _U32P, P(C.c_int64)]
             L.orc_cell_ranges.argtypes = [C.c_int64, _U32P, C.c_int64, P(C.c_int64), P(C.c_int64)]
             for f in (L.orc_neighbours_brute, L.orc_neighbours_cells):
-                f.argtypes = [P(Params), C.c_int64, _DP, _DP, _DP, C.c_int64, P(C.c_int32), P(C.c_int64)]
+                f.argtypes = [P(Params), C.c_int64, _DP, _DP, _DP, C.c_int64, P(C.c_int32), P(C.c_int64), _DP]
                 f.restype = C.c_int64
             L.orc_rates.argtypes = [P(Params), P(StateC), C.c_int64, P(C.c_int64), _DP, P(C.c_int32),
                                     P(C.c_int32)]
@@ -139,6 +139,7 @@ def params_of(scene) -> Params:
     p.cfl = scene.cfl
     p.integrator = int(getattr(scene, "integrator", 0) or 0)
     p.reconstruction = int(getattr(scene, "reconstruction", 0) or 0)
+    p.variable_h = int(getattr(scene, "variable_h", 0) or 0)
     p.nwalls = len(scene.walls)
     for k, (axis, pos) in enumerate(scene.walls):
         p.wall[k] = Wall(axis, 0, pos)
@@ -160,6 +161,7 @@ class OracleState:
         self.mat = np.zeros(n, np.uint8)
         self.label = np.zeros(n, np.uint8)
         self.id = np.arange(n, dtype=np.uint32)
+        self.h = None          # per-particle smoothing lengths (variable h), else None
 
     @classmethod
     def from_scene(cls, scene) -> "OracleState":
@@ -172,6 +174,8 @@ class OracleState:
         s.E[:] = 0.5 * ((s.vx * s.vx + s.vy * s.vy) + s.vz * s.vz)
         s.mat[:] = scene.material
         s.label[:] = scene.label
+        if getattr(scene, "variable_h", 0):
+            s.h = np.array(scene.hp, dtype=np.float64)
         return s
 
     @classmethod
@@ -180,10 +184,15 @@ class OracleState:
         s = cls(n)
         for f in FIELDS + ("mat", "label", "id"):
             getattr(s, f)[:] = d[f] if f in d else d["material"]
+        if d.get("h") is not None:
+            s.h = np.array(d["h"], dtype=np.float64)
         return s
 
     def arrays(self) -> dict:
-        return {f: getattr(self, f).copy() for f in FIELDS + ("mat", "label", "id")}
+        d = {f: getattr(self, f).copy() for f in FIELDS + ("mat", "label", "id")}
+        if self.h is not None:
+            d["h"] = self.h.copy()
+        return d
 
     def copy(self) -> "OracleState":
         return OracleState.from_arrays(self.arrays())
@@ -191,6 +200,8 @@ class OracleState:
     def permute(self, perm: np.ndarray) -> None:
         for f in FIELDS + ("mat", "label", "id"):
             setattr(self, f, np.ascontiguousarray(getattr(self, f)[perm]))
+        if self.h is not None:
+            self.h = np.ascontiguousarray(self.h[perm])
 
     def cstruct(self) -> StateC:
         for f in FIELDS:
@@ -202,6 +213,9 @@ class OracleState:
         c.mat = _ptr(self.mat, C.c_uint8)
         c.label = _ptr(self.label, C.c_uint8)
         c.id = _ptr(self.id, C.c_uint32)
+        if self.h is not None:
+            self.h = np.ascontiguousarray(self.h, dtype=np.float64)
+            c.h = _ptr(self.h, C.c_double)
         return c
 
 
@@ -236,15 +250,17 @@ def cell_ranges(sorted_key: np.ndarray, ncell: int):
     return st, en
 
 
-def neighbours(P: Params, x, y, z, cap: int = 256, brute: bool = False):
-    """Neighbour lists (each row sorted) and counts; image neighbours encoded as j + n (1 + wall)."""
+def neighbours(P: Params, x, y, z, cap: int = 256, brute: bool = False, h=None):
+    """Neighbour lists (each row sorted) and counts; image neighbours encoded as j + n (1 + wall).
+    h: per-particle smoothing lengths (support (h_i + h_j)^2), or None for the uniform 2h."""
     x, y, z = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z))
+    hp = None if h is None else np.ascontiguousarray(h, dtype=np.float64)
     n = len(x)
     cnt = np.zeros(n, np.int32)
     lst = np.full((n, cap), -1, np.int64)
     f = lib().orc_neighbours_brute if brute else lib().orc_neighbours_cells
     mx = f(C.byref(P), n, _ptr(x, C.c_double), _ptr(y, C.c_double), _ptr(z, C.c_double), cap,
-           _ptr(cnt, C.c_int32), _ptr(lst, C.c_int64))
+           _ptr(cnt, C.c_int32), _ptr(lst, C.c_int64), None if hp is None else _ptr(hp, C.c_double))
     if mx > cap:
         raise ValueError(f"neighbour cap {cap} exceeded ({mx})")
     return cnt, lst

@@ -83,6 +83,8 @@ class Scene:
     dx: float
     eos: list = None           # per material: None (linear, K) or (c0, s, gamma0) Mie-Gruneisen
     p_min: list = None         # per material: pressure cut-off (Pa, <= 0) or None
+    hp: np.ndarray = None      # (N,) per-particle smoothing lengths (variable_h = 1); h is their maximum
+    variable_h: int = 0
 
     @property
     def n(self) -> int:
@@ -132,6 +134,64 @@ def cube_impact(n_side: int = 16, dx: float = 1.0e-3, seed: int = 0, speed: floa
     label = _random_labels(ids, seed, K) if K > 1 else np.zeros(n, np.uint8)
     return Scene("cube_impact", pos, vel, np.full(n, dx ** 3), np.zeros(n, np.uint8), label,
                  [ALUMINIUM], h, 0.3, lo, dims, [(2, 0.0)], (0.0, 0.0, 0.0), K, 1, 0.1, steps, dx)
+
+
+def _graded(fine_xy, nz_fine, nz_coarse, dx, origin_xy, seed, jitter, keep=None):
+    """Two-resolution lattice along z: spacing dx for z < nz_fine dx, 2 dx above; h_i = 1.3 spacing."""
+    nxf, nyf = fine_xy
+    pf = _lattice(nxf, nyf, nz_fine, dx, origin=(origin_xy[0], origin_xy[1], 0.0))
+    pc = _lattice(nxf // 2, nyf // 2, nz_coarse, 2 * dx, origin=(origin_xy[0], origin_xy[1], nz_fine * dx))
+    if keep is not None:
+        pf, pc = pf[keep(pf)], pc[keep(pc)]
+    pos = np.concatenate([pf, pc])
+    spacing = np.concatenate([np.full(len(pf), dx), np.full(len(pc), 2 * dx)])
+    ids = np.arange(pos.shape[0], dtype=np.uint64)
+    if jitter:
+        pos = pos + (_jitter(pos, ids, seed, 1.0) - pos) * (jitter * spacing)[:, None]
+    return pos, spacing, ids
+
+
+def graded_block(n_side: int = 8, nz_fine: int = 8, nz_coarse: int = 4, dx: float = 1.0e-3, seed: int = 0,
+                 speed: float = 100.0, jitter: float = 0.01, K: int = 1, wall: bool = True) -> Scene:
+    """Aluminium block of two particle sizes (Sec. V's varying particle sizes): an n_side^2 x nz_fine
+    layer of spacing dx on the rigid wall z = 0, under an (n_side/2)^2 x nz_coarse layer of spacing 2 dx,
+    h_i = 1.3 x the particle's spacing, falling at `speed`."""
+    pos, spacing, ids = _graded((n_side, n_side), nz_fine, nz_coarse, dx, (0.0, 0.0), seed, jitter)
+    n = pos.shape[0]
+    hp = 1.3 * spacing
+    h = float(hp.max())
+    vel = np.zeros((n, 3))
+    vel[:, 2] = -speed
+    lo, dims = _grid_around(pos, h, (4 * h, 4 * h, 4 * h), (4 * h, 4 * h, 4 * h))
+    label = _random_labels(ids, seed, K) if K > 1 else np.zeros(n, np.uint8)
+    sc = Scene("graded_block", pos, vel, spacing ** 3, np.zeros(n, np.uint8), label, [ALUMINIUM], h, 0.3, lo,
+               dims, [(2, 0.0)] if wall else [], (0.0, 0.0, 0.0), K, 1, 0.1, 10, dx)
+    sc.hp = hp
+    sc.variable_h = 1
+    return sc
+
+
+def graded_bar(dx: float = 0.125e-3, radius: float = 5.0e-3, fine: float = 10.0e-3, length: float = 40.0e-3,
+               speed: float = 200.0, seed: int = 1, K: int = 4, swap_period: int = 1, steps: int = 100) -> Scene:
+    """The Taylor bar with two particle sizes: spacing dx over the impact end (z < fine), 2 dx over the
+    rest of the rod, h_i = 1.3 x spacing, random labels."""
+    nr = int(round(radius / dx))
+    nzf = int(round(fine / dx))
+    nzc = int(round((length - fine) / (2 * dx)))
+    keep = lambda p: p[:, 0] ** 2 + p[:, 1] ** 2 <= radius ** 2
+    pos, spacing, ids = _graded((2 * nr, 2 * nr), nzf, nzc, dx, (-nr * dx, -nr * dx), seed, 0.01, keep)
+    n = pos.shape[0]
+    hp = 1.3 * spacing
+    h = float(hp.max())
+    vel = np.zeros((n, 3))
+    vel[:, 2] = -speed
+    m = 4 * h
+    lo, dims = _grid_around(pos, h, (m, m, m), (m, m, m))
+    sc = Scene("graded_bar", pos, vel, spacing ** 3, np.zeros(n, np.uint8), _random_labels(ids, seed, K),
+               [ALUMINIUM], h, 0.3, lo, dims, [(2, 0.0)], (0.0, 0.0, 0.0), K, swap_period, 0.1, steps, dx)
+    sc.hp = hp
+    sc.variable_h = 1
+    return sc
 
 
 def taylor_bar(dx: float = 0.125e-3, radius: float = 5.0e-3, length: float = 40.0e-3,
