@@ -222,6 +222,7 @@ def main():
     ap.add_argument("--hvi-steps", type=int, default=50)
     ap.add_argument("--heun-steps", type=int, default=20)
     ap.add_argument("--muscl-steps", type=int, default=20)
+    ap.add_argument("--varh-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -377,6 +378,33 @@ def main():
              "phase_ms_per_step": {k[:-3]: v / max(tmm["steps"], 1) for k, v in tmm.items()
                                    if k.endswith("_ms") and v > 0}}
 
+    # per-particle smoothing lengths (Sec. V's varying particle sizes): the rod with a fine impact end,
+    # and the cost function per label there
+    s4 = scenes.graded_bar()
+    solv = gsph.Solver.from_scene(s4, device=local, stream=stream)
+    solv.step(3, stream)
+    solv.sync(stream)
+    solv.set_timing(args.varh_steps)
+    torch.cuda.synchronize()
+    v0 = torch.cuda.Event(enable_timing=True)
+    v1 = torch.cuda.Event(enable_timing=True)
+    v0.record(stream)
+    solv.step(args.varh_steps, stream)
+    v1.record(stream)
+    torch.cuda.synchronize()
+    msv = v0.elapsed_time(v1)
+    tmv = solv.timings()
+    stv = solv.exchange_stats()
+    solv.close()
+    varh = {"workload": "graded_bar: the Taylor bar with spacing 0.125 mm over its 10 mm impact end and 0.25 mm "
+                        "over the rest, h_i = 1.3 x spacing, K = 4 random labels",
+            "particles": s4.n, "value": world * s4.n * args.varh_steps / (msv * 1e-3), "unit": "particle-steps/s",
+            "ms_per_step": msv / args.varh_steps, "steps": args.varh_steps,
+            "phase_ms_per_step": {k[:-3]: v / max(tmv["steps"], 1) for k, v in tmv.items()
+                                  if k.endswith("_ms") and v > 0},
+            "cost_per_label": stv["cost"], "cost_imbalance": stv["cost_imbalance"],
+            "pairs_per_particle": float(sum(stv["cost"])) / s4.n}
+
     # the interaction in the order of Sec. II steps d-f (two passes, halo gather on a second stream)
     solo = gsph.Solver.from_scene(s, device=local, stream=stream, overlap=True)
     solo.step(3, stream)
@@ -481,6 +509,7 @@ def main():
         "hvi": hvi,
         "heun": heun,
         "muscl": muscl,
+        "varh": varh,
         "clocks": ck,
         "exchange": {k: st1[k] for k in ("boundary_total", "exchange_fraction", "bytes_boundary_broadcast",
                                          "swapped_last_pass", "swap_passes")},

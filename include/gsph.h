@@ -112,7 +112,13 @@ typedef struct {
                                    energy and impedance keep the particle values, the particle velocities
                                    stay the transport velocities. Euler only: not with integrator = 1 or
                                    overlap = 1, and gsph_adjoint_step refuses it */
-    int32_t pad2;
+    int32_t variable_h;         /* 0: one smoothing length h; 1: per-particle smoothing lengths h_i (Sec. V's
+                                   varying particle sizes, reading), constant in time, set with
+                                   gsph_put_field(GSPH_F_H) after gsph_set_particles (default h_i = h) in
+                                   [h/4, h]: h is the largest. Pair smoothing length h_ij = (h_i + h_j)/2,
+                                   support r_ij < 2 h_ij (r^2 < (h_i + h_j)^2, each operation rounded), the
+                                   kernel W(r, h_ij) in every pair term; buckets keep the side 2h; time step
+                                   dt = cfl / max_i fl32(s_i / fl32(h_i)). Not with overlap = 1 */
 } gsph_config;
 
 typedef enum {
@@ -134,6 +140,7 @@ typedef enum {
     GSPH_F_RATES,        /* FP64 n x 15 rates: dw, dm, d(mv)[3], d(mE), L[9] (diagnostics only) */
     GSPH_F_BOUNDARY,     /* uint32 slots of the MGPU boundary set, label-major, each label in
                             communication-hash order (Sec. II step d); length = boundary_total */
+    GSPH_F_H,            /* FP64 per-particle smoothing length (variable_h = 1 only; settable) */
     GSPH_F_COUNT_
 } gsph_field;
 
@@ -205,8 +212,10 @@ gsph_status gsph_set_particles(gsph_ctx *ctx, int64_t n, const double *pos, cons
                                const double *vol, const uint8_t *material, const uint8_t *label,
                                int32_t on_device, void *stream);
 
-/* Overwrite one state field (GSPH_F_X .. GSPH_F_ID) of the current slot order from src (n values
- * of the field's type). The time step is recomputed before the next step. */
+/* Overwrite one state field (GSPH_F_X .. GSPH_F_ID, or GSPH_F_H with variable_h = 1) of the current
+ * slot order from src (n values of the field's type). The time step is recomputed before the next
+ * step. Errors: INVALID_ARG (null pointers, another field, GSPH_F_H without variable_h or a length
+ * outside [h/4, h]), NOT_READY, CUDA_ERROR. */
 gsph_status gsph_put_field(gsph_ctx *ctx, gsph_field f, const void *src, int32_t on_device,
                            void *stream);
 
@@ -259,7 +268,8 @@ gsph_status gsph_set_dt(gsph_ctx *ctx, double dt, void *stream);
  * gsph_step). lam_prev: device, same layout, receives dJ/dy_n in the current slot order.
  * grad: host, receives this step's direct contributions to dJ/dY and dJ/dG of material 0.
  * Covers the linear EOS without a pressure cut-off (every material GSPH_EOS_LINEAR, p_min = -INFINITY)
- * and first-order Riemann states (reconstruction = 0). Does not advance the state. Errors: INVALID_ARG (null pointers, dt <= 0, wrong context kind or EOS),
+ * with first-order Riemann states and one smoothing length (reconstruction = 0, variable_h = 0). Does not
+ * advance the state. Errors: INVALID_ARG (null pointers, dt <= 0, wrong context kind or EOS),
  * NOT_READY, OOM, CUDA_ERROR. */
 gsph_status gsph_adjoint_step(gsph_ctx *ctx, const double *lam_next, double *lam_prev, double dt,
                               double grad[2], void *stream);

@@ -20,7 +20,7 @@ cudaError_t launch_hash(const DevParams &P, int64_t n, const double *x, const do
 cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint32_t *perm,
                            const State &A, double *xs, double *ys, double *zs, uint8_t *lab_s, uint8_t *mat_s,
                            uint32_t *id_s, uint2 *cellr, float *cxs, void *pos, void *rec, float *xf, float *yf,
-                           float *zf, int *err, cudaStream_t s);
+                           float *zf, double *hs, float *hsf, int *err, cudaStream_t s);
 cudaError_t launch_comm(const DevParams &P, int64_t n, const uint32_t *skey, const uint8_t *lab_s, uint32_t *mask,
                         uint8_t *flag, uint32_t *comm, uint32_t *block_counts, unsigned long long *label_total,
                         uint32_t *blist, uint32_t *hidx, cudaStream_t s);
@@ -39,7 +39,7 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
                             unsigned int *sig, unsigned long long *pairs, unsigned long long *cost,
                             int32_t *nreal, int32_t *nimage, double *rates, const OverlapBufs *ov,
-                            int stage, void *grad, cudaStream_t s);
+                            int stage, void *grad, const double *hs, const float *hsf, cudaStream_t s);
 cudaError_t launch_refresh(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const State &B,
                            void *pos, void *rec, cudaStream_t s);
 // k_swap.cu
@@ -114,6 +114,8 @@ struct gsph_ctx {
     int32_t *nreal = nullptr, *nimage = nullptr;
     double *rates = nullptr;
     void *grad = nullptr;                      // MUSCL gradient records (reconstruction = 1)
+    double *hs = nullptr;                      // variable h: sorted smoothing lengths
+    float *hsf = nullptr;
     void *swap_scratch = nullptr;
     uint16_t *bh = nullptr;
     double *cons_part = nullptr, *cons_out = nullptr;
@@ -161,6 +163,8 @@ static cudaError_t alloc_state(gsph_ctx *c, State &S, int64_t n) {
     cudaError_t e = dalloc(c, &S.mat, (size_t)n);
     if (e == cudaSuccess) e = dalloc(c, &S.label, (size_t)n);
     if (e == cudaSuccess) e = dalloc(c, &S.id, (size_t)n);
+    S.h = nullptr;
+    if (e == cudaSuccess && c->cfg.variable_h) e = dalloc(c, &S.h, (size_t)n);
     return e;
 }
 
@@ -209,6 +213,10 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     A_(dalloc(c, &c->bh, N));
     A_(dalloc(c, &c->cons_part, ((N + 255) / 256 + 1) * 6));
     A_(dalloc(c, &c->cons_out, 6));
+    if (c->cfg.variable_h) {   // sorted smoothing lengths, FP64 and FP32
+        A_(dalloc(c, &c->hs, N));
+        A_(dalloc(c, &c->hsf, N));
+    }
     if (c->cfg.reconstruction) {   // MUSCL gradient records: 7 float4 (split) or 7 D4 per slot
         if (c->split) A_(dalloc(c, (float4 **)&c->grad, N * 7));
         else A_(dalloc(c, (D4 **)&c->grad, N * 7));
@@ -262,6 +270,8 @@ static bool config_ok(const gsph_config *c) {
     if (c->integrator == 1 && c->overlap) return false;   // the two-pass order runs the Euler step only
     if (c->reconstruction != 0 && c->reconstruction != 1) return false;
     if (c->reconstruction == 1 && (c->integrator != 0 || c->overlap != 0)) return false;   // MUSCL: Euler, one pass
+    if (c->variable_h != 0 && c->variable_h != 1) return false;
+    if (c->variable_h == 1 && c->overlap != 0) return false;   // the halo records carry no smoothing length
     if (!(c->alpha >= 0.0 && c->alpha <= 1.0)) return false;
     return true;
 }
@@ -305,6 +315,11 @@ static void fill_params(const gsph_config &c, DevParams &P) {
     P.K_labels = c.K;
     P.f_cell = (float)P.cell;
     P.f_inv_cell = (float)(1.0 / P.cell);
+    P.variable_h = c.variable_h;
+    P.f_vlo = (float)(1.0 - kVarBand);
+    P.f_vhi = (float)(1.0 + kVarBand);
+    P.k5 = 210.0 / PI;
+    P.f_k5 = (float)P.k5;
     if (!std::isnormal(P.f_inv_cell)) P.f_inv_cell = std::nanf("");   // the hash then always divides in FP64
     P.f_inv_h = (float)(1.0 / c.h);
     P.f_kdw = (float)P.kdw;
@@ -358,7 +373,8 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     const bool do_swap = P.K_labels > 1 && c->cfg.swap_period > 0 && (c->step % c->cfg.swap_period) == 0;
     GSPH_CK(cudaMemsetAsync(c->cellr, 0, (size_t)P.ncell * sizeof(uint2), s));
     GSPH_CK(launch_reorder(c->split, P, n, c->skey, c->perm, c->A, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s,
-                           c->cellr, c->cxs, c->pos, c->rec, do_swap ? c->xf : nullptr, c->yf, c->zf, c->err, s));
+                           c->cellr, c->cxs, c->pos, c->rec, do_swap ? c->xf : nullptr, c->yf, c->zf, c->hs, c->hsf,
+                           c->err, s));
     c->launches += 1;
     rec_event(c, PH_REORDER, s);
     // Sec. III: periodic swap heuristic on the sorted view
@@ -385,7 +401,8 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     GSPH_CK(launch_interact(c->split, c->cfg.diagnostics != 0, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs,
                             c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, phase_event(c, PH_LIST),
                             c->lab_s, c->mat_s, c->id_s, c->dt, c->sig, c->pairs, c->cost, c->nreal, c->nimage,
-                            c->rates, c->cfg.overlap ? &ov : nullptr, c->cfg.integrator == 1 ? 1 : 0, c->grad, s));
+                            c->rates, c->cfg.overlap ? &ov : nullptr, c->cfg.integrator == 1 ? 1 : 0, c->grad, c->hs,
+                            c->hsf, s));
     if (c->cfg.overlap) c->launches += 2;   // halo gather, second pair pass
     if (c->cfg.integrator == 1) {
         // second Heun stage: records of the prediction, then its pairs over the same lists and the average
@@ -393,7 +410,7 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
         GSPH_CK(launch_interact(c->split, c->cfg.diagnostics != 0, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs,
                                 c->xs, c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr,
                                 c->lab_s, c->mat_s, c->id_s, c->dt, c->sig, c->pairs, c->cost, c->nreal,
-                                c->nimage, c->rates, nullptr, 2, nullptr, s));
+                                c->nimage, c->rates, nullptr, 2, nullptr, c->hs, c->hsf, s));
         c->launches += 2;
     }
     GSPH_CK(launch_finalize_dt(P, c->sig, c->dt, s));
@@ -421,10 +438,11 @@ static gsph_status enqueue_forward_pieces(gsph_ctx *c, cudaStream_t s) {
     c->perm = alt ? c->val1 : c->val0;
     GSPH_CK(cudaMemsetAsync(c->cellr, 0, (size_t)P.ncell * sizeof(uint2), s));
     GSPH_CK(launch_reorder(c->split, P, n, c->skey, c->perm, c->A, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s,
-                           c->cellr, c->cxs, c->pos, c->rec, nullptr, nullptr, nullptr, c->err, s));
+                           c->cellr, c->cxs, c->pos, c->rec, nullptr, nullptr, nullptr, nullptr, nullptr, c->err, s));
     GSPH_CK(launch_interact(c->split, true, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs, c->ys, c->zs,
                             kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr, c->lab_s, c->mat_s, c->id_s,
-                            c->dt, c->sig, c->pairs, c->cost, c->nreal, c->nimage, c->rates, nullptr, 0, nullptr, s));
+                            c->dt, c->sig, c->pairs, c->cost, c->nreal, c->nimage, c->rates, nullptr, 0, nullptr, nullptr,
+                            nullptr, s));
     c->launches += 4 + 3 * radix_passes(key_bits(P.ncell));
     c->dt_dirty = true;   // the signal-speed word now holds the scratch state's maximum
     return GSPH_OK;
@@ -445,7 +463,7 @@ static size_t field_elem_bytes(gsph_field f) {
         case GSPH_F_ID: case GSPH_F_HASH: case GSPH_F_COMM_HASH: case GSPH_F_NREAL: case GSPH_F_NIMAGE:
         case GSPH_F_BOUNDARY: return 4;
         case GSPH_F_RATES: return 8 * kNRate;
-        default: return 8;
+        default: return 8;   // FP64 fields, GSPH_F_H
     }
 }
 
@@ -574,12 +592,26 @@ gsph_status gsph_set_particles(gsph_ctx *c, int64_t n, const double *pos, const 
 }
 
 gsph_status gsph_put_field(gsph_ctx *c, gsph_field f, const void *src, int32_t on_device, void *stream) {
-    if (!c || !src || (int)f < 0 || f > GSPH_F_ID) return GSPH_INVALID_ARG;
+    if (!c || !src || (int)f < 0 || (f > GSPH_F_ID && f != GSPH_F_H)) return GSPH_INVALID_ARG;
+    if (f == GSPH_F_H && !c->cfg.variable_h) return GSPH_INVALID_ARG;
     if (c->n == 0) return GSPH_NOT_READY;
     GSPH_CK(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
+    std::vector<double> hcheck;
+    if (f == GSPH_F_H) {   // smoothing lengths in [h/4, h] (the bucket side and the list test's band)
+        const double *hv = (const double *)src;
+        if (on_device) {
+            hcheck.resize((size_t)c->n);
+            GSPH_CK(cudaMemcpyAsync(hcheck.data(), src, (size_t)c->n * 8, cudaMemcpyDeviceToHost, s));
+            GSPH_CK(cudaStreamSynchronize(s));
+            hv = hcheck.data();
+        }
+        for (int64_t i = 0; i < c->n; ++i)
+            if (!(hv[i] <= c->cfg.h && hv[i] >= 0.25 * c->cfg.h)) return GSPH_INVALID_ARG;
+    }
     void *dst = f <= GSPH_F_SYZ ? (void *)c->A.f[f]
-              : f == GSPH_F_MATERIAL ? (void *)c->A.mat : f == GSPH_F_LABEL ? (void *)c->A.label : (void *)c->A.id;
+              : f == GSPH_F_MATERIAL ? (void *)c->A.mat : f == GSPH_F_LABEL ? (void *)c->A.label
+              : f == GSPH_F_H ? (void *)c->A.h : (void *)c->A.id;
     GSPH_CK(cudaMemcpyAsync(dst, src, (size_t)c->n * field_elem_bytes(f),
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     if (!on_device) GSPH_CK(cudaStreamSynchronize(s));
@@ -595,7 +627,10 @@ gsph_status gsph_get_field(gsph_ctx *c, gsph_field f, void *dst, int32_t on_devi
     const void *src = nullptr;
     size_t count = (size_t)c->n;
     if (f <= GSPH_F_SYZ) src = c->A.f[f];
-    else if (f == GSPH_F_MATERIAL) src = c->A.mat;
+    else if (f == GSPH_F_H) {
+        if (!c->cfg.variable_h) return GSPH_INVALID_ARG;
+        src = c->A.h;
+    } else if (f == GSPH_F_MATERIAL) src = c->A.mat;
     else if (f == GSPH_F_LABEL) src = c->A.label;
     else if (f == GSPH_F_ID) src = c->A.id;
     else {
@@ -737,7 +772,7 @@ gsph_status gsph_set_dt(gsph_ctx *c, double dt, void *stream) {
 gsph_status gsph_adjoint_step(gsph_ctx *c, const double *lam_next, double *lam_prev, double dt, double grad[2],
                               void *stream) {
     if (!c || !lam_next || !lam_prev || !grad || !(dt > 0.0)) return GSPH_INVALID_ARG;
-    if (c->split || !c->cfg.diagnostics || c->cfg.reconstruction) return GSPH_INVALID_ARG;
+    if (c->split || !c->cfg.diagnostics || c->cfg.reconstruction || c->cfg.variable_h) return GSPH_INVALID_ARG;
     for (int k = 0; k < c->cfg.n_materials; ++k)   // the reverse mode covers the linear EOS without cut-off
         if (c->cfg.materials[k].eos != GSPH_EOS_LINEAR || !std::isinf(c->cfg.materials[k].p_min)) return GSPH_INVALID_ARG;
     if (c->n == 0) return GSPH_NOT_READY;

@@ -48,7 +48,14 @@ struct DevParams {
     double inv_rho0[kMaxMat], k0[kMaxMat], inv_2rho0[kMaxMat];   // 1/rho0, rho0 c0^2, 1/(2 rho0)
     // FP32 roundings for the signal speed: c0, s - 1, gamma0, 4G/3
     float f_c0[kMaxMat], f_sm1[kMaxMat], f_g0[kMaxMat], f_G43[kMaxMat];
+    // variable smoothing lengths: support r^2 < (h_i + h_j)^2; the FP32 list test decides outside the
+    // relative band [1 - d, 1 + d] around it (d = kVarBand, wide enough for size ratios up to 4)
+    int variable_h;
+    float f_vlo, f_vhi;      // 1 - d, 1 + d
+    float f_k5;              // |dW/dr| = k5 (1 / (h_i + h_j))^5 r (1 - r / (h_i + h_j))^3: 210 / pi
+    double k5;
 };
+constexpr double kVarBand = 1.0e-3;
 
 // Buffers, stream and events of the two-pass interaction order (Sec. II steps d-f), host side.
 struct OverlapBufs {
@@ -71,6 +78,7 @@ struct State {
     double *f[15];           // x y z vx vy vz w m E sxx syy szz sxy sxz syz
     uint8_t *mat, *label;
     uint32_t *id;
+    double *h;               // per-particle smoothing length (variable h), else null
 };
 enum { FX = 0, FY, FZ, FVX, FVY, FVZ, FW, FM, FE, FSXX, FSYY, FSZZ, FSXY, FSXZ, FSYZ };
 

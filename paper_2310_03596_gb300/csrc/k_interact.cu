@@ -29,6 +29,11 @@
 //   ends form the same reconstructed pair from the raw difference (odd in it), so the fluxes stay
 //   bitwise antisymmetric. The stress rate takes L from the gradient record.
 //
+// Variable smoothing lengths (VARH, variable_h = 1): the list test and every pair term take the pair's
+//   own support and kernel, r^2 < (h_i + h_j)^2 and |dW/dr| of h_ij = (h_i + h_j) / 2, from the sorted
+//   lengths (FP64 and their FP32 roundings); the FP32 list test decides outside a relative band of
+//   1e-3 around (h_i + h_j)^2, the FP64 positions and lengths inside it.
+//
 // Split path: pair math in FP32 from FP32 records (positions relative to each particle's bucket corner,
 // so differences keep ~2^-24 * 2h), FP32 sums with Kahan compensation for the conserved quantities
 // (volume, mass, momentum, energy) and plain FP32 sums for the velocity gradient, FP64 integration of
@@ -341,13 +346,20 @@ __device__ __forceinline__ void row_window(const DevParams &P, const uint2 *__re
 // Exact support predicate from the FP64 positions (real neighbour, or image in wall `wax` at `wpos`).
 __device__ __forceinline__ bool support_exact(const DevParams &P, const double *__restrict__ xs,
                                               const double *__restrict__ ys, const double *__restrict__ zs,
-                                              uint32_t j, double X, double Y, double Z, int wax, double wpos) {
+                                              uint32_t j, double X, double Y, double Z, int wax, double wpos,
+                                              double R2) {
     double qx = xs[j], qy = ys[j], qz = zs[j];
     const double two_w = __dmul_rn(2.0, wpos);
     if (wax == 0) qx = __dsub_rn(two_w, qx);
     if (wax == 1) qy = __dsub_rn(two_w, qy);
     if (wax == 2) qz = __dsub_rn(two_w, qz);
-    return dist2_rn(__dsub_rn(qx, X), __dsub_rn(qy, Y), __dsub_rn(qz, Z)) < P.R2;
+    return dist2_rn(__dsub_rn(qx, X), __dsub_rn(qy, Y), __dsub_rn(qz, Z)) < R2;
+}
+// support of a pair: (2h)^2, or (h_i + h_j)^2 with per-particle lengths, each operation rounded
+__device__ __forceinline__ double pair_R2(bool varh, const DevParams &P, double hi, double hj) {
+    if (!varh) return P.R2;
+    const double sij = __dadd_rn(hi, hj);
+    return __dmul_rn(sij, sij);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -356,22 +368,26 @@ __device__ __forceinline__ bool support_exact(const DevParams &P, const double *
 // cnt[i] = min(entries found, 255) | (neighbours in the stored entries) << 8. Entries found beyond kmax
 // are not stored: the pair kernel finds those neighbours by re-scanning.
 // ---------------------------------------------------------------------------------------------
-template <bool SPLIT>
+template <bool SPLIT, bool VARH>
 __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t n, const uint32_t *__restrict__ skey,
                                                          const uint2 *__restrict__ cellr,
                                                          const typename Types<SPLIT>::Pos *__restrict__ pos,
                                                          const float *__restrict__ cxs, const double *__restrict__ xs,
                                                          const double *__restrict__ ys, const double *__restrict__ zs,
                                                          int kmax, uint2 *__restrict__ list,
-                                                         uint32_t *__restrict__ cnt_out) {
+                                                         uint32_t *__restrict__ cnt_out, const double *__restrict__ hs,
+                                                         const float *__restrict__ hsf) {
     using Pos = typename Types<SPLIT>::Pos;
     // staged candidate: split path (c, |c|^2) with c = (x in the group frame, y, z in the row frame);
     // FP64 path (x, y, z, bucket x)
     // split path: four planes (x, y, z, |c|^2) of NL_THREADS floats, so that one 16-byte load gives a
     // coordinate of four candidates and the tests run on packed pairs; FP64 path: one D4 per candidate
-    __shared__ __align__(16) unsigned char stage_raw[NL_THREADS * sizeof(Pos)];
+    // (variable h: a fifth plane of FP32 lengths, or NL_THREADS FP64 lengths after the D4s)
+    using R = typename Types<SPLIT>::R;
+    __shared__ __align__(16) unsigned char stage_raw[NL_THREADS * (sizeof(Pos) + (VARH ? sizeof(R) : 0))];
     Pos *stage = (Pos *)stage_raw;
     float *splane = (float *)stage_raw;
+    double *hstage = (double *)(stage_raw + NL_THREADS * sizeof(Pos));
     const int tid = threadIdx.x, lane = tid & 31, wbase = tid & ~31;
     const int64_t s = (int64_t)blockIdx.x * NL_THREADS + tid;
     const bool valid = s < n;
@@ -388,6 +404,9 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
     }
     const float fcell = P.f_cell, hcell = 0.5f * P.f_cell;
     const uint32_t self = (uint32_t)s;
+    // variable h: the own length (FP32 for the fast test, FP64 for the exact one); 0 when unused
+    const float hif = VARH && active ? hsf[s] : 0.0f;
+    const double hid = VARH && active ? hs[s] : 0.0;
     uint32_t cnt = 0, nlisted = 0;
     uint2 *out = list + (size_t)s;             // next free list entry of this particle (column-major)
     const size_t colstep = (size_t)n;
@@ -416,7 +435,10 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
             // own y, z in the row frame (origin at the centre of the row's buckets in y and z); the test
             // below evaluates |c - o|^2 - R2lo as |c|^2 + (|o|^2 - R2lo) - 2 c.o
             const float oyr = fmaf(-(float)dcy - 0.5f, fcell, oy), ozr = fmaf(-(float)dcz - 0.5f, fcell, oz);
-            const float Kr = fmaf(oxg, oxg, fmaf(oyr, oyr, fmaf(ozr, ozr, -P.f_R2lo)));
+            // variable h: |c - o|^2 - (1 - d)(h_i + h_j)^2 = (|c|^2 - (1 - d) h_j^2) + mh h_j + Kr with
+            // Kr = |o|^2 - (1 - d) h_i^2 and mh = -2 (1 - d) h_i
+            const float Kr = fmaf(oxg, oxg, fmaf(oyr, oyr, fmaf(ozr, ozr, VARH ? -P.f_vlo * hif * hif : -P.f_R2lo)));
+            const float mh = -2.0f * P.f_vlo * hif;
             const float mx = -2.0f * oxg, my = -2.0f * oyr, mz = -2.0f * ozr;
             const uint32_t code_yz = (uint32_t)(dcy + 1) << 26 | (uint32_t)(dcz + 1) << 28;
             const int cxm1 = cx - 1;
@@ -432,14 +454,22 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                             const float qy = (float)q.y - hcell, qz = (float)q.z - hcell;
                             q.x = qx; q.y = qy; q.z = qz;
                             q.w = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
+                            if (VARH) {
+                                const float hj = hsf[jl];
+                                q.w = fmaf(-P.f_vlo * hj, hj, (float)q.w);
+                                splane[4 * NL_THREADS + tid] = hj;
+                            }
                         } else {
                             q.w = (double)cxj;
+                            if (VARH) hstage[tid] = hs[jl];
                         }
                     } else if (SPLIT) {
                         // past the end of the range: |c|^2 = +inf, which no test accepts
                         q.x = 0.0f; q.y = 0.0f; q.z = 0.0f; q.w = __int_as_float(0x7f800000);
+                        if (VARH) splane[4 * NL_THREADS + tid] = 0.0f;
                     } else {
                         q.x = 1.0e30; q.y = 1.0e30; q.z = 1.0e30; q.w = -1.0e9;
+                        if (VARH) hstage[tid] = 0.0;
                     }
                     if (SPLIT) {
                         splane[tid] = (float)q.x;
@@ -462,16 +492,21 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                         // ending at bit 31 - t; one reversal at the end restores bit t
                         // r^2 - R2lo = fma(mx, x, fma(my, y, fma(mz, z, |c|^2 + Kr))) on packed pairs of
                         // candidates (each lane of a pair rounded as the scalar operation)
-                        const uint32_t wbits = __float_as_uint(P.f_R2hi - P.f_R2lo);
+                        // (variable h: the widest band of this particle's pairs, h_j <= h)
+                        const float hw = hif + (float)P.h;
+                        const uint32_t wbits = VARH ? __float_as_uint((P.f_vhi - P.f_vlo) * hw * hw)
+                                                    : __float_as_uint(P.f_R2hi - P.f_R2lo);
                         uint32_t umin = 0xffffffffu;
                         const float2 mx2 = make_float2(mx, mx), my2 = make_float2(my, my), mz2 = make_float2(mz, mz);
-                        const float2 kr2 = make_float2(Kr, Kr);
+                        const float2 kr2 = make_float2(Kr, Kr), mh2 = make_float2(mh, mh);
 #pragma unroll
                         for (int t = 0; t < 32; t += 4) {
                             const float4 X4 = *(const float4 *)&splane[wbase + t];
                             const float4 Y4 = *(const float4 *)&splane[NL_THREADS + wbase + t];
                             const float4 Z4 = *(const float4 *)&splane[2 * NL_THREADS + wbase + t];
                             const float4 W4 = *(const float4 *)&splane[3 * NL_THREADS + wbase + t];
+                            float4 H4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (VARH) H4 = *(const float4 *)&splane[4 * NL_THREADS + wbase + t];
 #pragma unroll
                             for (int h2 = 0; h2 < 2; ++h2) {
                                 const float2 xx = h2 ? make_float2(X4.z, X4.w) : make_float2(X4.x, X4.y);
@@ -479,6 +514,7 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                                 const float2 zz = h2 ? make_float2(Z4.z, Z4.w) : make_float2(Z4.x, Z4.y);
                                 const float2 ww = h2 ? make_float2(W4.z, W4.w) : make_float2(W4.x, W4.y);
                                 float2 d = __fadd2_rn(ww, kr2);
+                                if (VARH) d = __ffma2_rn(mh2, h2 ? make_float2(H4.z, H4.w) : make_float2(H4.x, H4.y), d);
                                 d = __ffma2_rn(mz2, zz, d);
                                 d = __ffma2_rn(my2, yy, d);
                                 d = __ffma2_rn(mx2, xx, d);
@@ -495,8 +531,10 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                         if (umin < wbits) {
 #pragma unroll 4
                             for (int t = 0; t < 32; ++t) {
+                                float d0 = splane[3 * NL_THREADS + wbase + t] + Kr;
+                                if (VARH) d0 = fmaf(mh, splane[4 * NL_THREADS + wbase + t], d0);
                                 const float d = fmaf(mx, splane[wbase + t], fmaf(my, splane[NL_THREADS + wbase + t],
-                                                fmaf(mz, splane[2 * NL_THREADS + wbase + t], splane[3 * NL_THREADS + wbase + t] + Kr)));
+                                                fmaf(mz, splane[2 * NL_THREADS + wbase + t], d0)));
                                 if (__float_as_uint(d) < wbits) bandm |= 1u << t;
                             }
                         }
@@ -508,7 +546,7 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                             const int cxj = (int)pj.w;
                             if ((uint32_t)(cxj - cxm1) <= 2u &&
                                 dist2_rn(__dsub_rn((double)pj.x, X), __dsub_rn((double)pj.y, Y),
-                                         __dsub_rn((double)pj.z, Z)) < P.R2)
+                                         __dsub_rn((double)pj.z, Z)) < pair_R2(VARH, P, hid, VARH ? hstage[wbase + t] : 0.0))
                                 hitm |= 1u << t;
                         }
                     }
@@ -522,7 +560,8 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                         bandm &= bandm - 1;
                         const int cxj = (int)cxs[b + (uint32_t)t];
                         if ((uint32_t)(cxj - cxm1) <= 2u &&
-                            support_exact(P, xs, ys, zs, b + (uint32_t)t, xs[s], ys[s], zs[s], -1, 0.0))
+                            support_exact(P, xs, ys, zs, b + (uint32_t)t, xs[s], ys[s], zs[s], -1, 0.0,
+                                          pair_R2(VARH, P, hid, VARH ? hs[b + (uint32_t)t] : 0.0)))
                             hitm |= 1u << t;
                     }
                     if (hitm) {
@@ -600,9 +639,12 @@ struct PairArgs {
     int32_t *part_cnt;           // parked real and image neighbour counts: 2 * h, 2 * h + 1
     // MUSCL only: gradient records, 7 G4 per slot (written by PM_GRAD, read by PM_MUSCL)
     typename Types<SPLIT>::G4 *grad;
+    // variable h only: sorted smoothing lengths, FP64 and FP32
+    const double *hs;
+    const float *hsf;
 };
 
-template <bool SPLIT, bool DIAG, int MODE>
+template <bool SPLIT, bool DIAG, int MODE, bool VARH>
 __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, bool valid, int64_t hk) {
     using R = typename Types<SPLIT>::R;
     using Pos = typename Types<SPLIT>::Pos;
@@ -633,6 +675,22 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
     }
     const R inv_2h = SPLIT ? (R)(0.5f * P.f_inv_h) : (R)(0.5 / P.h);
     const R kdwh = SPLIT ? (R)(P.f_kdw * P.f_inv_h) : (R)(P.kdw / P.h);
+    // variable h: the own length; kernel factors of a pair with length hj: 1/(2 h_ij) = 1/(h_i + h_j)
+    // and kdw/h of h_ij = k5 (1/(h_i + h_j))^5, the same bits at both ends (h_i + h_j commutes)
+    const R hme = VARH && active ? (SPLIT ? (R)a.hsf[s] : (R)a.hs[s]) : R(0);
+    const double hmed = VARH && active ? a.hs[s] : 0.0;
+    auto kfac = [&](R hj, R &i2h, R &kw) {
+        if (VARH) {
+            const R inv = rcp_r(hme + hj);
+            const R i2 = inv * inv;
+            i2h = inv;
+            kw = (SPLIT ? (R)P.f_k5 : (R)P.k5) * (i2 * i2) * inv;
+        } else {
+            i2h = inv_2h;
+            kw = kdwh;
+        }
+    };
+    auto hof = [&](uint32_t j) -> R { return VARH ? (SPLIT ? (R)a.hsf[j] : (R)a.hs[j]) : R(0); };
     const R fcell = SPLIT ? (R)P.f_cell : (R)P.cell;
     // label filter of the two-pass order: PM_LOCAL takes neighbours of the own label, PM_BOUNDARY the others
     constexpr bool ALLPAIRS = MODE == PM_ALL || MODE == PM_HEUN1 || MODE == PM_HEUN2 || GRAD || RECON;
@@ -668,7 +726,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
     // one pair's work from the raw difference e (this end's x_oth - x_me) and the neighbour's state:
     // gradient sums, or the (reconstructed) fluxes. jg: the neighbour's slot for its gradient record,
     // wax >= 0 for a wall image (mirrored state and gradient; me is the left state)
-    auto pair_work = [&](R e0, R e1, R e2, const PIn<R> &oth, R sgn, R kw, uint32_t jg, int wax) {
+    auto pair_work = [&](R e0, R e1, R e2, const PIn<R> &oth, R sgn, R kw, R inv_2h, uint32_t jg, int wax) {
         if constexpr (GRAD) {
             const R r2 = e0 * e0 + e1 * e1 + e2 * e2;
             const R inv_r = rsqrt_r(r2);
@@ -717,7 +775,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
     // operands in the same order
     // act = false evaluates a harmless stand-in pair (a nonzero offset, kernel weight 0) that adds zeros,
     // so the listed-neighbour loop needs no branch around the pair
-    auto real_pair = [&](uint32_t jj, uint32_t code, R cxj, const Pos &pj, const Rec &rj, bool act) {
+    auto real_pair = [&](uint32_t jj, uint32_t code, R cxj, const Pos &pj, const Rec &rj, bool act, R hj) {
         const PIn<R> oth = unpack(rj, (R)pj.w);
         // x_j - x_i from this end; the exact factor sgn orients it L -> R inside the pair terms, so both
         // ends obtain the same canonical normal bit for bit (a - b = -(b - a) in IEEE arithmetic)
@@ -732,7 +790,9 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
             d0 = (R)pj.x - mrx; d1 = (R)pj.y - mry; d2 = (R)pj.z - mrz;
         }
         if (!act) d0 = fcell;
-        pair_work(d0, d1, d2, oth, sgn, act ? kdwh : R(0), jj, -1);
+        R i2h, kw;
+        kfac(hj, i2h, kw);
+        pair_work(d0, d1, d2, oth, sgn, act ? kw : R(0), i2h, jj, -1);
     };
 
     // ---- listed real neighbours, all lanes in lockstep: the set bits of the current entry give the
@@ -764,7 +824,8 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
             }
         };
         // record source: the particle arrays, or (second pass, other labels) the halo buffer
-        auto fetch = [&](uint32_t j, bool t, Pos &pj, Rec &rj, float &xj) {
+        auto fetch = [&](uint32_t j, bool t, Pos &pj, Rec &rj, float &xj, R &hj) {
+            hj = hof(j);
             if (MODE == PM_BOUNDARY) {
                 const uint32_t h = t ? a.hidx[j] : 0u;
                 pj = a.hpos[h];
@@ -783,19 +844,21 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         Pos p1;
         Rec r1;
         float x1;
-        fetch(j1, t1, p1, r1, x1);
+        R h1;
+        fetch(j1, t1, p1, r1, x1, h1);
 #pragma unroll 2
         for (int k = 0; k < mc; ++k) {
             const uint32_t j = j1, c = c1;
             const Pos pj = p1;
             const Rec rj = r1;
             const float xj = x1;
+            const R hj = h1;
             const bool tj = t1;
             if ((uint32_t)k + 1 < nlist) next(j1, c1);   // else j1 stays a valid slot
             t1 = take(j1);
-            fetch(j1, t1, p1, r1, x1);
+            fetch(j1, t1, p1, r1, x1, h1);
             const bool act = (uint32_t)k < nlist && tj;
-            real_pair(j, c, (R)xj, pj, rj, act);
+            real_pair(j, c, (R)xj, pj, rj, act, hj);
             if (!ALLPAIRS) nsel += act ? 1 : 0;
             if ((k & 7) == 7) acc.fold();
         }
@@ -853,24 +916,31 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
                 const Pos pj = pos[j];
                 const int dcx = (int)cxs[j] - bx;
                 bool hit;
+                const double R2j = pair_R2(VARH, P, hmed, VARH ? a.hs[j] : 0.0);
                 if (MODE == PM_HEUN2) {   // membership from the step's start: the FP64 positions
-                    hit = support_exact(P, xs, ys, zs, j, X, Y, Z, wax, wpos);
+                    hit = support_exact(P, xs, ys, zs, j, X, Y, Z, wax, wpos, R2j);
                 } else if (SPLIT) {
                     const float exf = ((float)pj.x - (float)ox) + (float)dcx * (float)fcell;
                     const float eyf = ((float)pj.y - (float)oy) + (float)dcy * (float)fcell;
                     const float ezf = ((float)pj.z - (float)oz) + (float)dcz * (float)fcell;
                     const float r2 = exf * exf + eyf * eyf + ezf * ezf;
-                    hit = r2 < P.f_R2lo;
-                    if (!hit && r2 < P.f_R2hi) hit = support_exact(P, xs, ys, zs, j, X, Y, Z, wax, wpos);
+                    float lo = P.f_R2lo, hi = P.f_R2hi;
+                    if (VARH) {
+                        const float sf = (float)hme + a.hsf[j];
+                        lo = P.f_vlo * sf * sf;
+                        hi = P.f_vhi * sf * sf;
+                    }
+                    hit = r2 < lo;
+                    if (!hit && r2 < hi) hit = support_exact(P, xs, ys, zs, j, X, Y, Z, wax, wpos, R2j);
                 } else {
-                    hit = support_exact(P, xs, ys, zs, j, X, Y, Z, wax, wpos);
+                    hit = support_exact(P, xs, ys, zs, j, X, Y, Z, wax, wpos, R2j);
                 }
                 if (!hit) continue;
                 if (src == 0) {
                     // real neighbour past the list capacity
                     if (seen++ < nlist) continue;
                     if (!take(j)) continue;
-                    real_pair(j, (uint32_t)(dcy + 1) | (uint32_t)(dcz + 1) << 2, (R)cxs[j], pj, rec[j], true);
+                    real_pair(j, (uint32_t)(dcy + 1) | (uint32_t)(dcz + 1) << 2, (R)cxs[j], pj, rec[j], true, hof(j));
                     ++nover;
                 } else {
                     if (!take(j)) continue;
@@ -892,7 +962,9 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
                         d0 = (R)(qx - XF); d1 = (R)(qy - YF); d2 = (R)(qz - ZF);
                     }
                     mirror<R>(oth, wax);
-                    pair_work(d0, d1, d2, oth, R(1), kdwh, j, wax);
+                    R i2h, kw;
+                    kfac(hof(j), i2h, kw);
+                    pair_work(d0, d1, d2, oth, R(1), kw, i2h, j, wax);
                     ++ni;
                 }
             }
@@ -1109,6 +1181,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         B.mat[s] = a.mat_s[s];
         B.label[s] = a.lab_s[s];
         B.id[s] = a.id_s[s];
+        if (VARH) B.h[s] = A.h[o];
         if (DIAG && MODE != PM_HEUN2) {   // the step's counts and rates: those of its start
             a.nreal_out[s] = nr;
             a.nimage_out[s] = ni;
@@ -1118,6 +1191,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         }
         // next step's CFL signal speed (correctly rounded FP32, reproducible bit for bit)
         if (MODE != PM_HEUN1) sp = signal_speed32(P, mt, mo, wo, nvx, nvy, nvz, En);
+        if (VARH) sp = __fdiv_rn(sp, a.hsf[s]);   // the time step from max s_i / h_i
     }
     const unsigned b = __reduce_max_sync(kFullMask, __float_as_uint(sp));
     if (lane == 0) {
@@ -1134,7 +1208,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
     }
 }
 
-template <bool SPLIT, bool DIAG, int MODE>
+template <bool SPLIT, bool DIAG, int MODE, bool VARH = false>
 __global__ void __launch_bounds__(PK_THREADS, SPLIT ? (MODE == PM_MUSCL ? 3 : 5) : 2) k_pair(const PairArgs<SPLIT> a) {
     if (MODE == PM_BOUNDARY) {
         // one lane per boundary particle, warp-uniform strides over the boundary list
@@ -1144,11 +1218,11 @@ __global__ void __launch_bounds__(PK_THREADS, SPLIT ? (MODE == PM_MUSCL ? 3 : 5)
             const int64_t k = kb + (threadIdx.x & 31);
             const bool valid = k < total;
             const int64_t s = valid ? (int64_t)a.blist[k] : 0;
-            pair_body<SPLIT, DIAG, MODE>(a, s, valid, k);
+            pair_body<SPLIT, DIAG, MODE, VARH>(a, s, valid, k);
         }
     } else {
         const int64_t s = (int64_t)blockIdx.x * PK_THREADS + threadIdx.x;
-        pair_body<SPLIT, DIAG, MODE>(a, s, s < a.n, 0);
+        pair_body<SPLIT, DIAG, MODE, VARH>(a, s, s < a.n, 0);
     }
 }
 
@@ -1174,7 +1248,7 @@ static PairArgs<SPLIT> pair_args(const DevParams &P, int64_t n, const uint32_t *
                                  const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s,
                                  const double *dt, unsigned int *sig, unsigned long long *pairs,
                                  unsigned long long *cost, int32_t *nreal, int32_t *nimage, double *rates,
-                                 const OverlapBufs *ov, void *grad) {
+                                 const OverlapBufs *ov, void *grad, const double *hs, const float *hsf) {
     using Pos = typename Types<SPLIT>::Pos;
     using Rec = typename Types<SPLIT>::Rec;
     PairArgs<SPLIT> a;
@@ -1192,6 +1266,8 @@ static PairArgs<SPLIT> pair_args(const DevParams &P, int64_t n, const uint32_t *
     a.part = ov ? ov->part : nullptr;
     a.part_cnt = ov ? ov->part_cnt : nullptr;
     a.grad = (typename Types<SPLIT>::G4 *)grad;
+    a.hs = hs;
+    a.hsf = hsf;
     return a;
 }
 
@@ -1202,23 +1278,32 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
                             unsigned int *sig, unsigned long long *pairs, unsigned long long *cost,
                             int32_t *nreal, int32_t *nimage, double *rates, const OverlapBufs *ov,
-                            int stage, void *grad, cudaStream_t s) {
+                            int stage, void *grad, const double *hs, const float *hsf, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
+    const bool varh = P.variable_h != 0;
     const unsigned gl = (unsigned)((n + NL_THREADS - 1) / NL_THREADS);
     const unsigned gp = (unsigned)((n + PK_THREADS - 1) / PK_THREADS);
-#define GSPH_NL_ARGS P, n, skey, cellr, (const typename Types<SP>::Pos *)pos, cxs, xs, ys, zs, kmax, list, cnt
+#define GSPH_NL_ARGS P, n, skey, cellr, (const typename Types<SP>::Pos *)pos, cxs, xs, ys, zs, kmax, list, cnt, hs, hsf
 #define GSPH_PAIR_ARGS pair_args<SP>(P, n, skey, cellr, pos, rec, cxs, xs, ys, zs, kmax, list, cnt, perm, A, B, \
-                                     lab_s, mat_s, id_s, dt, sig, pairs, cost, nreal, nimage, rates, ov, grad)
+                                     lab_s, mat_s, id_s, dt, sig, pairs, cost, nreal, nimage, rates, ov, grad, hs, hsf)
 #define GSPH_PAIRS(MODE_)                                                                   \
     do {                                                                                    \
         const auto pa = GSPH_PAIR_ARGS;                                                      \
         const unsigned g_ = MODE_ == PM_BOUNDARY ? ov->boundary_grid : gp;                  \
-        if (diag) k_pair<SP, true, MODE_><<<g_, PK_THREADS, 0, s>>>(pa);                     \
-        else k_pair<SP, false, MODE_><<<g_, PK_THREADS, 0, s>>>(pa);                        \
+        if (varh) {                                                                         \
+            if (diag) k_pair<SP, true, MODE_, true><<<g_, PK_THREADS, 0, s>>>(pa);          \
+            else k_pair<SP, false, MODE_, true><<<g_, PK_THREADS, 0, s>>>(pa);              \
+        } else {                                                                            \
+            if (diag) k_pair<SP, true, MODE_><<<g_, PK_THREADS, 0, s>>>(pa);                 \
+            else k_pair<SP, false, MODE_><<<g_, PK_THREADS, 0, s>>>(pa);                    \
+        }                                                                                   \
     } while (0)
 #define GSPH_INTERACT                                                                       \
     do {                                                                                    \
-        if (stage != 2) k_nbr_list<SP><<<gl, NL_THREADS, 0, s>>>(GSPH_NL_ARGS);             \
+        if (stage != 2) {                                                                   \
+            if (varh) k_nbr_list<SP, true><<<gl, NL_THREADS, 0, s>>>(GSPH_NL_ARGS);        \
+            else k_nbr_list<SP, false><<<gl, NL_THREADS, 0, s>>>(GSPH_NL_ARGS);            \
+        }                                                                                   \
         if (mid) cudaEventRecord(mid, s);                                                   \
         if (stage == 1) {                                                                   \
             GSPH_PAIRS(PM_HEUN1);                                                           \
@@ -1226,7 +1311,8 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
             GSPH_PAIRS(PM_HEUN2);                                                           \
         } else if (grad) {                                                                  \
             /* MUSCL: the gradient pass, then the reconstructed fluxes */                  \
-            k_pair<SP, false, PM_GRAD><<<gp, PK_THREADS, 0, s>>>(GSPH_PAIR_ARGS);           \
+            if (varh) k_pair<SP, false, PM_GRAD, true><<<gp, PK_THREADS, 0, s>>>(GSPH_PAIR_ARGS); \
+            else k_pair<SP, false, PM_GRAD><<<gp, PK_THREADS, 0, s>>>(GSPH_PAIR_ARGS);      \
             GSPH_PAIRS(PM_MUSCL);                                                           \
         } else if (!ov) {                                                                   \
             GSPH_PAIRS(PM_ALL);                                                             \

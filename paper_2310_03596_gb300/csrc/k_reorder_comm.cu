@@ -78,11 +78,17 @@ __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const u
                                                  uint2 *__restrict__ cellr, float *__restrict__ cxs,
                                                  void *__restrict__ pos_out, void *__restrict__ rec_out,
                                                  float *__restrict__ xf, float *__restrict__ yf,
-                                                 float *__restrict__ zf, int *__restrict__ err) {
+                                                 float *__restrict__ zf, double *__restrict__ hs,
+                                                 float *__restrict__ hsf, int *__restrict__ err) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     uint32_t k = skey[s];
     uint32_t o = perm[s];
+    if (hs) {   // variable h: the sorted smoothing lengths, FP64 and their FP32 roundings
+        const double hh = A.h[o];
+        hs[s] = hh;
+        hsf[s] = __double2float_rn(hh);
+    }
     double x = A.f[FX][o], y = A.f[FY][o], z = A.f[FZ][o];
     xs[s] = x; ys[s] = y; zs[s] = z;
     if (xf) {
@@ -134,15 +140,15 @@ cudaError_t launch_refresh(bool split, const DevParams &P, int64_t n, const uint
 cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint32_t *perm,
                            const State &A, double *xs, double *ys, double *zs, uint8_t *lab_s, uint8_t *mat_s,
                            uint32_t *id_s, uint2 *cellr, float *cxs, void *pos, void *rec, float *xf, float *yf,
-                           float *zf, int *err, cudaStream_t s) {
+                           float *zf, double *hs, float *hsf, int *err, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     unsigned g = (unsigned)((n + 255) / 256);
     if (split)
         k_reorder<true><<<g, 256, 0, s>>>(P, n, skey, perm, A, xs, ys, zs, lab_s, mat_s, id_s, cellr, cxs, pos, rec,
-                                          xf, yf, zf, err);
+                                          xf, yf, zf, hs, hsf, err);
     else
         k_reorder<false><<<g, 256, 0, s>>>(P, n, skey, perm, A, xs, ys, zs, lab_s, mat_s, id_s, cellr, cxs, pos, rec,
-                                           xf, yf, zf, err);
+                                           xf, yf, zf, hs, hsf, err);
     return cudaGetLastError();
 }
 
@@ -314,6 +320,7 @@ __global__ void k_init_state(DevParams P, int64_t n, const double *__restrict__ 
     A.mat[i] = m;
     A.label[i] = l;
     A.id[i] = (uint32_t)i;
+    if (A.h) A.h[i] = P.h;   // variable h: every particle starts at the largest length
 }
 
 cudaError_t launch_init(const DevParams &P, int64_t n, const double *pos, const double *vel, const double *vol,
@@ -324,13 +331,15 @@ cudaError_t launch_init(const DevParams &P, int64_t n, const double *pos, const 
 }
 
 // Maximum CFL signal speed over the state (bit pattern of a non-negative float, so the integer max is
-// the floating-point max), then dt = cfl * h / max.
+// the floating-point max), then dt = cfl * h / max. Variable h: the maximum of the FP32 quotients
+// s_i / h_i, then dt = cfl / max.
 __global__ void k_signal_max(DevParams P, int64_t n, State A, unsigned int *__restrict__ sig) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float v = 0.0f;
     if (i < n) {
         int m = A.mat[i] < P.nmat ? A.mat[i] : 0;
         v = signal_speed32(P, m, A.f[FM][i], A.f[FW][i], A.f[FVX][i], A.f[FVY][i], A.f[FVZ][i], A.f[FE][i]);
+        if (P.variable_h) v = __fdiv_rn(v, __double2float_rn(A.h[i]));
     }
     const unsigned b = __reduce_max_sync(kFullMask, __float_as_uint(v));
     if ((threadIdx.x & 31) == 0) atomicMax(sig, b);
@@ -338,7 +347,7 @@ __global__ void k_signal_max(DevParams P, int64_t n, State A, unsigned int *__re
 
 __global__ void k_finalize_dt(DevParams P, unsigned int *__restrict__ sig, double *__restrict__ dt) {
     const double mx = (double)__uint_as_float(*sig);
-    *dt = __ddiv_rn(__dmul_rn(P.cfl, P.h), mx);
+    *dt = P.variable_h ? __ddiv_rn(P.cfl, mx) : __ddiv_rn(__dmul_rn(P.cfl, P.h), mx);
     *sig = 0u;
 }
 

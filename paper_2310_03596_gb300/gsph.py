@@ -27,11 +27,11 @@ OK, INVALID_ARG, OOM, CUDA_ERROR, PARTICLE_LEFT_DOMAIN, DEVICE_TIMEOUT, NOT_READ
 
 # gsph_field
 FIELDS = ["x", "y", "z", "vx", "vy", "vz", "w", "m", "E", "sxx", "syy", "szz", "sxy", "sxz", "syz",
-          "material", "label", "id", "hash", "comm_hash", "flag", "nreal", "nimage", "rates", "boundary"]
+          "material", "label", "id", "hash", "comm_hash", "flag", "nreal", "nimage", "rates", "boundary", "h"]
 FIELD = {name: k for k, name in enumerate(FIELDS)}
 FIELD_DTYPE = {**{f: np.float64 for f in FIELDS[:15]}, "material": np.uint8, "label": np.uint8,
                "id": np.uint32, "hash": np.uint32, "comm_hash": np.uint32, "flag": np.uint8,
-               "nreal": np.int32, "nimage": np.int32, "rates": np.float64, "boundary": np.uint32}
+               "nreal": np.int32, "nimage": np.int32, "rates": np.float64, "boundary": np.uint32, "h": np.float64}
 
 
 class GsphError(RuntimeError):
@@ -57,7 +57,7 @@ class Config(C.Structure):
                 ("gravity", C.c_double * 3), ("alpha", C.c_double), ("swap_period", C.c_int32),
                 ("precision", C.c_int32), ("device", C.c_int32), ("diagnostics", C.c_int32),
                 ("overlap", C.c_int32), ("integrator", C.c_int32), ("reconstruction", C.c_int32),
-                ("pad2", C.c_int32)]
+                ("variable_h", C.c_int32)]
 
 
 class ExchangeStats(C.Structure):
@@ -165,6 +165,7 @@ def config_from_scene(scene, precision: int = FP32_SPLIT, device: int = 0, diagn
     c.overlap = int(overlap)
     c.integrator = int(getattr(scene, "integrator", 0) or 0)
     c.reconstruction = int(getattr(scene, "reconstruction", 0) or 0)
+    c.variable_h = int(getattr(scene, "variable_h", 0) or 0)
     return c
 
 
@@ -196,6 +197,8 @@ class Solver:
                    stream=None, overlap: bool = False) -> "Solver":
         s = cls(config_from_scene(scene, precision, device, diagnostics, overlap))
         s.set_particles(scene.pos, scene.vel, scene.vol, scene.material, scene.label, stream=stream)
+        if getattr(scene, "variable_h", 0):
+            s.put("h", np.asarray(scene.hp, dtype=np.float64), stream=stream)
         return s
 
     def close(self) -> None:
@@ -282,7 +285,10 @@ class Solver:
                 self.put(f, d[f], stream)
 
     def state(self, stream=None) -> dict:
-        return {f: self.get(f, stream) for f in FIELDS[:18]}
+        d = {f: self.get(f, stream) for f in FIELDS[:18]}
+        if self.cfg.variable_h:
+            d["h"] = self.get("h", stream)
+        return d
 
     # ---------------------------------------------------------------------------- queries
     def exchange_stats(self, stream=None) -> dict:
