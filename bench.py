@@ -223,6 +223,7 @@ def main():
     ap.add_argument("--heun-steps", type=int, default=20)
     ap.add_argument("--muscl-steps", type=int, default=20)
     ap.add_argument("--varh-steps", type=int, default=20)
+    ap.add_argument("--collapse-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -378,6 +379,35 @@ def main():
              "phase_ms_per_step": {k[:-3]: v / max(tmm["steps"], 1) for k, v in tmm.items()
                                    if k.endswith("_ms") and v > 0}}
 
+    # the largest workload: the 64 M-particle collapse block, K = 16, swap pass every 10 steps (step 0
+    # and step 10 of the timed window include one), exchange-volume fraction per step
+    collapse = None
+    if args.collapse_steps > 0:
+        s5 = scenes.collapse_block()
+        solc = gsph.Solver.from_scene(s5, device=local, stream=stream)
+        solc.step(1, stream)
+        solc.sync(stream)
+        solc.set_timing(args.collapse_steps)
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        solc.step(args.collapse_steps, stream)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        msc = c0.elapsed_time(c1)
+        tmc = solc.timings()
+        stc = solc.exchange_stats(stream)
+        solc.close()
+        collapse = {"workload": "collapse_block: Al block 0.4 x 0.2 x 0.1 m at dx 0.5 mm on a floor under gravity, "
+                                "K = 16 random labels, swap every 10 steps",
+                    "particles": s5.n, "value": world * s5.n * args.collapse_steps / (msc * 1e-3),
+                    "unit": "particle-steps/s", "ms_per_step": msc / args.collapse_steps,
+                    "steps": args.collapse_steps,
+                    "phase_ms_per_step": {k[:-3]: v / max(tmc["steps"], 1) for k, v in tmc.items()
+                                          if k.endswith("_ms") and v > 0},
+                    "exchange_fraction": stc["exchange_fraction"], "swap_passes": stc["swap_passes"]}
+
     # per-particle smoothing lengths (Sec. V's varying particle sizes): the rod with a fine impact end,
     # and the cost function per label there
     s4 = scenes.graded_bar()
@@ -510,6 +540,7 @@ def main():
         "heun": heun,
         "muscl": muscl,
         "varh": varh,
+        "collapse": collapse,
         "clocks": ck,
         "exchange": {k: st1[k] for k in ("boundary_total", "exchange_fraction", "bytes_boundary_broadcast",
                                          "swapped_last_pass", "swap_passes")},

@@ -170,7 +170,7 @@ __global__ void k_label_mask(DevParams P, int64_t n, const uint32_t *__restrict_
 }
 
 // Flags, communication hash and per-block counts per label (block_counts[label * nblk + block]).
-constexpr int CM_THREADS = 256;
+constexpr int CM_THREADS = 512;
 __global__ void __launch_bounds__(CM_THREADS) k_comm(DevParams P, int64_t n, const uint32_t *__restrict__ skey,
                                                      const uint8_t *__restrict__ lab_s,
                                                      const uint32_t *__restrict__ mask, uint8_t *__restrict__ flag,
@@ -180,28 +180,32 @@ __global__ void __launch_bounds__(CM_THREADS) k_comm(DevParams P, int64_t n, con
     if (threadIdx.x < kMaxLabel) cnt[threadIdx.x] = 0;
     __syncthreads();
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const uint32_t k = s < n ? skey[s] : P.ncell;
+    const bool in = s < n && k < P.ncell;
+    // the 27-bucket OR of each distinct bucket of the warp (sorted keys: a few per warp), its 27 masks
+    // fetched by 27 lanes at once and combined by one warp reduction
+    uint32_t acc = 0;
+    unsigned todo = __ballot_sync(kFullMask, in);
+    while (todo) {
+        const uint32_t kb = __shfl_sync(kFullMask, k, __ffs(todo) - 1);
+        int cx, cy, cz;
+        decode_cell(P, kb, cx, cy, cz);
+        uint32_t m = 0;
+        if (lane < 27) {
+            const int X = cx + lane % 3 - 1, Y = cy + (lane / 3) % 3 - 1, Z = cz + lane / 9 - 1;
+            if (X >= 0 && X < P.dims[0] && Y >= 0 && Y < P.dims[1] && Z >= 0 && Z < P.dims[2])
+                m = __ldg(mask + (uint32_t)X + (uint32_t)P.dims[0] * ((uint32_t)Y + (uint32_t)P.dims[1] * (uint32_t)Z));
+        }
+        const uint32_t orr = __reduce_or_sync(kFullMask, m);
+        const bool mine = in && k == kb;
+        if (mine) acc = orr;
+        todo &= ~__ballot_sync(kFullMask, mine);
+    }
     if (s < n) {
-        uint32_t k = skey[s];
         uint8_t f = 0;
-        if (k < P.ncell) {
-            int cx, cy, cz;
-            decode_cell(P, k, cx, cy, cz);
-            uint32_t acc = 0;
-            for (int dz = -1; dz <= 1; ++dz) {
-                int Z = cz + dz;
-                if (Z < 0 || Z >= P.dims[2]) continue;
-                for (int dy = -1; dy <= 1; ++dy) {
-                    int Y = cy + dy;
-                    if (Y < 0 || Y >= P.dims[1]) continue;
-                    uint32_t row = (uint32_t)P.dims[0] * ((uint32_t)Y + (uint32_t)P.dims[1] * (uint32_t)Z);
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        int X = cx + dx;
-                        if (X < 0 || X >= P.dims[0]) continue;
-                        acc |= __ldg(mask + row + (uint32_t)X);
-                    }
-                }
-            }
-            uint32_t lab = lab_s[s];
+        if (in) {
+            const uint32_t lab = lab_s[s];
             f = (acc & ~(1u << lab)) != 0u;
             if (f) atomicAdd(&cnt[lab], 1u);
         }
