@@ -214,6 +214,36 @@ def test_heun_integrator_lockstep(precision, tol):
     _lockstep(s, precision, 2, tol)
 
 
+def _free_run_100(s):
+    P = orc.params_of(s)
+    st = orc.OracleState.from_scene(s)
+    for _ in range(100):
+        orc.step(P, st)
+    sol = gsph.Solver.from_scene(s, precision=gsph.FP32_SPLIT)
+    try:
+        sol.step(100)
+        sol.sync()
+        g = sol.state()
+        order = np.argsort(g["id"])
+        ref = np.argsort(st.id)
+        for f in STATE_F:
+            e = _maxnorm_err(g[f][order], getattr(st, f)[ref])
+            assert e <= 1e-3, (f, e)
+    finally:
+        sol.close()
+
+
+def test_split_free_running_100_steps_variants():
+    # the 1e-3 bound after 100 free steps for the MUSCL, Heun and varying-size variants
+    s = scenes.cube_impact(n_side=12, steps=100)
+    s.reconstruction = 1
+    _free_run_100(s)
+    s = scenes.cube_impact(n_side=12, steps=100)
+    s.integrator = 1
+    _free_run_100(s)
+    _free_run_100(scenes.graded_block(n_side=10, nz_fine=8, nz_coarse=4, seed=6))
+
+
 def test_split_free_running_100_steps():
     s = scenes.cube_impact(n_side=12, steps=100)
     P = orc.params_of(s)
