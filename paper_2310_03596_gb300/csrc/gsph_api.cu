@@ -48,6 +48,7 @@ cudaError_t launch_round_positions(int64_t n, const double *x, const double *y, 
                                    float *yf, float *zf, cudaStream_t s);
 cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const float *x, const float *y, const float *z,
                              uint8_t *lab, const uint8_t *mat, const uint32_t *id, void *scratch, uint16_t *bh,
+                             uint32_t *sidx,
                              int *err, int grid, cudaStream_t s);
 int swap_grid_blocks();
 unsigned long long *swap_moved_ptr(void *scratch);
@@ -117,6 +118,7 @@ struct gsph_ctx {
     double *hs = nullptr;                      // variable h: sorted smoothing lengths
     float *hsf = nullptr;
     void *swap_scratch = nullptr;
+    uint32_t *sidx = nullptr;                  // swap pass label segments (2n)
     uint16_t *bh = nullptr;
     double *cons_part = nullptr, *cons_out = nullptr;
     double *adj_scratch = nullptr;   // allocated on the first adjoint step
@@ -211,6 +213,7 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     }
     A_(dalloc(c, (char **)&c->swap_scratch, swap_scratch_bytes(c->P.K_labels, c->P.nmat)));
     A_(dalloc(c, &c->bh, N));
+    A_(dalloc(c, &c->sidx, 2 * N + 2));   // swap pass: label segments and moved lists
     A_(dalloc(c, &c->cons_part, ((N + 255) / 256 + 1) * 6));
     A_(dalloc(c, &c->cons_out, 6));
     if (c->cfg.variable_h) {   // sorted smoothing lengths, FP64 and FP32
@@ -379,7 +382,7 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     rec_event(c, PH_REORDER, s);
     // Sec. III: periodic swap heuristic on the sorted view
     if (do_swap) {
-        GSPH_CK(launch_swap_pass(P, n, c->xf, c->yf, c->zf, c->lab_s, c->mat_s, c->id_s, c->swap_scratch, c->bh,
+        GSPH_CK(launch_swap_pass(P, n, c->xf, c->yf, c->zf, c->lab_s, c->mat_s, c->id_s, c->swap_scratch, c->bh, c->sidx,
                                  c->err, c->swap_grid, s));
         ++c->swap_passes;
         c->launches += swap_pass_launches(P);
@@ -675,7 +678,7 @@ gsph_status gsph_swap_now(gsph_ctx *c, void *stream) {
     GSPH_CK(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
     GSPH_CK(launch_round_positions(c->n, c->A.f[FX], c->A.f[FY], c->A.f[FZ], c->xf, c->yf, c->zf, s));
-    GSPH_CK(launch_swap_pass(c->P, c->n, c->xf, c->yf, c->zf, c->A.label, c->A.mat, c->A.id, c->swap_scratch, c->bh,
+    GSPH_CK(launch_swap_pass(c->P, c->n, c->xf, c->yf, c->zf, c->A.label, c->A.mat, c->A.id, c->swap_scratch, c->bh, c->sidx,
                              c->err, c->swap_grid, s));
     ++c->swap_passes;
     c->launches += 1 + swap_pass_launches(c->P);

@@ -43,12 +43,14 @@ struct SwapPair {
     uint32_t spec[2];                // the same at the pass-start labels and sums (speculative pass)
     uint32_t idh[3][2][SW_ID_BINS];
     uint32_t tcnt[2];                // threshold-bin list fill per side
+    uint32_t mvcnt[2];               // particles moved per side (their label-segment positions listed)
     unsigned long long moved;
 };
 
 struct SwapScratch {
     long long sums[kMaxLabel][SW_NT][3];
     long long cnt[kMaxLabel][SW_NT];
+    unsigned long long lcur[kMaxLabel];   // fill of each label's segment (pass start)
     unsigned long long moved;
     unsigned int bar_count;
     unsigned int bar_gen;
@@ -238,7 +240,8 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                                                           const uint8_t *__restrict__ mat,
                                                           const uint32_t *__restrict__ id, uint16_t *__restrict__ bh,
                                                           SwapScratch *__restrict__ S, SwapPair *__restrict__ pairs,
-                                                          uint2 *__restrict__ tl, int *__restrict__ err) {
+                                                          uint2 *__restrict__ tl, uint32_t *__restrict__ sidx,
+                                                          int *__restrict__ err) {
     __shared__ long long shs[kMaxLabel][SW_NT][4];
     __shared__ uint32_t hs[2][SW_BINS];
     __shared__ uint32_t ids[2][SW_ID_BINS];
@@ -296,6 +299,27 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
     const int npairs = K * (K - 1) / 2;
     const int ncombo = ntype * npairs;
     __shared__ int first_sh;
+    // label segments (K >= 8): sidx[0, n) holds the slots grouped by label (segment l at
+    // [loff[l], loff[l + 1])). A pair's swaps exchange equally many particles each way, so the segments
+    // keep their sizes; the moved particles exchange their segment positions after each pair (mv lists
+    // at sidx[n, 2n)), and a pair visits only its two labels' particles, 2n/K instead of n. Order within
+    // a segment is free: every use is a count, an exact sum or a select by persistent id. With fewer
+    // labels the segments cost more (their build, one more barrier per pair) than they save, and the
+    // pairs visit every slot.
+    const bool seg = K >= 8;
+    __shared__ long long loff_sh[kMaxLabel + 1];
+    if (threadIdx.x == 0) {
+        long long o = 0;
+        for (int l = 0; l < kMaxLabel; ++l) {
+            loff_sh[l] = o;
+            if (l < K) o += ((volatile long long *)&S->cnt[l][kMaxMat])[0];
+        }
+        loff_sh[kMaxLabel] = o;
+    }
+    uint32_t *const byl = sidx;
+    uint32_t *const mvl = sidx + n;                      // side 0 at [0, n/2), side 1 at [n/2, n)
+    const int64_t mvh = (n + 1) / 2;
+    __syncthreads();
     {
         Side *spec = (Side *)sbuf;
         uint32_t *scnt = (uint32_t *)(sbuf + SW_MAXCOMBO * sizeof(Side));
@@ -314,6 +338,14 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
             const int l = v ? (lab[i] & (kMaxLabel - 1)) : 0;
             const int T = (v && multi) ? (mat[i] < nmat ? mat[i] : 0) : 0;
             const float px = v ? x[i] : 0.0f, py = v ? y[i] : 0.0f, pz = v ? z[i] : 0.0f;
+            if (seg) {   // the slot's place in its label's segment (one atomic per label and warp)
+                const unsigned peers = __match_any_sync(kFullMask, v ? l : -1);
+                unsigned long long at = 0;
+                if (v && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
+                    at = atomicAdd(&S->lcur[l], (unsigned long long)__popc(peers));
+                at = __shfl_sync(kFullMask, at, __ffs(peers) - 1);
+                if (v) byl[loff_sh[l] + (long long)at + __popc(peers & lanemask_lt())] = (uint32_t)i;
+            }
             for (int o = 0; o < K; ++o) {   // the K - 1 pairs of the particle's label (warp-uniform loop)
                 const int a = l < o ? l : o, b = l < o ? o : l;
                 const int q = T * npairs + a * (2 * K - a - 1) / 2 + (b - a - 1);
@@ -355,6 +387,13 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
             for (int b = a + 1; b < K; ++b, ++idx) {
                 if (idx < first) continue;   // no positive hashes on a side: nothing to do
                 SwapPair *pr = pairs + idx;
+                // this pair's particles: the segments of a and b (their labels read from L2: another
+                // block may have written them in an earlier pair)
+                const long long oa = loff_sh[a], na = loff_sh[a + 1] - oa, ob = loff_sh[b];
+                const long long tot = seg ? na + (loff_sh[b + 1] - ob) : n;
+                // position k of the pair's iteration -> its segment position (without segments: the slot)
+                auto segpos = [&](long long k) { return !seg ? k : (k < na ? oa + k : ob + (k - na)); };
+                auto slot_at = [&](long long sp) { return seg ? __ldcg(&byl[sp]) : (uint32_t)sp; };
                 // -- pair geometry (every block, identical operations on the same sums): counts, then the
                 // Cg components in parallel, the Cg' blend and the segment, its length, then the direction
                 // and scale. Side b's direction is the exact negation of side a's (d_b = -d_a bit for bit).
@@ -407,11 +446,12 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                 // -- balancing hashes and their histograms
                 if (act) {
                     const Side s0 = side_sh[0], s1 = side_sh[1];
-                    for (int64_t base = (int64_t)blockIdx.x * SW_THREADS; base < n; base += gstride) {
-                        const int64_t i = base + threadIdx.x;
+                    for (int64_t base = (int64_t)blockIdx.x * SW_THREADS; base < tot; base += gstride) {
+                        const int64_t k = base + threadIdx.x;
                         int key = -1;
-                        if (i < n) {
-                            const uint8_t l = lab[i];
+                        if (k < tot) {
+                            const uint32_t i = slot_at(segpos(k));
+                            const uint8_t l = __ldcg(&lab[i]);
                             if ((l == a || l == b) && (type < 0 || mat[i] == type)) {
                                 const int sd = l == a ? 0 : 1;
                                 const int hv = balancing_hash(sd == 0 ? s0 : s1, x[i], y[i], z[i]);
@@ -481,11 +521,12 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                         const int shift = 18 - SW_ID_BITS * pass;
                         for (int k = threadIdx.x; k < 2 * SW_ID_BINS; k += SW_THREADS) (&ids[0][0])[k] = 0;
                         __syncthreads();
-                        for (int64_t i = g0; i < n; i += gstride) {
-                            const uint8_t l = lab[i];
+                        for (int64_t k = g0; k < tot; k += gstride) {
+                            const uint32_t i = slot_at(segpos(k));
+                            const uint8_t l = __ldcg(&lab[i]);
                             if ((l != a && l != b) || (type >= 0 && mat[i] != type)) continue;
                             const int sd = l == a ? 0 : 1;
-                            if (!idsel_sh[sd] || bh[i] != T_sh[sd]) continue;
+                            if (!idsel_sh[sd] || __ldcg(&bh[i]) != T_sh[sd]) continue;
                             const uint32_t v = id[i];
                             if ((v >> (shift + SW_ID_BITS)) == (idpre_sh[sd] >> (shift + SW_ID_BITS)))
                                 atomicAdd(&ids[sd][(v >> shift) & (SW_ID_BINS - 1)], 1u);
@@ -523,15 +564,18 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                 // list splits are collected instead
                 if (threadIdx.x < 8) (&dsum[0][0])[threadIdx.x] = 0;
                 __syncthreads();
-                for (int64_t base = (int64_t)blockIdx.x * SW_THREADS; base < n; base += gstride) {
-                    const int64_t i = base + threadIdx.x;
+                for (int64_t base = (int64_t)blockIdx.x * SW_THREADS; base < tot; base += gstride) {
+                    const int64_t k = base + threadIdx.x;
                     int sd = -1, ap = -1;
                     long long q0 = 0, q1 = 0, q2 = 0;
-                    if (i < n) {
-                        const uint8_t l = lab[i];
+                    uint32_t i = 0;
+                    const long long sp = k < tot ? segpos(k) : 0;
+                    if (k < tot) {
+                        i = slot_at(sp);
+                        const uint8_t l = __ldcg(&lab[i]);
                         if ((l == a || l == b) && (type < 0 || mat[i] == type)) {
                             const int side = l == a ? 0 : 1;
-                            const int hv = bh[i];
+                            const int hv = __ldcg(&bh[i]);
                             bool take = false;
                             if (hv > 0 && hv > T_sh[side]) {
                                 take = true;
@@ -550,7 +594,18 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                         }
                     }
                     if (__any_sync(kFullMask, sd >= 0)) warp_add_sums(dsum, sd < 0 ? 0 : sd, sd >= 0, q0, q1, q2);
-                    // warp-aggregated append of (id, slot) to the side's threshold-bin list
+                    // the moved particles' segment positions, per side
+#pragma unroll
+                    for (int side = 0; side < 2 && seg; ++side) {
+                        const unsigned mm = __ballot_sync(kFullMask, sd == side);
+                        if (!mm) continue;
+                        const int lane = threadIdx.x & 31, ld = __ffs(mm) - 1;
+                        uint32_t pos = 0;
+                        if (lane == ld) pos = atomicAdd(&pr->mvcnt[side], (uint32_t)__popc(mm));
+                        pos = __shfl_sync(kFullMask, pos, ld) + (uint32_t)__popc(mm & lanemask_lt());
+                        if (seg && sd == side) mvl[side * mvh + pos] = (uint32_t)sp;
+                    }
+                    // warp-aggregated append of (id, segment position) to the side's threshold-bin list
 #pragma unroll
                     for (int side = 0; side < 2; ++side) {
                         const unsigned am = __ballot_sync(kFullMask, ap == side);
@@ -560,13 +615,27 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                         if (lane == ld) pos = atomicAdd(&pr->tcnt[side], (uint32_t)__popc(am));
                         pos = __shfl_sync(kFullMask, pos, ld) + (uint32_t)__popc(am & lanemask_lt());
                         if (ap == side && pos < (uint32_t)SW_TCAP)
-                            tl[side * SW_TCAP + pos] = make_uint2(id[i], (uint32_t)i);
+                            tl[side * SW_TCAP + pos] = make_uint2(id[i], (uint32_t)sp);
                     }
                 }
                 __syncthreads();
                 flush_moved(S, dsum, a, b, type);
                 if (!grid_barrier(S, nb, err)) return;
-                if (!use_list || !(idsel_sh[0] || idsel_sh[1])) continue;
+                // (the moved particles exchange their segment positions once all of the pair's moves are in)
+                auto exchange_positions = [&]() -> bool {
+                    if (!seg) return true;
+                    for (int64_t r = g0; r < (int64_t)m; r += gstride) {
+                        const uint32_t ka = __ldcg(&mvl[r]), kb = __ldcg(&mvl[mvh + r]);
+                        const uint32_t ia = __ldcg(&byl[ka]), ib = __ldcg(&byl[kb]);
+                        byl[ka] = ib;
+                        byl[kb] = ia;
+                    }
+                    return grid_barrier(S, nb, err);
+                };
+                if (!use_list || !(idsel_sh[0] || idsel_sh[1])) {
+                    if (!exchange_positions()) return;
+                    continue;
+                }
                 // -- id threshold of each listed bin: radix select in shared memory, every block
                 for (int sd = 0; sd < 2; ++sd) {
                     if (!idsel_sh[sd]) continue;
@@ -619,9 +688,11 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                         long long q0 = 0, q1 = 0, q2 = 0;
                         if (k < c) {
                             const uint2 e = __ldcg(&tl[sd * SW_TCAP + k]);
-                            const uint32_t i = e.y;
-                            if ((i / SW_THREADS) % nb == blockIdx.x && e.x <= idpre_sh[sd]) {
+                            const uint32_t i = slot_at(e.y);
+                            if ((k / SW_THREADS) % nb == blockIdx.x && e.x <= idpre_sh[sd]) {
                                 mv = true;
+                                // (append the segment position to the side's moved list)
+                                if (seg) mvl[sd * mvh + atomicAdd(&pr->mvcnt[sd], 1u)] = e.y;
                                 lab[i] = (uint8_t)(sd == 0 ? b : a);
                                 q0 = quantise(x[i], Q.lo[0], Q.hi[0], Q.s[0]);
                                 q1 = quantise(y[i], Q.lo[1], Q.hi[1], Q.s[1]);
@@ -634,6 +705,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                 __syncthreads();
                 flush_moved(S, dsum, a, b, type);
                 if (!grid_barrier(S, nb, err)) return;
+                if (!exchange_positions()) return;
             }
     }
 }
@@ -669,10 +741,10 @@ int swap_grid_blocks() {
 }
 
 // x, y, z: FP32 roundings of the positions. scratch: swap_scratch_bytes() device bytes; bh: n uint16;
-// grid from swap_grid_blocks().
+// sidx: 2n uint32 (label segments and moved lists); grid from swap_grid_blocks().
 cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const float *x, const float *y, const float *z,
                              uint8_t *lab, const uint8_t *mat, const uint32_t *id, void *scratch, uint16_t *bh,
-                             int *err, int grid, cudaStream_t s) {
+                             uint32_t *sidx, int *err, int grid, cudaStream_t s) {
     if (n <= 0 || P.K_labels < 2) return cudaSuccess;
     if (grid < 1) return cudaErrorCooperativeLaunchTooLarge;
     const size_t bytes = swap_scratch_bytes(P.K_labels, P.nmat);
@@ -688,7 +760,7 @@ cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const float *x, cons
     int K = P.K_labels, nmat = P.nmat;
     void *args[] = {(void *)&n, (void *)&Q, (void *)&alpha, (void *)&K, (void *)&nmat, (void *)&x, (void *)&y,
                     (void *)&z, (void *)&lab, (void *)&mat, (void *)&id, (void *)&bh, (void *)&S, (void *)&pairs,
-                    (void *)&tl, (void *)&err};
+                    (void *)&tl, (void *)&sidx, (void *)&err};
     return cudaLaunchCooperativeKernel((const void *)k_swap_pass, dim3(grid), dim3(SW_THREADS), args, 0, s);
 }
 
