@@ -3,7 +3,7 @@
 Integer, index and order outputs (bucket hash, sort order, neighbour counts, flags, communication
 hash, boundary set, labels after swaps, dt) must match bit for bit. FP64 state must match within
 1e-12 of each field's max-norm per step; the split path within 2e-5 per step and 1e-3 after 100 free
-steps (spec tolerances; relative to the field's max-norm over particles).
+steps (the stated tolerances, relative to the field's max-norm over particles).
 """
 import numpy as np
 import pytest
