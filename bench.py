@@ -387,7 +387,7 @@ def main():
     # the largest workload: the 64 M-particle collapse block, K = 16, swap pass every 10 steps (step 0
     # and step 10 of the timed window include one), exchange-volume fraction per step
     collapse = None
-    if args.collapse_steps > 0:
+    if args.collapse_steps > 0 and world == 1:   # one GPU only: 80 GB of state, a minute of setup
         s5 = scenes.collapse_block()
         solc = gsph.Solver.from_scene(s5, device=local, stream=stream)
         solc.step(1, stream)
