@@ -4,17 +4,17 @@
 // k_nbr_list: one lane per sorted particle i; a warp holds 32 consecutive particles of the hash order,
 //   which share most of their 27-bucket neighbourhoods. The neighbourhood is visited as 9 rows of 3
 //   buckets that are contiguous in hash order. The warp streams the union of its lanes' candidate
-//   ranges through shared memory in batches of 32 records (x shifted into a frame common to the warp),
-//   every lane tests each staged candidate against its own 3-bucket window with straight-line code
-//   into a 32-bit hit mask, and appends one entry per batch with any hit to a column-major list in
-//   global memory (entry = hit mask, batch base slot | row offset). Light on registers, so the
-//   candidate stream runs at full occupancy; no per-neighbour bookkeeping.
-// k_pair: one lane per particle walks the set bits of its entries in ascending slot order (the next
-//   neighbour's record requested while the current pair is evaluated): pair fluxes, per-particle
-//   sums, then the wall images (mirror planes,
-//   searched around the mirrored point; only particles near a wall find any), then the integration.
-//   A particle with more neighbours than the list holds finishes the rest by re-scanning its
-//   buckets in the same order, so results never depend on the list capacity.
+//   ranges through shared memory in batches of 32 (four planes x, y, z, |c|^2 in a frame common to the
+//   group), every lane tests the staged candidates two at a time with packed FP32 operations into a
+//   32-bit hit mask, and appends one entry per batch with any hit to a column-major list in global
+//   memory (entry = hit mask, batch base slot | row offset). Light on registers, so the candidate
+//   stream runs at full occupancy; no per-neighbour bookkeeping.
+// k_pair: one lane per particle walks its entries in order and the set bits of each from the highest
+//   (the next neighbour's record requested while the current pair is evaluated, no branch around the
+//   pair): pair fluxes, per-particle sums, then the wall images (mirror planes, searched around the
+//   mirrored point; only particles near a wall find any), then the integration. A particle with more
+//   neighbours than the list holds finishes the rest by re-scanning its buckets in the same order, so
+//   results never depend on the list capacity.
 //
 // Pair formulation (reading of the Gamma-SPH-ALE interface state; the paper cites it from another
 // work): transport velocity v0 = v; acoustic Riemann problem on the pair normal n (L = lower sorted
@@ -35,11 +35,12 @@
 //   1e-3 around (h_i + h_j)^2, the FP64 positions and lengths inside it.
 //
 // Split path: pair math in FP32 from FP32 records (positions relative to each particle's bucket corner,
-// so differences keep ~2^-24 * 2h), FP32 sums with Kahan compensation for the conserved quantities
-// (volume, mass, momentum, energy) and plain FP32 sums for the velocity gradient, FP64 integration of
-// the conserved variables, positions and stress (the stress rate itself in FP32). The support predicate
-// stays exact: the FP32 r^2 decides only outside a band of relative width 3e-5 around (2h)^2, inside
-// which the FP64 positions decide with the same rounding as FP64 code.
+// so differences keep ~2^-24 * 2h; the stress diagonal stored as sigma = -p I + S), FP32 sums with
+// Kahan compensation for the conserved quantities (volume, mass, momentum, energy) and plain FP32 sums
+// for the velocity gradient; the FP64 state advances by increments of v, E and S formed in FP32 and
+// added once, w, m and x in FP64. The support predicate stays exact: the FP32 r^2 decides only outside
+// a band of relative width 3e-5 around (2h)^2, inside which the FP64 positions decide with the same
+// rounding as FP64 code.
 #include <type_traits>
 
 #include "gsph_internal.cuh"
