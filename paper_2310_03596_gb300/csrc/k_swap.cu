@@ -20,6 +20,11 @@
 //   by the same radix select run over all particles with a grid barrier per digit;
 //   the fixed-point sums are updated with the moved particles (exactly, so the next pair sees the
 //   same Cg as a recomputation).
+// Before the pairs, one speculative sweep counts every pair's positive hashes at the pass-start
+// state; the pairs before the first one with positives on both sides change nothing and are skipped.
+// With 8 or more labels the same sweep groups the slots by label, and each pair then visits only its
+// two labels' slots (the segments keep their sizes since a pair's swaps are 1:1; the moved particles
+// exchange their segment positions after the pair).
 #include <cuda/atomic>
 
 #include "gsph_internal.cuh"
