@@ -11,11 +11,14 @@
 namespace gsph {
 // k_sort.cu
 cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t *hist, uint32_t *tot,
-                             int64_t n, int bits, cudaStream_t s, bool *in_alt);
+                             int64_t n, int bits, cudaStream_t s, bool *in_alt, bool first_hist);
 size_t radix_hist_words(int64_t n);
 int radix_passes(int bits);
 cudaError_t launch_hash(const DevParams &P, int64_t n, const double *x, const double *y, const double *z,
                         uint32_t *key, uint32_t *val, unsigned long long *garbage, cudaStream_t s);
+cudaError_t launch_hash_hist(const DevParams &P, int64_t n, const double *x, const double *y, const double *z,
+                             uint32_t *key, uint32_t *val, unsigned long long *garbage, uint32_t *hist, int bits,
+                             cudaStream_t s);
 // k_reorder_comm.cu
 cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint32_t *perm,
                            const State &A, double *xs, double *ys, double *zs, uint8_t *lab_s, uint8_t *mat_s,
@@ -365,12 +368,15 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     rec_event(c, PH_START, s);
     // a. bucket hash and the radix sort by hash (Sec. I)
     GSPH_CK(cudaMemsetAsync(c->garbage, 0, sizeof(unsigned long long), s));
-    GSPH_CK(launch_hash(P, n, c->A.f[FX], c->A.f[FY], c->A.f[FZ], c->key0, c->val0, c->garbage, s));
+    // (the hash writes the first sort pass's tile histogram as well)
+    GSPH_CK(launch_hash_hist(P, n, c->A.f[FX], c->A.f[FY], c->A.f[FZ], c->key0, c->val0, c->garbage, c->hist,
+                             key_bits(P.ncell), s));
     bool alt = false;
-    GSPH_CK(radix_sort_pairs(c->key0, c->val0, c->key1, c->val1, c->hist, c->tot, n, key_bits(P.ncell), s, &alt));
+    GSPH_CK(radix_sort_pairs(c->key0, c->val0, c->key1, c->val1, c->hist, c->tot, n, key_bits(P.ncell), s, &alt,
+                             true));
     c->skey = alt ? c->key1 : c->key0;
     c->perm = alt ? c->val1 : c->val0;
-    c->launches += 1 + 3 * radix_passes(key_bits(P.ncell));
+    c->launches += 3 * radix_passes(key_bits(P.ncell));
     rec_event(c, PH_SORT, s);
     // sorted view, bucket ranges, interaction records
     const bool do_swap = P.K_labels > 1 && c->cfg.swap_period > 0 && (c->step % c->cfg.swap_period) == 0;
@@ -436,7 +442,8 @@ static gsph_status enqueue_forward_pieces(gsph_ctx *c, cudaStream_t s) {
     GSPH_CK(cudaMemsetAsync(c->garbage, 0, sizeof(unsigned long long), s));
     GSPH_CK(launch_hash(P, n, c->A.f[FX], c->A.f[FY], c->A.f[FZ], c->key0, c->val0, c->garbage, s));
     bool alt = false;
-    GSPH_CK(radix_sort_pairs(c->key0, c->val0, c->key1, c->val1, c->hist, c->tot, n, key_bits(P.ncell), s, &alt));
+    GSPH_CK(radix_sort_pairs(c->key0, c->val0, c->key1, c->val1, c->hist, c->tot, n, key_bits(P.ncell), s, &alt,
+                             false));
     c->skey = alt ? c->key1 : c->key0;
     c->perm = alt ? c->val1 : c->val0;
     GSPH_CK(cudaMemsetAsync(c->cellr, 0, (size_t)P.ncell * sizeof(uint2), s));

@@ -6,7 +6,8 @@
 //   k_rs_rowscan one block per digit value: exclusive scan of its per-tile counts, digit total;
 //   k_rs_scatter reloads the tile, ranks each key among equal digits in tile order (warp match_any,
 //                per-warp counters, cross-warp prefix), scatters keys and values.
-// The ranking follows tile order, so every pass is stable and the sort is stable overall.
+// The ranking follows tile order, so every pass is stable and the sort is stable overall. In a step the
+// bucket hash (k_hash_hist) builds the first pass's tile histogram as it writes the keys.
 // Bytes per key per pass: 4 (hist) + 8 read + 8 written (scatter) + 2*4*bins/4096 (counts).
 #include <mutex>
 
@@ -178,6 +179,42 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *__res
     }
 }
 
+// Sec. I: bucket hash of every slot fused with the first sort pass's tile histogram: the same tiles
+// and item order as k_rs_hist, so the histogram is the one k_rs_hist would build from the keys written
+// here (the first digit: shift 0, mask dmask). val = slot; particles outside the grid are counted.
+template <int DIG>
+__global__ void __launch_bounds__(RS_THREADS) k_hash_hist(DevParams P, int64_t n, const double *__restrict__ x,
+                                                          const double *__restrict__ y, const double *__restrict__ z,
+                                                          uint32_t *__restrict__ key, uint32_t *__restrict__ val,
+                                                          unsigned long long *__restrict__ garbage, uint32_t dmask,
+                                                          uint32_t *__restrict__ hist, int nblk) {
+    constexpr int BINS = 1 << DIG;
+    __shared__ uint32_t sh[BINS];
+    for (int i = threadIdx.x; i < BINS; i += RS_THREADS) sh[i] = 0;
+    __syncthreads();
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    unsigned gc = 0;
+#pragma unroll 4
+    for (int r = 0; r < RS_IPT; ++r) {
+        const int64_t idx = rs_item(base, w, r, l);
+        const bool valid = idx < n;
+        uint32_t k = 0u;
+        if (valid) {
+            k = hash_of(P, x[idx], y[idx], z[idx]);
+            key[idx] = k;
+            val[idx] = (uint32_t)idx;
+        }
+        gc += (unsigned)__popc(__ballot_sync(kFullMask, valid && k == P.ncell));
+        const uint32_t d = valid ? (k & dmask) : 0xffffffffu;
+        const unsigned peers = __match_any_sync(kFullMask, d);
+        if (valid && (__ffs(peers) - 1) == l) atomicAdd(&sh[d], (uint32_t)__popc(peers));
+    }
+    if (l == 0 && gc) atomicAdd(garbage, (unsigned long long)gc);
+    __syncthreads();
+    for (int i = threadIdx.x; i < BINS; i += RS_THREADS) hist[(size_t)i * nblk + blockIdx.x] = sh[i];
+}
+
 // Sec. I: bucket hash of every slot; val = slot. Counts particles outside the grid.
 __global__ void k_hash(DevParams P, int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                        const double *__restrict__ z, uint32_t *__restrict__ key, uint32_t *__restrict__ val,
@@ -205,8 +242,9 @@ size_t radix_hist_words(int64_t n) { return (size_t)RS_BINS * (size_t)(rs_nblk(n
 // result ends in (k1, v1).
 int radix_passes(int bits) { return (bits + RS_MAX_DIGIT - 1) / RS_MAX_DIGIT; }
 
+// first_hist: the first pass's tile histogram is already in hist (k_hash_hist).
 cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t *hist,
-                             uint32_t *tot, int64_t n, int bits, cudaStream_t s, bool *in_alt) {
+                             uint32_t *tot, int64_t n, int bits, cudaStream_t s, bool *in_alt, bool first_hist) {
     *in_alt = false;
     if (n <= 0) return cudaSuccess;
     int nblk = rs_nblk(n);
@@ -217,12 +255,13 @@ cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t 
         const int shift = dig * p;
         const int width = bits - shift < dig ? bits - shift : dig;
         const uint32_t dmask = (1u << width) - 1u;
+        const bool hist_done = first_hist && p == 0;
         if (dig > 8) {
-            k_rs_hist<9><<<nblk, RS_THREADS, 0, s>>>(ki, n, shift, dmask, hist, nblk);
+            if (!hist_done) k_rs_hist<9><<<nblk, RS_THREADS, 0, s>>>(ki, n, shift, dmask, hist, nblk);
             k_rs_rowscan<<<1 << 9, 1024, 0, s>>>(hist, nblk, tot);
             k_rs_scatter<9><<<nblk, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, dmask, hist, tot, nblk);
         } else {
-            k_rs_hist<8><<<nblk, RS_THREADS, 0, s>>>(ki, n, shift, dmask, hist, nblk);
+            if (!hist_done) k_rs_hist<8><<<nblk, RS_THREADS, 0, s>>>(ki, n, shift, dmask, hist, nblk);
             k_rs_rowscan<<<1 << 8, 1024, 0, s>>>(hist, nblk, tot);
             k_rs_scatter<8><<<nblk, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, dmask, hist, tot, nblk);
         }
@@ -230,6 +269,22 @@ cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t 
         t = vi; vi = vo; vo = t;
     }
     *in_alt = (passes & 1) != 0;
+    return cudaGetLastError();
+}
+
+// The hash with the first pass's histogram of a sort by the low `bits` bits (radix_sort_pairs with
+// first_hist = true follows).
+cudaError_t launch_hash_hist(const DevParams &P, int64_t n, const double *x, const double *y, const double *z,
+                             uint32_t *key, uint32_t *val, unsigned long long *garbage, uint32_t *hist, int bits,
+                             cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int nblk = rs_nblk(n);
+    const int passes = radix_passes(bits);
+    const int dig = (bits + passes - 1) / passes;
+    const int width = bits < dig ? bits : dig;
+    const uint32_t dmask = (1u << width) - 1u;
+    if (dig > 8) k_hash_hist<9><<<nblk, RS_THREADS, 0, s>>>(P, n, x, y, z, key, val, garbage, dmask, hist, nblk);
+    else k_hash_hist<8><<<nblk, RS_THREADS, 0, s>>>(P, n, x, y, z, key, val, garbage, dmask, hist, nblk);
     return cudaGetLastError();
 }
 
@@ -271,7 +326,7 @@ extern "C" gsph_status gsph_radix_sort_pairs(uint32_t *keys, uint32_t *vals, int
     p += align256(gsph::radix_hist_words(n) * 4);
     uint32_t *tot = (uint32_t *)p;
     bool alt = false;
-    cudaError_t e = gsph::radix_sort_pairs(keys, vals, k1, v1, hist, tot, n, key_bits, s, &alt);
+    cudaError_t e = gsph::radix_sort_pairs(keys, vals, k1, v1, hist, tot, n, key_bits, s, &alt, false);
     if (e == cudaSuccess && alt) {
         e = cudaMemcpyAsync(keys, k1, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(vals, v1, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
@@ -333,7 +388,7 @@ extern "C" gsph_status gsph_radix_sort_pairs_noalloc(uint32_t *keys, uint32_t *v
     // every scratch word the sort reads is written earlier in the same call (per-tile histograms,
     // their scans, the other key/value buffer), so nothing has to be cleared between calls
     bool alt = false;
-    cudaError_t e = gsph::radix_sort_pairs(keys, vals, k1, v1, hist, tot, n, key_bits, s, &alt);
+    cudaError_t e = gsph::radix_sort_pairs(keys, vals, k1, v1, hist, tot, n, key_bits, s, &alt, false);
     if (e == cudaSuccess && alt) {
         e = cudaMemcpyAsync(keys, k1, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(vals, v1, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
