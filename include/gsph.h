@@ -297,7 +297,7 @@ gsph_status gsph_radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, int
  * race, so serialise them. Errors: INVALID_ARG (null pointers, n out of range, key_bits not in
  * 1..32), CUDA_ERROR. */
 #define GSPH_SORT_NOALLOC_MAX_N 1048576
-#define GSPH_SORT_NOALLOC_BYTES 8914944
+#define GSPH_SORT_NOALLOC_BYTES 9439232
 gsph_status gsph_radix_sort_pairs_noalloc(uint32_t *keys, uint32_t *vals, int64_t n, int32_t key_bits,
                                           void *stream);
 

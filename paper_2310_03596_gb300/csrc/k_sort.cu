@@ -2,13 +2,13 @@
 //
 // Radix sort: ceil(bits / 9) passes of equal digits of at most 9 bits (18-bit bucket hashes: two passes
 // of 9), the last digit masked to the requested bits. Each pass is three launches:
-//   k_rs_hist    per-tile digit histogram (tile = 4096 keys), warp-aggregated shared atomics;
+//   k_rs_hist    per-tile digit histogram (tile = 2048 keys), warp-aggregated shared atomics;
 //   k_rs_rowscan one block per digit value: exclusive scan of its per-tile counts, digit total;
 //   k_rs_scatter reloads the tile, ranks each key among equal digits in tile order (warp match_any,
 //                per-warp counters, cross-warp prefix), scatters keys and values.
 // The ranking follows tile order, so every pass is stable and the sort is stable overall. In a step the
 // bucket hash (k_hash_hist) builds the first pass's tile histogram as it writes the keys.
-// Bytes per key per pass: 4 (hist) + 8 read + 8 written (scatter) + 2*4*bins/4096 (counts).
+// Bytes per key per pass: 4 (hist) + 8 read + 8 written (scatter) + 2*4*bins/2048 (counts).
 #include <mutex>
 
 #include "gsph_internal.cuh"
@@ -17,7 +17,7 @@ namespace gsph {
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_IPT = 16;
+constexpr int RS_IPT = 8;
 constexpr int RS_TILE = RS_THREADS * RS_IPT;
 constexpr int RS_MAX_DIGIT = 9;
 constexpr int RS_BINS = 1 << RS_MAX_DIGIT;   // histogram rows allocated per tile (the widest digit)
