@@ -847,7 +847,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         float x1;
         R h1;
         fetch(j1, t1, p1, r1, x1, h1);
-#pragma unroll 2
+#pragma unroll 4
         for (int k = 0; k < mc; ++k) {
             const uint32_t j = j1, c = c1;
             const Pos pj = p1;
