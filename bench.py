@@ -69,19 +69,27 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def code_sha256(kernel_src: str) -> str:
+    """sha256 of a CUDA source's code: comments removed and runs of blank space collapsed, so that an
+    edit of the comments alone keeps a profile's counters valid."""
+    src = open(kernel_src).read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return hashlib.sha256(" ".join(src.split()).encode()).hexdigest()
+
+
 def _traffic_from_profile(kernel_src: str, profile: str, kernel: str):
     """dram bytes per launch of `kernel` recorded in a committed ncu summary, if it was taken on this
-    source."""
+    source's code."""
     path = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(path):
         return None
     txt = open(path).read()
-    m = re.search(r"source_sha256:\s*([0-9a-f]{16,64})", txt)
+    m = re.search(r"code_sha256:\s*([0-9a-f]{16,64})", txt)
     t = re.search(r"dram_bytes_per_launch\.%s:\s*([0-9.eE+]+)" % re.escape(kernel), txt)
     if not m or not t:
         return None
-    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    return float(t.group(1)) if sha.startswith(m.group(1)) else None
+    return float(t.group(1)) if code_sha256(kernel_src).startswith(m.group(1)) else None
 
 
 class ClockSampler:

@@ -489,11 +489,12 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                     // cannot fall below the band and the fast test needs no window check.
                     uint32_t hitm = 0u, bandm = 0u;
                     if (SPLIT) {
-                        // the sign of r^2 - R2lo (resp. R2hi) is shifted into the masks, candidate t
-                        // ending at bit 31 - t; one reversal at the end restores bit t
-                        // r^2 - R2lo = fma(mx, x, fma(my, y, fma(mz, z, |c|^2 + Kr))) on packed pairs of
-                        // candidates (each lane of a pair rounded as the scalar operation)
-                        // (variable h: the widest band of this particle's pairs, h_j <= h)
+                        // the sign of r^2 - R2lo is shifted into the hit mask, candidate t ending at bit
+                        // 31 - t; one reversal at the end restores bit t. r^2 - R2lo =
+                        // fma(mx, x, fma(my, y, fma(mz, z, |c|^2 + Kr))) on packed pairs of candidates
+                        // (each lane of a pair rounded as the scalar operation); the band below R2hi is
+                        // found from the smallest unsigned value of r^2 - R2lo (variable h: the widest
+                        // band of this particle's pairs, h_j <= h)
                         const float hw = hif + (float)P.h;
                         const uint32_t wbits = VARH ? __float_as_uint((P.f_vhi - P.f_vlo) * hw * hw)
                                                     : __float_as_uint(P.f_R2hi - P.f_R2lo);

@@ -62,3 +62,19 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference" and line["metric"] == "particle-steps/sec"
     assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_profile_traffic_follows_the_code_not_the_comments(tmp_path, monkeypatch):
+    import bench
+    src = tmp_path / "k.cu"
+    src.write_text("// header\\n__global__ void k() { int a = 1; /* note */ }\\n")
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    h = bench.code_sha256(str(src))[:16]
+    (prof / "p.md").write_text(f"code_sha256: {h}\\ndram_bytes_per_launch.k: 1234\\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._traffic_from_profile(str(src), "p.md", "k") == 1234.0
+    src.write_text("// another header\\n__global__ void k() {  int a = 1;  }\\n")      # comments only
+    assert bench._traffic_from_profile(str(src), "p.md", "k") == 1234.0
+    src.write_text("__global__ void k() { int a = 2; }\\n")                              # code changed
+    assert bench._traffic_from_profile(str(src), "p.md", "k") is None
