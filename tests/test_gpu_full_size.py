@@ -1,6 +1,7 @@
 """Full-size parity in the benchmark's launch configuration (FP32 split, diagnostics off) on the Taylor
 bar (1,607,680 particles, K = 4, swap and communication hash every step), the projectile on the plate
-(4,565,752 particles, two materials, K = 8) and the collapse block (64,000,000 particles, K = 16).
+(4,565,752 particles, two materials, K = 8) and the collapse block (64,000,000 particles, K = 16), and
+the bench's variant lines at their sizes (the FP64 path, MUSCL, the two-resolution bar).
 
 Integer outputs are compared on every particle; the new floating-point state on a random sample of
 particles whose rates and integration the oracle computes one by one.
@@ -24,12 +25,12 @@ def _built():
     __graft_entry__.build()
 
 
-def _full_size_step(s, before, nsample=3000, seed=17):
+def _full_size_step(s, before, nsample=3000, seed=17, precision=gsph.FP32_SPLIT, tol=2e-5):
     """`before` steps on the GPU, then one step compared with the oracle: hash, sort, swap pass (when
     the step index is a multiple of the period), communication hash on every particle; the rates and
     integration of a sample (plus particles in wall contact) one by one."""
     P = orc.params_of(s)
-    sol = gsph.Solver.from_scene(s, precision=gsph.FP32_SPLIT)
+    sol = gsph.Solver.from_scene(s, precision=precision)
     try:
         sol.step(before)
         st = orc.OracleState.from_arrays(sol.state())
@@ -70,7 +71,7 @@ def _full_size_step(s, before, nsample=3000, seed=17):
         for f in STATE:
             gv, ov = g[f][sample], getattr(sub, f)
             scale = max(max(np.abs(getattr(st, c)).max() for c in group.get(f, (f,))), np.abs(ov).max(), 1e-300)
-            assert np.abs(gv - ov).max() <= 2e-5 * scale, f
+            assert np.abs(gv - ov).max() <= tol * scale, f
     finally:
         sol.close()
 
@@ -78,6 +79,23 @@ def _full_size_step(s, before, nsample=3000, seed=17):
 def test_taylor_bar_full_size_step():
     # 1,607,680 particles, K = 4, swaps every step; step 3: the impact has started
     _full_size_step(scenes.taylor_bar(), 3)
+
+
+def test_taylor_bar_full_size_fp64_step():
+    # the FP64 path at full size: 1e-12 of each field's max-norm
+    _full_size_step(scenes.taylor_bar(), 2, seed=21, precision=gsph.FP64, tol=1e-12)
+
+
+def test_taylor_bar_full_size_muscl_step():
+    # the bench's MUSCL line: gradient pass and reconstructed fluxes at full size
+    s = scenes.taylor_bar()
+    s.reconstruction = 1
+    _full_size_step(s, 3, seed=22)
+
+
+def test_graded_bar_full_size_step():
+    # the bench's varying-size line: 553,600 particles of two sizes
+    _full_size_step(scenes.graded_bar(), 3, seed=23)
 
 
 def test_projectile_plate_full_size_step():
