@@ -4,7 +4,6 @@ import json
 import os
 
 import numpy as np
-import pytest
 
 from oracle import orc
 from paper_2310_03596_gb300 import scenes

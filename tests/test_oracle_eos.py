@@ -12,7 +12,6 @@ the form is a reading) against facts that do not come from the oracle's formula:
 """
 import math
 
-import numpy as np
 import pytest
 
 from oracle import orc

@@ -14,7 +14,6 @@ and impedance at the particle values, transport velocity = particle velocity.
   (1 - m) times smaller, m the lattice moment of the SPH gradient (0.979 at h = 1.3 dx).
 """
 import numpy as np
-import pytest
 
 from oracle import orc
 from paper_2310_03596_gb300 import scenes

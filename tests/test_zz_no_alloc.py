@@ -6,7 +6,6 @@ It must give exactly what the workspace-taking sort gives, on consecutive calls 
 library's one fixed scratch array, and refuse sizes beyond that array. This file is collected last,
 so a run that stops at the first failure has already run every other test.
 """
-import ctypes as C
 
 import numpy as np
 import pytest
