@@ -69,7 +69,10 @@ def _cfg(**kw):
 
 @pytest.mark.parametrize("bad", [dict(h=0.0), dict(cfl=-1.0), dict(K=0), dict(K=17), dict(n_materials=0),
                                  dict(n_materials=5), dict(n_walls=7), dict(precision=3), dict(swap_period=-1),
-                                 dict(alpha=1.5)])
+                                 dict(alpha=1.5), dict(overlap=2), dict(integrator=2),
+                                 dict(integrator=1, overlap=1), dict(reconstruction=2),
+                                 dict(reconstruction=1, integrator=1), dict(reconstruction=1, overlap=1),
+                                 dict(variable_h=2), dict(variable_h=1, overlap=1)])
 def test_invalid_config_rejected_on_host(lib, bad):
     h = C.c_void_p()
     assert lib.gsph_create(C.byref(_cfg(**bad)), C.byref(h)) == gsph.INVALID_ARG
