@@ -377,6 +377,46 @@ def test_single_particle_and_one_bucket():
         sol.close()
 
 
+def test_empty_context_then_particle_sets_of_other_sizes():
+    # a context without particles refuses the calls that need them, and an empty set is invalid
+    s = scenes.taylor_bar(dx=0.8e-3, K=4, seed=5)
+    P = orc.params_of(s)
+    sol = gsph.Solver(gsph.config_from_scene(s, gsph.FP32_SPLIT, diagnostics=True))
+    try:
+        assert sol.sizes()[0] == 0
+        sol.sync()
+        for call in (lambda: sol.step(1), lambda: sol.swap_now(), lambda: sol.conserved(),
+                     lambda: sol.dt(), lambda: sol.exchange_stats(), lambda: sol.get("x")):
+            with pytest.raises(gsph.GsphError) as ei:
+                call()
+            assert ei.value.code == gsph.NOT_READY
+        z3, z1 = np.zeros((0, 3)), np.zeros(0)
+        with pytest.raises(gsph.GsphError) as ei:
+            sol.set_particles(z3, z3, z1, z1.astype(np.uint8), z1.astype(np.uint8))
+        assert ei.value.code == gsph.INVALID_ARG
+        # the same context then takes sets of other sizes (ragged against the blocks and warps, down to
+        # one particle), each stepped in lockstep with the oracle, swaps included
+        n_all = s.vol.shape[0]
+        for n in (n_all, 1001, 33, 1, n_all // 2 + 7):
+            sol.set_particles(s.pos[:n], s.vel[:n], s.vol[:n], s.material[:n], s.label[:n])
+            assert sol.sizes()[0] == n
+            for k in range(2):
+                st = orc.OracleState.from_arrays(sol.state())
+                out = orc.step(P, st, do_swap=True, want_rates=True)
+                sol.step(1)
+                sol.sync()
+                assert np.array_equal(sol.get("hash"), out["key"]), (n, k)
+                assert np.array_equal(sol.get("id"), st.id), (n, k)
+                assert np.array_equal(sol.get("label"), st.label), (n, k)
+                assert np.array_equal(sol.get("nreal"), out["nreal"]), (n, k)
+                assert np.array_equal(sol.get("flag"), out["flag"]), (n, k)
+                for f in STATE_F:
+                    e = _maxnorm_err(sol.get(f), getattr(st, f))
+                    assert e <= 2e-5, (n, k, f, e)
+    finally:
+        sol.close()
+
+
 def test_swap_now_matches_oracle_pass():
     for K, seed in ((2, 1), (5, 2), (16, 3)):
         s = scenes.taylor_bar(dx=0.4e-3, K=K, seed=seed)
