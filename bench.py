@@ -30,11 +30,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Algorithmic FP operations of one ordered pair evaluation: the pair flux (160: distance, normal,
-# kernel gradient, normal velocities and tractions, acoustic Riemann state, interface state, mass,
-# momentum and energy fluxes) plus the per-particle accumulation of volume, mass, momentum, energy
-# and velocity-gradient rates (60), counted on the oracle's pair function as written.
-FLOPS_PER_PAIR = 220
+# Algorithmic FP operations (+, -, *, /, sqrt) of one ordered pair evaluation: the pair flux (distance,
+# normal, kernel gradient, normal velocities and tractions, acoustic Riemann state, interface state, mass,
+# momentum and energy fluxes) plus one end's accumulation of its volume, mass, momentum, energy and
+# velocity-gradient rates, as counted by running the oracle's pair function on a counting scalar type
+# (a CPU test keeps the two equal).
+FLOPS_PER_PAIR = 233
 LINK_GBPS = 900.0   # modelled inter-GPU link bandwidth per direction (NVLink 5 class), for the overlap report
 SMS, FP32_LANES = 152, 128
 

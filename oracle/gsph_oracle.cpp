@@ -8,8 +8,11 @@
 // Pins (tests/test_oracle_*.py): brute-force neighbour sets equal the bucket search; 80 interior
 // neighbours on the jittered lattice; kernel closed form, unit integral and lattice sum; Riemann
 // special cases; antisymmetry and conservation of mass, momentum and energy; uniform-state patch test;
-// linear-velocity gradient; rigid-rotation stress rate; radial return; uniaxial wave speed; hand-worked
-// balancing hashes; label counts invariant under swaps; forward derivative against central differences.
+// linear-velocity gradient; rigid-rotation stress rate; radial return; uniaxial wave speed; first law of
+// the energy flux (pressure work); time step of the fastest particle; fixed-point Cg on exact grid points;
+// hand-worked balancing hashes, single-type and two-type (biased Cg') swaps; label counts invariant under
+// swaps; forward derivative against central differences. Every decision (hash, neighbour predicate,
+// time step, Cg, balancing hash) is taken in FP64.
 #include "gsph_oracle.h"
 
 #include <algorithm>
@@ -43,6 +46,24 @@ inline bool operator>(const Dual &a, const Dual &b) { return a.v > b.v; }
 inline double val(double x) { return x; }
 inline double val(const Dual &x) { return x.v; }
 using std::sqrt;
+
+// Operation-counting scalar: each +, -, *, / and sqrt adds one to the counter (negation and
+// comparisons add nothing). Run through the pair functions it gives the algorithmic FLOP count of one
+// ordered pair interaction as written here.
+thread_local int64_t g_flops = 0;
+struct Count {
+    double v;
+    Count() : v(0) {}
+    Count(double x) : v(x) {}
+};
+inline Count operator+(const Count &a, const Count &b) { ++g_flops; return Count(a.v + b.v); }
+inline Count operator-(const Count &a, const Count &b) { ++g_flops; return Count(a.v - b.v); }
+inline Count operator-(const Count &a) { return Count(-a.v); }
+inline Count operator*(const Count &a, const Count &b) { ++g_flops; return Count(a.v * b.v); }
+inline Count operator/(const Count &a, const Count &b) { ++g_flops; return Count(a.v / b.v); }
+inline Count sqrt(const Count &a) { ++g_flops; return Count(std::sqrt(a.v)); }
+inline bool operator>(const Count &a, const Count &b) { return a.v > b.v; }
+inline double val(const Count &x) { return x.v; }
 
 template <class T> struct Mat {
     T rho0, K, G, Y, c0, s, gamma0;
@@ -484,6 +505,22 @@ void reconstruct(const Prim<T> &L, const T *GL, const Prim<T> &R, const T *GR, c
     Rs.p = T(0.0);
 }
 
+// Adds one real pair to the rates r of particle i (Sec. II step f): volume rate from the transport
+// velocities, the mass, momentum and energy fluxes with the orientation sign of i, and the velocity
+// gradient L_i += w_j (v_j - v_i) (x) grad_i W_ij with grad_i W_ij = a n_{i->j}.
+template <class T>
+inline void accumulate_real(T *r, const Prim<T> &pi, const Prim<T> &pj, const PairOut<T> &o, bool i_left) {
+    double sg = i_left ? -1.0 : 1.0;
+    r[0] = r[0] + pi.w * pj.w * o.a * (o.uR - o.uL);
+    r[1] = r[1] + sg * o.Fm;
+    for (int k = 0; k < 3; ++k) r[2 + k] = r[2 + k] + sg * o.Fmv[k];
+    r[5] = r[5] + sg * o.Fe;
+    T nij[3];
+    for (int k = 0; k < 3; ++k) nij[k] = i_left ? o.n[k] : -o.n[k];
+    for (int u = 0; u < 3; ++u)
+        for (int v = 0; v < 3; ++v) r[6 + 3 * u + v] = r[6 + 3 * u + v] + pj.w * (pj.v[u] - pi.v[u]) * o.a * nij[v];
+}
+
 // Interaction loop (Sec. II step f): rates of particle i from all its real and image neighbours.
 template <class T>
 void rates_of(const orc_params *P, const StateT<T> &s, const Mat<T> *mats, const Buckets &b,
@@ -520,14 +557,7 @@ void rates_of(const orc_params *P, const StateT<T> &s, const Mat<T> *mats, const
             } else {
                 pair_flux(d, PL, PR, hij(j), o);
             }
-            double sg = i_left ? -1.0 : 1.0;
-            r[0] = r[0] + pi.w * pj.w * o.a * (o.uR - o.uL);
-            r[1] = r[1] + sg * o.Fm;
-            for (int k = 0; k < 3; ++k) r[2 + k] = r[2 + k] + sg * o.Fmv[k];
-            r[5] = r[5] + sg * o.Fe;
-            T nij[3];
-            for (int k = 0; k < 3; ++k) nij[k] = i_left ? o.n[k] : -o.n[k];
-            add_L(pj.w, pj.v, o.a, nij);
+            accumulate_real(r, pi, pj, o, i_left);
         },
         [&](int k, int64_t j) {
             ++ci;
@@ -601,47 +631,24 @@ void rates_all(const orc_params *P, const StateT<T> &s, const Mat<T> *mats, int6
     }
 }
 
-// CFL signal speed c + |v| of one particle (reading: evaluated in FP32, each operation correctly
-// rounded, from the FP32 roundings of m, w and v; the time step only needs a few digits, and the
-// FP32 sequence is cheap on GPUs whose FP64 units are scarce).
-float signal_speed(const orc_params *P, const orc_state *S, int64_t i) {
+// CFL signal speed c + |v| of one particle in FP64 (Sec. II step g; reading: the CFL condition on the
+// largest signal speed). rho = m / w, |v|^2 with each product and sum rounded; linear EOS:
+// c = sqrt(M / rho) with the longitudinal modulus M = K + 4G/3; Mie-Gruneisen: c = sqrt(c_b^2 + (4G/3) / rho)
+// with c_b^2 from eos_of at e = E - |v|^2 / 2.
+double signal_speed(const orc_params *P, const orc_state *S, int64_t i) {
     const orc_material &M = P->mat[S->mat[i]];
-    float rho = (float)S->m[i] / (float)S->w[i];
-    float vx = (float)S->vx[i], vy = (float)S->vy[i], vz = (float)S->vz[i];
-    float a = vx * vx;
-    float b = vy * vy;
-    float d = vz * vz;
-    float v2 = (a + b) + d;
-    float c;
+    double rho = S->m[i] / S->w[i];
+    double v2 = dist2(S->vx[i], S->vy[i], S->vz[i]);
+    double c;
     if (M.eos == 0) {
-        float Mmod = (float)(M.K + 4.0 * M.G / 3.0);
+        double Mmod = M.K + 4.0 * M.G / 3.0;
         c = std::sqrt(Mmod / rho);
     } else {
-        // the Mie-Gruneisen sound speed of eos_of in FP32, operation by operation, from the FP32
-        // roundings of the material constants, m, w, v and E
-        float rho0 = (float)M.rho0, c0 = (float)M.c0, sm1 = (float)(M.s - 1.0), g0 = (float)M.gamma0;
-        float e = (float)S->E[i] - 0.5f * v2;
-        float mu = rho / rho0 - 1.0f;
-        float k0 = (rho0 * c0) * c0;
-        float pH, dpH;
-        if (mu > 0.0f) {
-            float D = 1.0f - sm1 * mu;
-            float D2 = D * D;
-            float q = 1.0f + mu;
-            pH = ((k0 * mu) * q) / D2;
-            dpH = (k0 * ((1.0f + 2.0f * mu) * D + (2.0f * sm1) * (mu * q))) / (D2 * D);
-        } else {
-            pH = k0 * mu;
-            dpH = k0;
-        }
-        float q = 1.0f + mu;
-        float eH = (pH * mu) / ((2.0f * rho0) * q);
-        float deH = ((dpH * mu) * q + pH) / (((2.0f * rho0) * q) * q);
-        float gr = g0 * rho0;
-        float p = pH + gr * (e - eH);
-        float cb2 = (dpH - gr * deH) / rho0 + (p * gr) / (rho * rho);
-        if (!(cb2 > 0.0f)) cb2 = 0.0f;
-        float G43 = (float)(4.0 * M.G / 3.0);
+        Mat<double> mm[ORC_MAX_MAT];
+        mats_of(P, mm);
+        double p, cb2;
+        eos_of(mm[S->mat[i]], rho, S->E[i] - v2 / 2.0, p, cb2);
+        double G43 = 4.0 * M.G / 3.0;
         c = std::sqrt(cb2 + G43 / rho);
     }
     return c + std::sqrt(v2);
@@ -706,38 +713,35 @@ void integrate_one(const orc_params *P, StateT<T> &s, const Mat<T> *mats, int64_
     s.S[3][i] = Sn[0][1]; s.S[4][i] = Sn[0][2]; s.S[5][i] = Sn[1][2];
 }
 
-// Fixed-point position quantum for the centre of gravity (Sec. III.A; reading): the FP32 rounding of a
-// position, clamped to the FP32 grid box [lo, lo + ext], is scaled by s = 2^24 / ext (FP32) and
-// truncated, so every quantised coordinate is an exact integer below 2^24 + 1 and the per-label sums
-// are exact in int64. Cg = lo + (sum / count) * (1 / s) in FP64.
+// Fixed-point position for the centre of gravity (Sec. III.A; reading): per axis q = nearest integer
+// (ties to even) to (x - lo) * s with s = 2^32 / L, L = dims * 2h the extent of the bucket grid, clamped
+// to [0, 2^32 - 1] (NaN gives 0). The per-label sums of q are exact in int64 (at most 2^26 particles),
+// and Cg = lo + (sum / count) * (L 2^-32).
 struct Quant {
-    float lo[3], hi[3], s[3];
-    double inv[3];
+    double lo[3], s[3], step[3];
 };
 Quant quant_of(const orc_params *P) {
     Quant q;
     double cell = 2.0 * P->h;
     for (int a = 0; a < 3; ++a) {
         double ext = (double)P->dims[a] * cell;
-        q.lo[a] = (float)P->lo[a];
-        q.hi[a] = (float)(P->lo[a] + ext);
-        q.s[a] = (float)(16777216.0 / ext);
-        q.inv[a] = 1.0 / (double)q.s[a];
+        q.lo[a] = P->lo[a];
+        q.s[a] = 4294967296.0 / ext;
+        q.step[a] = ext * 0x1p-32;
     }
     return q;
 }
 inline int64_t quantise(const Quant &q, int a, double x) {
-    float xf = (float)x;
-    float xc = std::fmin(std::fmax(xf, q.lo[a]), q.hi[a]);   // NaN goes to lo
-    float d = xc - q.lo[a];
-    float t = d * q.s[a];
-    return (int64_t)t;
+    double t = (x - q.lo[a]) * q.s[a];
+    if (!(t > 0.0)) return 0;
+    if (t >= 4294967295.0) return 4294967295LL;
+    return (int64_t)std::nearbyint(t);
 }
 
 void cg_from_sums(const Quant &q, const int64_t sum[3], int64_t cnt, double cg[3]) {
     for (int a = 0; a < 3; ++a) {
         double mean = (double)sum[a] / (double)cnt;
-        cg[a] = (double)q.lo[a] + mean * q.inv[a];
+        cg[a] = q.lo[a] + mean * q.step[a];
     }
 }
 
@@ -747,6 +751,25 @@ void cg_from_sums(const Quant &q, const int64_t sum[3], int64_t cnt, double cg[3
 // C entry points
 // =============================================================================================
 extern "C" {
+
+int64_t orc_flops_per_pair(void) {
+    // one ordered pair of two particles in a generic state: the pair flux and its accumulation into the
+    // 15 rates of one end (first-order Riemann states, uniform h)
+    Prim<Count> L, R;
+    const double vl[3] = {12.0, -3.0, 5.0}, vr[3] = {-7.0, 4.0, 1.0};
+    const double sl[6] = {1e7, -2e7, 1e7, 3e6, -4e6, 5e6}, sr[6] = {-3e6, 1e6, 2e6, -1e6, 2e6, 7e6};
+    for (int k = 0; k < 3; ++k) { L.v[k] = vl[k]; R.v[k] = vr[k]; }
+    for (int k = 0; k < 6; ++k) { L.S[k] = sl[k]; R.S[k] = sr[k]; }
+    L.rho = 2700.0; R.rho = 2710.0; L.p = 1e8; R.p = 2e8; L.Z = 1.7e7; R.Z = 1.71e7;
+    L.E = 1e4; R.E = 2e4; L.w = 1e-9; R.w = 1.01e-9;
+    Count d[3] = {3e-4, -2e-4, 5e-4};
+    Count r[ORC_NRATE];
+    PairOut<Count> o;
+    g_flops = 0;
+    pair_flux(d, L, R, 1.3e-3, o);
+    accumulate_real(r, L, R, o, true);
+    return g_flops;
+}
 
 void orc_eos(const orc_params *P, int32_t mat, double rho, double e, double *p, double *cb2) {
     Mat<double> m[ORC_MAX_MAT];
@@ -839,13 +862,13 @@ void orc_rates(const orc_params *P, const orc_state *S, int64_t nsub, const int6
 }
 
 double orc_dt(const orc_params *P, const orc_state *S) {
-    float mx = 0.0f;
-    if (P->variable_h) {   // dt = cfl min_i h_i / s_i, from the FP32 quotients s_i / h_i
-        for (int64_t i = 0; i < S->n; ++i) mx = std::max(mx, signal_speed(P, S, i) / (float)S->h[i]);
-        return P->cfl / (double)mx;
+    double mx = 0.0;
+    if (P->variable_h) {   // dt = cfl min_i h_i / s_i = cfl / max_i (s_i / h_i)
+        for (int64_t i = 0; i < S->n; ++i) mx = std::max(mx, signal_speed(P, S, i) / S->h[i]);
+        return P->cfl / mx;
     }
     for (int64_t i = 0; i < S->n; ++i) mx = std::max(mx, signal_speed(P, S, i));
-    return (P->cfl * P->h) / (double)mx;
+    return (P->cfl * P->h) / mx;
 }
 
 void orc_integrate(const orc_params *P, orc_state *S, const double *rates, double dt) {
@@ -909,30 +932,26 @@ int64_t orc_cg(const orc_params *P, int64_t n, const double *x, const double *y,
 }
 
 int32_t orc_balancing_hash(const double own[3], const double oth[3], const double p[3]) {
-    // Per label pair (FP64): middle M of the Cg segment, unit direction u from the own Cg to the
-    // other, scale 1000 / (half the Cg distance).
+    // Sec. III.A in FP64: middle M of the Cg segment, d from the own Cg to the other, half-distance ell;
+    // t = (p - M) . d / |d| is the signed distance of the projection past the middle.
     double M[3], d[3];
     for (int a = 0; a < 3; ++a) {
         M[a] = (own[a] + oth[a]) * 0.5;
         d[a] = oth[a] - own[a];
     }
     double dn = std::sqrt(dist2(d[0], d[1], d[2]));
-    if (!(dn > 0.0)) return 0;
+    if (!(dn > 0.0)) return 0;                       // coincident Cgs: nothing to balance
     double ell = dn * 0.5;
-    float u[3] = {(float)(d[0] / dn), (float)(d[1] / dn), (float)(d[2] / dn)};
-    float scale = (float)(1000.0 / ell);
-    // Per particle (reading: FP32 arithmetic, each operation rounded, on the FP32 roundings of the
-    // position and of the middle): signed distance t of the projection past the middle.
-    float Mf[3] = {(float)M[0], (float)M[1], (float)M[2]};
-    float e0 = (float)p[0] - Mf[0], e1 = (float)p[1] - Mf[1], e2 = (float)p[2] - Mf[2];
-    float a0 = e0 * u[0];
-    float a1 = e1 * u[1];
-    float a2 = e2 * u[2];
-    float t = (a0 + a1) + a2;
-    if (!(t > 0.0f)) return 0;                       // own side of the middle: not a swap candidate
-    float k = std::floor(t * scale);                 // proportional to the distance past the middle
-    if (k >= (float)ORC_HASH_MAX) return ORC_HASH_MAX;   // at or beyond the other Cg
-    if (k < 1.0f) return 1;
+    double e0 = p[0] - M[0], e1 = p[1] - M[1], e2 = p[2] - M[2];
+    double a0 = e0 * d[0];
+    double a1 = e1 * d[1];
+    double a2 = e2 * d[2];
+    double t = ((a0 + a1) + a2) / dn;
+    if (!(t > 0.0)) return 0;                        // own side of the middle: not a swap candidate
+    if (t >= ell) return ORC_HASH_MAX;               // at or beyond the other Cg
+    double k = std::floor(1000.0 * t / ell);         // proportional to the distance past the middle
+    if (k < 1.0) return 1;
+    if (k >= (double)ORC_HASH_MAX) return ORC_HASH_MAX;
     return (int32_t)k;
 }
 

@@ -64,8 +64,7 @@ typedef struct {
                                         reading): pair smoothing length h_ij = (h_i + h_j) / 2, support
                                         r_ij < 2 h_ij, i.e. r^2 < (h_i + h_j)^2 each operation rounded;
                                         buckets keep the side 2h (h = the largest h_i); time step
-                                        dt = cfl / max_i fl32(s_i / fl32(h_i)) with s_i the FP32 signal
-                                        speed */
+                                        dt = cfl / max_i (s_i / h_i) with s_i the FP64 signal speed */
 } orc_params;
 
 typedef struct {
@@ -111,6 +110,11 @@ void orc_gradients(const orc_params *P, const orc_state *S, double *grads);
  * energy e (with the cut-off) and the square of the bulk sound speed (isentropic derivative of the
  * uncut pressure, floored at 0). */
 void orc_eos(const orc_params *P, int32_t mat, double rho, double e, double *p, double *cb2);
+
+/* Floating-point operations (+, -, *, /, sqrt) of one ordered pair interaction as the oracle writes it:
+ * the pair flux and its accumulation into one end's 15 rates, counted by running them on a counting
+ * scalar type. */
+int64_t orc_flops_per_pair(void);
 /* Time step from the current state: CFL * h / max_i (c_i + |v_i|). */
 double orc_dt(const orc_params *P, const orc_state *S);
 /* Sec. II step g: forward Euler update of the state (in place) from the rates. */

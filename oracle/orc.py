@@ -103,6 +103,8 @@ def lib():
             L.orc_gradients.argtypes = [P(Params), P(StateC), _DP]
             L.orc_forward_gradient.argtypes = [P(Params), P(StateC), C.c_int32, _DP, C.c_int64, _U32P, _DP]
             L.orc_forward_gradient.restype = C.c_double
+            L.orc_flops_per_pair.argtypes = []
+            L.orc_flops_per_pair.restype = C.c_int64
             _lib = L
     return _lib
 
@@ -359,6 +361,11 @@ def step(P: Params, st: OracleState, do_swap: bool = False, want_rates: bool = F
                    _ptr(r, C.c_double) if r is not None else None, _ptr(dtv, C.c_double))
     return {"key": key, "comm": comm, "flag": flag, "count": cnt, "nreal": nr, "nimage": ni,
             "rates": r, "dt": float(dtv[0])}
+
+
+def flops_per_pair() -> int:
+    """+, -, *, / and sqrt of one ordered pair (flux and one end's accumulation), counted by the oracle."""
+    return int(lib().orc_flops_per_pair())
 
 
 def kernel_w(r: float, h: float) -> float:

@@ -78,3 +78,10 @@ def test_profile_traffic_follows_the_code_not_the_comments(tmp_path, monkeypatch
     assert bench._traffic_from_profile(str(src), "p.md", "k") == 1234.0
     src.write_text("__global__ void k() { int a = 2; }\\n")                              # code changed
     assert bench._traffic_from_profile(str(src), "p.md", "k") is None
+
+
+def test_flops_per_pair_is_the_oracles_count():
+    # the roofline's FLOP unit equals the operations of one ordered pair in the oracle's pair function
+    # (flux and one end's accumulation), counted on a counting scalar type
+    from oracle import orc
+    assert bench.FLOPS_PER_PAIR == orc.flops_per_pair()

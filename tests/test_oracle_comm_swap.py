@@ -66,14 +66,36 @@ def test_boundary_lists_are_the_comm_hash_sort_order():
 def test_cg_is_the_mean_to_the_fixed_point_quantum():
     s = scenes.taylor_bar(dx=1e-3, K=3)
     P = orc.params_of(s)
+    step = np.array(s.grid_dims) * 2 * s.h / 2.0 ** 32      # the 32-bit fixed-point quantum
     for lab in range(3):
         cg, cnt = orc.cg(P, *s.pos.T, s.label, s.material, lab)
         sel = s.label == lab
         assert cnt == sel.sum()
-        # quantum of the 24-bit fixed point plus the FP32 rounding of the positions
-        q = np.array(s.grid_dims) * 2 * s.h / 2.0 ** 24
-        r = 2.0 ** -24 * np.abs(s.pos[sel]).max(axis=0)
-        assert np.all(np.abs(cg - s.pos[sel].mean(axis=0)) <= q + r + 1e-15)
+        # each quantised coordinate lies within half a quantum (plus the FP64 rounding of the scaled
+        # offset, 2^-20 quanta at most) of the position, so their mean does as well
+        mean = np.array([np.mean(s.pos[sel][:, a].astype(np.longdouble)) for a in range(3)], dtype=np.float64)
+        assert np.all(np.abs(cg - mean) <= step * (0.5 + 2.0 ** -19) + 4e-16 * np.abs(mean))
+
+
+def test_cg_quantum_on_exact_grid_points():
+    # a grid of extent 2^-4 at the origin: the quantum is 2^-36 and every position below is exact.
+    # Multiples of the quantum give their own value back, half-way points tie to the even neighbour,
+    # and positions outside the grid clamp to [0, 2^32 - 1] quanta
+    s = scenes.taylor_bar(dx=1e-3, K=1)
+    s.grid_lo, s.h, s.grid_dims = (0.0, 0.0, 0.0), 2.0 ** -8, (8, 8, 8)
+    P = orc.params_of(s)
+    q = 2.0 ** -36
+    one = np.zeros(1, np.uint8)
+    cases = [(0.0, 0), (q, 1), (7 * q, 7), ((2 ** 20 + 3) * q, 2 ** 20 + 3), (2.5 * q, 2), (3.5 * q, 4),
+             ((2 ** 31 + 0.5) * q, 2 ** 31), ((2 ** 32 - 2) * q, 2 ** 32 - 2), (-1.0, 0), (1.0, 2 ** 32 - 1),
+             (float("nan"), 0)]
+    for xv, k in cases:
+        cg, cnt = orc.cg(P, np.array([xv]), np.array([0.01]), np.array([0.01]), one, one, 0)
+        assert cnt == 1 and cg[0] == k * q, (xv, k, cg[0] / q)
+    # the sum of several is exact: the mean of 0, 1 and 2^32 - 2 quanta
+    xs = np.array([0.0, q, (2 ** 32 - 2) * q])
+    cg, _ = orc.cg(P, xs, np.full(3, 0.01), np.full(3, 0.01), np.zeros(3, np.uint8), np.zeros(3, np.uint8), 0)
+    assert cg[0] == ((2 ** 32 - 1) / 3.0) * q
 
 
 def test_balancing_hash_hand_worked():
@@ -164,3 +186,25 @@ def test_swap_selection_by_brute_force_tiny():
     want[pick(b)] = 0
     orc.swap_pass(P, st)
     assert np.array_equal(st.label, want)
+
+
+def test_swap_two_types_biased_cg_hand_worked():
+    # Sec. III.B's Cg' = alpha Cg_all + (1 - alpha) Cg_type, with Cg_all per label: a two-type,
+    # two-label example whose outcome changes under the other readings (see the fixture)
+    with open(os.path.join(GOLDEN, "swap_two_types_cg_prime.json")) as f:
+        g = json.load(f)
+    s = scenes.cube_impact(n_side=2)
+    s.h, s.grid_lo, s.grid_dims, s.K, s.alpha = g["h"], tuple(g["grid_lo"]), tuple(g["grid_dims"]), 2, g["alpha"]
+    s.materials = [s.materials[0], s.materials[0]]
+    P = orc.params_of(s)
+    assert P.nmat == 2
+    n = len(g["x"])
+    st = orc.OracleState(n)
+    st.x[:] = g["x"]
+    st.mat[:] = g["type"]
+    st.label[:] = g["label_in"]
+    st.id[:] = np.arange(n)
+    moved, pairs = orc.swap_pass(P, st)
+    assert moved == g["moved"] and pairs[0, 1] == 2
+    assert st.label.tolist() == g["label_out"]
+    assert g["label_out"] != g["label_out_other_readings"]

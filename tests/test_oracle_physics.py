@@ -137,6 +137,36 @@ def test_wall_conserves_mass_energy_and_tangential_momentum():
 
 
 # ----------------------------------------------------------------------------------- patch test
+def test_energy_flux_first_law_pressure_work():
+    # First law for the pair energy flux: with a uniform pressure p (sigma = -p I), random velocities
+    # and one impedance everywhere, the Riemann mass flux vanishes, and the heating
+    # m de/dt = d(mE)/dt - v . d(mv)/dt - (E - |v|^2) dm/dt changes with p by exactly the pressure
+    # work -p dw/dt, particle by particle. The two runs keep the density (so the impedance) and change
+    # the reference density, which sets p = K (rho / rho0 - 1).
+    s, P, st = _lattice_state(n_side=7, jitter=0.01)
+    rng = np.random.default_rng(31)
+    st.vx[:] = rng.normal(0, 20.0, st.n)
+    st.vy[:] = rng.normal(0, 20.0, st.n)
+    st.vz[:] = rng.normal(0, 20.0, st.n)
+    st.E[:] = 5e3 + 0.5 * (st.vx ** 2 + st.vy ** 2 + st.vz ** 2)
+    v = np.stack([st.vx, st.vy, st.vz], 1)
+
+    def heating(rho0):
+        P.mat[0].rho0 = rho0
+        r, _, _ = orc.rates(P, st)
+        return r[:, 5] - np.einsum("ij,ij->i", v, r[:, 2:5]) - (st.E - (v * v).sum(1)) * r[:, 1], r
+
+    h0, r0 = heating(RHO0)                   # p = 0
+    rho1 = RHO0 / 1.02
+    h1, r1 = heating(rho1)                   # p = 0.02 K
+    p = KB * (RHO0 / rho1 - 1.0)
+    assert np.array_equal(r0[:, 0], r1[:, 0])          # the volume rate does not see p
+    scale = np.abs(p * r1[:, 0]).max()
+    assert scale > 0
+    assert np.abs(r1[:, 1]).max() <= 1e-12 * np.abs(r1[:, 5]).max()   # no mass flux, to round-off
+    assert np.abs((h1 - h0) - (-p * r1[:, 0])).max() <= 1e-9 * scale
+
+
 def test_uniform_state_patch_test():
     s, P, st = _lattice_state(n_side=11, jitter=0.0)
     st.vx[:] = 12.0; st.vy[:] = -7.0; st.vz[:] = 30.0
@@ -209,8 +239,21 @@ def test_radial_return_caps_von_mises_stress():
 def test_dt_closed_form():
     s, P, st = _lattice_state(n_side=4, jitter=0.01)
     c0 = math.sqrt((KB + 4.0 * GS / 3.0) / RHO0)
-    # the signal speed is evaluated in FP32 (reading), so the time step carries ~1e-7 relative error
-    assert orc.dt(P, st) == pytest.approx(s.cfl * s.h / (c0 + 100.0), rel=1e-6)
+    # Sec. II step g (reading): dt = cfl h / max(c + |v|), evaluated in FP64
+    assert orc.dt(P, st) == pytest.approx(s.cfl * s.h / (c0 + 100.0), rel=4e-16)
+
+
+def test_dt_is_set_by_the_fastest_particle():
+    # one particle in tension (lower density: faster sound) and one moving faster: the maximum of
+    # c + |v| over the particles decides, whichever of the two terms makes it
+    s, P, st = _lattice_state(n_side=4, jitter=0.01)
+    c0 = math.sqrt((KB + 4.0 * GS / 3.0) / RHO0)
+    st.m[5] *= 0.81                                    # rho = 0.81 rho0: c = c0 / 0.9
+    want = s.cfl * s.h / (c0 / 0.9 + math.sqrt(st.vx[5] ** 2 + st.vy[5] ** 2 + st.vz[5] ** 2))
+    assert orc.dt(P, st) == pytest.approx(want, rel=4e-16)
+    st.vx[9] = 2000.0                                  # |v| = sqrt(2000^2 + 100^2)
+    want = s.cfl * s.h / (c0 + math.hypot(2000.0, 100.0))
+    assert orc.dt(P, st) == pytest.approx(want, rel=4e-16)
 
 
 def test_free_flight_under_gravity_without_neighbours():

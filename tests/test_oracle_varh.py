@@ -116,4 +116,4 @@ def test_time_step_at_rest_is_cfl_hmin_over_c():
     rho0, K, G, _ = s.materials[0]
     c = np.sqrt((K + 4 * G / 3) / rho0)
     dt = orc.dt(P, st)
-    assert dt == pytest.approx(s.cfl * st.h.min() / c, rel=2e-7)
+    assert dt == pytest.approx(s.cfl * st.h.min() / c, rel=1e-15)
