@@ -167,6 +167,13 @@ typedef struct {
        step, and max over labels / mean over labels */
     int64_t cost[GSPH_MAX_LABELS];
     double cost_imbalance;
+    /* exactness work of the last step (the time step and the balancing hash are defined in FP64 and
+       decided in FP32 outside a proven rounding bound): particles the warp filter listed as time-step
+       candidates, candidates whose FP32 interval reached the largest lower bound and were evaluated in
+       FP64, and balancing hashes of the last swap pass that the FP64 sequence decided */
+    int64_t dt_candidates;
+    int64_t dt_fp64_evaluations;
+    int64_t swap_fp64_hashes;
 } gsph_exchange_stats;
 
 typedef struct {

@@ -861,6 +861,8 @@ void orc_rates(const orc_params *P, const orc_state *S, int64_t nsub, const int6
     rates_all(P, s, mats, nsub, subset, rates, nreal, nimage);
 }
 
+double orc_signal_speed(const orc_params *P, const orc_state *S, int64_t i) { return signal_speed(P, S, i); }
+
 double orc_dt(const orc_params *P, const orc_state *S) {
     double mx = 0.0;
     if (P->variable_h) {   // dt = cfl min_i h_i / s_i = cfl / max_i (s_i / h_i)

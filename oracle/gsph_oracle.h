@@ -116,6 +116,8 @@ void orc_eos(const orc_params *P, int32_t mat, double rho, double e, double *p, 
  * scalar type. */
 int64_t orc_flops_per_pair(void);
 /* Time step from the current state: CFL * h / max_i (c_i + |v_i|). */
+/* CFL signal speed c + |v| of particle i in FP64 (the quantity whose maximum sets the time step). */
+double orc_signal_speed(const orc_params *P, const orc_state *S, int64_t i);
 double orc_dt(const orc_params *P, const orc_state *S);
 /* Sec. II step g: forward Euler update of the state (in place) from the rates. */
 void orc_integrate(const orc_params *P, orc_state *S, const double *rates, double dt);

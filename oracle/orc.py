@@ -81,6 +81,8 @@ def lib():
                 f.restype = C.c_int64
             L.orc_rates.argtypes = [P(Params), P(StateC), C.c_int64, P(C.c_int64), _DP, P(C.c_int32),
                                     P(C.c_int32)]
+            L.orc_signal_speed.argtypes = [P(Params), P(StateC), C.c_int64]
+            L.orc_signal_speed.restype = C.c_double
             L.orc_dt.argtypes = [P(Params), P(StateC)]
             L.orc_dt.restype = C.c_double
             L.orc_integrate.argtypes = [P(Params), P(StateC), _DP, C.c_double]
@@ -282,6 +284,12 @@ def rates(P: Params, st: OracleState, subset=None):
         lib().orc_rates(C.byref(P), C.byref(cs), len(sub), _ptr(sub, C.c_int64), _ptr(out, C.c_double),
                         _ptr(nr, C.c_int32), _ptr(ni, C.c_int32))
     return out, nr, ni
+
+
+def signal_speed(P: Params, st: OracleState) -> np.ndarray:
+    """FP64 signal speed c + |v| of every particle."""
+    cs = st.cstruct()
+    return np.array([lib().orc_signal_speed(C.byref(P), C.byref(cs), i) for i in range(st.n)])
 
 
 def dt(P: Params, st: OracleState) -> float:

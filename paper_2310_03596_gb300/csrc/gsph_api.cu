@@ -23,16 +23,18 @@ cudaError_t launch_hash_hist(const DevParams &P, int64_t n, const double *x, con
 cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint32_t *perm,
                            const State &A, double *xs, double *ys, double *zs, uint8_t *lab_s, uint8_t *mat_s,
                            uint32_t *id_s, uint2 *cellr, float *cxs, void *pos, void *rec, float *xf, float *yf,
-                           float *zf, double *hs, float *hsf, int *err, cudaStream_t s);
+                           float *zf, uint32_t *qx, uint32_t *qy, uint32_t *qz, double *hs, float *hsf, int *err,
+                           cudaStream_t s);
 cudaError_t launch_comm(const DevParams &P, int64_t n, const uint32_t *skey, const uint8_t *lab_s, uint32_t *mask,
                         uint8_t *flag, uint32_t *comm, uint32_t *block_counts, unsigned long long *label_total,
                         uint32_t *blist, uint32_t *hidx, cudaStream_t s);
 int comm_blocks(int64_t n);
 cudaError_t launch_init(const DevParams &P, int64_t n, const double *pos, const double *vel, const double *vol,
                         const uint8_t *mat, const uint8_t *lab, const State &A, int *err, cudaStream_t s);
-cudaError_t launch_dt_from_state(const DevParams &P, int64_t n, const State &A, unsigned int *sig, double *dt,
+cudaError_t launch_dt_from_state(const DevParams &P, int64_t n, const State &A, const DtArgs &d, double *dt,
                                  cudaStream_t s);
-cudaError_t launch_finalize_dt(const DevParams &P, unsigned int *sig, double *dt, cudaStream_t s);
+cudaError_t launch_finalize_dt(const DevParams &P, int64_t n, const DtArgs &d, const State &S, double *dt,
+                               cudaStream_t s);
 cudaError_t launch_conserved(int64_t n, const State &A, double *part, double *out, cudaStream_t s);
 // k_interact.cu
 cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n, const uint32_t *skey,
@@ -40,19 +42,19 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
                             const double *xs, const double *ys, const double *zs, int kmax, uint2 *list,
                             uint32_t *cnt, const uint32_t *perm, const State &A, const State &B, cudaEvent_t mid,
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
-                            unsigned int *sig, unsigned long long *pairs, unsigned long long *cost,
+                            const DtArgs &dtc, unsigned long long *pairs, unsigned long long *cost,
                             int32_t *nreal, int32_t *nimage, double *rates, const OverlapBufs *ov,
                             int stage, void *grad, const double *hs, const float *hsf, cudaStream_t s);
 cudaError_t launch_refresh(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const State &B,
                            void *pos, void *rec, cudaStream_t s);
 // k_swap.cu
 size_t swap_scratch_bytes(int K, int nmat);
-cudaError_t launch_round_positions(int64_t n, const double *x, const double *y, const double *z, float *xf,
-                                   float *yf, float *zf, cudaStream_t s);
-cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const float *x, const float *y, const float *z,
-                             uint8_t *lab, const uint8_t *mat, const uint32_t *id, void *scratch, uint16_t *bh,
-                             uint32_t *sidx,
-                             int *err, int grid, cudaStream_t s);
+cudaError_t launch_round_positions(const DevParams &P, int64_t n, const double *x, const double *y, const double *z,
+                                   float *xf, float *yf, float *zf, uint32_t *qx, uint32_t *qy, uint32_t *qz,
+                                   cudaStream_t s);
+cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const SwapPos &pos, uint8_t *lab, const uint8_t *mat,
+                             const uint32_t *id, void *scratch, uint16_t *bh, uint32_t *sidx, int *err, int grid,
+                             cudaStream_t s);
 int swap_grid_blocks();
 unsigned long long *swap_moved_ptr(void *scratch);
 // k_adjoint.cu
@@ -93,6 +95,7 @@ struct gsph_ctx {
     double *xs = nullptr, *ys = nullptr, *zs = nullptr;
     float *cxs = nullptr;
     float *xf = nullptr, *yf = nullptr, *zf = nullptr;   // FP32 roundings of the positions (swap pass)
+    uint32_t *qx = nullptr, *qy = nullptr, *qz = nullptr;   // fixed-point coordinates (swap pass Cg sums)
     uint2 *nbr = nullptr;                         // neighbour lists (kNbrMax x n entries, column-major)
     uint32_t *nbr_cnt = nullptr;                  // entries per particle
     uint8_t *lab_s = nullptr, *mat_s = nullptr;
@@ -111,7 +114,8 @@ struct gsph_ctx {
     unsigned long long *label_off = nullptr;   // K + 1
     unsigned long long *cost = nullptr;        // pair interactions per label, last step
     unsigned long long *garbage = nullptr;
-    unsigned int *sig = nullptr;
+    DtWords *dtw = nullptr;                   // time-step reduction words
+    uint2 *dt_cand = nullptr;                 // time-step candidates (n)
     unsigned long long *pairs = nullptr;
     double *dt = nullptr;
     int *err = nullptr;
@@ -134,6 +138,8 @@ struct gsph_ctx {
     int timing_max = 0, timing_used = 0;
     std::vector<cudaEvent_t> ev;
 };
+
+static DtArgs dt_args(const gsph_ctx *c) { return DtArgs{c->dtw, c->dt_cand, (uint32_t)c->n}; }
 
 #define GSPH_CK(call)                                      \
     do {                                                   \
@@ -188,6 +194,7 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     A_(dalloc(c, &c->xs, N)); A_(dalloc(c, &c->ys, N)); A_(dalloc(c, &c->zs, N));
     A_(dalloc(c, &c->cxs, N));
     A_(dalloc(c, &c->xf, N)); A_(dalloc(c, &c->yf, N)); A_(dalloc(c, &c->zf, N));
+    A_(dalloc(c, &c->qx, N)); A_(dalloc(c, &c->qy, N)); A_(dalloc(c, &c->qz, N));
     A_(dalloc(c, &c->nbr, N * (size_t)kNbrMax));
     A_(dalloc(c, &c->nbr_cnt, N));
     A_(dalloc(c, &c->lab_s, N)); A_(dalloc(c, &c->mat_s, N)); A_(dalloc(c, &c->id_s, N));
@@ -205,7 +212,8 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     A_(dalloc(c, &c->label_off, (size_t)kMaxLabel + 1));
     A_(dalloc(c, &c->cost, (size_t)kMaxLabel));
     A_(dalloc(c, &c->garbage, 1));
-    A_(dalloc(c, &c->sig, 1));
+    A_(dalloc(c, &c->dtw, 1));
+    A_(dalloc(c, &c->dt_cand, N));
     A_(dalloc(c, &c->pairs, 1));
     A_(dalloc(c, &c->dt, 1));
     A_(dalloc(c, &c->err, 1));
@@ -242,6 +250,7 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     }
 #undef A_
     e = cudaMemset(c->err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->dtw, 0, sizeof(DtWords));
     if (e == cudaSuccess) e = cudaMemset(c->garbage, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->pairs, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->label_off, 0, (kMaxLabel + 1) * sizeof(unsigned long long));
@@ -328,6 +337,11 @@ static void fill_params(const gsph_config &c, DevParams &P) {
     P.f_k5 = (float)P.k5;
     if (!std::isnormal(P.f_inv_cell)) P.f_inv_cell = std::nanf("");   // the hash then always divides in FP64
     P.f_inv_h = (float)(1.0 / c.h);
+    for (int a = 0; a < 3; ++a) {
+        const double ext = (double)c.grid_dims[a] * P.cell;
+        P.q_s[a] = 4294967296.0 / ext;
+        P.q_step[a] = ext * 0x1p-32;
+    }
     P.f_kdw = (float)P.kdw;
     // The FP32 evaluation of r^2 - R2lo for a candidate (the list kernel's |c|^2 + (|o|^2 - R2lo) - 2 c.o
     // in frames with |coordinates| < 5h, the re-scan's direct differences) is within 7e-6 R2 of the
@@ -361,7 +375,7 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     const DevParams &P = c->P;
     const int64_t n = c->n;
     if (c->dt_dirty) {
-        GSPH_CK(launch_dt_from_state(P, n, c->A, c->sig, c->dt, s));
+        GSPH_CK(launch_dt_from_state(P, n, c->A, dt_args(c), c->dt, s));
         c->dt_dirty = false;
         c->launches += 2;
     }
@@ -382,14 +396,15 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     const bool do_swap = P.K_labels > 1 && c->cfg.swap_period > 0 && (c->step % c->cfg.swap_period) == 0;
     GSPH_CK(cudaMemsetAsync(c->cellr, 0, (size_t)P.ncell * sizeof(uint2), s));
     GSPH_CK(launch_reorder(c->split, P, n, c->skey, c->perm, c->A, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s,
-                           c->cellr, c->cxs, c->pos, c->rec, do_swap ? c->xf : nullptr, c->yf, c->zf, c->hs, c->hsf,
-                           c->err, s));
+                           c->cellr, c->cxs, c->pos, c->rec, do_swap ? c->xf : nullptr, c->yf, c->zf, c->qx, c->qy,
+                           c->qz, c->hs, c->hsf, c->err, s));
     c->launches += 1;
     rec_event(c, PH_REORDER, s);
     // Sec. III: periodic swap heuristic on the sorted view
     if (do_swap) {
-        GSPH_CK(launch_swap_pass(P, n, c->xf, c->yf, c->zf, c->lab_s, c->mat_s, c->id_s, c->swap_scratch, c->bh, c->sidx,
-                                 c->err, c->swap_grid, s));
+        const SwapPos sp{c->xf, c->yf, c->zf, c->xs, c->ys, c->zs, c->qx, c->qy, c->qz};
+        GSPH_CK(launch_swap_pass(P, n, sp, c->lab_s, c->mat_s, c->id_s, c->swap_scratch, c->bh, c->sidx, c->err,
+                                 c->swap_grid, s));
         ++c->swap_passes;
         c->launches += swap_pass_launches(P);
     }
@@ -409,7 +424,7 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     }
     GSPH_CK(launch_interact(c->split, c->cfg.diagnostics != 0, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs,
                             c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, phase_event(c, PH_LIST),
-                            c->lab_s, c->mat_s, c->id_s, c->dt, c->sig, c->pairs, c->cost, c->nreal, c->nimage,
+                            c->lab_s, c->mat_s, c->id_s, c->dt, dt_args(c), c->pairs, c->cost, c->nreal, c->nimage,
                             c->rates, c->cfg.overlap ? &ov : nullptr, c->cfg.integrator == 1 ? 1 : 0, c->grad, c->hs,
                             c->hsf, s));
     if (c->cfg.overlap) c->launches += 2;   // halo gather, second pair pass
@@ -418,11 +433,11 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
         GSPH_CK(launch_refresh(c->split, P, n, c->skey, c->B, c->pos, c->rec, s));
         GSPH_CK(launch_interact(c->split, c->cfg.diagnostics != 0, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs,
                                 c->xs, c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr,
-                                c->lab_s, c->mat_s, c->id_s, c->dt, c->sig, c->pairs, c->cost, c->nreal,
+                                c->lab_s, c->mat_s, c->id_s, c->dt, dt_args(c), c->pairs, c->cost, c->nreal,
                                 c->nimage, c->rates, nullptr, 2, nullptr, c->hs, c->hsf, s));
         c->launches += 2;
     }
-    GSPH_CK(launch_finalize_dt(P, c->sig, c->dt, s));
+    GSPH_CK(launch_finalize_dt(P, n, dt_args(c), c->B, c->dt, s));
     c->launches += 3;
     rec_event(c, PH_INTERACT, s);
     if (c->timing_used < c->timing_max) ++c->timing_used;
@@ -448,13 +463,14 @@ static gsph_status enqueue_forward_pieces(gsph_ctx *c, cudaStream_t s) {
     c->perm = alt ? c->val1 : c->val0;
     GSPH_CK(cudaMemsetAsync(c->cellr, 0, (size_t)P.ncell * sizeof(uint2), s));
     GSPH_CK(launch_reorder(c->split, P, n, c->skey, c->perm, c->A, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s,
-                           c->cellr, c->cxs, c->pos, c->rec, nullptr, nullptr, nullptr, nullptr, nullptr, c->err, s));
+                           c->cellr, c->cxs, c->pos, c->rec, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                           nullptr, nullptr, c->err, s));
     GSPH_CK(launch_interact(c->split, true, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs, c->ys, c->zs,
                             kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr, c->lab_s, c->mat_s, c->id_s,
-                            c->dt, c->sig, c->pairs, c->cost, c->nreal, c->nimage, c->rates, nullptr, 0, nullptr, nullptr,
+                            c->dt, dt_args(c), c->pairs, c->cost, c->nreal, c->nimage, c->rates, nullptr, 0, nullptr, nullptr,
                             nullptr, s));
     c->launches += 4 + 3 * radix_passes(key_bits(P.ncell));
-    c->dt_dirty = true;   // the signal-speed word now holds the scratch state's maximum
+    c->dt_dirty = true;   // the time-step words now hold the scratch state's candidates
     return GSPH_OK;
 }
 
@@ -589,7 +605,7 @@ gsph_status gsph_set_particles(gsph_ctx *c, int64_t n, const double *pos, const 
     cudaError_t e = cudaMemsetAsync(c->err, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->pairs, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = launch_init(c->P, n, dpos, dvel, dvol, dmat, dlab, c->A, c->err, s);
-    if (e == cudaSuccess) e = launch_dt_from_state(c->P, n, c->A, c->sig, c->dt, s);
+    if (e == cudaSuccess) e = launch_dt_from_state(c->P, n, c->A, dt_args(c), c->dt, s);
     cudaError_t e2 = cudaStreamSynchronize(s);
     if (stage) cudaFree(stage);
     if (e != cudaSuccess || e2 != cudaSuccess) return GSPH_CUDA_ERROR;
@@ -684,9 +700,11 @@ gsph_status gsph_swap_now(gsph_ctx *c, void *stream) {
     if (c->n == 0) return GSPH_NOT_READY;
     GSPH_CK(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
-    GSPH_CK(launch_round_positions(c->n, c->A.f[FX], c->A.f[FY], c->A.f[FZ], c->xf, c->yf, c->zf, s));
-    GSPH_CK(launch_swap_pass(c->P, c->n, c->xf, c->yf, c->zf, c->A.label, c->A.mat, c->A.id, c->swap_scratch, c->bh, c->sidx,
-                             c->err, c->swap_grid, s));
+    GSPH_CK(launch_round_positions(c->P, c->n, c->A.f[FX], c->A.f[FY], c->A.f[FZ], c->xf, c->yf, c->zf, c->qx, c->qy,
+                                   c->qz, s));
+    const SwapPos sp{c->xf, c->yf, c->zf, c->A.f[FX], c->A.f[FY], c->A.f[FZ], c->qx, c->qy, c->qz};
+    GSPH_CK(launch_swap_pass(c->P, c->n, sp, c->A.label, c->A.mat, c->A.id, c->swap_scratch, c->bh, c->sidx, c->err,
+                             c->swap_grid, s));
     ++c->swap_passes;
     c->launches += 1 + swap_pass_launches(c->P);
     return GSPH_OK;
@@ -705,11 +723,13 @@ gsph_status gsph_get_exchange_stats(gsph_ctx *c, void *stream, gsph_exchange_sta
     GSPH_CK(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
     std::memset(out, 0, sizeof(*out));
-    unsigned long long off[kMaxLabel + 1] = {0}, garb = 0, moved = 0, pairs = 0, cost[kMaxLabel] = {0};
+    unsigned long long off[kMaxLabel + 1] = {0}, garb = 0, moved[2] = {0, 0}, pairs = 0, cost[kMaxLabel] = {0};
+    DtWords dw{};
     GSPH_CK(cudaMemcpyAsync(off, c->label_off, sizeof(off), cudaMemcpyDeviceToHost, s));
     GSPH_CK(cudaMemcpyAsync(cost, c->cost, sizeof(cost), cudaMemcpyDeviceToHost, s));
     GSPH_CK(cudaMemcpyAsync(&garb, c->garbage, sizeof(garb), cudaMemcpyDeviceToHost, s));
-    GSPH_CK(cudaMemcpyAsync(&moved, swap_moved_ptr(c->swap_scratch), sizeof(moved), cudaMemcpyDeviceToHost, s));
+    GSPH_CK(cudaMemcpyAsync(moved, swap_moved_ptr(c->swap_scratch), sizeof(moved), cudaMemcpyDeviceToHost, s));
+    GSPH_CK(cudaMemcpyAsync(&dw, c->dtw, sizeof(dw), cudaMemcpyDeviceToHost, s));
     GSPH_CK(cudaMemcpyAsync(&pairs, c->pairs, sizeof(pairs), cudaMemcpyDeviceToHost, s));
     GSPH_CK(cudaStreamSynchronize(s));
     const int K = c->P.K_labels;
@@ -725,8 +745,11 @@ gsph_status gsph_get_exchange_stats(gsph_ctx *c, void *stream, gsph_exchange_sta
     out->record_bytes = c->split ? (int64_t)(sizeof(float4) + sizeof(RecF)) : (int64_t)(sizeof(D4) + sizeof(RecD));
     out->bytes_hash_broadcast = c->n * 4 * (K - 1);
     out->bytes_boundary_broadcast = out->boundary_total * out->record_bytes * (K - 1);
-    out->swapped_last_pass = (int64_t)moved;
-    out->bytes_swap = (int64_t)moved * (15 * 8 + 6);
+    out->swapped_last_pass = (int64_t)moved[0];
+    out->bytes_swap = (int64_t)moved[0] * (15 * 8 + 6);
+    out->swap_fp64_hashes = (int64_t)moved[1];
+    out->dt_candidates = dw.last_ccount;
+    out->dt_fp64_evaluations = dw.last_eval;
     out->swap_passes = c->swap_passes;
     out->pairs_total = (int64_t)pairs;
     out->kernel_launches = c->launches;
@@ -759,7 +782,7 @@ gsph_status gsph_get_dt(gsph_ctx *c, void *stream, double *dt) {
     GSPH_CK(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
     if (c->dt_dirty) {
-        GSPH_CK(launch_dt_from_state(c->P, c->n, c->A, c->sig, c->dt, s));
+        GSPH_CK(launch_dt_from_state(c->P, c->n, c->A, dt_args(c), c->dt, s));
         c->dt_dirty = false;
     }
     GSPH_CK(cudaMemcpyAsync(dt, c->dt, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -773,7 +796,7 @@ gsph_status gsph_set_dt(gsph_ctx *c, double dt, void *stream) {
     GSPH_CK(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
     GSPH_CK(cudaMemcpyAsync(c->dt, &dt, sizeof(double), cudaMemcpyHostToDevice, s));
-    GSPH_CK(cudaMemsetAsync(c->sig, 0, sizeof(unsigned int), s));
+    GSPH_CK(cudaMemsetAsync(c->dtw, 0, offsetof(DtWords, last_ccount), s));
     GSPH_CK(cudaStreamSynchronize(s));
     c->dt_dirty = false;
     return GSPH_OK;

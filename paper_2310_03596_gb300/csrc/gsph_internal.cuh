@@ -42,18 +42,21 @@ struct DevParams {
     float f_cell, f_inv_h, f_kdw, f_R2lo, f_R2hi;
     float f_inv_cell;        // FP32 rounding of the FP64 reciprocal of the bucket side
     float f_rho0[kMaxMat], f_K[kMaxMat], f_G[kMaxMat], f_Mmod[kMaxMat];
+    // FP32 roundings for the time step's signal-speed bounds: c0, s - 1, gamma0, 4G/3
+    float f_c0[kMaxMat], f_sm1[kMaxMat], f_g0[kMaxMat], f_G43[kMaxMat];
     // equation of state per material (0 linear, 1 Mie-Gruneisen) and pressure cut-off
     int eos[kMaxMat];
     double c0[kMaxMat], s_hug[kMaxMat], gamma0[kMaxMat], p_min[kMaxMat];
     double inv_rho0[kMaxMat], k0[kMaxMat], inv_2rho0[kMaxMat];   // 1/rho0, rho0 c0^2, 1/(2 rho0)
-    // FP32 roundings for the signal speed: c0, s - 1, gamma0, 4G/3
-    float f_c0[kMaxMat], f_sm1[kMaxMat], f_g0[kMaxMat], f_G43[kMaxMat];
     // variable smoothing lengths: support r^2 < (h_i + h_j)^2; the FP32 list test decides outside the
     // relative band [1 - d, 1 + d] around it (d = kVarBand, wide enough for size ratios up to 4)
     int variable_h;
     float f_vlo, f_vhi;      // 1 - d, 1 + d
     float f_k5;              // |dW/dr| = k5 (1 / (h_i + h_j))^5 r (1 - r / (h_i + h_j))^3: 210 / pi
     double k5;
+    // fixed-point Cg of the swap pass (Sec. III.A): q = nearest integer to (x - lo) q_s, q_s = 2^32 / L,
+    // Cg = lo + mean(q) q_step, q_step = L 2^-32, L = dims * 2h the grid extent per axis
+    double q_s[3], q_step[3];
 };
 constexpr double kVarBand = 1.0e-3;
 
@@ -81,6 +84,14 @@ struct State {
     double *h;               // per-particle smoothing length (variable h), else null
 };
 enum { FX = 0, FY, FZ, FVX, FVY, FVZ, FW, FM, FE, FSXX, FSYY, FSZZ, FSXY, FSXZ, FSYZ };
+
+// Positions of the swap pass (Sec. III.A): FP32 roundings (the balancing hash's fast path), FP64 (its
+// exact fallback) and the fixed-point coordinates of the Cg sums (quantise64).
+struct SwapPos {
+    const float *x, *y, *z;
+    const double *X, *Y, *Z;
+    const uint32_t *qx, *qy, *qz;
+};
 
 // Interaction records of sorted particles.
 // Split path: pos4 = (x, y, z relative to the particle's own bucket corner, w) in FP32 and
@@ -147,6 +158,17 @@ __device__ __forceinline__ uint32_t hash_of(const DevParams &P, double x, double
     return (uint32_t)cx + (uint32_t)P.dims[0] * ((uint32_t)cy + (uint32_t)P.dims[1] * (uint32_t)cz);
 }
 
+// Fixed-point coordinate of the swap pass's Cg sums: nearest integer (ties to even) to (x - lo) s, clamped
+// to [0, 2^32 - 1] (NaN gives 0).
+__device__ __forceinline__ uint32_t quantise64(double x, double lo, double s) {
+    const double t = __dmul_rn(__dsub_rn(x, lo), s);
+    const long long b = __double_as_longlong(t);
+    if ((b & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) return 0u;   // NaN
+    long long q = __double2ll_rn(t);                                   // saturates beyond the int64 range
+    q = q < 0 ? 0 : (q > 4294967295LL ? 4294967295LL : q);
+    return (uint32_t)q;
+}
+
 __device__ __forceinline__ void decode_cell(const DevParams &P, uint32_t c, int &cx, int &cy, int &cz) {
     cx = (int)(c % (uint32_t)P.dims[0]);
     uint32_t r = c / (uint32_t)P.dims[0];
@@ -154,49 +176,227 @@ __device__ __forceinline__ void decode_cell(const DevParams &P, uint32_t c, int 
     cz = (int)(r / (uint32_t)P.dims[1]);
 }
 
-// CFL signal speed c + |v| of one particle, evaluated in FP32 with correctly rounded operations on
-// the FP32 roundings of m, w, v (the max over particles is order independent, so the time step is
-// reproducible bit for bit on any IEEE machine evaluating the same sequence).
-__device__ __forceinline__ float signal_speed32(const DevParams &P, int mat, double m, double w,
-                                                double vx, double vy, double vz, double E) {
-    const float rho = __fdiv_rn((float)m, (float)w);
-    const float fx = (float)vx, fy = (float)vy, fz = (float)vz;
-    const float v2 = __fadd_rn(__fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy)), __fmul_rn(fz, fz));
-    float c;
+// ---------------------------------------------------------------------------------------------
+// CFL time step (Sec. II step g): dt = cfl h / max_i s_i with the signal speed s_i = c_i + |v_i| in FP64
+// (variable h: dt = cfl / max_i (s_i / h_i)). The FP64 sequence below is the definition; a step never
+// evaluates it for every particle (GB300's FP64 units are scarce). Each particle first evaluates s in
+// FP32 together with a bound of the FP32 value's distance from the FP64 one (a running error bound,
+// below), giving an interval [lo, hi] that contains the FP64 value. The largest lo over all particles is
+// a lower bound of the FP64 maximum, so only particles whose hi reaches it can attain the maximum. A warp
+// first keeps its lanes whose hi reaches the warp's largest lo, drops the lanes whose FP64 inputs equal
+// bit for bit those of the lane holding that lo (same inputs, same FP64 value), and appends the rest to
+// a candidate list; a second kernel keeps the candidates whose hi reaches the grid's largest lo,
+// evaluates their FP64 signal speed, takes the exact maximum and forms dt.
+// ---------------------------------------------------------------------------------------------
+
+// FP64 signal speed of one particle, each operation rounded (no contraction): rho = m / w,
+// |v|^2 = (vx^2 + vy^2) + vz^2; linear EOS c = sqrt(M / rho), M = K + 4G/3; Mie-Gruneisen
+// c = sqrt(cb2 + (4G/3) / rho) with cb2 the isentropic bulk term at e = E - |v|^2 / 2, floored at 0.
+__device__ __forceinline__ double signal_speed64(const DevParams &P, int mat, double m, double w, double vx,
+                                                 double vy, double vz, double E) {
+    const double rho = __ddiv_rn(m, w);
+    const double v2 = dist2_rn(vx, vy, vz);
+    double c;
     if (P.eos[mat] == 0) {
-        c = __fsqrt_rn(__fdiv_rn(P.f_Mmod[mat], rho));
+        c = __dsqrt_rn(__ddiv_rn(P.Mmod[mat], rho));
     } else {
-        // Mie-Gruneisen sound speed: the same FP32 sequence as the host reference, each operation
-        // correctly rounded (no contraction)
-        const float rho0 = P.f_rho0[mat], c0 = P.f_c0[mat], sm1 = P.f_sm1[mat], g0 = P.f_g0[mat];
-        const float e = __fsub_rn((float)E, __fmul_rn(0.5f, v2));
-        const float mu = __fsub_rn(__fdiv_rn(rho, rho0), 1.0f);
-        const float k0 = __fmul_rn(__fmul_rn(rho0, c0), c0);
-        float pH, dpH;
-        if (mu > 0.0f) {
-            const float D = __fsub_rn(1.0f, __fmul_rn(sm1, mu));
-            const float D2 = __fmul_rn(D, D);
-            const float q = __fadd_rn(1.0f, mu);
-            pH = __fdiv_rn(__fmul_rn(__fmul_rn(k0, mu), q), D2);
-            const float t1 = __fmul_rn(__fadd_rn(1.0f, __fmul_rn(2.0f, mu)), D);
-            const float t2 = __fmul_rn(__fmul_rn(2.0f, sm1), __fmul_rn(mu, q));
-            dpH = __fdiv_rn(__fmul_rn(k0, __fadd_rn(t1, t2)), __fmul_rn(D2, D));
+        const double rho0 = P.rho0[mat], c0 = P.c0[mat], g0 = P.gamma0[mat];
+        const double e = __dsub_rn(E, __dmul_rn(v2, 0.5));
+        const double mu = __dsub_rn(__ddiv_rn(rho, rho0), 1.0);
+        const double k0 = __dmul_rn(__dmul_rn(rho0, c0), c0);
+        const double q = __dadd_rn(1.0, mu);
+        double pH, dpH;
+        if (mu > 0.0) {
+            const double sm1 = __dsub_rn(P.s_hug[mat], 1.0);
+            const double D = __dsub_rn(1.0, __dmul_rn(sm1, mu));
+            pH = __ddiv_rn(__dmul_rn(__dmul_rn(k0, mu), q), __dmul_rn(D, D));
+            const double a1 = __dmul_rn(__dadd_rn(1.0, __dmul_rn(2.0, mu)), D);
+            const double a2 = __dmul_rn(__dmul_rn(__dmul_rn(2.0, sm1), mu), q);
+            dpH = __ddiv_rn(__dmul_rn(k0, __dadd_rn(a1, a2)), __dmul_rn(__dmul_rn(D, D), D));
         } else {
-            pH = __fmul_rn(k0, mu);
+            pH = __dmul_rn(k0, mu);
             dpH = k0;
         }
-        const float q = __fadd_rn(1.0f, mu);
-        const float r2q = __fmul_rn(__fmul_rn(2.0f, rho0), q);
-        const float eH = __fdiv_rn(__fmul_rn(pH, mu), r2q);
-        const float deH = __fdiv_rn(__fadd_rn(__fmul_rn(__fmul_rn(dpH, mu), q), pH), __fmul_rn(r2q, q));
-        const float gr = __fmul_rn(g0, rho0);
-        const float p = __fadd_rn(pH, __fmul_rn(gr, __fsub_rn(e, eH)));
-        float cb2 = __fadd_rn(__fdiv_rn(__fsub_rn(dpH, __fmul_rn(gr, deH)), rho0),
-                              __fdiv_rn(__fmul_rn(p, gr), __fmul_rn(rho, rho)));
-        if (!(cb2 > 0.0f)) cb2 = 0.0f;
-        c = __fsqrt_rn(__fadd_rn(cb2, __fdiv_rn(P.f_G43[mat], rho)));
+        const double r2 = __dmul_rn(2.0, rho0);
+        const double eH = __ddiv_rn(__dmul_rn(pH, mu), __dmul_rn(r2, q));
+        const double deH = __ddiv_rn(__dadd_rn(__dmul_rn(__dmul_rn(dpH, mu), q), pH), __dmul_rn(__dmul_rn(r2, q), q));
+        const double gr = __dmul_rn(g0, rho0);
+        const double p = __dadd_rn(pH, __dmul_rn(gr, __dsub_rn(e, eH)));
+        double cb2 = __dadd_rn(__ddiv_rn(__dsub_rn(dpH, __dmul_rn(gr, deH)), rho0),
+                               __ddiv_rn(__dmul_rn(__dmul_rn(p, g0), rho0), __dmul_rn(rho, rho)));
+        if (cb2 < 0.0) cb2 = 0.0;
+        const double G43 = __ddiv_rn(__dmul_rn(4.0, P.G[mat]), 3.0);
+        c = __dsqrt_rn(__dadd_rn(cb2, __ddiv_rn(G43, rho)));
     }
-    return __fadd_rn(c, __fsqrt_rn(v2));
+    return __dadd_rn(c, __dsqrt_rn(v2));
+}
+
+// FP32 value with a bound e of its absolute distance from the exact value of the same expression on the
+// exact inputs. Each operation adds the propagated bounds of its operands and its own rounding (at most
+// 2^-24 of the result); a division by an operand whose bound reaches its magnitude, or an overflow,
+// gives an infinite bound.
+struct FErr { float v, e; };
+constexpr float kU32 = 0x1p-24f;
+__device__ __forceinline__ FErr fe_in(double x) {   // FP32 rounding of an exact FP64 input
+    const float v = __double2float_rn(x);
+    return FErr{v, __fmul_rn(kU32, fabsf(v))};
+}
+__device__ __forceinline__ FErr fe_add(FErr a, FErr b) {
+    const float v = __fadd_rn(a.v, b.v);
+    return FErr{v, __fadd_rn(__fadd_rn(a.e, b.e), __fmul_rn(kU32, fabsf(v)))};
+}
+__device__ __forceinline__ FErr fe_sub(FErr a, FErr b) {
+    const float v = __fsub_rn(a.v, b.v);
+    return FErr{v, __fadd_rn(__fadd_rn(a.e, b.e), __fmul_rn(kU32, fabsf(v)))};
+}
+__device__ __forceinline__ FErr fe_mul(FErr a, FErr b) {
+    const float v = __fmul_rn(a.v, b.v);
+    const float e = __fadd_rn(__fadd_rn(__fmul_rn(fabsf(a.v), b.e), __fmul_rn(fabsf(b.v), a.e)), __fmul_rn(a.e, b.e));
+    return FErr{v, __fadd_rn(e, __fmul_rn(kU32, fabsf(v)))};
+}
+__device__ __forceinline__ FErr fe_div(FErr a, FErr b) {
+    const float v = __fdiv_rn(a.v, b.v);
+    const float den = __fsub_rn(fabsf(b.v), b.e);
+    float e = den > 0.0f ? __fdiv_rn(__fadd_rn(a.e, __fmul_rn(fabsf(v), b.e)), den) : __int_as_float(0x7f800000);
+    return FErr{v, __fadd_rn(e, __fmul_rn(kU32, fabsf(v)))};
+}
+__device__ __forceinline__ FErr fe_sqrt(FErr a) {   // of a non-negative exact value
+    const float v = __fsqrt_rn(fmaxf(a.v, 0.0f));
+    const float r = __fsqrt_rn(a.e);
+    const float e = v > 0.0f ? fminf(__fdiv_rn(a.e, v), r) : r;
+    return FErr{v, __fadd_rn(e, __fmul_rn(kU32, v))};
+}
+__device__ __forceinline__ FErr fe_scale(FErr a, float k) {   // by an exact power of two
+    return FErr{a.v * k, a.e * fabsf(k)};
+}
+__device__ __forceinline__ FErr fe_c(float v) {   // FP32 rounding of an FP64 constant
+    return FErr{v, __fmul_rn(kU32, fabsf(v))};
+}
+
+// Interval [lo, hi] containing the FP64 signal speed of signal_speed64 (divided by h for variable h). The
+// bound covers the FP32 roundings; the factor 1 + 2^-8 covers the FP64 sequence's own roundings (2^-29
+// times the FP32 ones, through the same operations) and the roundings of the bound's evaluation.
+__device__ __forceinline__ void signal_bounds32(const DevParams &P, int mat, double m, double w, double vx,
+                                                double vy, double vz, double E, double h, float &lo, float &hi) {
+    const FErr rho = fe_div(fe_in(m), fe_in(w));
+    const FErr fx = fe_in(vx), fy = fe_in(vy), fz = fe_in(vz);
+    const FErr v2 = fe_add(fe_add(fe_mul(fx, fx), fe_mul(fy, fy)), fe_mul(fz, fz));
+    const FErr vn = fe_sqrt(v2);
+    FErr s1, s2;
+    if (P.eos[mat] == 0) {
+        s1 = fe_add(fe_sqrt(fe_div(fe_c(P.f_Mmod[mat]), rho)), vn);
+        s2 = s1;
+    } else {
+        const FErr rho0 = fe_c(P.f_rho0[mat]), c0 = fe_c(P.f_c0[mat]), g0 = fe_c(P.f_g0[mat]);
+        const FErr sm1 = fe_c(P.f_sm1[mat]);
+        const FErr one{1.0f, 0.0f};
+        const FErr e = fe_sub(fe_in(E), fe_scale(v2, 0.5f));
+        const FErr mu = fe_sub(fe_div(rho, rho0), one);
+        const FErr k0 = fe_mul(fe_mul(rho0, c0), c0);
+        const FErr q = fe_add(one, mu);
+        const FErr r2 = fe_scale(rho0, 2.0f);
+        const FErr gr = fe_mul(g0, rho0);
+        const FErr G43 = fe_c(P.f_G43[mat]);
+        // both branches of the reference curve when the sign of mu is not certain
+        auto branch = [&](bool comp) {
+            FErr pH, dpH;
+            if (comp) {
+                const FErr D = fe_sub(one, fe_mul(sm1, mu));
+                const FErr D2 = fe_mul(D, D);
+                pH = fe_div(fe_mul(fe_mul(k0, mu), q), D2);
+                const FErr a1 = fe_mul(fe_add(one, fe_scale(mu, 2.0f)), D);
+                const FErr a2 = fe_mul(fe_mul(fe_scale(sm1, 2.0f), mu), q);
+                dpH = fe_div(fe_mul(k0, fe_add(a1, a2)), fe_mul(D2, D));
+            } else {
+                pH = fe_mul(k0, mu);
+                dpH = k0;
+            }
+            const FErr eH = fe_div(fe_mul(pH, mu), fe_mul(r2, q));
+            const FErr deH = fe_div(fe_add(fe_mul(fe_mul(dpH, mu), q), pH), fe_mul(fe_mul(r2, q), q));
+            const FErr p = fe_add(pH, fe_mul(gr, fe_sub(e, eH)));
+            FErr cb2 = fe_add(fe_div(fe_sub(dpH, fe_mul(gr, deH)), rho0), fe_div(fe_mul(p, gr), fe_mul(rho, rho)));
+            cb2.v = fmaxf(cb2.v, 0.0f);   // the floor at 0 does not widen the bound
+            return fe_add(fe_sqrt(fe_add(cb2, fe_div(G43, rho))), vn);
+        };
+        const bool pos = mu.v > mu.e, neg = mu.v < -mu.e;
+        s1 = branch(!neg);
+        s2 = (pos || neg) ? s1 : branch(false);
+    }
+    if (P.variable_h) {
+        const FErr hh = fe_in(h);
+        s1 = fe_div(s1, hh);
+        s2 = fe_div(s2, hh);
+    }
+    const float k = 1.00390625f;   // 1 + 2^-8
+    const float e1 = __fmul_rn(s1.e, k), e2 = __fmul_rn(s2.e, k);
+    float l = fminf(__fmul_rn(__fsub_rn(s1.v, e1), 1.0f - 0x1p-20f), __fmul_rn(__fsub_rn(s2.v, e2), 1.0f - 0x1p-20f));
+    float u = fmaxf(__fmul_rn(__fadd_rn(s1.v, e1), 1.0f + 0x1p-20f), __fmul_rn(__fadd_rn(s2.v, e2), 1.0f + 0x1p-20f));
+    if (!(l > 0.0f)) l = 0.0f;                                       // also NaN
+    if (!(u >= l) || isinf(e1) || isinf(e2)) u = __int_as_float(0x7f800000);
+    lo = l;
+    hi = u;
+}
+
+// Words of the time-step reduction (zero between steps). sig: bits of the largest lo (non-negative
+// floats order like their bit patterns); sigd: bits of the largest FP64 signal speed of the candidates;
+// ccount: candidates listed; done: blocks of the final kernel that finished.
+struct DtWords {
+    unsigned long long sigd;
+    unsigned int sig, ccount, done, eval;
+    unsigned int last_ccount, last_eval;   // the last completed reduction's counts (statistics)
+};
+struct DtArgs {
+    DtWords *w;
+    uint2 *cand;      // (slot, bits of hi)
+    uint32_t cap;     // list capacity (the particle count: each particle is listed at most once)
+};
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Warp-collective (all 32 lanes): the candidate filter of one warp. ok: the lane has a particle whose
+// signal speed counts; its FP64 inputs and slot.
+__device__ __forceinline__ void dt_candidate(const DevParams &P, const DtArgs &d, bool ok, uint32_t slot, int mat,
+                                             double m, double w, double vx, double vy, double vz, double E,
+                                             double h) {
+    const unsigned full = 0xffffffffu;
+    float lo = 0.0f, hi = 0.0f;
+    if (ok) signal_bounds32(P, mat, m, w, vx, vy, vz, E, h, lo, hi);
+    const unsigned lob = __float_as_uint(lo);
+    const unsigned wmax = __reduce_max_sync(full, ok ? lob : 0u);
+    const unsigned lead = __ballot_sync(full, ok && lob == wmax);
+    if (lead == 0u) return;   // no particle in this warp
+    const int lane = threadIdx.x & 31, ld = __ffs(lead) - 1;
+    if (lane == ld) atomicMax(&d.w->sig, wmax);
+    bool cand = ok && __float_as_uint(hi) >= wmax;
+    if (__ballot_sync(full, cand) != (1u << ld)) {
+    // the leader's FP64 inputs: identical inputs give the identical FP64 value
+    const long long lm = __shfl_sync(full, __double_as_longlong(m), ld);
+    const long long lw = __shfl_sync(full, __double_as_longlong(w), ld);
+    const long long lx = __shfl_sync(full, __double_as_longlong(vx), ld);
+    const long long ly = __shfl_sync(full, __double_as_longlong(vy), ld);
+    const long long lz = __shfl_sync(full, __double_as_longlong(vz), ld);
+    const long long lE = __shfl_sync(full, __double_as_longlong(E), ld);
+    const long long lh = __shfl_sync(full, __double_as_longlong(h), ld);
+    const int lmat = __shfl_sync(full, mat, ld);
+    const bool same = lane != ld && lm == __double_as_longlong(m) && lw == __double_as_longlong(w) &&
+                      lx == __double_as_longlong(vx) && ly == __double_as_longlong(vy) &&
+                      lz == __double_as_longlong(vz) && lE == __double_as_longlong(E) &&
+                      lh == __double_as_longlong(h) && lmat == mat;
+    cand = cand && !same;
+    }
+    const unsigned cm = __ballot_sync(full, cand);
+    const int first = __ffs(cm) - 1;
+    unsigned base = 0u;
+    if (lane == first) base = atomicAdd(&d.w->ccount, (unsigned)__popc(cm));
+    base = __shfl_sync(full, base, first);
+    if (cand) {
+        const unsigned idx = base + (unsigned)__popc(cm & lanemask_lt());
+        if (idx < d.cap) d.cand[idx] = make_uint2(slot, __float_as_uint(hi));
+    }
 }
 
 // Pressure (with the cut-off) and sound speed (bulk part from the isentropic derivative of the uncut
@@ -229,12 +429,6 @@ __device__ __forceinline__ void eos_pc(const DevParams &P, int mat, double rho, 
         c = sqrt(cb2 + 4.0 * P.G[mat] / 3.0 * irho);
     }
     if (p < P.p_min[mat]) p = P.p_min[mat];
-}
-
-__device__ __forceinline__ unsigned lanemask_lt() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
 }
 
 }  // namespace gsph

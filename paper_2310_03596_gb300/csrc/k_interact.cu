@@ -147,7 +147,9 @@ __device__ __forceinline__ void pair_terms(R e0, R e1, R e2, const PIn<R> &me, c
     const R izs = rcp_r(me.Z + oth.Z);
     const R dRL_t = sgn * (ton - tmn);   // tR - tL
     const R dRL_u = sgn * (uo - um);     // uR - uL
-    const R us = (add_rn(mul_rn(me.Z, um), mul_rn(oth.Z, uo)) + dRL_t) * izs;
+    // u* - (uL + uR)/2 = ((ZR - ZL)(uR - uL)/2 + (tR - tL)) / (ZL + ZR): the product of the two
+    // differences is the same at both ends, and the correction is exactly 0 between equal states
+    const R dus = (half * (oth.Z - me.Z) * (uo - um) + dRL_t) * izs;
     const R ts = (add_rn(mul_rn(oth.Z, tmn), mul_rn(me.Z, ton)) + (me.Z * oth.Z) * dRL_u) * izs;
     // transport velocities of the particles (the interface states' own unless reconstructed)
     R um0 = um, uo0 = uo;
@@ -155,8 +157,8 @@ __device__ __forceinline__ void pair_terms(R e0, R e1, R e2, const PIn<R> &me, c
         um0 = me0.vx * n0 + me0.vy * n1 + me0.vz * n2;
         uo0 = oth0.vx * n0 + oth0.vy * n1 + oth0.vz * n2;
     }
-    const R du = us - half * (um0 + uo0);        // (v_E - v0_LR) . n, the mass flux's velocity
-    const R dus = RECON ? us - half * (um + uo) : du;   // u* - mean of the Riemann states' u
+    // (v_E - v0_LR) . n, the mass flux's velocity
+    const R du = RECON ? dus + half * ((um + uo) - (um0 + uo0)) : dus;
     // interface velocity and traction at twice their value (binary scalings, exact): V = 2 v_E =
     // (v_i + v_j) + 2 du n, T = 2 sigma_E n = 2 t* n + (sigma_i n + sigma_j n) - (t_i + t_j) n
     const R du2 = dus + dus, ts2 = ts + ts, tm2 = tmn + ton;
@@ -624,7 +626,7 @@ struct PairArgs {
     const uint8_t *lab_s, *mat_s;
     const uint32_t *id_s;
     const double *dt_ptr;
-    unsigned int *sig;
+    DtArgs dtc;                  // time-step reduction (candidate filter of the new state's signal speeds)
     unsigned long long *pairs;
     unsigned long long *cost;    // pair interactions per label of this step (Sec. V cost function)
     int32_t *nreal_out, *nimage_out;
@@ -1006,7 +1008,9 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
 
     // ---- integration (Sec. II step g): forward Euler on the conserved variables, Jaumann-rate
     // stress with radial return, positions with the velocity of the step's start.
-    float sp = 0.0f;
+    // (the new state's inputs of the next time step)
+    double tm_ = 0.0, tw = 1.0, tvx = 0.0, tvy = 0.0, tvz = 0.0, tE = 0.0;
+    int tmat = 0;
     if (integrate) {
         const State &A = a.A;
         const State &B = a.B;
@@ -1192,15 +1196,14 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
             for (int k = 0; k < kNRate; ++k)
                 a.rates_out[(size_t)s * kNRate + k] = (RECON && k >= 6) ? (double)Lm[(k - 6) / 3][(k - 6) % 3] : acc.get(k);
         }
-        // next step's CFL signal speed (correctly rounded FP32, reproducible bit for bit)
-        if (MODE != PM_HEUN1) sp = signal_speed32(P, mt, mo, wo, nvx, nvy, nvz, En);
-        if (VARH) sp = __fdiv_rn(sp, a.hsf[s]);   // the time step from max s_i / h_i
+        tm_ = mo; tw = wo; tvx = nvx; tvy = nvy; tvz = nvz; tE = En; tmat = mt;
     }
-    const unsigned b = __reduce_max_sync(kFullMask, __float_as_uint(sp));
-    if (lane == 0) {
-        atomicMax(a.sig, b);
-        atomicAdd(a.pairs, (unsigned long long)pc);
-    }
+    // next step's time step: the exact FP64 maximum of the signal speeds over the candidates this filter
+    // lists (the Heun prediction's state is not a step's end)
+    if (MODE != PM_HEUN1)
+        dt_candidate(P, a.dtc, integrate, (uint32_t)s, tmat, tm_, tw, tvx, tvy, tvz, tE,
+                     (VARH && integrate) ? a.hs[s] : 1.0);
+    if (lane == 0) atomicAdd(a.pairs, (unsigned long long)pc);
     // cost per label: this pass's pairs of the particle, summed over the lanes of each label
     {
         const uint32_t lab = valid ? (uint32_t)a.lab_s[s] : 0xffffffffu;
@@ -1251,7 +1254,7 @@ static PairArgs<SPLIT> pair_args(const DevParams &P, int64_t n, const uint32_t *
                                  const double *ys, const double *zs, int kmax, const uint2 *list,
                                  const uint32_t *cnt, const uint32_t *perm, const State &A, const State &B,
                                  const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s,
-                                 const double *dt, unsigned int *sig, unsigned long long *pairs,
+                                 const double *dt, const DtArgs &dtc, unsigned long long *pairs,
                                  unsigned long long *cost, int32_t *nreal, int32_t *nimage, double *rates,
                                  const OverlapBufs *ov, void *grad, const double *hs, const float *hsf) {
     using Pos = typename Types<SPLIT>::Pos;
@@ -1259,7 +1262,7 @@ static PairArgs<SPLIT> pair_args(const DevParams &P, int64_t n, const uint32_t *
     PairArgs<SPLIT> a;
     a.P = P; a.n = n; a.skey = skey; a.cellr = cellr; a.pos = (const Pos *)pos; a.rec = (const Rec *)rec;
     a.cxs = cxs; a.xs = xs; a.ys = ys; a.zs = zs; a.kmax = kmax; a.list = list; a.cnt_in = cnt; a.perm = perm;
-    a.A = A; a.B = B; a.lab_s = lab_s; a.mat_s = mat_s; a.id_s = id_s; a.dt_ptr = dt; a.sig = sig;
+    a.A = A; a.B = B; a.lab_s = lab_s; a.mat_s = mat_s; a.id_s = id_s; a.dt_ptr = dt; a.dtc = dtc;
     a.pairs = pairs; a.cost = cost; a.nreal_out = nreal; a.nimage_out = nimage; a.rates_out = rates;
     a.flag = ov ? ov->flag : nullptr;
     a.blist = ov ? ov->blist : nullptr;
@@ -1281,7 +1284,7 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
                             const double *xs, const double *ys, const double *zs, int kmax, uint2 *list,
                             uint32_t *cnt, const uint32_t *perm, const State &A, const State &B, cudaEvent_t mid,
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
-                            unsigned int *sig, unsigned long long *pairs, unsigned long long *cost,
+                            const DtArgs &dtc, unsigned long long *pairs, unsigned long long *cost,
                             int32_t *nreal, int32_t *nimage, double *rates, const OverlapBufs *ov,
                             int stage, void *grad, const double *hs, const float *hsf, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
@@ -1290,7 +1293,7 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
     const unsigned gp = (unsigned)((n + PK_THREADS - 1) / PK_THREADS);
 #define GSPH_NL_ARGS P, n, skey, cellr, (const typename Types<SP>::Pos *)pos, cxs, xs, ys, zs, kmax, list, cnt, hs, hsf
 #define GSPH_PAIR_ARGS pair_args<SP>(P, n, skey, cellr, pos, rec, cxs, xs, ys, zs, kmax, list, cnt, perm, A, B, \
-                                     lab_s, mat_s, id_s, dt, sig, pairs, cost, nreal, nimage, rates, ov, grad, hs, hsf)
+                                     lab_s, mat_s, id_s, dt, dtc, pairs, cost, nreal, nimage, rates, ov, grad, hs, hsf)
 #define GSPH_PAIRS(MODE_)                                                                   \
     do {                                                                                    \
         const auto pa = GSPH_PAIR_ARGS;                                                      \

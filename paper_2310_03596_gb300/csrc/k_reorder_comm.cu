@@ -78,8 +78,10 @@ __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const u
                                                  uint2 *__restrict__ cellr, float *__restrict__ cxs,
                                                  void *__restrict__ pos_out, void *__restrict__ rec_out,
                                                  float *__restrict__ xf, float *__restrict__ yf,
-                                                 float *__restrict__ zf, double *__restrict__ hs,
-                                                 float *__restrict__ hsf, int *__restrict__ err) {
+                                                 float *__restrict__ zf, uint32_t *__restrict__ qx,
+                                                 uint32_t *__restrict__ qy, uint32_t *__restrict__ qz,
+                                                 double *__restrict__ hs, float *__restrict__ hsf,
+                                                 int *__restrict__ err) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     uint32_t k = skey[s];
@@ -91,10 +93,13 @@ __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const u
     }
     double x = A.f[FX][o], y = A.f[FY][o], z = A.f[FZ][o];
     xs[s] = x; ys[s] = y; zs[s] = z;
-    if (xf) {
+    if (xf) {   // the swap pass's inputs: FP32 roundings and fixed-point coordinates
         xf[s] = __double2float_rn(x);
         yf[s] = __double2float_rn(y);
         zf[s] = __double2float_rn(z);
+        qx[s] = quantise64(x, P.lo[0], P.q_s[0]);
+        qy[s] = quantise64(y, P.lo[1], P.q_s[1]);
+        qz[s] = quantise64(z, P.lo[2], P.q_s[2]);
     }
     uint8_t lab = A.label[o], mat = A.mat[o];
     // invalid values are reported and clamped so that no later kernel indexes out of range
@@ -140,15 +145,16 @@ cudaError_t launch_refresh(bool split, const DevParams &P, int64_t n, const uint
 cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint32_t *perm,
                            const State &A, double *xs, double *ys, double *zs, uint8_t *lab_s, uint8_t *mat_s,
                            uint32_t *id_s, uint2 *cellr, float *cxs, void *pos, void *rec, float *xf, float *yf,
-                           float *zf, double *hs, float *hsf, int *err, cudaStream_t s) {
+                           float *zf, uint32_t *qx, uint32_t *qy, uint32_t *qz, double *hs, float *hsf, int *err,
+                           cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     unsigned g = (unsigned)((n + 255) / 256);
     if (split)
         k_reorder<true><<<g, 256, 0, s>>>(P, n, skey, perm, A, xs, ys, zs, lab_s, mat_s, id_s, cellr, cxs, pos, rec,
-                                          xf, yf, zf, hs, hsf, err);
+                                          xf, yf, zf, qx, qy, qz, hs, hsf, err);
     else
         k_reorder<false><<<g, 256, 0, s>>>(P, n, skey, perm, A, xs, ys, zs, lab_s, mat_s, id_s, cellr, cxs, pos, rec,
-                                           xf, yf, zf, hs, hsf, err);
+                                           xf, yf, zf, qx, qy, qz, hs, hsf, err);
     return cudaGetLastError();
 }
 
@@ -334,38 +340,76 @@ cudaError_t launch_init(const DevParams &P, int64_t n, const double *pos, const 
     return cudaGetLastError();
 }
 
-// Maximum CFL signal speed over the state (bit pattern of a non-negative float, so the integer max is
-// the floating-point max), then dt = cfl * h / max. Variable h: the maximum of the FP32 quotients
-// s_i / h_i, then dt = cfl / max.
-__global__ void k_signal_max(DevParams P, int64_t n, State A, unsigned int *__restrict__ sig) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float v = 0.0f;
-    if (i < n) {
-        int m = A.mat[i] < P.nmat ? A.mat[i] : 0;
-        v = signal_speed32(P, m, A.f[FM][i], A.f[FW][i], A.f[FVX][i], A.f[FVY][i], A.f[FVZ][i], A.f[FE][i]);
-        if (P.variable_h) v = __fdiv_rn(v, __double2float_rn(A.h[i]));
+// Time step of the state A (slot order): every particle goes through the warp candidate filter, then
+// k_dt_exact takes the exact FP64 maximum over the candidates.
+__global__ void k_signal_max(DevParams P, int64_t n, State A, DtArgs d) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = i < n;
+    const int m = ok && A.mat[i] < P.nmat ? A.mat[i] : 0;
+    dt_candidate(P, d, ok, (uint32_t)(ok ? i : 0), m, ok ? A.f[FM][i] : 0.0, ok ? A.f[FW][i] : 1.0,
+                 ok ? A.f[FVX][i] : 0.0, ok ? A.f[FVY][i] : 0.0, ok ? A.f[FVZ][i] : 0.0, ok ? A.f[FE][i] : 0.0,
+                 (ok && P.variable_h) ? A.h[i] : 1.0);
+}
+
+// Exact FP64 maximum of the candidates' signal speeds (those whose upper bound reaches the largest
+// lower bound), then dt = cfl h / max (variable h: cfl / max) by the last block to finish, which also
+// clears the reduction words for the next step. S: the state the candidates' slots index.
+constexpr int DT_THREADS = 256;
+__global__ void __launch_bounds__(DT_THREADS) k_dt_exact(DevParams P, DtArgs d, State S, double *__restrict__ dt) {
+    __shared__ bool last;
+    __shared__ unsigned nev;
+    if (threadIdx.x == 0) nev = 0u;
+    __syncthreads();
+    const unsigned T = *(volatile unsigned *)&d.w->sig;
+    const unsigned nc = min(*(volatile unsigned *)&d.w->ccount, d.cap);
+    for (unsigned k = blockIdx.x * DT_THREADS + threadIdx.x; k < nc; k += gridDim.x * DT_THREADS) {
+        const uint2 c = d.cand[k];
+        if (c.y < T) continue;
+        atomicAdd(&nev, 1u);
+        const uint32_t i = c.x;
+        const int m = S.mat[i] < P.nmat ? S.mat[i] : 0;
+        double v = signal_speed64(P, m, S.f[FM][i], S.f[FW][i], S.f[FVX][i], S.f[FVY][i], S.f[FVZ][i], S.f[FE][i]);
+        if (P.variable_h) v = __ddiv_rn(v, S.h[i]);
+        if (v == v) atomicMax(&d.w->sigd, (unsigned long long)__double_as_longlong(v));   // v >= 0: bits order
     }
-    const unsigned b = __reduce_max_sync(kFullMask, __float_as_uint(v));
-    if ((threadIdx.x & 31) == 0) atomicMax(sig, b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (nev) atomicAdd(&d.w->eval, nev);
+        __threadfence();
+        last = atomicAdd(&d.w->done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const double mx = __longlong_as_double((long long)atomicAdd(&d.w->sigd, 0ull));
+        *dt = P.variable_h ? __ddiv_rn(P.cfl, mx) : __ddiv_rn(__dmul_rn(P.cfl, P.h), mx);
+        d.w->last_ccount = d.w->ccount;
+        d.w->last_eval = atomicAdd(&d.w->eval, 0u);
+        d.w->sigd = 0ull;
+        d.w->sig = 0u;
+        d.w->ccount = 0u;
+        d.w->done = 0u;
+        d.w->eval = 0u;
+    }
 }
 
-__global__ void k_finalize_dt(DevParams P, unsigned int *__restrict__ sig, double *__restrict__ dt) {
-    const double mx = (double)__uint_as_float(*sig);
-    *dt = P.variable_h ? __ddiv_rn(P.cfl, mx) : __ddiv_rn(__dmul_rn(P.cfl, P.h), mx);
-    *sig = 0u;
+static unsigned dt_grid(int64_t n) {
+    const int64_t g = (n + DT_THREADS - 1) / DT_THREADS;
+    return (unsigned)(g < 1 ? 1 : (g > 304 ? 304 : g));
 }
 
-cudaError_t launch_dt_from_state(const DevParams &P, int64_t n, const State &A, unsigned int *sig, double *dt,
+cudaError_t launch_dt_from_state(const DevParams &P, int64_t n, const State &A, const DtArgs &d, double *dt,
                                  cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(sig, 0, sizeof(unsigned int), s);
+    cudaError_t e = cudaMemsetAsync(d.w, 0, offsetof(DtWords, last_ccount), s);
     if (e != cudaSuccess) return e;
-    if (n > 0) k_signal_max<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, n, A, sig);
-    k_finalize_dt<<<1, 1, 0, s>>>(P, sig, dt);
+    if (n > 0) k_signal_max<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, n, A, d);
+    k_dt_exact<<<dt_grid(n), DT_THREADS, 0, s>>>(P, d, A, dt);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_dt(const DevParams &P, unsigned int *sig, double *dt, cudaStream_t s) {
-    k_finalize_dt<<<1, 1, 0, s>>>(P, sig, dt);
+cudaError_t launch_finalize_dt(const DevParams &P, int64_t n, const DtArgs &d, const State &S, double *dt,
+                               cudaStream_t s) {
+    k_dt_exact<<<dt_grid(n), DT_THREADS, 0, s>>>(P, d, S, dt);
     return cudaGetLastError();
 }
 

@@ -4,14 +4,17 @@
 // bounded grid barrier; a barrier that does not complete within about a second records a timeout in the
 // error word and the pass returns. For each particle type (one pass over all particles when the scene
 // has one material) and each label pair (a, b) in lexicographic order:
-//   Cg of a and b from exact fixed-point sums (the FP32 roundings of the positions clamped to the
-//   FP32 grid box, scaled to [0, 2^24] and truncated, summed in int64), biased towards the label's
-//   all-types Cg by alpha when there are several types (Sec. III.B). Every block derives the pair's
-//   geometry from the sums itself, a few threads in parallel, with the same operations, so no block
-//   waits for another to publish it;
+//   Cg of a and b from exact fixed-point sums (per axis the nearest integer to (x - lo) 2^32 / L of the
+//   FP64 position, L the grid extent, clamped to [0, 2^32 - 1] and summed in int64; Cg = lo + mean L 2^-32),
+//   biased towards the label's all-types Cg by alpha when there are several types (Sec. III.B). Every
+//   block derives the pair's geometry (FP64) from the sums itself, a few threads in parallel, with the
+//   same operations, so no block waits for another to publish it;
 //   balancing hash of every particle of a w.r.t. b and of b w.r.t. a (0 on the own side of the
 //   middle of the Cg segment, 1000 beyond the other Cg, floor(1000 t / half-distance) in between, at
-//   least 1), in FP32 on the FP32 roundings of the position and of the middle;
+//   least 1), defined in FP64. Each particle evaluates it first in FP32 from the FP32 roundings of its
+//   position and of the pair geometry, with a bound of the FP32 value's distance from the FP64 one; only
+//   a particle whose interval reaches a decision boundary (an integer hash, the middle, the other Cg)
+//   evaluates the FP64 sequence from its FP64 position;
 //   n = min(#positive on each side); the n largest hashes of each side swap labels, ties broken by
 //   the lowest persistent id. A 1001-bin histogram finds the threshold hash. When the threshold bin
 //   holds more particles than are needed, the exchange pass collects that bin into a short list, and
@@ -57,33 +60,33 @@ struct SwapScratch {
     long long cnt[kMaxLabel][SW_NT];
     unsigned long long lcur[kMaxLabel];   // fill of each label's segment (pass start)
     unsigned long long moved;
+    unsigned long long fp64;              // balancing hashes the FP32 bound left to the FP64 sequence
     unsigned int bar_count;
     unsigned int bar_gen;
 };
 
-// FP32 grid box lo, hi = lo + ext and scale s = 2^24 / ext per axis, and inv = 1 / s in FP64.
+// Fixed-point Cg per axis: q = nearest integer (ties to even) to (x - lo) s, s = 2^32 / L, clamped to
+// [0, 2^32 - 1]; Cg = lo + (sum / count) step, step = L 2^-32 (L: the grid extent).
 struct QuantParams {
-    float lo[3], hi[3], s[3];
-    double inv[3];
+    double lo[3], s[3], step[3];
 };
 
-// Exact fixed-point coordinate of an FP32 position: clamp to [lo, hi] (NaN goes to lo), scale, truncate.
-__device__ __forceinline__ long long quantise(float x, float lo, float hi, float s) {
-    const float xc = fminf(fmaxf(x, lo), hi);
-    return (long long)__float2ll_rz(__fmul_rn(__fsub_rn(xc, lo), s));
-}
-
-// Pair geometry for one side: middle M and unit direction u from the own Cg to the other, scale
-// 1000 / half-distance, all rounded to FP32 for the per-particle hash.
-struct Side {
+// Pair geometry for one side, FP64 (the definition) and its FP32 roundings (the fast path): middle M,
+// direction d from the own Cg' to the other, |d| and the half-distance ell; unit direction u = d / |d|
+// and scale 1000 / ell in FP32.
+struct SideF {
     float M[3];
     float u[3];
     float scale;
 };
+struct Side {
+    SideF f;
+    double M[3], d[3], dn, ell;
+};
 
 // Geometry of label pair (a, b) of one type from the current sums, by one thread with the operations of
-// the per-pair code (every rounding explicit, so the values are the same bits). Returns false when a
-// side is empty or the two Cgs coincide.
+// the per-pair code (every rounding explicit, so the values are the same bits), for side a. Returns false
+// when a side is empty or the two Cgs coincide.
 __device__ bool combo_geometry(const SwapScratch *S, const QuantParams &Q, double alpha, bool multi, int slot, int a,
                                int b, Side &sd) {
     const int lab[2] = {a, b};
@@ -95,11 +98,11 @@ __device__ bool combo_geometry(const SwapScratch *S, const QuantParams &Q, doubl
         if ((w < 2 || multi) && cn[w] > 0)
             for (int ax = 0; ax < 3; ++ax) {
                 const long long sm = ((volatile const long long *)&S->sums[l][sl][ax])[0];
-                cg[w][ax] = __dadd_rn((double)Q.lo[ax], __dmul_rn(__ddiv_rn((double)sm, (double)cn[w]), Q.inv[ax]));
+                const double mean = __ddiv_rn(__ll2double_rn(sm), __ll2double_rn(cn[w]));
+                cg[w][ax] = __dadd_rn(Q.lo[ax], __dmul_rn(mean, Q.step[ax]));
             }
     }
     if (!(cn[0] > 0 && cn[1] > 0)) return false;
-    double d[3];
     for (int ax = 0; ax < 3; ++ax) {
         double ca = cg[0][ax], cb = cg[1][ax];
         if (multi) {
@@ -107,26 +110,57 @@ __device__ bool combo_geometry(const SwapScratch *S, const QuantParams &Q, doubl
             ca = __dadd_rn(__dmul_rn(alpha, cg[2][ax]), __dmul_rn(beta, ca));
             cb = __dadd_rn(__dmul_rn(alpha, cg[3][ax]), __dmul_rn(beta, cb));
         }
-        sd.M[ax] = (float)__dmul_rn(__dadd_rn(ca, cb), 0.5);
-        d[ax] = __dsub_rn(cb, ca);
+        sd.M[ax] = __dmul_rn(__dadd_rn(ca, cb), 0.5);
+        sd.f.M[ax] = (float)sd.M[ax];
+        sd.d[ax] = __dsub_rn(cb, ca);
     }
-    const double dn = __dsqrt_rn(dist2_rn(d[0], d[1], d[2]));
-    if (!(dn > 0.0)) return false;
-    for (int ax = 0; ax < 3; ++ax) sd.u[ax] = (float)__ddiv_rn(d[ax], dn);
-    sd.scale = (float)__ddiv_rn(1000.0, __dmul_rn(dn, 0.5));
+    sd.dn = __dsqrt_rn(dist2_rn(sd.d[0], sd.d[1], sd.d[2]));
+    if (!(sd.dn > 0.0)) return false;
+    sd.ell = __dmul_rn(sd.dn, 0.5);
+    for (int ax = 0; ax < 3; ++ax) sd.f.u[ax] = (float)__ddiv_rn(sd.d[ax], sd.dn);
+    sd.f.scale = (float)__ddiv_rn(1000.0, sd.ell);
     return true;
 }
 
-__device__ __forceinline__ int balancing_hash(const Side &sd, float p0, float p1, float p2) {
-    const float e0 = __fsub_rn(p0, sd.M[0]);
-    const float e1 = __fsub_rn(p1, sd.M[1]);
-    const float e2 = __fsub_rn(p2, sd.M[2]);
-    const float t = __fadd_rn(__fadd_rn(__fmul_rn(e0, sd.u[0]), __fmul_rn(e1, sd.u[1])), __fmul_rn(e2, sd.u[2]));
-    if (!(t > 0.0f)) return 0;
-    const float k = floorf(__fmul_rn(t, sd.scale));
-    if (k >= (float)GSPH_BALANCE_HASH_MAX) return GSPH_BALANCE_HASH_MAX;
-    if (k < 1.0f) return 1;
+// The balancing hash in FP64, each operation rounded: t = ((e0 d0 + e1 d1) + e2 d2) / |d| with e = x - M;
+// 0 when t <= 0, 1000 when t >= ell, else floor(1000 t / ell) clamped to [1, 1000].
+__device__ int balancing_hash64(const double M[3], const double d[3], double dn, double ell, double X, double Y,
+                                double Z) {
+    const double a0 = __dmul_rn(__dsub_rn(X, M[0]), d[0]);
+    const double a1 = __dmul_rn(__dsub_rn(Y, M[1]), d[1]);
+    const double a2 = __dmul_rn(__dsub_rn(Z, M[2]), d[2]);
+    const double t = __ddiv_rn(__dadd_rn(__dadd_rn(a0, a1), a2), dn);
+    if (!(t > 0.0)) return 0;
+    if (t >= ell) return GSPH_BALANCE_HASH_MAX;
+    const double k = floor(__ddiv_rn(__dmul_rn(1000.0, t), ell));
+    if (k < 1.0) return 1;
+    if (k >= (double)GSPH_BALANCE_HASH_MAX) return GSPH_BALANCE_HASH_MAX;
     return (int)k;
+}
+
+// The balancing hash from the FP32 roundings, or -1 when FP32 cannot decide it. v = t scale carries the
+// roundings of the position, the middle, the direction and the scale and of each operation; B bounds
+// |v - V| for the FP64 value V = 1000 t / ell (twice the first-order bound plus 8 ulp of v, which covers
+// the second-order terms, the FP64 sequence's own roundings and those of the bound). V lies in
+// [v - B, v + B]: below 0 the hash is 0, above 1000.5 it is 1000 (V <= 1000 (1 + 2^-52) while t < ell),
+// and inside [k, k + 1) with k <= 998 it is max(k, 1) (V < 999 means t < ell).
+__device__ __forceinline__ int balancing_hash_fast(const SideF &g, float p0, float p1, float p2) {
+    const float e0 = __fsub_rn(p0, g.M[0]), e1 = __fsub_rn(p1, g.M[1]), e2 = __fsub_rn(p2, g.M[2]);
+    const float a0 = __fmul_rn(e0, g.u[0]), a1 = __fmul_rn(e1, g.u[1]), a2 = __fmul_rn(e2, g.u[2]);
+    const float t = __fadd_rn(__fadd_rn(a0, a1), a2);
+    const float v = __fmul_rn(t, g.scale);
+    const float S = fabsf(a0) + fabsf(a1) + fabsf(a2);
+    const float X = fabsf(g.u[0]) * (fabsf(p0) + fabsf(g.M[0])) + fabsf(g.u[1]) * (fabsf(p1) + fabsf(g.M[1])) +
+                    fabsf(g.u[2]) * (fabsf(p2) + fabsf(g.M[2]));
+    const float B = 0x1p-23f * g.scale * (X + 5.0f * S) + 0x1p-21f * fabsf(v);
+    const float lo = v - B, hi = v + B;
+    if (hi < 0.0f) return 0;
+    if (lo > 1000.5f) return GSPH_BALANCE_HASH_MAX;
+    if (lo > 0.0f && hi < 999.0f) {
+        const float k = floorf(lo);
+        if (k == floorf(hi)) return k < 1.0f ? 1 : (int)k;
+    }
+    return -1;
 }
 
 // Sum of a non-negative 33-bit value over the lanes of `peers` (lanes sharing one key), exact: the
@@ -240,8 +274,7 @@ __device__ bool grid_barrier(SwapScratch *S, unsigned nblocks, int *err) {
 }
 
 __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantParams Q, double alpha, int K, int nmat,
-                                                          const float *__restrict__ x, const float *__restrict__ y,
-                                                          const float *__restrict__ z, uint8_t *__restrict__ lab,
+                                                          const SwapPos pos, uint8_t *__restrict__ lab,
                                                           const uint8_t *__restrict__ mat,
                                                           const uint32_t *__restrict__ id, uint16_t *__restrict__ bh,
                                                           SwapScratch *__restrict__ S, SwapPair *__restrict__ pairs,
@@ -280,9 +313,9 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
         const int t = (v && multi) ? (mat[i] < nmat ? mat[i] : 0) : 0;
         long long q0 = 0, q1 = 0, q2 = 0;
         if (v) {
-            q0 = quantise(x[i], Q.lo[0], Q.hi[0], Q.s[0]);
-            q1 = quantise(y[i], Q.lo[1], Q.hi[1], Q.s[1]);
-            q2 = quantise(z[i], Q.lo[2], Q.hi[2], Q.s[2]);
+            q0 = pos.qx[i];
+            q1 = pos.qy[i];
+            q2 = pos.qz[i];
         }
         long long(*flat)[4] = &shs[0][0];
         warp_add_sums(flat, l * SW_NT + kMaxMat, v, q0, q1, q2);
@@ -326,13 +359,15 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
     const int64_t mvh = (n + 1) / 2;
     __syncthreads();
     {
-        Side *spec = (Side *)sbuf;
-        uint32_t *scnt = (uint32_t *)(sbuf + SW_MAXCOMBO * sizeof(Side));
+        SideF *spec = (SideF *)sbuf;
+        uint32_t *scnt = (uint32_t *)(sbuf + SW_MAXCOMBO * sizeof(SideF));
         for (int q = threadIdx.x; q < ncombo; q += SW_THREADS) {
             const int T = q / npairs;
             int a = 0, rem = q % npairs;
             while (rem >= K - 1 - a) { rem -= K - 1 - a; ++a; }
-            if (!combo_geometry(S, Q, alpha, multi, multi ? T : kMaxMat, a, a + 1 + rem, spec[q])) spec[q].scale = -1.0f;
+            Side g;
+            if (combo_geometry(S, Q, alpha, multi, multi ? T : kMaxMat, a, a + 1 + rem, g)) spec[q] = g.f;
+            else spec[q].scale = -1.0f;
             scnt[2 * q] = 0u;
             scnt[2 * q + 1] = 0u;
         }
@@ -342,7 +377,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
             const bool v = i < n;
             const int l = v ? (lab[i] & (kMaxLabel - 1)) : 0;
             const int T = (v && multi) ? (mat[i] < nmat ? mat[i] : 0) : 0;
-            const float px = v ? x[i] : 0.0f, py = v ? y[i] : 0.0f, pz = v ? z[i] : 0.0f;
+            const float px = v ? pos.x[i] : 0.0f, py = v ? pos.y[i] : 0.0f, pz = v ? pos.z[i] : 0.0f;
             if (seg) {   // the slot's place in its label's segment (one atomic per label and warp)
                 const unsigned peers = __match_any_sync(kFullMask, v ? l : -1);
                 unsigned long long at = 0;
@@ -356,10 +391,18 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                 const int q = T * npairs + a * (2 * K - a - 1) / 2 + (b - a - 1);
                 int key = -1;
                 if (v && o != l) {
-                    Side g = spec[q];
+                    SideF g = spec[q];
                     if (g.scale >= 0.0f) {
                         if (l == b) { g.u[0] = -g.u[0]; g.u[1] = -g.u[1]; g.u[2] = -g.u[2]; }
-                        if (balancing_hash(g, px, py, pz) > 0) key = 2 * q + (l == a ? 0 : 1);
+                        int hv = balancing_hash_fast(g, px, py, pz);
+                        if (hv < 0) {   // rare: the FP64 geometry of the pair from the sums, then the FP64 hash
+                            Side G;
+                            combo_geometry(S, Q, alpha, multi, multi ? T : kMaxMat, a, b, G);
+                            if (l == b) { G.d[0] = -G.d[0]; G.d[1] = -G.d[1]; G.d[2] = -G.d[2]; }
+                            hv = balancing_hash64(G.M, G.d, G.dn, G.ell, pos.X[i], pos.Y[i], pos.Z[i]);
+                            atomicAdd(&S->fp64, 1ull);
+                        }
+                        if (hv > 0) key = 2 * q + (l == a ? 0 : 1);
                     }
                 }
                 if (__any_sync(kFullMask, key >= 0)) {   // positives are rare once labels have settled
@@ -409,8 +452,8 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                     if (ax == 0) gn_sh[w] = cn;
                     if ((w < 2 || multi) && cn > 0) {
                         const long long sm = ((volatile long long *)&S->sums[l][sl][ax])[0];
-                        const double mean = __ddiv_rn((double)sm, (double)cn);
-                        gcg_sh[w][ax] = __dadd_rn((double)Q.lo[ax], __dmul_rn(mean, Q.inv[ax]));
+                        const double mean = __ddiv_rn(__ll2double_rn(sm), __ll2double_rn(cn));
+                        gcg_sh[w][ax] = __dadd_rn(Q.lo[ax], __dmul_rn(mean, Q.step[ax]));
                     }
                 }
                 __syncthreads();
@@ -423,10 +466,15 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                         ca = __dadd_rn(__dmul_rn(alpha, gcg_sh[2][ax]), __dmul_rn(beta, ca));
                         cb = __dadd_rn(__dmul_rn(alpha, gcg_sh[3][ax]), __dmul_rn(beta, cb));
                     }
-                    const float M = (float)__dmul_rn(__dadd_rn(ca, cb), 0.5);
+                    const double M = __dmul_rn(__dadd_rn(ca, cb), 0.5);
+                    const double d = __dsub_rn(cb, ca);
                     side_sh[0].M[ax] = M;
                     side_sh[1].M[ax] = M;
-                    gd_sh[ax] = __dsub_rn(cb, ca);
+                    side_sh[0].f.M[ax] = (float)M;
+                    side_sh[1].f.M[ax] = (float)M;
+                    side_sh[0].d[ax] = d;
+                    side_sh[1].d[ax] = -d;
+                    gd_sh[ax] = d;
                 }
                 __syncthreads();
                 if (threadIdx.x == 0) gdn_sh = have ? __dsqrt_rn(dist2_rn(gd_sh[0], gd_sh[1], gd_sh[2])) : 0.0;
@@ -435,12 +483,17 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                 if (act_g && threadIdx.x < 4) {
                     if (threadIdx.x < 3) {
                         const float u = (float)__ddiv_rn(gd_sh[threadIdx.x], gdn_sh);
-                        side_sh[0].u[threadIdx.x] = u;
-                        side_sh[1].u[threadIdx.x] = -u;
+                        side_sh[0].f.u[threadIdx.x] = u;
+                        side_sh[1].f.u[threadIdx.x] = -u;
                     } else {
-                        const float sc = (float)__ddiv_rn(1000.0, __dmul_rn(gdn_sh, 0.5));
-                        side_sh[0].scale = sc;
-                        side_sh[1].scale = sc;
+                        const double ell = __dmul_rn(gdn_sh, 0.5);
+                        const float sc = (float)__ddiv_rn(1000.0, ell);
+                        side_sh[0].f.scale = sc;
+                        side_sh[1].f.scale = sc;
+                        side_sh[0].dn = gdn_sh;
+                        side_sh[1].dn = gdn_sh;
+                        side_sh[0].ell = ell;
+                        side_sh[1].ell = ell;
                     }
                 }
                 if (threadIdx.x == 0) act_sh = act_g;
@@ -450,7 +503,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                 const bool act = act_sh != 0;
                 // -- balancing hashes and their histograms
                 if (act) {
-                    const Side s0 = side_sh[0], s1 = side_sh[1];
+                    const SideF s0 = side_sh[0].f, s1 = side_sh[1].f;
                     for (int64_t base = (int64_t)blockIdx.x * SW_THREADS; base < tot; base += gstride) {
                         const int64_t k = base + threadIdx.x;
                         int key = -1;
@@ -459,7 +512,12 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                             const uint8_t l = __ldcg(&lab[i]);
                             if ((l == a || l == b) && (type < 0 || mat[i] == type)) {
                                 const int sd = l == a ? 0 : 1;
-                                const int hv = balancing_hash(sd == 0 ? s0 : s1, x[i], y[i], z[i]);
+                                int hv = balancing_hash_fast(sd == 0 ? s0 : s1, pos.x[i], pos.y[i], pos.z[i]);
+                                if (hv < 0) {   // within the FP32 bound of a decision boundary
+                                    const Side &G = side_sh[sd];
+                                    hv = balancing_hash64(G.M, G.d, G.dn, G.ell, pos.X[i], pos.Y[i], pos.Z[i]);
+                                    atomicAdd(&S->fp64, 1ull);
+                                }
                                 bh[i] = (uint16_t)hv;
                                 if (hv > 0) key = sd * SW_BINS + hv;   // only positive hashes are counted
                             }
@@ -592,9 +650,9 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                             if (take) {
                                 sd = side;
                                 lab[i] = (uint8_t)(side == 0 ? b : a);
-                                q0 = quantise(x[i], Q.lo[0], Q.hi[0], Q.s[0]);
-                                q1 = quantise(y[i], Q.lo[1], Q.hi[1], Q.s[1]);
-                                q2 = quantise(z[i], Q.lo[2], Q.hi[2], Q.s[2]);
+                                q0 = pos.qx[i];
+                                q1 = pos.qy[i];
+                                q2 = pos.qz[i];
                             }
                         }
                     }
@@ -699,9 +757,9 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                                 // (append the segment position to the side's moved list)
                                 if (seg) mvl[sd * mvh + atomicAdd(&pr->mvcnt[sd], 1u)] = e.y;
                                 lab[i] = (uint8_t)(sd == 0 ? b : a);
-                                q0 = quantise(x[i], Q.lo[0], Q.hi[0], Q.s[0]);
-                                q1 = quantise(y[i], Q.lo[1], Q.hi[1], Q.s[1]);
-                                q2 = quantise(z[i], Q.lo[2], Q.hi[2], Q.s[2]);
+                                q0 = pos.qx[i];
+                                q1 = pos.qy[i];
+                                q2 = pos.qz[i];
                             }
                         }
                         if (__any_sync(kFullMask, mv)) warp_add_sums(dsum, sd, mv, q0, q1, q2);
@@ -727,11 +785,9 @@ size_t swap_scratch_bytes(int K, int nmat) {
 static QuantParams quant_params(const DevParams &P) {
     QuantParams Q;
     for (int a = 0; a < 3; ++a) {
-        const double ext = (double)P.dims[a] * P.cell;
-        Q.lo[a] = (float)P.lo[a];
-        Q.hi[a] = (float)(P.lo[a] + ext);
-        Q.s[a] = (float)(16777216.0 / ext);
-        Q.inv[a] = 1.0 / (double)Q.s[a];
+        Q.lo[a] = P.lo[a];
+        Q.s[a] = P.q_s[a];
+        Q.step[a] = P.q_step[a];
     }
     return Q;
 }
@@ -745,11 +801,12 @@ int swap_grid_blocks() {
     return sms * (per < 2 ? per : 2);
 }
 
-// x, y, z: FP32 roundings of the positions. scratch: swap_scratch_bytes() device bytes; bh: n uint16;
-// sidx: 2n uint32 (label segments and moved lists); grid from swap_grid_blocks().
-cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const float *x, const float *y, const float *z,
-                             uint8_t *lab, const uint8_t *mat, const uint32_t *id, void *scratch, uint16_t *bh,
-                             uint32_t *sidx, int *err, int grid, cudaStream_t s) {
+// pos: the particles' FP32 and FP64 positions and fixed-point coordinates (launch_round_positions, or the
+// reorder). scratch: swap_scratch_bytes() device bytes; bh: n uint16; sidx: 2n uint32 (label segments and
+// moved lists); grid from swap_grid_blocks().
+cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const SwapPos &pos, uint8_t *lab, const uint8_t *mat,
+                             const uint32_t *id, void *scratch, uint16_t *bh, uint32_t *sidx, int *err, int grid,
+                             cudaStream_t s) {
     if (n <= 0 || P.K_labels < 2) return cudaSuccess;
     if (grid < 1) return cudaErrorCooperativeLaunchTooLarge;
     const size_t bytes = swap_scratch_bytes(P.K_labels, P.nmat);
@@ -763,31 +820,42 @@ cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const float *x, cons
     QuantParams Q = quant_params(P);
     double alpha = P.alpha;
     int K = P.K_labels, nmat = P.nmat;
-    void *args[] = {(void *)&n, (void *)&Q, (void *)&alpha, (void *)&K, (void *)&nmat, (void *)&x, (void *)&y,
-                    (void *)&z, (void *)&lab, (void *)&mat, (void *)&id, (void *)&bh, (void *)&S, (void *)&pairs,
-                    (void *)&tl, (void *)&sidx, (void *)&err};
+    SwapPos ps = pos;
+    void *args[] = {(void *)&n, (void *)&Q, (void *)&alpha, (void *)&K, (void *)&nmat, (void *)&ps, (void *)&lab,
+                    (void *)&mat, (void *)&id, (void *)&bh, (void *)&S, (void *)&pairs, (void *)&tl, (void *)&sidx,
+                    (void *)&err};
     return cudaLaunchCooperativeKernel((const void *)k_swap_pass, dim3(grid), dim3(SW_THREADS), args, 0, s);
 }
 
-// FP32 roundings of FP64 positions (the swap pass's inputs when it runs outside a step).
-__global__ void k_round_positions(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+// The swap pass's position inputs from FP64 positions (a pass outside a step): FP32 roundings and the
+// fixed-point coordinates of the Cg sums.
+__global__ void k_round_positions(DevParams P, int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                                   const double *__restrict__ z, float *__restrict__ xf, float *__restrict__ yf,
-                                  float *__restrict__ zf) {
+                                  float *__restrict__ zf, uint32_t *__restrict__ qx, uint32_t *__restrict__ qy,
+                                  uint32_t *__restrict__ qz, QuantParams Q) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    xf[i] = __double2float_rn(x[i]);
-    yf[i] = __double2float_rn(y[i]);
-    zf[i] = __double2float_rn(z[i]);
+    const double X = x[i], Y = y[i], Z = z[i];
+    xf[i] = __double2float_rn(X);
+    yf[i] = __double2float_rn(Y);
+    zf[i] = __double2float_rn(Z);
+    qx[i] = quantise64(X, Q.lo[0], Q.s[0]);
+    qy[i] = quantise64(Y, Q.lo[1], Q.s[1]);
+    qz[i] = quantise64(Z, Q.lo[2], Q.s[2]);
 }
 
-cudaError_t launch_round_positions(int64_t n, const double *x, const double *y, const double *z, float *xf,
-                                   float *yf, float *zf, cudaStream_t s) {
+cudaError_t launch_round_positions(const DevParams &P, int64_t n, const double *x, const double *y, const double *z,
+                                   float *xf, float *yf, float *zf, uint32_t *qx, uint32_t *qy, uint32_t *qz,
+                                   cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_round_positions<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, x, y, z, xf, yf, zf);
+    k_round_positions<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, n, x, y, z, xf, yf, zf, qx, qy, qz,
+                                                                  quant_params(P));
     return cudaGetLastError();
 }
 
 // Number of particles moved by the last pass (device pointer into the scratch).
 unsigned long long *swap_moved_ptr(void *scratch) { return &((SwapScratch *)scratch)->moved; }
+// Balancing hashes of the last pass that the FP64 sequence decided (the next word).
+static_assert(offsetof(SwapScratch, fp64) == offsetof(SwapScratch, moved) + 8, "moved, fp64 adjacent");
 
 }  // namespace gsph

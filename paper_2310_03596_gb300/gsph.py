@@ -67,7 +67,8 @@ class ExchangeStats(C.Structure):
                 ("bytes_hash_broadcast", C.c_int64), ("bytes_boundary_broadcast", C.c_int64),
                 ("bytes_swap", C.c_int64), ("swapped_last_pass", C.c_int64), ("swap_passes", C.c_int64),
                 ("pairs_total", C.c_int64), ("kernel_launches", C.c_int64),
-                ("cost", C.c_int64 * MAX_LABEL), ("cost_imbalance", C.c_double)]
+                ("cost", C.c_int64 * MAX_LABEL), ("cost_imbalance", C.c_double),
+                ("dt_candidates", C.c_int64), ("dt_fp64_evaluations", C.c_int64), ("swap_fp64_hashes", C.c_int64)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("pad", "boundary", "cost")}

@@ -1,6 +1,7 @@
 """Pins of the oracle's communication hash / MGPU boundary set (Sec. II steps b-d) and the swap
 heuristic (Sec. III.A, III.B)."""
 import json
+import math
 import os
 
 import numpy as np
@@ -208,3 +209,64 @@ def test_swap_two_types_biased_cg_hand_worked():
     assert moved == g["moved"] and pairs[0, 1] == 2
     assert st.label.tolist() == g["label_out"]
     assert g["label_out"] != g["label_out_other_readings"]
+
+
+def _hash_fast_f32(M, d, dn, ell, p):
+    """numpy float32 restatement of the swap kernel's FP32 fast path of the balancing hash: the hash
+    from the FP32 roundings of the position and of the pair geometry, or -1 where the FP32 value with
+    its error bound B (twice the first-order rounding bound plus 8 ulp) reaches a decision boundary."""
+    f = np.float32
+    Mf = np.array(M, dtype=np.float64).astype(f)
+    u = (np.array(d) / dn).astype(f)
+    scale = f(1000.0 / ell)
+    pf = np.array(p, dtype=np.float64).astype(f)
+    e = pf - Mf
+    a = e * u
+    t = (a[0] + a[1]) + a[2]
+    v = f(t * scale)
+    S = np.abs(a).sum(dtype=f)
+    X = (np.abs(u) * (np.abs(pf) + np.abs(Mf))).sum(dtype=f)
+    B = f(2.0 ** -23) * scale * (X + f(5) * S) + f(2.0 ** -21) * abs(v)
+    lo, hi = f(v - B), f(v + B)
+    if hi < 0:
+        return 0
+    if lo > 1000.5:
+        return 1000
+    if lo > 0 and hi < 999 and np.floor(lo) == np.floor(hi):
+        k = int(np.floor(lo))
+        return max(k, 1)
+    return -1
+
+
+def test_balancing_hash_fp32_fast_path_never_contradicts_fp64():
+    # The swap kernel decides most balancing hashes from FP32 roundings and falls back to the FP64
+    # definition within a rounding bound of a decision boundary. Positions placed within 1e-9 .. 1e-3
+    # hash units of every kind of boundary (the middle, integer hashes, the other Cg), at Taylor-bar
+    # scale coordinates: wherever the FP32 path decides, it equals the oracle's FP64 hash.
+    rng = np.random.default_rng(44)
+    decided = total = 0
+    mid_decided = mid_total = 0
+    for trial in range(60):
+        ca = rng.uniform(-5e-3, 40e-3, 3)
+        cb = ca + rng.normal(0, 10.0 ** rng.uniform(-6, -2), 3)
+        M = (ca + cb) * 0.5
+        d = cb - ca
+        dn = math.sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2])
+        ell = dn * 0.5
+        n = d / dn
+        perp = np.cross(n, rng.normal(size=3))
+        for k in (0, 1, 2, 250, 998, 999, 1000):
+            for delta in (-1e-3, -1e-6, -1e-9, 0.0, 1e-9, 1e-6, 1e-3, 0.37):
+                V = k + delta
+                p = M + (V / 1000.0 * ell) * n + rng.uniform(-2e-3, 2e-3) * perp
+                want = orc.balancing_hash(ca, cb, p)
+                got = _hash_fast_f32(M, d, dn, ell, p)
+                total += 1
+                if got >= 0:
+                    decided += 1
+                    assert got == want, (trial, k, delta, got, want)
+                if delta == 0.37 and k < 999 and ell > 2e-4:
+                    mid_total += 1
+                    mid_decided += got >= 0
+    # away from the boundaries (mid-interval, Cgs more than 0.4 mm apart) FP32 decides
+    assert decided > 0 and mid_total > 30 and mid_decided == mid_total
