@@ -281,6 +281,49 @@ gsph_status gsph_set_dt(gsph_ctx *ctx, double dt, void *stream);
 gsph_status gsph_adjoint_step(gsph_ctx *ctx, const double *lam_next, double *lam_prev, double dt,
                               double grad[2], void *stream);
 
+/* Checkpoint and resume of a context's particle state: the 15 FP64 fields, material, label and
+ * persistent id of every particle in the current slot order (and the smoothing lengths with
+ * variable_h = 1), with the step counter (the swap heuristic's phase, Sec. III) and the next time step.
+ * The blob is self-describing (a 64-byte header: magic "GSPHSTA1", particle count, flags, step, dt)
+ * and restoring it reproduces the following steps bit for bit. gsph_state_bytes gives the blob size
+ * for the context's current particle count. dst / src: host (on_device = 0) or device memory of the
+ * context's GPU, at least gsph_state_bytes bytes; device copies are ordered on stream, host copies are
+ * synchronous. gsph_load_state accepts a blob of another particle count (the context reallocates, as
+ * gsph_set_particles does) but not one saved with another variable_h setting. Errors: INVALID_ARG
+ * (null pointers, a buffer too small, a blob that is not a state blob or does not match the context),
+ * NOT_READY (save without particles), OOM, CUDA_ERROR. */
+size_t gsph_state_bytes(const gsph_ctx *ctx);
+gsph_status gsph_save_state(gsph_ctx *ctx, void *dst, size_t bytes, int32_t on_device, void *stream);
+gsph_status gsph_load_state(gsph_ctx *ctx, const void *src, size_t bytes, int32_t on_device, void *stream);
+
+/* Gradient of an impact observable (the differentiation pattern over Sec. II steps f-g): from the
+ * context's current state y_0, `steps` forward steps in the context's precision with a device
+ * checkpoint of the state every `every` steps, the observable J = mean z velocity of the particles whose
+ * persistent ids are listed, then the reverse sweep: each segment is recomputed from its checkpoint
+ * (bit for bit) and the FP64 reverse step (gsph_adjoint_step's operations, on an internal FP64 context)
+ * runs back through it. grad receives (dJ/dY, dJ/dG) of material 0 and dJ/dv0, v0 the initial z
+ * velocity common to every particle (v_z = v0 and E = |v|^2 / 2 + e with e independent of v0 in y_0).
+ * The time-step schedule is part of J's definition: with dts given (host, `steps` values) the forward
+ * takes those steps; with dts null it takes its own CFL steps, records them in dts_out (when given), and
+ * J and its gradient are those of the run with that schedule held fixed (the CFL step's own dependence
+ * on G and v0 is not differentiated). Memory: ceil(steps / every) + every + 1 state blobs and two adjoint
+ * vectors on the device, allocated for the call. Afterwards the context holds y_steps. Covers the
+ * configurations gsph_adjoint_step covers, with the Euler integrator. Errors: INVALID_ARG (null pointers,
+ * steps or every < 1, no observed particle, an id out of range, a non-positive dt, an unsupported
+ * configuration), NOT_READY, OOM, CUDA_ERROR, DEVICE_ERROR / DEVICE_TIMEOUT from the steps. */
+typedef struct {
+    int32_t steps;              /* forward steps, >= 1 */
+    int32_t every;              /* checkpoint interval in steps, >= 1 */
+    int64_t n_obs;              /* number of observed particles, >= 1 */
+    const uint32_t *obs_ids;    /* host: their persistent ids (e.g. the rear face of an impacting body) */
+    const double *dts;          /* host, `steps` values, or null (record the CFL steps) */
+    double *dts_out;            /* host, `steps` values, or null: the schedule the call used */
+    double *J;                  /* host, out (may be null): the observable after `steps` steps */
+    int32_t want_gradient;      /* 0: forward only (J and the schedule); grad is left untouched */
+    int32_t pad;
+} gsph_adj_cfg;
+gsph_status gsph_adjoint(gsph_ctx *ctx, const gsph_adj_cfg *cfg, double grad[3], void *stream);
+
 /* Stateless radix sort (Sec. I "radix sort" of the bucket hashes): stable ascending sort of n
  * (key, value) uint32 pairs in device memory by the low key_bits bits of the key (1..32), in
  * place. workspace: device scratch of at least gsph_radix_sort_workspace(n, key_bits) bytes,
@@ -301,8 +344,9 @@ gsph_status gsph_radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, int
  * The first call on a device looks up the array's device address (once per device, with that device
  * current); make that first call before any stream capture. All calls share the one array and it
  * keeps the last call's contents: calls that overlap on the GPU (two streams, two host threads)
- * race, so serialise them. Errors: INVALID_ARG (null pointers, n out of range, key_bits not in
- * 1..32), CUDA_ERROR. */
+ * race, so serialise them. The looked-up address stays cached for the life of the process: a
+ * cudaDeviceReset of that device invalidates it, so do not reset a device this entry point has run on.
+ * Errors: INVALID_ARG (null pointers, n out of range, key_bits not in 1..32), CUDA_ERROR. */
 #define GSPH_SORT_NOALLOC_MAX_N 1048576
 #define GSPH_SORT_NOALLOC_BYTES 9439232
 gsph_status gsph_radix_sort_pairs_noalloc(uint32_t *keys, uint32_t *vals, int64_t n, int32_t key_bits,

@@ -1,17 +1,14 @@
-"""Gradient of an impact observable through the hand-written adjoint of the step.
+"""Gradient of an impact observable through the library's checkpointed adjoint (gsph_adjoint).
 
 Observable J = mean z velocity, after N steps, of the rear-face particles: those whose initial lattice
 z index is the top layer of the impacting cube. Parameters theta = (Y, G, v0): yield stress and shear
 modulus of material 0, and the initial z velocity of every particle.
 
-Forward: the configured precision, a device checkpoint of the full state every `every` steps, and the
-dt of every step recorded. Backward: for each segment in reverse, the segment's states are recomputed
-from its checkpoint with the recorded dts (bit for bit, the kernels are deterministic), then
-gsph_adjoint_step (reverse mode of interaction + integration, FP64, neighbour set and dt of the step
-held fixed) runs backwards through the segment. Memory: the checkpoints plus one segment of states.
-
-The gradient w.r.t. v0 comes from the adjoint of the initial state: v_z of every particle equals v0
-and the specific total energy E = |v|^2 / 2 carries dE/dv0 = v_z.
+Everything runs inside the library: the forward in the context's precision with a device checkpoint
+every `every` steps, the recompute of each segment from its checkpoint, the FP64 reverse steps, and the
+assembly of dJ/dY, dJ/dG and dJ/dv0. The time-step schedule is part of J's definition: given, or the
+forward's own CFL steps, which the gradient then holds fixed. This module only builds the scene for a
+parameter vector and wraps the call in a torch.autograd.Function.
 """
 from __future__ import annotations
 
@@ -20,10 +17,6 @@ import copy
 import numpy as np
 
 from . import gsph
-
-STATE_FIELDS = tuple(gsph.FIELDS[:15])
-INT_FIELDS = ("material", "label", "id")
-FVZ, FE = STATE_FIELDS.index("vz"), STATE_FIELDS.index("E")
 
 
 def with_parameters(scene, Y: float, G: float, v0: float):
@@ -46,99 +39,33 @@ def rear_face_ids(scene) -> np.ndarray:
     return np.where(layer == layer.max())[0].astype(np.uint32)
 
 
-def _snapshot(sol, stream=None):
-    import torch
-    snap = {}
-    for f in STATE_FIELDS:
-        t = torch.empty(sol.n, dtype=torch.float64, device="cuda")
-        sol.get_into(f, t, stream)
-        snap[f] = t
-    for f, dt in (("material", torch.uint8), ("label", torch.uint8), ("id", torch.int32)):
-        t = torch.empty(sol.n, dtype=dt, device="cuda")
-        sol.get_into(f, t, stream)
-        snap[f] = t
-    return snap
+def observable(scene, steps: int, every: int, precision: int, dts=None, want_gradient: bool = True,
+               device: int = 0):
+    """(J, (dJ/dY, dJ/dG, dJ/dv0) or None, schedule) of the scene by one gsph_adjoint call."""
+    sol = gsph.Solver.from_scene(scene, precision=precision, device=device)
+    try:
+        return sol.adjoint(steps, every, rear_face_ids(scene), dts=dts, want_gradient=want_gradient)
+    finally:
+        sol.close()
 
 
-def _restore(sol, snap, stream=None):
-    for f in STATE_FIELDS + INT_FIELDS:
-        sol.put(f, snap[f], stream)
-
-
-class ForwardRecord:
-    """A forward run with checkpoints, ready for the reverse sweep."""
-
-    def __init__(self, scene, steps: int, every: int, precision: int, device: int = 0):
-        import torch
-
-        self.scene, self.steps, self.every, self.precision = scene, steps, every, precision
-        self.fwd = gsph.Solver.from_scene(scene, precision=precision, device=device)
-        self.dts = []
-        self.ckpts = {}
-        for k in range(steps):
-            if k % every == 0:
-                self.ckpts[k] = _snapshot(self.fwd)
-            self.dts.append(self.fwd.dt())
-            self.fwd.step(1)
-        self.fwd.sync()
-        rear = rear_face_ids(scene)
-        ids = self.fwd.get("id")
-        mask = np.isin(ids, rear)
-        vz = self.fwd.get("vz")
-        self.J = float(vz[mask].mean())
-        self.lam_final = torch.zeros((15, scene.n), dtype=torch.float64, device="cuda")
-        self.lam_final[FVZ][torch.from_numpy(mask).cuda()] = 1.0 / mask.sum()
-
-    def gradient(self, device: int = 0):
-        """(dJ/dY, dJ/dG, dJ/dv0) by the reverse sweep."""
-        import torch
-
-        adj = gsph.Solver.from_scene(self.scene, precision=gsph.FP64, device=device, diagnostics=True)
-        lam = self.lam_final.clone()
-        lam_prev = torch.empty_like(lam)
-        gY = gG = 0.0
-        starts = sorted(self.ckpts)
-        for si in reversed(range(len(starts))):
-            k0 = starts[si]
-            k1 = starts[si + 1] if si + 1 < len(starts) else self.steps
-            _restore(self.fwd, self.ckpts[k0])
-            states = [self.ckpts[k0]]
-            for k in range(k0, k1 - 1):
-                self.fwd.set_dt(self.dts[k])
-                self.fwd.step(1)
-                states.append(_snapshot(self.fwd))
-            for k in reversed(range(k0, k1)):
-                _restore(adj, states[k - k0])
-                y, g = adj.adjoint_step(lam, lam_prev, self.dts[k])
-                gY += y
-                gG += g
-                lam, lam_prev = lam_prev, lam
-        torch.cuda.synchronize()
-        vz0 = torch.from_numpy(np.ascontiguousarray(self.scene.vel[:, 2])).cuda()
-        g_v0 = float(lam[FVZ].sum() + (lam[FE] * vz0).sum())
-        adj.close()
-        return gY, gG, g_v0
-
-    def close(self):
-        self.fwd.close()
-
-
-def impact_observable(scene, theta, steps: int = 200, every: int = 20, precision: int = gsph.FP32_SPLIT):
-    """J(theta) as a torch scalar differentiable w.r.t. theta = tensor([Y, G, v0]) (float64, CPU)."""
+def impact_observable(scene, theta, steps: int = 200, every: int = 20, precision: int = gsph.FP32_SPLIT,
+                      dts=None):
+    """J(theta) as a torch scalar differentiable w.r.t. theta = tensor([Y, G, v0]) (float64, CPU). J is
+    defined on the time-step schedule dts (steps values), or, when dts is None, on the schedule of the
+    forward run at theta, held fixed; the gradient is that of this J."""
     import torch
 
     class _ImpactObservable(torch.autograd.Function):
         @staticmethod
         def forward(ctx, th):
             Y, G, v0 = (float(v) for v in th.detach().cpu())
-            rec = ForwardRecord(with_parameters(scene, Y, G, v0), steps, every, precision)
-            ctx.rec = rec
-            return torch.tensor(rec.J, dtype=torch.float64)
+            J, g, _ = observable(with_parameters(scene, Y, G, v0), steps, every, precision, dts=dts)
+            ctx.g = g
+            return torch.tensor(J, dtype=torch.float64)
 
         @staticmethod
         def backward(ctx, gJ):
-            g = ctx.rec.gradient()
-            ctx.rec.close()
-            return gJ * torch.tensor(g, dtype=torch.float64)
+            return gJ * torch.tensor(ctx.g, dtype=torch.float64)
 
     return _ImpactObservable.apply(theta)

@@ -115,7 +115,8 @@ struct gsph_ctx {
     unsigned long long *cost = nullptr;        // pair interactions per label, last step
     unsigned long long *garbage = nullptr;
     DtWords *dtw = nullptr;                   // time-step reduction words
-    uint2 *dt_cand = nullptr;                 // time-step candidates (n)
+    DtCand *dt_cand = nullptr;                // time-step candidates (dt_cap)
+    uint32_t dt_cap = 0;
     unsigned long long *pairs = nullptr;
     double *dt = nullptr;
     int *err = nullptr;
@@ -139,7 +140,7 @@ struct gsph_ctx {
     std::vector<cudaEvent_t> ev;
 };
 
-static DtArgs dt_args(const gsph_ctx *c) { return DtArgs{c->dtw, c->dt_cand, (uint32_t)c->n}; }
+static DtArgs dt_args(const gsph_ctx *c) { return DtArgs{c->dtw, c->dt_cand, c->dt_cap}; }
 
 #define GSPH_CK(call)                                      \
     do {                                                   \
@@ -213,7 +214,8 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     A_(dalloc(c, &c->cost, (size_t)kMaxLabel));
     A_(dalloc(c, &c->garbage, 1));
     A_(dalloc(c, &c->dtw, 1));
-    A_(dalloc(c, &c->dt_cand, N));
+    c->dt_cap = (uint32_t)(N / 4 + 1024);
+    A_(dalloc(c, &c->dt_cand, (size_t)c->dt_cap));
     A_(dalloc(c, &c->pairs, 1));
     A_(dalloc(c, &c->dt, 1));
     A_(dalloc(c, &c->err, 1));
@@ -889,3 +891,268 @@ gsph_status gsph_get_timings(gsph_ctx *c, gsph_timings *out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Checkpoint / resume: a 64-byte header and the state arrays, each at a 256-byte aligned offset.
+// ---------------------------------------------------------------------------------------------
+namespace {
+struct StateHeader {
+    char magic[8];       // "GSPHSTA1"
+    int64_t n;
+    int32_t flags;       // bit 0: smoothing lengths present (variable_h)
+    int32_t dt_valid;    // 1: dt is the next step's time step
+    int64_t step;
+    double dt;
+    int64_t pad[3];
+};
+static_assert(sizeof(StateHeader) == 64, "state header is 64 bytes");
+constexpr char kStateMagic[8] = {'G', 'S', 'P', 'H', 'S', 'T', 'A', '1'};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Offsets of the arrays: 15 FP64 fields, material, label, id, h (variable_h). Returns the blob size.
+size_t state_layout(int64_t n, bool varh, size_t off[19]) {
+    size_t o = align256(sizeof(StateHeader));
+    for (int k = 0; k < 15; ++k) { off[k] = o; o = align256(o + (size_t)n * 8); }
+    off[15] = o; o = align256(o + (size_t)n);
+    off[16] = o; o = align256(o + (size_t)n);
+    off[17] = o; o = align256(o + (size_t)n * 4);
+    off[18] = o;
+    if (varh) o = align256(o + (size_t)n * 8);
+    return o;
+}
+
+// The state arrays of A to (out = true) or from a blob, device or host, ordered on s.
+cudaError_t copy_state_arrays(gsph_ctx *c, char *blob, bool on_device, bool out, cudaStream_t s) {
+    size_t off[19];
+    state_layout(c->n, c->cfg.variable_h != 0, off);
+    const size_t N = (size_t)c->n;
+    struct A_ { void *p; size_t bytes; };
+    A_ arr[19];
+    int na = 0;
+    for (int k = 0; k < 15; ++k) arr[na++] = {c->A.f[k], N * 8};
+    arr[na++] = {c->A.mat, N};
+    arr[na++] = {c->A.label, N};
+    arr[na++] = {c->A.id, N * 4};
+    if (c->cfg.variable_h) arr[na++] = {c->A.h, N * 8};
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : (out ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
+    for (int k = 0; k < na; ++k) {
+        cudaError_t e = out ? cudaMemcpyAsync(blob + off[k], arr[k].p, arr[k].bytes, kind, s)
+                            : cudaMemcpyAsync(arr[k].p, blob + off[k], arr[k].bytes, kind, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+}  // namespace
+
+size_t gsph_state_bytes(const gsph_ctx *c) {
+    if (!c) return 0;
+    size_t off[19];
+    return state_layout(c->n, c->cfg.variable_h != 0, off);
+}
+
+gsph_status gsph_save_state(gsph_ctx *c, void *dst, size_t bytes, int32_t on_device, void *stream) {
+    if (!c || !dst) return GSPH_INVALID_ARG;
+    if (c->n == 0) return GSPH_NOT_READY;
+    if (bytes < gsph_state_bytes(c)) return GSPH_INVALID_ARG;
+    GSPH_CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->dt_dirty) {
+        GSPH_CK(launch_dt_from_state(c->P, c->n, c->A, dt_args(c), c->dt, s));
+        c->dt_dirty = false;
+    }
+    StateHeader h{};
+    std::memcpy(h.magic, kStateMagic, 8);
+    h.n = c->n;
+    h.flags = c->cfg.variable_h ? 1 : 0;
+    h.dt_valid = 1;
+    h.step = c->step;
+    GSPH_CK(cudaMemcpyAsync(&h.dt, c->dt, sizeof(double), cudaMemcpyDeviceToHost, s));
+    GSPH_CK(cudaStreamSynchronize(s));
+    char *b = (char *)dst;
+    if (on_device) GSPH_CK(cudaMemcpy(b, &h, sizeof(h), cudaMemcpyHostToDevice));
+    else std::memcpy(b, &h, sizeof(h));
+    GSPH_CK(copy_state_arrays(c, b, on_device != 0, true, s));
+    if (!on_device) GSPH_CK(cudaStreamSynchronize(s));
+    return GSPH_OK;
+}
+
+gsph_status gsph_load_state(gsph_ctx *c, const void *src, size_t bytes, int32_t on_device, void *stream) {
+    if (!c || !src || bytes < sizeof(StateHeader)) return GSPH_INVALID_ARG;
+    GSPH_CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    StateHeader h{};
+    if (on_device) {
+        GSPH_CK(cudaStreamSynchronize(s));
+        GSPH_CK(cudaMemcpy(&h, src, sizeof(h), cudaMemcpyDeviceToHost));
+    } else {
+        std::memcpy(&h, src, sizeof(h));
+    }
+    if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.n < 1 || h.n >= ((int64_t)1 << 26) ||
+        ((h.flags & 1) != 0) != (c->cfg.variable_h != 0) || !(h.dt > 0.0 || !h.dt_valid))
+        return GSPH_INVALID_ARG;
+    size_t off[19];
+    if (bytes < state_layout(h.n, c->cfg.variable_h != 0, off)) return GSPH_INVALID_ARG;
+    if (h.n != c->n) {
+        GSPH_CK(cudaStreamSynchronize(s));
+        free_buffers(c);
+        cudaError_t e = alloc_all(c, h.n);
+        if (e != cudaSuccess) {
+            free_buffers(c);
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? GSPH_OOM : GSPH_CUDA_ERROR;
+        }
+        c->n = h.n;
+        c->swap_passes = 0;
+        c->launches = 0;
+    }
+    GSPH_CK(copy_state_arrays(c, (char *)src, on_device != 0, false, s));
+    if (h.dt_valid) GSPH_CK(cudaMemcpyAsync(c->dt, &h.dt, sizeof(double), cudaMemcpyHostToDevice, s));
+    GSPH_CK(cudaMemsetAsync(c->dtw, 0, offsetof(DtWords, last_ccount), s));
+    GSPH_CK(cudaStreamSynchronize(s));
+    c->step = h.step;
+    c->dt_dirty = !h.dt_valid;
+    c->have_step = false;
+    return GSPH_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Gradient of the impact observable: checkpointed forward, segment recompute, FP64 reverse sweep.
+// ---------------------------------------------------------------------------------------------
+namespace {
+struct DevBufs {   // device allocations of one call, freed on every return path
+    std::vector<void *> p;
+    ~DevBufs() { for (void *q : p) cudaFree(q); }
+    cudaError_t get(void **q, size_t bytes) {
+        *q = nullptr;
+        cudaError_t e = cudaMalloc(q, bytes);
+        if (e == cudaSuccess) p.push_back(*q);
+        return e;
+    }
+};
+gsph_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return GSPH_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? GSPH_OOM : GSPH_CUDA_ERROR;
+}
+}  // namespace
+
+gsph_status gsph_adjoint(gsph_ctx *c, const gsph_adj_cfg *a, double grad[3], void *stream) {
+    if (!c || !a || a->steps < 1 || a->every < 1 || a->n_obs < 1 || !a->obs_ids) return GSPH_INVALID_ARG;
+    if (a->want_gradient && !grad) return GSPH_INVALID_ARG;
+    if (c->cfg.reconstruction || c->cfg.variable_h || c->cfg.integrator) return GSPH_INVALID_ARG;
+    for (int k = 0; k < c->cfg.n_materials; ++k)
+        if (c->cfg.materials[k].eos != GSPH_EOS_LINEAR || !std::isinf(c->cfg.materials[k].p_min)) return GSPH_INVALID_ARG;
+    if (c->n == 0) return GSPH_NOT_READY;
+    const int64_t n = c->n;
+    const int N = a->steps, every = a->every;
+    if (a->dts)
+        for (int k = 0; k < N; ++k)
+            if (!(a->dts[k] > 0.0)) return GSPH_INVALID_ARG;
+    std::vector<char> obs((size_t)n, 0);
+    for (int64_t q = 0; q < a->n_obs; ++q) {
+        if ((int64_t)a->obs_ids[q] >= n) return GSPH_INVALID_ARG;
+        obs[a->obs_ids[q]] = 1;
+    }
+    GSPH_CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t sb = gsph_state_bytes(c);
+    const int nck = (N + every - 1) / every;
+    DevBufs mem;
+    std::vector<char *> ck((size_t)nck), seg((size_t)every);
+    char *fin = nullptr;
+    for (int k = 0; k < nck; ++k) { gsph_status st = from_cuda(mem.get((void **)&ck[k], sb)); if (st) return st; }
+    { gsph_status st = from_cuda(mem.get((void **)&fin, sb)); if (st) return st; }
+    std::vector<double> dts((size_t)N);
+    gsph_status st;
+    // forward: checkpoints every `every` steps, the schedule given or recorded
+    for (int k = 0; k < N; ++k) {
+        if (k % every == 0 && (st = gsph_save_state(c, ck[k / every], sb, 1, stream)) != GSPH_OK) return st;
+        if (a->dts) {
+            if ((st = gsph_set_dt(c, a->dts[k], stream)) != GSPH_OK) return st;
+            dts[k] = a->dts[k];
+        } else if ((st = gsph_get_dt(c, stream, &dts[k])) != GSPH_OK) {
+            return st;
+        }
+        if ((st = enqueue_step(c, s)) != GSPH_OK) return st;
+    }
+    if ((st = gsph_sync(c, stream)) != GSPH_OK) return st;
+    if ((st = gsph_save_state(c, fin, sb, 1, stream)) != GSPH_OK) return st;
+    if (a->dts_out) std::memcpy(a->dts_out, dts.data(), (size_t)N * sizeof(double));
+    // J: mean z velocity of the observed particles, summed in slot order
+    std::vector<uint32_t> ids((size_t)n);
+    std::vector<double> vz((size_t)n);
+    GSPH_CK(cudaMemcpyAsync(ids.data(), c->A.id, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    GSPH_CK(cudaMemcpyAsync(vz.data(), c->A.f[FVZ], (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    GSPH_CK(cudaStreamSynchronize(s));
+    double sum = 0.0;
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (ids[i] < (uint32_t)n && obs[ids[i]]) { sum += vz[i]; ++cnt; }
+    if (cnt == 0) return GSPH_INVALID_ARG;
+    if (a->J) *a->J = sum / (double)cnt;
+    if (!a->want_gradient) return GSPH_OK;
+    // dJ/dy_N: 1 / count on the observed particles' v_z, in the final slot order
+    double *lam = nullptr, *lamp = nullptr;
+    if ((st = from_cuda(mem.get((void **)&lam, (size_t)n * 15 * 8))) != GSPH_OK) return st;
+    if ((st = from_cuda(mem.get((void **)&lamp, (size_t)n * 15 * 8))) != GSPH_OK) return st;
+    for (int k = 1; k < every && k < N; ++k)
+        if ((st = from_cuda(mem.get((void **)&seg[k], sb))) != GSPH_OK) return st;
+    {
+        std::vector<double> l0((size_t)n, 0.0);
+        for (int64_t i = 0; i < n; ++i)
+            if (ids[i] < (uint32_t)n && obs[ids[i]]) l0[i] = 1.0 / (double)cnt;
+        GSPH_CK(cudaMemsetAsync(lam, 0, (size_t)n * 15 * 8, s));
+        GSPH_CK(cudaMemcpyAsync(lam + (size_t)FVZ * n, l0.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
+        GSPH_CK(cudaStreamSynchronize(s));
+    }
+    // the FP64 context of the reverse steps (diagnostics: the step's FP64 rates)
+    gsph_config hc = c->cfg;
+    hc.precision = GSPH_FP64;
+    hc.diagnostics = 1;
+    hc.overlap = 0;
+    hc.swap_period = 0;
+    gsph_ctx *hctx = nullptr;
+    if ((st = gsph_create(&hc, &hctx)) != GSPH_OK) return st;
+    struct Guard { gsph_ctx *h; ~Guard() { gsph_destroy(h); } } guard{hctx};
+    {
+        cudaError_t e = alloc_all(hctx, n);
+        if (e != cudaSuccess) return from_cuda(e);
+        hctx->n = n;
+    }
+    double gY = 0.0, gG = 0.0;
+    for (int sgi = nck - 1; sgi >= 0; --sgi) {
+        const int k0 = sgi * every, k1 = k0 + every < N ? k0 + every : N;
+        seg[0] = ck[sgi];
+        if ((st = gsph_load_state(c, ck[sgi], sb, 1, stream)) != GSPH_OK) return st;
+        for (int k = k0; k < k1 - 1; ++k) {   // recompute the segment's states with the schedule
+            if ((st = gsph_set_dt(c, dts[k], stream)) != GSPH_OK) return st;
+            if ((st = enqueue_step(c, s)) != GSPH_OK) return st;
+            if ((st = gsph_save_state(c, seg[k - k0 + 1], sb, 1, stream)) != GSPH_OK) return st;
+        }
+        for (int k = k1 - 1; k >= k0; --k) {
+            if ((st = gsph_load_state(hctx, seg[k - k0], sb, 1, stream)) != GSPH_OK) return st;
+            double g2[2] = {0.0, 0.0};
+            if ((st = gsph_adjoint_step(hctx, lam, lamp, dts[k], g2, stream)) != GSPH_OK) return st;
+            gY += g2[0];
+            gG += g2[1];
+            double *t = lam; lam = lamp; lamp = t;
+        }
+    }
+    // dJ/dv0 through the initial state: v_z = v0 and E = |v|^2 / 2 + e, dE/dv0 = v_z
+    {
+        std::vector<double> lvz((size_t)n), lE((size_t)n), vz0((size_t)n);
+        size_t off[19];
+        state_layout(n, false, off);
+        GSPH_CK(cudaMemcpyAsync(lvz.data(), lam + (size_t)FVZ * n, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+        GSPH_CK(cudaMemcpyAsync(lE.data(), lam + (size_t)FE * n, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+        GSPH_CK(cudaMemcpyAsync(vz0.data(), ck[0] + off[FVZ], (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+        GSPH_CK(cudaStreamSynchronize(s));
+        double gv = 0.0;
+        for (int64_t i = 0; i < n; ++i) gv += lvz[i] + lE[i] * vz0[i];
+        grad[0] = gY;
+        grad[1] = gG;
+        grad[2] = gv;
+    }
+    return gsph_load_state(c, fin, sb, 1, stream);
+}

@@ -278,15 +278,39 @@ __device__ __forceinline__ FErr fe_c(float v) {   // FP32 rounding of an FP64 co
 // times the FP32 ones, through the same operations) and the roundings of the bound's evaluation.
 __device__ __forceinline__ void signal_bounds32(const DevParams &P, int mat, double m, double w, double vx,
                                                 double vy, double vz, double E, double h, float &lo, float &hi) {
+    if (P.eos[mat] == 0) {
+        // Linear EOS: every quantity is non-negative, so relative errors compose. The roundings of m, w
+        // and the quotient give rho within 3u, M / rho within 5u (M's rounding), the root within 3.5u; each
+        // v component and its square within 3u, the sums within 5u, the root within 3.5u; their sum
+        // within 4.5u (u = 2^-24, first order); the quotient by h adds 2u. 2^-20 = 16u covers these, the
+        // second-order terms and the FP64 sequence's own roundings, when m, w (and h) are normal positive
+        // FP32 numbers; otherwise the interval is unbounded.
+        const float mf = __double2float_rn(m), wf = __double2float_rn(w);
+        const float fx = __double2float_rn(vx), fy = __double2float_rn(vy), fz = __double2float_rn(vz);
+        const float rho = __fdiv_rn(mf, wf);
+        const float v2 = __fadd_rn(__fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy)), __fmul_rn(fz, fz));
+        float sv = __fadd_rn(__fsqrt_rn(__fdiv_rn(P.f_Mmod[mat], rho)), __fsqrt_rn(v2));
+        bool good = mf >= 0x1p-126f && wf >= 0x1p-126f && mf < 0x1p127f && wf < 0x1p127f;
+        if (P.variable_h) {
+            const float hf = __double2float_rn(h);
+            good = good && hf >= 0x1p-126f;
+            sv = __fdiv_rn(sv, hf);
+        }
+        if (good && sv > 0.0f && sv < 0x1p120f) {
+            lo = __fmul_rn(sv, 1.0f - 0x1p-20f);
+            hi = __fmul_rn(sv, 1.0f + 0x1p-20f);
+        } else {
+            lo = 0.0f;
+            hi = __int_as_float(0x7f800000);
+        }
+        return;
+    }
     const FErr rho = fe_div(fe_in(m), fe_in(w));
     const FErr fx = fe_in(vx), fy = fe_in(vy), fz = fe_in(vz);
     const FErr v2 = fe_add(fe_add(fe_mul(fx, fx), fe_mul(fy, fy)), fe_mul(fz, fz));
     const FErr vn = fe_sqrt(v2);
     FErr s1, s2;
-    if (P.eos[mat] == 0) {
-        s1 = fe_add(fe_sqrt(fe_div(fe_c(P.f_Mmod[mat]), rho)), vn);
-        s2 = s1;
-    } else {
+    {
         const FErr rho0 = fe_c(P.f_rho0[mat]), c0 = fe_c(P.f_c0[mat]), g0 = fe_c(P.f_g0[mat]);
         const FErr sm1 = fe_c(P.f_sm1[mat]);
         const FErr one{1.0f, 0.0f};
@@ -345,10 +369,16 @@ struct DtWords {
     unsigned int sig, ccount, done, eval;
     unsigned int last_ccount, last_eval;   // the last completed reduction's counts (statistics)
 };
+// A listed candidate: its FP64 inputs, material and the upper end of its interval.
+struct __align__(16) DtCand {
+    double m, w, vx, vy, vz, E, h;
+    unsigned int hi;
+    int mat;
+};
 struct DtArgs {
     DtWords *w;
-    uint2 *cand;      // (slot, bits of hi)
-    uint32_t cap;     // list capacity (the particle count: each particle is listed at most once)
+    DtCand *cand;
+    uint32_t cap;     // list capacity; a step that lists more evaluates every particle in FP64 instead
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -359,7 +389,7 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 // Warp-collective (all 32 lanes): the candidate filter of one warp. ok: the lane has a particle whose
 // signal speed counts; its FP64 inputs and slot.
-__device__ __forceinline__ void dt_candidate(const DevParams &P, const DtArgs &d, bool ok, uint32_t slot, int mat,
+__device__ __forceinline__ void dt_candidate(const DevParams &P, const DtArgs &d, bool ok, int mat,
                                              double m, double w, double vx, double vy, double vz, double E,
                                              double h) {
     const unsigned full = 0xffffffffu;
@@ -395,7 +425,13 @@ __device__ __forceinline__ void dt_candidate(const DevParams &P, const DtArgs &d
     base = __shfl_sync(full, base, first);
     if (cand) {
         const unsigned idx = base + (unsigned)__popc(cm & lanemask_lt());
-        if (idx < d.cap) d.cand[idx] = make_uint2(slot, __float_as_uint(hi));
+        if (idx < d.cap) {
+            DtCand c;
+            c.m = m; c.w = w; c.vx = vx; c.vy = vy; c.vz = vz; c.E = E; c.h = h;
+            c.hi = __float_as_uint(hi);
+            c.mat = mat;
+            d.cand[idx] = c;
+        }
     }
 }
 

@@ -1201,7 +1201,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
     // next step's time step: the exact FP64 maximum of the signal speeds over the candidates this filter
     // lists (the Heun prediction's state is not a step's end)
     if (MODE != PM_HEUN1)
-        dt_candidate(P, a.dtc, integrate, (uint32_t)s, tmat, tm_, tw, tvx, tvy, tvz, tE,
+        dt_candidate(P, a.dtc, integrate, tmat, tm_, tw, tvx, tvy, tvz, tE,
                      (VARH && integrate) ? a.hs[s] : 1.0);
     if (lane == 0) atomicAdd(a.pairs, (unsigned long long)pc);
     // cost per label: this pass's pairs of the particle, summed over the lanes of each label

@@ -346,31 +346,76 @@ __global__ void k_signal_max(DevParams P, int64_t n, State A, DtArgs d) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool ok = i < n;
     const int m = ok && A.mat[i] < P.nmat ? A.mat[i] : 0;
-    dt_candidate(P, d, ok, (uint32_t)(ok ? i : 0), m, ok ? A.f[FM][i] : 0.0, ok ? A.f[FW][i] : 1.0,
+    dt_candidate(P, d, ok, m, ok ? A.f[FM][i] : 0.0, ok ? A.f[FW][i] : 1.0,
                  ok ? A.f[FVX][i] : 0.0, ok ? A.f[FVY][i] : 0.0, ok ? A.f[FVZ][i] : 0.0, ok ? A.f[FE][i] : 0.0,
                  (ok && P.variable_h) ? A.h[i] : 1.0);
 }
 
 // Exact FP64 maximum of the candidates' signal speeds (those whose upper bound reaches the largest
 // lower bound), then dt = cfl h / max (variable h: cfl / max) by the last block to finish, which also
-// clears the reduction words for the next step. S: the state the candidates' slots index.
+// clears the reduction words for the next step. A block loads its candidates, drops those equal bit for
+// bit to the previous candidate (neighbouring warps of a uniform region list the same inputs), compacts
+// the rest in shared memory and evaluates them densely. A list that overflowed its capacity falls back
+// to every particle of S.
 constexpr int DT_THREADS = 256;
-__global__ void __launch_bounds__(DT_THREADS) k_dt_exact(DevParams P, DtArgs d, State S, double *__restrict__ dt) {
+__device__ __forceinline__ double dt_value(const DevParams &P, int mat, double m, double w, double vx, double vy,
+                                           double vz, double E, double h) {
+    double v = signal_speed64(P, mat, m, w, vx, vy, vz, E);
+    if (P.variable_h) v = __ddiv_rn(v, h);
+    return v;
+}
+__device__ __forceinline__ bool same_inputs(const DtCand &a, const DtCand &b) {
+    return __double_as_longlong(a.m) == __double_as_longlong(b.m) && __double_as_longlong(a.w) == __double_as_longlong(b.w) &&
+           __double_as_longlong(a.vx) == __double_as_longlong(b.vx) && __double_as_longlong(a.vy) == __double_as_longlong(b.vy) &&
+           __double_as_longlong(a.vz) == __double_as_longlong(b.vz) && __double_as_longlong(a.E) == __double_as_longlong(b.E) &&
+           __double_as_longlong(a.h) == __double_as_longlong(b.h) && a.mat == b.mat;
+}
+__global__ void __launch_bounds__(DT_THREADS) k_dt_exact(DevParams P, DtArgs d, int64_t n, State S,
+                                                         double *__restrict__ dt) {
     __shared__ bool last;
-    __shared__ unsigned nev;
-    if (threadIdx.x == 0) nev = 0u;
-    __syncthreads();
+    __shared__ unsigned nev, nq;
+    __shared__ unsigned short q[DT_THREADS];
+    __shared__ DtCand prev_sh;
     const unsigned T = *(volatile unsigned *)&d.w->sig;
-    const unsigned nc = min(*(volatile unsigned *)&d.w->ccount, d.cap);
-    for (unsigned k = blockIdx.x * DT_THREADS + threadIdx.x; k < nc; k += gridDim.x * DT_THREADS) {
-        const uint2 c = d.cand[k];
-        if (c.y < T) continue;
-        atomicAdd(&nev, 1u);
-        const uint32_t i = c.x;
-        const int m = S.mat[i] < P.nmat ? S.mat[i] : 0;
-        double v = signal_speed64(P, m, S.f[FM][i], S.f[FW][i], S.f[FVX][i], S.f[FVY][i], S.f[FVZ][i], S.f[FE][i]);
-        if (P.variable_h) v = __ddiv_rn(v, S.h[i]);
-        if (v == v) atomicMax(&d.w->sigd, (unsigned long long)__double_as_longlong(v));   // v >= 0: bits order
+    const unsigned ncount = *(volatile unsigned *)&d.w->ccount;
+    if (threadIdx.x == 0) nev = 0u;
+    if (ncount <= d.cap) {
+        for (unsigned base = blockIdx.x * DT_THREADS; base < ncount; base += gridDim.x * DT_THREADS) {
+            const unsigned k = base + threadIdx.x;
+            if (threadIdx.x == 0) {
+                nq = 0u;
+                if (base > 0) prev_sh = d.cand[base - 1];
+            }
+            __syncthreads();
+            DtCand c{};
+            bool take = false;
+            if (k < ncount) {
+                c = d.cand[k];
+                take = c.hi >= T;
+                if (take && k > 0) {   // a run of equal candidates is evaluated once, at its start
+                    const DtCand p = threadIdx.x > 0 ? d.cand[k - 1] : prev_sh;
+                    take = !(p.hi >= T && same_inputs(p, c));
+                }
+            }
+            if (take) q[atomicAdd(&nq, 1u)] = (unsigned short)threadIdx.x;
+            __syncthreads();
+            const unsigned m = nq;
+            if (threadIdx.x < m) {
+                const DtCand e = d.cand[base + q[threadIdx.x]];
+                const double v = dt_value(P, e.mat, e.m, e.w, e.vx, e.vy, e.vz, e.E, e.h);
+                if (v == v) atomicMax(&d.w->sigd, (unsigned long long)__double_as_longlong(v));   // v >= 0
+            }
+            if (threadIdx.x == 0) nev += m;
+            __syncthreads();
+        }
+    } else {   // overflow: every particle of the state
+        for (int64_t i = (int64_t)blockIdx.x * DT_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * DT_THREADS) {
+            const int m = S.mat[i] < P.nmat ? S.mat[i] : 0;
+            const double v = dt_value(P, m, S.f[FM][i], S.f[FW][i], S.f[FVX][i], S.f[FVY][i], S.f[FVZ][i],
+                                      S.f[FE][i], P.variable_h ? S.h[i] : 1.0);
+            if (v == v) atomicMax(&d.w->sigd, (unsigned long long)__double_as_longlong(v));
+        }
+        if (threadIdx.x == 0 && blockIdx.x == 0) nev = (unsigned)n;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -403,13 +448,13 @@ cudaError_t launch_dt_from_state(const DevParams &P, int64_t n, const State &A, 
     cudaError_t e = cudaMemsetAsync(d.w, 0, offsetof(DtWords, last_ccount), s);
     if (e != cudaSuccess) return e;
     if (n > 0) k_signal_max<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, n, A, d);
-    k_dt_exact<<<dt_grid(n), DT_THREADS, 0, s>>>(P, d, A, dt);
+    k_dt_exact<<<dt_grid(n), DT_THREADS, 0, s>>>(P, d, n, A, dt);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finalize_dt(const DevParams &P, int64_t n, const DtArgs &d, const State &S, double *dt,
                                cudaStream_t s) {
-    k_dt_exact<<<dt_grid(n), DT_THREADS, 0, s>>>(P, d, S, dt);
+    k_dt_exact<<<dt_grid(n), DT_THREADS, 0, s>>>(P, d, n, S, dt);
     return cudaGetLastError();
 }
 

@@ -77,6 +77,13 @@ class ExchangeStats(C.Structure):
         return d
 
 
+class AdjConfig(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("every", C.c_int32), ("n_obs", C.c_int64),
+                ("obs_ids", C.POINTER(C.c_uint32)), ("dts", C.POINTER(C.c_double)),
+                ("dts_out", C.POINTER(C.c_double)), ("J", C.POINTER(C.c_double)),
+                ("want_gradient", C.c_int32), ("pad", C.c_int32)]
+
+
 class Timings(C.Structure):
     _fields_ = [("hash_sort_ms", C.c_double), ("reorder_ms", C.c_double), ("swap_ms", C.c_double),
                 ("comm_ms", C.c_double), ("interact_ms", C.c_double), ("steps", C.c_int64),
@@ -91,7 +98,8 @@ EXPORTS = ["gsph_status_str", "gsph_create", "gsph_destroy", "gsph_set_particles
            "gsph_get_field", "gsph_step", "gsph_swap_now", "gsph_sync", "gsph_get_exchange_stats",
            "gsph_get_conserved", "gsph_get_dt", "gsph_get_sizes", "gsph_set_timing", "gsph_get_timings",
            "gsph_radix_sort_workspace", "gsph_radix_sort_pairs", "gsph_radix_sort_pairs_noalloc",
-           "gsph_set_dt", "gsph_adjoint_step"]
+           "gsph_set_dt", "gsph_adjoint_step", "gsph_state_bytes", "gsph_save_state", "gsph_load_state",
+           "gsph_adjoint"]
 SORT_NOALLOC_MAX_N = 1 << 20
 
 _lib = None
@@ -131,6 +139,11 @@ def load(path: str = LIB_PATH):
         L.gsph_radix_sort_pairs_noalloc.argtypes = [vp, vp, C.c_int64, C.c_int32, vp]
         L.gsph_set_dt.argtypes = [vp, C.c_double, vp]
         L.gsph_adjoint_step.argtypes = [vp, vp, vp, C.c_double, P(C.c_double), vp]
+        L.gsph_state_bytes.argtypes = [vp]
+        L.gsph_state_bytes.restype = C.c_size_t
+        L.gsph_save_state.argtypes = [vp, vp, C.c_size_t, C.c_int32, vp]
+        L.gsph_load_state.argtypes = [vp, vp, C.c_size_t, C.c_int32, vp]
+        L.gsph_adjoint.argtypes = [vp, P(AdjConfig), P(C.c_double), vp]
         _lib = L
         return L
 
@@ -326,6 +339,57 @@ class Solver:
                                        _stream_handle(stream)), "gsph_adjoint_step")
         return g[0], g[1]
 
+    # ------------------------------------------------------------------ checkpoint / resume
+    def state_bytes(self) -> int:
+        return int(self.L.gsph_state_bytes(self.h))
+
+    def save_state(self, out=None, stream=None):
+        """The context's state as a blob: a new host uint8 array, or `out` (a host array or a device
+        tensor of at least state_bytes() bytes)."""
+        nb = self.state_bytes()
+        if out is None:
+            out = np.empty(nb, np.uint8)
+        if _is_torch(out) and out.is_cuda:
+            assert out.is_contiguous() and out.numel() * out.element_size() >= nb
+            check(self.L.gsph_save_state(self.h, out.data_ptr(), nb, 1, _stream_handle(stream)), "gsph_save_state")
+        else:
+            assert out.flags.c_contiguous and out.nbytes >= nb
+            check(self.L.gsph_save_state(self.h, out.ctypes.data, nb, 0, _stream_handle(stream)), "gsph_save_state")
+        return out
+
+    def load_state(self, blob, stream=None) -> None:
+        if _is_torch(blob) and blob.is_cuda:
+            assert blob.is_contiguous()
+            nb = blob.numel() * blob.element_size()
+            check(self.L.gsph_load_state(self.h, blob.data_ptr(), nb, 1, _stream_handle(stream)), "gsph_load_state")
+        else:
+            a = np.ascontiguousarray(blob)
+            check(self.L.gsph_load_state(self.h, a.ctypes.data, a.nbytes, 0, _stream_handle(stream)), "gsph_load_state")
+        self.n = self.sizes()[0]
+
+    def adjoint(self, steps: int, every: int, obs_ids, dts=None, want_gradient: bool = True, stream=None):
+        """gsph_adjoint: J = mean z velocity of the particles obs_ids after `steps` steps from the current
+        state and, with want_gradient, (dJ/dY, dJ/dG, dJ/dv0) by the checkpointed reverse sweep. dts: the
+        time-step schedule (steps values), or None for the run's own CFL steps, held fixed. Returns
+        (J, grad or None, the schedule used)."""
+        ids = np.ascontiguousarray(obs_ids, np.uint32)
+        a = AdjConfig()
+        a.steps, a.every, a.n_obs = int(steps), int(every), int(ids.size)
+        a.obs_ids = ids.ctypes.data_as(C.POINTER(C.c_uint32))
+        dv = None
+        if dts is not None:
+            dv = np.ascontiguousarray(dts, np.float64)
+            assert dv.size == steps
+            a.dts = dv.ctypes.data_as(C.POINTER(C.c_double))
+        out = np.empty(int(steps), np.float64)
+        a.dts_out = out.ctypes.data_as(C.POINTER(C.c_double))
+        J = C.c_double()
+        a.J = C.pointer(J)
+        a.want_gradient = int(bool(want_gradient))
+        g = (C.c_double * 3)()
+        check(self.L.gsph_adjoint(self.h, C.byref(a), g, _stream_handle(stream)), "gsph_adjoint")
+        return J.value, (tuple(g[:]) if want_gradient else None), out
+
     def set_timing(self, max_steps: int) -> None:
         check(self.L.gsph_set_timing(self.h, int(max_steps)), "gsph_set_timing")
 
@@ -335,12 +399,27 @@ class Solver:
         return t.as_dict()
 
 
+def _sort_args(keys, vals) -> int:
+    """Checks the two tensors of a sort: 32-bit integer, contiguous, the same length, on the current
+    CUDA device (the sort writes both in place). Returns their length."""
+    import torch
+
+    for t in (keys, vals):
+        if not (_is_torch(t) and t.is_cuda and t.is_contiguous() and t.dtype in (torch.int32, torch.uint32)):
+            raise ValueError("keys and vals must be contiguous 32-bit integer CUDA tensors")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError("keys and vals must be on the current CUDA device")
+    if keys.numel() != vals.numel():
+        raise ValueError("keys and vals must have the same length")
+    return int(keys.numel())
+
+
 def radix_sort_pairs(keys, vals, key_bits: int, stream=None) -> None:
     """Stable in-place sort of two uint32 device tensors (torch int32 views) by the low key_bits."""
     import torch
 
     L = load()
-    n = int(keys.numel())
+    n = _sort_args(keys, vals)
     ws_bytes = int(L.gsph_radix_sort_workspace(n, key_bits))
     ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=keys.device)
     check(L.gsph_radix_sort_pairs(keys.data_ptr(), vals.data_ptr(), n, key_bits, ws.data_ptr(), ws_bytes,
@@ -351,5 +430,6 @@ def radix_sort_pairs_noalloc(keys, vals, key_bits: int, stream=None) -> None:
     """The same sort with no allocation at all (library-owned fixed scratch, n <= SORT_NOALLOC_MAX_N),
     for callers that cannot allocate device memory. Calls that overlap on the GPU race."""
     L = load()
-    check(L.gsph_radix_sort_pairs_noalloc(keys.data_ptr(), vals.data_ptr(), int(keys.numel()), key_bits,
+    n = _sort_args(keys, vals)
+    check(L.gsph_radix_sort_pairs_noalloc(keys.data_ptr(), vals.data_ptr(), n, key_bits,
                                           _stream_handle(stream)), "gsph_radix_sort_pairs_noalloc")

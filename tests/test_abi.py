@@ -47,7 +47,7 @@ def _c_layout(tmp_path, struct, fields):
 
 @pytest.mark.parametrize("py,cname", [(gsph.Material, "gsph_material"), (gsph.Wall, "gsph_wall"),
                                       (gsph.Config, "gsph_config"), (gsph.ExchangeStats, "gsph_exchange_stats"),
-                                      (gsph.Timings, "gsph_timings")])
+                                      (gsph.Timings, "gsph_timings"), (gsph.AdjConfig, "gsph_adj_cfg")])
 def test_struct_layout_matches_header(tmp_path, py, cname):
     fields = [f for f, _ in py._fields_]
     got = _c_layout(tmp_path, cname, fields)
