@@ -94,56 +94,105 @@ def _traffic_from_profile(kernel_src: str, profile: str, kernel: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 50 ms during the timed region (the sampler
-    is running, its first row written and dropped, before the region starts)."""
+    """SM clock and clock-event reasons read during the timed region (reads only; nothing is set).
+    NVML through ctypes, sampled every 2 ms by a thread, so that a short timed region still has samples;
+    the GPU is found by its UUID. Without NVML, nvidia-smi at its shortest period (samples only when
+    the region outlasts it). The summary says why it has no samples when it has none."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    Q = ("uuid,clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
 
     def __init__(self, index: int):
         self.index = index
-        self.proc = None
-        self.path = None
+        self.rows = []
+        self.why = None
+        self.proc = self.thread = None
+        self.uuid = None
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(index).uuid)
+            self.uuid = u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            pass
+
+    def _nvml(self):
+        import ctypes as C
+        lib = C.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        h = C.c_void_p()
+        ok = -1
+        if self.uuid:
+            ok = lib.nvmlDeviceGetHandleByUUID(self.uuid.encode(), C.byref(h))
+        if ok != 0:
+            ok = lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(self.index), C.byref(h))
+        if ok != 0:
+            raise RuntimeError("no NVML handle for the device")
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        return lib, h, reasons
 
     def start(self):
+        import threading
+        try:
+            import ctypes as C
+            lib, h, reasons = self._nvml()
+            self.stop_flag = False
+
+            def run():
+                clk, mx, rs = C.c_uint(), C.c_uint(), C.c_ulonglong()
+                while not self.stop_flag:
+                    if (lib.nvmlDeviceGetClockInfo(h, 1, C.byref(clk)) == 0 and
+                            lib.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(mx)) == 0 and reasons(h, C.byref(rs)) == 0):
+                        self.rows.append((float(clk.value), float(mx.value), int(rs.value)))
+                    time.sleep(0.002)
+
+            self.thread = threading.Thread(target=run, daemon=True)
+            self.thread.start()
+            return
+        except Exception as e:   # no NVML: nvidia-smi
+            self.why = f"NVML unavailable ({e}); nvidia-smi"
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
-                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
-            t0 = time.time()
-            while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0 and self.proc.poll() is None:
-                time.sleep(0.01)
-            self.skip = 1 if os.path.getsize(self.path) > 0 else 0
-        except Exception:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "20"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception as e:
             self.proc = None
+            self.why = f"no clock source: {e}"
 
     def stop(self):
-        if self.proc is None:
-            return None
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        rows = []
-        for line in list(open(self.path))[getattr(self, "skip", 0):]:
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 8:
-                continue
+        if self.thread is not None:
+            self.stop_flag = True
+            self.thread.join(timeout=2)
+        elif self.proc is not None:
+            self.proc.terminate()
             try:
-                rows.append((float(parts[1]), float(parts[2]), parts[4:8]))
-            except ValueError:
-                continue
-        os.unlink(self.path)
-        if not rows:
-            return None
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
-        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 7 or (self.uuid and parts[0] != self.uuid):
+                    continue
+                try:
+                    bits = sum(self.BITS[nm] for nm, v in zip(names, parts[3:7]) if v.lower() == "active")
+                    self.rows.append((float(parts[1]), float(parts[2]), bits))
+                except ValueError:
+                    continue
+            os.unlink(self.path)
+        if not self.rows:
+            return {"samples": 0, "reason_no_samples": self.why or "the timed region ended before the first sample"}
+        reasons = sorted({nm for _, _, b in self.rows for nm, bit in self.BITS.items() if b & bit})
+        out = {"sm_mhz": statistics.median(r[0] for r in self.rows), "sm_max_mhz": max(r[1] for r in self.rows),
+               "reasons": reasons, "samples": len(self.rows)}
+        if self.why:
+            out["source"] = self.why
+        return out
 
 
 def reduce_max(x: float, dist, device=None) -> float:
@@ -187,6 +236,7 @@ def run_reference(args, rank: int):
     P = orc.params_of(s)
     st = orc.OracleState.from_scene(s)
     orc.lib()
+    cores = orc.set_threads(os.cpu_count() or 1)
     for k in range(args.warmup):
         orc.step(P, st, do_swap=True)
     t = time.perf_counter()
@@ -203,26 +253,55 @@ def run_reference(args, rank: int):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(full.n, full.K, full.swap_period, args.gpus),
             "pair_interactions_per_s": pairs / el,
-            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": sample + f", per-particle loops on {cores} host threads"},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def cpu_baseline():
-    """One full oracle step of the whole workload on one host core."""
+def cpu_baseline(device: int = 0):
+    """One full oracle step of the whole workload on the host cores: on one core, and with its
+    per-particle loops on every core (OpenMP). The same step on the GPU's FP32-split path from the same
+    initial state gives the per-field error of that path against the FP64 oracle."""
     from oracle import orc
-    from paper_2310_03596_gb300 import scenes
+    from paper_2310_03596_gb300 import gsph, scenes
 
     s = scenes.taylor_bar()
     P = orc.params_of(s)
-    st = orc.OracleState.from_scene(s)
     orc.lib()
-    t = time.perf_counter()
-    orc.step(P, st, do_swap=True)
-    el = time.perf_counter() - t
-    return {"value": s.n / el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"one full step (hash, sort, swap pass, comm hash, interaction, integration) of the "
-                      f"{s.n}-particle Taylor bar, {el:.1f} s on one core"}
+    out = {}
+    ncores = os.cpu_count() or 1
+    st1 = None
+    for threads in (1, ncores):
+        used = orc.set_threads(threads)
+        st = orc.OracleState.from_scene(s)
+        t = time.perf_counter()
+        orc.step(P, st, do_swap=True)
+        el = time.perf_counter() - t
+        out[used] = (s.n / el, el)
+        st1 = st
+    orc.set_threads(1)
+    sol = gsph.Solver.from_scene(s, precision=gsph.FP32_SPLIT, device=device)
+    sol.step(1)
+    sol.sync()
+    g = sol.state()
+    sol.close()
+    og = np.argsort(g["id"])
+    oo = np.argsort(st1.id)
+    err = {}
+    for f in orc.FIELDS:
+        a, b = g[f][og], getattr(st1, f)[oo]
+        err[f] = float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+    used_max = max(out)
+    v1, el1 = out[min(out)]
+    vm, elm = out[used_max]
+    return ({"value": vm, "unit": "particle-steps/s", "cores": used_max, "kind": "oracle",
+             "sample": f"one full step (hash, sort, swap pass, comm hash, interaction, integration) of the "
+                       f"{s.n}-particle Taylor bar: {elm:.1f} s with the per-particle loops on {used_max} "
+                       f"host threads (nproc {ncores}); {el1:.1f} s on one core",
+             "single_core": {"value": v1, "cores": 1, "seconds": el1}},
+            {"what": "FP32-split path after one step of the Taylor bar against the FP64 oracle's step from "
+                     "the same state: max-norm relative error per field", "max": max(err.values()),
+             "per_field": err})
 
 
 def main():
@@ -238,6 +317,8 @@ def main():
     ap.add_argument("--muscl-steps", type=int, default=20)
     ap.add_argument("--varh-steps", type=int, default=20)
     ap.add_argument("--collapse-steps", type=int, default=10)
+    ap.add_argument("--plate-steps", type=int, default=50)
+    ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -422,6 +503,65 @@ def main():
                                           if k.endswith("_ms") and v > 0},
                     "exchange_fraction": stc["exchange_fraction"], "swap_passes": stc["swap_passes"]}
 
+    # the projectile-on-plate workload: steel sphere into an aluminium plate, two materials, K = 8 x-slab
+    # labels with per-type swaps (Sec. III.B) at the scene's period
+    plate = None
+    if args.plate_steps > 0:
+        s6 = scenes.projectile_plate()
+        solp = gsph.Solver.from_scene(s6, device=local, stream=stream)
+        solp.step(3, stream)
+        solp.sync(stream)
+        solp.set_timing(args.plate_steps)
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        solp.step(args.plate_steps, stream)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        msp = p0.elapsed_time(p1)
+        tmp = solp.timings()
+        stp = solp.exchange_stats(stream)
+        solp.close()
+        plate = {"workload": "projectile_plate: steel sphere r 5 mm at 1000 m/s onto an Al plate 60 x 60 x 10 mm, "
+                             "dx 0.2 mm, two materials, K = 8 x-slab labels, per-type swaps every "
+                             f"{s6.swap_period} steps",
+                 "particles": s6.n, "value": world * s6.n * args.plate_steps / (msp * 1e-3),
+                 "unit": "particle-steps/s", "ms_per_step": msp / args.plate_steps, "steps": args.plate_steps,
+                 "phase_ms_per_step": {k[:-3]: v / max(tmp["steps"], 1) for k, v in tmp.items()
+                                       if k.endswith("_ms") and v > 0},
+                 "exchange_fraction": stp["exchange_fraction"], "swap_passes": stp["swap_passes"]}
+
+    # the adjoint workload: gradient of the rear-face mean z velocity of the 64^3 cube w.r.t. (Y, G, v0),
+    # FP32-split forward of 200 steps with a checkpoint every 20, recompute and FP64 reverse sweep, all in
+    # one gsph_adjoint call
+    adj = None
+    if args.adjoint_steps > 0:
+        from paper_2310_03596_gb300 import adjoint as adjm
+        sa = scenes.adjoint_cube()
+        ids = adjm.rear_face_ids(sa)
+        sola = gsph.Solver.from_scene(sa, device=local, stream=stream)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        Jf, _, dts = sola.adjoint(args.adjoint_steps, 20, ids, want_gradient=False, stream=stream)
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t
+        sola.close()
+        sola = gsph.Solver.from_scene(sa, device=local, stream=stream)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        Ja, ga, _ = sola.adjoint(args.adjoint_steps, 20, ids, stream=stream)
+        torch.cuda.synchronize()
+        ta = time.perf_counter() - t
+        sola.close()
+        adj = {"workload": "adjoint_cube: Al cube 64^3 at dx 1 mm, 100 m/s onto a wall; J = rear-face mean v_z",
+               "particles": sa.n, "steps": args.adjoint_steps, "checkpoint_every": 20,
+               "forward_only_ms_per_step": 1e3 * tf / args.adjoint_steps,
+               "forward_and_reverse_ms_per_step": 1e3 * ta / args.adjoint_steps,
+               "what": "one gsph_adjoint call: split forward with device checkpoints, segment recompute, FP64 "
+                       "reverse steps, dJ/d(Y, G, v0); wall time of the call (host-driven, synchronous)",
+               "J": Ja, "grad": list(ga)}
+
     # per-particle smoothing lengths (Sec. V's varying particle sizes): the rod with a fine impact end,
     # and the cost function per label there
     s4 = scenes.graded_bar()
@@ -555,13 +695,16 @@ def main():
         "muscl": muscl,
         "varh": varh,
         "collapse": collapse,
+        "projectile_plate": plate,
+        "adjoint": adj,
         "clocks": ck,
         "exchange": {k: st1[k] for k in ("boundary_total", "exchange_fraction", "bytes_boundary_broadcast",
-                                         "swapped_last_pass", "swap_passes")},
+                                         "swapped_last_pass", "swap_passes", "dt_candidates",
+                                         "dt_fp64_evaluations", "swap_fp64_hashes")},
     }
     sol.close()
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"], line["split_path_error"] = cpu_baseline(local)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

@@ -8,7 +8,8 @@
  * Conventions (all calls):
  *  - Every call returns a gsph_status; nothing aborts the process. Kernel launches are asynchronous:
  *    an error raised inside a kernel (a bounded wait that ran out, an invalid label) is recorded in
- *    the context and returned by the next synchronising call (gsph_sync, gsph_get_*).
+ *    the context and returned by the next synchronising call (gsph_sync, gsph_get_*), once: reporting
+ *    it clears it.
  *  - Caller pointers are borrowed for the duration of the call only. `on_device` = 1 means the
  *    pointer is a device pointer of the context's GPU, 0 a host pointer. Host transfers are
  *    synchronous with respect to the host; device transfers are ordered on `stream`.
@@ -213,7 +214,8 @@ void gsph_destroy(gsph_ctx *ctx);
 /* Sec. II premise: load n particles (1 <= n < 2^26). pos and vel are n x 3 row-major FP64; vol is
  * the particle volume; material and label are uint8 (material < n_materials, label < K). Mass is
  * rho0 * vol, the specific total energy |v|^2 / 2, deviatoric stress 0; ids are 0..n-1 in input
- * order. Reallocates device buffers if n grows. Errors: INVALID_ARG, OOM, CUDA_ERROR,
+ * order. Reallocates device buffers if n changes: the new set is allocated before the old one is
+ * released, so OOM leaves the context with its previous particles. Errors: INVALID_ARG, OOM, CUDA_ERROR,
  * DEVICE_ERROR (a material or label out of range, found on the device). */
 gsph_status gsph_set_particles(gsph_ctx *ctx, int64_t n, const double *pos, const double *vel,
                                const double *vol, const uint8_t *material, const uint8_t *label,
@@ -323,6 +325,17 @@ typedef struct {
     int32_t pad;
 } gsph_adj_cfg;
 gsph_status gsph_adjoint(gsph_ctx *ctx, const gsph_adj_cfg *cfg, double grad[3], void *stream);
+
+/* Failure-detection hooks (the paper has no counterpart; used by the tests of the error paths).
+ * gsph_set_wait_limit: the bounded wait of the swap pass's grid barrier gives up after spin_limit polls of
+ * about 64 ns each (0 restores the default, about a second) and records a timeout, which the next
+ * synchronising call returns as GSPH_DEVICE_TIMEOUT; extra_blocks = 1 makes the barrier expect one block
+ * more than the pass launches, so that the wait runs out in every block (the pass then returns without
+ * changing any label). Errors: INVALID_ARG (null context, extra_blocks > 1).
+ * gsph_debug_fail_alloc: the k-th device allocation the library makes from now on (any context) fails as
+ * on an exhausted device, without calling cudaMalloc; 0 turns it off. */
+gsph_status gsph_set_wait_limit(gsph_ctx *ctx, uint32_t spin_limit, uint32_t extra_blocks);
+void gsph_debug_fail_alloc(int32_t k);
 
 /* Stateless radix sort (Sec. I "radix sort" of the bucket hashes): stable ascending sort of n
  * (key, value) uint32 pairs in device memory by the low key_bits bits of the key (1..32), in

@@ -21,6 +21,9 @@
 #include <cstring>
 #include <numeric>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -617,15 +620,20 @@ void rates_all(const orc_params *P, const StateT<T> &s, const Mat<T> *mats, int6
     Buckets b = make_buckets(P, n, key.data());
     // MUSCL: the gradients of every particle first (a pair needs both ends')
     std::vector<T> G;
+    // (each particle's sums are its own: the loops over particles may run on several host threads,
+    // orc_set_threads, without changing a bit)
     if (P->reconstruction == 1) {
         G.assign((size_t)n * NGRAD, T(0.0));
+#pragma omp parallel for schedule(dynamic, 256)
         for (int64_t i = 0; i < n; ++i) grads_of(P, s, mats, b, xv, yv, zv, key, i, G.data() + NGRAD * i);
     }
     const T *gp = G.empty() ? nullptr : G.data();
     if (subset) {
+#pragma omp parallel for schedule(dynamic, 64)
         for (int64_t q = 0; q < nsub; ++q)
             rates_of(P, s, mats, b, xv, yv, zv, key, subset[q], rates + ORC_NRATE * subset[q], nreal, nimage, gp);
     } else {
+#pragma omp parallel for schedule(dynamic, 256)
         for (int64_t i = 0; i < n; ++i)
             rates_of(P, s, mats, b, xv, yv, zv, key, i, rates + ORC_NRATE * i, nreal, nimage, gp);
     }
@@ -751,6 +759,16 @@ void cg_from_sums(const Quant &q, const int64_t sum[3], int64_t cnt, double cg[3
 // C entry points
 // =============================================================================================
 extern "C" {
+
+int32_t orc_set_threads(int32_t nthreads) {
+#ifdef _OPENMP
+    omp_set_num_threads(nthreads > 0 ? nthreads : 1);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
 
 int64_t orc_flops_per_pair(void) {
     // one ordered pair of two particles in a generic state: the pair flux and its accumulation into the

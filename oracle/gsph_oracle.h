@@ -115,6 +115,10 @@ void orc_eos(const orc_params *P, int32_t mat, double rho, double e, double *p, 
  * the pair flux and its accumulation into one end's 15 rates, counted by running them on a counting
  * scalar type. */
 int64_t orc_flops_per_pair(void);
+
+/* Host threads of the per-particle loops (rates, gradients): results are the same for any count.
+ * Returns the count in effect (1 when built without OpenMP). */
+int32_t orc_set_threads(int32_t nthreads);
 /* Time step from the current state: CFL * h / max_i (c_i + |v_i|). */
 /* CFL signal speed c + |v| of particle i in FP64 (the quantity whose maximum sets the time step). */
 double orc_signal_speed(const orc_params *P, const orc_state *S, int64_t i);

@@ -31,8 +31,10 @@ def build(force: bool = False) -> str:
                                                   os.path.getmtime(os.path.join(HERE, "gsph_oracle.h")))):
         return LIB_PATH
     tmp = LIB_PATH + f".{os.getpid()}.tmp"
-    subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                           "-shared", "-o", tmp, SRC])
+    base = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, SRC]
+    # the per-particle loops may use OpenMP host threads (orc_set_threads); without it they run on one
+    if subprocess.call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL) != 0:
+        subprocess.check_call(base)
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
 
@@ -107,6 +109,9 @@ def lib():
             L.orc_forward_gradient.restype = C.c_double
             L.orc_flops_per_pair.argtypes = []
             L.orc_flops_per_pair.restype = C.c_int64
+            L.orc_set_threads.argtypes = [C.c_int32]
+            L.orc_set_threads.restype = C.c_int32
+            L.orc_set_threads(1)
             _lib = L
     return _lib
 
@@ -369,6 +374,11 @@ def step(P: Params, st: OracleState, do_swap: bool = False, want_rates: bool = F
                    _ptr(r, C.c_double) if r is not None else None, _ptr(dtv, C.c_double))
     return {"key": key, "comm": comm, "flag": flag, "count": cnt, "nreal": nr, "nimage": ni,
             "rates": r, "dt": float(dtv[0])}
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's per-particle loops (1 by default); returns the count in effect."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def flops_per_pair() -> int:

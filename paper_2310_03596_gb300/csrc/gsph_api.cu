@@ -54,7 +54,7 @@ cudaError_t launch_round_positions(const DevParams &P, int64_t n, const double *
                                    cudaStream_t s);
 cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const SwapPos &pos, uint8_t *lab, const uint8_t *mat,
                              const uint32_t *id, void *scratch, uint16_t *bh, uint32_t *sidx, int *err, int grid,
-                             cudaStream_t s);
+                             unsigned spin_limit, unsigned extra_blocks, cudaStream_t s);
 int swap_grid_blocks();
 unsigned long long *swap_moved_ptr(void *scratch);
 // k_adjoint.cu
@@ -132,6 +132,7 @@ struct gsph_ctx {
     double *adj_scratch = nullptr;   // allocated on the first adjoint step
     size_t adj_scratch_n = 0;
     int swap_grid = 0;
+    unsigned wait_spin = 0, wait_extra = 0;   // the swap barrier's bounded wait (0: default limit)
     // statistics
     int64_t swap_passes = 0;
     int64_t launches = 0;
@@ -158,7 +159,15 @@ static void free_buffers(gsph_ctx *c) {
     c->n = 0;
 }
 
+// Failure-detection test hook: the k-th device allocation from now on (0: none) fails as on an
+// exhausted device, before cudaMalloc is called.
+static int g_alloc_fail_at = 0;
+
 template <class T> static cudaError_t dalloc(gsph_ctx *c, T **p, size_t count) {
+    if (g_alloc_fail_at > 0 && --g_alloc_fail_at == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     void *q = nullptr;
     cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
     if (e != cudaSuccess) { *p = nullptr; return e; }
@@ -258,6 +267,34 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     if (e == cudaSuccess) e = cudaMemset(c->label_off, 0, (kMaxLabel + 1) * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->swap_scratch, 0, swap_scratch_bytes(c->P.K_labels, c->P.nmat));
     return e;
+}
+
+// Buffers for n particles. A trial set is allocated beside the current one first, so that a failed
+// allocation leaves the context (its particles and buffers) as it was; then the current set is
+// replaced. (Only if the second allocation fails after the trial succeeded - another user took the
+// memory in between - is the context left without particles.)
+static gsph_status realloc_for(gsph_ctx *c, int64_t n) {
+    gsph_ctx *t = new (std::nothrow) gsph_ctx();
+    if (!t) return GSPH_OOM;
+    t->cfg = c->cfg;
+    t->P = c->P;
+    t->split = c->split;
+    cudaError_t e = alloc_all(t, n);
+    free_buffers(t);
+    delete t;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? GSPH_OOM : GSPH_CUDA_ERROR;
+    }
+    free_buffers(c);
+    e = alloc_all(c, n);
+    if (e != cudaSuccess) {
+        free_buffers(c);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? GSPH_OOM : GSPH_CUDA_ERROR;
+    }
+    c->n = n;
+    return GSPH_OK;
 }
 
 static bool config_ok(const gsph_config *c) {
@@ -406,7 +443,7 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     if (do_swap) {
         const SwapPos sp{c->xf, c->yf, c->zf, c->xs, c->ys, c->zs, c->qx, c->qy, c->qz};
         GSPH_CK(launch_swap_pass(P, n, sp, c->lab_s, c->mat_s, c->id_s, c->swap_scratch, c->bh, c->sidx, c->err,
-                                 c->swap_grid, s));
+                                 c->swap_grid, c->wait_spin, c->wait_extra, s));
         ++c->swap_passes;
         c->launches += swap_pass_launches(P);
     }
@@ -480,6 +517,10 @@ static gsph_status read_err(gsph_ctx *c, cudaStream_t s) {
     int h = 0;
     GSPH_CK(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     GSPH_CK(cudaStreamSynchronize(s));
+    if (h) {   // reported once: the word is cleared for the work that follows
+        GSPH_CK(cudaMemsetAsync(c->err, 0, sizeof(int), s));
+        GSPH_CK(cudaStreamSynchronize(s));
+    }
     if (h & kErrTimeout) return GSPH_DEVICE_TIMEOUT;
     if (h) return GSPH_DEVICE_ERROR;
     return GSPH_OK;
@@ -568,14 +609,8 @@ gsph_status gsph_set_particles(gsph_ctx *c, int64_t n, const double *pos, const 
     cudaStream_t s = (cudaStream_t)stream;
     GSPH_CK(cudaStreamSynchronize(s));
     if (n != c->n) {
-        free_buffers(c);
-        cudaError_t e = alloc_all(c, n);
-        if (e != cudaSuccess) {
-            free_buffers(c);
-            cudaGetLastError();
-            return e == cudaErrorMemoryAllocation ? GSPH_OOM : GSPH_CUDA_ERROR;
-        }
-        c->n = n;
+        gsph_status st = realloc_for(c, n);
+        if (st != GSPH_OK) return st;
     }
     void *stage = nullptr;
     const double *dpos = pos, *dvel = vel, *dvol = vol;
@@ -706,7 +741,7 @@ gsph_status gsph_swap_now(gsph_ctx *c, void *stream) {
                                    c->qz, s));
     const SwapPos sp{c->xf, c->yf, c->zf, c->A.f[FX], c->A.f[FY], c->A.f[FZ], c->qx, c->qy, c->qz};
     GSPH_CK(launch_swap_pass(c->P, c->n, sp, c->A.label, c->A.mat, c->A.id, c->swap_scratch, c->bh, c->sidx, c->err,
-                             c->swap_grid, s));
+                             c->swap_grid, c->wait_spin, c->wait_extra, s));
     ++c->swap_passes;
     c->launches += 1 + swap_pass_launches(c->P);
     return GSPH_OK;
@@ -995,14 +1030,8 @@ gsph_status gsph_load_state(gsph_ctx *c, const void *src, size_t bytes, int32_t 
     if (bytes < state_layout(h.n, c->cfg.variable_h != 0, off)) return GSPH_INVALID_ARG;
     if (h.n != c->n) {
         GSPH_CK(cudaStreamSynchronize(s));
-        free_buffers(c);
-        cudaError_t e = alloc_all(c, h.n);
-        if (e != cudaSuccess) {
-            free_buffers(c);
-            cudaGetLastError();
-            return e == cudaErrorMemoryAllocation ? GSPH_OOM : GSPH_CUDA_ERROR;
-        }
-        c->n = h.n;
+        gsph_status st = realloc_for(c, h.n);
+        if (st != GSPH_OK) return st;
         c->swap_passes = 0;
         c->launches = 0;
     }
@@ -1156,3 +1185,15 @@ gsph_status gsph_adjoint(gsph_ctx *c, const gsph_adj_cfg *a, double grad[3], voi
     }
     return gsph_load_state(c, fin, sb, 1, stream);
 }
+
+// ---------------------------------------------------------------------------------------------
+// Failure-detection hooks (tests)
+// ---------------------------------------------------------------------------------------------
+gsph_status gsph_set_wait_limit(gsph_ctx *c, uint32_t spin_limit, uint32_t extra_blocks) {
+    if (!c || extra_blocks > 1) return GSPH_INVALID_ARG;
+    c->wait_spin = spin_limit;
+    c->wait_extra = extra_blocks;
+    return GSPH_OK;
+}
+
+void gsph_debug_fail_alloc(int32_t k) { g_alloc_fail_at = k > 0 ? k : 0; }

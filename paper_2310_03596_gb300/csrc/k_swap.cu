@@ -244,7 +244,16 @@ __device__ void block_inclusive_scan(uint32_t *a, int nv) {
 
 // Bounded grid barrier (generation counter). Returns false, with the timeout bit set, when the
 // other blocks do not arrive within the spin limit.
-__device__ bool grid_barrier(SwapScratch *S, unsigned nblocks, int *err) {
+// Bounded wait of the swap pass's grid barrier: spin limit (iterations of about 64 ns) and blocks the
+// barrier expects beyond those launched (0 in normal use; a failure-detection test makes the wait run
+// out with 1 and a short limit).
+struct WaitCfg {
+    unsigned spin_limit;
+    unsigned extra_blocks;
+};
+
+__device__ bool grid_barrier(SwapScratch *S, unsigned nblocks, int *err, const WaitCfg &wc) {
+    nblocks += wc.extra_blocks;
     __shared__ int ok_sh;
     __threadfence();   // this thread's writes of the phase are visible device-wide before arrival
     __syncthreads();
@@ -259,7 +268,7 @@ __device__ bool grid_barrier(SwapScratch *S, unsigned nblocks, int *err) {
         } else {
             unsigned it = 0;
             while (gen.load(cuda::memory_order_acquire) == g) {
-                if (++it > (1u << 24)) {   // about a second with the back-off below
+                if (++it > wc.spin_limit) {   // default 2^24: about a second with the back-off below
                     atomicOr(err, kErrTimeout);
                     ok = 0;
                     break;
@@ -279,7 +288,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                                                           const uint32_t *__restrict__ id, uint16_t *__restrict__ bh,
                                                           SwapScratch *__restrict__ S, SwapPair *__restrict__ pairs,
                                                           uint2 *__restrict__ tl, uint32_t *__restrict__ sidx,
-                                                          int *__restrict__ err) {
+                                                          int *__restrict__ err, const WaitCfg wc) {
     __shared__ long long shs[kMaxLabel][SW_NT][4];
     __shared__ uint32_t hs[2][SW_BINS];
     __shared__ uint32_t ids[2][SW_ID_BINS];
@@ -328,7 +337,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
         for (int a = 0; a < 3; ++a) atomicAdd((unsigned long long *)&S->sums[l][t][a], (unsigned long long)shs[l][t][a]);
         atomicAdd((unsigned long long *)&S->cnt[l][t], (unsigned long long)shs[l][t][3]);
     }
-    if (!grid_barrier(S, nb, err)) return;
+    if (!grid_barrier(S, nb, err, wc)) return;
 
     // ---- speculative pass (exact): positive-hash counts of every (type, label pair) at the pass-start
     // labels and sums. A pair with no positive hash on one side swaps nothing and changes nothing, so
@@ -415,7 +424,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
         __syncthreads();
         for (int q = threadIdx.x; q < 2 * ncombo; q += SW_THREADS)
             if (scnt[q]) atomicAdd(&pairs[q >> 1].spec[q & 1], scnt[q]);
-        if (!grid_barrier(S, nb, err)) return;
+        if (!grid_barrier(S, nb, err, wc)) return;
         if (threadIdx.x == 0) {
             int f = ncombo;
             for (int q = 0; q < ncombo && f == ncombo; ++q)
@@ -543,7 +552,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                         if (v) atomicAdd(&(&pr->hist[0][0])[k], v);
                     }
                 }
-                if (!grid_barrier(S, nb, err)) return;
+                if (!grid_barrier(S, nb, err, wc)) return;
                 if (!act) continue;
                 // n = min(#positive): no scans when a side has none (the same decision in every block)
                 if (((volatile uint32_t *)&pr->npos[0])[0] == 0u || ((volatile uint32_t *)&pr->npos[1])[0] == 0u) continue;
@@ -599,7 +608,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                             const uint32_t v = (&ids[0][0])[k];
                             if (v) atomicAdd(&(&pr->idh[pass][0][0])[k], v);
                         }
-                        if (!grid_barrier(S, nb, err)) return;
+                        if (!grid_barrier(S, nb, err, wc)) return;
                         for (int k = threadIdx.x; k < 2 * SW_ID_BINS; k += SW_THREADS)
                             (&ids[0][0])[k] = ((volatile uint32_t *)&pr->idh[pass][0][0])[k];
                         __syncthreads();
@@ -683,7 +692,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                 }
                 __syncthreads();
                 flush_moved(S, dsum, a, b, type);
-                if (!grid_barrier(S, nb, err)) return;
+                if (!grid_barrier(S, nb, err, wc)) return;
                 // (the moved particles exchange their segment positions once all of the pair's moves are in)
                 auto exchange_positions = [&]() -> bool {
                     if (!seg) return true;
@@ -693,7 +702,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                         byl[ka] = ib;
                         byl[kb] = ia;
                     }
-                    return grid_barrier(S, nb, err);
+                    return grid_barrier(S, nb, err, wc);
                 };
                 if (!use_list || !(idsel_sh[0] || idsel_sh[1])) {
                     if (!exchange_positions()) return;
@@ -767,7 +776,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                 }
                 __syncthreads();
                 flush_moved(S, dsum, a, b, type);
-                if (!grid_barrier(S, nb, err)) return;
+                if (!grid_barrier(S, nb, err, wc)) return;
                 if (!exchange_positions()) return;
             }
     }
@@ -806,7 +815,7 @@ int swap_grid_blocks() {
 // moved lists); grid from swap_grid_blocks().
 cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const SwapPos &pos, uint8_t *lab, const uint8_t *mat,
                              const uint32_t *id, void *scratch, uint16_t *bh, uint32_t *sidx, int *err, int grid,
-                             cudaStream_t s) {
+                             unsigned spin_limit, unsigned extra_blocks, cudaStream_t s) {
     if (n <= 0 || P.K_labels < 2) return cudaSuccess;
     if (grid < 1) return cudaErrorCooperativeLaunchTooLarge;
     const size_t bytes = swap_scratch_bytes(P.K_labels, P.nmat);
@@ -821,9 +830,10 @@ cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const SwapPos &pos, 
     double alpha = P.alpha;
     int K = P.K_labels, nmat = P.nmat;
     SwapPos ps = pos;
+    WaitCfg wc{spin_limit > 0 ? spin_limit : (1u << 24), extra_blocks};
     void *args[] = {(void *)&n, (void *)&Q, (void *)&alpha, (void *)&K, (void *)&nmat, (void *)&ps, (void *)&lab,
                     (void *)&mat, (void *)&id, (void *)&bh, (void *)&S, (void *)&pairs, (void *)&tl, (void *)&sidx,
-                    (void *)&err};
+                    (void *)&err, (void *)&wc};
     return cudaLaunchCooperativeKernel((const void *)k_swap_pass, dim3(grid), dim3(SW_THREADS), args, 0, s);
 }
 

@@ -99,7 +99,7 @@ EXPORTS = ["gsph_status_str", "gsph_create", "gsph_destroy", "gsph_set_particles
            "gsph_get_conserved", "gsph_get_dt", "gsph_get_sizes", "gsph_set_timing", "gsph_get_timings",
            "gsph_radix_sort_workspace", "gsph_radix_sort_pairs", "gsph_radix_sort_pairs_noalloc",
            "gsph_set_dt", "gsph_adjoint_step", "gsph_state_bytes", "gsph_save_state", "gsph_load_state",
-           "gsph_adjoint"]
+           "gsph_adjoint", "gsph_set_wait_limit", "gsph_debug_fail_alloc"]
 SORT_NOALLOC_MAX_N = 1 << 20
 
 _lib = None
@@ -144,6 +144,9 @@ def load(path: str = LIB_PATH):
         L.gsph_save_state.argtypes = [vp, vp, C.c_size_t, C.c_int32, vp]
         L.gsph_load_state.argtypes = [vp, vp, C.c_size_t, C.c_int32, vp]
         L.gsph_adjoint.argtypes = [vp, P(AdjConfig), P(C.c_double), vp]
+        L.gsph_set_wait_limit.argtypes = [vp, C.c_uint32, C.c_uint32]
+        L.gsph_debug_fail_alloc.argtypes = [C.c_int32]
+        L.gsph_debug_fail_alloc.restype = None
         _lib = L
         return L
 
