@@ -513,13 +513,13 @@ def main():
         solp.sync(stream)
         solp.set_timing(args.plate_steps)
         torch.cuda.synchronize()
-        p0 = torch.cuda.Event(enable_timing=True)
-        p1 = torch.cuda.Event(enable_timing=True)
-        p0.record(stream)
+        pe0 = torch.cuda.Event(enable_timing=True)
+        pe1 = torch.cuda.Event(enable_timing=True)
+        pe0.record(stream)
         solp.step(args.plate_steps, stream)
-        p1.record(stream)
+        pe1.record(stream)
         torch.cuda.synchronize()
-        msp = p0.elapsed_time(p1)
+        msp = pe0.elapsed_time(pe1)
         tmp = solp.timings()
         stp = solp.exchange_stats(stream)
         solp.close()

@@ -376,6 +376,7 @@ static void fill_params(const gsph_config &c, DevParams &P) {
     P.f_k5 = (float)P.k5;
     if (!std::isnormal(P.f_inv_cell)) P.f_inv_cell = std::nanf("");   // the hash then always divides in FP64
     P.f_inv_h = (float)(1.0 / c.h);
+    P.wall_reach = P.cell * (1.0 + 1e-6);
     for (int a = 0; a < 3; ++a) {
         const double ext = (double)c.grid_dims[a] * P.cell;
         P.q_s[a] = 4294967296.0 / ext;

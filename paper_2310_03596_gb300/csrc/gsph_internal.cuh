@@ -57,6 +57,7 @@ struct DevParams {
     // fixed-point Cg of the swap pass (Sec. III.A): q = nearest integer to (x - lo) q_s, q_s = 2^32 / L,
     // Cg = lo + mean(q) q_step, q_step = L 2^-32, L = dims * 2h the grid extent per axis
     double q_s[3], q_step[3];
+    double wall_reach;       // (2h)(1 + 1e-6): beyond this distance from a wall plane no image is in the support
 };
 constexpr double kVarBand = 1.0e-3;
 

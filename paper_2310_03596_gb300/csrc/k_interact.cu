@@ -885,6 +885,15 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
     for (int src = (__any_sync(kFullMask, (int)cnt > kmax) ? 0 : 1); src <= P.nwalls; ++src) {
         const int wax = src > 0 ? P.wall_axis[src - 1] : -1;
         const double wpos = src > 0 ? P.wall_pos[src - 1] : 0.0;
+        // a particle farther than the support from the wall plane (with a 1e-6 margin over the FP64
+        // roundings) has no image neighbour: |x_i - x_j'| >= |x_i - w| for j on the same side. Warps with
+        // no particle near the wall skip the mirrored search.
+        bool near = src == 0;
+        if (src > 0) {
+            const double dw = __dsub_rn(wax == 0 ? X : (wax == 1 ? Y : Z), wpos);
+            near = fabs(dw) <= P.wall_reach;
+            if (!__any_sync(kFullMask, active && near)) continue;
+        }
         double CX = X, CY = Y, CZ = Z;
         int bx = cx, by = cy, bz = cz;
         R ox = mrx, oy = mry, oz = mrz;
@@ -909,7 +918,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
                 ox = (R)FX_; oy = (R)FY_; oz = (R)FZ_;
             }
         }
-        const bool mine = active && (src > 0 || (int)cnt > kmax);
+        const bool mine = active && (src > 0 ? near : (int)cnt > kmax);
         if (!__any_sync(kFullMask, mine)) continue;
         uint32_t seen = 0;
         for (int row = 0; row < 9 && mine; ++row) {
