@@ -834,7 +834,7 @@ gsph_status gsph_set_dt(gsph_ctx *c, double dt, void *stream) {
     GSPH_CK(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
     GSPH_CK(cudaMemcpyAsync(c->dt, &dt, sizeof(double), cudaMemcpyHostToDevice, s));
-    GSPH_CK(cudaMemsetAsync(c->dtw, 0, offsetof(DtWords, last_ccount), s));
+    GSPH_CK(cudaMemsetAsync(c->dtw, 0, offsetof(DtWords, hint), s));   // the state (and its hint) stays
     GSPH_CK(cudaStreamSynchronize(s));
     c->dt_dirty = false;
     return GSPH_OK;

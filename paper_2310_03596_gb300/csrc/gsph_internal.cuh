@@ -368,7 +368,12 @@ __device__ __forceinline__ void signal_bounds32(const DevParams &P, int mat, dou
 struct DtWords {
     unsigned long long sigd;
     unsigned int sig, ccount, done, eval;
+    // bits of a listing threshold from the previous step: 2^-10 below its largest lower end (0: none).
+    // Lanes below it are not listed; if this step's largest lower end falls below it, a dropped lane
+    // might have mattered, and the final kernel evaluates every particle instead
+    unsigned int hint;
     unsigned int last_ccount, last_eval;   // the last completed reduction's counts (statistics)
+    unsigned int pad;
 };
 // A listed candidate: its FP64 inputs, material and the upper end of its interval.
 struct __align__(16) DtCand {
@@ -402,7 +407,8 @@ __device__ __forceinline__ void dt_candidate(const DevParams &P, const DtArgs &d
     if (lead == 0u) return;   // no particle in this warp
     const int lane = threadIdx.x & 31, ld = __ffs(lead) - 1;
     if (lane == ld) atomicMax(&d.w->sig, wmax);
-    bool cand = ok && __float_as_uint(hi) >= wmax;
+    const unsigned hint = *(volatile unsigned *)&d.w->hint;
+    bool cand = ok && __float_as_uint(hi) >= (wmax > hint ? wmax : hint);
     if (__ballot_sync(full, cand) != (1u << ld)) {
     // the leader's FP64 inputs: identical inputs give the identical FP64 value
     const long long lm = __shfl_sync(full, __double_as_longlong(m), ld);

@@ -378,8 +378,9 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt_exact(DevParams P, DtArgs d, 
     __shared__ DtCand prev_sh;
     const unsigned T = *(volatile unsigned *)&d.w->sig;
     const unsigned ncount = *(volatile unsigned *)&d.w->ccount;
+    const unsigned hint = *(volatile unsigned *)&d.w->hint;
     if (threadIdx.x == 0) nev = 0u;
-    if (ncount <= d.cap) {
+    if (ncount <= d.cap && T >= hint) {
         for (unsigned base = blockIdx.x * DT_THREADS; base < ncount; base += gridDim.x * DT_THREADS) {
             const unsigned k = base + threadIdx.x;
             if (threadIdx.x == 0) {
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt_exact(DevParams P, DtArgs d, 
             if (threadIdx.x == 0) nev += m;
             __syncthreads();
         }
-    } else {   // overflow: every particle of the state
+    } else {   // overflow, or a listing threshold above this step's lower bound: every particle
         for (int64_t i = (int64_t)blockIdx.x * DT_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * DT_THREADS) {
             const int m = S.mat[i] < P.nmat ? S.mat[i] : 0;
             const double v = dt_value(P, m, S.f[FM][i], S.f[FW][i], S.f[FVX][i], S.f[FVY][i], S.f[FVZ][i],
@@ -430,6 +431,7 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt_exact(DevParams P, DtArgs d, 
         *dt = P.variable_h ? __ddiv_rn(P.cfl, mx) : __ddiv_rn(__dmul_rn(P.cfl, P.h), mx);
         d.w->last_ccount = d.w->ccount;
         d.w->last_eval = atomicAdd(&d.w->eval, 0u);
+        d.w->hint = __float_as_uint(__fmul_rn(__uint_as_float(T), 1.0f - 0x1p-10f));
         d.w->sigd = 0ull;
         d.w->sig = 0u;
         d.w->ccount = 0u;
