@@ -27,8 +27,9 @@ cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint
                            cudaStream_t s);
 cudaError_t launch_comm(const DevParams &P, int64_t n, const uint32_t *skey, const uint8_t *lab_s, uint32_t *mask,
                         uint8_t *flag, uint32_t *comm, uint32_t *block_counts, unsigned long long *label_total,
-                        uint32_t *blist, uint32_t *hidx, cudaStream_t s);
+                        uint32_t *blist, uint32_t *hidx, uint32_t *scan_part, int *launches, cudaStream_t s);
 int comm_blocks(int64_t n);
+int comm_scan_chunks(int64_t n);
 cudaError_t launch_init(const DevParams &P, int64_t n, const double *pos, const double *vel, const double *vol,
                         const uint8_t *mat, const uint8_t *lab, const State &A, int *err, cudaStream_t s);
 cudaError_t launch_dt_from_state(const DevParams &P, int64_t n, const State &A, const DtArgs &d, double *dt,
@@ -103,6 +104,7 @@ struct gsph_ctx {
     void *pos = nullptr, *rec = nullptr;
     uint8_t *flag = nullptr;
     uint32_t *comm = nullptr, *blist = nullptr, *bcounts = nullptr;
+    uint32_t *scan_part = nullptr;               // chunk sums of the boundary-count scan
     // two-pass interaction order (cfg.overlap)
     uint32_t *hidx = nullptr;
     void *hpos = nullptr, *hrec = nullptr, *part = nullptr;
@@ -219,6 +221,7 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     A_(dalloc(c, &c->comm, N));
     A_(dalloc(c, &c->blist, N));
     A_(dalloc(c, &c->bcounts, (size_t)kMaxLabel * (size_t)comm_blocks(n)));
+    A_(dalloc(c, &c->scan_part, (size_t)comm_scan_chunks(n)));
     A_(dalloc(c, &c->label_off, (size_t)kMaxLabel + 1));
     A_(dalloc(c, &c->cost, (size_t)kMaxLabel));
     A_(dalloc(c, &c->garbage, 1));
@@ -450,9 +453,10 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     }
     rec_event(c, PH_SWAP, s);
     // b-d. communication hash, MGPU boundary flags and set
+    int nl = 0;
     GSPH_CK(launch_comm(P, n, c->skey, c->lab_s, c->mask, c->flag, c->comm, c->bcounts, c->label_off, c->blist,
-                        c->hidx, s));
-    c->launches += 4;
+                        c->hidx, c->scan_part, &nl, s));
+    c->launches += nl;
     rec_event(c, PH_COMM, s);
     // f-g. interaction loop fused with the integration; next dt
     GSPH_CK(cudaMemsetAsync(c->cost, 0, (size_t)kMaxLabel * sizeof(unsigned long long), s));

@@ -289,21 +289,108 @@ __global__ void __launch_bounds__(CM_THREADS) k_boundary_scatter(int64_t n, cons
     }
 }
 
+// Large count arrays (many blocks, many labels): a two-level scan. Chunks of SC_CHUNK entries: the
+// chunk sums (one block each), their exclusive scan (one block), then every chunk's prefixes offset by
+// its chunk's prefix (one block each), all loads and stores coalesced.
+constexpr int SC_THREADS = 1024, SC_PER = 4, SC_CHUNK = SC_THREADS * SC_PER;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t &total) {
+    __shared__ uint32_t wsum[SC_THREADS / 32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFullMask, x, o);
+        if (l >= o) x += y;
+    }
+    if (l == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = wsum[l];
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFullMask, t, o);
+            if (l >= o) t += y;
+        }
+        wsum[l] = t;
+    }
+    __syncthreads();
+    total = wsum[31];
+    const uint32_t r = (w > 0 ? wsum[w - 1] : 0u) + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_partial(const uint32_t *__restrict__ a, int64_t entries,
+                                                             uint32_t *__restrict__ part) {
+    const int64_t base = (int64_t)blockIdx.x * SC_CHUNK;
+    uint32_t v = 0;
+    for (int k = 0; k < SC_PER; ++k) {
+        const int64_t i = base + (int64_t)k * SC_THREADS + threadIdx.x;
+        if (i < entries) v += a[i];
+    }
+    uint32_t tot;
+    block_exclusive_scan(v, tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_chunks(uint32_t *__restrict__ part, int nchunk, int K,
+                                                            unsigned long long *__restrict__ label_total) {
+    const uint32_t v = threadIdx.x < nchunk ? part[threadIdx.x] : 0u;
+    uint32_t tot;
+    const uint32_t e = block_exclusive_scan(v, tot);
+    if (threadIdx.x < nchunk) part[threadIdx.x] = e;
+    if (threadIdx.x == 0) label_total[K] = tot;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_apply(uint32_t *__restrict__ a, int64_t entries,
+                                                           const uint32_t *__restrict__ part, int nblk,
+                                                           unsigned long long *__restrict__ label_total) {
+    const int64_t i0 = (int64_t)blockIdx.x * SC_CHUNK + (int64_t)threadIdx.x * SC_PER;
+    uint32_t c[SC_PER], v = 0;
+    for (int k = 0; k < SC_PER; ++k) {
+        c[k] = i0 + k < entries ? a[i0 + k] : 0u;
+        v += c[k];
+    }
+    uint32_t tot;
+    uint32_t e = block_exclusive_scan(v, tot) + part[blockIdx.x];
+    for (int k = 0; k < SC_PER; ++k) {
+        const int64_t i = i0 + k;
+        if (i < entries) {
+            a[i] = e;
+            if (i % nblk == 0) label_total[i / nblk] = e;   // the first entry of each label row
+        }
+        e += c[k];
+    }
+}
+
 cudaError_t launch_comm(const DevParams &P, int64_t n, const uint32_t *skey, const uint8_t *lab_s, uint32_t *mask,
                         uint8_t *flag, uint32_t *comm, uint32_t *block_counts, unsigned long long *label_total,
-                        uint32_t *blist, uint32_t *hidx, cudaStream_t s) {
+                        uint32_t *blist, uint32_t *hidx, uint32_t *scan_part, int *launches, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(mask, 0, (size_t)P.ncell * 4, s);
     if (e != cudaSuccess) return e;
     unsigned g = (unsigned)((n + CM_THREADS - 1) / CM_THREADS);
     k_label_mask<<<g, CM_THREADS, 0, s>>>(P, n, skey, lab_s, mask);
     k_comm<<<g, CM_THREADS, 0, s>>>(P, n, skey, lab_s, mask, flag, comm, block_counts, (int)g);
-    k_comm_scan<<<1, 1024, 0, s>>>(block_counts, (int64_t)P.K_labels * g, (int)g, P.K_labels, label_total);
+    const int64_t entries = (int64_t)P.K_labels * g;
+    if (entries <= 8 * SC_CHUNK) {   // a few chunks: the one-block scan
+        k_comm_scan<<<1, 1024, 0, s>>>(block_counts, entries, (int)g, P.K_labels, label_total);
+        *launches = 4;
+    } else {
+        const int nchunk = (int)((entries + SC_CHUNK - 1) / SC_CHUNK);
+        k_scan_partial<<<nchunk, SC_THREADS, 0, s>>>(block_counts, entries, scan_part);
+        k_scan_chunks<<<1, SC_THREADS, 0, s>>>(scan_part, nchunk, P.K_labels, label_total);
+        k_scan_apply<<<nchunk, SC_THREADS, 0, s>>>(block_counts, entries, scan_part, (int)g, label_total);
+        *launches = 6;
+    }
     k_boundary_scatter<<<g, CM_THREADS, 0, s>>>(n, lab_s, flag, block_counts, (int)g, blist, hidx);
     return cudaGetLastError();
 }
 
 int comm_blocks(int64_t n) { return (int)((n + CM_THREADS - 1) / CM_THREADS); }
+// chunk sums of the two-level scan (K = 16 labels and 2^26 particles: 512 chunks)
+int comm_scan_chunks(int64_t n) {
+    return (int)(((int64_t)kMaxLabel * comm_blocks(n) + SC_CHUNK - 1) / SC_CHUNK) + 1;
+}
 
 // ---------------------------------------------------------------------------------------------
 // Initialisation from user arrays (pos/vel n x 3 row-major).
