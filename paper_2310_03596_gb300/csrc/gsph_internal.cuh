@@ -373,7 +373,9 @@ struct DtWords {
     // might have mattered, and the final kernel evaluates every particle instead
     unsigned int hint;
     unsigned int last_ccount, last_eval;   // the last completed reduction's counts (statistics)
-    unsigned int pad;
+    // relative width of the threshold (0: 2^-10); doubled after a step whose lower bound fell below
+    // the threshold, halved after a step that listed more candidates than half the capacity
+    float delta;
 };
 // A listed candidate: its FP64 inputs, material and the upper end of its interval.
 struct __align__(16) DtCand {

@@ -518,7 +518,11 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt_exact(DevParams P, DtArgs d, 
         *dt = P.variable_h ? __ddiv_rn(P.cfl, mx) : __ddiv_rn(__dmul_rn(P.cfl, P.h), mx);
         d.w->last_ccount = d.w->ccount;
         d.w->last_eval = atomicAdd(&d.w->eval, 0u);
-        d.w->hint = __float_as_uint(__fmul_rn(__uint_as_float(T), 1.0f - 0x1p-10f));
+        float delta = d.w->delta > 0.0f ? d.w->delta : 0x1p-10f;
+        if (T < hint) delta = fminf(2.0f * delta, 0.5f);                   // the threshold was too tight
+        else if (d.w->ccount > d.cap / 2) delta = fmaxf(0.5f * delta, 0x1p-16f);   // too wide
+        d.w->delta = delta;
+        d.w->hint = __float_as_uint(__fmul_rn(__uint_as_float(T), 1.0f - delta));
         d.w->sigd = 0ull;
         d.w->sig = 0u;
         d.w->ccount = 0u;
