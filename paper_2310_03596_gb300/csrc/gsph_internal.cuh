@@ -106,36 +106,6 @@ __host__ __device__ __forceinline__ D4 make_d4(double x, double y, double z, dou
 struct RecD { D4 a, b, c, d; };
 
 // ---------------------------------------------------------------------------------------------
-// Conversions between FP64 and FP32 by integer operations: GB300 runs the conversion instructions on
-// its scarce FP64 pipe, the integer pipe has many times its throughput. Same results as the conversion
-// instructions: f32_rn rounds to nearest even (results in the normal FP32 range and zeros here, the
-// rest by the instruction); f64_of widens exactly (normal numbers and zeros here).
-// ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ float f32_rn(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned long long a = b & 0x7fffffffffffffffull;
-    const unsigned int sgn = (unsigned int)(b >> 32) & 0x80000000u;
-    // 2^-126 <= |x| < 2^128: rebias the exponent (1023 - 127 = 896), round the 29 dropped mantissa bits
-    // to nearest even (a carry may reach the exponent, up to infinity), shift
-    if (a - 0x3810000000000000ull < 0x47f0000000000000ull - 0x3810000000000000ull) {
-        unsigned long long m = a - 0x3800000000000000ull;
-        m += 0x0fffffffull + ((m >> 29) & 1ull);
-        return __uint_as_float((unsigned int)(m >> 29) | sgn);
-    }
-    if (a == 0ull) return __uint_as_float(sgn);
-    return __double2float_rn(x);
-}
-__device__ __forceinline__ double f64_of(float f) {
-    const unsigned int u = __float_as_uint(f);
-    const unsigned int a = u & 0x7fffffffu;
-    const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
-    if (a - 0x00800000u < 0x7f800000u - 0x00800000u)   // normal: rebias 127 -> 1023, widen the mantissa
-        return __longlong_as_double((long long)((((unsigned long long)a << 29) + 0x3800000000000000ull) | sgn));
-    if (a == 0u) return __longlong_as_double((long long)sgn);
-    return (double)f;
-}
-
-// ---------------------------------------------------------------------------------------------
 // Exactly rounded FP64 helpers: every product and sum rounded separately (no contraction), so that
 // the integer decisions made from them (hash, support predicate, balancing hash) are the same on
 // any IEEE machine that evaluates the same operation sequence.
@@ -316,14 +286,14 @@ __device__ __forceinline__ void signal_bounds32(const DevParams &P, int mat, dou
         // within 4.5u (u = 2^-24, first order); the quotient by h adds 2u. 2^-20 = 16u covers these, the
         // second-order terms and the FP64 sequence's own roundings, when m, w (and h) are normal positive
         // FP32 numbers; otherwise the interval is unbounded.
-        const float mf = f32_rn(m), wf = f32_rn(w);
-        const float fx = f32_rn(vx), fy = f32_rn(vy), fz = f32_rn(vz);
+        const float mf = __double2float_rn(m), wf = __double2float_rn(w);
+        const float fx = __double2float_rn(vx), fy = __double2float_rn(vy), fz = __double2float_rn(vz);
         const float rho = __fdiv_rn(mf, wf);
         const float v2 = __fadd_rn(__fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy)), __fmul_rn(fz, fz));
         float sv = __fadd_rn(__fsqrt_rn(__fdiv_rn(P.f_Mmod[mat], rho)), __fsqrt_rn(v2));
         bool good = mf >= 0x1p-126f && wf >= 0x1p-126f && mf < 0x1p127f && wf < 0x1p127f;
         if (P.variable_h) {
-            const float hf = f32_rn(h);
+            const float hf = __double2float_rn(h);
             good = good && hf >= 0x1p-126f;
             sv = __fdiv_rn(sv, hf);
         }

@@ -273,7 +273,7 @@ template <> struct Acc<float> {
     }
     // the compensated sum s - c rounded once to FP32 keeps the compensation's benefit (one rounding
     // of the final value instead of one per term) and widens with a single conversion
-    __device__ __forceinline__ double get(int k) const { return f64_of(k < 6 ? s[k] - c[k] : s[k]); }
+    __device__ __forceinline__ double get(int k) const { return (double)(k < 6 ? s[k] - c[k] : s[k]); }
     __device__ __forceinline__ float getr(int k) const { return k < 6 ? s[k] - c[k] : s[k]; }
 };
 template <> struct Acc<double> {
@@ -1092,17 +1092,17 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         }
         const R Yr = SPLIT ? (R)(float)P.Y[mt] : (R)P.Y[mt];
         if (FAST) {
-            const float dtf = f32_rn(dt), imf = 1.0f / f32_rn(mn), mf = me.rho * me.w, dm = acc.getr(1);
+            const float dtf = (float)dt, imf = 1.0f / (float)mn, mf = (float)(me.rho * me.w), dm = (float)acc.getr(1);
             float F[3] = {(float)acc.getr(2), (float)acc.getr(3), (float)acc.getr(4)}, dE = (float)acc.getr(5);
             if (P.has_gravity) {
                 const float g0 = (float)P.g[0], g1 = (float)P.g[1], g2 = (float)P.g[2];
                 F[0] += mf * g0; F[1] += mf * g1; F[2] += mf * g2;
                 dE += mf * (g0 * me.vx + g1 * me.vy + g2 * me.vz);
             }
-            nvx = vx + f64_of(dtf * (F[0] - me.vx * dm) * imf);
-            nvy = vy + f64_of(dtf * (F[1] - me.vy * dm) * imf);
-            nvz = vz + f64_of(dtf * (F[2] - me.vz * dm) * imf);
-            En = E + f64_of(dtf * (dE - me.E * dm) * imf);
+            nvx = vx + (double)(dtf * (F[0] - me.vx * dm) * imf);
+            nvy = vy + (double)(dtf * (F[1] - me.vy * dm) * imf);
+            nvz = vz + (double)(dtf * (F[2] - me.vz * dm) * imf);
+            En = E + (double)(dtf * (dE - me.E * dm) * imf);
             // stress increment; its trace removed in FP32 (the state's own trace is zero to rounding)
             float dS[6];
 #pragma unroll
@@ -1112,7 +1112,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
             const float a0 = (float)Sr[0][0] + dS[0], a1 = (float)Sr[1][1] + dS[1], a2 = (float)Sr[2][2] + dS[2];
             const float a3 = (float)Sr[0][1] + dS[3], a4 = (float)Sr[0][2] + dS[4], a5 = (float)Sr[1][2] + dS[5];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) Sn[q] = S[q] + f64_of(dS[q]);
+            for (int q = 0; q < 6; ++q) Sn[q] = S[q] + (double)dS[q];
             const float ss = a0 * a0 + a1 * a1 + a2 * a2 + 2.0f * (a3 * a3 + a4 * a4 + a5 * a5);
             const float seq = sqrtf(1.5f * ss);
             if (seq > (float)Yr) {

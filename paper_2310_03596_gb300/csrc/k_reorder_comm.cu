@@ -22,37 +22,36 @@ __device__ __forceinline__ void write_record(const DevParams &P, int64_t s, uint
                                              void *__restrict__ rec_out) {
     if (SPLIT) {
         RecF r;
-        // (FP32 roundings by integer operations, f32_rn: the same values as the conversion instruction)
-        float4 p4 = make_float4(0.f, 0.f, 0.f, f32_rn(w));
+        float4 p4 = make_float4(0.f, 0.f, 0.f, (float)w);
         if (k < P.ncell) {
             int cx, cy, cz;
             decode_cell(P, k, cx, cy, cz);
             // position relative to the particle's own bucket corner: |.| < 2h, so FP32 keeps it to
             // about 2^-24 * 2h
-            p4.x = f32_rn(x - (P.lo[0] + (double)cx * P.cell));
-            p4.y = f32_rn(y - (P.lo[1] + (double)cy * P.cell));
-            p4.z = f32_rn(z - (P.lo[2] + (double)cz * P.cell));
+            p4.x = (float)(x - (P.lo[0] + (double)cx * P.cell));
+            p4.y = (float)(y - (P.lo[1] + (double)cy * P.cell));
+            p4.z = (float)(z - (P.lo[2] + (double)cz * P.cell));
         }
-        float rho = f32_rn(m) / p4.w;
+        float rho = (float)m / (float)w;
         float pf, Zf;
         if (P.eos[mat] == 0) {
             // p = K (rho/rho0 - 1) = K (m - rho0 w) / (rho0 w): the cancelling difference in FP64
             double rw = P.rho0[mat] * w;
-            pf = P.f_K[mat] * f32_rn(m - rw) / f32_rn(rw);
+            pf = P.f_K[mat] * (float)(m - rw) / (float)rw;
             if (pf < (float)P.p_min[mat]) pf = (float)P.p_min[mat];
             Zf = rho * sqrtf(P.f_Mmod[mat] / rho);
         } else {   // Mie-Gruneisen in FP64 (its Hugoniot terms cancel as well), rounded once
             double pd, cd;
             const double rd = m / w;
             eos_pc(P, mat, rd, E - 0.5 * (vx * vx + vy * vy + vz * vz), pd, cd);
-            pf = f32_rn(pd);
-            Zf = f32_rn(rd * cd);
+            pf = (float)pd;
+            Zf = (float)(rd * cd);
         }
         // the diagonal of the full stress sigma = -p I + S (S traceless in FP32: S_zz = -(S_xx + S_yy))
-        const float fxx = f32_rn(sxx), fyy = f32_rn(syy), fzz = -(fxx + fyy);
-        r.a = make_float4(f32_rn(vx), f32_rn(vy), f32_rn(vz), rho);
-        r.b = make_float4(fzz - pf, Zf, f32_rn(E), fxx - pf);
-        r.c = make_float4(fyy - pf, f32_rn(sxy), f32_rn(sxz), f32_rn(syz));
+        const float fxx = (float)sxx, fyy = (float)syy, fzz = -(fxx + fyy);
+        r.a = make_float4((float)vx, (float)vy, (float)vz, rho);
+        r.b = make_float4(fzz - pf, Zf, (float)E, fxx - pf);
+        r.c = make_float4(fyy - pf, (float)sxy, (float)sxz, (float)syz);
         ((float4 *)pos_out)[s] = p4;
         ((RecF *)rec_out)[s] = r;
         (void)szz;
@@ -90,14 +89,14 @@ __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const u
     if (hs) {   // variable h: the sorted smoothing lengths, FP64 and their FP32 roundings
         const double hh = A.h[o];
         hs[s] = hh;
-        hsf[s] = f32_rn(hh);
+        hsf[s] = __double2float_rn(hh);
     }
     double x = A.f[FX][o], y = A.f[FY][o], z = A.f[FZ][o];
     xs[s] = x; ys[s] = y; zs[s] = z;
     if (xf) {   // the swap pass's inputs: FP32 roundings and fixed-point coordinates
-        xf[s] = f32_rn(x);
-        yf[s] = f32_rn(y);
-        zf[s] = f32_rn(z);
+        xf[s] = __double2float_rn(x);
+        yf[s] = __double2float_rn(y);
+        zf[s] = __double2float_rn(z);
         qx[s] = quantise64(x, P.lo[0], P.q_s[0]);
         qy[s] = quantise64(y, P.lo[1], P.q_s[1]);
         qz[s] = quantise64(z, P.lo[2], P.q_s[2]);
