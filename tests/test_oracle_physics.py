@@ -312,3 +312,19 @@ def test_uniaxial_strain_wave_speed():
     tc = {p: acc[p][0] / acc[p][1] for p in probes}
     c = (probes[1] - probes[0]) * dx / (tc[probes[1]] - tc[probes[0]])
     assert c == pytest.approx(c_th, rel=0.03)
+
+
+def test_rates_are_the_same_on_any_number_of_host_threads():
+    # the per-particle loops may run on several host threads (the CPU baseline on all cores): each
+    # particle's sums are its own, so the rates are bit for bit those of one thread
+    s, P, st = _lattice_state(n_side=9, jitter=0.01, walls=((2, 0.0),))
+    _randomise(st, np.random.default_rng(12))
+    orc.set_threads(1)
+    r1, n1, i1 = orc.rates(P, st)
+    used = orc.set_threads(4)
+    try:
+        r4, n4, i4 = orc.rates(P, st)
+    finally:
+        orc.set_threads(1)
+    assert used >= 1
+    assert np.array_equal(r1, r4) and np.array_equal(n1, n4) and np.array_equal(i1, i4)
