@@ -142,3 +142,51 @@ def test_sharded_run_matches_single_device(world, kind):
     halos = [p["halo"] for parts in per_step for p in parts]
     assert min(halos) > 0          # every rank received boundary records at every step
     print(kind, world, "halo sizes", halos, "moved", swaps)
+
+
+def _rank_leaves(rank, world, port, q):
+    import datetime
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    from paper_2310_03596_gb300 import scenes, sharded
+    from oracle import orc
+    s = _scene("cube", world)
+    sol = sharded.ShardedSolver(s, OracleEngine(orc.params_of(s)))
+    sol.step()
+    if rank == world - 1:
+        q.put((rank, "left"))       # this rank leaves between steps, with no collective in flight
+        q.close()
+        q.join_thread()
+        os._exit(0)
+    try:
+        sol.step()                  # the next step's collectives cannot complete
+        q.put((rank, "no error"))
+    except Exception as e:          # noqa: BLE001
+        q.put((rank, type(e).__name__))
+    q.close()
+    q.join_thread()
+    os._exit(0)
+
+
+def test_a_rank_that_leaves_ends_the_others_next_step_with_an_error():
+    # failure detection on the host: the remaining ranks' next collective ends with an error within
+    # the process group's timeout instead of waiting forever
+    import time
+    from oracle import orc
+    orc.build()
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    t0 = time.time()
+    procs = [ctx.Process(target=_rank_leaves, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+    assert got[world - 1] == "left"
+    assert got[0] != "no error", got
+    assert time.time() - t0 < 110
