@@ -304,18 +304,26 @@ def cpu_baseline(device: int = 0):
              "per_field": err})
 
 
+def _at_least_one(v):
+    k = int(v)
+    if k < 1:
+        raise argparse.ArgumentTypeError("must be at least 1")
+    return k
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=5)
-    ap.add_argument("--overlap-steps", type=int, default=20)
-    ap.add_argument("--hvi-steps", type=int, default=50)
-    ap.add_argument("--heun-steps", type=int, default=20)
-    ap.add_argument("--muscl-steps", type=int, default=20)
-    ap.add_argument("--varh-steps", type=int, default=20)
+    # the lines without a switch-off (0 skips the collapse block, the plate and the adjoint)
+    ap.add_argument("--fp64-steps", type=_at_least_one, default=5)
+    ap.add_argument("--overlap-steps", type=_at_least_one, default=20)
+    ap.add_argument("--hvi-steps", type=_at_least_one, default=50)
+    ap.add_argument("--heun-steps", type=_at_least_one, default=20)
+    ap.add_argument("--muscl-steps", type=_at_least_one, default=20)
+    ap.add_argument("--varh-steps", type=_at_least_one, default=20)
     ap.add_argument("--collapse-steps", type=int, default=10)
     ap.add_argument("--plate-steps", type=int, default=50)
     ap.add_argument("--adjoint-steps", type=int, default=200)

@@ -396,7 +396,7 @@ static void fill_params(const gsph_config &c, DevParams &P) {
 
 static int64_t swap_pass_launches(const DevParams &P) {
     (void)P;
-    return 1;   // one cooperative kernel per pass
+    return 4;   // sums, pair geometry, speculative counts, the cooperative pair loop
 }
 
 static int key_bits(uint32_t ncell) {

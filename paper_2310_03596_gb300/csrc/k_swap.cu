@@ -1,8 +1,9 @@
 // k_swap.cu - the communication-load-balancing heuristic (Sec. III.A, III.B) on K virtual labels.
 //
-// One swap pass is a single cooperative kernel (all blocks resident) whose phases are separated by a
-// bounded grid barrier; a barrier that does not complete within about a second records a timeout in the
-// error word and the pass returns. For each particle type (one pass over all particles when the scene
+// One swap pass is three streaming kernels (the fixed-point sums, the pair geometries, the speculative
+// counts) and one cooperative kernel (all blocks resident) for the sequential pair loop, whose phases are
+// separated by a bounded grid barrier; a barrier that does not complete within about a second records a
+// timeout in the error word and the pass returns. For each particle type (one pass over all particles when the scene
 // has one material) and each label pair (a, b) in lexicographic order:
 //   Cg of a and b from exact fixed-point sums (per axis the nearest integer to (x - lo) 2^32 / L of the
 //   FP64 position, L the grid extent, clamped to [0, 2^32 - 1] and summed in int64; Cg = lo + mean L 2^-32),
@@ -41,9 +42,7 @@ constexpr int SW_THREADS = 512;
 constexpr int SW_NT = kMaxMat + 1;   // per-type slots + the all-types slot
 constexpr int SW_TCAP = 2048;        // threshold-bin list capacity per side
 constexpr int SW_MAXCOMBO = kMaxMat * (kMaxLabel * (kMaxLabel - 1) / 2);   // (type, label pair) combinations
-constexpr int SW_SBUF = SW_MAXCOMBO * (int)(7 * sizeof(float)) + SW_MAXCOMBO * 2 * 4 > 2 * SW_TCAP * 4
-                            ? SW_MAXCOMBO * (int)(7 * sizeof(float)) + SW_MAXCOMBO * 2 * 4
-                            : 2 * SW_TCAP * 4;
+constexpr int SW_SBUF = 2 * SW_TCAP * 4;
 
 struct SwapPair {
     uint32_t hist[2][SW_BINS];
@@ -63,6 +62,7 @@ struct SwapScratch {
     unsigned long long fp64;              // balancing hashes the FP32 bound left to the FP64 sequence
     unsigned int bar_count;
     unsigned int bar_gen;
+    float spec[SW_MAXCOMBO][7];            // pass-start geometry of every (type, label pair): SideF
 };
 
 // Fixed-point Cg per axis: q = nearest integer (ties to even) to (x - lo) s, s = 2^32 / L, clamped to
@@ -282,37 +282,17 @@ __device__ bool grid_barrier(SwapScratch *S, unsigned nblocks, int *err, const W
     return ok_sh != 0;
 }
 
-__global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantParams Q, double alpha, int K, int nmat,
-                                                          const SwapPos pos, uint8_t *__restrict__ lab,
-                                                          const uint8_t *__restrict__ mat,
-                                                          const uint32_t *__restrict__ id, uint16_t *__restrict__ bh,
-                                                          SwapScratch *__restrict__ S, SwapPair *__restrict__ pairs,
-                                                          uint2 *__restrict__ tl, uint32_t *__restrict__ sidx,
-                                                          int *__restrict__ err, const WaitCfg wc) {
+// The pass's two streaming phases run as separate kernels at full occupancy; the cooperative kernel
+// starts from their results and returns at once when no label pair can swap (the usual case once the
+// labels have settled).
+// Phase 1: exact fixed-point sums per (label, type) and per label (warp-aggregated shared atomics, one
+// global atomic per non-zero entry and block).
+__global__ void __launch_bounds__(SW_THREADS) k_swap_sums(int64_t n, int nmat, const SwapPos pos,
+                                                          const uint8_t *__restrict__ lab,
+                                                          const uint8_t *__restrict__ mat, SwapScratch *__restrict__ S) {
     __shared__ long long shs[kMaxLabel][SW_NT][4];
-    __shared__ uint32_t hs[2][SW_BINS];
-    __shared__ uint32_t ids[2][SW_ID_BINS];
-    __shared__ Side side_sh[2];
-    __shared__ int act_sh;
-    __shared__ long long gn_sh[4];       // counts of a, b (this type) and of a, b (all types)
-    __shared__ uint32_t npos_sh[2];      // this block's positive hashes per side
-    __shared__ double gcg_sh[4][3];      // their Cgs
-    __shared__ double gd_sh[3], gdn_sh;  // Cg_b - Cg_a, its length
-    __shared__ int T_sh[2], idsel_sh[2];
-    __shared__ uint32_t need_sh[2], idpre_sh[2];
-    __shared__ long long dsum[2][4];   // per side: moved q0 q1 q2, count
-    __shared__ uint32_t cntT_sh[2];    // particles in the threshold bin
-    __shared__ int list_sh;            // threshold bins split through the list (else the grid select)
-    // tkey (tie-break select) and the speculative pass's geometry and counters share one buffer
-    __shared__ __align__(16) unsigned char sbuf[SW_SBUF];
-    uint32_t(*tkey)[SW_TCAP] = (uint32_t(*)[SW_TCAP])sbuf;
-    const unsigned nb = gridDim.x;
-    const int64_t gstride = (int64_t)gridDim.x * SW_THREADS;
-    const int64_t g0 = (int64_t)blockIdx.x * SW_THREADS + threadIdx.x;
     const bool multi = nmat > 1;
-    const int ntype = multi ? nmat : 1;
-
-    // ---- exact fixed-point sums per (label, type) and per label (warp-aggregated shared atomics)
+    const int64_t gstride = (int64_t)gridDim.x * SW_THREADS;
     for (int i = threadIdx.x; i < kMaxLabel * SW_NT * 4; i += SW_THREADS) (&shs[0][0][0])[i] = 0;
     __syncthreads();
     for (int64_t base = (int64_t)blockIdx.x * SW_THREADS; base < n; base += gstride) {
@@ -337,22 +317,152 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
         for (int a = 0; a < 3; ++a) atomicAdd((unsigned long long *)&S->sums[l][t][a], (unsigned long long)shs[l][t][a]);
         atomicAdd((unsigned long long *)&S->cnt[l][t], (unsigned long long)shs[l][t][3]);
     }
-    if (!grid_barrier(S, nb, err, wc)) return;
+}
 
-    // ---- speculative pass (exact): positive-hash counts of every (type, label pair) at the pass-start
-    // labels and sums. A pair with no positive hash on one side swaps nothing and changes nothing, so
-    // the sequential loop starts at the first pair with positive hashes on both sides: until then the
-    // labels and sums each pair sees are the pass-start ones, the state this pass evaluates.
+// Pass-start geometry of every (type, label pair) from the sums (one block).
+__global__ void __launch_bounds__(SW_THREADS) k_swap_geom(QuantParams Q, double alpha, int K, int nmat,
+                                                          SwapScratch *__restrict__ S) {
+    const bool multi = nmat > 1;
+    const int npairs = K * (K - 1) / 2, ncombo = (multi ? nmat : 1) * npairs;
+    for (int q = threadIdx.x; q < ncombo; q += SW_THREADS) {
+        const int T = q / npairs;
+        int a = 0, rem = q % npairs;
+        while (rem >= K - 1 - a) { rem -= K - 1 - a; ++a; }
+        Side g;
+        SideF f;
+        if (combo_geometry(S, Q, alpha, multi, multi ? T : kMaxMat, a, a + 1 + rem, g)) f = g.f;
+        else f.scale = -1.0f;
+        float *o = S->spec[q];
+        o[0] = f.M[0]; o[1] = f.M[1]; o[2] = f.M[2]; o[3] = f.u[0]; o[4] = f.u[1]; o[5] = f.u[2]; o[6] = f.scale;
+    }
+}
+
+// The balancing hash of one particle by the FP64 sequence: the pair's FP64 geometry from the sums, the
+// direction flipped for a particle of label b.
+__device__ __forceinline__ int spec_hash64(const SwapScratch *S, const QuantParams &Q, double alpha, bool multi, int T,
+                                        int a, int b, bool flip, double X, double Y, double Z) {
+    Side G;
+    combo_geometry(S, Q, alpha, multi, T, a, b, G);
+    if (flip) { G.d[0] = -G.d[0]; G.d[1] = -G.d[1]; G.d[2] = -G.d[2]; }
+    atomicAdd((unsigned long long *)&S->fp64, 1ull);
+    return balancing_hash64(G.M, G.d, G.dn, G.ell, X, Y, Z);
+}
+
+// Phase 2 (exact speculative pass): positive-hash counts of every (type, label pair) at the pass-start
+// labels and sums. A pair with no positive hash on one side swaps nothing and changes nothing, so the
+// sequential loop starts at the first pair with positive hashes on both sides: until then the labels and
+// sums each pair sees are the pass-start ones, the state this pass evaluates. With 8 or more labels the
+// same sweep groups the slots by label (the label segments of the pair loop).
+__global__ void __launch_bounds__(SW_THREADS) k_swap_spec(int64_t n, QuantParams Q, double alpha, int K, int nmat,
+                                                          const SwapPos pos, const uint8_t *__restrict__ lab,
+                                                          const uint8_t *__restrict__ mat, SwapScratch *__restrict__ S,
+                                                          SwapPair *__restrict__ pairs, uint32_t *__restrict__ sidx) {
+    __shared__ SideF spec[SW_MAXCOMBO];
+    __shared__ uint32_t scnt[2 * SW_MAXCOMBO];
+    __shared__ long long loff_sh[kMaxLabel + 1];
+    const bool multi = nmat > 1;
+    const int npairs = K * (K - 1) / 2, ncombo = (multi ? nmat : 1) * npairs;
+    const int64_t gstride = (int64_t)gridDim.x * SW_THREADS;
+    const bool seg = K >= 8;
+    for (int q = threadIdx.x; q < ncombo; q += SW_THREADS) {
+        const float *g = S->spec[q];
+        SideF f;
+        f.M[0] = g[0]; f.M[1] = g[1]; f.M[2] = g[2]; f.u[0] = g[3]; f.u[1] = g[4]; f.u[2] = g[5]; f.scale = g[6];
+        spec[q] = f;
+        scnt[2 * q] = 0u;
+        scnt[2 * q + 1] = 0u;
+    }
+    if (threadIdx.x == 0) {
+        long long o = 0;
+        for (int l = 0; l < kMaxLabel; ++l) {
+            loff_sh[l] = o;
+            if (l < K) o += S->cnt[l][kMaxMat];
+        }
+        loff_sh[kMaxLabel] = o;
+    }
+    __syncthreads();
+    uint32_t *const byl = sidx;
+    for (int64_t base = (int64_t)blockIdx.x * SW_THREADS; base < n; base += gstride) {
+        const int64_t i = base + threadIdx.x;
+        const bool v = i < n;
+        const int l = v ? (lab[i] & (kMaxLabel - 1)) : 0;
+        const int T = (v && multi) ? (mat[i] < nmat ? mat[i] : 0) : 0;
+        const float px = v ? pos.x[i] : 0.0f, py = v ? pos.y[i] : 0.0f, pz = v ? pos.z[i] : 0.0f;
+        if (seg) {   // the slot's place in its label's segment (one atomic per label and warp)
+            const unsigned peers = __match_any_sync(kFullMask, v ? l : -1);
+            unsigned long long at = 0;
+            if (v && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
+                at = atomicAdd(&S->lcur[l], (unsigned long long)__popc(peers));
+            at = __shfl_sync(kFullMask, at, __ffs(peers) - 1);
+            if (v) byl[loff_sh[l] + (long long)at + __popc(peers & lanemask_lt())] = (uint32_t)i;
+        }
+        for (int o = 0; o < K; ++o) {   // the K - 1 pairs of the particle's label (warp-uniform loop)
+            const int a = l < o ? l : o, b = l < o ? o : l;
+            const int q = T * npairs + a * (2 * K - a - 1) / 2 + (b - a - 1);
+            int key = -1;
+            if (v && o != l) {
+                SideF g = spec[q];
+                if (g.scale >= 0.0f) {
+                    if (l == b) { g.u[0] = -g.u[0]; g.u[1] = -g.u[1]; g.u[2] = -g.u[2]; }
+                    int hv = balancing_hash_fast(g, px, py, pz);
+                    if (hv < 0)   // rare: the FP64 sequence
+                        hv = spec_hash64(S, Q, alpha, multi, multi ? T : kMaxMat, a, b, l == b, pos.X[i], pos.Y[i],
+                                         pos.Z[i]);
+                    if (hv > 0) key = 2 * q + (l == a ? 0 : 1);
+                }
+            }
+            if (__any_sync(kFullMask, key >= 0)) {   // positives are rare once labels have settled
+                const unsigned peers = __match_any_sync(kFullMask, key);
+                if (key >= 0 && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
+                    atomicAdd(&scnt[key], (uint32_t)__popc(peers));
+            }
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * ncombo; q += SW_THREADS)
+        if (scnt[q]) atomicAdd(&pairs[q >> 1].spec[q & 1], scnt[q]);
+}
+
+__global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantParams Q, double alpha, int K, int nmat,
+                                                          const SwapPos pos, uint8_t *__restrict__ lab,
+                                                          const uint8_t *__restrict__ mat,
+                                                          const uint32_t *__restrict__ id, uint16_t *__restrict__ bh,
+                                                          SwapScratch *__restrict__ S, SwapPair *__restrict__ pairs,
+                                                          uint2 *__restrict__ tl, uint32_t *__restrict__ sidx,
+                                                          int *__restrict__ err, const WaitCfg wc) {
+    __shared__ uint32_t hs[2][SW_BINS];
+    __shared__ uint32_t ids[2][SW_ID_BINS];
+    __shared__ Side side_sh[2];
+    __shared__ int act_sh;
+    __shared__ long long gn_sh[4];       // counts of a, b (this type) and of a, b (all types)
+    __shared__ uint32_t npos_sh[2];      // this block's positive hashes per side
+    __shared__ double gcg_sh[4][3];      // their Cgs
+    __shared__ double gd_sh[3], gdn_sh;  // Cg_b - Cg_a, its length
+    __shared__ int T_sh[2], idsel_sh[2];
+    __shared__ uint32_t need_sh[2], idpre_sh[2];
+    __shared__ long long dsum[2][4];   // per side: moved q0 q1 q2, count
+    __shared__ uint32_t cntT_sh[2];    // particles in the threshold bin
+    __shared__ int list_sh;            // threshold bins split through the list (else the grid select)
+    // tkey (tie-break select)
+    __shared__ __align__(16) unsigned char sbuf[SW_SBUF];
+    uint32_t(*tkey)[SW_TCAP] = (uint32_t(*)[SW_TCAP])sbuf;
+    const unsigned nb = gridDim.x;
+    const int64_t gstride = (int64_t)gridDim.x * SW_THREADS;
+    const int64_t g0 = (int64_t)blockIdx.x * SW_THREADS + threadIdx.x;
+    const bool multi = nmat > 1;
+    const int ntype = multi ? nmat : 1;
+
+    // the fixed-point sums and the speculative counts come from k_swap_sums and k_swap_spec
     const int npairs = K * (K - 1) / 2;
     const int ncombo = ntype * npairs;
     __shared__ int first_sh;
     // label segments (K >= 8): sidx[0, n) holds the slots grouped by label (segment l at
-    // [loff[l], loff[l + 1])). A pair's swaps exchange equally many particles each way, so the segments
-    // keep their sizes; the moved particles exchange their segment positions after each pair (mv lists
-    // at sidx[n, 2n)), and a pair visits only its two labels' particles, 2n/K instead of n. Order within
-    // a segment is free: every use is a count, an exact sum or a select by persistent id. With fewer
-    // labels the segments cost more (their build, one more barrier per pair) than they save, and the
-    // pairs visit every slot.
+    // [loff[l], loff[l + 1]), built by k_swap_spec). A pair's swaps exchange equally many particles each
+    // way, so the segments keep their sizes; the moved particles exchange their segment positions after
+    // each pair (mv lists at sidx[n, 2n)), and a pair visits only its two labels' particles, 2n/K
+    // instead of n. Order within a segment is free: every use is a count, an exact sum or a select by
+    // persistent id. With fewer labels the segments cost more (their build, one more barrier per pair)
+    // than they save, and the pairs visit every slot.
     const bool seg = K >= 8;
     __shared__ long long loff_sh[kMaxLabel + 1];
     if (threadIdx.x == 0) {
@@ -362,88 +472,33 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
             if (l < K) o += ((volatile long long *)&S->cnt[l][kMaxMat])[0];
         }
         loff_sh[kMaxLabel] = o;
+        // the first pair with positive hashes on both sides at the pass-start state; the pairs before
+        // it swap nothing and change nothing
+        int f = ncombo;
+        for (int q = 0; q < ncombo && f == ncombo; ++q)
+            if (((volatile uint32_t *)&pairs[q].spec[0])[0] > 0u && ((volatile uint32_t *)&pairs[q].spec[1])[0] > 0u) f = q;
+        first_sh = f;
     }
     uint32_t *const byl = sidx;
     uint32_t *const mvl = sidx + n;                      // side 0 at [0, n/2), side 1 at [n/2, n)
     const int64_t mvh = (n + 1) / 2;
     __syncthreads();
-    {
-        SideF *spec = (SideF *)sbuf;
-        uint32_t *scnt = (uint32_t *)(sbuf + SW_MAXCOMBO * sizeof(SideF));
-        for (int q = threadIdx.x; q < ncombo; q += SW_THREADS) {
-            const int T = q / npairs;
-            int a = 0, rem = q % npairs;
-            while (rem >= K - 1 - a) { rem -= K - 1 - a; ++a; }
-            Side g;
-            if (combo_geometry(S, Q, alpha, multi, multi ? T : kMaxMat, a, a + 1 + rem, g)) spec[q] = g.f;
-            else spec[q].scale = -1.0f;
-            scnt[2 * q] = 0u;
-            scnt[2 * q + 1] = 0u;
-        }
-        __syncthreads();
-        for (int64_t base = (int64_t)blockIdx.x * SW_THREADS; base < n; base += gstride) {
-            const int64_t i = base + threadIdx.x;
-            const bool v = i < n;
-            const int l = v ? (lab[i] & (kMaxLabel - 1)) : 0;
-            const int T = (v && multi) ? (mat[i] < nmat ? mat[i] : 0) : 0;
-            const float px = v ? pos.x[i] : 0.0f, py = v ? pos.y[i] : 0.0f, pz = v ? pos.z[i] : 0.0f;
-            if (seg) {   // the slot's place in its label's segment (one atomic per label and warp)
-                const unsigned peers = __match_any_sync(kFullMask, v ? l : -1);
-                unsigned long long at = 0;
-                if (v && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
-                    at = atomicAdd(&S->lcur[l], (unsigned long long)__popc(peers));
-                at = __shfl_sync(kFullMask, at, __ffs(peers) - 1);
-                if (v) byl[loff_sh[l] + (long long)at + __popc(peers & lanemask_lt())] = (uint32_t)i;
-            }
-            for (int o = 0; o < K; ++o) {   // the K - 1 pairs of the particle's label (warp-uniform loop)
-                const int a = l < o ? l : o, b = l < o ? o : l;
-                const int q = T * npairs + a * (2 * K - a - 1) / 2 + (b - a - 1);
-                int key = -1;
-                if (v && o != l) {
-                    SideF g = spec[q];
-                    if (g.scale >= 0.0f) {
-                        if (l == b) { g.u[0] = -g.u[0]; g.u[1] = -g.u[1]; g.u[2] = -g.u[2]; }
-                        int hv = balancing_hash_fast(g, px, py, pz);
-                        if (hv < 0) {   // rare: the FP64 geometry of the pair from the sums, then the FP64 hash
-                            Side G;
-                            combo_geometry(S, Q, alpha, multi, multi ? T : kMaxMat, a, b, G);
-                            if (l == b) { G.d[0] = -G.d[0]; G.d[1] = -G.d[1]; G.d[2] = -G.d[2]; }
-                            hv = balancing_hash64(G.M, G.d, G.dn, G.ell, pos.X[i], pos.Y[i], pos.Z[i]);
-                            atomicAdd(&S->fp64, 1ull);
-                        }
-                        if (hv > 0) key = 2 * q + (l == a ? 0 : 1);
-                    }
-                }
-                if (__any_sync(kFullMask, key >= 0)) {   // positives are rare once labels have settled
-                    const unsigned peers = __match_any_sync(kFullMask, key);
-                    if (key >= 0 && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
-                        atomicAdd(&scnt[key], (uint32_t)__popc(peers));
-                }
-            }
-        }
-        __syncthreads();
-        for (int q = threadIdx.x; q < 2 * ncombo; q += SW_THREADS)
-            if (scnt[q]) atomicAdd(&pairs[q >> 1].spec[q & 1], scnt[q]);
-        if (!grid_barrier(S, nb, err, wc)) return;
-        if (threadIdx.x == 0) {
-            int f = ncombo;
-            for (int q = 0; q < ncombo && f == ncombo; ++q)
-                if (((volatile uint32_t *)&pairs[q].spec[0])[0] > 0u && ((volatile uint32_t *)&pairs[q].spec[1])[0] > 0u) f = q;
-            first_sh = f;
-        }
-        __syncthreads();
-    }
     const int first = first_sh;   // the same in every block
     if (first >= ncombo) return;
 
+    // labels whose particles or sums a pair of this pass has changed (the same in every thread: every
+    // block takes the same decisions). A pair of two unchanged labels sees the pass-start state, so its
+    // speculative counts are its own: an empty side means the pair swaps nothing and changes nothing.
+    uint32_t dirty = 0u;
     int idx = 0;
     for (int T = 0; T < ntype; ++T) {
         const int type = multi ? T : -1;
         const int slot = multi ? T : kMaxMat;
         for (int a = 0; a < K - 1; ++a)
             for (int b = a + 1; b < K; ++b, ++idx) {
-                if (idx < first) continue;   // no positive hashes on a side: nothing to do
                 SwapPair *pr = pairs + idx;
+                if (idx < first) continue;   // no positive hashes on a side: nothing to do
+                if (!(dirty & ((1u << a) | (1u << b))) && (pr->spec[0] == 0u || pr->spec[1] == 0u)) continue;
                 // this pair's particles: the segments of a and b (their labels read from L2: another
                 // block may have written them in an earlier pair)
                 const long long oa = loff_sh[a], na = loff_sh[a + 1] - oa, ob = loff_sh[b];
@@ -568,6 +623,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
                 block_inclusive_scan(cum[1], SW_BINS - 1);
                 const uint32_t m = min(cum[0][SW_BINS - 2], cum[1][SW_BINS - 2]);
                 if (m == 0) continue;    // the same decision in every block: no barrier is skipped unevenly
+                dirty |= (1u << a) | (1u << b);
                 for (int k = threadIdx.x; k < 2 * (SW_BINS - 1); k += SW_THREADS) {
                     const int sd = k / (SW_BINS - 1), r = k % (SW_BINS - 1);
                     const uint32_t above = r > 0 ? cum[sd][r - 1] : 0u;
@@ -783,7 +839,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantPar
 }
 
 // ---------------------------------------------------------------------------------------------
-// Host side: one full pass, one cooperative launch.
+// Host side: one full pass, three streaming launches and one cooperative launch.
 // ---------------------------------------------------------------------------------------------
 size_t swap_scratch_bytes(int K, int nmat) {
     const int ntype = nmat > 1 ? nmat : 1;
@@ -830,6 +886,14 @@ cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const SwapPos &pos, 
     double alpha = P.alpha;
     int K = P.K_labels, nmat = P.nmat;
     SwapPos ps = pos;
+    // the streaming phases: two blocks per cooperative block, at most one thread per particle
+    const int64_t want = (n + SW_THREADS - 1) / SW_THREADS;
+    const unsigned sgrid = (unsigned)(want < 2 * (int64_t)grid ? want : 2 * (int64_t)grid);
+    k_swap_sums<<<sgrid, SW_THREADS, 0, s>>>(n, nmat, ps, lab, mat, S);
+    k_swap_geom<<<1, SW_THREADS, 0, s>>>(Q, alpha, K, nmat, S);
+    k_swap_spec<<<sgrid, SW_THREADS, 0, s>>>(n, Q, alpha, K, nmat, ps, lab, mat, S, pairs, sidx);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     WaitCfg wc{spin_limit > 0 ? spin_limit : (1u << 24), extra_blocks};
     void *args[] = {(void *)&n, (void *)&Q, (void *)&alpha, (void *)&K, (void *)&nmat, (void *)&ps, (void *)&lab,
                     (void *)&mat, (void *)&id, (void *)&bh, (void *)&S, (void *)&pairs, (void *)&tl, (void *)&sidx,
@@ -867,5 +931,6 @@ cudaError_t launch_round_positions(const DevParams &P, int64_t n, const double *
 unsigned long long *swap_moved_ptr(void *scratch) { return &((SwapScratch *)scratch)->moved; }
 // Balancing hashes of the last pass that the FP64 sequence decided (the next word).
 static_assert(offsetof(SwapScratch, fp64) == offsetof(SwapScratch, moved) + 8, "moved, fp64 adjacent");
+static_assert(kMaxLabel <= 32, "the pair loop keeps its changed labels in one 32-bit mask");
 
 }  // namespace gsph
