@@ -179,15 +179,18 @@ typedef struct {
 
 typedef struct {
     /* summed device time per phase (ms) over the steps recorded since gsph_set_timing, from CUDA
-       events recorded on the launch stream around each phase */
+       events recorded around each phase. After the swap pass a step runs two branches at once: the
+       communication hash on the library's second stream and the neighbour-list build on the launch
+       stream; the pair kernel starts when both have ended. comm_ms and nbr_list_ms are the two branches'
+       own spans (they overlap), pair_ms runs from the end of the later one. */
     double hash_sort_ms;   /* bucket hash + radix sort */
     double reorder_ms;     /* permutation into sorted order, bucket ranges, interaction records */
     double swap_ms;        /* swap heuristic passes */
-    double comm_ms;        /* communication hash, flags, boundary lists */
+    double comm_ms;        /* communication hash, flags, boundary lists (second stream) */
     double interact_ms;    /* interaction loop + integration: nbr_list_ms + pair_ms */
     int64_t steps;         /* steps recorded */
     int64_t interact_launches;
-    double nbr_list_ms;    /* of which the neighbour-list kernel */
+    double nbr_list_ms;    /* of which the neighbour-list kernel (beside the communication hash) */
     double pair_ms;        /* of which the pair kernel(s) (fluxes, integration; with reconstruction = 1 also
                               the gradient pass) and the time-step reduction */
     /* overlap = 1 only: the two interaction passes on the launch stream, and the halo gather on the
@@ -236,7 +239,9 @@ gsph_status gsph_get_field(gsph_ctx *ctx, gsph_field f, void *dst, int32_t on_de
 /* Sec. II steps a-g, repeated nsteps times, enqueued on stream: dt from the current state, bucket
  * hash, radix sort, reorder, swap heuristic when the step index is a multiple of swap_period
  * (Sec. III), communication hash and MGPU boundary set (K > 1), interaction loop with integration.
- * Asynchronous: returns after enqueueing. */
+ * Asynchronous: returns after enqueueing. Within a step the communication hash runs on a second,
+ * high-priority stream of the context, forked from `stream` after the swap pass and joined back before
+ * the pair kernel, so work enqueued on `stream` afterwards is ordered after the whole step. */
 gsph_status gsph_step(gsph_ctx *ctx, int32_t nsteps, void *stream);
 
 /* Sec. III.A/B: one swap-heuristic pass over all label pairs on the current state, enqueued on

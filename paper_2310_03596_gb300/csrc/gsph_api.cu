@@ -23,8 +23,8 @@ cudaError_t launch_hash_hist(const DevParams &P, int64_t n, const double *x, con
 cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint32_t *perm,
                            const State &A, double *xs, double *ys, double *zs, uint8_t *lab_s, uint8_t *mat_s,
                            uint32_t *id_s, uint2 *cellr, float *cxs, void *pos, void *rec, float *xf, float *yf,
-                           float *zf, uint32_t *qx, uint32_t *qy, uint32_t *qz, double *hs, float *hsf, int *err,
-                           cudaStream_t s);
+                           float *zf, uint32_t *qx, uint32_t *qy, uint32_t *qz, double *hs, float *hsf,
+                           const void *rec_in, int *err, cudaStream_t s);
 cudaError_t launch_comm(const DevParams &P, int64_t n, const uint32_t *skey, const uint8_t *lab_s, uint32_t *mask,
                         uint8_t *flag, uint32_t *comm, uint32_t *block_counts, unsigned long long *label_total,
                         uint32_t *blist, uint32_t *hidx, uint32_t *scan_part, int *launches, cudaStream_t s);
@@ -45,7 +45,12 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
                             const DtArgs &dtc, unsigned long long *pairs, unsigned long long *cost,
                             int32_t *nreal, int32_t *nimage, double *rates, const OverlapBufs *ov,
-                            int stage, void *grad, const double *hs, const float *hsf, cudaStream_t s);
+                            int stage, bool with_list, void *grad, const double *hs, const float *hsf,
+                            void *rec_next, cudaStream_t s);
+cudaError_t launch_nbr_list(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint2 *cellr,
+                            const void *pos, const float *cxs, const double *xs, const double *ys, const double *zs,
+                            int kmax, uint2 *list, uint32_t *cnt, const double *hs, const float *hsf,
+                            cudaStream_t s);
 cudaError_t launch_refresh(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const State &B,
                            void *pos, void *rec, cudaStream_t s);
 // k_swap.cu
@@ -102,6 +107,11 @@ struct gsph_ctx {
     uint8_t *lab_s = nullptr, *mat_s = nullptr;
     uint32_t *id_s = nullptr;
     void *pos = nullptr, *rec = nullptr;
+    // split path with the linear EOS: the interaction records of the state the last step integrated, in
+    // that step's slot order, written by its integration; the next reorder gathers them instead of
+    // converting the FP64 state (valid only while no call other than a step has changed the state)
+    RecF *rec_next = nullptr;
+    bool rec_next_ok = false;
     uint8_t *flag = nullptr;
     uint32_t *comm = nullptr, *blist = nullptr, *bcounts = nullptr;
     uint32_t *scan_part = nullptr;               // chunk sums of the boundary-count scan
@@ -191,6 +201,14 @@ static cudaError_t alloc_state(gsph_ctx *c, State &S, int64_t n) {
     return e;
 }
 
+// The integration writes the next step's records (split path, every material on the linear EOS).
+static bool record_cache_applies(const gsph_ctx *c) {
+    if (!c->split) return false;
+    for (int k = 0; k < c->P.nmat; ++k)
+        if (c->P.eos[k] != 0) return false;
+    return true;
+}
+
 static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     const size_t N = (size_t)n, C = (size_t)c->P.ncell;
     cudaError_t e;
@@ -213,6 +231,7 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     if (c->split) {
         A_(dalloc(c, (float4 **)&c->pos, N));
         A_(dalloc(c, (RecF **)&c->rec, N));
+        if (record_cache_applies(c)) A_(dalloc(c, &c->rec_next, N));
     } else {
         A_(dalloc(c, (D4 **)&c->pos, N));
         A_(dalloc(c, (RecD **)&c->rec, N));
@@ -440,7 +459,8 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     GSPH_CK(cudaMemsetAsync(c->cellr, 0, (size_t)P.ncell * sizeof(uint2), s));
     GSPH_CK(launch_reorder(c->split, P, n, c->skey, c->perm, c->A, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s,
                            c->cellr, c->cxs, c->pos, c->rec, do_swap ? c->xf : nullptr, c->yf, c->zf, c->qx, c->qy,
-                           c->qz, c->hs, c->hsf, c->err, s));
+                           c->qz, c->hs, c->hsf, c->rec_next_ok ? c->rec_next : nullptr, c->err, s));
+    c->rec_next_ok = false;   // until this step's integration has rewritten them
     c->launches += 1;
     rec_event(c, PH_REORDER, s);
     // Sec. III: periodic swap heuristic on the sorted view
@@ -452,12 +472,25 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
         c->launches += swap_pass_launches(P);
     }
     rec_event(c, PH_SWAP, s);
+    // Two branches from here until the pair kernel: the communication hash (flags, boundary set) on the
+    // second stream, at high priority, while the neighbour lists are built on the launch stream. The lists
+    // read the sorted positions and bucket ranges only, and the communication hash reads no list.
+    GSPH_CK(cudaEventRecord(c->ev_fork, s));
+    GSPH_CK(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+    const cudaStream_t sl = c->aux;
     // b-d. communication hash, MGPU boundary flags and set
     int nl = 0;
     GSPH_CK(launch_comm(P, n, c->skey, c->lab_s, c->mask, c->flag, c->comm, c->bcounts, c->label_off, c->blist,
-                        c->hidx, c->scan_part, &nl, s));
+                        c->hidx, c->scan_part, &nl, sl));
     c->launches += nl;
-    rec_event(c, PH_COMM, s);
+    rec_event(c, PH_COMM, sl);
+    GSPH_CK(cudaEventRecord(c->ev_join, sl));
+    // f. neighbour lists of the step (real neighbours), then the join of the two branches
+    GSPH_CK(launch_nbr_list(c->split, P, n, c->skey, c->cellr, c->pos, c->cxs, c->xs, c->ys, c->zs, kNbrMax, c->nbr,
+                            c->nbr_cnt, c->hs, c->hsf, s));
+    c->launches += 1;
+    rec_event(c, PH_LIST, s);
+    GSPH_CK(cudaStreamWaitEvent(s, c->ev_join, 0));
     // f-g. interaction loop fused with the integration; next dt
     GSPH_CK(cudaMemsetAsync(c->cost, 0, (size_t)kMaxLabel * sizeof(unsigned long long), s));
     OverlapBufs ov{};
@@ -467,10 +500,10 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
                          phase_event(c, PH_HALO1), phase_event(c, PH_LOCAL), c->gather_grid, c->boundary_grid};
     }
     GSPH_CK(launch_interact(c->split, c->cfg.diagnostics != 0, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs,
-                            c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, phase_event(c, PH_LIST),
-                            c->lab_s, c->mat_s, c->id_s, c->dt, dt_args(c), c->pairs, c->cost, c->nreal, c->nimage,
-                            c->rates, c->cfg.overlap ? &ov : nullptr, c->cfg.integrator == 1 ? 1 : 0, c->grad, c->hs,
-                            c->hsf, s));
+                            c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr, c->lab_s,
+                            c->mat_s, c->id_s, c->dt, dt_args(c), c->pairs, c->cost, c->nreal, c->nimage, c->rates,
+                            c->cfg.overlap ? &ov : nullptr, c->cfg.integrator == 1 ? 1 : 0, false, c->grad, c->hs,
+                            c->hsf, c->rec_next, s));
     if (c->cfg.overlap) c->launches += 2;   // halo gather, second pair pass
     if (c->cfg.integrator == 1) {
         // second Heun stage: records of the prediction, then its pairs over the same lists and the average
@@ -478,11 +511,12 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
         GSPH_CK(launch_interact(c->split, c->cfg.diagnostics != 0, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs,
                                 c->xs, c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr,
                                 c->lab_s, c->mat_s, c->id_s, c->dt, dt_args(c), c->pairs, c->cost, c->nreal,
-                                c->nimage, c->rates, nullptr, 2, nullptr, c->hs, c->hsf, s));
+                                c->nimage, c->rates, nullptr, 2, true, nullptr, c->hs, c->hsf, c->rec_next,
+                                s));
         c->launches += 2;
     }
     GSPH_CK(launch_finalize_dt(P, n, dt_args(c), c->B, c->dt, s));
-    c->launches += 3;
+    c->launches += 2;   // pair kernel, time step
     rec_event(c, PH_INTERACT, s);
     if (c->timing_used < c->timing_max) ++c->timing_used;
     State t = c->A;
@@ -490,6 +524,7 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     c->B = t;
     ++c->step;
     c->have_step = true;
+    c->rec_next_ok = c->rec_next != nullptr;
     return GSPH_OK;
 }
 
@@ -508,13 +543,14 @@ static gsph_status enqueue_forward_pieces(gsph_ctx *c, cudaStream_t s) {
     GSPH_CK(cudaMemsetAsync(c->cellr, 0, (size_t)P.ncell * sizeof(uint2), s));
     GSPH_CK(launch_reorder(c->split, P, n, c->skey, c->perm, c->A, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s,
                            c->cellr, c->cxs, c->pos, c->rec, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                           nullptr, nullptr, c->err, s));
+                           nullptr, nullptr, nullptr, c->err, s));
     GSPH_CK(launch_interact(c->split, true, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs, c->ys, c->zs,
                             kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr, c->lab_s, c->mat_s, c->id_s,
-                            c->dt, dt_args(c), c->pairs, c->cost, c->nreal, c->nimage, c->rates, nullptr, 0, nullptr, nullptr,
-                            nullptr, s));
+                            c->dt, dt_args(c), c->pairs, c->cost, c->nreal, c->nimage, c->rates, nullptr, 0, true, nullptr,
+                            nullptr, nullptr, nullptr, s));
     c->launches += 4 + 3 * radix_passes(key_bits(P.ncell));
     c->dt_dirty = true;   // the time-step words now hold the scratch state's candidates
+    c->rec_next_ok = false;
     return GSPH_OK;
 }
 
@@ -576,9 +612,11 @@ gsph_status gsph_create(const gsph_config *cfg, gsph_ctx **out) {
             return GSPH_CUDA_ERROR;
         }
     }
-    if (cfg->overlap) {
-        // the halo gather runs at the highest stream priority, so its few blocks are scheduled ahead of
-        // the first pair pass's and the gather (the broadcast) completes early in that pass
+    {
+        // the second stream runs at the highest priority: the swap pass and the communication hash beside
+        // the list build, so that their few blocks are scheduled ahead of the list kernel's, and with
+        // overlap = 1 the halo gather, ahead of the first pair pass's blocks, so that the gather (the
+        // broadcast) completes early in that pass
         int sms = 0, prio_lo = 0, prio_hi = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg->device) != cudaSuccess ||
             cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess ||
@@ -654,6 +692,7 @@ gsph_status gsph_set_particles(gsph_ctx *c, int64_t n, const double *pos, const 
     c->dt_dirty = false;
     c->step = 0;
     c->have_step = false;
+    c->rec_next_ok = false;
     c->swap_passes = 0;
     c->launches = 3;
     return read_err(c, s);
@@ -684,6 +723,7 @@ gsph_status gsph_put_field(gsph_ctx *c, gsph_field f, const void *src, int32_t o
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     if (!on_device) GSPH_CK(cudaStreamSynchronize(s));
     c->dt_dirty = true;
+    c->rec_next_ok = false;
     return GSPH_OK;
 }
 
@@ -907,10 +947,26 @@ gsph_status gsph_get_timings(gsph_ctx *c, gsph_timings *out) {
         cudaEvent_t *e = &c->ev[(size_t)k * PH_COUNT];
         GSPH_CK(cudaEventSynchronize(e[PH_INTERACT]));
         float t[PH_COUNT] = {0};
-        for (int p = 1; p <= PH_INTERACT; ++p) GSPH_CK(cudaEventElapsedTime(&t[p], e[p - 1], e[p]));
+        for (int p = 1; p <= PH_COMM; ++p) GSPH_CK(cudaEventElapsedTime(&t[p], e[p - 1], e[p]));
+        // the two branches after the swap pass: communication hash on the second stream, the list build on
+        // the launch stream; the pair kernel starts once both have ended
+        GSPH_CK(cudaEventElapsedTime(&t[PH_LIST], e[PH_SWAP], e[PH_LIST]));
+        float t_join = 0.f;   // from the end of the later branch to the end of the step
+        {
+            float a = 0.f, b = 0.f;
+            GSPH_CK(cudaEventElapsedTime(&a, e[PH_LIST], e[PH_INTERACT]));
+            GSPH_CK(cudaEventElapsedTime(&b, e[PH_COMM], e[PH_INTERACT]));
+            t_join = a < b ? a : b;
+        }
+        t[PH_INTERACT] = t_join;
         if (c->cfg.overlap) {
             float tl = 0.f, tb = 0.f, th = 0.f;
             GSPH_CK(cudaEventElapsedTime(&tl, e[PH_LIST], e[PH_LOCAL]));
+            {
+                float b = 0.f;
+                GSPH_CK(cudaEventElapsedTime(&b, e[PH_COMM], e[PH_LOCAL]));
+                tl = tl < b ? tl : b;
+            }
             GSPH_CK(cudaEventElapsedTime(&tb, e[PH_LOCAL], e[PH_INTERACT]));
             GSPH_CK(cudaEventElapsedTime(&th, e[PH_HALO0], e[PH_HALO1]));
             out->local_ms += tl;
@@ -1047,6 +1103,7 @@ gsph_status gsph_load_state(gsph_ctx *c, const void *src, size_t bytes, int32_t 
     c->step = h.step;
     c->dt_dirty = !h.dt_valid;
     c->have_step = false;
+    c->rec_next_ok = false;
     return GSPH_OK;
 }
 

@@ -476,4 +476,26 @@ __device__ __forceinline__ void eos_pc(const DevParams &P, int mat, double rho, 
     if (p < P.p_min[mat]) p = P.p_min[mat];
 }
 
+// Split-path interaction record of a state, the position part aside: FP32 velocity and density, the
+// diagonal of the full stress sigma = -p I + S (S traceless in FP32: S_zz = -(S_xx + S_yy)), impedance
+// and energy; linear EOS, p = K (rho/rho0 - 1) = K (m - rho0 w) / (rho0 w) with the cancelling difference
+// in FP64. Every operation is an explicitly rounded intrinsic, so the reorder (from the gathered FP64
+// state) and the integration (from the new state it has just formed) produce the same bits.
+__device__ __forceinline__ RecF record_split_linear(const DevParams &P, int mat, double w, double m, double vx,
+                                                    double vy, double vz, double E, double sxx, double syy,
+                                                    double sxy, double sxz, double syz) {
+    const float rho = __fdiv_rn(__double2float_rn(m), __double2float_rn(w));
+    const double rw = __dmul_rn(P.rho0[mat], w);
+    float pf = __fdiv_rn(__fmul_rn(P.f_K[mat], __double2float_rn(__dsub_rn(m, rw))), __double2float_rn(rw));
+    const float pmin = __double2float_rn(P.p_min[mat]);
+    if (pf < pmin) pf = pmin;
+    const float Zf = __fmul_rn(rho, __fsqrt_rn(__fdiv_rn(P.f_Mmod[mat], rho)));
+    const float fxx = __double2float_rn(sxx), fyy = __double2float_rn(syy), fzz = -__fadd_rn(fxx, fyy);
+    RecF r;
+    r.a = make_float4(__double2float_rn(vx), __double2float_rn(vy), __double2float_rn(vz), rho);
+    r.b = make_float4(__fsub_rn(fzz, pf), Zf, __double2float_rn(E), __fsub_rn(fxx, pf));
+    r.c = make_float4(__fsub_rn(fyy, pf), __double2float_rn(sxy), __double2float_rn(sxz), __double2float_rn(syz));
+    return r;
+}
+
 }  // namespace gsph

@@ -646,6 +646,8 @@ struct PairArgs {
     // variable h only: sorted smoothing lengths, FP64 and FP32
     const double *hs;
     const float *hsf;
+    // split path, linear EOS: the records of the integrated state by slot (the next reorder gathers them)
+    RecF *rec_next;
 };
 
 template <bool SPLIT, bool DIAG, int MODE, bool VARH>
@@ -816,16 +818,18 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         // entry in flight when the current one is used up. The record loads that follow are
         // unconditional (a lane past its last neighbour reloads its last valid slot), which keeps the
         // loop body free of branches around them
-        auto next = [&](uint32_t &j, uint32_t &c) {
-            const int t = 31 - __clz(m);
-            m ^= 1u << t;
-            j = (y & IT_JMASK) + (uint32_t)t;
-            c = y >> 26;
-            if (m == 0u) {
-                m = nx.x; y = nx.y;
-                if (ke < ne) nx = lp[(size_t)ke * colstep];
-                ++ke;
-            }
+        auto next = [&](bool more, uint32_t &j, uint32_t &c) {
+            const int t = 31 - __clz(m | 1u);
+            const uint32_t mn = m ^ (1u << t);
+            const uint32_t jn = (y & IT_JMASK) + (uint32_t)t;
+            const uint32_t cn = y >> 26;
+            j = more ? jn : j;
+            c = more ? cn : c;
+            const bool rf = more && mn == 0u;
+            m = more ? (rf ? nx.x : mn) : m;
+            y = rf ? nx.y : y;
+            if (rf && ke < ne) nx = lp[(size_t)ke * colstep];
+            ke += rf ? 1 : 0;
         };
         // record source: the particle arrays, or (second pass, other labels) the halo buffer
         auto fetch = [&](uint32_t j, bool t, Pos &pj, Rec &rj, float &xj, R &hj) {
@@ -843,7 +847,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         };
         const int mc = (int)__reduce_max_sync(kFullMask, nlist);
         uint32_t j1 = 0u, c1 = 0u;
-        if (nlist > 0) next(j1, c1);
+        next(nlist > 0, j1, c1);
         bool t1 = take(j1);
         Pos p1;
         Rec r1;
@@ -851,7 +855,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         R h1;
         fetch(j1, t1, p1, r1, x1, h1);
         // unrolled 4 times; the MUSCL flux pass (168 registers) measured faster with the loop rolled
-#pragma unroll (MODE == PM_MUSCL ? 1 : 4)
+#pragma unroll (MODE == PM_MUSCL ? 1 : 2)
         for (int k = 0; k < mc; ++k) {
             const uint32_t j = j1, c = c1;
             const Pos pj = p1;
@@ -859,7 +863,7 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
             const float xj = x1;
             const R hj = h1;
             const bool tj = t1;
-            if ((uint32_t)k + 1 < nlist) next(j1, c1);   // else j1 stays a valid slot
+            next((uint32_t)k + 1 < nlist, j1, c1);   // else j1 stays a valid slot
             t1 = take(j1);
             fetch(j1, t1, p1, r1, x1, h1);
             const bool act = (uint32_t)k < nlist && tj;
@@ -1197,6 +1201,8 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         B.mat[s] = a.mat_s[s];
         B.label[s] = a.lab_s[s];
         B.id[s] = a.id_s[s];
+        if (SPLIT && MODE != PM_HEUN1 && a.rec_next)   // the end state's record, as the reorder forms it
+            a.rec_next[s] = record_split_linear(P, mt, wo, mo, nvx, nvy, nvz, En, Sn[0], Sn[1], Sn[3], Sn[4], Sn[5]);
         if (VARH) B.h[s] = A.h[o];
         if (DIAG && MODE != PM_HEUN2) {   // the step's counts and rates: those of its start
             a.nreal_out[s] = nr;
@@ -1265,7 +1271,8 @@ static PairArgs<SPLIT> pair_args(const DevParams &P, int64_t n, const uint32_t *
                                  const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s,
                                  const double *dt, const DtArgs &dtc, unsigned long long *pairs,
                                  unsigned long long *cost, int32_t *nreal, int32_t *nimage, double *rates,
-                                 const OverlapBufs *ov, void *grad, const double *hs, const float *hsf) {
+                                 const OverlapBufs *ov, void *grad, const double *hs, const float *hsf,
+                                 RecF *rec_next) {
     using Pos = typename Types<SPLIT>::Pos;
     using Rec = typename Types<SPLIT>::Rec;
     PairArgs<SPLIT> a;
@@ -1285,7 +1292,31 @@ static PairArgs<SPLIT> pair_args(const DevParams &P, int64_t n, const uint32_t *
     a.grad = (typename Types<SPLIT>::G4 *)grad;
     a.hs = hs;
     a.hsf = hsf;
+    a.rec_next = SPLIT ? rec_next : nullptr;
     return a;
+}
+
+// The neighbour lists alone (the step then calls launch_interact with with_list = false): they read
+// the sorted positions and bucket ranges only, so they can be built while the labels are still changing.
+cudaError_t launch_nbr_list(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint2 *cellr,
+                            const void *pos, const float *cxs, const double *xs, const double *ys, const double *zs,
+                            int kmax, uint2 *list, uint32_t *cnt, const double *hs, const float *hsf,
+                            cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const unsigned gl = (unsigned)((n + NL_THREADS - 1) / NL_THREADS);
+    const bool varh = P.variable_h != 0;
+#define GSPH_LIST_LAUNCH(SP)                                                                        \
+    do {                                                                                            \
+        const auto *p = (const typename Types<SP>::Pos *)pos;                                       \
+        if (varh) k_nbr_list<SP, true><<<gl, NL_THREADS, 0, s>>>(P, n, skey, cellr, p, cxs, xs, ys, zs, \
+                                                                 kmax, list, cnt, hs, hsf);          \
+        else k_nbr_list<SP, false><<<gl, NL_THREADS, 0, s>>>(P, n, skey, cellr, p, cxs, xs, ys, zs,     \
+                                                              kmax, list, cnt, hs, hsf);            \
+    } while (0)
+    if (split) GSPH_LIST_LAUNCH(true);
+    else GSPH_LIST_LAUNCH(false);
+#undef GSPH_LIST_LAUNCH
+    return cudaGetLastError();
 }
 
 cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n, const uint32_t *skey,
@@ -1295,14 +1326,16 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
                             const DtArgs &dtc, unsigned long long *pairs, unsigned long long *cost,
                             int32_t *nreal, int32_t *nimage, double *rates, const OverlapBufs *ov,
-                            int stage, void *grad, const double *hs, const float *hsf, cudaStream_t s) {
+                            int stage, bool with_list, void *grad, const double *hs, const float *hsf,
+                            void *rec_next, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const bool varh = P.variable_h != 0;
     const unsigned gl = (unsigned)((n + NL_THREADS - 1) / NL_THREADS);
     const unsigned gp = (unsigned)((n + PK_THREADS - 1) / PK_THREADS);
 #define GSPH_NL_ARGS P, n, skey, cellr, (const typename Types<SP>::Pos *)pos, cxs, xs, ys, zs, kmax, list, cnt, hs, hsf
 #define GSPH_PAIR_ARGS pair_args<SP>(P, n, skey, cellr, pos, rec, cxs, xs, ys, zs, kmax, list, cnt, perm, A, B, \
-                                     lab_s, mat_s, id_s, dt, dtc, pairs, cost, nreal, nimage, rates, ov, grad, hs, hsf)
+                                     lab_s, mat_s, id_s, dt, dtc, pairs, cost, nreal, nimage, rates, ov, grad, hs, hsf, \
+                                     (RecF *)rec_next)
 #define GSPH_PAIRS(MODE_)                                                                   \
     do {                                                                                    \
         const auto pa = GSPH_PAIR_ARGS;                                                      \
@@ -1317,7 +1350,7 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
     } while (0)
 #define GSPH_INTERACT                                                                       \
     do {                                                                                    \
-        if (stage != 2) {                                                                   \
+        if (stage != 2 && with_list) {                                                      \
             if (varh) k_nbr_list<SP, true><<<gl, NL_THREADS, 0, s>>>(GSPH_NL_ARGS);        \
             else k_nbr_list<SP, false><<<gl, NL_THREADS, 0, s>>>(GSPH_NL_ARGS);            \
         }                                                                                   \

@@ -14,6 +14,20 @@ namespace gsph {
 // Interaction record of one particle in slot s with bucket hash k: split path, the position relative
 // to the own bucket corner and the FP32 state with the stress diagonal as sigma = -p I + S; FP64 path,
 // the FP64 position and state. Pressure and impedance from the equation of state.
+// Split-path position record: the position relative to the particle's own bucket corner (|.| < 2h, so
+// FP32 keeps it to about 2^-24 * 2h) and the FP32 volume.
+__device__ __forceinline__ float4 pos_split(const DevParams &P, uint32_t k, double x, double y, double z, double w) {
+    float4 p4 = make_float4(0.f, 0.f, 0.f, (float)w);
+    if (k < P.ncell) {
+        int cx, cy, cz;
+        decode_cell(P, k, cx, cy, cz);
+        p4.x = (float)(x - (P.lo[0] + (double)cx * P.cell));
+        p4.y = (float)(y - (P.lo[1] + (double)cy * P.cell));
+        p4.z = (float)(z - (P.lo[2] + (double)cz * P.cell));
+    }
+    return p4;
+}
+
 template <bool SPLIT>
 __device__ __forceinline__ void write_record(const DevParams &P, int64_t s, uint32_t k, double x, double y, double z,
                                              double w, double m, double vx, double vy, double vz, double E,
@@ -22,37 +36,21 @@ __device__ __forceinline__ void write_record(const DevParams &P, int64_t s, uint
                                              void *__restrict__ rec_out) {
     if (SPLIT) {
         RecF r;
-        float4 p4 = make_float4(0.f, 0.f, 0.f, (float)w);
-        if (k < P.ncell) {
-            int cx, cy, cz;
-            decode_cell(P, k, cx, cy, cz);
-            // position relative to the particle's own bucket corner: |.| < 2h, so FP32 keeps it to
-            // about 2^-24 * 2h
-            p4.x = (float)(x - (P.lo[0] + (double)cx * P.cell));
-            p4.y = (float)(y - (P.lo[1] + (double)cy * P.cell));
-            p4.z = (float)(z - (P.lo[2] + (double)cz * P.cell));
-        }
-        float rho = (float)m / (float)w;
-        float pf, Zf;
+        ((float4 *)pos_out)[s] = pos_split(P, k, x, y, z, w);
         if (P.eos[mat] == 0) {
-            // p = K (rho/rho0 - 1) = K (m - rho0 w) / (rho0 w): the cancelling difference in FP64
-            double rw = P.rho0[mat] * w;
-            pf = P.f_K[mat] * (float)(m - rw) / (float)rw;
-            if (pf < (float)P.p_min[mat]) pf = (float)P.p_min[mat];
-            Zf = rho * sqrtf(P.f_Mmod[mat] / rho);
+            r = record_split_linear(P, mat, w, m, vx, vy, vz, E, sxx, syy, sxy, sxz, syz);
         } else {   // Mie-Gruneisen in FP64 (its Hugoniot terms cancel as well), rounded once
+            const float rho = (float)m / (float)w;
             double pd, cd;
             const double rd = m / w;
             eos_pc(P, mat, rd, E - 0.5 * (vx * vx + vy * vy + vz * vz), pd, cd);
-            pf = (float)pd;
-            Zf = (float)(rd * cd);
+            const float pf = (float)pd, Zf = (float)(rd * cd);
+            // the diagonal of the full stress sigma = -p I + S (S traceless in FP32: S_zz = -(S_xx + S_yy))
+            const float fxx = (float)sxx, fyy = (float)syy, fzz = -(fxx + fyy);
+            r.a = make_float4((float)vx, (float)vy, (float)vz, rho);
+            r.b = make_float4(fzz - pf, Zf, (float)E, fxx - pf);
+            r.c = make_float4(fyy - pf, (float)sxy, (float)sxz, (float)syz);
         }
-        // the diagonal of the full stress sigma = -p I + S (S traceless in FP32: S_zz = -(S_xx + S_yy))
-        const float fxx = (float)sxx, fyy = (float)syy, fzz = -(fxx + fyy);
-        r.a = make_float4((float)vx, (float)vy, (float)vz, rho);
-        r.b = make_float4(fzz - pf, Zf, (float)E, fxx - pf);
-        r.c = make_float4(fyy - pf, (float)sxy, (float)sxz, (float)syz);
-        ((float4 *)pos_out)[s] = p4;
         ((RecF *)rec_out)[s] = r;
         (void)szz;
     } else {
@@ -81,7 +79,7 @@ __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const u
                                                  float *__restrict__ zf, uint32_t *__restrict__ qx,
                                                  uint32_t *__restrict__ qy, uint32_t *__restrict__ qz,
                                                  double *__restrict__ hs, float *__restrict__ hsf,
-                                                 int *__restrict__ err) {
+                                                 const RecF *__restrict__ rec_in, int *__restrict__ err) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     uint32_t k = skey[s];
@@ -115,6 +113,11 @@ __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const u
     } else {
         cxs[s] = -1.0e9f;
     }
+    if (SPLIT && rec_in) {   // the record the previous step's integration wrote from the same state
+        ((float4 *)pos_out)[s] = pos_split(P, k, x, y, z, A.f[FW][o]);
+        ((RecF *)rec_out)[s] = rec_in[o];
+        return;
+    }
     write_record<SPLIT>(P, s, k, x, y, z, A.f[FW][o], A.f[FM][o], A.f[FVX][o], A.f[FVY][o], A.f[FVZ][o],
                         A.f[FE][o], A.f[FSXX][o], A.f[FSYY][o], A.f[FSZZ][o], A.f[FSXY][o], A.f[FSXZ][o],
                         A.f[FSYZ][o], mat, pos_out, rec_out);
@@ -145,16 +148,16 @@ cudaError_t launch_refresh(bool split, const DevParams &P, int64_t n, const uint
 cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint32_t *perm,
                            const State &A, double *xs, double *ys, double *zs, uint8_t *lab_s, uint8_t *mat_s,
                            uint32_t *id_s, uint2 *cellr, float *cxs, void *pos, void *rec, float *xf, float *yf,
-                           float *zf, uint32_t *qx, uint32_t *qy, uint32_t *qz, double *hs, float *hsf, int *err,
-                           cudaStream_t s) {
+                           float *zf, uint32_t *qx, uint32_t *qy, uint32_t *qz, double *hs, float *hsf,
+                           const void *rec_in, int *err, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     unsigned g = (unsigned)((n + 255) / 256);
     if (split)
         k_reorder<true><<<g, 256, 0, s>>>(P, n, skey, perm, A, xs, ys, zs, lab_s, mat_s, id_s, cellr, cxs, pos, rec,
-                                          xf, yf, zf, qx, qy, qz, hs, hsf, err);
+                                          xf, yf, zf, qx, qy, qz, hs, hsf, (const RecF *)rec_in, err);
     else
         k_reorder<false><<<g, 256, 0, s>>>(P, n, skey, perm, A, xs, ys, zs, lab_s, mat_s, id_s, cellr, cxs, pos, rec,
-                                           xf, yf, zf, qx, qy, qz, hs, hsf, err);
+                                           xf, yf, zf, qx, qy, qz, hs, hsf, nullptr, err);
     return cudaGetLastError();
 }
 
