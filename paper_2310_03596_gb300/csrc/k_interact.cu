@@ -427,6 +427,7 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
         const bool ing = need && cy == gby && cz == gbz &&
                          (SPLIT ? (unsigned)(cx - gbx) <= 2u : abs(cx - gbx) <= 4);
         const float oxg = fmaf((float)(cx - gbx) - 1.5f, fcell, ox);   // own x in the group frame
+        const float gx15 = (float)gbx + 1.5f;   // exact: candidate x in the group frame is (cx_j - gx15) 2h + x
         for (int row = 0; row < 9; ++row) {
             const int dcy = row % 3 - 1, dcz = row / 3 - 1;
             const int Yc = gby + dcy, Zc = gbz + dcz;
@@ -447,136 +448,128 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
             const int cxm1 = cx - 1;
             for (uint32_t b = lo; b < hi; b += 32) {
                 const uint32_t jl = b + lane;
-                {
+                if constexpr (SPLIT) {
+                    // stage: slots past the range load the last slot of the range and get |c|^2 = +inf,
+                    // which no test accepts (inf plus finite terms stays inf, above the band)
+                    const bool inr = jl < hi;
+                    const uint32_t jc = inr ? jl : hi - 1u;
+                    const Pos q = pos[jc];
+                    const float qx = fmaf(cxs[jc] - gx15, fcell, (float)q.x);
+                    const float qy = (float)q.y - hcell, qz = (float)q.z - hcell;
+                    float qw = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
+                    if (VARH) {
+                        const float hj = hsf[jc];
+                        qw = fmaf(-P.f_vlo * hj, hj, qw);
+                        splane[4 * NL_THREADS + tid] = inr ? hj : 0.0f;
+                    }
+                    splane[tid] = qx;
+                    splane[NL_THREADS + tid] = qy;
+                    splane[2 * NL_THREADS + tid] = qz;
+                    splane[3 * NL_THREADS + tid] = inr ? qw : __int_as_float(0x7f800000);
+                } else {
                     Pos q;
                     if (jl < hi) {
                         q = pos[jl];
-                        const float cxj = cxs[jl];
-                        if (SPLIT) {
-                            const float qx = fmaf(cxj - (float)gbx - 1.5f, fcell, (float)q.x);
-                            const float qy = (float)q.y - hcell, qz = (float)q.z - hcell;
-                            q.x = qx; q.y = qy; q.z = qz;
-                            q.w = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
-                            if (VARH) {
-                                const float hj = hsf[jl];
-                                q.w = fmaf(-P.f_vlo * hj, hj, (float)q.w);
-                                splane[4 * NL_THREADS + tid] = hj;
-                            }
-                        } else {
-                            q.w = (double)cxj;
-                            if (VARH) hstage[tid] = hs[jl];
-                        }
-                    } else if (SPLIT) {
-                        // past the end of the range: |c|^2 = +inf, which no test accepts
-                        q.x = 0.0f; q.y = 0.0f; q.z = 0.0f; q.w = __int_as_float(0x7f800000);
-                        if (VARH) splane[4 * NL_THREADS + tid] = 0.0f;
+                        q.w = (double)cxs[jl];
+                        if (VARH) hstage[tid] = hs[jl];
                     } else {
                         q.x = 1.0e30; q.y = 1.0e30; q.z = 1.0e30; q.w = -1.0e9;
                         if (VARH) hstage[tid] = 0.0;
                     }
-                    if (SPLIT) {
-                        splane[tid] = (float)q.x;
-                        splane[NL_THREADS + tid] = (float)q.y;
-                        splane[2 * NL_THREADS + tid] = (float)q.z;
-                        splane[3 * NL_THREADS + tid] = (float)q.w;
-                    } else {
-                        stage[tid] = q;
-                    }
+                    stage[tid] = q;
                 }
                 __syncwarp();
-                if (ing) {
-                    // straight-line tests build a hit mask and a band mask over the staged batch;
-                    // stores and the rare FP64 decisions follow per set bit. On the split path a
-                    // candidate outside the own 3-bucket window is more than 2h away, so its FP32 r^2
-                    // cannot fall below the band and the fast test needs no window check.
-                    uint32_t hitm = 0u, bandm = 0u;
-                    if (SPLIT) {
-                        // the sign of r^2 - R2lo is shifted into the hit mask, candidate t ending at bit
-                        // 31 - t; one reversal at the end restores bit t. r^2 - R2lo =
-                        // fma(mx, x, fma(my, y, fma(mz, z, |c|^2 + Kr))) on packed pairs of candidates
-                        // (each lane of a pair rounded as the scalar operation); the band below R2hi is
-                        // found from the smallest unsigned value of r^2 - R2lo (variable h: the widest
-                        // band of this particle's pairs, h_j <= h)
-                        const float hw = hif + (float)P.h;
-                        const uint32_t wbits = VARH ? __float_as_uint((P.f_vhi - P.f_vlo) * hw * hw)
-                                                    : __float_as_uint(P.f_R2hi - P.f_R2lo);
-                        uint32_t umin = 0xffffffffu;
-                        const float2 mx2 = make_float2(mx, mx), my2 = make_float2(my, my), mz2 = make_float2(mz, mz);
-                        const float2 kr2 = make_float2(Kr, Kr), mh2 = make_float2(mh, mh);
+                // never its own neighbour
+                const uint32_t selfbit = (self - b < 32u) ? 1u << (self - b) : 0u;
+                uint32_t hitm = 0u, bandm = 0u;
+                if constexpr (SPLIT) {
+                    // every lane tests (lanes outside the group discard their mask): straight-line packed
+                    // tests build the hit mask; the sign of r^2 - R2lo is shifted into the mask, candidate t
+                    // ending at bit 31 - t after the alignment shift, and one reversal restores bit t. r^2 - R2lo =
+                    // fma(mx, x, fma(my, y, fma(mz, z, |c|^2 + Kr))) on packed pairs of candidates (each lane
+                    // of a pair rounded as the scalar operation); the band below R2hi is found from the
+                    // smallest unsigned value of r^2 - R2lo (variable h: the widest band of this particle's
+                    // pairs, h_j <= h). A candidate outside the own 3-bucket window is more than 2h away, so
+                    // its FP32 r^2 cannot fall below the band and the fast test needs no window check.
+                    const float hw = hif + (float)P.h;
+                    const uint32_t wbits = VARH ? __float_as_uint((P.f_vhi - P.f_vlo) * hw * hw)
+                                                : __float_as_uint(P.f_R2hi - P.f_R2lo);
+                    uint32_t umin = 0xffffffffu;
+                    const float2 mx2 = make_float2(mx, mx), my2 = make_float2(my, my), mz2 = make_float2(mz, mz);
+                    const float2 kr2 = make_float2(Kr, Kr), mh2 = make_float2(mh, mh);
+                    // the last batch of a row tests only its staged slots, in groups of four (the slots past
+                    // the range hold |c|^2 = +inf and would add no hit)
+                    const uint32_t nt = min(hi - b, 32u), ntest = (nt + 3u) & ~3u;
 #pragma unroll
-                        for (int t = 0; t < 32; t += 4) {
-                            const float4 X4 = *(const float4 *)&splane[wbase + t];
-                            const float4 Y4 = *(const float4 *)&splane[NL_THREADS + wbase + t];
-                            const float4 Z4 = *(const float4 *)&splane[2 * NL_THREADS + wbase + t];
-                            const float4 W4 = *(const float4 *)&splane[3 * NL_THREADS + wbase + t];
-                            float4 H4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                            if (VARH) H4 = *(const float4 *)&splane[4 * NL_THREADS + wbase + t];
+                    for (int t = 0; t < 32; t += 4) {
+                        if (t > 0 && (uint32_t)t >= ntest) break;
+                        const float4 X4 = *(const float4 *)&splane[wbase + t];
+                        const float4 Y4 = *(const float4 *)&splane[NL_THREADS + wbase + t];
+                        const float4 Z4 = *(const float4 *)&splane[2 * NL_THREADS + wbase + t];
+                        const float4 W4 = *(const float4 *)&splane[3 * NL_THREADS + wbase + t];
+                        float4 H4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (VARH) H4 = *(const float4 *)&splane[4 * NL_THREADS + wbase + t];
 #pragma unroll
-                            for (int h2 = 0; h2 < 2; ++h2) {
-                                const float2 xx = h2 ? make_float2(X4.z, X4.w) : make_float2(X4.x, X4.y);
-                                const float2 yy = h2 ? make_float2(Y4.z, Y4.w) : make_float2(Y4.x, Y4.y);
-                                const float2 zz = h2 ? make_float2(Z4.z, Z4.w) : make_float2(Z4.x, Z4.y);
-                                const float2 ww = h2 ? make_float2(W4.z, W4.w) : make_float2(W4.x, W4.y);
-                                float2 d = __fadd2_rn(ww, kr2);
-                                if (VARH) d = __ffma2_rn(mh2, h2 ? make_float2(H4.z, H4.w) : make_float2(H4.x, H4.y), d);
-                                d = __ffma2_rn(mz2, zz, d);
-                                d = __ffma2_rn(my2, yy, d);
-                                d = __ffma2_rn(mx2, xx, d);
-                                hitm = __funnelshift_l(__float_as_uint(d.x), hitm, 1);
-                                hitm = __funnelshift_l(__float_as_uint(d.y), hitm, 1);
-                                umin = min(umin, min(__float_as_uint(d.x), __float_as_uint(d.y)));
-                            }
-                        }
-                        hitm = __brev(hitm);
-                        // a candidate is in the band when 0 <= d < R2hi - R2lo, i.e. its bits as an unsigned
-                        // integer are below those of the band width (negative d has the sign bit set); the
-                        // smallest such bits of the batch say whether any is, and the rare batch that has
-                        // one rebuilds the band mask with the same scalar roundings
-                        if (umin < wbits) {
-#pragma unroll 4
-                            for (int t = 0; t < 32; ++t) {
-                                float d0 = splane[3 * NL_THREADS + wbase + t] + Kr;
-                                if (VARH) d0 = fmaf(mh, splane[4 * NL_THREADS + wbase + t], d0);
-                                const float d = fmaf(mx, splane[wbase + t], fmaf(my, splane[NL_THREADS + wbase + t],
-                                                fmaf(mz, splane[2 * NL_THREADS + wbase + t], d0)));
-                                if (__float_as_uint(d) < wbits) bandm |= 1u << t;
-                            }
+                        for (int h2 = 0; h2 < 2; ++h2) {
+                            const float2 xx = h2 ? make_float2(X4.z, X4.w) : make_float2(X4.x, X4.y);
+                            const float2 yy = h2 ? make_float2(Y4.z, Y4.w) : make_float2(Y4.x, Y4.y);
+                            const float2 zz = h2 ? make_float2(Z4.z, Z4.w) : make_float2(Z4.x, Z4.y);
+                            const float2 ww = h2 ? make_float2(W4.z, W4.w) : make_float2(W4.x, W4.y);
+                            float2 d = __fadd2_rn(ww, kr2);
+                            if (VARH) d = __ffma2_rn(mh2, h2 ? make_float2(H4.z, H4.w) : make_float2(H4.x, H4.y), d);
+                            d = __ffma2_rn(mz2, zz, d);
+                            d = __ffma2_rn(my2, yy, d);
+                            d = __ffma2_rn(mx2, xx, d);
+                            hitm = __funnelshift_l(__float_as_uint(d.x), hitm, 1);
+                            hitm = __funnelshift_l(__float_as_uint(d.y), hitm, 1);
+                            umin = min(umin, min(__float_as_uint(d.x), __float_as_uint(d.y)));
                         }
                     }
-                    if (!SPLIT) {
-#pragma unroll
+                    hitm = __brev(hitm << (32u - ntest)) & ~selfbit;
+                    // a candidate is in the band when 0 <= d < R2hi - R2lo, i.e. its bits as an unsigned
+                    // integer are below those of the band width (negative d has the sign bit set); the
+                    // smallest such bits of the batch say whether any is, and the rare batch that has one
+                    // rebuilds the band mask with the same scalar roundings, then decides each member with
+                    // its own window and the exactly rounded FP64 predicate
+                    if (ing && umin < wbits) {
+#pragma unroll 4
                         for (int t = 0; t < 32; ++t) {
-                            const Pos pj = stage[wbase + t];
-                            const int cxj = (int)pj.w;
+                            float d0 = splane[3 * NL_THREADS + wbase + t] + Kr;
+                            if (VARH) d0 = fmaf(mh, splane[4 * NL_THREADS + wbase + t], d0);
+                            const float d = fmaf(mx, splane[wbase + t], fmaf(my, splane[NL_THREADS + wbase + t],
+                                            fmaf(mz, splane[2 * NL_THREADS + wbase + t], d0)));
+                            if (__float_as_uint(d) < wbits) bandm |= 1u << t;
+                        }
+                        bandm &= ~(hitm | selfbit);
+                        while (bandm) {
+                            const int t = __ffs(bandm) - 1;
+                            bandm &= bandm - 1;
+                            const int cxj = (int)cxs[b + (uint32_t)t];
                             if ((uint32_t)(cxj - cxm1) <= 2u &&
-                                dist2_rn(__dsub_rn((double)pj.x, X), __dsub_rn((double)pj.y, Y),
-                                         __dsub_rn((double)pj.z, Z)) < pair_R2(VARH, P, hid, VARH ? hstage[wbase + t] : 0.0))
+                                support_exact(P, xs, ys, zs, b + (uint32_t)t, xs[s], ys[s], zs[s], -1, 0.0,
+                                              pair_R2(VARH, P, hid, VARH ? hs[b + (uint32_t)t] : 0.0)))
                                 hitm |= 1u << t;
                         }
                     }
-                    bandm &= ~hitm;
-                    if (self - b < 32u) {   // never its own neighbour
-                        hitm &= ~(1u << (self - b));
-                        bandm &= ~(1u << (self - b));
-                    }
-                    while (bandm) {         // rounding band: own window, then exactly rounded FP64 decides
-                        const int t = __ffs(bandm) - 1;
-                        bandm &= bandm - 1;
-                        const int cxj = (int)cxs[b + (uint32_t)t];
+                    if (!ing) hitm = 0u;
+                } else if (ing) {
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) {
+                        const Pos pj = stage[wbase + t];
+                        const int cxj = (int)pj.w;
                         if ((uint32_t)(cxj - cxm1) <= 2u &&
-                            support_exact(P, xs, ys, zs, b + (uint32_t)t, xs[s], ys[s], zs[s], -1, 0.0,
-                                          pair_R2(VARH, P, hid, VARH ? hs[b + (uint32_t)t] : 0.0)))
+                            dist2_rn(__dsub_rn((double)pj.x, X), __dsub_rn((double)pj.y, Y),
+                                     __dsub_rn((double)pj.z, Z)) < pair_R2(VARH, P, hid, VARH ? hstage[wbase + t] : 0.0))
                             hitm |= 1u << t;
                     }
-                    if (hitm) {
-                        if (cnt < (uint32_t)kmax) {
-                            *out = make_uint2(hitm, b | code_yz);
-                            nlisted += (uint32_t)__popc(hitm);
-                        }
-                        out += colstep;
-                        ++cnt;
-                    }
+                    hitm &= ~selfbit;
                 }
+                // one entry per batch with a hit
+                const bool any = hitm != 0u;
+                if (any && cnt < (uint32_t)kmax) *out = make_uint2(hitm, b | code_yz);
+                nlisted += (any && cnt < (uint32_t)kmax) ? (uint32_t)__popc(hitm) : 0u;
+                out += any ? colstep : 0;
+                cnt += any ? 1u : 0u;
                 __syncwarp();
             }
         }
