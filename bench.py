@@ -40,16 +40,20 @@ LINK_GBPS = 900.0   # modelled inter-GPU link bandwidth per direction (NVLink 5 
 SMS, FP32_LANES = 152, 128
 
 
-def algorithmic_bytes_per_particle_step(key_passes: int, K: int, swap_every: int) -> dict:
-    """Compulsory HBM bytes per particle and step of each kernel (state read/written once)."""
+def algorithmic_bytes_per_particle_step(key_passes: int, K: int, swap_every: int, record_copy: bool = True) -> dict:
+    """Compulsory HBM bytes per particle and step of each kernel (state read/written once). With
+    record_copy (split path, linear EOS) the integration writes the next step's 48-byte state record and
+    the reorder gathers it with the positions, volume and ids instead of the whole FP64 state."""
     state = 15 * 8 + 6          # FP64 fields + material, label, id
     rec = 64                    # FP32 interaction record (position + state)
+    gathered = (4 * 8 + 6 + 48) if record_copy else state
     b = {
         "hash": 24 + 8,                                   # x y z in, key + slot out
         "sort": key_passes * (4 + 8 + 8),                 # histogram read + key/slot in and out
-        "reorder": 8 + state + 24 + 6 + rec,              # key+perm, gathered state, sorted x, ids, records
+        "reorder": 8 + gathered + 24 + 6 + rec,           # key+perm, gathered input, sorted x, ids, records
         "comm": 4 + 1 + 1 + 4 + 4,                        # key, label, flag, comm hash, list entry
-        "interact": rec + 8 + state + 24 + 6 + state,     # own record, key/perm, state in, state out
+        # own record, key/perm, state in, state out (and the next record)
+        "interact": rec + 8 + state + 24 + 6 + state + (48 if record_copy else 0),
     }
     if K > 1 and swap_every > 0:
         # the reorder writes the FP32 positions (12 B); the pass reads them and the labels once for the
