@@ -220,6 +220,15 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     A_(dalloc(c, &c->hist, radix_hist_words(n)));
     A_(dalloc(c, &c->tot, 512));   // one total per digit value (digits of at most 9 bits)
     A_(dalloc(c, &c->cellr, C));
+    for (int a = 0; a < 3; ++a) {   // bucket corners fma(i, 2h, lo), the same bits as the device's __fma_rn
+        double *t = nullptr;
+        const int d = c->P.dims[a] > 0 ? c->P.dims[a] : 1;
+        A_(dalloc(c, &t, (size_t)d));
+        std::vector<double> h((size_t)d);
+        for (int i = 0; i < d; ++i) h[(size_t)i] = std::fma((double)i, c->P.cell, c->P.lo[a]);
+        A_(cudaMemcpy(t, h.data(), (size_t)d * sizeof(double), cudaMemcpyHostToDevice));
+        c->P.corner[a] = t;
+    }
     A_(dalloc(c, &c->mask, C));
     A_(dalloc(c, &c->xs, N)); A_(dalloc(c, &c->ys, N)); A_(dalloc(c, &c->zs, N));
     A_(dalloc(c, &c->cxs, N));

@@ -58,6 +58,8 @@ struct DevParams {
     // Cg = lo + mean(q) q_step, q_step = L 2^-32, L = dims * 2h the grid extent per axis
     double q_s[3], q_step[3];
     double wall_reach;       // (2h)(1 + 1e-6): beyond this distance from a wall plane no image is in the support
+    // bucket corners per axis, fma(c, 2h, lo) for c in [0, dims): device tables of the buffer set
+    const double *corner[3];
 };
 constexpr double kVarBand = 1.0e-3;
 

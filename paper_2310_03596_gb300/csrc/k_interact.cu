@@ -908,9 +908,10 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
             if (wax == 1) FY_ = __dsub_rn(two_w, YF);
             if (wax == 2) FZ_ = __dsub_rn(two_w, ZF);
             if (SPLIT) {
-                ox = (R)(FX_ - (P.lo[0] + (double)bx * P.cell));
-                oy = (R)(FY_ - (P.lo[1] + (double)by * P.cell));
-                oz = (R)(FZ_ - (P.lo[2] + (double)bz * P.cell));
+                // (the corner as the reorder's tables hold it; bx may lie outside the grid here)
+                ox = (R)(FX_ - __fma_rn((double)bx, P.cell, P.lo[0]));
+                oy = (R)(FY_ - __fma_rn((double)by, P.cell, P.lo[1]));
+                oz = (R)(FZ_ - __fma_rn((double)bz, P.cell, P.lo[2]));
             } else {
                 ox = (R)FX_; oy = (R)FY_; oz = (R)FZ_;
             }

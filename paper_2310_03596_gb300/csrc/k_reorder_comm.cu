@@ -15,15 +15,16 @@ namespace gsph {
 // to the own bucket corner and the FP32 state with the stress diagonal as sigma = -p I + S; FP64 path,
 // the FP64 position and state. Pressure and impedance from the equation of state.
 // Split-path position record: the position relative to the particle's own bucket corner (|.| < 2h, so
-// FP32 keeps it to about 2^-24 * 2h) and the FP32 volume.
+// FP32 keeps it to about 2^-24 * 2h) and the FP32 volume. The corners come from per-axis tables
+// (fma(c, 2h, lo), formed once per buffer set), which saves the FP64 product of every particle.
 __device__ __forceinline__ float4 pos_split(const DevParams &P, uint32_t k, double x, double y, double z, double w) {
     float4 p4 = make_float4(0.f, 0.f, 0.f, (float)w);
     if (k < P.ncell) {
         int cx, cy, cz;
         decode_cell(P, k, cx, cy, cz);
-        p4.x = (float)(x - (P.lo[0] + (double)cx * P.cell));
-        p4.y = (float)(y - (P.lo[1] + (double)cy * P.cell));
-        p4.z = (float)(z - (P.lo[2] + (double)cz * P.cell));
+        p4.x = (float)(x - P.corner[0][cx]);
+        p4.y = (float)(y - P.corner[1][cy]);
+        p4.z = (float)(z - P.corner[2][cz]);
     }
     return p4;
 }
