@@ -806,11 +806,12 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         if (ne > 0) { const uint2 e = lp[0]; m = e.x; y = e.y; }
         if (ne > 1) nx = lp[colstep];
         int ke = 2;
-        // next listed neighbour (called only while one is left): slot j, row code c, the highest set bit
-        // of the mask first (the order within a batch only affects rounding); refills the mask from the
-        // entry in flight when the current one is used up. The record loads that follow are
-        // unconditional (a lane past its last neighbour reloads its last valid slot), which keeps the
-        // loop body free of branches around them
+        // next listed neighbour when `more` (a neighbour is left), by selects rather than a branch: slot j,
+        // row code c, the highest set bit of the mask first (the order within a batch only affects
+        // rounding); refills the mask from the entry in flight when the current one is used up (the
+        // refill's load predicated). Without `more`, j and c keep a valid slot. The record loads that
+        // follow are unconditional (a lane past its last neighbour reloads its last valid slot), which
+        // keeps the loop body free of branches
         auto next = [&](bool more, uint32_t &j, uint32_t &c) {
             const int t = 31 - __clz(m | 1u);
             const uint32_t mn = m ^ (1u << t);
@@ -847,7 +848,8 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
         float x1;
         R h1;
         fetch(j1, t1, p1, r1, x1, h1);
-        // unrolled 4 times; the MUSCL flux pass (168 registers) measured faster with the loop rolled
+        // unrolled twice (measured faster than 1, 3, 4 or 8); the MUSCL flux pass (168 registers) measured
+        // faster with the loop rolled
 #pragma unroll (MODE == PM_MUSCL ? 1 : 2)
         for (int k = 0; k < mc; ++k) {
             const uint32_t j = j1, c = c1;
