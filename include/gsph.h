@@ -192,7 +192,8 @@ typedef struct {
     int64_t interact_launches;
     double nbr_list_ms;    /* of which the neighbour-list kernel (beside the communication hash) */
     double pair_ms;        /* of which the pair kernel(s) (fluxes, integration; with reconstruction = 1 also
-                              the gradient pass) and the time-step reduction */
+                              the gradient pass); the time-step reduction that follows runs on the
+                              second stream and is in no phase */
     /* overlap = 1 only: the two interaction passes on the launch stream, and the halo gather on the
        second stream (events there), which runs concurrently with the first pass */
     double local_ms;       /* pairs within a label, integration of particles without other labels near */
@@ -241,7 +242,9 @@ gsph_status gsph_get_field(gsph_ctx *ctx, gsph_field f, void *dst, int32_t on_de
  * (Sec. III), communication hash and MGPU boundary set (K > 1), interaction loop with integration.
  * Asynchronous: returns after enqueueing. Within a step the communication hash runs on a second,
  * high-priority stream of the context, forked from `stream` after the swap pass and joined back before
- * the pair kernel, so work enqueued on `stream` afterwards is ordered after the whole step. */
+ * the pair kernel; each step's time-step reduction runs on that stream too, beside the next step's
+ * hash, sort and reorder, and the last step of the call joins it back. Work enqueued on `stream`
+ * afterwards is ordered after all of it. */
 gsph_status gsph_step(gsph_ctx *ctx, int32_t nsteps, void *stream);
 
 /* Sec. III.A/B: one swap-heuristic pass over all label pairs on the current state, enqueued on

@@ -122,6 +122,10 @@ struct gsph_ctx {
     int32_t *part_cnt = nullptr;
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the time-step reduction of a step runs on the second stream beside the next step's first phases;
+    // ev_dt marks its end, which the next pair kernel (or the end of the gsph_step call) waits for
+    cudaEvent_t ev_pair = nullptr, ev_dt = nullptr;
+    bool dt_pending = false;
     unsigned gather_grid = 0, boundary_grid = 0;
     unsigned long long *label_off = nullptr;   // K + 1
     unsigned long long *cost = nullptr;        // pair interactions per label, last step
@@ -442,7 +446,9 @@ static cudaEvent_t phase_event(gsph_ctx *c, int phase) {
     return c->timing_used < c->timing_max ? c->ev[(size_t)c->timing_used * PH_COUNT + phase] : nullptr;
 }
 
-static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
+// One step. settle = false (a further step of the same gsph_step call follows) leaves the step's
+// time-step reduction running on the second stream; the next step's pair kernel waits for it.
+static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s, bool settle = true) {
     const DevParams &P = c->P;
     const int64_t n = c->n;
     if (c->dt_dirty) {
@@ -501,6 +507,10 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     rec_event(c, PH_LIST, s);
     GSPH_CK(cudaStreamWaitEvent(s, c->ev_join, 0));
     // f-g. interaction loop fused with the integration; next dt
+    if (c->dt_pending) {   // the previous step's time step, which the integration uses
+        GSPH_CK(cudaStreamWaitEvent(s, c->ev_dt, 0));
+        c->dt_pending = false;
+    }
     GSPH_CK(cudaMemsetAsync(c->cost, 0, (size_t)kMaxLabel * sizeof(unsigned long long), s));
     OverlapBufs ov{};
     if (c->cfg.overlap) {
@@ -524,9 +534,15 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
                                 s));
         c->launches += 2;
     }
-    GSPH_CK(launch_finalize_dt(P, n, dt_args(c), c->B, c->dt, s));
-    c->launches += 2;   // pair kernel, time step
+    // the next time step from the integration's candidates, on the second stream: it needs only the
+    // pair kernel's output, and only the next pair kernel needs it
     rec_event(c, PH_INTERACT, s);
+    GSPH_CK(cudaEventRecord(c->ev_pair, s));
+    GSPH_CK(cudaStreamWaitEvent(c->aux, c->ev_pair, 0));
+    GSPH_CK(launch_finalize_dt(P, n, dt_args(c), c->B, c->dt, c->aux));
+    GSPH_CK(cudaEventRecord(c->ev_dt, c->aux));
+    c->dt_pending = true;
+    c->launches += 2;   // pair kernel, time step
     if (c->timing_used < c->timing_max) ++c->timing_used;
     State t = c->A;
     c->A = c->B;
@@ -534,6 +550,10 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s) {
     ++c->step;
     c->have_step = true;
     c->rec_next_ok = c->rec_next != nullptr;
+    if (settle) {   // work enqueued on s after this call sees the step's time step
+        GSPH_CK(cudaStreamWaitEvent(s, c->ev_dt, 0));
+        c->dt_pending = false;
+    }
     return GSPH_OK;
 }
 
@@ -631,7 +651,9 @@ gsph_status gsph_create(const gsph_config *cfg, gsph_ctx **out) {
             cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess ||
             cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_pair, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_dt, cudaEventDisableTiming) != cudaSuccess) {
             gsph_destroy(c);
             return GSPH_CUDA_ERROR;
         }
@@ -650,6 +672,8 @@ void gsph_destroy(gsph_ctx *c) {
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_pair) cudaEventDestroy(c->ev_pair);
+    if (c->ev_dt) cudaEventDestroy(c->ev_dt);
     if (c->aux) cudaStreamDestroy(c->aux);
     delete c;
 }
@@ -780,7 +804,7 @@ gsph_status gsph_step(gsph_ctx *c, int32_t nsteps, void *stream) {
     GSPH_CK(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
     for (int k = 0; k < nsteps; ++k) {
-        gsph_status st = enqueue_step(c, s);
+        gsph_status st = enqueue_step(c, s, k == nsteps - 1);
         if (st != GSPH_OK) return st;
     }
     return GSPH_OK;
