@@ -353,7 +353,7 @@ __device__ __forceinline__ int spec_hash64(const SwapScratch *S, const QuantPara
 // sequential loop starts at the first pair with positive hashes on both sides: until then the labels and
 // sums each pair sees are the pass-start ones, the state this pass evaluates. With 8 or more labels the
 // same sweep groups the slots by label (the label segments of the pair loop).
-__global__ void __launch_bounds__(SW_THREADS) k_swap_spec(int64_t n, QuantParams Q, double alpha, int K, int nmat,
+__global__ void __launch_bounds__(SW_THREADS, 2) k_swap_spec(int64_t n, QuantParams Q, double alpha, int K, int nmat,
                                                           const SwapPos pos, const uint8_t *__restrict__ lab,
                                                           const uint8_t *__restrict__ mat, SwapScratch *__restrict__ S,
                                                           SwapPair *__restrict__ pairs, uint32_t *__restrict__ sidx) {
