@@ -405,6 +405,31 @@ __global__ void __launch_bounds__(128) k_adj_integrate(DevParams P, int64_t n, c
 // ---------------------------------------------------------------------------------------------
 constexpr uint32_t ADJ_JMASK = (1u << 26) - 1;
 
+// x = c ? a : b, y = c ? b : a, field by field
+__device__ __forceinline__ void sel_prim(bool c, const Prim64 &a, const Prim64 &b, Prim64 &x, Prim64 &y) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { x.v[k] = c ? a.v[k] : b.v[k]; y.v[k] = c ? b.v[k] : a.v[k]; }
+    x.rho = c ? a.rho : b.rho; y.rho = c ? b.rho : a.rho;
+    x.p = c ? a.p : b.p; y.p = c ? b.p : a.p;
+    x.Z = c ? a.Z : b.Z; y.Z = c ? b.Z : a.Z;
+    x.E = c ? a.E : b.E; y.E = c ? b.E : a.E;
+    x.w = c ? a.w : b.w; y.w = c ? b.w : a.w;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { x.S[k] = c ? a.S[k] : b.S[k]; y.S[k] = c ? b.S[k] : a.S[k]; }
+}
+// acc += c ? a : b, field by field
+__device__ __forceinline__ void sel_add_bar(PBar &acc, bool c, const PBar &a, const PBar &b) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc.v[k] += c ? a.v[k] : b.v[k];
+    acc.rho += c ? a.rho : b.rho;
+    acc.p += c ? a.p : b.p;
+    acc.Z += c ? a.Z : b.Z;
+    acc.E += c ? a.E : b.E;
+    acc.w += c ? a.w : b.w;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc.S[k] += c ? a.S[k] : b.S[k];
+}
+
 __device__ __forceinline__ void load_mu(const double *__restrict__ mu, int64_t n, int64_t i, double out[kNRate]) {
     for (int k = 0; k < kNRate; ++k) out[k] = mu[(size_t)k * n + i];
 }
@@ -509,18 +534,34 @@ __global__ void __launch_bounds__(128) k_adj_pair(DevParams P, int64_t n, const 
                 bL.zero();
                 bR.zero();
                 double db[3];
-                if (kL) pair_reverse(d, me, oth, ih, kdw, ob, bL, bR, db);
-                else pair_reverse(d, oth, me, ih, kdw, ob, bL, bR, db);
-                add_bar(bk, kL ? bL : bR);
+                // one sweep with the operands in the pair's orientation (selects, so that the lanes of a
+                // warp whose pairs have either orientation run it together)
+                Prim64 Lq, Rq;
+                sel_prim(kL, me, oth, Lq, Rq);
+                pair_reverse(d, Lq, Rq, ih, kdw, ob, bL, bR, db);
+                sel_add_bar(bk, kL, bL, bR);
                 for (int c = 0; c < 3; ++c) xb[c] += kL ? -db[c] : db[c];
             };
             // listed neighbours: the set bits of each entry's mask, slots base + t in ascending order
-            const uint32_t cnt = cnt_in[s] & 255u;   // entries found (low byte; the rest is a count)
-            const int ne = (int)min(cnt, (uint32_t)kmax);
-            uint32_t nlist = 0;
-            for (int k = 0; k < ne; ++k) {
-                const uint2 e = list[(size_t)k * n + s];
-                for (uint32_t m = e.x; m; m &= m - 1u, ++nlist) real_pair((e.y & ADJ_JMASK) + (uint32_t)(__ffs(m) - 1));
+            // one flat loop over the listed neighbours (the lanes of a warp iterate together; only the
+            // entry refill branches), lowest set bit first
+            const uint32_t cw = cnt_in[s];
+            const uint32_t cnt = cw & 255u;          // entries found (low byte)
+            const uint32_t nlist = cw >> 8;          // neighbours in the stored entries
+            {
+                uint32_t m = 0u, yb = 0u;
+                size_t ke = 0;
+                for (uint32_t it = 0; it < nlist; ++it) {
+                    while (m == 0u) {   // stored entries all have a hit
+                        const uint2 e = list[ke * (size_t)n + s];
+                        m = e.x;
+                        yb = e.y & ADJ_JMASK;
+                        ++ke;
+                    }
+                    const uint32_t t = (uint32_t)(__ffs(m) - 1);
+                    m &= m - 1u;
+                    real_pair(yb + t);
+                }
             }
             // beyond the list capacity, and the wall images: re-scan around the own / mirrored point
             int cx, cy, cz;
