@@ -24,7 +24,7 @@ cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint
                            const State &A, double *xs, double *ys, double *zs, uint8_t *lab_s, uint8_t *mat_s,
                            uint32_t *id_s, uint2 *cellr, float *cxs, void *pos, void *rec, float *xf, float *yf,
                            float *zf, uint32_t *qx, uint32_t *qy, uint32_t *qz, double *hs, float *hsf,
-                           const void *rec_in, int *err, cudaStream_t s);
+                           const void *rec_in, float4 *posf, int *err, cudaStream_t s);
 cudaError_t launch_comm(const DevParams &P, int64_t n, const uint32_t *skey, const uint8_t *lab_s, uint32_t *mask,
                         uint8_t *flag, uint32_t *comm, uint32_t *block_counts, unsigned long long *label_total,
                         uint32_t *blist, uint32_t *hidx, uint32_t *scan_part, int *launches, cudaStream_t s);
@@ -45,12 +45,12 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
                             const DtArgs &dtc, unsigned long long *pairs, unsigned long long *cost,
                             int32_t *nreal, int32_t *nimage, double *rates, const OverlapBufs *ov,
-                            int stage, bool with_list, void *grad, const double *hs, const float *hsf,
-                            void *rec_next, cudaStream_t s);
-cudaError_t launch_nbr_list(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint2 *cellr,
-                            const void *pos, const float *cxs, const double *xs, const double *ys, const double *zs,
-                            int kmax, uint2 *list, uint32_t *cnt, const double *hs, const float *hsf,
+                            int stage, void *grad, const double *hs, const float *hsf, void *rec_next,
                             cudaStream_t s);
+cudaError_t launch_nbr_list(const DevParams &P, int64_t n, const uint32_t *skey, const uint2 *cellr,
+                            const float4 *pos_rel, const float *cxs, const double *xs, const double *ys,
+                            const double *zs, int kmax, uint2 *list, uint32_t *cnt, const double *hs,
+                            const float *hsf, cudaStream_t s);
 cudaError_t launch_refresh(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const State &B,
                            void *pos, void *rec, cudaStream_t s);
 // k_swap.cu
@@ -107,6 +107,7 @@ struct gsph_ctx {
     uint8_t *lab_s = nullptr, *mat_s = nullptr;
     uint32_t *id_s = nullptr;
     void *pos = nullptr, *rec = nullptr;
+    float4 *posf = nullptr;   // FP64 path: FP32 bucket-relative positions for the neighbour-list build
     // split path with the linear EOS: the interaction records of the state the last step integrated, in
     // that step's slot order, written by its integration; the next reorder gathers them instead of
     // converting the FP64 state (valid only while no call other than a step has changed the state)
@@ -248,6 +249,7 @@ static cudaError_t alloc_all(gsph_ctx *c, int64_t n) {
     } else {
         A_(dalloc(c, (D4 **)&c->pos, N));
         A_(dalloc(c, (RecD **)&c->rec, N));
+        A_(dalloc(c, &c->posf, N));
     }
     A_(dalloc(c, &c->flag, N));
     A_(dalloc(c, &c->comm, N));
@@ -474,7 +476,7 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s, bool settle = true)
     GSPH_CK(cudaMemsetAsync(c->cellr, 0, (size_t)P.ncell * sizeof(uint2), s));
     GSPH_CK(launch_reorder(c->split, P, n, c->skey, c->perm, c->A, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s,
                            c->cellr, c->cxs, c->pos, c->rec, do_swap ? c->xf : nullptr, c->yf, c->zf, c->qx, c->qy,
-                           c->qz, c->hs, c->hsf, c->rec_next_ok ? c->rec_next : nullptr, c->err, s));
+                           c->qz, c->hs, c->hsf, c->rec_next_ok ? c->rec_next : nullptr, c->posf, c->err, s));
     c->rec_next_ok = false;   // until this step's integration has rewritten them
     c->launches += 1;
     rec_event(c, PH_REORDER, s);
@@ -501,8 +503,8 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s, bool settle = true)
     rec_event(c, PH_COMM, sl);
     GSPH_CK(cudaEventRecord(c->ev_join, sl));
     // f. neighbour lists of the step (real neighbours), then the join of the two branches
-    GSPH_CK(launch_nbr_list(c->split, P, n, c->skey, c->cellr, c->pos, c->cxs, c->xs, c->ys, c->zs, kNbrMax, c->nbr,
-                            c->nbr_cnt, c->hs, c->hsf, s));
+    GSPH_CK(launch_nbr_list(P, n, c->skey, c->cellr, c->split ? (const float4 *)c->pos : c->posf, c->cxs, c->xs,
+                            c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->hs, c->hsf, s));
     c->launches += 1;
     rec_event(c, PH_LIST, s);
     GSPH_CK(cudaStreamWaitEvent(s, c->ev_join, 0));
@@ -521,7 +523,7 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s, bool settle = true)
     GSPH_CK(launch_interact(c->split, c->cfg.diagnostics != 0, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs,
                             c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr, c->lab_s,
                             c->mat_s, c->id_s, c->dt, dt_args(c), c->pairs, c->cost, c->nreal, c->nimage, c->rates,
-                            c->cfg.overlap ? &ov : nullptr, c->cfg.integrator == 1 ? 1 : 0, false, c->grad, c->hs,
+                            c->cfg.overlap ? &ov : nullptr, c->cfg.integrator == 1 ? 1 : 0, c->grad, c->hs,
                             c->hsf, c->rec_next, s));
     if (c->cfg.overlap) c->launches += 2;   // halo gather, second pair pass
     if (c->cfg.integrator == 1) {
@@ -530,8 +532,7 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s, bool settle = true)
         GSPH_CK(launch_interact(c->split, c->cfg.diagnostics != 0, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs,
                                 c->xs, c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr,
                                 c->lab_s, c->mat_s, c->id_s, c->dt, dt_args(c), c->pairs, c->cost, c->nreal,
-                                c->nimage, c->rates, nullptr, 2, true, nullptr, c->hs, c->hsf, c->rec_next,
-                                s));
+                                c->nimage, c->rates, nullptr, 2, nullptr, c->hs, c->hsf, c->rec_next, s));
         c->launches += 2;
     }
     // the next time step from the integration's candidates, on the second stream: it needs only the
@@ -572,10 +573,12 @@ static gsph_status enqueue_forward_pieces(gsph_ctx *c, cudaStream_t s) {
     GSPH_CK(cudaMemsetAsync(c->cellr, 0, (size_t)P.ncell * sizeof(uint2), s));
     GSPH_CK(launch_reorder(c->split, P, n, c->skey, c->perm, c->A, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s,
                            c->cellr, c->cxs, c->pos, c->rec, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                           nullptr, nullptr, nullptr, c->err, s));
+                           nullptr, nullptr, nullptr, c->posf, c->err, s));
+    GSPH_CK(launch_nbr_list(P, n, c->skey, c->cellr, c->split ? (const float4 *)c->pos : c->posf, c->cxs, c->xs,
+                            c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->hs, c->hsf, s));
     GSPH_CK(launch_interact(c->split, true, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs, c->ys, c->zs,
                             kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr, c->lab_s, c->mat_s, c->id_s,
-                            c->dt, dt_args(c), c->pairs, c->cost, c->nreal, c->nimage, c->rates, nullptr, 0, true, nullptr,
+                            c->dt, dt_args(c), c->pairs, c->cost, c->nreal, c->nimage, c->rates, nullptr, 0, nullptr,
                             nullptr, nullptr, nullptr, s));
     c->launches += 4 + 3 * radix_passes(key_bits(P.ncell));
     c->dt_dirty = true;   // the time-step words now hold the scratch state's candidates

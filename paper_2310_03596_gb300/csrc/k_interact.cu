@@ -369,28 +369,23 @@ __device__ __forceinline__ double pair_R2(bool varh, const DevParams &P, double 
 // Neighbour list (real neighbours). list[k * n + i], k < kmax: (mask, base | (dcy + 1) << 26 | (dcz + 1) << 28),
 // the neighbours being slots base + t for the set bits t of mask, in ascending (row, slot) order;
 // cnt[i] = min(entries found, 255) | (neighbours in the stored entries) << 8. Entries found beyond kmax
-// are not stored: the pair kernel finds those neighbours by re-scanning.
+// are not stored: the pair kernel finds those neighbours by re-scanning. Both precisions build their
+// lists here, from the FP32 positions relative to each particle's bucket corner (the split record's, or
+// a copy the FP64 path's reorder writes): the decision is the exact FP64 predicate either way.
 // ---------------------------------------------------------------------------------------------
-template <bool SPLIT, bool VARH>
+template <bool VARH>
 __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t n, const uint32_t *__restrict__ skey,
                                                          const uint2 *__restrict__ cellr,
-                                                         const typename Types<SPLIT>::Pos *__restrict__ pos,
+                                                         const float4 *__restrict__ pos,
                                                          const float *__restrict__ cxs, const double *__restrict__ xs,
                                                          const double *__restrict__ ys, const double *__restrict__ zs,
                                                          int kmax, uint2 *__restrict__ list,
                                                          uint32_t *__restrict__ cnt_out, const double *__restrict__ hs,
                                                          const float *__restrict__ hsf) {
-    using Pos = typename Types<SPLIT>::Pos;
-    // staged candidate: split path (c, |c|^2) with c = (x in the group frame, y, z in the row frame);
-    // FP64 path (x, y, z, bucket x)
-    // split path: four planes (x, y, z, |c|^2) of NL_THREADS floats, so that one 16-byte load gives a
-    // coordinate of four candidates and the tests run on packed pairs; FP64 path: one D4 per candidate
-    // (variable h: a fifth plane of FP32 lengths, or NL_THREADS FP64 lengths after the D4s)
-    using R = typename Types<SPLIT>::R;
-    __shared__ __align__(16) unsigned char stage_raw[NL_THREADS * (sizeof(Pos) + (VARH ? sizeof(R) : 0))];
-    Pos *stage = (Pos *)stage_raw;
-    float *splane = (float *)stage_raw;
-    double *hstage = (double *)(stage_raw + NL_THREADS * sizeof(Pos));
+    // staged candidate (c, |c|^2) with c = (x in the group frame, y, z in the row frame), as four planes
+    // (x, y, z, |c|^2) of NL_THREADS floats, so that one 16-byte load gives a coordinate of four candidates
+    // and the tests run on packed pairs (variable h: a fifth plane of FP32 lengths)
+    __shared__ __align__(16) float splane[NL_THREADS * (VARH ? 5 : 4)];
     const int tid = threadIdx.x, lane = tid & 31, wbase = tid & ~31;
     const int64_t s = (int64_t)blockIdx.x * NL_THREADS + tid;
     const bool valid = s < n;
@@ -399,11 +394,9 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
     int cx = 0, cy = 0, cz = 0;
     if (active) decode_cell(P, key, cx, cy, cz);
     float ox = 0.f, oy = 0.f, oz = 0.f;
-    double X = 0.0, Y = 0.0, Z = 0.0;
     if (active) {
-        const Pos p = pos[s];
-        ox = (float)p.x; oy = (float)p.y; oz = (float)p.z;
-        if (!SPLIT) { X = (double)p.x; Y = (double)p.y; Z = (double)p.z; }
+        const float4 p = pos[s];
+        ox = p.x; oy = p.y; oz = p.z;
     }
     const float fcell = P.f_cell, hcell = 0.5f * P.f_cell;
     const uint32_t self = (uint32_t)s;
@@ -420,12 +413,11 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
         const int leader = __ffs(todo) - 1;
         const int gby = __shfl_sync(kFullMask, cy, leader), gbz = __shfl_sync(kFullMask, cz, leader);
         const int gbx = __shfl_sync(kFullMask, cx, leader);
-        // a group shares the bucket row. Split path: its buckets are the leader's and the next two in x
-        // (the leader has the lowest x bucket of its row among the remaining lanes), and the group frame
-        // has its x origin 1.5 buckets above the leader's bucket corner, so |x| < 5h for own positions
-        // and window candidates. FP64 path: within 4 buckets of the leader.
-        const bool ing = need && cy == gby && cz == gbz &&
-                         (SPLIT ? (unsigned)(cx - gbx) <= 2u : abs(cx - gbx) <= 4);
+        // a group shares the bucket row: its buckets are the leader's and the next two in x (the leader
+        // has the lowest x bucket of its row among the remaining lanes), and the group frame has its x
+        // origin 1.5 buckets above the leader's bucket corner, so |x| < 5h for own positions and window
+        // candidates
+        const bool ing = need && cy == gby && cz == gbz && (unsigned)(cx - gbx) <= 2u;
         const float oxg = fmaf((float)(cx - gbx) - 1.5f, fcell, ox);   // own x in the group frame
         const float gx15 = (float)gbx + 1.5f;   // exact: candidate x in the group frame is (cx_j - gx15) 2h + x
         for (int row = 0; row < 9; ++row) {
@@ -448,14 +440,14 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
             const int cxm1 = cx - 1;
             for (uint32_t b = lo; b < hi; b += 32) {
                 const uint32_t jl = b + lane;
-                if constexpr (SPLIT) {
+                {
                     // stage: slots past the range load the last slot of the range and get |c|^2 = +inf,
                     // which no test accepts (inf plus finite terms stays inf, above the band)
                     const bool inr = jl < hi;
                     const uint32_t jc = inr ? jl : hi - 1u;
-                    const Pos q = pos[jc];
-                    const float qx = fmaf(cxs[jc] - gx15, fcell, (float)q.x);
-                    const float qy = (float)q.y - hcell, qz = (float)q.z - hcell;
+                    const float4 q = pos[jc];
+                    const float qx = fmaf(cxs[jc] - gx15, fcell, q.x);
+                    const float qy = q.y - hcell, qz = q.z - hcell;
                     float qw = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
                     if (VARH) {
                         const float hj = hsf[jc];
@@ -466,23 +458,12 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                     splane[NL_THREADS + tid] = qy;
                     splane[2 * NL_THREADS + tid] = qz;
                     splane[3 * NL_THREADS + tid] = inr ? qw : __int_as_float(0x7f800000);
-                } else {
-                    Pos q;
-                    if (jl < hi) {
-                        q = pos[jl];
-                        q.w = (double)cxs[jl];
-                        if (VARH) hstage[tid] = hs[jl];
-                    } else {
-                        q.x = 1.0e30; q.y = 1.0e30; q.z = 1.0e30; q.w = -1.0e9;
-                        if (VARH) hstage[tid] = 0.0;
-                    }
-                    stage[tid] = q;
                 }
                 __syncwarp();
                 // never its own neighbour
                 const uint32_t selfbit = (self - b < 32u) ? 1u << (self - b) : 0u;
                 uint32_t hitm = 0u, bandm = 0u;
-                if constexpr (SPLIT) {
+                {
                     // every lane tests (lanes outside the group discard their mask): straight-line packed
                     // tests build the hit mask; the sign of r^2 - R2lo is shifted into the mask, candidate t
                     // ending at bit 31 - t after the alignment shift, and one reversal restores bit t. r^2 - R2lo =
@@ -552,17 +533,6 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                         }
                     }
                     if (!ing) hitm = 0u;
-                } else if (ing) {
-#pragma unroll
-                    for (int t = 0; t < 32; ++t) {
-                        const Pos pj = stage[wbase + t];
-                        const int cxj = (int)pj.w;
-                        if ((uint32_t)(cxj - cxm1) <= 2u &&
-                            dist2_rn(__dsub_rn((double)pj.x, X), __dsub_rn((double)pj.y, Y),
-                                     __dsub_rn((double)pj.z, Z)) < pair_R2(VARH, P, hid, VARH ? hstage[wbase + t] : 0.0))
-                            hitm |= 1u << t;
-                    }
-                    hitm &= ~selfbit;
                 }
                 // one entry per batch with a hit
                 const bool any = hitm != 0u;
@@ -1292,26 +1262,21 @@ static PairArgs<SPLIT> pair_args(const DevParams &P, int64_t n, const uint32_t *
     return a;
 }
 
-// The neighbour lists alone (the step then calls launch_interact with with_list = false): they read
-// the sorted positions and bucket ranges only, so they can be built while the labels are still changing.
-cudaError_t launch_nbr_list(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint2 *cellr,
-                            const void *pos, const float *cxs, const double *xs, const double *ys, const double *zs,
-                            int kmax, uint2 *list, uint32_t *cnt, const double *hs, const float *hsf,
-                            cudaStream_t s) {
+// The neighbour lists (before launch_interact): they read the sorted FP32 bucket-relative positions
+// (pos_rel: the split record's, or the FP64 path's copy) and the bucket ranges only, so they can be built
+// while the labels are still changing.
+cudaError_t launch_nbr_list(const DevParams &P, int64_t n, const uint32_t *skey, const uint2 *cellr,
+                            const float4 *pos_rel, const float *cxs, const double *xs, const double *ys,
+                            const double *zs, int kmax, uint2 *list, uint32_t *cnt, const double *hs,
+                            const float *hsf, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const unsigned gl = (unsigned)((n + NL_THREADS - 1) / NL_THREADS);
-    const bool varh = P.variable_h != 0;
-#define GSPH_LIST_LAUNCH(SP)                                                                        \
-    do {                                                                                            \
-        const auto *p = (const typename Types<SP>::Pos *)pos;                                       \
-        if (varh) k_nbr_list<SP, true><<<gl, NL_THREADS, 0, s>>>(P, n, skey, cellr, p, cxs, xs, ys, zs, \
-                                                                 kmax, list, cnt, hs, hsf);          \
-        else k_nbr_list<SP, false><<<gl, NL_THREADS, 0, s>>>(P, n, skey, cellr, p, cxs, xs, ys, zs,     \
-                                                              kmax, list, cnt, hs, hsf);            \
-    } while (0)
-    if (split) GSPH_LIST_LAUNCH(true);
-    else GSPH_LIST_LAUNCH(false);
-#undef GSPH_LIST_LAUNCH
+    if (P.variable_h != 0)
+        k_nbr_list<true><<<gl, NL_THREADS, 0, s>>>(P, n, skey, cellr, pos_rel, cxs, xs, ys, zs, kmax, list, cnt, hs,
+                                                   hsf);
+    else
+        k_nbr_list<false><<<gl, NL_THREADS, 0, s>>>(P, n, skey, cellr, pos_rel, cxs, xs, ys, zs, kmax, list, cnt, hs,
+                                                    hsf);
     return cudaGetLastError();
 }
 
@@ -1322,13 +1287,11 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
                             const uint8_t *lab_s, const uint8_t *mat_s, const uint32_t *id_s, const double *dt,
                             const DtArgs &dtc, unsigned long long *pairs, unsigned long long *cost,
                             int32_t *nreal, int32_t *nimage, double *rates, const OverlapBufs *ov,
-                            int stage, bool with_list, void *grad, const double *hs, const float *hsf,
-                            void *rec_next, cudaStream_t s) {
+                            int stage, void *grad, const double *hs, const float *hsf, void *rec_next,
+                            cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const bool varh = P.variable_h != 0;
-    const unsigned gl = (unsigned)((n + NL_THREADS - 1) / NL_THREADS);
     const unsigned gp = (unsigned)((n + PK_THREADS - 1) / PK_THREADS);
-#define GSPH_NL_ARGS P, n, skey, cellr, (const typename Types<SP>::Pos *)pos, cxs, xs, ys, zs, kmax, list, cnt, hs, hsf
 #define GSPH_PAIR_ARGS pair_args<SP>(P, n, skey, cellr, pos, rec, cxs, xs, ys, zs, kmax, list, cnt, perm, A, B, \
                                      lab_s, mat_s, id_s, dt, dtc, pairs, cost, nreal, nimage, rates, ov, grad, hs, hsf, \
                                      (RecF *)rec_next)
@@ -1346,10 +1309,6 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
     } while (0)
 #define GSPH_INTERACT                                                                       \
     do {                                                                                    \
-        if (stage != 2 && with_list) {                                                      \
-            if (varh) k_nbr_list<SP, true><<<gl, NL_THREADS, 0, s>>>(GSPH_NL_ARGS);        \
-            else k_nbr_list<SP, false><<<gl, NL_THREADS, 0, s>>>(GSPH_NL_ARGS);            \
-        }                                                                                   \
         if (mid) cudaEventRecord(mid, s);                                                   \
         if (stage == 1) {                                                                   \
             GSPH_PAIRS(PM_HEUN1);                                                           \
@@ -1388,7 +1347,6 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
 #undef GSPH_INTERACT
 #undef GSPH_PAIRS
 #undef GSPH_PAIR_ARGS
-#undef GSPH_NL_ARGS
     return cudaGetLastError();
 }
 

@@ -80,7 +80,8 @@ __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const u
                                                  float *__restrict__ zf, uint32_t *__restrict__ qx,
                                                  uint32_t *__restrict__ qy, uint32_t *__restrict__ qz,
                                                  double *__restrict__ hs, float *__restrict__ hsf,
-                                                 const RecF *__restrict__ rec_in, int *__restrict__ err) {
+                                                 const RecF *__restrict__ rec_in, float4 *__restrict__ posf,
+                                                 int *__restrict__ err) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     uint32_t k = skey[s];
@@ -113,6 +114,9 @@ __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const u
         cxs[s] = (float)(k % (uint32_t)P.dims[0]);
     } else {
         cxs[s] = -1.0e9f;
+    }
+    if (!SPLIT && posf) {   // FP64 path: the FP32 bucket-relative positions of the neighbour-list build
+        posf[s] = pos_split(P, k, x, y, z, A.f[FW][o]);
     }
     if (SPLIT && rec_in) {   // the record the previous step's integration wrote from the same state
         ((float4 *)pos_out)[s] = pos_split(P, k, x, y, z, A.f[FW][o]);
@@ -150,15 +154,15 @@ cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint
                            const State &A, double *xs, double *ys, double *zs, uint8_t *lab_s, uint8_t *mat_s,
                            uint32_t *id_s, uint2 *cellr, float *cxs, void *pos, void *rec, float *xf, float *yf,
                            float *zf, uint32_t *qx, uint32_t *qy, uint32_t *qz, double *hs, float *hsf,
-                           const void *rec_in, int *err, cudaStream_t s) {
+                           const void *rec_in, float4 *posf, int *err, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     unsigned g = (unsigned)((n + 255) / 256);
     if (split)
         k_reorder<true><<<g, 256, 0, s>>>(P, n, skey, perm, A, xs, ys, zs, lab_s, mat_s, id_s, cellr, cxs, pos, rec,
-                                          xf, yf, zf, qx, qy, qz, hs, hsf, (const RecF *)rec_in, err);
+                                          xf, yf, zf, qx, qy, qz, hs, hsf, (const RecF *)rec_in, nullptr, err);
     else
         k_reorder<false><<<g, 256, 0, s>>>(P, n, skey, perm, A, xs, ys, zs, lab_s, mat_s, id_s, cellr, cxs, pos, rec,
-                                           xf, yf, zf, qx, qy, qz, hs, hsf, nullptr, err);
+                                           xf, yf, zf, qx, qy, qz, hs, hsf, nullptr, posf, err);
     return cudaGetLastError();
 }
 
