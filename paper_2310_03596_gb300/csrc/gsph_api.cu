@@ -406,6 +406,7 @@ static void fill_params(const gsph_config &c, DevParams &P) {
     P.K_labels = c.K;
     P.f_cell = (float)P.cell;
     P.f_inv_cell = (float)(1.0 / P.cell);
+    for (int a = 0; a < 3; ++a) P.f_lo[a] = (float)P.lo[a];
     P.variable_h = c.variable_h;
     P.f_vlo = (float)(1.0 - kVarBand);
     P.f_vhi = (float)(1.0 + kVarBand);

@@ -41,6 +41,7 @@ struct DevParams {
     // FP32 copies for the split path
     float f_cell, f_inv_h, f_kdw, f_R2lo, f_R2hi;
     float f_inv_cell;        // FP32 rounding of the FP64 reciprocal of the bucket side
+    float f_lo[3];           // FP32 roundings of the grid's lower corner (the hash's fast path)
     float f_rho0[kMaxMat], f_K[kMaxMat], f_G[kMaxMat], f_Mmod[kMaxMat];
     // FP32 roundings for the time step's signal-speed bounds: c0, s - 1, gamma0, 4G/3
     float f_c0[kMaxMat], f_sm1[kMaxMat], f_g0[kMaxMat], f_G43[kMaxMat];
@@ -127,24 +128,39 @@ __device__ __forceinline__ int bucket_coord(double x, double lo, double cell, in
     return (int)t;
 }
 
-// bucket_coord without the FP64 division in the common case. The FP32 quotient tf of the FP32 rounding
-// of d = x - lo by the FP32 reciprocal carries three FP32 roundings, so it lies within 3.01 * 2^-24 |t|
-// of the exact d / cell, and the correctly rounded FP64 quotient t within another 2^-53 |t|. When tf
-// is farther than 2^-22 (|tf| + 1) from every integer, t lies strictly between the same two integers
-// and floor(tf) = floor(t). Otherwise (near a bucket face, NaN, infinities, differences beyond the
-// FP32 range or below its normal range, a reciprocal that is not a normal FP32 number - passed as NaN)
-// the FP64 division decides.
-__device__ __forceinline__ int bucket_coord_fast(double x, double lo, double cell, float inv_cell, int dim) {
-    const double d = __dsub_rn(x, lo);
-    const float df = __double2float_rn(d);
-    const float tf = __fmul_rn(df, inv_cell);
-    const float fl = floorf(tf);
-    const float fr = __fsub_rn(tf, fl);   // exact
-    const float eps = __fmul_rn(0x1p-22f, __fadd_rn(fabsf(tf), 1.0f));
-    if (fr > eps && fr < __fsub_rn(1.0f, eps) && fabsf(df) >= 0x1p-126f) {
-        if (fl < 0.0f) return -1;
-        if (fl >= (float)dim) return dim;
-        return (int)fl;
+// FP32 value of x with the FP64 significand truncated (|x - f| < 2^-23 |x|), formed with integer
+// operations from the bits; false when x is zero, infinite, NaN or outside the FP32 normal range.
+__device__ __forceinline__ bool trunc_to_f32(double x, float &f) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    if (e < 1023 - 126 || e > 1023 + 127) return false;
+    f = __uint_as_float((hi & 0x80000000u) | ((unsigned)(e - 896) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+    return true;
+}
+
+// bucket_coord without an FP64 operation in the common case. With xt the truncated FP32 value of x
+// (below 2^-23 |x| away), lof the FP32 rounding of lo (2^-24 |lo|), and three FP32 roundings (the
+// difference, the reciprocal 1/cell and the product), the FP32 quotient tf lies within
+// 2^-23 |x| / cell + 2^-24 |lo| / cell + 3.01 * 2^-24 |tf| of the exact (x - lo) / cell, and the
+// correctly rounded FP64 quotient t within another 2^-52 |t|. When tf is farther than
+// 2^-22 (|tf| + 1 + (|xt| + |lof|) / cell) from every integer, t lies strictly between the same two
+// integers and floor(tf) = floor(t). Otherwise (near a bucket face, x zero, NaN, infinite or beyond the
+// FP32 normal range, a difference below that range, a reciprocal that is not a normal FP32 number -
+// passed as NaN) the FP64 division decides.
+__device__ __forceinline__ int bucket_coord_fast(double x, double lo, float lof, double cell, float inv_cell, int dim) {
+    float xt;
+    if (trunc_to_f32(x, xt)) {
+        const float df = __fsub_rn(xt, lof);
+        const float tf = __fmul_rn(df, inv_cell);
+        const float fl = floorf(tf);
+        const float fr = __fsub_rn(tf, fl);   // exact
+        const float span = __fmul_rn(__fadd_rn(fabsf(xt), fabsf(lof)), inv_cell);
+        const float eps = __fmul_rn(0x1p-22f, __fadd_rn(__fadd_rn(fabsf(tf), 1.0f), span));
+        if (fr > eps && fr < __fsub_rn(1.0f, eps) && fabsf(df) >= 0x1p-126f) {
+            if (fl < 0.0f) return -1;
+            if (fl >= (float)dim) return dim;
+            return (int)fl;
+        }
     }
     return bucket_coord(x, lo, cell, dim);
 }
@@ -154,9 +170,9 @@ __device__ __forceinline__ int bucket_coord_signed(double x, double lo, double c
 }
 
 __device__ __forceinline__ uint32_t hash_of(const DevParams &P, double x, double y, double z) {
-    int cx = bucket_coord_fast(x, P.lo[0], P.cell, P.f_inv_cell, P.dims[0]);
-    int cy = bucket_coord_fast(y, P.lo[1], P.cell, P.f_inv_cell, P.dims[1]);
-    int cz = bucket_coord_fast(z, P.lo[2], P.cell, P.f_inv_cell, P.dims[2]);
+    int cx = bucket_coord_fast(x, P.lo[0], P.f_lo[0], P.cell, P.f_inv_cell, P.dims[0]);
+    int cy = bucket_coord_fast(y, P.lo[1], P.f_lo[1], P.cell, P.f_inv_cell, P.dims[1]);
+    int cz = bucket_coord_fast(z, P.lo[2], P.f_lo[2], P.cell, P.f_inv_cell, P.dims[2]);
     if (cx < 0 || cy < 0 || cz < 0 || cx >= P.dims[0] || cy >= P.dims[1] || cz >= P.dims[2]) return P.ncell;
     return (uint32_t)cx + (uint32_t)P.dims[0] * ((uint32_t)cy + (uint32_t)P.dims[1] * (uint32_t)cz);
 }
