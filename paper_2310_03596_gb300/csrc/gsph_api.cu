@@ -431,7 +431,7 @@ static void fill_params(const gsph_config &c, DevParams &P) {
 
 static int64_t swap_pass_launches(const DevParams &P) {
     (void)P;
-    return 4;   // sums, pair geometry, speculative counts, the cooperative pair loop
+    return 3;   // sums, speculative counts (with the pair geometries), the cooperative pair loop
 }
 
 static int key_bits(uint32_t ncell) {

@@ -1,7 +1,8 @@
 // k_swap.cu - the communication-load-balancing heuristic (Sec. III.A, III.B) on K virtual labels.
 //
-// One swap pass is three streaming kernels (the fixed-point sums, the pair geometries, the speculative
-// counts) and one cooperative kernel (all blocks resident) for the sequential pair loop, whose phases are
+// One swap pass is two streaming kernels (the fixed-point sums; the speculative counts, each block
+// forming the pass-start pair geometries itself) and one cooperative kernel (all blocks resident) for the
+// sequential pair loop, whose phases are
 // separated by a bounded grid barrier; a barrier that does not complete within about a second records a
 // timeout in the error word and the pass returns. For each particle type (one pass over all particles when the scene
 // has one material) and each label pair (a, b) in lexicographic order:
@@ -62,7 +63,6 @@ struct SwapScratch {
     unsigned long long fp64;              // balancing hashes the FP32 bound left to the FP64 sequence
     unsigned int bar_count;
     unsigned int bar_gen;
-    float spec[SW_MAXCOMBO][7];            // pass-start geometry of every (type, label pair): SideF
 };
 
 // Fixed-point Cg per axis: q = nearest integer (ties to even) to (x - lo) s, s = 2^32 / L, clamped to
@@ -319,24 +319,6 @@ __global__ void __launch_bounds__(SW_THREADS) k_swap_sums(int64_t n, int nmat, c
     }
 }
 
-// Pass-start geometry of every (type, label pair) from the sums (one block).
-__global__ void __launch_bounds__(SW_THREADS) k_swap_geom(QuantParams Q, double alpha, int K, int nmat,
-                                                          SwapScratch *__restrict__ S) {
-    const bool multi = nmat > 1;
-    const int npairs = K * (K - 1) / 2, ncombo = (multi ? nmat : 1) * npairs;
-    for (int q = threadIdx.x; q < ncombo; q += SW_THREADS) {
-        const int T = q / npairs;
-        int a = 0, rem = q % npairs;
-        while (rem >= K - 1 - a) { rem -= K - 1 - a; ++a; }
-        Side g;
-        SideF f;
-        if (combo_geometry(S, Q, alpha, multi, multi ? T : kMaxMat, a, a + 1 + rem, g)) f = g.f;
-        else f.scale = -1.0f;
-        float *o = S->spec[q];
-        o[0] = f.M[0]; o[1] = f.M[1]; o[2] = f.M[2]; o[3] = f.u[0]; o[4] = f.u[1]; o[5] = f.u[2]; o[6] = f.scale;
-    }
-}
-
 // The balancing hash of one particle by the FP64 sequence: the pair's FP64 geometry from the sums, the
 // direction flipped for a particle of label b.
 __device__ __forceinline__ int spec_hash64(const SwapScratch *S, const QuantParams &Q, double alpha, bool multi, int T,
@@ -364,10 +346,16 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_swap_spec(int64_t n, QuantPar
     const int npairs = K * (K - 1) / 2, ncombo = (multi ? nmat : 1) * npairs;
     const int64_t gstride = (int64_t)gridDim.x * SW_THREADS;
     const bool seg = K >= 8;
+    // the pass-start geometry of every (type, label pair) from the sums, formed by each block (a few FP64
+    // operations per pair) rather than by a separate one-block kernel
     for (int q = threadIdx.x; q < ncombo; q += SW_THREADS) {
-        const float *g = S->spec[q];
+        const int T = q / npairs;
+        int a = 0, rem = q % npairs;
+        while (rem >= K - 1 - a) { rem -= K - 1 - a; ++a; }
+        Side g;
         SideF f;
-        f.M[0] = g[0]; f.M[1] = g[1]; f.M[2] = g[2]; f.u[0] = g[3]; f.u[1] = g[4]; f.u[2] = g[5]; f.scale = g[6];
+        if (combo_geometry(S, Q, alpha, multi, multi ? T : kMaxMat, a, a + 1 + rem, g)) f = g.f;
+        else f.scale = -1.0f;
         spec[q] = f;
         scnt[2 * q] = 0u;
         scnt[2 * q + 1] = 0u;
@@ -890,7 +878,6 @@ cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const SwapPos &pos, 
     const int64_t want = (n + SW_THREADS - 1) / SW_THREADS;
     const unsigned sgrid = (unsigned)(want < 2 * (int64_t)grid ? want : 2 * (int64_t)grid);
     k_swap_sums<<<sgrid, SW_THREADS, 0, s>>>(n, nmat, ps, lab, mat, S);
-    k_swap_geom<<<1, SW_THREADS, 0, s>>>(Q, alpha, K, nmat, S);
     k_swap_spec<<<sgrid, SW_THREADS, 0, s>>>(n, Q, alpha, K, nmat, ps, lab, mat, S, pairs, sidx);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
