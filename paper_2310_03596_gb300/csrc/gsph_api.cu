@@ -18,7 +18,7 @@ cudaError_t launch_hash(const DevParams &P, int64_t n, const double *x, const do
                         uint32_t *key, uint32_t *val, unsigned long long *garbage, cudaStream_t s);
 cudaError_t launch_hash_hist(const DevParams &P, int64_t n, const double *x, const double *y, const double *z,
                              uint32_t *key, uint32_t *val, unsigned long long *garbage, uint32_t *hist, int bits,
-                             cudaStream_t s);
+                             uint2 *zero8, int64_t nzero8, uint32_t *zero4, int64_t nzero4, cudaStream_t s);
 // k_reorder_comm.cu
 cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const uint32_t *perm,
                            const State &A, double *xs, double *ys, double *zs, uint8_t *lab_s, uint8_t *mat_s,
@@ -60,7 +60,7 @@ cudaError_t launch_round_positions(const DevParams &P, int64_t n, const double *
                                    cudaStream_t s);
 cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const SwapPos &pos, uint8_t *lab, const uint8_t *mat,
                              const uint32_t *id, void *scratch, uint16_t *bh, uint32_t *sidx, int *err, int grid,
-                             unsigned spin_limit, unsigned extra_blocks, cudaStream_t s);
+                             unsigned spin_limit, unsigned extra_blocks, bool scratch_clear, cudaStream_t s);
 int swap_grid_blocks();
 unsigned long long *swap_moved_ptr(void *scratch);
 // k_adjoint.cu
@@ -459,12 +459,17 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s, bool settle = true)
         c->dt_dirty = false;
         c->launches += 2;
     }
+    const bool do_swap = P.K_labels > 1 && c->cfg.swap_period > 0 && (c->step % c->cfg.swap_period) == 0;
     rec_event(c, PH_START, s);
     // a. bucket hash and the radix sort by hash (Sec. I)
     GSPH_CK(cudaMemsetAsync(c->garbage, 0, sizeof(unsigned long long), s));
-    // (the hash writes the first sort pass's tile histogram as well)
+    // (the hash writes the first sort pass's tile histogram as well, and clears the bucket ranges and, on a
+    // swap step, the swap pass's sums, so that the kernels from the hash to the swap pass follow one another
+    // as programmatic dependent launches with no clearing between them)
+    const int64_t swap_words = do_swap ? (int64_t)(swap_scratch_bytes(P.K_labels, P.nmat) / 4) : 0;
     GSPH_CK(launch_hash_hist(P, n, c->A.f[FX], c->A.f[FY], c->A.f[FZ], c->key0, c->val0, c->garbage, c->hist,
-                             key_bits(P.ncell), s));
+                             key_bits(P.ncell), c->cellr, (int64_t)P.ncell, (uint32_t *)c->swap_scratch, swap_words,
+                             s));
     bool alt = false;
     GSPH_CK(radix_sort_pairs(c->key0, c->val0, c->key1, c->val1, c->hist, c->tot, n, key_bits(P.ncell), s, &alt,
                              true));
@@ -473,8 +478,6 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s, bool settle = true)
     c->launches += 3 * radix_passes(key_bits(P.ncell));
     rec_event(c, PH_SORT, s);
     // sorted view, bucket ranges, interaction records
-    const bool do_swap = P.K_labels > 1 && c->cfg.swap_period > 0 && (c->step % c->cfg.swap_period) == 0;
-    GSPH_CK(cudaMemsetAsync(c->cellr, 0, (size_t)P.ncell * sizeof(uint2), s));
     GSPH_CK(launch_reorder(c->split, P, n, c->skey, c->perm, c->A, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s,
                            c->cellr, c->cxs, c->pos, c->rec, do_swap ? c->xf : nullptr, c->yf, c->zf, c->qx, c->qy,
                            c->qz, c->hs, c->hsf, c->rec_next_ok ? c->rec_next : nullptr, c->posf, c->err, s));
@@ -485,7 +488,7 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s, bool settle = true)
     if (do_swap) {
         const SwapPos sp{c->xf, c->yf, c->zf, c->xs, c->ys, c->zs, c->qx, c->qy, c->qz};
         GSPH_CK(launch_swap_pass(P, n, sp, c->lab_s, c->mat_s, c->id_s, c->swap_scratch, c->bh, c->sidx, c->err,
-                                 c->swap_grid, c->wait_spin, c->wait_extra, s));
+                                 c->swap_grid, c->wait_spin, c->wait_extra, true, s));
         ++c->swap_passes;
         c->launches += swap_pass_launches(P);
     }
@@ -823,7 +826,7 @@ gsph_status gsph_swap_now(gsph_ctx *c, void *stream) {
                                    c->qz, s));
     const SwapPos sp{c->xf, c->yf, c->zf, c->A.f[FX], c->A.f[FY], c->A.f[FZ], c->qx, c->qy, c->qz};
     GSPH_CK(launch_swap_pass(c->P, c->n, sp, c->A.label, c->A.mat, c->A.id, c->swap_scratch, c->bh, c->sidx, c->err,
-                             c->swap_grid, c->wait_spin, c->wait_extra, s));
+                             c->swap_grid, c->wait_spin, c->wait_extra, false, s));
     ++c->swap_passes;
     c->launches += 1 + swap_pass_launches(c->P);
     return GSPH_OK;

@@ -407,6 +407,32 @@ struct DtArgs {
     uint32_t cap;     // list capacity; a step that lists more evaluates every particle in FP64 instead
 };
 
+// ---------------------------------------------------------------------------------------------
+// Programmatic dependent launch: a chain of kernels on one stream whose successors are launched with
+// pdl_launch may have a successor's blocks scheduled while its predecessor drains, which hides the
+// launch latency between short kernels. Every kernel launched with pdl_launch calls pdl_wait() first,
+// in every block and before any access to device memory: it returns once the previous kernel on the
+// stream has completed and its writes are visible (at once for a normal launch), so each kernel of the
+// chain completes after everything before it. pdl_release() then allows the next kernel's launch.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -82,6 +82,8 @@ __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const u
                                                  double *__restrict__ hs, float *__restrict__ hsf,
                                                  const RecF *__restrict__ rec_in, float4 *__restrict__ posf,
                                                  int *__restrict__ err) {
+    pdl_wait();      // launched after the sort as a programmatic dependent launch
+    pdl_release();
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     uint32_t k = skey[s];
@@ -157,13 +159,13 @@ cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint
                            const void *rec_in, float4 *posf, int *err, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     unsigned g = (unsigned)((n + 255) / 256);
+    const uint32_t *key = skey, *pm = perm;
     if (split)
-        k_reorder<true><<<g, 256, 0, s>>>(P, n, skey, perm, A, xs, ys, zs, lab_s, mat_s, id_s, cellr, cxs, pos, rec,
-                                          xf, yf, zf, qx, qy, qz, hs, hsf, (const RecF *)rec_in, nullptr, err);
-    else
-        k_reorder<false><<<g, 256, 0, s>>>(P, n, skey, perm, A, xs, ys, zs, lab_s, mat_s, id_s, cellr, cxs, pos, rec,
-                                           xf, yf, zf, qx, qy, qz, hs, hsf, nullptr, posf, err);
-    return cudaGetLastError();
+        return pdl_launch(k_reorder<true>, dim3(g), dim3(256), s, P, n, key, pm, A, xs, ys, zs, lab_s, mat_s, id_s,
+                          cellr, cxs, pos, rec, xf, yf, zf, qx, qy, qz, hs, hsf, (const RecF *)rec_in,
+                          (float4 *)nullptr, err);
+    return pdl_launch(k_reorder<false>, dim3(g), dim3(256), s, P, n, key, pm, A, xs, ys, zs, lab_s, mat_s, id_s,
+                      cellr, cxs, pos, rec, xf, yf, zf, qx, qy, qz, hs, hsf, (const RecF *)nullptr, posf, err);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -7,7 +7,10 @@
 //   k_rs_scatter reloads the tile, ranks each key among equal digits in tile order (warp match_any,
 //                per-warp counters, cross-warp prefix), scatters keys and values.
 // The ranking follows tile order, so every pass is stable and the sort is stable overall. In a step the
-// bucket hash (k_hash_hist) builds the first pass's tile histogram as it writes the keys.
+// bucket hash (k_hash_hist) builds the first pass's tile histogram as it writes the keys. The launches
+// after the hash are programmatic dependent launches (pdl_launch): each kernel's blocks may be scheduled
+// while its predecessor drains and wait for it in pdl_wait(), which hides the launch gaps of these
+// short kernels.
 // Bytes per key per pass: 4 (hist) + 8 read + 8 written (scatter) + 2*4*bins/2048 (counts).
 #include <mutex>
 
@@ -31,6 +34,8 @@ __device__ __forceinline__ int64_t rs_item(int64_t tile_base, int w, int r, int 
 template <int DIG>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t *__restrict__ keys, int64_t n, int shift,
                                                         uint32_t dmask, uint32_t *__restrict__ hist, int nblk) {
+    pdl_wait();
+    pdl_release();
     constexpr int BINS = 1 << DIG;
     __shared__ uint32_t sh[BINS];
     for (int i = threadIdx.x; i < BINS; i += RS_THREADS) sh[i] = 0;
@@ -79,6 +84,8 @@ __device__ __forceinline__ uint32_t block_excl_scan_1024(uint32_t v, uint32_t *w
 
 __global__ void __launch_bounds__(1024) k_rs_rowscan(uint32_t *__restrict__ hist, int nblk,
                                                      uint32_t *__restrict__ tot) {
+    pdl_wait();
+    pdl_release();
     __shared__ uint32_t warp_tmp[32];
     uint32_t *row = hist + (size_t)blockIdx.x * nblk;
     uint32_t carry = 0;
@@ -100,6 +107,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *__res
                                                            uint32_t *__restrict__ vout, int64_t n, int shift,
                                                            uint32_t dmask, const uint32_t *__restrict__ hist,
                                                            const uint32_t *__restrict__ tot, int nblk) {
+    pdl_wait();
+    pdl_release();
     constexpr int BINS = 1 << DIG;
     constexpr int DPT = BINS / RS_THREADS;   // digit values per thread in the per-digit phases
     static_assert(DPT >= 1 && BINS % RS_THREADS == 0, "digit width");
@@ -187,10 +196,19 @@ __global__ void __launch_bounds__(RS_THREADS) k_hash_hist(DevParams P, int64_t n
                                                           const double *__restrict__ y, const double *__restrict__ z,
                                                           uint32_t *__restrict__ key, uint32_t *__restrict__ val,
                                                           unsigned long long *__restrict__ garbage, uint32_t dmask,
-                                                          uint32_t *__restrict__ hist, int nblk) {
+                                                          uint32_t *__restrict__ hist, int nblk,
+                                                          uint2 *__restrict__ zero8, int64_t nzero8,
+                                                          uint32_t *__restrict__ zero4, int64_t nzero4) {
+    pdl_wait();
+    pdl_release();
     constexpr int BINS = 1 << DIG;
     __shared__ uint32_t sh[BINS];
     for (int i = threadIdx.x; i < BINS; i += RS_THREADS) sh[i] = 0;
+    // buffers that later kernels of the step fill (the bucket ranges, the swap pass's sums) cleared here,
+    // so that no separate clearing breaks the launch chain; nothing reads them before the sort ends
+    const int64_t gstride = (int64_t)gridDim.x * RS_THREADS;
+    for (int64_t i = (int64_t)blockIdx.x * RS_THREADS + threadIdx.x; i < nzero8; i += gstride) zero8[i] = make_uint2(0u, 0u);
+    for (int64_t i = (int64_t)blockIdx.x * RS_THREADS + threadIdx.x; i < nzero4; i += gstride) zero4[i] = 0u;
     __syncthreads();
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int64_t base = (int64_t)blockIdx.x * RS_TILE;
@@ -251,19 +269,30 @@ cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t 
     const int passes = radix_passes(bits);
     const int dig = (bits + passes - 1) / passes;   // <= 9
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
+    cudaError_t e = cudaSuccess;
     for (int p = 0; p < passes; ++p) {
         const int shift = dig * p;
         const int width = bits - shift < dig ? bits - shift : dig;
         const uint32_t dmask = (1u << width) - 1u;
         const bool hist_done = first_hist && p == 0;
         if (dig > 8) {
-            if (!hist_done) k_rs_hist<9><<<nblk, RS_THREADS, 0, s>>>(ki, n, shift, dmask, hist, nblk);
-            k_rs_rowscan<<<1 << 9, 1024, 0, s>>>(hist, nblk, tot);
-            k_rs_scatter<9><<<nblk, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, dmask, hist, tot, nblk);
+            if (!hist_done && (e = pdl_launch(k_rs_hist<9>, dim3(nblk), dim3(RS_THREADS), s, (const uint32_t *)ki, n,
+                                              shift, dmask, hist, nblk)) != cudaSuccess)
+                return e;
+            if ((e = pdl_launch(k_rs_rowscan, dim3(1u << 9), dim3(1024), s, hist, nblk, tot)) != cudaSuccess) return e;
+            if ((e = pdl_launch(k_rs_scatter<9>, dim3(nblk), dim3(RS_THREADS), s, (const uint32_t *)ki,
+                                (const uint32_t *)vi, ko, vo, n, shift, dmask, (const uint32_t *)hist,
+                                (const uint32_t *)tot, nblk)) != cudaSuccess)
+                return e;
         } else {
-            if (!hist_done) k_rs_hist<8><<<nblk, RS_THREADS, 0, s>>>(ki, n, shift, dmask, hist, nblk);
-            k_rs_rowscan<<<1 << 8, 1024, 0, s>>>(hist, nblk, tot);
-            k_rs_scatter<8><<<nblk, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, dmask, hist, tot, nblk);
+            if (!hist_done && (e = pdl_launch(k_rs_hist<8>, dim3(nblk), dim3(RS_THREADS), s, (const uint32_t *)ki, n,
+                                              shift, dmask, hist, nblk)) != cudaSuccess)
+                return e;
+            if ((e = pdl_launch(k_rs_rowscan, dim3(1u << 8), dim3(1024), s, hist, nblk, tot)) != cudaSuccess) return e;
+            if ((e = pdl_launch(k_rs_scatter<8>, dim3(nblk), dim3(RS_THREADS), s, (const uint32_t *)ki,
+                                (const uint32_t *)vi, ko, vo, n, shift, dmask, (const uint32_t *)hist,
+                                (const uint32_t *)tot, nblk)) != cudaSuccess)
+                return e;
         }
         uint32_t *t = ki; ki = ko; ko = t;
         t = vi; vi = vo; vo = t;
@@ -273,18 +302,23 @@ cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t 
 }
 
 // The hash with the first pass's histogram of a sort by the low `bits` bits (radix_sort_pairs with
-// first_hist = true follows).
+// first_hist = true follows). It also clears zero8[0, nzero8) and zero4[0, nzero4) (either may be empty),
+// buffers that kernels after the sort fill.
 cudaError_t launch_hash_hist(const DevParams &P, int64_t n, const double *x, const double *y, const double *z,
                              uint32_t *key, uint32_t *val, unsigned long long *garbage, uint32_t *hist, int bits,
-                             cudaStream_t s) {
+                             uint2 *zero8, int64_t nzero8, uint32_t *zero4, int64_t nzero4, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const int nblk = rs_nblk(n);
     const int passes = radix_passes(bits);
     const int dig = (bits + passes - 1) / passes;
     const int width = bits < dig ? bits : dig;
     const uint32_t dmask = (1u << width) - 1u;
-    if (dig > 8) k_hash_hist<9><<<nblk, RS_THREADS, 0, s>>>(P, n, x, y, z, key, val, garbage, dmask, hist, nblk);
-    else k_hash_hist<8><<<nblk, RS_THREADS, 0, s>>>(P, n, x, y, z, key, val, garbage, dmask, hist, nblk);
+    if (dig > 8)
+        k_hash_hist<9><<<nblk, RS_THREADS, 0, s>>>(P, n, x, y, z, key, val, garbage, dmask, hist, nblk, zero8, nzero8,
+                                                   zero4, nzero4);
+    else
+        k_hash_hist<8><<<nblk, RS_THREADS, 0, s>>>(P, n, x, y, z, key, val, garbage, dmask, hist, nblk, zero8, nzero8,
+                                                   zero4, nzero4);
     return cudaGetLastError();
 }
 

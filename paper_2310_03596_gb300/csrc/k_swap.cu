@@ -290,6 +290,8 @@ __device__ bool grid_barrier(SwapScratch *S, unsigned nblocks, int *err, const W
 __global__ void __launch_bounds__(SW_THREADS) k_swap_sums(int64_t n, int nmat, const SwapPos pos,
                                                           const uint8_t *__restrict__ lab,
                                                           const uint8_t *__restrict__ mat, SwapScratch *__restrict__ S) {
+    pdl_wait();      // launched after the reorder as a programmatic dependent launch
+    pdl_release();
     __shared__ long long shs[kMaxLabel][SW_NT][4];
     const bool multi = nmat > 1;
     const int64_t gstride = (int64_t)gridDim.x * SW_THREADS;
@@ -339,6 +341,7 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_swap_spec(int64_t n, QuantPar
                                                           const SwapPos pos, const uint8_t *__restrict__ lab,
                                                           const uint8_t *__restrict__ mat, SwapScratch *__restrict__ S,
                                                           SwapPair *__restrict__ pairs, uint32_t *__restrict__ sidx) {
+    pdl_wait();      // launched after the sums as a programmatic dependent launch
     __shared__ SideF spec[SW_MAXCOMBO];
     __shared__ uint32_t scnt[2 * SW_MAXCOMBO];
     __shared__ long long loff_sh[kMaxLabel + 1];
@@ -855,16 +858,18 @@ int swap_grid_blocks() {
 }
 
 // pos: the particles' FP32 and FP64 positions and fixed-point coordinates (launch_round_positions, or the
-// reorder). scratch: swap_scratch_bytes() device bytes; bh: n uint16; sidx: 2n uint32 (label segments and
-// moved lists); grid from swap_grid_blocks().
+// reorder). scratch: swap_scratch_bytes() device bytes, cleared here unless scratch_clear says that an
+// earlier kernel on the stream has cleared it; bh: n uint16; sidx: 2n uint32 (label segments and moved
+// lists); grid from swap_grid_blocks(). The sums and the speculative pass are programmatic dependent
+// launches.
 cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const SwapPos &pos, uint8_t *lab, const uint8_t *mat,
                              const uint32_t *id, void *scratch, uint16_t *bh, uint32_t *sidx, int *err, int grid,
-                             unsigned spin_limit, unsigned extra_blocks, cudaStream_t s) {
+                             unsigned spin_limit, unsigned extra_blocks, bool scratch_clear, cudaStream_t s) {
     if (n <= 0 || P.K_labels < 2) return cudaSuccess;
     if (grid < 1) return cudaErrorCooperativeLaunchTooLarge;
     const size_t bytes = swap_scratch_bytes(P.K_labels, P.nmat);
-    cudaError_t e = cudaMemsetAsync(scratch, 0, bytes, s);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (!scratch_clear && (e = cudaMemsetAsync(scratch, 0, bytes, s)) != cudaSuccess) return e;
     SwapScratch *S = (SwapScratch *)scratch;
     SwapPair *pairs = (SwapPair *)((char *)scratch + sizeof(SwapScratch));
     const int ntype = P.nmat > 1 ? P.nmat : 1;
@@ -877,10 +882,12 @@ cudaError_t launch_swap_pass(const DevParams &P, int64_t n, const SwapPos &pos, 
     // the streaming phases: two blocks per cooperative block, at most one thread per particle
     const int64_t want = (n + SW_THREADS - 1) / SW_THREADS;
     const unsigned sgrid = (unsigned)(want < 2 * (int64_t)grid ? want : 2 * (int64_t)grid);
-    k_swap_sums<<<sgrid, SW_THREADS, 0, s>>>(n, nmat, ps, lab, mat, S);
-    k_swap_spec<<<sgrid, SW_THREADS, 0, s>>>(n, Q, alpha, K, nmat, ps, lab, mat, S, pairs, sidx);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    const uint8_t *labc = lab;
+    if ((e = pdl_launch(k_swap_sums, dim3(sgrid), dim3(SW_THREADS), s, n, nmat, ps, labc, mat, S)) != cudaSuccess)
+        return e;
+    if ((e = pdl_launch(k_swap_spec, dim3(sgrid), dim3(SW_THREADS), s, n, Q, alpha, K, nmat, ps, labc, mat, S, pairs,
+                        sidx)) != cudaSuccess)
+        return e;
     WaitCfg wc{spin_limit > 0 ? spin_limit : (1u << 24), extra_blocks};
     void *args[] = {(void *)&n, (void *)&Q, (void *)&alpha, (void *)&K, (void *)&nmat, (void *)&ps, (void *)&lab,
                     (void *)&mat, (void *)&id, (void *)&bh, (void *)&S, (void *)&pairs, (void *)&tl, (void *)&sidx,
