@@ -270,6 +270,12 @@ gsph_status gsph_get_sizes(gsph_ctx *ctx, int64_t *n, int64_t *ncell);
 /* Per-phase CUDA-event timing: max_steps > 0 arms it for up to max_steps steps (resets the
  * totals), 0 disarms. gsph_get_timings synchronises and returns the totals so far. */
 gsph_status gsph_set_timing(gsph_ctx *ctx, int32_t max_steps);
+/* The same with a scope: pair_only = 0 times every phase (gsph_set_timing), pair_only = 1 records only
+ * the three events per step that bound the pair kernel (the ends of the two branches and of the step)
+ * instead of seven, so that the dominant kernel is timed with the least added work in the stream;
+ * gsph_get_timings then fills pair_ms and steps and leaves the other phases 0. Other values of
+ * pair_only: GSPH_INVALID_ARG. */
+gsph_status gsph_set_timing_ex(gsph_ctx *ctx, int32_t max_steps, int32_t pair_only);
 gsph_status gsph_get_timings(gsph_ctx *ctx, gsph_timings *out);
 
 /* Overrides the time step of the next gsph_step (the one after is again the CFL step). Used to replay

@@ -155,6 +155,7 @@ struct gsph_ctx {
     int64_t launches = 0;
     // timing
     int timing_max = 0, timing_used = 0;
+    bool timing_pair_only = false;   // only the events that bound the pair kernel are recorded
     std::vector<cudaEvent_t> ev;
 };
 
@@ -440,13 +441,20 @@ static int key_bits(uint32_t ncell) {
     return b;
 }
 
-static void rec_event(gsph_ctx *c, int phase, cudaStream_t s) {
-    if (c->timing_used < c->timing_max) cudaEventRecord(c->ev[(size_t)c->timing_used * PH_COUNT + phase], s);
+// Whether the step being enqueued records the event of `phase` (timing armed, and the phase in scope:
+// all phases, or with pair-only timing the ends of the two branches and of the step).
+static bool timed_phase(const gsph_ctx *c, int phase) {
+    if (c->timing_used >= c->timing_max) return false;
+    return !c->timing_pair_only || phase == PH_LIST || phase == PH_COMM || phase == PH_INTERACT;
 }
 
-// The event of `phase` in the step being enqueued when timing is armed (recorded by the callee), else null.
+static void rec_event(gsph_ctx *c, int phase, cudaStream_t s) {
+    if (timed_phase(c, phase)) cudaEventRecord(c->ev[(size_t)c->timing_used * PH_COUNT + phase], s);
+}
+
+// The event of `phase` in the step being enqueued when it is timed (recorded by the callee), else null.
 static cudaEvent_t phase_event(gsph_ctx *c, int phase) {
-    return c->timing_used < c->timing_max ? c->ev[(size_t)c->timing_used * PH_COUNT + phase] : nullptr;
+    return timed_phase(c, phase) ? c->ev[(size_t)c->timing_used * PH_COUNT + phase] : nullptr;
 }
 
 // One step. settle = false (a further step of the same gsph_step call follows) leaves the step's
@@ -964,14 +972,17 @@ gsph_status gsph_get_sizes(gsph_ctx *c, int64_t *n, int64_t *ncell) {
     return GSPH_OK;
 }
 
-gsph_status gsph_set_timing(gsph_ctx *c, int32_t max_steps) {
-    if (!c || max_steps < 0) return GSPH_INVALID_ARG;
+gsph_status gsph_set_timing(gsph_ctx *c, int32_t max_steps) { return gsph_set_timing_ex(c, max_steps, 0); }
+
+gsph_status gsph_set_timing_ex(gsph_ctx *c, int32_t max_steps, int32_t pair_only) {
+    if (!c || max_steps < 0 || (pair_only != 0 && pair_only != 1)) return GSPH_INVALID_ARG;
     GSPH_CK(cudaSetDevice(c->cfg.device));
     GSPH_CK(cudaDeviceSynchronize());
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     c->ev.clear();
     c->timing_max = 0;
     c->timing_used = 0;
+    c->timing_pair_only = pair_only != 0;
     if (max_steps == 0) return GSPH_OK;
     c->ev.resize((size_t)max_steps * PH_COUNT);
     for (auto &e : c->ev) GSPH_CK(cudaEventCreate(&e));
@@ -986,6 +997,13 @@ gsph_status gsph_get_timings(gsph_ctx *c, gsph_timings *out) {
     for (int k = 0; k < c->timing_used; ++k) {
         cudaEvent_t *e = &c->ev[(size_t)k * PH_COUNT];
         GSPH_CK(cudaEventSynchronize(e[PH_INTERACT]));
+        if (c->timing_pair_only) {   // from the end of the later branch to the end of the step
+            float a = 0.f, b = 0.f;
+            GSPH_CK(cudaEventElapsedTime(&a, e[PH_LIST], e[PH_INTERACT]));
+            GSPH_CK(cudaEventElapsedTime(&b, e[PH_COMM], e[PH_INTERACT]));
+            out->pair_ms += a < b ? a : b;
+            continue;
+        }
         float t[PH_COUNT] = {0};
         for (int p = 1; p <= PH_COMM; ++p) GSPH_CK(cudaEventElapsedTime(&t[p], e[p - 1], e[p]));
         // the two branches after the swap pass: communication hash on the second stream, the list build on

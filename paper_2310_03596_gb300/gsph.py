@@ -96,7 +96,8 @@ class Timings(C.Structure):
 
 EXPORTS = ["gsph_status_str", "gsph_create", "gsph_destroy", "gsph_set_particles", "gsph_put_field",
            "gsph_get_field", "gsph_step", "gsph_swap_now", "gsph_sync", "gsph_get_exchange_stats",
-           "gsph_get_conserved", "gsph_get_dt", "gsph_get_sizes", "gsph_set_timing", "gsph_get_timings",
+           "gsph_get_conserved", "gsph_get_dt", "gsph_get_sizes", "gsph_set_timing", "gsph_set_timing_ex",
+           "gsph_get_timings",
            "gsph_radix_sort_workspace", "gsph_radix_sort_pairs", "gsph_radix_sort_pairs_noalloc",
            "gsph_set_dt", "gsph_adjoint_step", "gsph_state_bytes", "gsph_save_state", "gsph_load_state",
            "gsph_adjoint", "gsph_set_wait_limit", "gsph_debug_fail_alloc"]
@@ -132,6 +133,7 @@ def load(path: str = LIB_PATH):
         L.gsph_get_dt.argtypes = [vp, vp, P(C.c_double)]
         L.gsph_get_sizes.argtypes = [vp, P(C.c_int64), P(C.c_int64)]
         L.gsph_set_timing.argtypes = [vp, C.c_int32]
+        L.gsph_set_timing_ex.argtypes = [vp, C.c_int32, C.c_int32]
         L.gsph_get_timings.argtypes = [vp, P(Timings)]
         L.gsph_radix_sort_workspace.argtypes = [C.c_int64, C.c_int32]
         L.gsph_radix_sort_workspace.restype = C.c_size_t
@@ -393,8 +395,10 @@ class Solver:
         check(self.L.gsph_adjoint(self.h, C.byref(a), g, _stream_handle(stream)), "gsph_adjoint")
         return J.value, (tuple(g[:]) if want_gradient else None), out
 
-    def set_timing(self, max_steps: int) -> None:
-        check(self.L.gsph_set_timing(self.h, int(max_steps)), "gsph_set_timing")
+    def set_timing(self, max_steps: int, pair_only: bool = False) -> None:
+        """Arms CUDA-event timing for up to max_steps steps: every phase, or (pair_only) only the events
+        that bound the pair kernel, the other phases then reading 0."""
+        check(self.L.gsph_set_timing_ex(self.h, int(max_steps), 1 if pair_only else 0), "gsph_set_timing_ex")
 
     def timings(self) -> dict:
         t = Timings()

@@ -54,3 +54,29 @@ def test_one_call_equals_n_calls_sixteen_labels_every_other_step():
 def test_one_call_equals_n_calls_two_pass_order():
     s = scenes.taylor_bar(dx=0.5e-3, K=4, swap_period=1)
     _same_after(s, gsph.FP32_SPLIT, 5, overlap=True)
+
+
+@pytest.mark.parametrize("overlap", [False, True])
+def test_timing_scopes_leave_the_state_alone(overlap):
+    """Phase events (every phase, or only those that bound the pair kernel) change no bit of the state;
+    the pair-only scope fills pair_ms alone, and its pair time agrees with the full scope's."""
+    s = scenes.taylor_bar(dx=0.5e-3, K=4, swap_period=1)
+    sols = {k: gsph.Solver.from_scene(s, overlap=overlap) for k in ("none", "all", "pair")}
+    try:
+        sols["all"].set_timing(6)
+        sols["pair"].set_timing(6, pair_only=True)
+        for sol in sols.values():
+            sol.step(6)
+            sol.sync()
+        for f in FIELDS:
+            assert np.array_equal(sols["none"].get(f), sols["all"].get(f)), f
+            assert np.array_equal(sols["none"].get(f), sols["pair"].get(f)), f
+        ta, tp = sols["all"].timings(), sols["pair"].timings()
+        assert ta["steps"] == tp["steps"] == 6
+        assert ta["hash_sort_ms"] > 0 and ta["nbr_list_ms"] > 0 and ta["pair_ms"] > 0
+        assert tp["pair_ms"] > 0
+        assert all(v == 0 for k, v in tp.items() if k.endswith("_ms") and k != "pair_ms")
+        assert 0.5 < tp["pair_ms"] / ta["pair_ms"] < 2.0
+    finally:
+        for sol in sols.values():
+            sol.close()
