@@ -24,7 +24,8 @@ cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint
                            const State &A, double *xs, double *ys, double *zs, uint8_t *lab_s, uint8_t *mat_s,
                            uint32_t *id_s, uint2 *cellr, float *cxs, void *pos, void *rec, float *xf, float *yf,
                            float *zf, uint32_t *qx, uint32_t *qy, uint32_t *qz, double *hs, float *hsf,
-                           const void *rec_in, float4 *posf, int *err, cudaStream_t s);
+                           const void *rec_in, float4 *posf, int *err, unsigned long long *garbage,
+                           cudaStream_t s);
 cudaError_t launch_comm(const DevParams &P, int64_t n, const uint32_t *skey, const uint8_t *lab_s, uint32_t *mask,
                         uint8_t *flag, uint32_t *comm, uint32_t *block_counts, unsigned long long *label_total,
                         uint32_t *blist, uint32_t *hidx, uint32_t *scan_part, int *launches, cudaStream_t s);
@@ -50,7 +51,7 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
 cudaError_t launch_nbr_list(const DevParams &P, int64_t n, const uint32_t *skey, const uint2 *cellr,
                             const float4 *pos_rel, const float *cxs, const double *xs, const double *ys,
                             const double *zs, int kmax, uint2 *list, uint32_t *cnt, const double *hs,
-                            const float *hsf, cudaStream_t s);
+                            const float *hsf, unsigned long long *cost_clear, cudaStream_t s);
 cudaError_t launch_refresh(bool split, const DevParams &P, int64_t n, const uint32_t *skey, const State &B,
                            void *pos, void *rec, cudaStream_t s);
 // k_swap.cu
@@ -470,12 +471,11 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s, bool settle = true)
     const bool do_swap = P.K_labels > 1 && c->cfg.swap_period > 0 && (c->step % c->cfg.swap_period) == 0;
     rec_event(c, PH_START, s);
     // a. bucket hash and the radix sort by hash (Sec. I)
-    GSPH_CK(cudaMemsetAsync(c->garbage, 0, sizeof(unsigned long long), s));
     // (the hash writes the first sort pass's tile histogram as well, and clears the bucket ranges and, on a
     // swap step, the swap pass's sums, so that the kernels from the hash to the swap pass follow one another
     // as programmatic dependent launches with no clearing between them)
     const int64_t swap_words = do_swap ? (int64_t)(swap_scratch_bytes(P.K_labels, P.nmat) / 4) : 0;
-    GSPH_CK(launch_hash_hist(P, n, c->A.f[FX], c->A.f[FY], c->A.f[FZ], c->key0, c->val0, c->garbage, c->hist,
+    GSPH_CK(launch_hash_hist(P, n, c->A.f[FX], c->A.f[FY], c->A.f[FZ], c->key0, c->val0, nullptr, c->hist,
                              key_bits(P.ncell), c->cellr, (int64_t)P.ncell, (uint32_t *)c->swap_scratch, swap_words,
                              s));
     bool alt = false;
@@ -488,7 +488,8 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s, bool settle = true)
     // sorted view, bucket ranges, interaction records
     GSPH_CK(launch_reorder(c->split, P, n, c->skey, c->perm, c->A, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s,
                            c->cellr, c->cxs, c->pos, c->rec, do_swap ? c->xf : nullptr, c->yf, c->zf, c->qx, c->qy,
-                           c->qz, c->hs, c->hsf, c->rec_next_ok ? c->rec_next : nullptr, c->posf, c->err, s));
+                           c->qz, c->hs, c->hsf, c->rec_next_ok ? c->rec_next : nullptr, c->posf, c->err,
+                           c->garbage, s));
     c->rec_next_ok = false;   // until this step's integration has rewritten them
     c->launches += 1;
     rec_event(c, PH_REORDER, s);
@@ -516,7 +517,7 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s, bool settle = true)
     GSPH_CK(cudaEventRecord(c->ev_join, sl));
     // f. neighbour lists of the step (real neighbours), then the join of the two branches
     GSPH_CK(launch_nbr_list(P, n, c->skey, c->cellr, c->split ? (const float4 *)c->pos : c->posf, c->cxs, c->xs,
-                            c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->hs, c->hsf, s));
+                            c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->hs, c->hsf, c->cost, s));
     c->launches += 1;
     rec_event(c, PH_LIST, s);
     GSPH_CK(cudaStreamWaitEvent(s, c->ev_join, 0));
@@ -525,7 +526,6 @@ static gsph_status enqueue_step(gsph_ctx *c, cudaStream_t s, bool settle = true)
         GSPH_CK(cudaStreamWaitEvent(s, c->ev_dt, 0));
         c->dt_pending = false;
     }
-    GSPH_CK(cudaMemsetAsync(c->cost, 0, (size_t)kMaxLabel * sizeof(unsigned long long), s));
     OverlapBufs ov{};
     if (c->cfg.overlap) {
         ov = OverlapBufs{c->flag, c->blist, c->label_off + P.K_labels, c->hidx, c->hpos, c->hrec, c->hcx, c->part,
@@ -585,9 +585,9 @@ static gsph_status enqueue_forward_pieces(gsph_ctx *c, cudaStream_t s) {
     GSPH_CK(cudaMemsetAsync(c->cellr, 0, (size_t)P.ncell * sizeof(uint2), s));
     GSPH_CK(launch_reorder(c->split, P, n, c->skey, c->perm, c->A, c->xs, c->ys, c->zs, c->lab_s, c->mat_s, c->id_s,
                            c->cellr, c->cxs, c->pos, c->rec, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                           nullptr, nullptr, nullptr, c->posf, c->err, s));
+                           nullptr, nullptr, nullptr, c->posf, c->err, nullptr, s));
     GSPH_CK(launch_nbr_list(P, n, c->skey, c->cellr, c->split ? (const float4 *)c->pos : c->posf, c->cxs, c->xs,
-                            c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->hs, c->hsf, s));
+                            c->ys, c->zs, kNbrMax, c->nbr, c->nbr_cnt, c->hs, c->hsf, nullptr, s));
     GSPH_CK(launch_interact(c->split, true, P, n, c->skey, c->cellr, c->pos, c->rec, c->cxs, c->xs, c->ys, c->zs,
                             kNbrMax, c->nbr, c->nbr_cnt, c->perm, c->A, c->B, nullptr, c->lab_s, c->mat_s, c->id_s,
                             c->dt, dt_args(c), c->pairs, c->cost, c->nreal, c->nimage, c->rates, nullptr, 0, nullptr,

@@ -381,7 +381,13 @@ __global__ void __launch_bounds__(NL_THREADS, 4) k_nbr_list(DevParams P, int64_t
                                                          const double *__restrict__ ys, const double *__restrict__ zs,
                                                          int kmax, uint2 *__restrict__ list,
                                                          uint32_t *__restrict__ cnt_out, const double *__restrict__ hs,
-                                                         const float *__restrict__ hsf) {
+                                                         const float *__restrict__ hsf,
+                                                         unsigned long long *__restrict__ cost_clear) {
+    pdl_wait();      // a programmatic dependent launch (its predecessor's writes are visible from here)
+    pdl_release();
+    // the step's per-label pair counters, which the pair kernel fills, cleared here rather than by a
+    // separate clearing before the pair kernel
+    if (cost_clear && blockIdx.x == 0 && threadIdx.x < kMaxLabel) cost_clear[threadIdx.x] = 0ull;
     // staged candidate (c, |c|^2) with c = (x in the group frame, y, z in the row frame), as four planes
     // (x, y, z, |c|^2) of NL_THREADS floats, so that one 16-byte load gives a coordinate of four candidates
     // and the tests run on packed pairs (variable h: a fifth plane of FP32 lengths)
@@ -1199,6 +1205,8 @@ __device__ __forceinline__ void pair_body(const PairArgs<SPLIT> &a, int64_t s, b
 // pass, 3 for the MUSCL flux pass (168 registers)
 template <bool SPLIT, bool DIAG, int MODE, bool VARH = false>
 __global__ void __launch_bounds__(PK_THREADS, SPLIT ? (MODE == PM_MUSCL ? 3 : (MODE == PM_GRAD ? 5 : 4)) : 2) k_pair(const PairArgs<SPLIT> a) {
+    pdl_wait();      // a programmatic dependent launch (its predecessor's writes are visible from here)
+    pdl_release();
     if (MODE == PM_BOUNDARY) {
         // one lane per boundary particle, warp-uniform strides over the boundary list
         const int64_t total = (int64_t)*a.btotal;
@@ -1268,16 +1276,14 @@ static PairArgs<SPLIT> pair_args(const DevParams &P, int64_t n, const uint32_t *
 cudaError_t launch_nbr_list(const DevParams &P, int64_t n, const uint32_t *skey, const uint2 *cellr,
                             const float4 *pos_rel, const float *cxs, const double *xs, const double *ys,
                             const double *zs, int kmax, uint2 *list, uint32_t *cnt, const double *hs,
-                            const float *hsf, cudaStream_t s) {
+                            const float *hsf, unsigned long long *cost_clear, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const unsigned gl = (unsigned)((n + NL_THREADS - 1) / NL_THREADS);
     if (P.variable_h != 0)
-        k_nbr_list<true><<<gl, NL_THREADS, 0, s>>>(P, n, skey, cellr, pos_rel, cxs, xs, ys, zs, kmax, list, cnt, hs,
-                                                   hsf);
-    else
-        k_nbr_list<false><<<gl, NL_THREADS, 0, s>>>(P, n, skey, cellr, pos_rel, cxs, xs, ys, zs, kmax, list, cnt, hs,
-                                                    hsf);
-    return cudaGetLastError();
+        return pdl_launch(k_nbr_list<true>, dim3(gl), dim3(NL_THREADS), s, P, n, skey, cellr, pos_rel, cxs, xs, ys, zs,
+                          kmax, list, cnt, hs, hsf, cost_clear);
+    return pdl_launch(k_nbr_list<false>, dim3(gl), dim3(NL_THREADS), s, P, n, skey, cellr, pos_rel, cxs, xs, ys, zs,
+                      kmax, list, cnt, hs, hsf, cost_clear);
 }
 
 cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n, const uint32_t *skey,
@@ -1300,11 +1306,11 @@ cudaError_t launch_interact(bool split, bool diag, const DevParams &P, int64_t n
         const auto pa = GSPH_PAIR_ARGS;                                                      \
         const unsigned g_ = MODE_ == PM_BOUNDARY ? ov->boundary_grid : gp;                  \
         if (varh) {                                                                         \
-            if (diag) k_pair<SP, true, MODE_, true><<<g_, PK_THREADS, 0, s>>>(pa);          \
-            else k_pair<SP, false, MODE_, true><<<g_, PK_THREADS, 0, s>>>(pa);              \
+            if (diag) pdl_launch(k_pair<SP, true, MODE_, true>, dim3(g_), dim3(PK_THREADS), s, pa);  \
+            else pdl_launch(k_pair<SP, false, MODE_, true>, dim3(g_), dim3(PK_THREADS), s, pa);      \
         } else {                                                                            \
-            if (diag) k_pair<SP, true, MODE_><<<g_, PK_THREADS, 0, s>>>(pa);                 \
-            else k_pair<SP, false, MODE_><<<g_, PK_THREADS, 0, s>>>(pa);                    \
+            if (diag) pdl_launch(k_pair<SP, true, MODE_>, dim3(g_), dim3(PK_THREADS), s, pa);         \
+            else pdl_launch(k_pair<SP, false, MODE_>, dim3(g_), dim3(PK_THREADS), s, pa);             \
         }                                                                                   \
     } while (0)
 #define GSPH_INTERACT                                                                       \

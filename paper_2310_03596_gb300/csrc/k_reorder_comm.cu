@@ -81,13 +81,17 @@ __global__ void __launch_bounds__(256) k_reorder(DevParams P, int64_t n, const u
                                                  uint32_t *__restrict__ qy, uint32_t *__restrict__ qz,
                                                  double *__restrict__ hs, float *__restrict__ hsf,
                                                  const RecF *__restrict__ rec_in, float4 *__restrict__ posf,
-                                                 int *__restrict__ err) {
+                                                 int *__restrict__ err, unsigned long long *__restrict__ garbage) {
     pdl_wait();      // launched after the sort as a programmatic dependent launch
     pdl_release();
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     uint32_t k = skey[s];
     uint32_t o = perm[s];
+    if (garbage) {   // particles outside the grid sort last (key ncell): their count from where they start
+        if (k >= P.ncell && (s == 0 || skey[s - 1] < P.ncell)) *garbage = (unsigned long long)(n - s);
+        if (s == n - 1 && k < P.ncell) *garbage = 0ull;
+    }
     if (hs) {   // variable h: the sorted smoothing lengths, FP64 and their FP32 roundings
         const double hh = A.h[o];
         hs[s] = hh;
@@ -156,16 +160,17 @@ cudaError_t launch_reorder(bool split, const DevParams &P, int64_t n, const uint
                            const State &A, double *xs, double *ys, double *zs, uint8_t *lab_s, uint8_t *mat_s,
                            uint32_t *id_s, uint2 *cellr, float *cxs, void *pos, void *rec, float *xf, float *yf,
                            float *zf, uint32_t *qx, uint32_t *qy, uint32_t *qz, double *hs, float *hsf,
-                           const void *rec_in, float4 *posf, int *err, cudaStream_t s) {
+                           const void *rec_in, float4 *posf, int *err, unsigned long long *garbage,
+                           cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     unsigned g = (unsigned)((n + 255) / 256);
     const uint32_t *key = skey, *pm = perm;
     if (split)
         return pdl_launch(k_reorder<true>, dim3(g), dim3(256), s, P, n, key, pm, A, xs, ys, zs, lab_s, mat_s, id_s,
                           cellr, cxs, pos, rec, xf, yf, zf, qx, qy, qz, hs, hsf, (const RecF *)rec_in,
-                          (float4 *)nullptr, err);
+                          (float4 *)nullptr, err, garbage);
     return pdl_launch(k_reorder<false>, dim3(g), dim3(256), s, P, n, key, pm, A, xs, ys, zs, lab_s, mat_s, id_s,
-                      cellr, cxs, pos, rec, xf, yf, zf, qx, qy, qz, hs, hsf, (const RecF *)nullptr, posf, err);
+                      cellr, cxs, pos, rec, xf, yf, zf, qx, qy, qz, hs, hsf, (const RecF *)nullptr, posf, err, garbage);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -7,10 +7,11 @@
 //   k_rs_scatter reloads the tile, ranks each key among equal digits in tile order (warp match_any,
 //                per-warp counters, cross-warp prefix), scatters keys and values.
 // The ranking follows tile order, so every pass is stable and the sort is stable overall. In a step the
-// bucket hash (k_hash_hist) builds the first pass's tile histogram as it writes the keys. The launches
-// after the hash are programmatic dependent launches (pdl_launch): each kernel's blocks may be scheduled
-// while its predecessor drains and wait for it in pdl_wait(), which hides the launch gaps of these
-// short kernels.
+// bucket hash (k_hash_hist) builds the first pass's tile histogram as it writes the keys. The hash and
+// the launches after it are programmatic dependent launches (pdl_launch): each kernel's blocks may be
+// scheduled while its predecessor drains and wait for it in pdl_wait(), which hides the launch gaps of
+// these short kernels. In a step the hash counts no particles outside the grid (garbage = null): the
+// reorder reads their count off the sorted keys.
 // Bytes per key per pass: 4 (hist) + 8 read + 8 written (scatter) + 2*4*bins/2048 (counts).
 #include <mutex>
 
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_hash_hist(DevParams P, int64_t n
         const unsigned peers = __match_any_sync(kFullMask, d);
         if (valid && (__ffs(peers) - 1) == l) atomicAdd(&sh[d], (uint32_t)__popc(peers));
     }
-    if (l == 0 && gc) atomicAdd(garbage, (unsigned long long)gc);
+    if (garbage && l == 0 && gc) atomicAdd(garbage, (unsigned long long)gc);
     __syncthreads();
     for (int i = threadIdx.x; i < BINS; i += RS_THREADS) hist[(size_t)i * nblk + blockIdx.x] = sh[i];
 }
@@ -314,11 +315,10 @@ cudaError_t launch_hash_hist(const DevParams &P, int64_t n, const double *x, con
     const int width = bits < dig ? bits : dig;
     const uint32_t dmask = (1u << width) - 1u;
     if (dig > 8)
-        k_hash_hist<9><<<nblk, RS_THREADS, 0, s>>>(P, n, x, y, z, key, val, garbage, dmask, hist, nblk, zero8, nzero8,
-                                                   zero4, nzero4);
-    else
-        k_hash_hist<8><<<nblk, RS_THREADS, 0, s>>>(P, n, x, y, z, key, val, garbage, dmask, hist, nblk, zero8, nzero8,
-                                                   zero4, nzero4);
+        return pdl_launch(k_hash_hist<9>, dim3(nblk), dim3(RS_THREADS), s, P, n, x, y, z, key, val, garbage, dmask,
+                          hist, nblk, zero8, nzero8, zero4, nzero4);
+    return pdl_launch(k_hash_hist<8>, dim3(nblk), dim3(RS_THREADS), s, P, n, x, y, z, key, val, garbage, dmask, hist,
+                      nblk, zero8, nzero8, zero4, nzero4);
     return cudaGetLastError();
 }
 
