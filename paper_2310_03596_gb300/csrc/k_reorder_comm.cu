@@ -478,9 +478,14 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt_exact(DevParams P, DtArgs d, 
     __shared__ unsigned nev, nq;
     __shared__ unsigned short q[DT_THREADS];
     __shared__ DtCand prev_sh;
+    __shared__ unsigned long long wmax_sh[DT_THREADS / 32];
     const unsigned T = *(volatile unsigned *)&d.w->sig;
     const unsigned ncount = *(volatile unsigned *)&d.w->ccount;
     const unsigned hint = *(volatile unsigned *)&d.w->hint;
+    // the largest signal speed this thread evaluates, as the bits of a non-NaN double (the maximum of the
+    // bit patterns, which is what the global word keeps): one atomic per block instead of one per value,
+    // and the same maximum whatever the grouping
+    unsigned long long vmax = 0ull;
     if (threadIdx.x == 0) nev = 0u;
     if (ncount <= d.cap && T >= hint) {
         for (unsigned base = blockIdx.x * DT_THREADS; base < ncount; base += gridDim.x * DT_THREADS) {
@@ -506,7 +511,7 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt_exact(DevParams P, DtArgs d, 
             if (threadIdx.x < m) {
                 const DtCand e = d.cand[base + q[threadIdx.x]];
                 const double v = dt_value(P, e.mat, e.m, e.w, e.vx, e.vy, e.vz, e.E, e.h);
-                if (v == v) atomicMax(&d.w->sigd, (unsigned long long)__double_as_longlong(v));   // v >= 0
+                if (v == v) vmax = max(vmax, (unsigned long long)__double_as_longlong(v));   // v >= 0
             }
             if (threadIdx.x == 0) nev += m;
             __syncthreads();
@@ -516,12 +521,18 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt_exact(DevParams P, DtArgs d, 
             const int m = S.mat[i] < P.nmat ? S.mat[i] : 0;
             const double v = dt_value(P, m, S.f[FM][i], S.f[FW][i], S.f[FVX][i], S.f[FVY][i], S.f[FVZ][i],
                                       S.f[FE][i], P.variable_h ? S.h[i] : 1.0);
-            if (v == v) atomicMax(&d.w->sigd, (unsigned long long)__double_as_longlong(v));
+            if (v == v) vmax = max(vmax, (unsigned long long)__double_as_longlong(v));
         }
         if (threadIdx.x == 0 && blockIdx.x == 0) nev = (unsigned)n;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vmax = max(vmax, __shfl_xor_sync(kFullMask, vmax, o));
+    if ((threadIdx.x & 31) == 0) wmax_sh[threadIdx.x >> 5] = vmax;
     __syncthreads();
     if (threadIdx.x == 0) {
+        unsigned long long bm = 0ull;
+        for (int w = 0; w < DT_THREADS / 32; ++w) bm = max(bm, wmax_sh[w]);
+        if (bm) atomicMax(&d.w->sigd, bm);
         if (nev) atomicAdd(&d.w->eval, nev);
         __threadfence();
         last = atomicAdd(&d.w->done, 1u) == gridDim.x - 1;
