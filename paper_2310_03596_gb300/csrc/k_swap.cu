@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_swap_spec(int64_t n, QuantPar
         if (scnt[q]) atomicAdd(&pairs[q >> 1].spec[q & 1], scnt[q]);
 }
 
-__global__ void __launch_bounds__(SW_THREADS, 1) k_swap_pass(int64_t n, QuantParams Q, double alpha, int K, int nmat,
+__global__ void __launch_bounds__(SW_THREADS, 2) k_swap_pass(int64_t n, QuantParams Q, double alpha, int K, int nmat,
                                                           const SwapPos pos, uint8_t *__restrict__ lab,
                                                           const uint8_t *__restrict__ mat,
                                                           const uint32_t *__restrict__ id, uint16_t *__restrict__ bh,
