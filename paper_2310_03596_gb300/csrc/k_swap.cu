@@ -414,6 +414,9 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_swap_spec(int64_t n, QuantPar
         if (scnt[q]) atomicAdd(&pairs[q >> 1].spec[q & 1], scnt[q]);
 }
 
+// Two blocks per SM (64 registers): the phases between grid barriers are latency-bound streams over the
+// pair's particles, which more resident warps cover better (measured faster than one block per SM at
+// 109 registers, with the same labels).
 __global__ void __launch_bounds__(SW_THREADS, 2) k_swap_pass(int64_t n, QuantParams Q, double alpha, int K, int nmat,
                                                           const SwapPos pos, uint8_t *__restrict__ lab,
                                                           const uint8_t *__restrict__ mat,
