@@ -97,6 +97,9 @@ def test_null_arguments_rejected(lib):
     assert lib.gsph_radix_sort_pairs(None, None, 10, 8, None, 0, None) == gsph.INVALID_ARG
     assert lib.gsph_radix_sort_pairs(None, None, 0, 8, None, 0, None) == gsph.OK
     assert lib.gsph_radix_sort_pairs(None, None, 10, 33, None, 0, None) == gsph.INVALID_ARG
+    assert lib.gsph_set_timing(None, 1) == gsph.INVALID_ARG
+    assert lib.gsph_set_timing_ex(None, 1, 1) == gsph.INVALID_ARG
+    assert lib.gsph_get_timings(None, None) == gsph.INVALID_ARG
 
 
 def test_sort_workspace_grows_with_n(lib):
