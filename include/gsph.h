@@ -244,7 +244,10 @@ gsph_status gsph_get_field(gsph_ctx *ctx, gsph_field f, void *dst, int32_t on_de
  * high-priority stream of the context, forked from `stream` after the swap pass and joined back before
  * the pair kernel; each step's time-step reduction runs on that stream too, beside the next step's
  * hash, sort and reorder, and the last step of the call joins it back. Work enqueued on `stream`
- * afterwards is ordered after all of it. */
+ * afterwards is ordered after all of it. The kernels on `stream` (all but the swap pass's cooperative
+ * kernel) are programmatic dependent launches: each may be scheduled while the work before it on the
+ * stream drains, and waits for that work to complete before touching memory, so stream order is kept
+ * for the caller's own work before and after the call. */
 gsph_status gsph_step(gsph_ctx *ctx, int32_t nsteps, void *stream);
 
 /* Sec. III.A/B: one swap-heuristic pass over all label pairs on the current state, enqueued on
